@@ -1,0 +1,177 @@
+"""Pins of the oracle's time step (§3.1) and Q dynamics (Eqs. 1, 2, 7, 24) against closed forms
+and invariants.
+
+* Passive relaxation of a uniform Q (u = 0, zeta = 0): H = -(A + C tr Q^2) Q with tr Q^2 = 2 q^2,
+  so the discrete map is q_{n+1} = q_n (1 - dt Gamma (A + 2 C q_n^2)) and the director is fixed;
+  the continuous solution for A = 0 is q(t) = q0 / sqrt(1 + 4 Gamma C q0^2 t).
+* Rigid rotation u = w (-y, x): the corrected velocity gradient is exactly [[0, -w], [w, 0]] and
+  the director turns at rate w (this fixes the index convention of grad u).
+* Pure straining with Q = 0: m = 2 c lambda E (traceless part), the flow-aligning term.
+* Trace of the unprojected m: 2 lambda (1 - 2c) Q:E + 2 c lambda div u + Gamma B tr(Q^2)/3.
+* Pair-antisymmetric momentum mode: total momentum is conserved to 1e-12 over 100 steps.
+* Translation invariance of the whole step; ghost-layer and cell-grid searches give the same step.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import sph_inputs as si
+
+
+def _uniform_q_state(nx, q0, theta):
+    ic = si.jittered_lattice(nx, seed=0, jitter=0.0)
+    n = ic["n"]
+    st = {k: ic[k] for k in ("x", "y", "ux", "uy", "rho")}
+    st["q11"] = np.full(n, q0 * math.cos(2 * theta))
+    st["q12"] = np.full(n, q0 * math.sin(2 * theta))
+    return ic, st
+
+
+@pytest.mark.parametrize("A,C", [(0.0, 1.0), (0.5, 1.0), (1.0, 0.0)])
+def test_uniform_q_relaxation_discrete_map(orc, A, C):
+    ic, st = _uniform_q_state(24, 0.9, 0.3)
+    h = 1.3 * ic["dx"]
+    dt, Gamma, nsteps = 2e-3, 0.34, 25
+    P = orc.make_params(h=h, dt=dt, Gamma=Gamma, A=A, C=C, K=0.04, zeta=0.0, eta=1.0, lam=0.7)
+    out, _ = orc.step(P, st, nsteps)
+    q = 0.9
+    for _ in range(nsteps):
+        q = q * (1.0 - dt * Gamma * (A + 2.0 * C * q * q))
+    qn = np.hypot(out["q11"], out["q12"])
+    assert np.abs(qn - q).max() < 1e-14
+    ang = 0.5 * np.arctan2(out["q12"], out["q11"])
+    assert np.abs(ang - 0.3).max() < 1e-14
+    assert np.abs(out["ux"]).max() == 0.0 and np.array_equal(out["x"], st["x"])
+
+
+def test_uniform_q_relaxation_closed_form(orc):
+    # A = 0: q(t) = q0 / sqrt(1 + 4 Gamma C q0^2 t); first-order convergence in dt
+    ic, st = _uniform_q_state(16, 1.0, 1.1)
+    h = 1.3 * ic["dx"]
+    Gamma, C, T = 0.34, 1.0, 0.2
+    errs = []
+    for dt in (4e-3, 2e-3, 1e-3):
+        P = orc.make_params(h=h, dt=dt, Gamma=Gamma, A=0.0, C=C, zeta=0.0)
+        out, _ = orc.step(P, st, int(round(T / dt)))
+        exact = 1.0 / math.sqrt(1.0 + 4.0 * Gamma * C * T)
+        errs.append(abs(np.hypot(out["q11"][0], out["q12"][0]) - exact))
+    assert errs[0] / errs[1] == pytest.approx(2.0, rel=0.05)
+    assert errs[1] / errs[2] == pytest.approx(2.0, rel=0.05)
+    assert errs[2] < 2e-4
+
+
+def test_rigid_rotation_gradient_and_director_rate(orc):
+    ic = si.jittered_lattice(40, seed=1, jitter=0.25)
+    h = 1.3 * ic["dx"]
+    nb = orc.Nbrs(ic["x"], ic["y"], 1.0, h)
+    _, V = orc.volumes(nb)
+    B = orc.correction(nb, V)[:3]
+    w = 0.7
+    ux = -w * (ic["y"] - 0.5)
+    uy = w * (ic["x"] - 0.5)
+    gx = orc.gradient(nb, V, B, ux)
+    gy = orc.gradient(nb, V, B, uy)
+    m = (np.abs(ic["x"] - 0.5) < 0.5 - 3 * h - 1e-3) & (np.abs(ic["y"] - 0.5) < 0.5 - 3 * h - 1e-3)
+    # D[a][b] = du_a/dx_b
+    assert np.abs(gx[m, 0]).max() < 1e-12 and np.abs(gx[m, 1] + w).max() < 1e-12
+    assert np.abs(gy[m, 0] - w).max() < 1e-12 and np.abs(gy[m, 1]).max() < 1e-12
+    P = orc.make_params(h=h, A=0.0, B=0.0, C=0.0, K=0.0, lam=0.9)
+    for theta, q in ((0.2, 1.0), (1.3, 0.6), (2.9, 0.3)):
+        D = [[0.0, -w], [w, 0.0]]
+        m11, m12, tr = orc.q_rate(P, q * math.cos(2 * theta), q * math.sin(2 * theta), D, np.zeros(4))
+        # d/dt (q cos 2t, q sin 2t) at dtheta/dt = w
+        assert m11 == pytest.approx(-2 * w * q * math.sin(2 * theta), abs=1e-14)
+        assert m12 == pytest.approx(2 * w * q * math.cos(2 * theta), abs=1e-14)
+        assert tr == pytest.approx(0.0, abs=1e-14)
+
+
+@pytest.mark.parametrize("c_shift", [1.0 / 3.0, 0.5])
+def test_flow_aligning_term_for_isotropic_q(orc, c_shift):
+    lam = 0.7
+    P = orc.make_params(lam=lam, c_shift=c_shift, A=0.0, B=0.0, C=0.0, K=0.0)
+    D = np.array([[0.3, 0.5], [0.1, -0.2]])
+    E = 0.5 * (D + D.T)
+    m11, m12, _ = orc.q_rate(P, 0.0, 0.0, D, np.zeros(4))
+    Etl = E - 0.5 * np.trace(E) * np.eye(2)
+    assert m11 == pytest.approx(2 * c_shift * lam * Etl[0, 0], abs=1e-15)
+    assert m12 == pytest.approx(2 * c_shift * lam * Etl[0, 1], abs=1e-15)
+
+
+@pytest.mark.parametrize("c_shift", [1.0 / 3.0, 0.5])
+def test_trace_of_unprojected_rate(orc, c_shift):
+    lam, Gamma, Bc = 0.7, 0.34, 0.8
+    P = orc.make_params(lam=lam, c_shift=c_shift, Gamma=Gamma, A=0.3, B=Bc, C=1.0, K=0.04)
+    rng = si.uniform53(21, 60).reshape(10, 6) - 0.5
+    for r in rng:
+        q11, q12 = r[0], r[1]
+        D = np.array([[r[2], r[3]], [r[4], r[5]]])
+        lap = np.array([[1.3, -0.4], [-0.4, -1.3]])
+        _, _, tr = orc.q_rate(P, q11, q12, D, lap)
+        Q = np.array([[q11, q12], [q12, -q11]])
+        E = 0.5 * (D + D.T)
+        trQ2 = 2 * (q11 * q11 + q12 * q12)
+        want = (2 * lam * (1 - 2 * c_shift) * np.sum(Q * E) + 2 * c_shift * lam * np.trace(D)
+                + Gamma * Bc * trQ2 / 3.0)
+        assert tr == pytest.approx(want, abs=1e-14)
+
+
+def _active_state(nx, seed, u_scale=1e-3):
+    ic = si.jittered_lattice(nx, seed=seed)
+    st = {k: ic[k] for k in ("x", "y", "q11", "q12", "rho")}
+    r = si.uniform53(seed + 100, 2 * ic["n"]).reshape(2, ic["n"]) - 0.5
+    st["ux"] = u_scale * r[0]
+    st["uy"] = u_scale * r[1]
+    return ic, st
+
+
+def test_conservative_mode_conserves_momentum(orc):
+    ic, st = _active_state(24, 7)
+    h = 1.3 * ic["dx"]
+    P = orc.make_params(h=h, dt=5e-5, conservative=1, c0_min=0.5, zeta=0.05, eta=0.05)
+    mass = 1.0 / ic["n"]
+    p0 = mass * np.array([st["ux"].sum(), st["uy"].sum()])
+    out, _ = orc.step(P, st, 100)
+    p1 = mass * np.array([out["ux"].sum(), out["uy"].sum()])
+    scale = mass * np.abs(np.concatenate([out["ux"], out["uy"]])).sum()
+    assert np.abs(out["ux"] - st["ux"]).max() > 1e-6   # the velocity field did change
+    assert np.abs(p1 - p0).max() <= 1e-12 * scale
+
+
+def test_translation_invariance(orc):
+    ic, st = _active_state(24, 3)
+    h = 1.3 * ic["dx"]
+    P = orc.make_params(h=h, c0_min=0.2)
+    a, _ = orc.step(P, st, 3)
+    sh = dict(st)
+    sh["x"] = si.wrap_positions(st["x"] + 0.37, 1.0)
+    sh["y"] = si.wrap_positions(st["y"] + 0.81, 1.0)
+    b, _ = orc.step(P, sh, 3)
+    for k in ("ux", "uy", "q11", "q12", "rho"):
+        assert np.abs(a[k] - b[k]).max() <= 1e-12 * max(1.0, np.abs(a[k]).max())
+    dxs = (b["x"] - a["x"] - 0.37 + 0.5) % 1.0 - 0.5
+    dys = (b["y"] - a["y"] - 0.81 + 0.5) % 1.0 - 0.5
+    assert np.abs(dxs).max() < 1e-12 and np.abs(dys).max() < 1e-12
+
+
+def test_search_modes_give_identical_steps(orc):
+    ic, st = _active_state(32, 5)
+    h = 1.3 * ic["dx"]
+    outs = [orc.step(orc.make_params(h=h, c0_min=0.1, nbr_mode=m), st, 2)[0]
+            for m in ("brute", "ghost", "cells")]
+    for k in ("x", "y", "ux", "uy", "q11", "q12", "rho"):
+        assert np.array_equal(outs[0][k], outs[1][k]) and np.array_equal(outs[0][k], outs[2][k])
+
+
+def test_step_records_and_zero_velocity_start(orc):
+    # from rest with Q noise: c0 = 0 so p = 0; u^{1} = dt/2 a with a = -zeta div Q^{1} / rho_hat
+    ic = si.jittered_lattice(32, seed=2)
+    st = {k: ic[k] for k in ("x", "y", "ux", "uy", "q11", "q12", "rho")}
+    h = 1.3 * ic["dx"]
+    P = orc.make_params(h=h)
+    out, rec = orc.step(P, st, 1, record=True)
+    assert rec["c0"] == 0.0 and np.all(rec["p"] == 0.0)
+    assert np.all(rec["nnbr"] == 44)
+    want_ax = -0.05 * rec["divQx"] / rec["rho_hat"]
+    assert np.abs(rec["ax"] - want_ax).max() <= 1e-15 * np.abs(want_ax).max()
+    assert np.abs(out["ux"] - 0.5 * 1e-4 * rec["ax"]).max() <= 1e-18 + 1e-15 * np.abs(out["ux"]).max()
