@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the SPH active-nematic time step on GB300.
+
+Workload: the high-resolution set-up, a 1024 x 1024 jittered lattice (1,048,576 particles) in the
+periodic unit box, h = 1.3 dx, zeta = 0.08, K = 0.02, the other parameters of the paper's 2D
+set-up, FP32 pair arithmetic with FP64 positions, dt = the stable step (viscous limit).  Inputs are
+synthetic (seeded lattice, random director); the working set (~0.5 GB) exceeds the 129 MB L2.
+
+Metric: particle-steps/s (particles x steps / time), with the directed pair interactions per second
+reported beside it.  One step = all kernels of the step (predictor, cell sort, passes A-D).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) each rank advances its own ensemble member (seed = rank) with no collective
+on the data path: weak scaling; the timing is the max over ranks.  ``--impl reference`` times the
+FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = 1024
+PARAMS = dict(zeta=0.08, K=0.02)
+METRIC = "particle-steps/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+KERNEL_SRC = os.path.join(ROOT, "paper_2108_08919_gb300", "csrc", "ann_kernels.cu")
+
+# FP32 flops per directed neighbour pair of each pass (FMA = 2), counted from the formulas:
+#   pair geometry and kernel value/derivative (d, |d|^2, 1/r, b, quintic pieces)   ~32
+#   pass A: geometry + W (24) + the cell-stencil candidate tests (5 flops x ~3.1 candidates/pair)
+#   pass B: + alpha (6), velocity-gradient sums (10), Q-Laplacian sums (16), V F d (4)    = 70
+#   pass C: + Shepard sum (3), div Q sums (13)                                            = 48
+#   pass D: + pressure (7), viscous (12), APD sums (11)                                    = 62
+FLOPS_PER_PAIR = {"pass_a": 24 + 15.5, "pass_b": 70.0, "pass_c": 48.0, "pass_d": 62.0}
+# Algorithmic DRAM bytes per particle of each pass: per-particle arrays read/written once, halo
+# arrays re-read 2.25x (6x6 halo cells per 4x4 tile), neighbour lists (2 B per neighbour).
+BYTES_PER_PARTICLE = {"predict": 56, "cell_scan": 1, "cell_scatter": 12, "cell_order": 76,
+                      "pass_a": 8 * 2.25 + 4 + 4 + 4 + 88, "pass_b": 20 * 2.25 + 16 + 88 + 36,
+                      "pass_c": 16 * 2.25 + 16 + 88 + 16, "pass_d": 20 * 2.25 + 36 + 88 + 48}
+
+
+def _rank_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        reasons = set()
+        for _, _, hw, hwt, swt, swp in rows:
+            for name, v in (("hw_slowdown", hw), ("hw_thermal_slowdown", hwt),
+                            ("sw_thermal_slowdown", swt), ("sw_power_cap", swp)):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def make_params(B, nx):
+    p = B.ann_default_params(n=nx * nx, h=1.3 / nx, zeta=PARAMS["zeta"], K=PARAMS["K"], dt_mode=1)
+    return p
+
+
+def _traffic_for(kernel: str):
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+        with open(KERNEL_SRC, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        if t.get("kernel") == kernel and t.get("source_sha256") == sha:
+            return t.get("dram_bytes_per_launch"), t
+    except (OSError, ValueError):
+        pass
+    return None, None
+
+
+def cpu_baseline(nx: int, budget_s: float = 10.0, max_steps: int = 6):
+    """The FP64 oracle, as it stands, on the host cores: whole steps of the same workload."""
+    import numpy as np  # noqa: F401
+
+    import oracle
+    import sph_inputs as si
+
+    ic = si.jittered_lattice(nx, seed=0)
+    h = 1.3 / nx
+    dt = min(1e-4, 0.125 * h * h / 1.0, 0.125 * h * h / (0.34 * PARAMS["K"]))
+    P = oracle.make_params(h=h, dt=dt, zeta=PARAMS["zeta"], K=PARAMS["K"], nbr_mode="cells")
+    st = {k: ic[k] for k in ("x", "y", "ux", "uy", "q11", "q12", "rho")}
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        st, _ = oracle.step(P, st, 1)
+        steps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": nx * nx * steps / el, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{steps} whole FP64 oracle step(s) of the {nx}x{nx} workload (cell-grid search, "
+                      f"OpenMP over particles), {el:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle on the host cores, timed like our arm: each step one oracle step of a periodic
+    sub-box of the workload (same dx, h, parameters and density), sized so the run stays short."""
+    import oracle
+    import sph_inputs as si
+
+    ws, rank, _ = _rank_info()
+    if rank != 0:
+        return 0
+    oracle.build()
+    h = 1.3 / NX
+    dt = min(1e-4, 0.125 * h * h, 0.125 * h * h / (0.34 * PARAMS["K"]))
+    # calibrate the oracle's cost per particle-step on a 64 x 64 sub-box
+    def sub(side):
+        L = side / NX
+        ic = si.jittered_lattice(side, seed=0, L=L)
+        P = oracle.make_params(L=L, h=h, dt=dt, zeta=PARAMS["zeta"], K=PARAMS["K"], nbr_mode="cells")
+        return P, {k: ic[k] for k in ("x", "y", "ux", "uy", "q11", "q12", "rho")}
+    P, st = sub(64)
+    t0 = time.perf_counter()
+    oracle.step(P, st, 2)
+    per = (time.perf_counter() - t0) / (2 * 64 * 64)
+    total = args.steps + args.warmup
+    side = int(math.sqrt(max(90.0 / (per * max(total, 1)), 32 * 32)))
+    side = max(32, min(NX, side))
+    P, st = sub(side)
+    for _ in range(args.warmup):
+        st, _ = oracle.step(P, st, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st, _ = oracle.step(P, st, 1)
+    el = time.perf_counter() - t0
+    value = side * side * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(1),
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"each step: one FP64 oracle step of a {side}x{side} periodic sub-box "
+                                   f"of the workload (same dx, h, parameters)"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def _config(ws):
+    return {"workload": f"sph_active_nematic_{NX}x{NX}", "particles": NX * NX, "h_over_dx": 1.3,
+            "zeta": PARAMS["zeta"], "K": PARAMS["K"], "dt": "stable (viscous limit)",
+            "box": "periodic unit square", "parallelism": f"ensemble x{ws}" if ws > 1 else "single GPU",
+            "l2": "working set > L2 (no flush needed)"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import sph_inputs as si
+    from paper_2108_08919_gb300 import binding as B
+    from paper_2108_08919_gb300 import build as cuda_build
+
+    ws, rank, local = _rank_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(cuda_build.LIB):
+        cuda_build.build()
+    if dist:
+        dist.barrier()
+    n = NX * NX
+    p = make_params(B, NX)
+    grid = B.ann_grid_info(p)
+    ic = si.jittered_lattice(NX, seed=rank)
+    ctx = B.ann_create(p)
+    stream = torch.cuda.Stream()
+    B.ann_set_stream(ctx, stream)
+    B.ann_set_particles(ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"], ic["rho"])
+    B.ann_step(ctx, max(args.warmup, 3))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            B.ann_step(ctx, args.steps)
+            e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    diag = B.ann_get_diagnostics(ctx)
+    pairs_per_step = diag["nbr_mean"] * n
+    value = ws * n * args.steps / (ms_max * 1e-3)
+
+    # per-kernel device times (CUDA events around each kernel launch, same stream, same state)
+    kprof = B.ann_step_profile(ctx, args.profile_steps)
+    kms = {k: v / args.profile_steps for k, v in kprof.items()}
+    dom = max(kms, key=kms.get)
+
+    # end to end through the C-ABI with host buffers: pinned inputs -> set_particles -> step ->
+    # state fields back to pinned host arrays, every step
+    pin = {k: torch.from_numpy(np.ascontiguousarray(ic[k], dtype=np.float64)).pin_memory().numpy()
+           for k in ("x", "y", "ux", "uy", "q11", "q12", "rho")}
+    outs = {"X": np.float64, "Y": np.float64, "UX": np.float32, "UY": np.float32, "Q11": np.float32,
+            "Q12": np.float32, "DRHO": np.float32}
+    pout = {k: torch.empty(n, dtype=torch.float64 if dt == np.float64 else torch.float32).pin_memory().numpy()
+            for k, dt in outs.items()}
+    h2d = sum(a.nbytes for a in pin.values())
+    d2h = sum(a.nbytes for a in pout.values())
+    e2e_steps = max(5, min(50, args.steps // 20))
+
+    def e2e_iter():
+        B.ann_set_particles(ctx, pin["x"], pin["y"], pin["ux"], pin["uy"], pin["q11"], pin["q12"], pin["rho"])
+        B.ann_step(ctx, 1)
+        for k in outs:
+            B.ann_get_field(ctx, k, n, out=pout[k])
+
+    e2e_iter()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_iter()
+    torch.cuda.synchronize()
+    e2e_el = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_el], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = ws * n * e2e_steps / float(e2e_t.item())
+    B.ann_destroy(ctx)
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    peaks, src = _peaks()
+    clocks = clk.summary()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    flops_launch = FLOPS_PER_PAIR.get(dom, 0.0) * pairs_per_step
+    achieved_tf = flops_launch / (kms[dom] * 1e-3) / 1e12 if kms[dom] > 0 else 0.0
+    peak_tf = fp32_peak_tflops(sm_mhz)
+    traffic, _ = _traffic_for(dom)
+    bytes_launch = BYTES_PER_PARTICLE.get(dom, 0) * n
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 positions and reductions)",
+        "data": "synthetic", "config": _config(ws),
+        "pair_interactions_per_s": pairs_per_step * ws * args.steps / (ms_max * 1e-3),
+        "dt": grid.dt_effective,
+        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved_tf,
+                     "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
+                     "traffic": traffic,
+                     "peak_source": f"FP32 152 SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz "
+                                    f"(sm_max_mhz of MEASURED_PEAKS.json, {src})",
+                     "flops_per_launch": flops_launch, "avg_launch_ms": kms[dom],
+                     "hbm_achieved_gbs": bytes_launch / (kms[dom] * 1e-3) / 1e9,
+                     "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                     "hbm_frac": bytes_launch / (kms[dom] * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)},
+        "kernel_ms": kms,
+        "kernel_share": {k: v / sum(kms.values()) for k, v in kms.items()},
+        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "gpu_launches": args.steps * B.ann_kernel_count(),
+        "clocks": clocks,
+        "diag": {"nbr_mean": diag["nbr_mean"], "error_bits": diag["error_bits"],
+                 "band_checks": diag["band_checks"], "max_speed": diag["max_speed"]},
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(NX)
+    print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--profile-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,235 @@
+/*
+ * ann.h -- C-ABI of the GB300 (sm_103a) SPH active-nematic solver.
+ *
+ * The library advances the weakly compressible SPH discretisation of the Beris-Edwards active
+ * nematic equations of Saghatchi, Kolukisa and Yildiz (arXiv 2108.08919) on one GPU: a 2D periodic
+ * box of side L holding n particles with position r (FP64), velocity u, order parameter
+ * Q = [[q11, q12], [q12, -q11]], density rho and the previous acceleration a (FP32 on the device).
+ *
+ * One step (ann_step) is the paper's modified-Euler predictor-corrector (§3.1, Eq. 27) with one
+ * neighbour search at the projected configuration, evaluated as:
+ *   predictor and cell keys    u' = u + dt/2 a, r' = r + dt/2 u' (re-inserted into [0, L), Eq. 30)
+ *   cell sort                  particles binned into square cells of side >= 3h (§4); periodic
+ *                              images of cells replace the paper's ghost particles (Eq. 30)
+ *   pass A                     neighbour lists (|d|^2 < (3h)^2), sum_j W_ij and V = 1/sum (Eqs. 18-19)
+ *   pass B                     correction tensor and B = alpha^-1 (Eq. 22), corrected velocity
+ *                              gradient (Eq. 20), continuity (Eq. 25), Q Laplacian (Eq. 21), molecular
+ *                              field (Eq. 7), Q rate (Eqs. 2, 24) and Q^{n+1}
+ *   pass C                     density filter (Eq. 28), equation of state (Eq. 26) with
+ *                              c0 = max(10 max|u'|, c0_min), divergence of Q^{n+1}
+ *   pass D                     momentum (Eq. 23, active term -zeta/rho div Q), corrector, artificial
+ *                              particle displacement (Eq. 29), re-insertion
+ *
+ * Conventions for every call:
+ *   - Return value: ANN_OK (0) or a negative ANN_ERR_* code.  No exception crosses the ABI.  The
+ *     text of the last error of a context is available from ann_last_error.
+ *   - Pointers are plain host or device pointers, as each call states.  Host buffers are owned by
+ *     the caller and only read or written during the call.  A context owns all device memory it
+ *     allocates (cudaMalloc on the device current at ann_create) and frees it in ann_destroy.
+ *   - Per-particle arrays exchanged through the ABI are indexed by particle ID 0..n-1, the order
+ *     in which ann_set_particles received them; the device keeps particles in cell order
+ *     internally and un-permutes on output.
+ *   - Work is issued on the context's stream (ann_set_stream; default: a stream the context
+ *     creates).  Calls that return data or a status synchronise that stream before returning.
+ */
+#ifndef ANN_H
+#define ANN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ANN_ABI_VERSION 1
+
+/* Status codes. */
+#define ANN_OK 0
+#define ANN_ERR_INVALID_ARG (-1)     /* a parameter or argument is out of its stated range */
+#define ANN_ERR_OOM (-2)             /* device or host allocation failed */
+#define ANN_ERR_CUDA (-3)            /* a CUDA runtime call failed (text in ann_last_error) */
+#define ANN_ERR_CELL_OVERFLOW (-4)   /* a cell or a tile halo held more particles than the kernels stage */
+#define ANN_ERR_NBR_OVERFLOW (-5)    /* a particle had more than ANN_MAX_NEIGHBORS neighbours */
+#define ANN_ERR_NONFINITE (-6)       /* a position, velocity, Q or density became NaN or infinite */
+#define ANN_ERR_SINGULAR_ALPHA (-7)  /* det(alpha) <= 0 for some particle (Eq. 22 not invertible) */
+#define ANN_ERR_IO (-8)              /* checkpoint file could not be written or read */
+#define ANN_ERR_STATE (-9)           /* call out of order (e.g. ann_step before ann_set_particles) */
+#define ANN_ERR_NOT_AVAILABLE (-10)  /* no CUDA device */
+
+/* Limits of the device kernels. */
+#define ANN_MAX_NEIGHBORS 64         /* neighbours per particle */
+#define ANN_MAX_PER_CELL 64          /* particles per cell */
+
+/* momentum_mode */
+#define ANN_MOMENTUM_PAPER 0         /* Eq. 23 as printed: B-corrected sums, particle volumes V */
+#define ANN_MOMENTUM_CONSERVATIVE 1  /* pair-antisymmetric forms, fixed masses rho0 L^2 / n, no B */
+
+/* dt_mode */
+#define ANN_DT_FIXED 0               /* dt as given */
+#define ANN_DT_STABLE 1              /* dt = min(dt, 0.125 h^2/nu, 0.125 h^2/(Gamma K), 0.25 h/c0_min), fixed at create */
+
+/*
+ * Parameters (plain data).  Names follow the paper: rho0 reference density, eta dynamic viscosity
+ * (nu = eta/rho0), Gamma rotational diffusivity, lambda tumbling parameter, A, B, C Landau-de Gennes
+ * coefficients, K elastic constant, zeta activity (> 0 extensile), gamma_eos EoS exponent (7),
+ * beta density-filter coefficient (1 = Shepard), h smoothing length (support 3h).
+ * c0_min: floor of the sound speed c0 = max(10 max|u'|, c0_min).
+ * c_shift: c in Q + c I of the co-rotation term (Eq. 2 prints 1/3).
+ * q_new_in_momentum: 1 uses Q^{n+1} in the active force (text order of §3.1), 0 uses Q^n.
+ * apd: 1 applies the artificial particle displacement of Eq. 29.
+ * Valid ranges (ann_validate_params): n >= 1, L > 0, 0 < h, 3h <= L/3 (at least three cells across
+ * the box), dt > 0, rho0 > 0, eta >= 0, Gamma >= 0, gamma_eos > 0, 0 <= beta <= 1, c0_min >= 0, and
+ * at most ANN_MAX_NEIGHBORS expected neighbours (pi (3h)^2 n / L^2 <= 0.85 ANN_MAX_NEIGHBORS).
+ */
+typedef struct ann_params {
+    int64_t n;
+    double L, h, dt;
+    double rho0, eta, Gamma, lambda, A, B, C, K, zeta;
+    double gamma_eos, beta, c0_min, c_shift;
+    int32_t apd;
+    int32_t momentum_mode;
+    int32_t q_new_in_momentum;
+    int32_t dt_mode;
+    int32_t reserved[4];
+} ann_params;
+
+/* Cell grid and step size a parameter set implies (host computation, no GPU needed). */
+typedef struct ann_grid {
+    int32_t cells_per_side;      /* n_c = floor(L / (3h (1 + 1e-9))) */
+    int32_t tiles_per_side;      /* ceil(n_c / 4): one CUDA block per 4 x 4 cells */
+    double cell_size;            /* L / n_c >= 3h */
+    double dt_effective;         /* dt after dt_mode */
+    double expected_neighbors;   /* pi (3h)^2 n / L^2 */
+    int64_t device_bytes;        /* device memory ann_create will allocate */
+} ann_grid;
+
+/* Diagnostics, FP64 reductions over all particles. */
+typedef struct ann_diag {
+    double t;                    /* simulated time */
+    int64_t step;                /* completed steps */
+    double momentum[2];          /* sum_i m_i u_i; m_i = rho_i V_i (paper mode) or rho0 L^2/n */
+    double kinetic_energy;       /* 1/2 <|u|^2>, the spatial mean of the paper's Eq. 31 */
+    double max_speed;            /* max |u| */
+    double c0;                   /* sound speed of the last step */
+    double mass;                 /* sum_i m_i */
+    double mean_q;               /* mean nematic order q = sqrt(q11^2 + q12^2) */
+    double nbr_mean;             /* mean neighbour count of the last evaluation */
+    int32_t nbr_min, nbr_max;
+    double min_det_alpha;        /* smallest det(alpha) of the last evaluation */
+    uint32_t error_bits;         /* sticky device error bits (see ann_status_string) */
+    int32_t reserved;
+    uint64_t band_checks;        /* pair tests that fell in the FP32 uncertainty band and were decided in FP64 */
+} ann_diag;
+
+/* Field identifiers for ann_get_field.  Element type: FP64 for ANN_FIELD_X/Y, int32 for
+ * ANN_FIELD_NNBR, FP32 otherwise.  Fields after ANN_FIELD_AY are values of the last evaluated
+ * step (at the midpoint configuration); the GRADU/LAPQ/APD ones need ann_set_record(ctx, 1). */
+enum ann_field {
+    ANN_FIELD_X = 0, ANN_FIELD_Y, ANN_FIELD_UX, ANN_FIELD_UY, ANN_FIELD_Q11, ANN_FIELD_Q12,
+    ANN_FIELD_DRHO,        /* rho/rho0 - 1 */
+    ANN_FIELD_AX, ANN_FIELD_AY,
+    ANN_FIELD_SUMW, ANN_FIELD_V, ANN_FIELD_B11, ANN_FIELD_B12, ANN_FIELD_B22,
+    ANN_FIELD_K,           /* continuity rate k/rho0 (Eq. 25) */
+    ANN_FIELD_DRHO_HALF,   /* rho^{n+1/2}/rho0 - 1 */
+    ANN_FIELD_DRHO_HAT,    /* filtered density / rho0 - 1 (Eq. 28) */
+    ANN_FIELD_P,           /* pressure (Eq. 26) */
+    ANN_FIELD_DIVQX, ANN_FIELD_DIVQY,
+    ANN_FIELD_NNBR,
+    ANN_FIELD_GRADU_XX, ANN_FIELD_GRADU_XY, ANN_FIELD_GRADU_YX, ANN_FIELD_GRADU_YY, /* du_a/dx_b */
+    ANN_FIELD_LAPQ11, ANN_FIELD_LAPQ12,
+    ANN_FIELD_APDX, ANN_FIELD_APDY,
+    ANN_FIELD_COUNT
+};
+
+typedef struct ann_ctx ann_ctx;
+
+/* ABI version (ANN_ABI_VERSION). */
+int ann_version(void);
+
+/* Human-readable text of a status code. Static storage; never NULL. */
+const char *ann_status_string(int status);
+
+/* Fill *p with the paper's 2D set-up used as default: L = 1, h = 1.3 dx for n = 64 x 64,
+ * dt = 1e-4, rho0 = 1, eta = 1, Gamma = 0.34, lambda = 0.7, A = B = 0, C = 1, K = 0.04, zeta = 0.05,
+ * gamma_eos = 7, beta = 1, c0_min = 0, c_shift = 1/3, apd = 1, paper momentum, Q^{n+1} in the
+ * momentum, fixed dt.  Host only. */
+int ann_default_params(ann_params *p);
+
+/* Check every field of *p against the ranges stated above.  Host only, no GPU needed.
+ * Returns ANN_OK or ANN_ERR_INVALID_ARG. */
+int ann_validate_params(const ann_params *p);
+
+/* Cell grid, tile count, effective dt and device memory of *p.  Host only. */
+int ann_grid_info(const ann_params *p, ann_grid *out);
+
+/* Create a context on the current CUDA device: validates *p, allocates all device buffers and
+ * captures one step as a CUDA graph.  *out receives the context (NULL on failure).
+ * Errors: INVALID_ARG, OOM, CUDA, NOT_AVAILABLE. */
+int ann_create(const ann_params *p, ann_ctx **out);
+
+/* Free all device memory of ctx.  NULL is ignored. */
+void ann_destroy(ann_ctx *ctx);
+
+/* Issue subsequent work on `stream` (a cudaStream_t of the context's device; NULL selects the
+ * legacy default stream).  The context's own stream is used until this is called. */
+int ann_set_stream(ann_ctx *ctx, void *stream);
+
+/* Load the state.  n must equal the n of ann_create.  Arrays are FP64 of length n in particle-ID
+ * order: x, y positions (re-inserted into [0, L)), ux, uy velocity, q11, q12 order parameter, rho
+ * density (NULL: rho0).  a^0 is set to zero, the step counter and t to zero.  is_device = 0: host
+ * pointers; 1: device pointers on the context's device.  Errors: INVALID_ARG (n mismatch, NULL
+ * required pointer), NONFINITE (a NaN or infinite entry), CUDA. */
+int ann_set_particles(ann_ctx *ctx, int64_t n, const double *x, const double *y, const double *ux,
+                      const double *uy, const double *q11, const double *q12, const double *rho,
+                      int is_device);
+
+/* Advance nsteps >= 0 steps (one CUDA-graph launch per step) and synchronise.  Errors:
+ * STATE (no particles), CELL_OVERFLOW, NBR_OVERFLOW, NONFINITE, SINGULAR_ALPHA (device error
+ * bits; once one is raised the remaining kernels of the call return without work, so the state is
+ * that of the failing step, partly updated; ann_get_diagnostics reports the bits; ann_set_particles
+ * or ann_load_state clears them), CUDA. */
+int ann_step(ann_ctx *ctx, int64_t nsteps);
+
+/* Advance nsteps steps launching the kernels one by one with a CUDA event before and after each,
+ * and add the total device time of each kernel (ms) to kernel_ms[ann_kernel_count()] (the caller
+ * zeroes it).  Same physics and errors as ann_step. */
+int ann_step_profile(ann_ctx *ctx, int64_t nsteps, double *kernel_ms);
+
+/* Number of kernels in one step, and the name of kernel k (static storage; NULL if out of range). */
+int ann_kernel_count(void);
+const char *ann_kernel_name(int k);
+
+/* Record the GRADU, LAPQ and APD intermediates in later steps (on = 1) or not (0, default).
+ * Recording adds stores to passes B and D and re-captures the step graph. */
+int ann_set_record(ann_ctx *ctx, int on);
+
+/* Copy field `field` (enum ann_field) in particle-ID order to dst, which holds `bytes` >= n times
+ * the element size.  dst_is_device = 0: host pointer; 1: device pointer.  Errors: INVALID_ARG
+ * (unknown field, short buffer), STATE (no particles), CUDA. */
+int ann_get_field(ann_ctx *ctx, int field, void *dst, int64_t bytes, int dst_is_device);
+
+/* FP64 diagnostics of the current state.  Errors: STATE, CUDA. */
+int ann_get_diagnostics(ann_ctx *ctx, ann_diag *out);
+
+/* Neighbour lists of the current positions (no time advance): builds the cell sort and pass A at
+ * the present configuration and writes them as CSR in particle IDs, each row ascending: rowptr has
+ * n+1 entries (host), cols `cap` entries (host).  With cols == NULL only rowptr is written, so a
+ * caller can size cols from rowptr[n].  Errors: INVALID_ARG (cap < rowptr[n]), STATE, the step's
+ * device errors, CUDA, OOM. */
+int ann_get_neighbors(ann_ctx *ctx, int64_t *rowptr, int32_t *cols, int64_t cap);
+
+/* Write / read the full state (positions, velocities, Q, density, a, internal particle order, t,
+ * step count, parameters) to / from a binary file.  A loaded state continues bit-identically to an
+ * uninterrupted run.  ann_load_state requires a context created with the same n.  Errors: IO,
+ * INVALID_ARG (format or n mismatch), STATE, CUDA. */
+int ann_save_state(ann_ctx *ctx, const char *path);
+int ann_load_state(ann_ctx *ctx, const char *path);
+
+/* Text of the last error raised on ctx (empty string if none; never NULL). */
+const char *ann_last_error(ann_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ANN_H */

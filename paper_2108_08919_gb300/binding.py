@@ -1,0 +1,262 @@
+"""Python binding of the C-ABI in ``include/ann.h`` (ctypes, argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does nothing but convert
+arguments: numpy arrays are passed as host pointers, CUDA tensors (anything with ``data_ptr()`` and
+``is_cuda``) as device pointers.  All arithmetic of the method runs in the CUDA library
+``_lib/libann.so``; if that library is missing this module raises instead of falling back to any
+other implementation.  Negative status codes raise :class:`AnnError`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libann.so")
+
+MAX_NEIGHBORS = 64
+MOMENTUM_PAPER, MOMENTUM_CONSERVATIVE = 0, 1
+DT_FIXED, DT_STABLE = 0, 1
+
+FIELDS = ["X", "Y", "UX", "UY", "Q11", "Q12", "DRHO", "AX", "AY", "SUMW", "V", "B11", "B12", "B22",
+          "K", "DRHO_HALF", "DRHO_HAT", "P", "DIVQX", "DIVQY", "NNBR", "GRADU_XX", "GRADU_XY",
+          "GRADU_YX", "GRADU_YY", "LAPQ11", "LAPQ12", "APDX", "APDY"]
+FIELD_ID = {name: k for k, name in enumerate(FIELDS)}
+
+
+def field_dtype(name: str):
+    if name in ("X", "Y"):
+        return np.float64
+    if name == "NNBR":
+        return np.int32
+    return np.float32
+
+
+class ann_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64)] + [(k, ctypes.c_double) for k in (
+        "L", "h", "dt", "rho0", "eta", "Gamma", "lambda_", "A", "B", "C", "K", "zeta", "gamma_eos",
+        "beta", "c0_min", "c_shift")] + [(k, ctypes.c_int32) for k in (
+        "apd", "momentum_mode", "q_new_in_momentum", "dt_mode")] + [("reserved", ctypes.c_int32 * 4)]
+
+
+class ann_grid(ctypes.Structure):
+    _fields_ = [("cells_per_side", ctypes.c_int32), ("tiles_per_side", ctypes.c_int32),
+                ("cell_size", ctypes.c_double), ("dt_effective", ctypes.c_double),
+                ("expected_neighbors", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+
+class ann_diag(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("step", ctypes.c_int64), ("momentum", ctypes.c_double * 2),
+                ("kinetic_energy", ctypes.c_double), ("max_speed", ctypes.c_double),
+                ("c0", ctypes.c_double), ("mass", ctypes.c_double), ("mean_q", ctypes.c_double),
+                ("nbr_mean", ctypes.c_double), ("nbr_min", ctypes.c_int32),
+                ("nbr_max", ctypes.c_int32), ("min_det_alpha", ctypes.c_double),
+                ("error_bits", ctypes.c_uint32), ("reserved", ctypes.c_int32),
+                ("band_checks", ctypes.c_uint64)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "momentum")}
+        d["momentum"] = (self.momentum[0], self.momentum[1])
+        return d
+
+
+class AnnError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.POINTER
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library {LIB_PATH} is missing; build it with "
+                           "paper_2108_08919_gb300.build.build() (nvcc, sm_103a)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+    sig = {
+        "ann_version": (i32, []),
+        "ann_status_string": (ctypes.c_char_p, [i32]),
+        "ann_default_params": (i32, [_P(ann_params)]),
+        "ann_validate_params": (i32, [_P(ann_params)]),
+        "ann_grid_info": (i32, [_P(ann_params), _P(ann_grid)]),
+        "ann_create": (i32, [_P(ann_params), _P(vp)]),
+        "ann_destroy": (None, [vp]),
+        "ann_set_stream": (i32, [vp, vp]),
+        "ann_set_particles": (i32, [vp, i64, dp, dp, dp, dp, dp, dp, dp, i32]),
+        "ann_step": (i32, [vp, i64]),
+        "ann_step_profile": (i32, [vp, i64, _P(ctypes.c_double)]),
+        "ann_kernel_count": (i32, []),
+        "ann_kernel_name": (ctypes.c_char_p, [i32]),
+        "ann_set_record": (i32, [vp, i32]),
+        "ann_get_field": (i32, [vp, i32, vp, i64, i32]),
+        "ann_get_diagnostics": (i32, [vp, _P(ann_diag)]),
+        "ann_get_neighbors": (i32, [vp, _P(ctypes.c_int64), _P(ctypes.c_int32), i64]),
+        "ann_save_state": (i32, [vp, ctypes.c_char_p]),
+        "ann_load_state": (i32, [vp, ctypes.c_char_p]),
+        "ann_last_error": (ctypes.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int, ctx=None, what: str = ""):
+    if status < 0:
+        detail = ""
+        if ctx is not None:
+            detail = lib().ann_last_error(ctx).decode()
+        text = lib().ann_status_string(status).decode()
+        raise AnnError(status, f"{what}: {text}" + (f" ({detail})" if detail else ""))
+    return status
+
+
+def _ptr(a):
+    """(pointer, is_device, keepalive) of a numpy array or CUDA tensor; None passes NULL."""
+    if a is None:
+        return None, None, None
+    if hasattr(a, "data_ptr") and getattr(a, "is_cuda", False):
+        return ctypes.c_void_p(a.data_ptr()), True, a
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    return arr.ctypes.data_as(ctypes.c_void_p), False, arr
+
+
+# ------------------------------------------------------------------------------------------------
+# entry points
+# ------------------------------------------------------------------------------------------------
+
+def ann_version() -> int:
+    return lib().ann_version()
+
+
+def ann_status_string(status: int) -> str:
+    return lib().ann_status_string(status).decode()
+
+
+def ann_default_params(**overrides) -> ann_params:
+    p = ann_params()
+    _check(lib().ann_default_params(ctypes.byref(p)), what="ann_default_params")
+    for k, v in overrides.items():
+        setattr(p, "lambda_" if k == "lambda" else k, v)
+    return p
+
+
+def ann_validate_params(p: ann_params) -> int:
+    return lib().ann_validate_params(ctypes.byref(p))
+
+
+def ann_grid_info(p: ann_params) -> ann_grid:
+    g = ann_grid()
+    _check(lib().ann_grid_info(ctypes.byref(p), ctypes.byref(g)), what="ann_grid_info")
+    return g
+
+
+def ann_create(p: ann_params) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(lib().ann_create(ctypes.byref(p), ctypes.byref(ctx)), what="ann_create")
+    return ctx
+
+
+def ann_destroy(ctx) -> None:
+    if ctx:
+        lib().ann_destroy(ctx)
+
+
+def ann_set_stream(ctx, stream) -> None:
+    """``stream``: an integer cudaStream_t handle or an object with ``cuda_stream``."""
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(lib().ann_set_stream(ctx, ctypes.c_void_p(int(handle) if handle else 0)), ctx, "ann_set_stream")
+
+
+def ann_set_particles(ctx, x, y, ux, uy, q11, q12, rho=None) -> None:
+    """FP64 arrays (numpy on the host, or CUDA tensors on the device) in particle-ID order."""
+    arrs = [_ptr(a) for a in (x, y, ux, uy, q11, q12, rho)]
+    dev = {d for _, d, _ in arrs if d is not None}
+    if len(dev) != 1:
+        raise ValueError("inputs must all be host arrays or all CUDA tensors")
+    n = int(len(arrs[0][2]) if not hasattr(arrs[0][2], "numel") else arrs[0][2].numel())
+    _check(lib().ann_set_particles(ctx, n, *[a[0] for a in arrs], int(dev.pop())), ctx,
+           "ann_set_particles")
+
+
+def ann_step(ctx, nsteps: int) -> None:
+    _check(lib().ann_step(ctx, int(nsteps)), ctx, "ann_step")
+
+
+def ann_kernel_count() -> int:
+    return lib().ann_kernel_count()
+
+
+def ann_kernel_name(k: int) -> str:
+    return lib().ann_kernel_name(k).decode()
+
+
+def ann_step_profile(ctx, nsteps: int) -> dict:
+    """Per-kernel device time (ms, summed over the steps), from CUDA events around each kernel."""
+    k = ann_kernel_count()
+    ms = (ctypes.c_double * k)()
+    _check(lib().ann_step_profile(ctx, int(nsteps), ms), ctx, "ann_step_profile")
+    return {ann_kernel_name(i): ms[i] for i in range(k)}
+
+
+def ann_set_record(ctx, on: bool) -> None:
+    _check(lib().ann_set_record(ctx, int(bool(on))), ctx, "ann_set_record")
+
+
+def ann_get_field(ctx, field: str, n: int, out=None):
+    """Field ``field`` (a name of FIELDS) in particle-ID order: a new numpy array, or written into
+    ``out`` (numpy array or CUDA tensor of the field's dtype and length n)."""
+    dt = field_dtype(field)
+    if out is None:
+        out = np.empty(n, dtype=dt)
+    if hasattr(out, "data_ptr") and getattr(out, "is_cuda", False):
+        ptr, dev, nbytes = out.data_ptr(), 1, out.numel() * out.element_size()
+    else:
+        if out.dtype != dt or not out.flags.c_contiguous:
+            raise ValueError(f"out must be a contiguous {np.dtype(dt).name} array")
+        ptr, dev, nbytes = out.ctypes.data, 0, out.nbytes
+    _check(lib().ann_get_field(ctx, FIELD_ID[field], ctypes.c_void_p(ptr), nbytes, dev), ctx,
+           f"ann_get_field({field})")
+    return out
+
+
+def ann_get_diagnostics(ctx) -> dict:
+    d = ann_diag()
+    _check(lib().ann_get_diagnostics(ctx, ctypes.byref(d)), ctx, "ann_get_diagnostics")
+    return d.as_dict()
+
+
+def ann_get_neighbors(ctx, n: int):
+    """CSR neighbour lists of the current positions: (rowptr int64[n+1], cols int32[nnz])."""
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    L = lib()
+    _check(L.ann_get_neighbors(ctx, rowptr.ctypes.data_as(_P(ctypes.c_int64)), None, 0), ctx,
+           "ann_get_neighbors")
+    cols = np.zeros(max(int(rowptr[-1]), 1), dtype=np.int32)
+    _check(L.ann_get_neighbors(ctx, rowptr.ctypes.data_as(_P(ctypes.c_int64)),
+                               cols.ctypes.data_as(_P(ctypes.c_int32)), cols.size), ctx,
+           "ann_get_neighbors")
+    return rowptr, cols[: int(rowptr[-1])]
+
+
+def ann_save_state(ctx, path: str) -> None:
+    _check(lib().ann_save_state(ctx, os.fsencode(path)), ctx, "ann_save_state")
+
+
+def ann_load_state(ctx, path: str) -> None:
+    _check(lib().ann_load_state(ctx, os.fsencode(path)), ctx, "ann_load_state")
+
+
+def ann_last_error(ctx) -> str:
+    return lib().ann_last_error(ctx).decode()

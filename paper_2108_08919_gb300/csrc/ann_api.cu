@@ -1,0 +1,682 @@
+// C-ABI of the SPH active-nematic solver: context, device buffers, CUDA-graph step, I/O.
+#include "../../include/ann.h"
+#include "ann_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace ann;
+
+struct ann_ctx {
+    ann_params prm{};
+    DevParams P{};
+    Bufs b{};
+    int device = 0;
+    cudaStream_t own = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool have_particles = false;
+    int64_t steps = 0;
+    double t = 0.0;
+    std::string last_err;
+    std::vector<void *> allocs;
+    void *tmp = nullptr;          // staging: max(7 n doubles, MAXN n ints)
+    double *diag_part = nullptr;  // diag_blocks(n) x NDIAG
+    double *diag_out = nullptr;   // NDIAG
+    uint32_t *h_err = nullptr;    // pinned
+};
+
+namespace {
+
+constexpr double kCellSlack = 1e-9;
+
+const char *status_text(int s)
+{
+    switch (s) {
+    case ANN_OK: return "ok";
+    case ANN_ERR_INVALID_ARG: return "invalid argument";
+    case ANN_ERR_OOM: return "out of memory";
+    case ANN_ERR_CUDA: return "CUDA error";
+    case ANN_ERR_CELL_OVERFLOW: return "cell or tile halo overflow";
+    case ANN_ERR_NBR_OVERFLOW: return "neighbour list overflow";
+    case ANN_ERR_NONFINITE: return "non-finite state";
+    case ANN_ERR_SINGULAR_ALPHA: return "singular correction tensor";
+    case ANN_ERR_IO: return "checkpoint I/O error";
+    case ANN_ERR_STATE: return "call out of order";
+    case ANN_ERR_NOT_AVAILABLE: return "no CUDA device";
+    default: return "unknown status";
+    }
+}
+
+int fail(ann_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->last_err = msg;
+    return code;
+}
+
+int cuda_fail(ann_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, e == cudaErrorMemoryAllocation ? ANN_ERR_OOM : ANN_ERR_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+int cells_per_side(const ann_params &p)
+{
+    return (int)std::floor(p.L / (3.0 * p.h * (1.0 + kCellSlack)));
+}
+
+double effective_dt(const ann_params &p)
+{
+    double dt = p.dt;
+    if (p.dt_mode == ANN_DT_STABLE) {
+        double nu = p.eta / p.rho0;
+        if (nu > 0.0) dt = std::min(dt, 0.125 * p.h * p.h / nu);
+        if (p.Gamma * p.K > 0.0) dt = std::min(dt, 0.125 * p.h * p.h / (p.Gamma * p.K));
+        if (p.c0_min > 0.0) dt = std::min(dt, 0.25 * p.h / p.c0_min);
+    }
+    return dt;
+}
+
+int64_t device_bytes(const ann_params &p)
+{
+    int64_t n = p.n, nc = cells_per_side(p), ncell = nc * nc;
+    int64_t per = 2 * 8 + 7 * 4 + 4           // S
+                  + 2 * 8 + 7 * 4 + 4         // M
+                  + 3 * 4                     // key, rank, perm
+                  + (MAXN / 2) * 4 + 4        // lists, counts
+                  + 11 * 4                    // intermediates
+                  + 8 * 4;                    // recording
+    int64_t tmp = std::max<int64_t>(7 * 8, MAXN * 4) * n;
+    return per * n + tmp + 2 * 4 * (ncell + 1) + 4096;
+}
+
+int validate(const ann_params *p, std::string &why)
+{
+    if (!p) { why = "null parameters"; return ANN_ERR_INVALID_ARG; }
+    if (p->n < 1 || p->n > (int64_t)1 << 30) { why = "n must be in [1, 2^30]"; return ANN_ERR_INVALID_ARG; }
+    if (!finite_pos(p->L) || !finite_pos(p->h) || !finite_pos(p->dt) || !finite_pos(p->rho0)) {
+        why = "L, h, dt and rho0 must be finite and positive";
+        return ANN_ERR_INVALID_ARG;
+    }
+    if (cells_per_side(*p) < 3) { why = "need at least three cells of side 3h across the box"; return ANN_ERR_INVALID_ARG; }
+    const double nonneg[] = {p->eta, p->Gamma, p->gamma_eos, p->c0_min};
+    for (double v : nonneg)
+        if (!std::isfinite(v) || v < 0.0) { why = "eta, Gamma, gamma_eos, c0_min must be finite and >= 0"; return ANN_ERR_INVALID_ARG; }
+    if (!(p->gamma_eos > 0.0)) { why = "gamma_eos must be > 0"; return ANN_ERR_INVALID_ARG; }
+    if (!(p->beta >= 0.0 && p->beta <= 1.0)) { why = "beta must be in [0, 1]"; return ANN_ERR_INVALID_ARG; }
+    const double fin[] = {p->lambda, p->A, p->B, p->C, p->K, p->zeta, p->c_shift};
+    for (double v : fin)
+        if (!std::isfinite(v)) { why = "lambda, A, B, C, K, zeta, c_shift must be finite"; return ANN_ERR_INVALID_ARG; }
+    if (p->apd != 0 && p->apd != 1) { why = "apd must be 0 or 1"; return ANN_ERR_INVALID_ARG; }
+    if (p->momentum_mode != ANN_MOMENTUM_PAPER && p->momentum_mode != ANN_MOMENTUM_CONSERVATIVE) {
+        why = "unknown momentum_mode";
+        return ANN_ERR_INVALID_ARG;
+    }
+    if (p->q_new_in_momentum != 0 && p->q_new_in_momentum != 1) { why = "q_new_in_momentum must be 0 or 1"; return ANN_ERR_INVALID_ARG; }
+    if (p->dt_mode != ANN_DT_FIXED && p->dt_mode != ANN_DT_STABLE) { why = "unknown dt_mode"; return ANN_ERR_INVALID_ARG; }
+    double R = 3.0 * p->h;
+    double expected = M_PI * R * R * (double)p->n / (p->L * p->L);
+    if (expected > 0.85 * MAXN) { why = "too many expected neighbours for the list capacity"; return ANN_ERR_INVALID_ARG; }
+    // a 4 x 4-cell tile plus halo must fit its staging buffer with room for fluctuations
+    double cell = p->L / cells_per_side(*p);
+    double per_cell = (double)p->n * cell * cell / (p->L * p->L);
+    if (per_cell * NHC > 0.7 * HCAP || per_cell > 0.6 * MAXC) {
+        why = "too many particles per cell (3h is large against the particle spacing)";
+        return ANN_ERR_INVALID_ARG;
+    }
+    return ANN_OK;
+}
+
+DevParams make_dev(const ann_params &p)
+{
+    DevParams d{};
+    d.n = (int)p.n;
+    d.nc = cells_per_side(p);
+    d.ncell = d.nc * d.nc;
+    d.tiles = (d.nc + TILE - 1) / TILE;
+    d.apd = p.apd;
+    d.conservative = p.momentum_mode == ANN_MOMENTUM_CONSERVATIVE;
+    d.qnew = p.q_new_in_momentum;
+    d.record = 0;
+    d.L = p.L;
+    d.cell = p.L / d.nc;
+    d.inv_cell = (double)d.nc / p.L;
+    d.R2 = (3.0 * p.h) * (3.0 * p.h);
+    double dt = effective_dt(p);
+    d.dt_d = dt;
+    d.half_dt_d = 0.5 * dt;
+    d.cell_f = (float)d.cell;
+    // The FP32 |d|^2 from tile-local coordinates is within ~2e-5 (3h)^2 of the FP64 value; pairs
+    // inside a band of +-2^-13 relative are decided in FP64.
+    const double band = 1.0 / 8192.0;
+    d.R2lo = (float)(d.R2 * (1.0 - band));
+    d.R2hi = (float)(d.R2 * (1.0 + band));
+    d.inv_h = (float)(1.0 / p.h);
+    double ad = 7.0 / (478.0 * M_PI * p.h * p.h);
+    d.ad = (float)ad;
+    d.W0 = (float)(ad * 66.0);   // W(0) = a_d (3^5 - 6 2^5 + 15)
+    d.Fc = (float)(ad / p.h);
+    d.dt = (float)dt;
+    d.half_dt = (float)(0.5 * dt);
+    d.rho0 = (float)p.rho0;
+    d.nu = (float)(p.eta / p.rho0);
+    d.mu = (float)p.eta;
+    d.Gamma = (float)p.Gamma;
+    d.lambda = (float)p.lambda;
+    d.A = (float)p.A;
+    d.C = (float)p.C;
+    d.K = (float)p.K;
+    d.zeta = (float)p.zeta;
+    d.gamma_eos = (float)p.gamma_eos;
+    d.beta = (float)p.beta;
+    d.c0_min = (float)p.c0_min;
+    d.c_shift = (float)p.c_shift;
+    d.mass = (float)(p.rho0 * p.L * p.L / (double)p.n);
+    return d;
+}
+
+template <typename T>
+cudaError_t dalloc(ann_ctx *c, T *&ptr, size_t count)
+{
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(T));
+    if (e) return e;
+    c->allocs.push_back(v);
+    ptr = static_cast<T *>(v);
+    return cudaMemset(v, 0, std::max<size_t>(count, 1) * sizeof(T));
+}
+
+cudaError_t alloc_all(ann_ctx *c)
+{
+    size_t n = (size_t)c->P.n, ncell = (size_t)c->P.ncell;
+    Bufs &b = c->b;
+    cudaError_t e;
+#define A_(p, cnt) if ((e = dalloc(c, b.p, cnt))) return e
+    A_(sx, n); A_(sy, n); A_(sux, n); A_(suy, n); A_(sq11, n); A_(sq12, n); A_(sdr, n); A_(sax, n);
+    A_(say, n); A_(sid, n);
+    A_(mx, n); A_(my, n); A_(mux, n); A_(muy, n); A_(mq11, n); A_(mq12, n); A_(mdr, n); A_(xix, n);
+    A_(xiy, n); A_(mid, n);
+    A_(cell_count, ncell + 1); A_(cell_start, ncell + 1); A_(key, n); A_(rank, n); A_(perm, n);
+    A_(nbr, n * (MAXN / 2)); A_(nnbr, n);
+    A_(sumW, n); A_(V, n); A_(B11, n); A_(B12, n); A_(B22, n); A_(kr, n); A_(dh, n); A_(dhat, n);
+    A_(p, n); A_(divx, n); A_(divy, n);
+    A_(rec_gu, 4 * n); A_(rec_lap, 2 * n); A_(rec_apd, 2 * n);
+    A_(err, 1); A_(maxu, 1); A_(band, 1);
+#undef A_
+    unsigned char *tmp = nullptr;
+    if ((e = dalloc(c, tmp, std::max<size_t>(7 * 8, MAXN * 4) * n))) return e;
+    c->tmp = tmp;
+    if ((e = dalloc(c, c->diag_part, (size_t)diag_blocks((int)n) * NDIAG))) return e;
+    if ((e = dalloc(c, c->diag_out, NDIAG))) return e;
+    return cudaSuccess;
+}
+
+cudaError_t capture(ann_ctx *c)
+{
+    if (c->exec) {
+        cudaGraphExecDestroy(c->exec);
+        c->exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->own, cudaStreamCaptureModeThreadLocal);
+    if (e) return e;
+    cudaError_t e2 = enqueue_step(c->P, c->b, c->own, nullptr);
+    e = cudaStreamEndCapture(c->own, &g);
+    if (e2) { if (g) cudaGraphDestroy(g); return e2; }
+    if (e) return e;
+    e = cudaGraphInstantiate(&c->exec, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+// Read and clear nothing: returns the status implied by the sticky device error word.
+int device_status(ann_ctx *c)
+{
+    cudaError_t e = cudaMemcpyAsync(c->h_err, c->b.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "reading the device status");
+    uint32_t bits = *c->h_err;
+    if (!bits) return ANN_OK;
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "device error bits 0x%x (1 cell, 2 halo, 4 neighbours, 8 non-finite, 16 alpha)", bits);
+    c->last_err = buf;
+    if (bits & EB_NONFINITE) return ANN_ERR_NONFINITE;
+    if (bits & (EB_CELL | EB_HALO)) return ANN_ERR_CELL_OVERFLOW;
+    if (bits & EB_NBR) return ANN_ERR_NBR_OVERFLOW;
+    return ANN_ERR_SINGULAR_ALPHA;
+}
+
+cudaError_t clear_flags(ann_ctx *c)
+{
+    cudaError_t e = cudaMemsetAsync(c->b.err, 0, sizeof(uint32_t), c->stream);
+    if (!e) e = cudaMemsetAsync(c->b.maxu, 0, sizeof(uint32_t), c->stream);
+    if (!e) e = cudaMemsetAsync(c->b.cell_count, 0, sizeof(uint32_t) * (c->P.ncell + 1), c->stream);
+    return e;
+}
+
+struct Field {
+    const void *ptr;
+    int es;
+    bool state;   // in S order (else M order)
+    int stride;   // interleaved component count
+    int comp;
+};
+
+bool field_of(ann_ctx *c, int f, Field &out)
+{
+    const Bufs &b = c->b;
+    out = Field{nullptr, 4, false, 1, 0};
+    switch (f) {
+    case ANN_FIELD_X: out = {b.sx, 8, true, 1, 0}; return true;
+    case ANN_FIELD_Y: out = {b.sy, 8, true, 1, 0}; return true;
+    case ANN_FIELD_UX: out = {b.sux, 4, true, 1, 0}; return true;
+    case ANN_FIELD_UY: out = {b.suy, 4, true, 1, 0}; return true;
+    case ANN_FIELD_Q11: out = {b.sq11, 4, true, 1, 0}; return true;
+    case ANN_FIELD_Q12: out = {b.sq12, 4, true, 1, 0}; return true;
+    case ANN_FIELD_DRHO: out = {b.sdr, 4, true, 1, 0}; return true;
+    case ANN_FIELD_AX: out = {b.sax, 4, true, 1, 0}; return true;
+    case ANN_FIELD_AY: out = {b.say, 4, true, 1, 0}; return true;
+    case ANN_FIELD_SUMW: out.ptr = b.sumW; return true;
+    case ANN_FIELD_V: out.ptr = b.V; return true;
+    case ANN_FIELD_B11: out.ptr = b.B11; return true;
+    case ANN_FIELD_B12: out.ptr = b.B12; return true;
+    case ANN_FIELD_B22: out.ptr = b.B22; return true;
+    case ANN_FIELD_K: out.ptr = b.kr; return true;
+    case ANN_FIELD_DRHO_HALF: out.ptr = b.dh; return true;
+    case ANN_FIELD_DRHO_HAT: out.ptr = b.dhat; return true;
+    case ANN_FIELD_P: out.ptr = b.p; return true;
+    case ANN_FIELD_DIVQX: out.ptr = b.divx; return true;
+    case ANN_FIELD_DIVQY: out.ptr = b.divy; return true;
+    case ANN_FIELD_NNBR: out.ptr = b.nnbr; return true;
+    case ANN_FIELD_GRADU_XX: case ANN_FIELD_GRADU_XY: case ANN_FIELD_GRADU_YX: case ANN_FIELD_GRADU_YY:
+        out = {b.rec_gu, 4, false, 4, f - ANN_FIELD_GRADU_XX}; return true;
+    case ANN_FIELD_LAPQ11: case ANN_FIELD_LAPQ12:
+        out = {b.rec_lap, 4, false, 2, f - ANN_FIELD_LAPQ11}; return true;
+    case ANN_FIELD_APDX: case ANN_FIELD_APDY:
+        out = {b.rec_apd, 4, false, 2, f - ANN_FIELD_APDX}; return true;
+    default: return false;
+    }
+}
+
+__global__ void k_deinterleave(const float *src, float *dst, int n, int stride, int comp)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[(size_t)i * stride + comp];
+}
+
+const char kMagic[8] = {'A', 'N', 'N', 'S', 'T', 'A', 'T', '1'};
+
+}  // namespace
+
+extern "C" {
+
+int ann_version(void) { return ANN_ABI_VERSION; }
+
+const char *ann_status_string(int status) { return status_text(status); }
+
+int ann_default_params(ann_params *p)
+{
+    if (!p) return ANN_ERR_INVALID_ARG;
+    std::memset(p, 0, sizeof *p);
+    p->n = 64 * 64;
+    p->L = 1.0;
+    p->h = 1.3 / 64.0;
+    p->dt = 1e-4;
+    p->rho0 = 1.0;
+    p->eta = 1.0;
+    p->Gamma = 0.34;
+    p->lambda = 0.7;
+    p->A = 0.0;
+    p->B = 0.0;
+    p->C = 1.0;
+    p->K = 0.04;
+    p->zeta = 0.05;
+    p->gamma_eos = 7.0;
+    p->beta = 1.0;
+    p->c0_min = 0.0;
+    p->c_shift = 1.0 / 3.0;
+    p->apd = 1;
+    p->momentum_mode = ANN_MOMENTUM_PAPER;
+    p->q_new_in_momentum = 1;
+    p->dt_mode = ANN_DT_FIXED;
+    return ANN_OK;
+}
+
+int ann_validate_params(const ann_params *p)
+{
+    std::string why;
+    return validate(p, why);
+}
+
+int ann_grid_info(const ann_params *p, ann_grid *out)
+{
+    std::string why;
+    int s = validate(p, why);
+    if (s) return s;
+    if (!out) return ANN_ERR_INVALID_ARG;
+    out->cells_per_side = cells_per_side(*p);
+    out->tiles_per_side = (out->cells_per_side + TILE - 1) / TILE;
+    out->cell_size = p->L / out->cells_per_side;
+    out->dt_effective = effective_dt(*p);
+    out->expected_neighbors = M_PI * 9.0 * p->h * p->h * (double)p->n / (p->L * p->L);
+    out->device_bytes = device_bytes(*p);
+    return ANN_OK;
+}
+
+int ann_create(const ann_params *p, ann_ctx **out)
+{
+    if (!out) return ANN_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::string why;
+    int s = validate(p, why);
+    if (s) return s;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return ANN_ERR_NOT_AVAILABLE;
+    }
+    ann_ctx *c = new (std::nothrow) ann_ctx();
+    if (!c) return ANN_ERR_OOM;
+    c->prm = *p;
+    c->P = make_dev(*p);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (!e) e = prepare_kernels();
+    if (!e) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+    if (!e) { c->stream = c->own; e = alloc_all(c); }
+    if (!e) e = cudaMallocHost(&c->h_err, sizeof(uint32_t));
+    if (!e) e = capture(c);
+    if (!e) e = cudaStreamSynchronize(c->own);
+    if (e) {
+        int code = cuda_fail(c, e, "ann_create");
+        ann_destroy(c);
+        return code;
+    }
+    *out = c;
+    return ANN_OK;
+}
+
+void ann_destroy(ann_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    for (void *v : c->allocs) cudaFree(v);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->own) cudaStreamDestroy(c->own);
+    delete c;
+}
+
+int ann_set_stream(ann_ctx *c, void *stream)
+{
+    if (!c) return ANN_ERR_INVALID_ARG;
+    cudaStreamSynchronize(c->stream);
+    c->stream = static_cast<cudaStream_t>(stream);
+    return ANN_OK;
+}
+
+int ann_set_particles(ann_ctx *c, int64_t n, const double *x, const double *y, const double *ux,
+                      const double *uy, const double *q11, const double *q12, const double *rho,
+                      int is_device)
+{
+    if (!c) return ANN_ERR_INVALID_ARG;
+    if (n != c->prm.n) return fail(c, ANN_ERR_INVALID_ARG, "n differs from the n of ann_create");
+    if (!x || !y || !ux || !uy || !q11 || !q12) return fail(c, ANN_ERR_INVALID_ARG, "null input array");
+    cudaError_t e = clear_flags(c);
+    if (e) return cuda_fail(c, e, "ann_set_particles");
+    const double *src[7] = {x, y, ux, uy, q11, q12, rho};
+    const double *dev[7] = {x, y, ux, uy, q11, q12, rho};
+    if (!is_device) {
+        double *t = static_cast<double *>(c->tmp);
+        for (int k = 0; k < 7; k++) {
+            if (!src[k]) { dev[k] = nullptr; continue; }
+            e = cudaMemcpyAsync(t + (size_t)k * n, src[k], sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
+            if (e) return cuda_fail(c, e, "ann_set_particles copy");
+            dev[k] = t + (size_t)k * n;
+        }
+    }
+    e = enqueue_load(c->P, c->b, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5], dev[6], c->stream);
+    if (e) return cuda_fail(c, e, "ann_set_particles load");
+    c->have_particles = true;
+    c->steps = 0;
+    c->t = 0.0;
+    int s = device_status(c);
+    if (s) {
+        c->have_particles = false;
+        clear_flags(c);
+        cudaStreamSynchronize(c->stream);
+    }
+    return s;
+}
+
+int ann_step(ann_ctx *c, int64_t nsteps)
+{
+    if (!c || nsteps < 0) return ANN_ERR_INVALID_ARG;
+    if (!c->have_particles) return fail(c, ANN_ERR_STATE, "ann_step before ann_set_particles");
+    for (int64_t s = 0; s < nsteps; s++) {
+        cudaError_t e = cudaGraphLaunch(c->exec, c->stream);
+        if (e) return cuda_fail(c, e, "ann_step graph launch");
+    }
+    int s = device_status(c);
+    c->steps += nsteps;
+    c->t += nsteps * c->P.dt_d;
+    return s;
+}
+
+int ann_step_profile(ann_ctx *c, int64_t nsteps, double *kernel_ms)
+{
+    if (!c || nsteps < 0 || !kernel_ms) return ANN_ERR_INVALID_ARG;
+    if (!c->have_particles) return fail(c, ANN_ERR_STATE, "ann_step_profile before ann_set_particles");
+    std::vector<cudaEvent_t> ev((size_t)(NKERNELS + 1) * (size_t)nsteps);
+    cudaError_t e = cudaSuccess;
+    size_t made = 0;
+    for (; made < ev.size() && !e; made++) e = cudaEventCreate(&ev[made]);
+    for (int64_t s = 0; s < nsteps && !e; s++) e = enqueue_step(c->P, c->b, c->stream, &ev[(size_t)s * (NKERNELS + 1)]);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    for (int64_t s = 0; s < nsteps && !e; s++) {
+        for (int k = 0; k < NKERNELS && !e; k++) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[(size_t)s * (NKERNELS + 1) + k], ev[(size_t)s * (NKERNELS + 1) + k + 1]);
+            kernel_ms[k] += ms;
+        }
+    }
+    for (size_t k = 0; k < made; k++) if (ev[k]) cudaEventDestroy(ev[k]);
+    if (e) return cuda_fail(c, e, "ann_step_profile");
+    int s = device_status(c);
+    c->steps += nsteps;
+    c->t += nsteps * c->P.dt_d;
+    return s;
+}
+
+int ann_kernel_count(void) { return NKERNELS; }
+
+const char *ann_kernel_name(int k) { return kernel_name(k); }
+
+int ann_set_record(ann_ctx *c, int on)
+{
+    if (!c || (on != 0 && on != 1)) return ANN_ERR_INVALID_ARG;
+    if (c->P.record == on) return ANN_OK;
+    cudaStreamSynchronize(c->stream);
+    c->P.record = on;
+    cudaError_t e = capture(c);
+    if (e) return cuda_fail(c, e, "ann_set_record");
+    return ANN_OK;
+}
+
+int ann_get_field(ann_ctx *c, int field, void *dst, int64_t bytes, int dst_is_device)
+{
+    if (!c || !dst) return ANN_ERR_INVALID_ARG;
+    if (!c->have_particles) return fail(c, ANN_ERR_STATE, "no particles");
+    Field f;
+    if (!field_of(c, field, f)) return fail(c, ANN_ERR_INVALID_ARG, "unknown field");
+    int n = c->P.n;
+    if (bytes < (int64_t)n * f.es) return fail(c, ANN_ERR_INVALID_ARG, "destination too small");
+    cudaError_t e = cudaSuccess;
+    const void *src = f.ptr;
+    unsigned char *tmp = static_cast<unsigned char *>(c->tmp);
+    if (f.stride > 1) {
+        float *d = reinterpret_cast<float *>(tmp + (size_t)8 * n);
+        k_deinterleave<<<(n + 255) / 256, 256, 0, c->stream>>>(static_cast<const float *>(f.ptr), d, n, f.stride, f.comp);
+        e = cudaGetLastError();
+        src = d;
+    }
+    if (!e) e = enqueue_unpermute(src, f.state ? c->b.sid : c->b.mid, tmp, n, f.es, c->stream);
+    if (!e) e = cudaMemcpyAsync(dst, tmp, (size_t)n * f.es,
+                                dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "ann_get_field");
+    return ANN_OK;
+}
+
+int ann_get_diagnostics(ann_ctx *c, ann_diag *out)
+{
+    if (!c || !out) return ANN_ERR_INVALID_ARG;
+    if (!c->have_particles) return fail(c, ANN_ERR_STATE, "no particles");
+    int nb = diag_blocks(c->P.n);
+    double h[NDIAG];
+    uint32_t bits = 0;
+    unsigned long long band = 0;
+    cudaError_t e = enqueue_diag(c->P, c->b, c->diag_part, nb, c->diag_out, c->stream);
+    if (!e) e = cudaMemcpyAsync(h, c->diag_out, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(&bits, c->b.err, sizeof bits, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(&band, c->b.band, sizeof band, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "ann_get_diagnostics");
+    std::memset(out, 0, sizeof *out);
+    int n = c->P.n;
+    out->t = c->t;
+    out->step = c->steps;
+    out->momentum[0] = h[0];
+    out->momentum[1] = h[1];
+    out->kinetic_energy = h[2] / n;
+    out->max_speed = h[3];
+    // c0 of the last step is not kept on the device; report the bound it obeys now
+    out->c0 = std::max(10.0 * h[3], c->prm.c0_min);
+    out->mass = h[4];
+    out->mean_q = h[5] / n;
+    out->nbr_mean = h[6] / n;
+    out->nbr_min = (int32_t)h[7];
+    out->nbr_max = (int32_t)h[8];
+    out->min_det_alpha = h[9];
+    out->error_bits = bits;
+    out->band_checks = band;
+    return ANN_OK;
+}
+
+int ann_get_neighbors(ann_ctx *c, int64_t *rowptr, int32_t *cols, int64_t cap)
+{
+    if (!c || !rowptr) return ANN_ERR_INVALID_ARG;
+    if (!c->have_particles) return fail(c, ANN_ERR_STATE, "no particles");
+    int n = c->P.n;
+    DevParams Q = c->P;
+    Q.half_dt = 0.f;
+    Q.half_dt_d = 0.0;
+    cudaError_t e = enqueue_search(Q, c->b, c->stream);
+    if (e) return cuda_fail(c, e, "ann_get_neighbors search");
+    int s = device_status(c);
+    if (s) return s;
+    std::vector<int> nn(n), mid(n);
+    e = cudaMemcpyAsync(nn.data(), c->b.nnbr, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(mid.data(), c->b.mid, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "ann_get_neighbors counts");
+    std::vector<int64_t> cnt(n + 1, 0);
+    for (int g = 0; g < n; g++) cnt[mid[g] + 1] = nn[g];
+    rowptr[0] = 0;
+    for (int i = 0; i < n; i++) rowptr[i + 1] = rowptr[i] + cnt[i + 1];
+    if (!cols) return ANN_OK;
+    if (cap < rowptr[n]) return fail(c, ANN_ERR_INVALID_ARG, "cols capacity below rowptr[n]");
+    int *dcols = static_cast<int *>(c->tmp);
+    e = enqueue_export_nbrs(c->P, c->b, dcols, c->stream);
+    std::vector<int> hc;
+    try {
+        hc.resize((size_t)MAXN * n);
+    } catch (...) {
+        return fail(c, ANN_ERR_OOM, "host allocation");
+    }
+    if (!e) e = cudaMemcpyAsync(hc.data(), dcols, sizeof(int) * (size_t)MAXN * n, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "ann_get_neighbors export");
+    for (int g = 0; g < n; g++) {
+        int i = mid[g];
+        int32_t *row = cols + rowptr[i];
+        for (int k = 0; k < nn[g]; k++) row[k] = hc[(size_t)k * n + g];
+        std::sort(row, row + nn[g]);
+    }
+    return ANN_OK;
+}
+
+int ann_save_state(ann_ctx *c, const char *path)
+{
+    if (!c || !path) return ANN_ERR_INVALID_ARG;
+    if (!c->have_particles) return fail(c, ANN_ERR_STATE, "no particles");
+    size_t n = (size_t)c->P.n;
+    std::vector<double> d(2 * n);
+    std::vector<float> f(7 * n);
+    std::vector<int> id(n);
+    const Bufs &b = c->b;
+    const float *fs[7] = {b.sux, b.suy, b.sq11, b.sq12, b.sdr, b.sax, b.say};
+    cudaError_t e = cudaMemcpyAsync(d.data(), b.sx, 8 * n, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(d.data() + n, b.sy, 8 * n, cudaMemcpyDeviceToHost, c->stream);
+    for (int k = 0; k < 7 && !e; k++) e = cudaMemcpyAsync(f.data() + k * n, fs[k], 4 * n, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(id.data(), b.sid, 4 * n, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "ann_save_state");
+    FILE *fp = std::fopen(path, "wb");
+    if (!fp) return fail(c, ANN_ERR_IO, std::string("cannot open ") + path);
+    int64_t nn = (int64_t)n;
+    bool ok = std::fwrite(kMagic, 1, 8, fp) == 8 && std::fwrite(&nn, 8, 1, fp) == 1 &&
+              std::fwrite(&c->prm, sizeof c->prm, 1, fp) == 1 && std::fwrite(&c->t, 8, 1, fp) == 1 &&
+              std::fwrite(&c->steps, 8, 1, fp) == 1 && std::fwrite(d.data(), 8, 2 * n, fp) == 2 * n &&
+              std::fwrite(f.data(), 4, 7 * n, fp) == 7 * n && std::fwrite(id.data(), 4, n, fp) == n;
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? ANN_OK : fail(c, ANN_ERR_IO, "short write");
+}
+
+int ann_load_state(ann_ctx *c, const char *path)
+{
+    if (!c || !path) return ANN_ERR_INVALID_ARG;
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) return fail(c, ANN_ERR_IO, std::string("cannot open ") + path);
+    char magic[8];
+    int64_t nn = 0;
+    ann_params prm;
+    double t = 0.0;
+    int64_t steps = 0;
+    bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+              std::fread(&nn, 8, 1, fp) == 1 && std::fread(&prm, sizeof prm, 1, fp) == 1 &&
+              std::fread(&t, 8, 1, fp) == 1 && std::fread(&steps, 8, 1, fp) == 1;
+    if (!ok) { std::fclose(fp); return fail(c, ANN_ERR_INVALID_ARG, "not a state file"); }
+    if (nn != c->prm.n) { std::fclose(fp); return fail(c, ANN_ERR_INVALID_ARG, "state file n differs"); }
+    size_t n = (size_t)nn;
+    std::vector<double> d(2 * n);
+    std::vector<float> f(7 * n);
+    std::vector<int> id(n);
+    ok = std::fread(d.data(), 8, 2 * n, fp) == 2 * n && std::fread(f.data(), 4, 7 * n, fp) == 7 * n &&
+         std::fread(id.data(), 4, n, fp) == n;
+    std::fclose(fp);
+    if (!ok) return fail(c, ANN_ERR_IO, "short read");
+    const Bufs &b = c->b;
+    float *fs[7] = {b.sux, b.suy, b.sq11, b.sq12, b.sdr, b.sax, b.say};
+    cudaError_t e = clear_flags(c);
+    if (!e) e = cudaMemcpyAsync(b.sx, d.data(), 8 * n, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaMemcpyAsync(b.sy, d.data() + n, 8 * n, cudaMemcpyHostToDevice, c->stream);
+    for (int k = 0; k < 7 && !e; k++) e = cudaMemcpyAsync(fs[k], f.data() + k * n, 4 * n, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaMemcpyAsync(b.sid, id.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "ann_load_state");
+    c->have_particles = true;
+    c->t = t;
+    c->steps = steps;
+    return ANN_OK;
+}
+
+const char *ann_last_error(ann_ctx *c) { return c ? c->last_err.c_str() : ""; }
+
+}  // extern "C"

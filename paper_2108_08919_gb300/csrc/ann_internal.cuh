@@ -1,0 +1,80 @@
+// Internal declarations shared by the kernels and the C-ABI of the SPH active-nematic solver.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ann {
+
+// Tiling of the pair passes: one CUDA block per TILE x TILE cells; it stages the particles of the
+// (TILE+2) x (TILE+2) cells around them (periodic images included) in shared memory.
+constexpr int TILE = 4;
+constexpr int HALO = TILE + 2;
+constexpr int NHC = HALO * HALO;      // halo cells per tile
+constexpr int HCAP = 1024;            // halo particles a tile may stage
+constexpr int MAXN = 64;              // neighbours per particle (ANN_MAX_NEIGHBORS)
+constexpr int MAXC = 64;              // particles per cell (ANN_MAX_PER_CELL)
+constexpr int PT = 256;               // threads per pair-pass block
+constexpr int NKERNELS = 8;
+
+// Sticky device error bits.
+enum : uint32_t {
+    EB_CELL = 1u,        // a cell held more than MAXC particles
+    EB_HALO = 2u,        // a tile halo held more than HCAP particles
+    EB_NBR = 4u,         // a particle had more than MAXN neighbours
+    EB_NONFINITE = 8u,   // NaN / infinity in the state
+    EB_SINGULAR = 16u,   // det(alpha) <= 0
+};
+
+// Parameters in the form the kernels use (FP64 where positions are involved).
+struct DevParams {
+    int n, nc, ncell, tiles;
+    int apd, conservative, qnew, record;
+    double L, cell, inv_cell, R2, dt_d, half_dt_d;
+    float cell_f, R2lo, R2hi, inv_h, ad, W0, Fc, dt, half_dt;
+    float rho0, nu, mu, Gamma, lambda, A, C, K, zeta, gamma_eos, beta, c0_min, c_shift, mass;
+};
+
+// Device buffers.  S: state at the end of a step, in the particle order of that step's evaluation.
+// M: the current step's cell-sorted copy.  Per-particle intermediates are in M order.
+struct Bufs {
+    double *sx, *sy;
+    float *sux, *suy, *sq11, *sq12, *sdr, *sax, *say;
+    int *sid;
+    double *mx, *my;
+    float *mux, *muy, *mq11, *mq12, *mdr, *xix, *xiy;
+    int *mid;
+    uint32_t *cell_count, *cell_start, *key, *rank, *perm;
+    uint32_t *nbr;      // packed slot pairs, (MAXN/2) x n, row-major in the pair index
+    int *nnbr;
+    float *sumW, *V, *B11, *B12, *B22, *kr, *dh, *dhat, *p, *divx, *divy;
+    float *rec_gu, *rec_lap, *rec_apd;   // 4n, 2n, 2n (recording only)
+    uint32_t *err, *maxu;
+    unsigned long long *band;
+};
+
+// Launch-configuration helpers (defined with the kernels).
+const char *kernel_name(int k);
+cudaError_t prepare_kernels();
+// Enqueue one time step on `s`.  With `ev` non-null, ev[0..NKERNELS] are recorded around the
+// kernels (ev[k] before kernel k, ev[NKERNELS] after the last).
+cudaError_t enqueue_step(const DevParams &P, const Bufs &b, cudaStream_t s, cudaEvent_t *ev);
+// Cell sort and pass A only (neighbour lists and volumes) at the positions in S advanced by
+// P.half_dt (callers pass 0 to keep them).
+cudaError_t enqueue_search(const DevParams &P, const Bufs &b, cudaStream_t s);
+// Load FP64 inputs (ID order) into S; rho may be null.
+cudaError_t enqueue_load(const DevParams &P, const Bufs &b, const double *x, const double *y,
+                         const double *ux, const double *uy, const double *q11, const double *q12,
+                         const double *rho, cudaStream_t s);
+// Scatter field f (M or S order, element size es) into out[id[g]].
+cudaError_t enqueue_unpermute(const void *f, const int *id, void *out, int n, int es, cudaStream_t s);
+// Neighbour export: for each M-order particle g and k < nnbr[g], cols_tmp[k * n + g] = original ID
+// of its k-th neighbour.
+cudaError_t enqueue_export_nbrs(const DevParams &P, const Bufs &b, int *cols_tmp, cudaStream_t s);
+// Diagnostics: deterministic two-level FP64 reductions into out[0..ndiag).
+constexpr int NDIAG = 12;
+cudaError_t enqueue_diag(const DevParams &P, const Bufs &b, double *partials, int nblocks,
+                         double *out, cudaStream_t s);
+int diag_blocks(int n);
+
+}  // namespace ann

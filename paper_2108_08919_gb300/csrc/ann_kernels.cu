@@ -1,0 +1,930 @@
+// sm_103a kernels of one SPH active-nematic time step (arXiv 2108.08919, §3 and §3.1).
+//
+// Layout: particles live in structure-of-arrays form, sorted by square cells of side >= 3h (§4);
+// cells are numbered row-major.  A pair pass runs one block per 4 x 4 cells ("tile"): the block
+// stages the particles of the surrounding 6 x 6 cells in shared memory -- periodic images of the
+// cells on the far side of the box take the place of the paper's ghost particles (Eq. 30) -- and
+// each thread accumulates the sums of one particle over its neighbours.  Pair vectors are formed in
+// FP32 from tile-local coordinates; the support test |d|^2 < (3h)^2 is decided in FP32 unless it
+// falls within a rounding band of the cutoff, where it is redone in FP64 from the FP64 positions
+// exactly as the definition states.
+#include "ann_internal.cuh"
+
+#include <cmath>
+
+namespace ann {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ double wrap_d(double a, double L)
+{
+    if (a < 0.0) a = a + L;
+    if (a >= L) a = a - L;
+    return a;
+}
+
+__device__ __forceinline__ int wrapc(int c, int nc) { return c < 0 ? c + nc : (c >= nc ? c - nc : c); }
+
+__device__ __forceinline__ bool stopped(const Bufs &b) { return *(volatile uint32_t *)b.err != 0u; }
+
+// Quintic kernel of Eq. (18) in branch-free form: W(b) = a_d [t3^5 - 6 t2^5 + 15 t1^5] with
+// t_k = max(k - b, 0), and F = W'(b) / (h r), so that grad_i W_ij = F d_ij.
+__device__ __forceinline__ void kernel_wf(float r2, const DevParams &P, float &W, float &F, float &rinv)
+{
+    rinv = rsqrtf(r2);
+    float bq = r2 * rinv * P.inv_h;
+    float t3 = fmaxf(3.f - bq, 0.f), t2 = fmaxf(2.f - bq, 0.f), t1 = fmaxf(1.f - bq, 0.f);
+    float s3 = t3 * t3, s2 = t2 * t2, s1 = t1 * t1;
+    float q3 = s3 * s3, q2 = s2 * s2, q1 = s1 * s1;
+    W = P.ad * (q3 * t3 - 6.f * q2 * t2 + 15.f * q1 * t1);
+    F = (-5.f * q3 + 30.f * q2 - 75.f * q1) * P.Fc * rinv;
+}
+
+__device__ __forceinline__ float kernel_w(float r2, const DevParams &P)
+{
+    float bq = sqrtf(r2) * P.inv_h;
+    float t3 = fmaxf(3.f - bq, 0.f), t2 = fmaxf(2.f - bq, 0.f), t1 = fmaxf(1.f - bq, 0.f);
+    float s3 = t3 * t3, s2 = t2 * t2, s1 = t1 * t1;
+    return P.ad * (s3 * s3 * t3 - 6.f * s2 * s2 * t2 + 15.f * s1 * s1 * t1);
+}
+
+// FP64 support test of the definition for particles gi (inner cell) and gj (halo image with cell
+// shift (sx, sy) in units of L): d = (x_i - x_j) -+ L, |d|^2 = d_x*d_x + d_y*d_y, no fused ops.
+__device__ __noinline__ bool support64(const DevParams &P, const Bufs &b, int gi, int gj, int sx, int sy)
+{
+    double dx = __dsub_rn(b.mx[gi], b.mx[gj]);
+    if (sx > 0) dx = __dsub_rn(dx, P.L);
+    else if (sx < 0) dx = __dadd_rn(dx, P.L);
+    double dy = __dsub_rn(b.my[gi], b.my[gj]);
+    if (sy > 0) dy = __dsub_rn(dy, P.L);
+    else if (sy < 0) dy = __dadd_rn(dy, P.L);
+    double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    return r2 < P.R2;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Tile bookkeeping shared by the pair passes
+// ---------------------------------------------------------------------------------------------
+
+struct TileShared {
+    int off[NHC + 1];      // exclusive prefix of halo-cell particle counts (slots)
+    int start[NHC];        // first sorted index of each halo cell
+    int rowpre[TILE + 1];  // prefix of inner-row slot counts
+};
+
+struct Tile {
+    int cx0, cy0, wx, wy, HX, NH, H, Ni;
+};
+
+__device__ __forceinline__ bool tile_begin(const DevParams &P, const Bufs &b, TileShared &ts, Tile &T)
+{
+    int tx = blockIdx.x % P.tiles, ty = blockIdx.x / P.tiles;
+    T.cx0 = tx * TILE;
+    T.cy0 = ty * TILE;
+    T.wx = min(TILE, P.nc - T.cx0);
+    T.wy = min(TILE, P.nc - T.cy0);
+    T.HX = T.wx + 2;
+    T.NH = T.HX * (T.wy + 2);
+    int t = threadIdx.x;
+    if (t < T.NH) {
+        int hx = t % T.HX, hy = t / T.HX;
+        int c = wrapc(T.cy0 - 1 + hy, P.nc) * P.nc + wrapc(T.cx0 - 1 + hx, P.nc);
+        uint32_t s0 = b.cell_start[c], s1 = b.cell_start[c + 1];
+        ts.start[t] = (int)s0;
+        ts.off[t + 1] = (int)(s1 - s0);
+    }
+    __syncthreads();
+    if (t == 0) {
+        ts.off[0] = 0;
+        for (int h = 0; h < T.NH; h++) ts.off[h + 1] += ts.off[h];
+        int acc = 0;
+        ts.rowpre[0] = 0;
+        for (int r = 0; r < T.wy; r++) {
+            int row = (r + 1) * T.HX;
+            acc += ts.off[row + T.wx + 1] - ts.off[row + 1];
+            ts.rowpre[r + 1] = acc;
+        }
+    }
+    __syncthreads();
+    T.H = ts.off[T.NH];
+    T.Ni = ts.rowpre[T.wy];
+    return T.H <= HCAP;
+}
+
+// Halo cell holding slot t (largest h with off[h] <= t).
+__device__ __forceinline__ int slot_cell(const TileShared &ts, int NH, int t)
+{
+    int lo = 0, hi = NH - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (ts.off[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Slot of the q-th particle of the tile's inner cells.
+__device__ __forceinline__ int inner_slot(const TileShared &ts, const Tile &T, int q)
+{
+    int r = 0;
+    while (r + 1 < T.wy && ts.rowpre[r + 1] <= q) r++;
+    return ts.off[(r + 1) * T.HX + 1] + (q - ts.rowpre[r]);
+}
+
+// Sorted index and tile-local position of slot t.
+struct SlotInfo {
+    int g, h;
+    float ex, ey;
+};
+
+__device__ __forceinline__ SlotInfo slot_info(const DevParams &P, const Bufs &b, const TileShared &ts,
+                                              const Tile &T, int t)
+{
+    SlotInfo s;
+    s.h = slot_cell(ts, T.NH, t);
+    s.g = ts.start[s.h] + (t - ts.off[s.h]);
+    int hx = s.h % T.HX, hy = s.h / T.HX;
+    s.ex = b.xix[s.g] + (float)hx * P.cell_f;
+    s.ey = b.xiy[s.g] + (float)hy * P.cell_f;
+    return s;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Kernel 0: predictor, re-insertion, cell key, max |u'|                         (§3.1, Eq. 30)
+// ---------------------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_predict(DevParams P, Bufs b)
+{
+    if (stopped(b)) return;
+    __shared__ float wmax[8];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float sp = 0.f;
+    if (i < P.n) {
+        float ux = b.sux[i] + P.half_dt * b.sax[i];
+        float uy = b.suy[i] + P.half_dt * b.say[i];
+        double x = wrap_d(b.sx[i] + P.half_dt_d * (double)ux, P.L);
+        double y = wrap_d(b.sy[i] + P.half_dt_d * (double)uy, P.L);
+        if (!(isfinite(x) && isfinite(y) && isfinite(ux) && isfinite(uy) && x >= 0.0 && x < P.L &&
+              y >= 0.0 && y < P.L)) {
+            atomicOr(b.err, EB_NONFINITE);
+            x = 0.0;
+            y = 0.0;
+            ux = 0.f;
+            uy = 0.f;
+        }
+        b.sux[i] = ux;
+        b.suy[i] = uy;
+        b.sx[i] = x;
+        b.sy[i] = y;
+        int cx = min(max((int)(x * P.inv_cell), 0), P.nc - 1);
+        int cy = min(max((int)(y * P.inv_cell), 0), P.nc - 1);
+        uint32_t key = (uint32_t)(cy * P.nc + cx);
+        b.key[i] = key;
+        b.rank[i] = atomicAdd(&b.cell_count[key], 1u);
+        sp = sqrtf(ux * ux + uy * uy);
+    }
+    for (int o = 16; o > 0; o >>= 1) sp = fmaxf(sp, __shfl_xor_sync(FULL, sp, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = sp;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        sp = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) sp = fmaxf(sp, __shfl_xor_sync(FULL, sp, o));
+        if (threadIdx.x == 0 && sp > 0.f) atomicMax(b.maxu, __float_as_uint(sp));
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Kernel 1: exclusive scan of cell counts -> cell starts; clears the counts for the next step
+// ---------------------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(1024) k_scan(DevParams P, Bufs b)
+{
+    if (stopped(b)) return;
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t s_carry, s_max;
+    int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) {
+        s_carry = 0;
+        s_max = 0;
+    }
+    __syncthreads();
+    uint32_t mx = 0;
+    for (int base = 0; base < P.ncell; base += 4096) {
+        int c0 = base + 4 * t;
+        uint32_t v[4], s = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            v[k] = (c0 + k < P.ncell) ? b.cell_count[c0 + k] : 0u;
+            s += v[k];
+            mx = max(mx, v[k]);
+        }
+        uint32_t inc = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t u = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += u;
+        }
+        if (lane == 31) wsum[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t x = wsum[lane], xi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t u = __shfl_up_sync(FULL, xi, o);
+                if (lane >= o) xi += u;
+            }
+            wsum[lane] = xi - x;
+        }
+        __syncthreads();
+        uint32_t run = s_carry + wsum[w] + inc - s;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (c0 + k < P.ncell) {
+                b.cell_start[c0 + k] = run;
+                b.cell_count[c0 + k] = 0u;
+            }
+            run += v[k];
+        }
+        __syncthreads();
+        if (t == 1023) s_carry = run;
+        __syncthreads();
+    }
+    atomicMax(&s_max, mx);
+    __syncthreads();
+    if (t == 0) {
+        b.cell_start[P.ncell] = (uint32_t)P.n;
+        if (s_max > (uint32_t)MAXC) atomicOr(b.err, EB_CELL);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Kernel 2: scatter particle indices into their cells
+// ---------------------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_scatter(DevParams P, Bufs b)
+{
+    if (stopped(b)) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P.n) b.perm[b.cell_start[b.key[i]] + b.rank[i]] = (uint32_t)i;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Kernel 3: order each cell by previous index (a stable sort overall) and gather the state into
+// cell order; FP32 offsets from the cell corner.  One warp per cell.
+// ---------------------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_cell_order(DevParams P, Bufs b)
+{
+    if (stopped(b)) return;
+    __shared__ uint32_t srt[8][MAXC];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int c = blockIdx.x * 8 + w;
+    if (c >= P.ncell) return;
+    uint32_t start = b.cell_start[c];
+    int cnt = (int)(b.cell_start[c + 1] - start);   // <= MAXC: k_scan raised EB_CELL otherwise
+    uint32_t v0 = lane < cnt ? b.perm[start + lane] : 0xffffffffu;
+    uint32_t v1 = lane + 32 < cnt ? b.perm[start + 32 + lane] : 0xffffffffu;
+    int r0 = 0, r1 = 0;
+#pragma unroll 8
+    for (int k = 0; k < 32; k++) {
+        uint32_t a = __shfl_sync(FULL, v0, k), d = __shfl_sync(FULL, v1, k);
+        r0 += (a < v0) + (d < v0);
+        r1 += (a < v1) + (d < v1);
+    }
+    if (lane < cnt) srt[w][r0] = v0;
+    if (lane + 32 < cnt) srt[w][r1] = v1;
+    __syncwarp();
+    int cx = c % P.nc, cy = c / P.nc;
+    double ox = (double)cx * P.cell, oy = (double)cy * P.cell;
+    for (int s = lane; s < cnt; s += 32) {
+        uint32_t old = srt[w][s], g = start + (uint32_t)s;
+        double x = b.sx[old], y = b.sy[old];
+        b.mx[g] = x;
+        b.my[g] = y;
+        b.xix[g] = (float)(x - ox);
+        b.xiy[g] = (float)(y - oy);
+        b.mux[g] = b.sux[old];
+        b.muy[g] = b.suy[old];
+        b.mq11[g] = b.sq11[old];
+        b.mq12[g] = b.sq12[old];
+        b.mdr[g] = b.sdr[old];
+        b.mid[g] = b.sid[old];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Kernel 4: pass A -- neighbour lists, sum_j W_ij (self included) and V = 1/sum  (Eqs. 18, 19)
+// ---------------------------------------------------------------------------------------------
+
+constexpr int SMEM_A = HCAP * (8 + 4 + 1) + MAXN * PT * 2;
+
+__global__ void __launch_bounds__(PT) k_pass_a(DevParams P, Bufs b)
+{
+    if (stopped(b)) return;
+    __shared__ TileShared ts;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float2 *pos = reinterpret_cast<float2 *>(dsm);
+    int *sg = reinterpret_cast<int *>(pos + HCAP);
+    uint16_t *lst = reinterpret_cast<uint16_t *>(sg + HCAP);
+    unsigned char *shc = reinterpret_cast<unsigned char *>(lst + MAXN * PT);
+    Tile T;
+    if (!tile_begin(P, b, ts, T)) {
+        if (threadIdx.x == 0) atomicOr(b.err, EB_HALO);
+        return;
+    }
+    for (int t = threadIdx.x; t < T.H; t += PT) {
+        SlotInfo s = slot_info(P, b, ts, T, t);
+        pos[t] = make_float2(s.ex, s.ey);
+        sg[t] = s.g;
+        shc[t] = (unsigned char)s.h;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < T.Ni; q += PT) {
+        int si = inner_slot(ts, T, q);
+        int h = shc[si], hx = h % T.HX, hy = h / T.HX;
+        float2 pi = pos[si];
+        int cnt = 0;
+        for (int oy = -1; oy <= 1; oy++) {
+            int row = (hy + oy) * T.HX + hx;
+            int j0 = ts.off[row - 1], j1 = ts.off[row + 2];
+            for (int j = j0; j < j1; j++) {
+                float2 pj = pos[j];
+                float dx = pi.x - pj.x, dy = pi.y - pj.y;
+                float r2 = dx * dx + dy * dy;
+                bool in = r2 < P.R2lo;
+                if (!in && r2 < P.R2hi) {
+                    int hj = shc[j];
+                    int cxu = T.cx0 - 1 + hj % T.HX, cyu = T.cy0 - 1 + hj / T.HX;
+                    int sx = cxu < 0 ? -1 : (cxu >= P.nc ? 1 : 0);
+                    int sy = cyu < 0 ? -1 : (cyu >= P.nc ? 1 : 0);
+                    in = support64(P, b, sg[si], sg[j], sx, sy);
+                    atomicAdd(b.band, 1ull);
+                }
+                if (in && j != si) {
+                    if (cnt < MAXN) lst[cnt * PT + threadIdx.x] = (uint16_t)j;
+                    cnt++;
+                }
+            }
+        }
+        if (cnt > MAXN) atomicOr(b.err, EB_NBR);
+        int c = min(cnt, MAXN);
+        float sw = P.W0;
+        for (int k = 0; k < c; k++) {
+            float2 pj = pos[lst[k * PT + threadIdx.x]];
+            float dx = pi.x - pj.x, dy = pi.y - pj.y;
+            sw += kernel_w(dx * dx + dy * dy, P);
+        }
+        int gi = sg[si];
+        b.sumW[gi] = sw;
+        b.V[gi] = 1.0f / sw;
+        b.nnbr[gi] = c;
+        for (int k2 = 0; 2 * k2 < c; k2++) {
+            uint32_t lo = lst[(2 * k2) * PT + threadIdx.x];
+            uint32_t hi = (2 * k2 + 1 < c) ? lst[(2 * k2 + 1) * PT + threadIdx.x] : 0xffffu;
+            b.nbr[(size_t)k2 * P.n + gi] = lo | (hi << 16);
+        }
+    }
+}
+
+// Neighbour slot k of particle gi (w caches the packed pair).
+__device__ __forceinline__ int nbr_slot(const DevParams &P, const Bufs &b, int gi, int k, uint32_t &w)
+{
+    if ((k & 1) == 0) w = b.nbr[(size_t)(k >> 1) * P.n + gi];
+    return (k & 1) ? (int)(w >> 16) : (int)(w & 0xffffu);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Kernel 5: pass B -- correction tensor alpha and B = alpha^-1 (Eq. 22), corrected velocity
+// gradient (Eq. 20), continuity (Eq. 25) and half-step density, Q Laplacian (Eq. 21), molecular
+// field (Eq. 7), co-rotation term (Eq. 2) and the Q update of Eq. (24).
+// ---------------------------------------------------------------------------------------------
+
+constexpr int SMEM_B = HCAP * (16 + 16 + 4);
+
+template <bool QOLD>
+__global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
+{
+    if (stopped(b)) return;
+    __shared__ TileShared ts;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float4 *sa = reinterpret_cast<float4 *>(dsm);     // (x, y, V, ux)
+    float4 *sb = sa + HCAP;                           // (uy, q11, q12, -)
+    int *sg = reinterpret_cast<int *>(sb + HCAP);
+    Tile T;
+    if (!tile_begin(P, b, ts, T)) {
+        if (threadIdx.x == 0) atomicOr(b.err, EB_HALO);
+        return;
+    }
+    for (int t = threadIdx.x; t < T.H; t += PT) {
+        SlotInfo s = slot_info(P, b, ts, T, t);
+        sa[t] = make_float4(s.ex, s.ey, b.V[s.g], b.mux[s.g]);
+        sb[t] = make_float4(b.muy[s.g], b.mq11[s.g], b.mq12[s.g], 0.f);
+        sg[t] = s.g;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < T.Ni; q += PT) {
+        int si = inner_slot(ts, T, q);
+        int gi = sg[si];
+        float4 ai = sa[si], bi = sb[si];
+        float a11 = 0.f, a12 = 0.f, a22 = 0.f;
+        float l00 = 0.f, l01 = 0.f, l10 = 0.f, l11 = 0.f;
+        float r1xx = 0.f, r1xy = 0.f, r1yy = 0.f, r2xx = 0.f, r2xy = 0.f, r2yy = 0.f;
+        float g1x = 0.f, g1y = 0.f, g2x = 0.f, g2y = 0.f;
+        int c = b.nnbr[gi];
+        uint32_t w = 0;
+        for (int k = 0; k < c; k++) {
+            int j = nbr_slot(P, b, gi, k, w);
+            if (j >= T.H) continue;
+            float4 aj = sa[j], bj = sb[j];
+            float dx = ai.x - aj.x, dy = ai.y - aj.y;
+            float r2 = dx * dx + dy * dy;
+            float Wv, F, rinv;
+            kernel_wf(r2, P, Wv, F, rinv);
+            float g = aj.z * F;
+            float gx = g * dx, gy = g * dy;
+            float mxx = gx * dx, mxy = gx * dy, myy = gy * dy;
+            a11 -= mxx;
+            a12 -= mxy;
+            a22 -= myy;
+            float dux = aj.w - ai.w, duy = bj.x - bi.x;
+            l00 += dux * gx;
+            l01 += dux * gy;
+            l10 += duy * gx;
+            l11 += duy * gy;
+            float dq1 = bj.y - bi.y, dq2 = bj.z - bi.z;
+            float rinv2 = rinv * rinv;
+            float e1 = -dq1 * rinv2, e2 = -dq2 * rinv2;
+            r1xx += e1 * mxx;
+            r1xy += e1 * mxy;
+            r1yy += e1 * myy;
+            r2xx += e2 * mxx;
+            r2xy += e2 * mxy;
+            r2yy += e2 * myy;
+            if (QOLD) {
+                g1x += dq1 * gx;
+                g1y += dq1 * gy;
+                g2x += dq2 * gx;
+                g2y += dq2 * gy;
+            }
+        }
+        float det = a11 * a22 - a12 * a12;
+        if (!(det > 0.f)) atomicOr(b.err, EB_SINGULAR);
+        float idet = 1.f / det;
+        float B11 = a22 * idet, B12 = -a12 * idet, B22 = a11 * idet;
+        // D[a][b] = du_a/dx_b = sum_l L[a][l] B[l][b]
+        float D00 = l00 * B11 + l01 * B12, D01 = l00 * B12 + l01 * B22;
+        float D10 = l10 * B11 + l11 * B12, D11 = l10 * B12 + l11 * B22;
+        float divu = D00 + D11;
+        float di = b.mdr[gi];
+        float kr = -(1.f + di) * divu;
+        float lap1 = 2.f * (B11 * r1xx + 2.f * B12 * r1xy + B22 * r1yy);
+        float lap2 = 2.f * (B11 * r2xx + 2.f * B12 * r2xy + B22 * r2yy);
+        // Q rate, projected on symmetric traceless tensors.  With E = sym(D), w = (D10 - D01)/2:
+        //   S_tl = lambda tr(E) Q + 2 c lambda E_tl + (Omega Q - Q Omega) - 2 lambda (Q:E) Q
+        //   H_tl = -A Q - C tr(Q^2) Q + K lap Q        (the B term of Eq. 7 is isotropic in 2D)
+        float q1 = bi.y, q2 = bi.z;
+        float E12 = 0.5f * (D01 + D10), om = 0.5f * (D10 - D01);
+        float QE = q1 * (D00 - D11) + 2.f * q2 * E12;
+        float trQ2 = 2.f * (q1 * q1 + q2 * q2);
+        float lam = P.lambda, cl = P.c_shift * lam;
+        float hb = -P.A - P.C * trQ2;
+        float m1 = lam * divu * q1 + cl * (D00 - D11) - 2.f * om * q2 - 2.f * lam * QE * q1 +
+                   P.Gamma * (hb * q1 + P.K * lap1);
+        float m2 = lam * divu * q2 + 2.f * cl * E12 + 2.f * om * q1 - 2.f * lam * QE * q2 +
+                   P.Gamma * (hb * q2 + P.K * lap2);
+        b.sq11[gi] = q1 + P.dt * m1;
+        b.sq12[gi] = q2 + P.dt * m2;
+        b.B11[gi] = B11;
+        b.B12[gi] = B12;
+        b.B22[gi] = B22;
+        b.kr[gi] = kr;
+        b.dh[gi] = di + P.half_dt * kr;
+        if (QOLD) {
+            float q1x = g1x * B11 + g1y * B12, q1y = g1x * B12 + g1y * B22;
+            float q2x = g2x * B11 + g2y * B12, q2y = g2x * B12 + g2y * B22;
+            b.divx[gi] = q1x + q2y;
+            b.divy[gi] = q2x - q1y;
+        }
+        if (P.record) {
+            b.rec_gu[4 * gi + 0] = D00;
+            b.rec_gu[4 * gi + 1] = D01;
+            b.rec_gu[4 * gi + 2] = D10;
+            b.rec_gu[4 * gi + 3] = D11;
+            b.rec_lap[2 * gi + 0] = lap1;
+            b.rec_lap[2 * gi + 1] = lap2;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Kernel 6: pass C -- density filter (Eq. 28), equation of state (Eq. 26), div Q^{n+1}
+// ---------------------------------------------------------------------------------------------
+
+constexpr int SMEM_C = HCAP * (16 + 8 + 4);
+
+template <bool QNEW>
+__global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
+{
+    if (stopped(b)) return;
+    __shared__ TileShared ts;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float4 *sa = reinterpret_cast<float4 *>(dsm);      // (x, y, V, dh)
+    float2 *sq = reinterpret_cast<float2 *>(sa + HCAP); // Q^{n+1}
+    int *sg = reinterpret_cast<int *>(sq + HCAP);
+    Tile T;
+    if (!tile_begin(P, b, ts, T)) {
+        if (threadIdx.x == 0) atomicOr(b.err, EB_HALO);
+        return;
+    }
+    for (int t = threadIdx.x; t < T.H; t += PT) {
+        SlotInfo s = slot_info(P, b, ts, T, t);
+        sa[t] = make_float4(s.ex, s.ey, b.V[s.g], b.dh[s.g]);
+        sq[t] = QNEW ? make_float2(b.sq11[s.g], b.sq12[s.g]) : make_float2(0.f, 0.f);
+        sg[t] = s.g;
+    }
+    __syncthreads();
+    float c0 = fmaxf(10.f * __uint_as_float(*b.maxu), P.c0_min);
+    float pref = P.rho0 * c0 * c0 / P.gamma_eos;
+    for (int q = threadIdx.x; q < T.Ni; q += PT) {
+        int si = inner_slot(ts, T, q);
+        int gi = sg[si];
+        float4 ai = sa[si];
+        float2 qi = sq[si];
+        float shep = 0.f, g1x = 0.f, g1y = 0.f, g2x = 0.f, g2y = 0.f;
+        int c = b.nnbr[gi];
+        uint32_t w = 0;
+        for (int k = 0; k < c; k++) {
+            int j = nbr_slot(P, b, gi, k, w);
+            if (j >= T.H) continue;
+            float4 aj = sa[j];
+            float dx = ai.x - aj.x, dy = ai.y - aj.y;
+            float r2 = dx * dx + dy * dy;
+            float Wv, F, rinv;
+            kernel_wf(r2, P, Wv, F, rinv);
+            shep += (ai.w - aj.w) * Wv;
+            if (QNEW) {
+                float2 qj = sq[j];
+                float g = aj.z * F;
+                float gx = g * dx, gy = g * dy;
+                float dq1 = qj.x - qi.x, dq2 = qj.y - qi.y;
+                g1x += dq1 * gx;
+                g1y += dq1 * gy;
+                g2x += dq2 * gx;
+                g2y += dq2 * gy;
+            }
+        }
+        float dhat = ai.w - P.beta * shep / b.sumW[gi];
+        b.dhat[gi] = dhat;
+        b.p[gi] = pref * expm1f(P.gamma_eos * log1pf(dhat));
+        if (QNEW) {
+            float B11 = b.B11[gi], B12 = b.B12[gi], B22 = b.B22[gi];
+            float q1x = g1x * B11 + g1y * B12, q1y = g1x * B12 + g1y * B22;
+            float q2x = g2x * B11 + g2y * B12, q2y = g2x * B12 + g2y * B22;
+            b.divx[gi] = q1x + q2y;
+            b.divy[gi] = q2x - q1y;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Kernel 7: pass D -- momentum (Eq. 23), corrector (§3.1), APD (Eq. 29), re-insertion (Eq. 30)
+// ---------------------------------------------------------------------------------------------
+
+constexpr int SMEM_D = HCAP * (16 + 16 + 4);
+
+template <bool CONS>
+__global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
+{
+    if (stopped(b)) return;
+    __shared__ TileShared ts;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float4 *sa = reinterpret_cast<float4 *>(dsm);      // paper: (x, y, V, p/rho^2)   cons: (x, y, p/rho^2, 1/rho)
+    float4 *sb = sa + HCAP;                            // paper: (ux, uy, -, -)        cons: (ux, uy, q11/rho^2, q12/rho^2)
+    int *sg = reinterpret_cast<int *>(sb + HCAP);
+    Tile T;
+    if (!tile_begin(P, b, ts, T)) {
+        if (threadIdx.x == 0) atomicOr(b.err, EB_HALO);
+        return;
+    }
+    for (int t = threadIdx.x; t < T.H; t += PT) {
+        SlotInfo s = slot_info(P, b, ts, T, t);
+        float rho = P.rho0 * (1.f + b.dhat[s.g]);
+        float irho = 1.f / rho;
+        float pr = b.p[s.g] * irho * irho;
+        if (CONS) {
+            float q1 = P.qnew ? b.sq11[s.g] : b.mq11[s.g];
+            float q2 = P.qnew ? b.sq12[s.g] : b.mq12[s.g];
+            sa[t] = make_float4(s.ex, s.ey, pr, irho);
+            sb[t] = make_float4(b.mux[s.g], b.muy[s.g], q1 * irho * irho, q2 * irho * irho);
+        } else {
+            sa[t] = make_float4(s.ex, s.ey, b.V[s.g], pr);
+            sb[t] = make_float4(b.mux[s.g], b.muy[s.g], 0.f, 0.f);
+        }
+        sg[t] = s.g;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *b.maxu = 0u;   // pass C has consumed it
+    for (int q = threadIdx.x; q < T.Ni; q += PT) {
+        int si = inner_slot(ts, T, q);
+        int gi = sg[si];
+        float4 ai = sa[si], bi = sb[si];
+        float fx = 0.f, fy = 0.f, vx = 0.f, vy = 0.f;
+        float sux = 0.f, suy = 0.f, sr = 0.f, sdx = 0.f, sdy = 0.f;
+        int c = b.nnbr[gi];
+        uint32_t w = 0;
+        for (int k = 0; k < c; k++) {
+            int j = nbr_slot(P, b, gi, k, w);
+            if (j >= T.H) continue;
+            float4 aj = sa[j], bj = sb[j];
+            float dx = ai.x - aj.x, dy = ai.y - aj.y;
+            float r2 = dx * dx + dy * dy;
+            float Wv, F, rinv;
+            kernel_wf(r2, P, Wv, F, rinv);
+            float ux = bi.x - bj.x, uy = bi.y - bj.y;
+            float ud = ux * dx + uy * dy;
+            float rinv2 = rinv * rinv;
+            if (CONS) {
+                float gx = F * dx, gy = F * dy;
+                float cp = ai.z + aj.z;
+                float visc = 8.f * P.mu * ai.w * aj.w * ud * rinv2;
+                float qa = bi.z + bj.z, qb = bi.w + bj.w;
+                fx += (visc - cp) * gx - P.zeta * (qa * gx + qb * gy);
+                fy += (visc - cp) * gy - P.zeta * (qb * gx - qa * gy);
+            } else {
+                float cp = aj.z * (ai.w + aj.w) * F;
+                fx += cp * dx;
+                fy += cp * dy;
+                float v = aj.z * ud * F * rinv2;
+                vx += v * dx;
+                vy += v * dy;
+            }
+            sux += ux * Wv;
+            suy += uy * Wv;
+            float r = r2 * rinv;
+            sr += r;
+            float rinv3 = rinv2 * rinv;
+            sdx += dx * rinv3;
+            sdy += dy * rinv3;
+        }
+        float ax, ay;
+        float dhat = b.dhat[gi];
+        float rho = P.rho0 * (1.f + dhat);
+        if (CONS) {
+            ax = P.mass * fx;
+            ay = P.mass * fy;
+        } else {
+            float B11 = b.B11[gi], B12 = b.B12[gi], B22 = b.B22[gi];
+            float pbx = B11 * fx + B12 * fy, pby = B12 * fx + B22 * fy;
+            float vbx = B11 * vx + B12 * vy, vby = B12 * vx + B22 * vy;
+            float irho = 1.f / rho;
+            float kv = 8.f * P.nu * P.rho0 * irho;
+            ax = -rho * pbx + kv * vbx - P.zeta * irho * b.divx[gi];
+            ay = -rho * pby + kv * vby - P.zeta * irho * b.divy[gi];
+        }
+        float unx = bi.x + P.half_dt * ax, uny = bi.y + P.half_dt * ay;
+        float apx = 0.f, apy = 0.f;
+        if (P.apd && c > 0) {
+            float uv = sqrtf(sux * sux + suy * suy) / b.sumW[gi];
+            float r0 = sr / (float)c;
+            float s = P.dt * uv * r0 * r0;
+            apx = s * sdx;
+            apy = s * sdy;
+        }
+        double xn = wrap_d(b.mx[gi] + P.half_dt_d * (double)unx + (double)apx, P.L);
+        double yn = wrap_d(b.my[gi] + P.half_dt_d * (double)uny + (double)apy, P.L);
+        float dn = dhat + P.half_dt * b.kr[gi];
+        if (!(isfinite(unx) && isfinite(uny) && isfinite(dn) && isfinite(xn) && isfinite(yn) &&
+              isfinite(b.sq11[gi]) && isfinite(b.sq12[gi])))
+            atomicOr(b.err, EB_NONFINITE);
+        b.sx[gi] = xn;
+        b.sy[gi] = yn;
+        b.sux[gi] = unx;
+        b.suy[gi] = uny;
+        b.sdr[gi] = dn;
+        b.sax[gi] = ax;
+        b.say[gi] = ay;
+        b.sid[gi] = b.mid[gi];
+        if (P.record) {
+            b.rec_apd[2 * gi + 0] = apx;
+            b.rec_apd[2 * gi + 1] = apy;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Utility kernels (outside the time step)
+// ---------------------------------------------------------------------------------------------
+
+__global__ void k_load(DevParams P, Bufs b, const double *x, const double *y, const double *ux,
+                       const double *uy, const double *q11, const double *q12, const double *rho)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    double xx = x[i], yy = y[i];
+    double r = rho ? rho[i] : (double)P.rho0;
+    bool ok = isfinite(xx) && isfinite(yy) && isfinite(ux[i]) && isfinite(uy[i]) &&
+              isfinite(q11[i]) && isfinite(q12[i]) && isfinite(r) && r > 0.0;
+    if (!ok) {
+        atomicOr(b.err, EB_NONFINITE);
+        xx = 0.0;
+        yy = 0.0;
+    }
+    if (xx < -P.L || xx >= 2.0 * P.L) xx = xx - floor(xx / P.L) * P.L;
+    if (yy < -P.L || yy >= 2.0 * P.L) yy = yy - floor(yy / P.L) * P.L;
+    b.sx[i] = wrap_d(xx, P.L);
+    b.sy[i] = wrap_d(yy, P.L);
+    b.sux[i] = (float)ux[i];
+    b.suy[i] = (float)uy[i];
+    b.sq11[i] = (float)q11[i];
+    b.sq12[i] = (float)q12[i];
+    b.sdr[i] = rho ? (float)(r / (double)P.rho0 - 1.0) : 0.f;
+    b.sax[i] = 0.f;
+    b.say[i] = 0.f;
+    b.sid[i] = i;
+}
+
+template <typename T>
+__global__ void k_unpermute(const T *f, const int *id, T *out, int n)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) out[id[g]] = f[g];
+}
+
+__global__ void __launch_bounds__(PT) k_export_nbrs(DevParams P, Bufs b, int *cols)
+{
+    __shared__ TileShared ts;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    int *sg = reinterpret_cast<int *>(dsm);
+    Tile T;
+    if (!tile_begin(P, b, ts, T)) return;
+    for (int t = threadIdx.x; t < T.H; t += PT) {
+        int h = slot_cell(ts, T.NH, t);
+        sg[t] = ts.start[h] + (t - ts.off[h]);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < T.Ni; q += PT) {
+        int si = inner_slot(ts, T, q);
+        int gi = sg[si];
+        int c = b.nnbr[gi];
+        uint32_t w = 0;
+        for (int k = 0; k < c; k++) {
+            int j = nbr_slot(P, b, gi, k, w);
+            cols[(size_t)k * P.n + gi] = j < T.H ? b.mid[sg[j]] : -1;
+        }
+    }
+}
+
+// Per-block partial sums in FP64: out[blk * NDIAG + q].
+__global__ void __launch_bounds__(256) k_diag_partial(DevParams P, Bufs b, double *part)
+{
+    __shared__ double red[256];
+    double v[NDIAG];
+    for (int q = 0; q < NDIAG; q++) v[q] = 0.0;
+    v[3] = 0.0;
+    v[7] = 1e300;
+    v[8] = -1e300;
+    v[9] = 1e300;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < P.n; g += gridDim.x * blockDim.x) {
+        double ux = b.sux[g], uy = b.suy[g];
+        double rho = (double)P.rho0 * (1.0 + (double)b.sdr[g]);
+        double m = P.conservative ? (double)P.mass : rho * (double)b.V[g];
+        v[0] += m * ux;
+        v[1] += m * uy;
+        v[2] += 0.5 * (ux * ux + uy * uy);
+        v[3] = fmax(v[3], sqrt(ux * ux + uy * uy));
+        v[4] += m;
+        v[5] += sqrt((double)b.sq11[g] * b.sq11[g] + (double)b.sq12[g] * b.sq12[g]);
+        double nn = (double)b.nnbr[g];
+        v[6] += nn;
+        v[7] = fmin(v[7], nn);
+        v[8] = fmax(v[8], nn);
+        double b11 = b.B11[g], b12 = b.B12[g], b22 = b.B22[g];
+        double detb = b11 * b22 - b12 * b12;
+        v[9] = fmin(v[9], detb != 0.0 ? 1.0 / detb : 1e300);
+    }
+    for (int q = 0; q < NDIAG; q++) {
+        red[threadIdx.x] = v[q];
+        __syncthreads();
+        for (int s = 128; s > 0; s >>= 1) {
+            if (threadIdx.x < s) {
+                double a = red[threadIdx.x], c = red[threadIdx.x + s];
+                red[threadIdx.x] = (q == 3 || q == 8) ? fmax(a, c) : ((q == 7 || q == 9) ? fmin(a, c) : a + c);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[blockIdx.x * NDIAG + q] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_diag_final(const double *part, int nblocks, double *out)
+{
+    int q = threadIdx.x;
+    if (q >= NDIAG) return;
+    double acc = (q == 7 || q == 9) ? 1e300 : ((q == 8) ? -1e300 : 0.0);
+    for (int k = 0; k < nblocks; k++) {
+        double a = part[k * NDIAG + q];
+        acc = (q == 3 || q == 8) ? fmax(acc, a) : ((q == 7 || q == 9) ? fmin(acc, a) : acc + a);
+    }
+    out[q] = acc;
+}
+
+const char *const kNames[NKERNELS] = {"predict", "cell_scan", "cell_scatter", "cell_order",
+                                      "pass_a",  "pass_b",    "pass_c",       "pass_d"};
+
+inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
+
+}  // namespace
+
+const char *kernel_name(int k) { return (k >= 0 && k < NKERNELS) ? kNames[k] : nullptr; }
+
+cudaError_t prepare_kernels()
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_pass_a, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_A))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_B))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_b<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_B))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_c<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_C))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_c<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_C))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_D))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_D))) return e;
+    return cudaSuccess;
+}
+
+static cudaError_t launch_front(const DevParams &P, const Bufs &b, cudaStream_t s, cudaEvent_t *ev)
+{
+    int nb = blocks_for(P.n, 256);
+    if (ev) cudaEventRecord(ev[0], s);
+    k_predict<<<nb, 256, 0, s>>>(P, b);
+    if (ev) cudaEventRecord(ev[1], s);
+    k_scan<<<1, 1024, 0, s>>>(P, b);
+    if (ev) cudaEventRecord(ev[2], s);
+    k_scatter<<<nb, 256, 0, s>>>(P, b);
+    if (ev) cudaEventRecord(ev[3], s);
+    k_cell_order<<<blocks_for(P.ncell, 8), 256, 0, s>>>(P, b);
+    if (ev) cudaEventRecord(ev[4], s);
+    k_pass_a<<<P.tiles * P.tiles, PT, SMEM_A, s>>>(P, b);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_step(const DevParams &P, const Bufs &b, cudaStream_t s, cudaEvent_t *ev)
+{
+    cudaError_t e = launch_front(P, b, s, ev);
+    if (e) return e;
+    int nt = P.tiles * P.tiles;
+    if (ev) cudaEventRecord(ev[5], s);
+    if (P.qnew) k_pass_b<false><<<nt, PT, SMEM_B, s>>>(P, b);
+    else k_pass_b<true><<<nt, PT, SMEM_B, s>>>(P, b);
+    if (ev) cudaEventRecord(ev[6], s);
+    if (P.qnew) k_pass_c<true><<<nt, PT, SMEM_C, s>>>(P, b);
+    else k_pass_c<false><<<nt, PT, SMEM_C, s>>>(P, b);
+    if (ev) cudaEventRecord(ev[7], s);
+    if (P.conservative) k_pass_d<true><<<nt, PT, SMEM_D, s>>>(P, b);
+    else k_pass_d<false><<<nt, PT, SMEM_D, s>>>(P, b);
+    if (ev) cudaEventRecord(ev[8], s);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_search(const DevParams &P, const Bufs &b, cudaStream_t s)
+{
+    cudaError_t e = launch_front(P, b, s, nullptr);
+    if (e) return e;
+    return cudaMemsetAsync(b.maxu, 0, sizeof(uint32_t), s);
+}
+
+cudaError_t enqueue_load(const DevParams &P, const Bufs &b, const double *x, const double *y,
+                         const double *ux, const double *uy, const double *q11, const double *q12,
+                         const double *rho, cudaStream_t s)
+{
+    k_load<<<blocks_for(P.n, 256), 256, 0, s>>>(P, b, x, y, ux, uy, q11, q12, rho);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_unpermute(const void *f, const int *id, void *out, int n, int es, cudaStream_t s)
+{
+    if (es == 8)
+        k_unpermute<unsigned long long><<<blocks_for(n, 256), 256, 0, s>>>(
+            (const unsigned long long *)f, id, (unsigned long long *)out, n);
+    else
+        k_unpermute<uint32_t><<<blocks_for(n, 256), 256, 0, s>>>((const uint32_t *)f, id, (uint32_t *)out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_export_nbrs(const DevParams &P, const Bufs &b, int *cols_tmp, cudaStream_t s)
+{
+    k_export_nbrs<<<P.tiles * P.tiles, PT, HCAP * 4, s>>>(P, b, cols_tmp);
+    return cudaGetLastError();
+}
+
+int diag_blocks(int n) { return std::min(std::max(blocks_for(n, 256), 1), 1024); }
+
+cudaError_t enqueue_diag(const DevParams &P, const Bufs &b, double *partials, int nblocks, double *out,
+                         cudaStream_t s)
+{
+    k_diag_partial<<<nblocks, 256, 0, s>>>(P, b, partials);
+    k_diag_final<<<1, 32, 0, s>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ann

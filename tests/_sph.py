@@ -1,0 +1,117 @@
+"""Helpers shared by the GPU parity tests: one parameter vocabulary mapped onto both the oracle and
+the C-ABI, runners for each side, and the error measure.
+
+Parity measure: the normwise relative error ||gpu - oracle||_2 / ||oracle||_2 of a whole field,
+the measure the 1e-5 FP32 bound is stated in.  Positions are compared through their displacement
+from the start (minimum image), since the positions themselves barely change over a step.
+"""
+import math
+
+import numpy as np
+
+import sph_inputs as si
+
+# The paper's 2D set-up for the 64 x 64 and 256 x 256 lattices (dx = 1/nx, h = 1.3 dx).
+BASE = dict(L=1.0, dt=1e-4, rho0=1.0, eta=1.0, Gamma=0.34, lam=0.7, A=0.0, B=0.0, C=1.0, K=0.04,
+            zeta=0.05, gamma_eos=7.0, beta=1.0, c0_min=0.0, c_shift=1.0 / 3.0, apd=1,
+            conservative=0, q_new_in_momentum=1)
+
+STATE = ("x", "y", "ux", "uy", "q11", "q12", "drho", "ax", "ay")
+GPU_NAME = {"x": "X", "y": "Y", "ux": "UX", "uy": "UY", "q11": "Q11", "q12": "Q12",
+            "drho": "DRHO", "ax": "AX", "ay": "AY"}
+
+
+def params(nx, **kw):
+    p = dict(BASE)
+    p["h"] = 1.3 / nx * p["L"]
+    p.update(kw)
+    return p
+
+
+def oracle_params(orc, p, nbr_mode="brute"):
+    return orc.make_params(nbr_mode=nbr_mode, **p)
+
+
+def gpu_params(B, p, n):
+    return B.ann_default_params(
+        n=n, L=p["L"], h=p["h"], dt=p["dt"], rho0=p["rho0"], eta=p["eta"], Gamma=p["Gamma"],
+        lambda_=p["lam"], A=p["A"], B=p["B"], C=p["C"], K=p["K"], zeta=p["zeta"],
+        gamma_eos=p["gamma_eos"], beta=p["beta"], c0_min=p["c0_min"], c_shift=p["c_shift"],
+        apd=p["apd"], momentum_mode=p["conservative"], q_new_in_momentum=p["q_new_in_momentum"],
+        dt_mode=0)
+
+
+def relerr(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return float(np.linalg.norm(a))
+    return float(np.linalg.norm(a - b) / nb)
+
+
+def min_image(d, L=1.0):
+    return (d + 0.5 * L) % L - 0.5 * L
+
+
+class GpuRun:
+    """A context holding one state, advanced through the C-ABI."""
+
+    def __init__(self, B, p, ic):
+        self.B = B
+        self.n = int(ic["n"]) if "n" in ic else len(ic["x"])
+        self.ctx = B.ann_create(gpu_params(B, p, self.n))
+        rho = ic.get("rho")
+        B.ann_set_particles(self.ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"], rho)
+
+    def field(self, name):
+        return self.B.ann_get_field(self.ctx, name, self.n).astype(np.float64)
+
+    def state(self):
+        return {k: self.field(GPU_NAME[k]) for k in STATE}
+
+    def step(self, k=1):
+        self.B.ann_step(self.ctx, k)
+
+    def close(self):
+        self.B.ann_destroy(self.ctx)
+        self.ctx = None
+
+
+def oracle_state(ic, rho0=1.0):
+    return {"x": ic["x"], "y": ic["y"], "ux": ic["ux"], "uy": ic["uy"], "q11": ic["q11"],
+            "q12": ic["q12"], "rho": ic.get("rho", np.full(len(ic["x"]), rho0))}
+
+
+def compare_state(gpu, orc_state, x0, y0, rho0=1.0):
+    """Normwise relative errors of every state field (positions as displacements)."""
+    out = {}
+    out["dx"] = relerr(min_image(gpu["x"] - x0), min_image(orc_state["x"] - x0))
+    out["dy"] = relerr(min_image(gpu["y"] - y0), min_image(orc_state["y"] - y0))
+    for k in ("ux", "uy", "q11", "q12", "ax", "ay"):
+        out[k] = relerr(gpu[k], orc_state[k])
+    out["drho"] = relerr(gpu["drho"], orc_state["rho"] / rho0 - 1.0)
+    return out
+
+
+def random_velocity_ic(nx, seed, u_scale=1e-3, rho_scale=0.0):
+    ic = si.jittered_lattice(nx, seed=seed)
+    r = si.uniform53(seed + 1000, 3 * ic["n"]).reshape(3, ic["n"]) - 0.5
+    ic["ux"] = u_scale * r[0]
+    ic["uy"] = u_scale * r[1]
+    ic["rho"] = 1.0 + rho_scale * r[2]
+    return ic
+
+
+def smooth_ic(nx, seed, u_amp=1e-2):
+    """Smooth periodic velocity and director fields (exercise cancellation in the pair sums)."""
+    ic = si.jittered_lattice(nx, seed=seed)
+    x, y = ic["x"], ic["y"]
+    tp = 2 * math.pi
+    ic["ux"] = u_amp * np.sin(tp * y) * np.cos(tp * x)
+    ic["uy"] = -u_amp * np.sin(tp * x) * np.cos(tp * y)
+    th = 0.7 * np.sin(tp * x) + 0.4 * np.cos(2 * tp * y)
+    ic["q11"] = 0.8 * np.cos(2 * th)
+    ic["q12"] = 0.8 * np.sin(2 * th)
+    ic["rho"] = 1.0 + 1e-4 * np.cos(tp * (x + y))
+    return ic

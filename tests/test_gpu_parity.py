@@ -1,0 +1,157 @@
+"""GPU parity against the FP64 oracle, through the C-ABI.
+
+* Neighbour lists: bit-exact (same sets) on lattices, random sets, ragged tilings, three-cell
+  boxes and particles hugging the periodic faces.
+* One step's intermediates (V, B, grad u, lap Q, k, rho_half, rho_hat, p, div Q, a, APD).
+* State fields per step over 10 steps on the 64 x 64 set-up and on 256 x 256 at three
+  activities: normwise relative error <= 1e-5 (FP32 arithmetic against FP64).
+"""
+import numpy as np
+import pytest
+
+import sph_inputs as si
+from _sph import (GpuRun, compare_state, oracle_params, oracle_state, params, random_velocity_ic,
+                  relerr, smooth_ic)
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_08919_gb300 import binding, build
+
+    build.build()
+    return binding
+
+
+def _nbr_case(name):
+    if name == "lattice64":
+        ic = si.jittered_lattice(64, seed=0)
+        return ic, 1.3 / 64
+    if name == "ragged45":         # 11 cells across: the last tile column / row is partial
+        ic = si.jittered_lattice(45, seed=2, jitter=0.3)
+        return ic, 1.3 / 45
+    if name == "random3000":       # Poisson counts: mean pi 3.3^2 = 34 neighbours, far below 64
+        ic = si.uniform_random(3000, seed=4)
+        return ic, 1.1 / np.sqrt(3000)
+    if name == "three_cells":
+        ic = si.uniform_random(160, seed=6)
+        return ic, 1.0 / 9.5 * 0.999
+    if name == "faces":
+        # 100 particles in each 2e-3 strip along the four faces, 600 uniform
+        u = si.uniform53(11, 2000).reshape(1000, 2)
+        e = 2e-3 * u[:, 0]
+        x = np.concatenate([e[:100], 1.0 - e[100:200], u[200:, 0]])
+        y = np.concatenate([u[:200, 1], e[200:300], 1.0 - e[300:400], u[400:, 1]])
+        ic = {"x": si.wrap_positions(x, 1.0), "y": si.wrap_positions(y, 1.0)}
+        ic.update({k: np.zeros(1000) for k in ("ux", "uy", "q11", "q12")})
+        return ic, 0.018
+    if name == "lattice256":
+        ic = si.jittered_lattice(256, seed=1)
+        return ic, 1.3 / 256
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("case", ["lattice64", "ragged45", "random3000", "three_cells", "faces",
+                                  "lattice256"])
+def test_neighbor_lists_bit_exact(B, orc, case):
+    ic, h = _nbr_case(case)
+    n = len(ic["x"])
+    p = params(64, h=h)
+    run = GpuRun(B, p, ic)
+    try:
+        rp_g, cols_g = B.ann_get_neighbors(run.ctx, n)
+    finally:
+        run.close()
+    mode = "cells" if n > 20000 else "brute"
+    rp_o, cols_o = orc.neighbors(ic["x"], ic["y"], 1.0, h, mode)
+    assert np.array_equal(rp_g, rp_o)
+    assert np.array_equal(cols_g, cols_o)
+
+
+def _oracle_one_step(orc, p, ic, nbr_mode="brute"):
+    st, rec = orc.step(oracle_params(orc, p, nbr_mode), oracle_state(ic), 1, record=True)
+    return st, rec
+
+
+@pytest.mark.parametrize("kind", ["random_u", "smooth"])
+def test_one_step_intermediates(B, orc, kind):
+    nx = 64
+    ic = random_velocity_ic(nx, 3, rho_scale=2e-4) if kind == "random_u" else smooth_ic(nx, 5)
+    p = params(nx, c0_min=0.05)
+    run = GpuRun(B, p, ic)
+    try:
+        B.ann_set_record(run.ctx, True)
+        run.step(1)
+        g = {k: run.field(k) for k in ("SUMW", "V", "B11", "B12", "B22", "K", "DRHO_HALF",
+                                       "DRHO_HAT", "P", "DIVQX", "DIVQY", "AX", "AY", "LAPQ11",
+                                       "LAPQ12", "GRADU_XX", "GRADU_XY", "GRADU_YX", "GRADU_YY",
+                                       "APDX", "APDY", "NNBR")}
+    finally:
+        run.close()
+    _, r = _oracle_one_step(orc, p, ic)
+    assert np.array_equal(g["NNBR"], r["nnbr"])
+    checks = {
+        "SUMW": r["sumW"], "V": r["V"], "B11": r["B11"], "B12": r["B12"], "B22": r["B22"],
+        "K": r["k"], "DRHO_HALF": r["rho_half"] - 1.0, "DRHO_HAT": r["rho_hat"] - 1.0,
+        "P": r["p"], "DIVQX": r["divQx"], "DIVQY": r["divQy"], "AX": r["ax"], "AY": r["ay"],
+        "LAPQ11": r["lapQ11"], "LAPQ12": r["lapQ12"], "GRADU_XX": r["gradu"][:, 0],
+        "GRADU_XY": r["gradu"][:, 1], "GRADU_YX": r["gradu"][:, 2], "GRADU_YY": r["gradu"][:, 3],
+    }
+    errs = {k: relerr(g[k], v) for k, v in checks.items()}
+    bad = {k: e for k, e in errs.items() if not e <= TOL}
+    assert not bad, bad
+    # APD: small displacements formed from nearly cancelling sums; FP32 resolves them to 1e-4
+    for k, ref in (("APDX", r["apdx"]), ("APDY", r["apdy"])):
+        assert relerr(g[k], ref) <= 1e-4, (k, relerr(g[k], ref))
+
+
+def _ten_steps(B, orc, nx, p, ic, nbr_mode, nsteps=10):
+    run = GpuRun(B, p, ic)
+    st = oracle_state(ic)
+    P = oracle_params(orc, p, nbr_mode)
+    worst = {}
+    try:
+        for s in range(nsteps):
+            run.step(1)
+            st, _ = orc.step(P, st, 1)
+            errs = compare_state(run.state(), st, ic["x"], ic["y"])
+            for k, e in errs.items():
+                worst[k] = max(worst.get(k, 0.0), e)
+    finally:
+        run.close()
+    return worst
+
+
+def test_ten_steps_64(B, orc):
+    """The 64 x 64 set-up: random director, S = 1, 1e-3 noise, u = 0, dt = 1e-4, zeta = 0.05."""
+    ic = si.jittered_lattice(64, seed=0)
+    worst = _ten_steps(B, orc, 64, params(64), ic, "brute")
+    bad = {k: e for k, e in worst.items() if not e <= TOL}
+    assert not bad, worst
+
+
+@pytest.mark.parametrize("zeta", [0.02, 0.05, 0.1])
+def test_ten_steps_256(B, orc, zeta):
+    ic = si.jittered_lattice(256, seed=1)
+    worst = _ten_steps(B, orc, 256, params(256, zeta=zeta), ic, "cells")
+    bad = {k: e for k, e in worst.items() if not e <= TOL}
+    assert not bad, worst
+
+
+@pytest.mark.parametrize("variant", ["conservative", "q_old", "c_half", "no_apd", "beta_half",
+                                     "landau_A"])
+def test_variants_five_steps(B, orc, variant):
+    kw = {"conservative": dict(conservative=1, c0_min=0.05), "q_old": dict(q_new_in_momentum=0),
+          "c_half": dict(c_shift=0.5), "no_apd": dict(apd=0), "beta_half": dict(beta=0.5),
+          "landau_A": dict(A=0.3, C=0.5)}[variant]
+    ic = random_velocity_ic(48, 9, rho_scale=1e-4)
+    worst = _ten_steps(B, orc, 48, params(48, **kw), ic, "brute", nsteps=5)
+    bad = {k: e for k, e in worst.items() if not e <= TOL}
+    assert not bad, worst

@@ -1,0 +1,186 @@
+"""GPU behaviour at full size and at the edges, through the C-ABI.
+
+* The 1024 x 1024 (~1.05 M particle) high-resolution set-up, in the launch configuration the
+  benchmark times: two steps against the oracle on every particle (the oracle's cell-grid search,
+  itself pinned bit-exact to brute force).
+* Error statuses raised on the host or by the kernels' own bounds checks: wrong n, NaN input,
+  an overfull cell, stepping before loading; none of them faults the device.
+* Checkpoint and resume continue bit-identically; two contexts on the same input agree bitwise.
+* Conservative momentum mode keeps total momentum to FP32 round-off on the GPU.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import sph_inputs as si
+from _sph import (GpuRun, compare_state, gpu_params, oracle_params, oracle_state, params,
+                  random_velocity_ic)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_08919_gb300 import binding, build
+
+    build.build()
+    return binding
+
+
+def test_full_size_two_steps(B, orc):
+    p = params(1024, zeta=0.08, K=0.02)
+    gp = gpu_params(B, p, 1024 * 1024)
+    gp.dt_mode = 1
+    p["dt"] = B.ann_grid_info(gp).dt_effective
+    ic = si.jittered_lattice(1024, seed=0)
+    run = GpuRun(B, p, ic)
+    st = oracle_state(ic)
+    P = oracle_params(orc, p, "cells")
+    try:
+        for _ in range(2):
+            run.step(1)
+            st, rec = orc.step(P, st, 1, record=True)
+            errs = compare_state(run.state(), st, ic["x"], ic["y"])
+            bad = {k: e for k, e in errs.items() if not e <= 1e-5}
+            assert not bad, errs
+        assert np.array_equal(run.field("NNBR"), rec["nnbr"])
+        d = B.ann_get_diagnostics(run.ctx)
+        assert d["error_bits"] == 0 and d["nbr_min"] == 44 and d["nbr_max"] == 44
+    finally:
+        run.close()
+
+
+def test_wrong_n_and_null_inputs(B):
+    ic = si.jittered_lattice(32, seed=0)
+    ctx = B.ann_create(gpu_params(B, params(32), 32 * 32))
+    try:
+        with pytest.raises(B.AnnError) as e:
+            B.ann_set_particles(ctx, ic["x"][:-1], ic["y"][:-1], ic["ux"][:-1], ic["uy"][:-1],
+                                ic["q11"][:-1], ic["q12"][:-1])
+        assert e.value.status == -1
+        with pytest.raises(B.AnnError) as e:
+            B.ann_step(ctx, 1)
+        assert e.value.status == -9            # no particles yet
+        with pytest.raises(B.AnnError) as e:
+            B.ann_get_field(ctx, "UX", 1024)
+        assert e.value.status == -9
+    finally:
+        B.ann_destroy(ctx)
+
+
+def test_nonfinite_input_is_rejected(B):
+    ic = si.jittered_lattice(32, seed=0)
+    ctx = B.ann_create(gpu_params(B, params(32), 32 * 32))
+    try:
+        q = ic["q11"].copy()
+        q[100] = np.nan
+        with pytest.raises(B.AnnError) as e:
+            B.ann_set_particles(ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], q, ic["q12"])
+        assert e.value.status == -6
+        # a clean load afterwards works and steps
+        B.ann_set_particles(ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"])
+        B.ann_step(ctx, 2)
+    finally:
+        B.ann_destroy(ctx)
+
+
+def test_overfull_cell_is_reported_not_faulted(B):
+    # 100 extra particles piled into one cell: the cell-capacity check raises CELL_OVERFLOW
+    ic = si.jittered_lattice(32, seed=0)
+    x, y = ic["x"].copy(), ic["y"].copy()
+    x[:100] = 0.5 + 1e-4 * np.arange(100) / 100
+    y[:100] = 0.5
+    ctx = B.ann_create(gpu_params(B, params(32), 32 * 32))
+    try:
+        B.ann_set_particles(ctx, x, y, ic["ux"], ic["uy"], ic["q11"], ic["q12"])
+        with pytest.raises(B.AnnError) as e:
+            B.ann_step(ctx, 1)
+        assert e.value.status == -4
+        assert B.ann_get_diagnostics(ctx)["error_bits"] & 1
+        # the context stays usable: a fresh load clears the sticky bits
+        B.ann_set_particles(ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"])
+        B.ann_step(ctx, 1)
+    finally:
+        B.ann_destroy(ctx)
+
+
+def test_checkpoint_resume_is_bit_identical(B, tmp_path):
+    ic = random_velocity_ic(64, 4)
+    p = params(64, c0_min=0.05)
+    a = GpuRun(B, p, ic)
+    b = GpuRun(B, p, ic)
+    try:
+        a.step(20)
+        b.step(10)
+        path = str(tmp_path / "state.bin")
+        B.ann_save_state(b.ctx, path)
+        b.close()
+        c = GpuRun(B, p, si.jittered_lattice(64, seed=99))
+        B.ann_load_state(c.ctx, path)
+        assert B.ann_get_diagnostics(c.ctx)["step"] == 10
+        c.step(10)
+        sa, sc = a.state(), c.state()
+        for k in sa:
+            assert np.array_equal(sa[k], sc[k]), k
+        c.close()
+    finally:
+        a.close()
+
+
+def test_two_contexts_agree_bitwise(B):
+    ic = random_velocity_ic(96, 5)
+    p = params(96, c0_min=0.05)
+    runs = [GpuRun(B, p, ic) for _ in range(2)]
+    try:
+        for r in runs:
+            r.step(15)
+        s0, s1 = runs[0].state(), runs[1].state()
+        for k in s0:
+            assert np.array_equal(s0[k], s1[k]), k
+    finally:
+        for r in runs:
+            r.close()
+
+
+def test_conservative_momentum_on_gpu(B):
+    ic = random_velocity_ic(64, 8)
+    p = params(64, conservative=1, c0_min=0.5, eta=0.05, dt=5e-5)
+    run = GpuRun(B, p, ic)
+    try:
+        m = 1.0 / run.n
+        p0 = m * np.array([ic["ux"].sum(), ic["uy"].sum()])
+        run.step(100)
+        s = run.state()
+        p1 = m * np.array([s["ux"].sum(), s["uy"].sum()])
+        scale = m * (np.abs(s["ux"]).sum() + np.abs(s["uy"]).sum())
+        assert np.abs(s["ux"] - ic["ux"]).max() > 1e-6
+        assert np.abs(p1 - p0).max() <= 1e-5 * scale
+    finally:
+        run.close()
+
+
+def test_device_inputs_and_outputs(B):
+    import torch
+
+    ic = si.jittered_lattice(48, seed=3)
+    n = ic["n"]
+    p = params(48)
+    dev = {k: torch.tensor(ic[k], dtype=torch.float64, device="cuda") for k in
+           ("x", "y", "ux", "uy", "q11", "q12", "rho")}
+    ctx = B.ann_create(gpu_params(B, p, n))
+    try:
+        B.ann_set_stream(ctx, torch.cuda.current_stream())
+        B.ann_set_particles(ctx, dev["x"], dev["y"], dev["ux"], dev["uy"], dev["q11"], dev["q12"],
+                            dev["rho"])
+        B.ann_step(ctx, 3)
+        out = torch.empty(n, dtype=torch.float32, device="cuda")
+        B.ann_get_field(ctx, "Q11", n, out=out)
+        host = B.ann_get_field(ctx, "Q11", n)
+        assert np.array_equal(out.cpu().numpy(), host)
+    finally:
+        B.ann_destroy(ctx)
