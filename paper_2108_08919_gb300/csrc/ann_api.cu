@@ -88,7 +88,7 @@ int64_t device_bytes(const ann_params &p)
 {
     int64_t n = p.n, nc = cells_per_side(p), ncell = nc * nc;
     int64_t per = 2 * 8 + 7 * 4 + 4           // S
-                  + 2 * 8 + 7 * 4 + 4         // M
+                  + 2 * 8 + 5 * 4 + 16 + 4    // M
                   + 3 * 4                     // key, rank, perm
                   + (MAXN / 2) * 4 + 4        // lists, counts
                   + 11 * 4                    // intermediates
@@ -152,10 +152,18 @@ DevParams make_dev(const ann_params &p)
     double dt = effective_dt(p);
     d.dt_d = dt;
     d.half_dt_d = 0.5 * dt;
-    d.cell_f = (float)d.cell;
-    // The FP32 |d|^2 from tile-local coordinates is within ~2e-5 (3h)^2 of the FP64 value; pairs
-    // inside a band of +-2^-13 relative are decided in FP64.
-    const double band = 1.0 / 8192.0;
+    // Pair vectors are formed as (hi_i - hi_j) + (lo_i - lo_j): the hi parts lie on a power-of-two
+    // grid q = 2^(floor(log2 cell) - 12) with at most 16 significant bits, so their difference is
+    // exact in FP32 and d is correctly rounded up to ~2^-33 cell.  |d|^2 is then within
+    // 4 * 2^-24 of the FP64 value; pairs within a relative band of 2^-20 of (3h)^2 are decided in
+    // FP64 from the positions, exactly as the definition states.
+    int ex = 0;
+    std::frexp(d.cell, &ex);               // cell = m 2^ex, m in [0.5, 1)
+    d.q = std::ldexp(1.0, ex - 13);
+    double chi = std::nearbyint(d.cell / d.q) * d.q;
+    d.cell_hi = (float)chi;
+    d.cell_lo = (float)(d.cell - chi);
+    const double band = 1.0 / 1048576.0;
     d.R2lo = (float)(d.R2 * (1.0 - band));
     d.R2hi = (float)(d.R2 * (1.0 + band));
     d.inv_h = (float)(1.0 / p.h);
@@ -201,8 +209,7 @@ cudaError_t alloc_all(ann_ctx *c)
 #define A_(p, cnt) if ((e = dalloc(c, b.p, cnt))) return e
     A_(sx, n); A_(sy, n); A_(sux, n); A_(suy, n); A_(sq11, n); A_(sq12, n); A_(sdr, n); A_(sax, n);
     A_(say, n); A_(sid, n);
-    A_(mx, n); A_(my, n); A_(mux, n); A_(muy, n); A_(mq11, n); A_(mq12, n); A_(mdr, n); A_(xix, n);
-    A_(xiy, n); A_(mid, n);
+    A_(mx, n); A_(my, n); A_(mux, n); A_(muy, n); A_(mq11, n); A_(mq12, n); A_(mdr, n); A_(xi, n); A_(mid, n);
     A_(cell_count, ncell + 1); A_(cell_start, ncell + 1); A_(key, n); A_(rank, n); A_(perm, n);
     A_(nbr, n * (MAXN / 2)); A_(nnbr, n);
     A_(sumW, n); A_(V, n); A_(B11, n); A_(B12, n); A_(B22, n); A_(kr, n); A_(dh, n); A_(dhat, n);

@@ -31,7 +31,9 @@ struct DevParams {
     int n, nc, ncell, tiles;
     int apd, conservative, qnew, record;
     double L, cell, inv_cell, R2, dt_d, half_dt_d;
-    float cell_f, R2lo, R2hi, inv_h, ad, W0, Fc, dt, half_dt;
+    double q;              // power-of-two grid of the "hi" coordinate part: cell / q in [2^12, 2^13)
+    float cell_hi, cell_lo;  // cell = cell_hi + cell_lo, cell_hi a multiple of q
+    float R2lo, R2hi, inv_h, ad, W0, Fc, dt, half_dt;
     float rho0, nu, mu, Gamma, lambda, A, C, K, zeta, gamma_eos, beta, c0_min, c_shift, mass;
 };
 
@@ -42,7 +44,8 @@ struct Bufs {
     float *sux, *suy, *sq11, *sq12, *sdr, *sax, *say;
     int *sid;
     double *mx, *my;
-    float *mux, *muy, *mq11, *mq12, *mdr, *xix, *xiy;
+    float *mux, *muy, *mq11, *mq12, *mdr;
+    float4 *xi;         // cell-local offset split as (hi_x, hi_y, lo_x, lo_y), hi on the q grid
     int *mid;
     uint32_t *cell_count, *cell_start, *key, *rank, *perm;
     uint32_t *nbr;      // packed slot pairs, (MAXN/2) x n, row-major in the pair index

@@ -4,10 +4,11 @@
 // cells are numbered row-major.  A pair pass runs one block per 4 x 4 cells ("tile"): the block
 // stages the particles of the surrounding 6 x 6 cells in shared memory -- periodic images of the
 // cells on the far side of the box take the place of the paper's ghost particles (Eq. 30) -- and
-// each thread accumulates the sums of one particle over its neighbours.  Pair vectors are formed in
-// FP32 from tile-local coordinates; the support test |d|^2 < (3h)^2 is decided in FP32 unless it
-// falls within a rounding band of the cutoff, where it is redone in FP64 from the FP64 positions
-// exactly as the definition states.
+// each thread accumulates the sums of one particle over its neighbours.  Positions are FP64; the pair
+// passes use a split tile-local coordinate hi + lo in FP32 whose hi parts lie on a power-of-two grid,
+// so d = (hi_i - hi_j) + (lo_i - lo_j) is the correctly rounded FP32 pair vector.  The support test
+// |d|^2 < (3h)^2 is decided in FP32 unless it falls within a rounding band of the cutoff, where it is
+// redone in FP64 from the FP64 positions exactly as the definition states.
 #include "ann_internal.cuh"
 
 #include <cmath>
@@ -132,10 +133,11 @@ __device__ __forceinline__ int inner_slot(const TileShared &ts, const Tile &T, i
     return ts.off[(r + 1) * T.HX + 1] + (q - ts.rowpre[r]);
 }
 
-// Sorted index and tile-local position of slot t.
+// Sorted index and tile-local position (hi_x, hi_y, lo_x, lo_y) of slot t.  The halo cell offset
+// hx * cell is added as hx * cell_hi (exact on the q grid) plus hx * cell_lo.
 struct SlotInfo {
     int g, h;
-    float ex, ey;
+    float4 e;
 };
 
 __device__ __forceinline__ SlotInfo slot_info(const DevParams &P, const Bufs &b, const TileShared &ts,
@@ -144,10 +146,16 @@ __device__ __forceinline__ SlotInfo slot_info(const DevParams &P, const Bufs &b,
     SlotInfo s;
     s.h = slot_cell(ts, T.NH, t);
     s.g = ts.start[s.h] + (t - ts.off[s.h]);
-    int hx = s.h % T.HX, hy = s.h / T.HX;
-    s.ex = b.xix[s.g] + (float)hx * P.cell_f;
-    s.ey = b.xiy[s.g] + (float)hy * P.cell_f;
+    float hx = (float)(s.h % T.HX), hy = (float)(s.h / T.HX);
+    float4 o = b.xi[s.g];
+    s.e = make_float4(o.x + hx * P.cell_hi, o.y + hy * P.cell_hi, o.z + hx * P.cell_lo, o.w + hy * P.cell_lo);
     return s;
+}
+
+// Pair vector d_ij from two split tile-local positions.
+__device__ __forceinline__ float2 pair_d(const float4 &a, const float4 &b)
+{
+    return make_float2((a.x - b.x) + (a.z - b.z), (a.y - b.y) + (a.w - b.w));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -297,13 +305,15 @@ __global__ void __launch_bounds__(256) k_cell_order(DevParams P, Bufs b)
     __syncwarp();
     int cx = c % P.nc, cy = c / P.nc;
     double ox = (double)cx * P.cell, oy = (double)cy * P.cell;
+    double iq = 1.0 / P.q;   // power of two: exact
     for (int s = lane; s < cnt; s += 32) {
         uint32_t old = srt[w][s], g = start + (uint32_t)s;
         double x = b.sx[old], y = b.sy[old];
         b.mx[g] = x;
         b.my[g] = y;
-        b.xix[g] = (float)(x - ox);
-        b.xiy[g] = (float)(y - oy);
+        double ux_ = x - ox, uy_ = y - oy;
+        double hx = rint(ux_ * iq) * P.q, hy = rint(uy_ * iq) * P.q;
+        b.xi[g] = make_float4((float)hx, (float)hy, (float)(ux_ - hx), (float)(uy_ - hy));
         b.mux[g] = b.sux[old];
         b.muy[g] = b.suy[old];
         b.mq11[g] = b.sq11[old];
@@ -317,14 +327,14 @@ __global__ void __launch_bounds__(256) k_cell_order(DevParams P, Bufs b)
 // Kernel 4: pass A -- neighbour lists, sum_j W_ij (self included) and V = 1/sum  (Eqs. 18, 19)
 // ---------------------------------------------------------------------------------------------
 
-constexpr int SMEM_A = HCAP * (8 + 4 + 1) + MAXN * PT * 2;
+constexpr int SMEM_A = HCAP * (16 + 4 + 1) + MAXN * PT * 2;
 
 __global__ void __launch_bounds__(PT) k_pass_a(DevParams P, Bufs b)
 {
     if (stopped(b)) return;
     __shared__ TileShared ts;
     extern __shared__ __align__(16) unsigned char dsm[];
-    float2 *pos = reinterpret_cast<float2 *>(dsm);
+    float4 *pos = reinterpret_cast<float4 *>(dsm);
     int *sg = reinterpret_cast<int *>(pos + HCAP);
     uint16_t *lst = reinterpret_cast<uint16_t *>(sg + HCAP);
     unsigned char *shc = reinterpret_cast<unsigned char *>(lst + MAXN * PT);
@@ -335,7 +345,7 @@ __global__ void __launch_bounds__(PT) k_pass_a(DevParams P, Bufs b)
     }
     for (int t = threadIdx.x; t < T.H; t += PT) {
         SlotInfo s = slot_info(P, b, ts, T, t);
-        pos[t] = make_float2(s.ex, s.ey);
+        pos[t] = s.e;
         sg[t] = s.g;
         shc[t] = (unsigned char)s.h;
     }
@@ -343,15 +353,14 @@ __global__ void __launch_bounds__(PT) k_pass_a(DevParams P, Bufs b)
     for (int q = threadIdx.x; q < T.Ni; q += PT) {
         int si = inner_slot(ts, T, q);
         int h = shc[si], hx = h % T.HX, hy = h / T.HX;
-        float2 pi = pos[si];
+        float4 pi = pos[si];
         int cnt = 0;
         for (int oy = -1; oy <= 1; oy++) {
             int row = (hy + oy) * T.HX + hx;
             int j0 = ts.off[row - 1], j1 = ts.off[row + 2];
             for (int j = j0; j < j1; j++) {
-                float2 pj = pos[j];
-                float dx = pi.x - pj.x, dy = pi.y - pj.y;
-                float r2 = dx * dx + dy * dy;
+                float2 d = pair_d(pi, pos[j]);
+                float r2 = d.x * d.x + d.y * d.y;
                 bool in = r2 < P.R2lo;
                 if (!in && r2 < P.R2hi) {
                     int hj = shc[j];
@@ -371,9 +380,8 @@ __global__ void __launch_bounds__(PT) k_pass_a(DevParams P, Bufs b)
         int c = min(cnt, MAXN);
         float sw = P.W0;
         for (int k = 0; k < c; k++) {
-            float2 pj = pos[lst[k * PT + threadIdx.x]];
-            float dx = pi.x - pj.x, dy = pi.y - pj.y;
-            sw += kernel_w(dx * dx + dy * dy, P);
+            float2 d = pair_d(pi, pos[lst[k * PT + threadIdx.x]]);
+            sw += kernel_w(d.x * d.x + d.y * d.y, P);
         }
         int gi = sg[si];
         b.sumW[gi] = sw;
@@ -400,7 +408,7 @@ __device__ __forceinline__ int nbr_slot(const DevParams &P, const Bufs &b, int g
 // field (Eq. 7), co-rotation term (Eq. 2) and the Q update of Eq. (24).
 // ---------------------------------------------------------------------------------------------
 
-constexpr int SMEM_B = HCAP * (16 + 16 + 4);
+constexpr int SMEM_B = HCAP * (16 + 16 + 4 + 4);
 
 template <bool QOLD>
 __global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
@@ -408,9 +416,10 @@ __global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
     if (stopped(b)) return;
     __shared__ TileShared ts;
     extern __shared__ __align__(16) unsigned char dsm[];
-    float4 *sa = reinterpret_cast<float4 *>(dsm);     // (x, y, V, ux)
-    float4 *sb = sa + HCAP;                           // (uy, q11, q12, -)
-    int *sg = reinterpret_cast<int *>(sb + HCAP);
+    float4 *sp = reinterpret_cast<float4 *>(dsm);     // split position
+    float4 *sb = sp + HCAP;                           // (V, ux, uy, q11)
+    float *sq = reinterpret_cast<float *>(sb + HCAP); // q12
+    int *sg = reinterpret_cast<int *>(sq + HCAP);
     Tile T;
     if (!tile_begin(P, b, ts, T)) {
         if (threadIdx.x == 0) atomicOr(b.err, EB_HALO);
@@ -418,15 +427,17 @@ __global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
     }
     for (int t = threadIdx.x; t < T.H; t += PT) {
         SlotInfo s = slot_info(P, b, ts, T, t);
-        sa[t] = make_float4(s.ex, s.ey, b.V[s.g], b.mux[s.g]);
-        sb[t] = make_float4(b.muy[s.g], b.mq11[s.g], b.mq12[s.g], 0.f);
+        sp[t] = s.e;
+        sb[t] = make_float4(b.V[s.g], b.mux[s.g], b.muy[s.g], b.mq11[s.g]);
+        sq[t] = b.mq12[s.g];
         sg[t] = s.g;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < T.Ni; q += PT) {
         int si = inner_slot(ts, T, q);
         int gi = sg[si];
-        float4 ai = sa[si], bi = sb[si];
+        float4 pi = sp[si], bi = sb[si];
+        float q2i = sq[si];
         float a11 = 0.f, a12 = 0.f, a22 = 0.f;
         float l00 = 0.f, l01 = 0.f, l10 = 0.f, l11 = 0.f;
         float r1xx = 0.f, r1xy = 0.f, r1yy = 0.f, r2xx = 0.f, r2xy = 0.f, r2yy = 0.f;
@@ -436,23 +447,23 @@ __global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
         for (int k = 0; k < c; k++) {
             int j = nbr_slot(P, b, gi, k, w);
             if (j >= T.H) continue;
-            float4 aj = sa[j], bj = sb[j];
-            float dx = ai.x - aj.x, dy = ai.y - aj.y;
-            float r2 = dx * dx + dy * dy;
+            float4 bj = sb[j];
+            float2 d = pair_d(pi, sp[j]);
+            float r2 = d.x * d.x + d.y * d.y;
             float Wv, F, rinv;
             kernel_wf(r2, P, Wv, F, rinv);
-            float g = aj.z * F;
-            float gx = g * dx, gy = g * dy;
-            float mxx = gx * dx, mxy = gx * dy, myy = gy * dy;
+            float g = bj.x * F;
+            float gx = g * d.x, gy = g * d.y;
+            float mxx = gx * d.x, mxy = gx * d.y, myy = gy * d.y;
             a11 -= mxx;
             a12 -= mxy;
             a22 -= myy;
-            float dux = aj.w - ai.w, duy = bj.x - bi.x;
+            float dux = bj.y - bi.y, duy = bj.z - bi.z;
             l00 += dux * gx;
             l01 += dux * gy;
             l10 += duy * gx;
             l11 += duy * gy;
-            float dq1 = bj.y - bi.y, dq2 = bj.z - bi.z;
+            float dq1 = bj.w - bi.w, dq2 = sq[j] - q2i;
             float rinv2 = rinv * rinv;
             float e1 = -dq1 * rinv2, e2 = -dq2 * rinv2;
             r1xx += e1 * mxx;
@@ -483,7 +494,7 @@ __global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
         // Q rate, projected on symmetric traceless tensors.  With E = sym(D), w = (D10 - D01)/2:
         //   S_tl = lambda tr(E) Q + 2 c lambda E_tl + (Omega Q - Q Omega) - 2 lambda (Q:E) Q
         //   H_tl = -A Q - C tr(Q^2) Q + K lap Q        (the B term of Eq. 7 is isotropic in 2D)
-        float q1 = bi.y, q2 = bi.z;
+        float q1 = bi.w, q2 = q2i;
         float E12 = 0.5f * (D01 + D10), om = 0.5f * (D10 - D01);
         float QE = q1 * (D00 - D11) + 2.f * q2 * E12;
         float trQ2 = 2.f * (q1 * q1 + q2 * q2);
@@ -521,7 +532,7 @@ __global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
 // Kernel 6: pass C -- density filter (Eq. 28), equation of state (Eq. 26), div Q^{n+1}
 // ---------------------------------------------------------------------------------------------
 
-constexpr int SMEM_C = HCAP * (16 + 8 + 4);
+constexpr int SMEM_C = HCAP * (16 + 16 + 4);
 
 template <bool QNEW>
 __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
@@ -529,9 +540,9 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
     if (stopped(b)) return;
     __shared__ TileShared ts;
     extern __shared__ __align__(16) unsigned char dsm[];
-    float4 *sa = reinterpret_cast<float4 *>(dsm);      // (x, y, V, dh)
-    float2 *sq = reinterpret_cast<float2 *>(sa + HCAP); // Q^{n+1}
-    int *sg = reinterpret_cast<int *>(sq + HCAP);
+    float4 *sp = reinterpret_cast<float4 *>(dsm);      // split position
+    float4 *sb = sp + HCAP;                            // (V, drho_half, q11^{n+1}, q12^{n+1})
+    int *sg = reinterpret_cast<int *>(sb + HCAP);
     Tile T;
     if (!tile_begin(P, b, ts, T)) {
         if (threadIdx.x == 0) atomicOr(b.err, EB_HALO);
@@ -539,8 +550,9 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
     }
     for (int t = threadIdx.x; t < T.H; t += PT) {
         SlotInfo s = slot_info(P, b, ts, T, t);
-        sa[t] = make_float4(s.ex, s.ey, b.V[s.g], b.dh[s.g]);
-        sq[t] = QNEW ? make_float2(b.sq11[s.g], b.sq12[s.g]) : make_float2(0.f, 0.f);
+        sp[t] = s.e;
+        sb[t] = QNEW ? make_float4(b.V[s.g], b.dh[s.g], b.sq11[s.g], b.sq12[s.g])
+                     : make_float4(b.V[s.g], b.dh[s.g], 0.f, 0.f);
         sg[t] = s.g;
     }
     __syncthreads();
@@ -549,32 +561,30 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
     for (int q = threadIdx.x; q < T.Ni; q += PT) {
         int si = inner_slot(ts, T, q);
         int gi = sg[si];
-        float4 ai = sa[si];
-        float2 qi = sq[si];
+        float4 pi = sp[si], bi = sb[si];
         float shep = 0.f, g1x = 0.f, g1y = 0.f, g2x = 0.f, g2y = 0.f;
         int c = b.nnbr[gi];
         uint32_t w = 0;
         for (int k = 0; k < c; k++) {
             int j = nbr_slot(P, b, gi, k, w);
             if (j >= T.H) continue;
-            float4 aj = sa[j];
-            float dx = ai.x - aj.x, dy = ai.y - aj.y;
-            float r2 = dx * dx + dy * dy;
+            float4 bj = sb[j];
+            float2 d = pair_d(pi, sp[j]);
+            float r2 = d.x * d.x + d.y * d.y;
             float Wv, F, rinv;
             kernel_wf(r2, P, Wv, F, rinv);
-            shep += (ai.w - aj.w) * Wv;
+            shep += (bi.y - bj.y) * Wv;
             if (QNEW) {
-                float2 qj = sq[j];
-                float g = aj.z * F;
-                float gx = g * dx, gy = g * dy;
-                float dq1 = qj.x - qi.x, dq2 = qj.y - qi.y;
+                float g = bj.x * F;
+                float gx = g * d.x, gy = g * d.y;
+                float dq1 = bj.z - bi.z, dq2 = bj.w - bi.w;
                 g1x += dq1 * gx;
                 g1y += dq1 * gy;
                 g2x += dq2 * gx;
                 g2y += dq2 * gy;
             }
         }
-        float dhat = ai.w - P.beta * shep / b.sumW[gi];
+        float dhat = bi.y - P.beta * shep / b.sumW[gi];
         b.dhat[gi] = dhat;
         b.p[gi] = pref * expm1f(P.gamma_eos * log1pf(dhat));
         if (QNEW) {
@@ -591,7 +601,7 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
 // Kernel 7: pass D -- momentum (Eq. 23), corrector (§3.1), APD (Eq. 29), re-insertion (Eq. 30)
 // ---------------------------------------------------------------------------------------------
 
-constexpr int SMEM_D = HCAP * (16 + 16 + 4);
+constexpr int SMEM_D = HCAP * (16 + 16 + 8 + 4);
 
 template <bool CONS>
 __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
@@ -599,9 +609,10 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
     if (stopped(b)) return;
     __shared__ TileShared ts;
     extern __shared__ __align__(16) unsigned char dsm[];
-    float4 *sa = reinterpret_cast<float4 *>(dsm);      // paper: (x, y, V, p/rho^2)   cons: (x, y, p/rho^2, 1/rho)
-    float4 *sb = sa + HCAP;                            // paper: (ux, uy, -, -)        cons: (ux, uy, q11/rho^2, q12/rho^2)
-    int *sg = reinterpret_cast<int *>(sb + HCAP);
+    float4 *sp = reinterpret_cast<float4 *>(dsm);       // split position
+    float4 *sb = sp + HCAP;                             // paper: (V, p/rho^2, ux, uy)  cons: (p/rho^2, 1/rho, ux, uy)
+    float2 *sc = reinterpret_cast<float2 *>(sb + HCAP); // cons: (q11/rho^2, q12/rho^2)
+    int *sg = reinterpret_cast<int *>(sc + HCAP);
     Tile T;
     if (!tile_begin(P, b, ts, T)) {
         if (threadIdx.x == 0) atomicOr(b.err, EB_HALO);
@@ -612,14 +623,14 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
         float rho = P.rho0 * (1.f + b.dhat[s.g]);
         float irho = 1.f / rho;
         float pr = b.p[s.g] * irho * irho;
+        sp[t] = s.e;
         if (CONS) {
             float q1 = P.qnew ? b.sq11[s.g] : b.mq11[s.g];
             float q2 = P.qnew ? b.sq12[s.g] : b.mq12[s.g];
-            sa[t] = make_float4(s.ex, s.ey, pr, irho);
-            sb[t] = make_float4(b.mux[s.g], b.muy[s.g], q1 * irho * irho, q2 * irho * irho);
+            sb[t] = make_float4(pr, irho, b.mux[s.g], b.muy[s.g]);
+            sc[t] = make_float2(q1 * irho * irho, q2 * irho * irho);
         } else {
-            sa[t] = make_float4(s.ex, s.ey, b.V[s.g], pr);
-            sb[t] = make_float4(b.mux[s.g], b.muy[s.g], 0.f, 0.f);
+            sb[t] = make_float4(b.V[s.g], pr, b.mux[s.g], b.muy[s.g]);
         }
         sg[t] = s.g;
     }
@@ -628,7 +639,8 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
     for (int q = threadIdx.x; q < T.Ni; q += PT) {
         int si = inner_slot(ts, T, q);
         int gi = sg[si];
-        float4 ai = sa[si], bi = sb[si];
+        float4 pi = sp[si], bi = sb[si];
+        float2 ci = CONS ? sc[si] : make_float2(0.f, 0.f);
         float fx = 0.f, fy = 0.f, vx = 0.f, vy = 0.f;
         float sux = 0.f, suy = 0.f, sr = 0.f, sdx = 0.f, sdy = 0.f;
         int c = b.nnbr[gi];
@@ -636,36 +648,36 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
         for (int k = 0; k < c; k++) {
             int j = nbr_slot(P, b, gi, k, w);
             if (j >= T.H) continue;
-            float4 aj = sa[j], bj = sb[j];
-            float dx = ai.x - aj.x, dy = ai.y - aj.y;
-            float r2 = dx * dx + dy * dy;
+            float4 bj = sb[j];
+            float2 d = pair_d(pi, sp[j]);
+            float r2 = d.x * d.x + d.y * d.y;
             float Wv, F, rinv;
             kernel_wf(r2, P, Wv, F, rinv);
-            float ux = bi.x - bj.x, uy = bi.y - bj.y;
-            float ud = ux * dx + uy * dy;
+            float ux = bi.z - bj.z, uy = bi.w - bj.w;
+            float ud = ux * d.x + uy * d.y;
             float rinv2 = rinv * rinv;
             if (CONS) {
-                float gx = F * dx, gy = F * dy;
-                float cp = ai.z + aj.z;
-                float visc = 8.f * P.mu * ai.w * aj.w * ud * rinv2;
-                float qa = bi.z + bj.z, qb = bi.w + bj.w;
+                float2 cj = sc[j];
+                float gx = F * d.x, gy = F * d.y;
+                float cp = bi.x + bj.x;
+                float visc = 8.f * P.mu * bi.y * bj.y * ud * rinv2;
+                float qa = ci.x + cj.x, qb = ci.y + cj.y;
                 fx += (visc - cp) * gx - P.zeta * (qa * gx + qb * gy);
                 fy += (visc - cp) * gy - P.zeta * (qb * gx - qa * gy);
             } else {
-                float cp = aj.z * (ai.w + aj.w) * F;
-                fx += cp * dx;
-                fy += cp * dy;
-                float v = aj.z * ud * F * rinv2;
-                vx += v * dx;
-                vy += v * dy;
+                float cp = bj.x * (bi.y + bj.y) * F;
+                fx += cp * d.x;
+                fy += cp * d.y;
+                float v = bj.x * ud * F * rinv2;
+                vx += v * d.x;
+                vy += v * d.y;
             }
             sux += ux * Wv;
             suy += uy * Wv;
-            float r = r2 * rinv;
-            sr += r;
+            sr += r2 * rinv;
             float rinv3 = rinv2 * rinv;
-            sdx += dx * rinv3;
-            sdy += dy * rinv3;
+            sdx += d.x * rinv3;
+            sdy += d.y * rinv3;
         }
         float ax, ay;
         float dhat = b.dhat[gi];
@@ -682,14 +694,14 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
             ax = -rho * pbx + kv * vbx - P.zeta * irho * b.divx[gi];
             ay = -rho * pby + kv * vby - P.zeta * irho * b.divy[gi];
         }
-        float unx = bi.x + P.half_dt * ax, uny = bi.y + P.half_dt * ay;
+        float unx = bi.z + P.half_dt * ax, uny = bi.w + P.half_dt * ay;
         float apx = 0.f, apy = 0.f;
         if (P.apd && c > 0) {
             float uv = sqrtf(sux * sux + suy * suy) / b.sumW[gi];
             float r0 = sr / (float)c;
-            float s = P.dt * uv * r0 * r0;
-            apx = s * sdx;
-            apy = s * sdy;
+            float sc_ = P.dt * uv * r0 * r0;
+            apx = sc_ * sdx;
+            apy = sc_ * sdy;
         }
         double xn = wrap_d(b.mx[gi] + P.half_dt_d * (double)unx + (double)apx, P.L);
         double yn = wrap_d(b.my[gi] + P.half_dt_d * (double)uny + (double)apy, P.L);

@@ -11,7 +11,7 @@ import pytest
 
 import sph_inputs as si
 from _sph import (GpuRun, compare_state, oracle_params, oracle_state, params, random_velocity_ic,
-                  relerr, smooth_ic)
+                  relerr, relerr_group, smooth_ic, stable_dt)
 
 pytestmark = pytest.mark.gpu
 
@@ -97,19 +97,23 @@ def test_one_step_intermediates(B, orc, kind):
         run.close()
     _, r = _oracle_one_step(orc, p, ic)
     assert np.array_equal(g["NNBR"], r["nnbr"])
-    checks = {
-        "SUMW": r["sumW"], "V": r["V"], "B11": r["B11"], "B12": r["B12"], "B22": r["B22"],
-        "K": r["k"], "DRHO_HALF": r["rho_half"] - 1.0, "DRHO_HAT": r["rho_hat"] - 1.0,
-        "P": r["p"], "DIVQX": r["divQx"], "DIVQY": r["divQy"], "AX": r["ax"], "AY": r["ay"],
-        "LAPQ11": r["lapQ11"], "LAPQ12": r["lapQ12"], "GRADU_XX": r["gradu"][:, 0],
-        "GRADU_XY": r["gradu"][:, 1], "GRADU_YX": r["gradu"][:, 2], "GRADU_YY": r["gradu"][:, 3],
+    r11, r12, r22 = r["B11"], r["B12"], r["B22"]
+    errs = {
+        "SUMW": relerr(g["SUMW"], r["sumW"]), "V": relerr(g["V"], r["V"]),
+        "B": relerr_group([g["B11"], g["B12"], g["B12"], g["B22"]], [r11, r12, r12, r22]),
+        "K": relerr(g["K"], r["k"]),
+        "DRHO_HALF": relerr(g["DRHO_HALF"], r["rho_half"] - 1.0),
+        "DRHO_HAT": relerr(g["DRHO_HAT"], r["rho_hat"] - 1.0),
+        "P": relerr(g["P"], r["p"]),
+        "divQ": relerr_group([g["DIVQX"], g["DIVQY"]], [r["divQx"], r["divQy"]]),
+        "a": relerr_group([g["AX"], g["AY"]], [r["ax"], r["ay"]]),
+        "lapQ": relerr_group([g["LAPQ11"], g["LAPQ12"]], [r["lapQ11"], r["lapQ12"]]),
+        "gradu": relerr_group([g["GRADU_XX"], g["GRADU_XY"], g["GRADU_YX"], g["GRADU_YY"]],
+                              [r["gradu"][:, 0], r["gradu"][:, 1], r["gradu"][:, 2], r["gradu"][:, 3]]),
+        "apd": relerr_group([g["APDX"], g["APDY"]], [r["apdx"], r["apdy"]]),
     }
-    errs = {k: relerr(g[k], v) for k, v in checks.items()}
     bad = {k: e for k, e in errs.items() if not e <= TOL}
-    assert not bad, bad
-    # APD: small displacements formed from nearly cancelling sums; FP32 resolves them to 1e-4
-    for k, ref in (("APDX", r["apdx"]), ("APDY", r["apdy"])):
-        assert relerr(g[k], ref) <= 1e-4, (k, relerr(g[k], ref))
+    assert not bad, errs
 
 
 def _ten_steps(B, orc, nx, p, ic, nbr_mode, nsteps=10):
@@ -139,8 +143,13 @@ def test_ten_steps_64(B, orc):
 
 @pytest.mark.parametrize("zeta", [0.02, 0.05, 0.1])
 def test_ten_steps_256(B, orc, zeta):
+    """256 x 256 at three activities.  dt = 1e-4 is 30x beyond the explicit viscous limit
+    0.125 h^2/nu at this resolution (the run diverges within a few steps on both sides), so the
+    stable dt is used."""
     ic = si.jittered_lattice(256, seed=1)
-    worst = _ten_steps(B, orc, 256, params(256, zeta=zeta), ic, "cells")
+    p = params(256, zeta=zeta)
+    p["dt"] = stable_dt(p)
+    worst = _ten_steps(B, orc, 256, p, ic, "cells")
     bad = {k: e for k, e in worst.items() if not e <= TOL}
     assert not bad, worst
 

@@ -15,7 +15,7 @@ import pytest
 
 import sph_inputs as si
 from _sph import (GpuRun, compare_state, gpu_params, oracle_params, oracle_state, params,
-                  random_velocity_ic)
+                  random_velocity_ic, stable_dt)
 
 pytestmark = pytest.mark.gpu
 
@@ -135,6 +135,7 @@ def test_checkpoint_resume_is_bit_identical(B, tmp_path):
 def test_two_contexts_agree_bitwise(B):
     ic = random_velocity_ic(96, 5)
     p = params(96, c0_min=0.05)
+    p["dt"] = stable_dt(p)
     runs = [GpuRun(B, p, ic) for _ in range(2)]
     try:
         for r in runs:
