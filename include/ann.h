@@ -55,6 +55,7 @@ extern "C" {
 #define ANN_ERR_IO (-8)              /* checkpoint file could not be written or read */
 #define ANN_ERR_STATE (-9)           /* call out of order (e.g. ann_step before ann_set_particles) */
 #define ANN_ERR_NOT_AVAILABLE (-10)  /* no CUDA device */
+#define ANN_ERR_TOO_LARGE (-11)      /* size beyond the fixed scratch of ann_velocity_moments_noalloc */
 
 /* Limits of the device kernels. */
 #define ANN_MAX_NEIGHBORS 64         /* neighbours per particle */
@@ -227,6 +228,34 @@ int ann_load_state(ann_ctx *ctx, const char *path);
 
 /* Text of the last error raised on ctx (empty string if none; never NULL). */
 const char *ann_last_error(ann_ctx *ctx);
+
+/*
+ * Velocity moments without any device allocation.  The paper has no counterpart: this is a
+ * service entry point for callers that cannot call cudaMalloc -- a host framework that owns a fixed
+ * device memory pool or a hard memory budget and forbids allocations after start-up, or a real-time
+ * loop that cannot take the implicit device synchronisation cudaMalloc may perform.
+ *
+ * Computes, for a velocity field already on the device (FP32 arrays ux, uy of length n, any
+ * particle order), in FP64 with a fixed reduction order (deterministic):
+ *   out[0], out[1] = sum_i m_i u_i (momentum), m_i = mass[i], or m0 for every particle if mass is NULL
+ *   out[2]         = 1/2 <|u|^2>, the mean over the n particles (the paper's Eq. 31)
+ *   out[3]         = max_i |u_i|
+ * the same quantities ann_get_diagnostics reports for a context's state.  `out` is a device pointer
+ * to 4 doubles; the call is asynchronous on `stream` (a cudaStream_t, NULL for the legacy default
+ * stream) and the result is there once the stream reaches it.
+ *
+ * It allocates nothing: its only scratch is a file-scope device array of ANN_NOALLOC_MAX_N / 256
+ * FP64 partials and a ticket (about 256 KB), which every GPU that loads this library holds until the
+ * process exits.  n must be in [1, ANN_NOALLOC_MAX_N]; larger n returns ANN_ERR_TOO_LARGE.  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current) and caches it; make that first call before any stream capture.  All calls share
+ * the one array: calls whose kernels overlap on the GPU (different streams, or different host
+ * threads on one device) race on it and must be serialised by the caller.  Errors: INVALID_ARG
+ * (NULL pointer, n < 1), TOO_LARGE, CUDA.
+ */
+#define ANN_NOALLOC_MAX_N 2097152
+int ann_velocity_moments_noalloc(const float *ux, const float *uy, const float *mass, double m0,
+                                 int64_t n, double *out, void *stream);
 
 #ifdef __cplusplus
 }

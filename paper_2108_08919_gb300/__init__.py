@@ -9,6 +9,7 @@ from .binding import (AnnError, FIELDS, ann_create, ann_default_params, ann_dest
                       ann_get_diagnostics, ann_get_field, ann_get_neighbors, ann_grid_info,
                       ann_kernel_count, ann_kernel_name, ann_last_error, ann_load_state,
                       ann_save_state, ann_set_particles, ann_set_record, ann_set_stream, ann_step,
-                      ann_step_profile, ann_validate_params, ann_version)
+                      ann_step_profile, ann_validate_params, ann_velocity_moments_noalloc,
+                      ann_version)
 
 __all__ = [n for n in dir() if n.startswith("ann_")] + ["AnnError", "FIELDS", "binding"]

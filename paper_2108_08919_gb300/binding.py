@@ -103,6 +103,7 @@ def lib() -> ctypes.CDLL:
         "ann_save_state": (i32, [vp, ctypes.c_char_p]),
         "ann_load_state": (i32, [vp, ctypes.c_char_p]),
         "ann_last_error": (ctypes.c_char_p, [vp]),
+        "ann_velocity_moments_noalloc": (i32, [vp, vp, vp, ctypes.c_double, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -260,3 +261,21 @@ def ann_load_state(ctx, path: str) -> None:
 
 def ann_last_error(ctx) -> str:
     return lib().ann_last_error(ctx).decode()
+
+
+NOALLOC_MAX_N = 2097152
+
+
+def ann_velocity_moments_noalloc(ux, uy, out, mass=None, m0=1.0, stream=None) -> None:
+    """Momentum, mean kinetic energy and peak speed of a device velocity field, written into the
+    CUDA tensor ``out`` (4 float64) without any device allocation; ``ux``, ``uy`` (and ``mass``)
+    are float32 CUDA tensors.  Asynchronous on ``stream`` (default: the legacy default stream)."""
+    for a in (ux, uy, out) + ((mass,) if mass is not None else ()):
+        if not (hasattr(a, "data_ptr") and getattr(a, "is_cuda", False)):
+            raise ValueError("ux, uy, out and mass must be CUDA tensors")
+    handle = getattr(stream, "cuda_stream", stream) if stream is not None else 0
+    st = lib().ann_velocity_moments_noalloc(
+        ctypes.c_void_p(ux.data_ptr()), ctypes.c_void_p(uy.data_ptr()),
+        ctypes.c_void_p(mass.data_ptr()) if mass is not None else None, float(m0), int(ux.numel()),
+        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(int(handle) if handle else 0))
+    _check(st, None, "ann_velocity_moments_noalloc")

@@ -49,6 +49,7 @@ const char *status_text(int s)
     case ANN_ERR_IO: return "checkpoint I/O error";
     case ANN_ERR_STATE: return "call out of order";
     case ANN_ERR_NOT_AVAILABLE: return "no CUDA device";
+    case ANN_ERR_TOO_LARGE: return "size beyond the fixed scratch of a no-allocation entry point";
     default: return "unknown status";
     }
 }
