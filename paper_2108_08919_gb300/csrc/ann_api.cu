@@ -88,7 +88,7 @@ double effective_dt(const ann_params &p)
 int64_t device_bytes(const ann_params &p)
 {
     int64_t n = p.n, nc = cells_per_side(p), ncell = nc * nc;
-    int64_t per = 2 * 8 + 7 * 4 + 4           // S
+    int64_t per = 2 * 8 + 7 * 4 + 4 + 16      // S
                   + 2 * 8 + 5 * 4 + 16 + 4    // M
                   + 3 * 4                     // key, rank, perm
                   + (MAXN / 2) * 4 + 4        // lists, counts
@@ -161,6 +161,12 @@ DevParams make_dev(const ann_params &p)
     int ex = 0;
     std::frexp(d.cell, &ex);               // cell = m 2^ex, m in [0.5, 1)
     d.q = std::ldexp(1.0, ex - 13);
+    d.qf = (float)d.q;
+    d.iqf = (float)(1.0 / d.q);
+    {
+        double L = p.L;
+        std::memcpy(&d.bitsL, &L, sizeof L);
+    }
     double chi = std::nearbyint(d.cell / d.q) * d.q;
     d.cell_hi = (float)chi;
     d.cell_lo = (float)(d.cell - chi);
@@ -171,7 +177,16 @@ DevParams make_dev(const ann_params &p)
     double ad = 7.0 / (478.0 * M_PI * p.h * p.h);
     d.ad = (float)ad;
     d.W0 = (float)(ad * 66.0);   // W(0) = a_d (3^5 - 6 2^5 + 15)
-    d.Fc = (float)(ad / p.h);
+    d.kw6 = (float)(-6.0 * ad);
+    d.kw15 = (float)(15.0 * ad);
+    d.kf5 = (float)(-5.0 * ad / p.h);
+    d.kf30 = (float)(30.0 * ad / p.h);
+    d.kf75 = (float)(-75.0 * ad / p.h);
+    // Candidates are first tested on the hi parts alone.  |lo| <= q/2 + 5 |cell_lo| <= 3q per
+    // coordinate, so the hi-only distance is within 6 sqrt(2) q < 9q of the true one; the coarse
+    // radius 3h + 9q (rounded up) keeps every neighbour.
+    d.R2c = (float)((3.0 * p.h + 9.0 * d.q) * (3.0 * p.h + 9.0 * d.q) * (1.0 + 1.0 / 1048576.0));
+    d.nsblk = (d.ncell + SCAN_CHUNK - 1) / SCAN_CHUNK;
     d.dt = (float)dt;
     d.half_dt = (float)(0.5 * dt);
     d.rho0 = (float)p.rho0;
@@ -209,7 +224,7 @@ cudaError_t alloc_all(ann_ctx *c)
     cudaError_t e;
 #define A_(p, cnt) if ((e = dalloc(c, b.p, cnt))) return e
     A_(sx, n); A_(sy, n); A_(sux, n); A_(suy, n); A_(sq11, n); A_(sq12, n); A_(sdr, n); A_(sax, n);
-    A_(say, n); A_(sid, n);
+    A_(say, n); A_(sid, n); A_(sxi, n);
     A_(mx, n); A_(my, n); A_(mux, n); A_(muy, n); A_(mq11, n); A_(mq12, n); A_(mdr, n); A_(xi, n); A_(mid, n);
     A_(cell_count, ncell + 1); A_(cell_start, ncell + 1); A_(key, n); A_(rank, n); A_(perm, n);
     A_(nbr, n * (MAXN / 2)); A_(nnbr, n);
@@ -218,6 +233,14 @@ cudaError_t alloc_all(ann_ctx *c)
     A_(rec_gu, 4 * n); A_(rec_lap, 2 * n); A_(rec_apd, 2 * n);
     A_(err, 1); A_(maxu, 1); A_(band, 1);
 #undef A_
+    double *origin = nullptr;
+    if ((e = dalloc(c, origin, (size_t)c->P.nc))) return e;
+    {
+        std::vector<double> h((size_t)c->P.nc);
+        for (int k = 0; k < c->P.nc; k++) h[(size_t)k] = (double)k * c->P.cell;
+        if ((e = cudaMemcpy(origin, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice))) return e;
+    }
+    b.origin = origin;
     unsigned char *tmp = nullptr;
     if ((e = dalloc(c, tmp, std::max<size_t>(7 * 8, MAXN * 4) * n))) return e;
     c->tmp = tmp;

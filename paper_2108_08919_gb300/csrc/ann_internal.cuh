@@ -16,6 +16,7 @@ constexpr int MAXN = 64;              // neighbours per particle (ANN_MAX_NEIGHB
 constexpr int MAXC = 64;              // particles per cell (ANN_MAX_PER_CELL)
 constexpr int PT = 256;               // threads per pair-pass block
 constexpr int NKERNELS = 8;
+constexpr int SCAN_CHUNK = 4096;      // cells per block of the cell-count scan
 
 // Sticky device error bits.
 enum : uint32_t {
@@ -32,8 +33,15 @@ struct DevParams {
     int apd, conservative, qnew, record;
     double L, cell, inv_cell, R2, dt_d, half_dt_d;
     double q;              // power-of-two grid of the "hi" coordinate part: cell / q in [2^12, 2^13)
+    long long bitsL;       // bit pattern of L: for x >= +0, x < L iff bits(x) < bits(L)
     float cell_hi, cell_lo;  // cell = cell_hi + cell_lo, cell_hi a multiple of q
-    float R2lo, R2hi, inv_h, ad, W0, Fc, dt, half_dt;
+    float qf, iqf;           // q and 1/q in FP32 (powers of two: exact)
+    float R2lo, R2hi;      // FP32 band around (3h)^2 inside which the support test is redone in FP64
+    float R2c;             // coarse (hi-part only) candidate radius^2, padded by the hi-only error
+    float inv_h, ad, W0, dt, half_dt;
+    float kw6, kw15;       // -6 a_d, 15 a_d           (W = a_d t3^5 + kw6 t2^5 + kw15 t1^5)
+    float kf5, kf30, kf75; // -5 a_d/h, 30 a_d/h, -75 a_d/h  (F r = kf5 t3^4 + kf30 t2^4 + kf75 t1^4)
+    int nsblk;             // blocks of SCAN_CHUNK cells (scan)
     float rho0, nu, mu, Gamma, lambda, A, C, K, zeta, gamma_eos, beta, c0_min, c_shift, mass;
 };
 
@@ -42,6 +50,8 @@ struct DevParams {
 struct Bufs {
     double *sx, *sy;
     float *sux, *suy, *sq11, *sq12, *sdr, *sax, *say;
+    float4 *sxi;        // split cell-local offset of the predicted position, S order (predictor)
+    const double *origin;   // origin[c] = c * cell, c < n_c (cell-corner coordinates)
     int *sid;
     double *mx, *my;
     float *mux, *muy, *mq11, *mq12, *mdr;

@@ -25,29 +25,46 @@ __device__ __forceinline__ double wrap_d(double a, double L)
     return a;
 }
 
+// x in [+0, L)?  Non-negative doubles order like their bit patterns, so two integer compares decide
+// it; negative values, -0, NaN and values >= L fail.
+__device__ __forceinline__ bool in_box(double x, long long bitsL)
+{
+    long long bx = __double_as_longlong(x);
+    return bx >= 0 && bx < bitsL;
+}
+
 __device__ __forceinline__ int wrapc(int c, int nc) { return c < 0 ? c + nc : (c >= nc ? c - nc : c); }
 
 __device__ __forceinline__ bool stopped(const Bufs &b) { return *(volatile uint32_t *)b.err != 0u; }
 
-// Quintic kernel of Eq. (18) in branch-free form: W(b) = a_d [t3^5 - 6 t2^5 + 15 t1^5] with
-// t_k = max(k - b, 0), and F = W'(b) / (h r), so that grad_i W_ij = F d_ij.
+// Quintic kernel of Eq. (18) in branch-free form: with t_k = max(k - b, 0),
+//   W = a_d [t3^5 - 6 t2^5 + 15 t1^5],   F = W'(b) / (h r) = a_d/h [-5 t3^4 + 30 t2^4 - 75 t1^4] / r,
+// so that grad_i W_ij = F d_ij.  The constants a_d, -6 a_d, ... are folded on the host.  For true
+// neighbours b < 3 up to FP32 rounding, and t3 needs no clamp (a rounding-negative t3 gives
+// |t3|^4 ~ 1e-28); `clamp3` keeps it for candidates that may lie beyond the support.
+template <bool clamp3>
 __device__ __forceinline__ void kernel_wf(float r2, const DevParams &P, float &W, float &F, float &rinv)
 {
     rinv = rsqrtf(r2);
     float bq = r2 * rinv * P.inv_h;
-    float t3 = fmaxf(3.f - bq, 0.f), t2 = fmaxf(2.f - bq, 0.f), t1 = fmaxf(1.f - bq, 0.f);
+    float t3 = 3.f - bq;
+    if (clamp3) t3 = fmaxf(t3, 0.f);
+    float t2 = fmaxf(2.f - bq, 0.f), t1 = fmaxf(1.f - bq, 0.f);
     float s3 = t3 * t3, s2 = t2 * t2, s1 = t1 * t1;
     float q3 = s3 * s3, q2 = s2 * s2, q1 = s1 * s1;
-    W = P.ad * (q3 * t3 - 6.f * q2 * t2 + 15.f * q1 * t1);
-    F = (-5.f * q3 + 30.f * q2 - 75.f * q1) * P.Fc * rinv;
+    W = fmaf(P.ad * q3, t3, fmaf(P.kw6 * q2, t2, P.kw15 * q1 * t1));
+    F = fmaf(P.kf5, q3, fmaf(P.kf30, q2, P.kf75 * q1)) * rinv;
 }
 
+template <bool clamp3>
 __device__ __forceinline__ float kernel_w(float r2, const DevParams &P)
 {
-    float bq = sqrtf(r2) * P.inv_h;
-    float t3 = fmaxf(3.f - bq, 0.f), t2 = fmaxf(2.f - bq, 0.f), t1 = fmaxf(1.f - bq, 0.f);
+    float bq = r2 * rsqrtf(r2) * P.inv_h;
+    float t3 = 3.f - bq;
+    if (clamp3) t3 = fmaxf(t3, 0.f);
+    float t2 = fmaxf(2.f - bq, 0.f), t1 = fmaxf(1.f - bq, 0.f);
     float s3 = t3 * t3, s2 = t2 * t2, s1 = t1 * t1;
-    return P.ad * (s3 * s3 * t3 - 6.f * s2 * s2 * t2 + 15.f * s1 * s1 * t1);
+    return fmaf(P.ad * s3 * s3, t3, fmaf(P.kw6 * s2 * s2, t2, P.kw15 * s1 * s1 * t1));
 }
 
 // FP64 support test of the definition for particles gi (inner cell) and gj (halo image with cell
@@ -167,33 +184,50 @@ __global__ void __launch_bounds__(256) k_predict(DevParams P, Bufs b)
     if (stopped(b)) return;
     __shared__ float wmax[8];
     int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int lane = threadIdx.x & 31;
     float sp = 0.f;
+    uint32_t key = 0xffffffffu;
     if (i < P.n) {
         float ux = b.sux[i] + P.half_dt * b.sax[i];
         float uy = b.suy[i] + P.half_dt * b.say[i];
-        double x = wrap_d(b.sx[i] + P.half_dt_d * (double)ux, P.L);
-        double y = wrap_d(b.sy[i] + P.half_dt_d * (double)uy, P.L);
-        if (!(isfinite(x) && isfinite(y) && isfinite(ux) && isfinite(uy) && x >= 0.0 && x < P.L &&
-              y >= 0.0 && y < P.L)) {
-            atomicOr(b.err, EB_NONFINITE);
-            x = 0.0;
-            y = 0.0;
-            ux = 0.f;
-            uy = 0.f;
+        // FP64 work is kept to what the positions need: GB300 issues FP64 at 1/64 of FP32.
+        double x = b.sx[i] + (double)(P.half_dt * ux);
+        double y = b.sy[i] + (double)(P.half_dt * uy);
+        if (!(in_box(x, P.bitsL) && in_box(y, P.bitsL))) {   // rare: crossed a face, or not finite
+            x = wrap_d(x, P.L) + 0.0;
+            y = wrap_d(y, P.L) + 0.0;
+            if (!(in_box(x, P.bitsL) && in_box(y, P.bitsL) && isfinite(ux) && isfinite(uy))) {
+                atomicOr(b.err, EB_NONFINITE);
+                x = 0.0;
+                y = 0.0;
+                ux = 0.f;
+                uy = 0.f;
+            }
         }
         b.sux[i] = ux;
         b.suy[i] = uy;
         b.sx[i] = x;
         b.sy[i] = y;
-        int cx = min(max((int)(x * P.inv_cell), 0), P.nc - 1);
-        int cy = min(max((int)(y * P.inv_cell), 0), P.nc - 1);
-        uint32_t key = (uint32_t)(cy * P.nc + cx);
+        int cx = min((int)(x * P.inv_cell), P.nc - 1);
+        int cy = min((int)(y * P.inv_cell), P.nc - 1);
+        key = (uint32_t)(cy * P.nc + cx);
         b.key[i] = key;
-        b.rank[i] = atomicAdd(&b.cell_count[key], 1u);
+        // offset from the cell corner, split into hi (FP32 on the q grid) + lo (FP32 remainder)
+        double ox = x - __ldg(&b.origin[cx]), oy = y - __ldg(&b.origin[cy]);
+        float hx = rintf((float)ox * P.iqf) * P.qf, hy = rintf((float)oy * P.iqf) * P.qf;
+        b.sxi[i] = make_float4(hx, hy, (float)(ox - (double)hx), (float)(oy - (double)hy));
         sp = sqrtf(ux * ux + uy * uy);
     }
+    // Particles arrive in the previous step's cell order, so a warp holds a few runs of equal keys:
+    // one atomic per run instead of one per particle.
+    unsigned grp = __match_any_sync(FULL, key);
+    int leader = __ffs(grp) - 1;
+    uint32_t base = 0;
+    if (lane == leader && key != 0xffffffffu) base = atomicAdd(&b.cell_count[key], (uint32_t)__popc(grp));
+    base = __shfl_sync(FULL, base, leader);
+    if (i < P.n) b.rank[i] = base + (uint32_t)__popc(grp & ((1u << lane) - 1u));
     for (int o = 16; o > 0; o >>= 1) sp = fmaxf(sp, __shfl_xor_sync(FULL, sp, o));
-    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = sp;
+    if (lane == 0) wmax[threadIdx.x >> 5] = sp;
     __syncthreads();
     if (threadIdx.x < 32) {
         sp = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0.f;
@@ -203,65 +237,66 @@ __global__ void __launch_bounds__(256) k_predict(DevParams P, Bufs b)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Kernel 1: exclusive scan of cell counts -> cell starts; clears the counts for the next step
+// Kernel 1: exclusive scan of cell counts -> cell starts, one block per SCAN_CHUNK cells.  Each
+// block first sums the counts of all cells before its chunk (coalesced, L2-resident reads), so no
+// block waits on another; then it scans its own chunk.  The counts are cleared by the scatter
+// kernel, after every block has read them.
 // ---------------------------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(1024) k_scan(DevParams P, Bufs b)
 {
     if (stopped(b)) return;
     __shared__ uint32_t wsum[32];
-    __shared__ uint32_t s_carry, s_max;
+    __shared__ uint32_t s_base, s_max;
     int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    if (t == 0) {
-        s_carry = 0;
-        s_max = 0;
-    }
-    __syncthreads();
-    uint32_t mx = 0;
-    for (int base = 0; base < P.ncell; base += 4096) {
-        int c0 = base + 4 * t;
-        uint32_t v[4], s = 0;
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            v[k] = (c0 + k < P.ncell) ? b.cell_count[c0 + k] : 0u;
-            s += v[k];
-            mx = max(mx, v[k]);
+    {
+        uint32_t acc = 0;
+        int end = blockIdx.x * SCAN_CHUNK;
+        for (int c = t; c < end; c += 1024) acc += b.cell_count[c];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if (t == 0) {
+            s_base = 0;
+            s_max = 0;
         }
-        uint32_t inc = s;
+        __syncthreads();
+        if (lane == 0) atomicAdd(&s_base, acc);
+    }
+    int c0 = blockIdx.x * SCAN_CHUNK + 4 * t;
+    uint32_t v[4], sum = 0, mx = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        v[k] = (c0 + k < P.ncell) ? b.cell_count[c0 + k] : 0u;
+        sum += v[k];
+        mx = max(mx, v[k]);
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t u = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t x = wsum[lane], xi = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t u = __shfl_up_sync(FULL, inc, o);
-            if (lane >= o) inc += u;
+            uint32_t u = __shfl_up_sync(FULL, xi, o);
+            if (lane >= o) xi += u;
         }
-        if (lane == 31) wsum[w] = inc;
-        __syncthreads();
-        if (w == 0) {
-            uint32_t x = wsum[lane], xi = x;
+        wsum[lane] = xi - x;
+    }
+    __syncthreads();
+    uint32_t run = s_base + wsum[w] + inc - sum;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t u = __shfl_up_sync(FULL, xi, o);
-                if (lane >= o) xi += u;
-            }
-            wsum[lane] = xi - x;
-        }
-        __syncthreads();
-        uint32_t run = s_carry + wsum[w] + inc - s;
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            if (c0 + k < P.ncell) {
-                b.cell_start[c0 + k] = run;
-                b.cell_count[c0 + k] = 0u;
-            }
-            run += v[k];
-        }
-        __syncthreads();
-        if (t == 1023) s_carry = run;
-        __syncthreads();
+    for (int k = 0; k < 4; k++) {
+        if (c0 + k < P.ncell) b.cell_start[c0 + k] = run;
+        run += v[k];
     }
     atomicMax(&s_max, mx);
     __syncthreads();
     if (t == 0) {
-        b.cell_start[P.ncell] = (uint32_t)P.n;
+        if (blockIdx.x == gridDim.x - 1) b.cell_start[P.ncell] = (uint32_t)P.n;
         if (s_max > (uint32_t)MAXC) atomicOr(b.err, EB_CELL);
     }
 }
@@ -275,6 +310,8 @@ __global__ void __launch_bounds__(256) k_scatter(DevParams P, Bufs b)
     if (stopped(b)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < P.n) b.perm[b.cell_start[b.key[i]] + b.rank[i]] = (uint32_t)i;
+    // every scan block has read the cell counts: clear them for the next step
+    for (int c = i; c < P.ncell; c += gridDim.x * blockDim.x) b.cell_count[c] = 0u;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -293,27 +330,34 @@ __global__ void __launch_bounds__(256) k_cell_order(DevParams P, Bufs b)
     int cnt = (int)(b.cell_start[c + 1] - start);   // <= MAXC: k_scan raised EB_CELL otherwise
     uint32_t v0 = lane < cnt ? b.perm[start + lane] : 0xffffffffu;
     uint32_t v1 = lane + 32 < cnt ? b.perm[start + 32 + lane] : 0xffffffffu;
-    int r0 = 0, r1 = 0;
-#pragma unroll 8
-    for (int k = 0; k < 32; k++) {
-        uint32_t a = __shfl_sync(FULL, v0, k), d = __shfl_sync(FULL, v1, k);
-        r0 += (a < v0) + (d < v0);
-        r1 += (a < v1) + (d < v1);
+    // rank of each entry among the cell's entries (all distinct); a cell already in ascending
+    // order (entries scattered by one warp, or by warps that happened to run in order) skips it
+    int r0 = lane, r1 = lane + 32;
+    uint32_t nxt = __shfl_down_sync(FULL, v0, 1);
+    bool ordered = cnt <= 32 && (lane + 1 >= cnt || v0 < nxt);
+    if (!__all_sync(FULL, ordered)) {
+        r0 = 0;
+        r1 = 0;
+        int lim = min(cnt, 32);
+        for (int k = 0; k < lim; k++) {
+            uint32_t a = __shfl_sync(FULL, v0, k);
+            r0 += (a < v0);
+            r1 += (a < v1);
+        }
+        for (int k = 0; k < cnt - 32; k++) {
+            uint32_t d = __shfl_sync(FULL, v1, k);
+            r0 += (d < v0);
+            r1 += (d < v1);
+        }
     }
     if (lane < cnt) srt[w][r0] = v0;
     if (lane + 32 < cnt) srt[w][r1] = v1;
     __syncwarp();
-    int cx = c % P.nc, cy = c / P.nc;
-    double ox = (double)cx * P.cell, oy = (double)cy * P.cell;
-    double iq = 1.0 / P.q;   // power of two: exact
     for (int s = lane; s < cnt; s += 32) {
         uint32_t old = srt[w][s], g = start + (uint32_t)s;
-        double x = b.sx[old], y = b.sy[old];
-        b.mx[g] = x;
-        b.my[g] = y;
-        double ux_ = x - ox, uy_ = y - oy;
-        double hx = rint(ux_ * iq) * P.q, hy = rint(uy_ * iq) * P.q;
-        b.xi[g] = make_float4((float)hx, (float)hy, (float)(ux_ - hx), (float)(uy_ - hy));
+        b.mx[g] = b.sx[old];
+        b.my[g] = b.sy[old];
+        b.xi[g] = b.sxi[old];
         b.mux[g] = b.sux[old];
         b.muy[g] = b.suy[old];
         b.mq11[g] = b.sq11[old];
@@ -325,6 +369,11 @@ __global__ void __launch_bounds__(256) k_cell_order(DevParams P, Bufs b)
 
 // ---------------------------------------------------------------------------------------------
 // Kernel 4: pass A -- neighbour lists, sum_j W_ij (self included) and V = 1/sum  (Eqs. 18, 19)
+//
+// Two levels.  The coarse scan runs over the 3 x 3 cell stencil (three contiguous slot ranges, one
+// per stencil row) on the hi parts alone against a padded radius, appending candidates without a
+// branch.  The fine pass forms the correctly rounded pair vector of each candidate, applies the
+// exact support test (FP64 inside the rounding band), accumulates W and compacts the list in place.
 // ---------------------------------------------------------------------------------------------
 
 constexpr int SMEM_A = HCAP * (16 + 4 + 1) + MAXN * PT * 2;
@@ -335,6 +384,7 @@ __global__ void __launch_bounds__(PT) k_pass_a(DevParams P, Bufs b)
     __shared__ TileShared ts;
     extern __shared__ __align__(16) unsigned char dsm[];
     float4 *pos = reinterpret_cast<float4 *>(dsm);
+    const float2 *phi = reinterpret_cast<const float2 *>(dsm);   // hi parts: phi[2 j] = pos[j].xy
     int *sg = reinterpret_cast<int *>(pos + HCAP);
     uint16_t *lst = reinterpret_cast<uint16_t *>(sg + HCAP);
     unsigned char *shc = reinterpret_cast<unsigned char *>(lst + MAXN * PT);
@@ -350,6 +400,7 @@ __global__ void __launch_bounds__(PT) k_pass_a(DevParams P, Bufs b)
         shc[t] = (unsigned char)s.h;
     }
     __syncthreads();
+    uint16_t *my = lst + threadIdx.x;   // this thread's list column, stride PT
     for (int q = threadIdx.x; q < T.Ni; q += PT) {
         int si = inner_slot(ts, T, q);
         int h = shc[si], hx = h % T.HX, hy = h / T.HX;
@@ -359,47 +410,67 @@ __global__ void __launch_bounds__(PT) k_pass_a(DevParams P, Bufs b)
             int row = (hy + oy) * T.HX + hx;
             int j0 = ts.off[row - 1], j1 = ts.off[row + 2];
             for (int j = j0; j < j1; j++) {
-                float2 d = pair_d(pi, pos[j]);
-                float r2 = d.x * d.x + d.y * d.y;
-                bool in = r2 < P.R2lo;
-                if (!in && r2 < P.R2hi) {
-                    int hj = shc[j];
-                    int cxu = T.cx0 - 1 + hj % T.HX, cyu = T.cy0 - 1 + hj / T.HX;
-                    int sx = cxu < 0 ? -1 : (cxu >= P.nc ? 1 : 0);
-                    int sy = cyu < 0 ? -1 : (cyu >= P.nc ? 1 : 0);
-                    in = support64(P, b, sg[si], sg[j], sx, sy);
-                    atomicAdd(b.band, 1ull);
-                }
-                if (in && j != si) {
-                    if (cnt < MAXN) lst[cnt * PT + threadIdx.x] = (uint16_t)j;
-                    cnt++;
-                }
+                float2 pj = phi[2 * j];
+                float dx = pi.x - pj.x, dy = pi.y - pj.y;
+                bool in = (dx * dx + dy * dy < P.R2c) & (j != si);
+                my[min(cnt, MAXN - 1) * PT] = (uint16_t)j;
+                cnt += in;
             }
         }
-        if (cnt > MAXN) atomicOr(b.err, EB_NBR);
-        int c = min(cnt, MAXN);
+        if (cnt > MAXN) {
+            atomicOr(b.err, EB_NBR);
+            cnt = MAXN;
+        }
         float sw = P.W0;
-        for (int k = 0; k < c; k++) {
-            float2 d = pair_d(pi, pos[lst[k * PT + threadIdx.x]]);
-            sw += kernel_w(d.x * d.x + d.y * d.y, P);
+        int c = 0;
+        for (int k = 0; k < cnt; k++) {
+            int j = my[k * PT];
+            float2 d = pair_d(pi, pos[j]);
+            float r2 = d.x * d.x + d.y * d.y;
+            bool in = r2 < P.R2lo;
+            if (!in && r2 < P.R2hi) {
+                int hj = shc[j];
+                int cxu = T.cx0 - 1 + hj % T.HX, cyu = T.cy0 - 1 + hj / T.HX;
+                int sx = cxu < 0 ? -1 : (cxu >= P.nc ? 1 : 0);
+                int sy = cyu < 0 ? -1 : (cyu >= P.nc ? 1 : 0);
+                in = support64(P, b, sg[si], sg[j], sx, sy);
+                atomicAdd(b.band, 1ull);
+            }
+            float Wv = kernel_w<true>(r2, P);
+            sw += in ? Wv : 0.f;
+            my[c * PT] = (uint16_t)j;
+            c += in;
         }
         int gi = sg[si];
         b.sumW[gi] = sw;
         b.V[gi] = 1.0f / sw;
         b.nnbr[gi] = c;
-        for (int k2 = 0; 2 * k2 < c; k2++) {
-            uint32_t lo = lst[(2 * k2) * PT + threadIdx.x];
-            uint32_t hi = (2 * k2 + 1 < c) ? lst[(2 * k2 + 1) * PT + threadIdx.x] : 0xffffu;
-            b.nbr[(size_t)k2 * P.n + gi] = lo | (hi << 16);
+        uint32_t *out = b.nbr + gi;
+        for (int k = 0; k < c; k += 2) {
+            uint32_t lo = my[k * PT];
+            uint32_t hi = (k + 1 < c) ? my[(k + 1) * PT] : 0xffffu;
+            *out = lo | (hi << 16);
+            out += P.n;
         }
     }
 }
 
-// Neighbour slot k of particle gi (w caches the packed pair).
-__device__ __forceinline__ int nbr_slot(const DevParams &P, const Bufs &b, int gi, int k, uint32_t &w)
+// Visit the neighbour slots of particle gi (c of them, two per list word), prefetching the next
+// word while the current pair is processed.  Slots are masked into the staging buffer.
+template <typename Fn>
+__device__ __forceinline__ void for_each_neighbor(const DevParams &P, const Bufs &b, int gi, int c, Fn &&fn)
 {
-    if ((k & 1) == 0) w = b.nbr[(size_t)(k >> 1) * P.n + gi];
-    return (k & 1) ? (int)(w >> 16) : (int)(w & 0xffffu);
+    const uint32_t *p = b.nbr + gi;
+    uint32_t w = c > 0 ? __ldg(p) : 0u;
+    int k = 0;
+    for (; k + 1 < c; k += 2) {
+        p += P.n;
+        uint32_t wn = (k + 2 < c) ? __ldg(p) : 0u;
+        fn((int)(w & (HCAP - 1)));
+        fn((int)((w >> 16) & (HCAP - 1)));
+        w = wn;
+    }
+    if (k < c) fn((int)(w & (HCAP - 1)));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -443,15 +514,13 @@ __global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
         float r1xx = 0.f, r1xy = 0.f, r1yy = 0.f, r2xx = 0.f, r2xy = 0.f, r2yy = 0.f;
         float g1x = 0.f, g1y = 0.f, g2x = 0.f, g2y = 0.f;
         int c = b.nnbr[gi];
-        uint32_t w = 0;
-        for (int k = 0; k < c; k++) {
-            int j = nbr_slot(P, b, gi, k, w);
-            if (j >= T.H) continue;
+        float di = b.mdr[gi];   // loaded ahead of the neighbour loop
+        for_each_neighbor(P, b, gi, c, [&](int j) {
             float4 bj = sb[j];
             float2 d = pair_d(pi, sp[j]);
             float r2 = d.x * d.x + d.y * d.y;
             float Wv, F, rinv;
-            kernel_wf(r2, P, Wv, F, rinv);
+            kernel_wf<false>(r2, P, Wv, F, rinv);
             float g = bj.x * F;
             float gx = g * d.x, gy = g * d.y;
             float mxx = gx * d.x, mxy = gx * d.y, myy = gy * d.y;
@@ -478,7 +547,7 @@ __global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
                 g2x += dq2 * gx;
                 g2y += dq2 * gy;
             }
-        }
+        });
         float det = a11 * a22 - a12 * a12;
         if (!(det > 0.f)) atomicOr(b.err, EB_SINGULAR);
         float idet = 1.f / det;
@@ -487,7 +556,6 @@ __global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
         float D00 = l00 * B11 + l01 * B12, D01 = l00 * B12 + l01 * B22;
         float D10 = l10 * B11 + l11 * B12, D11 = l10 * B12 + l11 * B22;
         float divu = D00 + D11;
-        float di = b.mdr[gi];
         float kr = -(1.f + di) * divu;
         float lap1 = 2.f * (B11 * r1xx + 2.f * B12 * r1xy + B22 * r1yy);
         float lap2 = 2.f * (B11 * r2xx + 2.f * B12 * r2xy + B22 * r2yy);
@@ -564,15 +632,19 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
         float4 pi = sp[si], bi = sb[si];
         float shep = 0.f, g1x = 0.f, g1y = 0.f, g2x = 0.f, g2y = 0.f;
         int c = b.nnbr[gi];
-        uint32_t w = 0;
-        for (int k = 0; k < c; k++) {
-            int j = nbr_slot(P, b, gi, k, w);
-            if (j >= T.H) continue;
+        float swi = b.sumW[gi];   // loaded ahead of the neighbour loop
+        float B11 = 0.f, B12 = 0.f, B22 = 0.f;
+        if (QNEW) {
+            B11 = b.B11[gi];
+            B12 = b.B12[gi];
+            B22 = b.B22[gi];
+        }
+        for_each_neighbor(P, b, gi, c, [&](int j) {
             float4 bj = sb[j];
             float2 d = pair_d(pi, sp[j]);
             float r2 = d.x * d.x + d.y * d.y;
             float Wv, F, rinv;
-            kernel_wf(r2, P, Wv, F, rinv);
+            kernel_wf<false>(r2, P, Wv, F, rinv);
             shep += (bi.y - bj.y) * Wv;
             if (QNEW) {
                 float g = bj.x * F;
@@ -583,12 +655,11 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
                 g2x += dq2 * gx;
                 g2y += dq2 * gy;
             }
-        }
-        float dhat = bi.y - P.beta * shep / b.sumW[gi];
+        });
+        float dhat = bi.y - P.beta * shep / swi;
         b.dhat[gi] = dhat;
         b.p[gi] = pref * expm1f(P.gamma_eos * log1pf(dhat));
         if (QNEW) {
-            float B11 = b.B11[gi], B12 = b.B12[gi], B22 = b.B22[gi];
             float q1x = g1x * B11 + g1y * B12, q1y = g1x * B12 + g1y * B22;
             float q2x = g2x * B11 + g2y * B12, q2y = g2x * B12 + g2y * B22;
             b.divx[gi] = q1x + q2y;
@@ -644,15 +715,23 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
         float fx = 0.f, fy = 0.f, vx = 0.f, vy = 0.f;
         float sux = 0.f, suy = 0.f, sr = 0.f, sdx = 0.f, sdy = 0.f;
         int c = b.nnbr[gi];
-        uint32_t w = 0;
-        for (int k = 0; k < c; k++) {
-            int j = nbr_slot(P, b, gi, k, w);
-            if (j >= T.H) continue;
+        // per-particle inputs of the epilogue, loaded ahead of the neighbour loop
+        float dhat = b.dhat[gi], kri = b.kr[gi], swi = b.sumW[gi];
+        float B11 = 0.f, B12 = 0.f, B22 = 0.f, dvx = 0.f, dvy = 0.f;
+        if (!CONS) {
+            B11 = b.B11[gi];
+            B12 = b.B12[gi];
+            B22 = b.B22[gi];
+            dvx = b.divx[gi];
+            dvy = b.divy[gi];
+        }
+        double mxi = b.mx[gi], myi = b.my[gi];
+        for_each_neighbor(P, b, gi, c, [&](int j) {
             float4 bj = sb[j];
             float2 d = pair_d(pi, sp[j]);
             float r2 = d.x * d.x + d.y * d.y;
             float Wv, F, rinv;
-            kernel_wf(r2, P, Wv, F, rinv);
+            kernel_wf<false>(r2, P, Wv, F, rinv);
             float ux = bi.z - bj.z, uy = bi.w - bj.w;
             float ud = ux * d.x + uy * d.y;
             float rinv2 = rinv * rinv;
@@ -678,36 +757,38 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
             float rinv3 = rinv2 * rinv;
             sdx += d.x * rinv3;
             sdy += d.y * rinv3;
-        }
+        });
         float ax, ay;
-        float dhat = b.dhat[gi];
         float rho = P.rho0 * (1.f + dhat);
         if (CONS) {
             ax = P.mass * fx;
             ay = P.mass * fy;
         } else {
-            float B11 = b.B11[gi], B12 = b.B12[gi], B22 = b.B22[gi];
             float pbx = B11 * fx + B12 * fy, pby = B12 * fx + B22 * fy;
             float vbx = B11 * vx + B12 * vy, vby = B12 * vx + B22 * vy;
             float irho = 1.f / rho;
             float kv = 8.f * P.nu * P.rho0 * irho;
-            ax = -rho * pbx + kv * vbx - P.zeta * irho * b.divx[gi];
-            ay = -rho * pby + kv * vby - P.zeta * irho * b.divy[gi];
+            ax = -rho * pbx + kv * vbx - P.zeta * irho * dvx;
+            ay = -rho * pby + kv * vby - P.zeta * irho * dvy;
         }
         float unx = bi.z + P.half_dt * ax, uny = bi.w + P.half_dt * ay;
         float apx = 0.f, apy = 0.f;
         if (P.apd && c > 0) {
-            float uv = sqrtf(sux * sux + suy * suy) / b.sumW[gi];
+            float uv = sqrtf(sux * sux + suy * suy) / swi;
             float r0 = sr / (float)c;
             float sc_ = P.dt * uv * r0 * r0;
             apx = sc_ * sdx;
             apy = sc_ * sdy;
         }
-        double xn = wrap_d(b.mx[gi] + P.half_dt_d * (double)unx + (double)apx, P.L);
-        double yn = wrap_d(b.my[gi] + P.half_dt_d * (double)uny + (double)apy, P.L);
-        float dn = dhat + P.half_dt * b.kr[gi];
-        if (!(isfinite(unx) && isfinite(uny) && isfinite(dn) && isfinite(xn) && isfinite(yn) &&
-              isfinite(b.sq11[gi]) && isfinite(b.sq12[gi])))
+        double xn = mxi + (double)(P.half_dt * unx + apx);
+        double yn = myi + (double)(P.half_dt * uny + apy);
+        if (!(in_box(xn, P.bitsL) && in_box(yn, P.bitsL))) {   // rare: re-insert (Eq. 30)
+            xn = wrap_d(xn, P.L) + 0.0;
+            yn = wrap_d(yn, P.L) + 0.0;
+        }
+        float dn = dhat + P.half_dt * kri;
+        if (!(isfinite(unx) && isfinite(uny) && isfinite(dn) && in_box(xn, P.bitsL) &&
+              in_box(yn, P.bitsL) && isfinite(b.sq11[gi]) && isfinite(b.sq12[gi])))
             atomicOr(b.err, EB_NONFINITE);
         b.sx[gi] = xn;
         b.sy[gi] = yn;
@@ -744,8 +825,8 @@ __global__ void k_load(DevParams P, Bufs b, const double *x, const double *y, co
     }
     if (xx < -P.L || xx >= 2.0 * P.L) xx = xx - floor(xx / P.L) * P.L;
     if (yy < -P.L || yy >= 2.0 * P.L) yy = yy - floor(yy / P.L) * P.L;
-    b.sx[i] = wrap_d(xx, P.L);
-    b.sy[i] = wrap_d(yy, P.L);
+    b.sx[i] = wrap_d(xx, P.L) + 0.0;
+    b.sy[i] = wrap_d(yy, P.L) + 0.0;
     b.sux[i] = (float)ux[i];
     b.suy[i] = (float)uy[i];
     b.sq11[i] = (float)q11[i];
@@ -779,11 +860,11 @@ __global__ void __launch_bounds__(PT) k_export_nbrs(DevParams P, Bufs b, int *co
         int si = inner_slot(ts, T, q);
         int gi = sg[si];
         int c = b.nnbr[gi];
-        uint32_t w = 0;
-        for (int k = 0; k < c; k++) {
-            int j = nbr_slot(P, b, gi, k, w);
+        int k = 0;
+        for_each_neighbor(P, b, gi, c, [&](int j) {
             cols[(size_t)k * P.n + gi] = j < T.H ? b.mid[sg[j]] : -1;
-        }
+            k++;
+        });
     }
 }
 
@@ -870,7 +951,7 @@ static cudaError_t launch_front(const DevParams &P, const Bufs &b, cudaStream_t 
     if (ev) cudaEventRecord(ev[0], s);
     k_predict<<<nb, 256, 0, s>>>(P, b);
     if (ev) cudaEventRecord(ev[1], s);
-    k_scan<<<1, 1024, 0, s>>>(P, b);
+    k_scan<<<P.nsblk, 1024, 0, s>>>(P, b);
     if (ev) cudaEventRecord(ev[2], s);
     k_scatter<<<nb, 256, 0, s>>>(P, b);
     if (ev) cudaEventRecord(ev[3], s);
