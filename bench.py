@@ -44,11 +44,16 @@ KERNEL_SRC = os.path.join(ROOT, "paper_2108_08919_gb300", "csrc", "ann_kernels.c
 #   pass C: + Shepard sum (3), div Q sums (13)                                            = 48
 #   pass D: + pressure (7), viscous (12), APD sums (11)                                    = 62
 FLOPS_PER_PAIR = {"pass_a": 24 + 15.5, "pass_b": 70.0, "pass_c": 48.0, "pass_d": 62.0}
-# Algorithmic DRAM bytes per particle of each pass: per-particle arrays read/written once, halo
-# arrays re-read 2.25x (6x6 halo cells per 4x4 tile), neighbour lists (2 B per neighbour).
-BYTES_PER_PARTICLE = {"predict": 56, "cell_scan": 1, "cell_scatter": 12, "cell_order": 76,
-                      "pass_a": 8 * 2.25 + 4 + 4 + 4 + 88, "pass_b": 20 * 2.25 + 16 + 88 + 36,
-                      "pass_c": 16 * 2.25 + 16 + 88 + 16, "pass_d": 20 * 2.25 + 36 + 88 + 48}
+# Compulsory DRAM bytes per particle of each kernel: every array it must read or write, once
+# (positions as the split float4, neighbour lists at 2 B per neighbour, 44 neighbours):
+#   predict     r, u, a in; r, u, key, rank, split position out                          80
+#   cell_order  permutation, state and split position in; the sorted copy out             116
+#   pass_a      split position in; sum W, V, count, lists out                             116
+#   pass_b      position, V, u, Q, delta, count, lists in; Q^{n+1}, B, k, delta_half out   160
+#   pass_c      position, V, delta_half, Q^{n+1}, count, sum W, B, lists in; 4 fields out  156
+#   pass_d      everything the momentum, corrector and APD read; the new state out        224
+BYTES_PER_PARTICLE = {"predict": 80, "cell_scan": 0.5, "cell_scatter": 16, "cell_order": 116,
+                      "pass_a": 116, "pass_b": 160, "pass_c": 156, "pass_d": 224}
 
 
 def _rank_info():
