@@ -63,6 +63,27 @@ def _rank_info():
     return ws, rank, local
 
 
+def ensemble_seed(rank: int) -> int:
+    """Each rank advances its own ensemble member: an independent problem of the same size."""
+    return rank
+
+
+def slowest(local_value: float, dist=None, device=None) -> float:
+    """The maximum of a per-rank time over all ranks (the job is as slow as its slowest rank)."""
+    if dist is None:
+        return float(local_value)
+    import torch
+
+    t = torch.tensor([float(local_value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world_size: int, particles: int, steps: int, seconds: float) -> float:
+    """Whole-job particle-steps/s: every rank advances `particles` particles `steps` times."""
+    return world_size * particles * steps / seconds
+
+
 def _peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -247,7 +268,7 @@ def run_ours(args):
     n = NX * NX
     p = make_params(B, NX)
     grid = B.ann_grid_info(p)
-    ic = si.jittered_lattice(NX, seed=rank)
+    ic = si.jittered_lattice(NX, seed=ensemble_seed(rank))
     ctx = B.ann_create(p)
     stream = torch.cuda.Stream()
     B.ann_set_stream(ctx, stream)
@@ -265,14 +286,10 @@ def run_ours(args):
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = slowest(e0.elapsed_time(e1), dist, "cuda")
     diag = B.ann_get_diagnostics(ctx)
     pairs_per_step = diag["nbr_mean"] * n
-    value = ws * n * args.steps / (ms_max * 1e-3)
+    value = job_throughput(ws, n, args.steps, ms_max * 1e-3)
 
     # per-kernel device times (CUDA events around each kernel launch, same stream, same state)
     kprof = B.ann_step_profile(ctx, args.profile_steps)
@@ -304,10 +321,7 @@ def run_ours(args):
         e2e_iter()
     torch.cuda.synchronize()
     e2e_el = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_el], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = ws * n * e2e_steps / float(e2e_t.item())
+    e2e_value = job_throughput(ws, n, e2e_steps, slowest(e2e_el, dist, "cuda"))
     B.ann_destroy(ctx)
 
     if rank != 0:
