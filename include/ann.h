@@ -96,7 +96,7 @@ typedef struct ann_params {
 
 /* Cell grid and step size a parameter set implies (host computation, no GPU needed). */
 typedef struct ann_grid {
-    int32_t cells_per_side;      /* n_c = floor(L / (3h (1 + 1e-9))) */
+    int32_t cells_per_side;      /* n_c = floor(L / (3h (1 + 0.02) (1 + 1e-9))): cells hold the candidate radius */
     int32_t tiles_per_side;      /* ceil(n_c / 4): one CUDA block per 4 x 4 cells */
     double cell_size;            /* L / n_c >= 3h */
     double dt_effective;         /* dt after dt_mode */
@@ -118,7 +118,7 @@ typedef struct ann_diag {
     int32_t nbr_min, nbr_max;
     double min_det_alpha;        /* smallest det(alpha) of the last evaluation */
     uint32_t error_bits;         /* sticky device error bits (see ann_status_string) */
-    int32_t reserved;
+    int32_t resorts;             /* steps that re-sorted the particles and rebuilt the candidate lists */
     uint64_t band_checks;        /* pair tests that fell in the FP32 uncertainty band and were decided in FP64 */
 } ann_diag;
 

@@ -53,11 +53,11 @@ class ann_diag(ctypes.Structure):
                 ("c0", ctypes.c_double), ("mass", ctypes.c_double), ("mean_q", ctypes.c_double),
                 ("nbr_mean", ctypes.c_double), ("nbr_min", ctypes.c_int32),
                 ("nbr_max", ctypes.c_int32), ("min_det_alpha", ctypes.c_double),
-                ("error_bits", ctypes.c_uint32), ("reserved", ctypes.c_int32),
+                ("error_bits", ctypes.c_uint32), ("resorts", ctypes.c_int32),
                 ("band_checks", ctypes.c_uint64)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "momentum")}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "momentum"}
         d["momentum"] = (self.momentum[0], self.momentum[1])
         return d
 

@@ -18,6 +18,7 @@ struct ann_ctx {
     Bufs b{};
     int device = 0;
     cudaStream_t own = nullptr;
+    cudaStream_t aux = nullptr;     // captures the bodies of the step graph's conditional node
     cudaStream_t stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool have_particles = false;
@@ -68,9 +69,10 @@ int cuda_fail(ann_ctx *c, cudaError_t e, const char *where)
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
+// Cells are at least as wide as the candidate radius 3h (1 + SKIN).
 int cells_per_side(const ann_params &p)
 {
-    return (int)std::floor(p.L / (3.0 * p.h * (1.0 + kCellSlack)));
+    return (int)std::floor(p.L / (3.0 * p.h * (1.0 + SKIN) * (1.0 + kCellSlack)));
 }
 
 double effective_dt(const ann_params &p)
@@ -91,7 +93,8 @@ int64_t device_bytes(const ann_params &p)
     int64_t per = 2 * 8 + 7 * 4 + 4 + 16      // S
                   + 2 * 8 + 5 * 4 + 16 + 4    // M
                   + 3 * 4                     // key, rank, perm
-                  + (MAXN / 2) * 4 + 4        // lists, counts
+                  + 4 + 8                     // neighbour counts, neighbour masks
+                  + (MAXV / 2) * 4 + 4 + 16 + 4   // candidate lists, counts, split at re-sort, cell
                   + 11 * 4                    // intermediates
                   + 8 * 4;                    // recording
     int64_t tmp = std::max<int64_t>(7 * 8, MAXN * 4) * n;
@@ -185,7 +188,13 @@ DevParams make_dev(const ann_params &p)
     // Candidates are first tested on the hi parts alone.  |lo| <= q/2 + 5 |cell_lo| <= 3q per
     // coordinate, so the hi-only distance is within 6 sqrt(2) q < 9q of the true one; the coarse
     // radius 3h + 9q (rounded up) keeps every neighbour.
-    d.R2c = (float)((3.0 * p.h + 9.0 * d.q) * (3.0 * p.h + 9.0 * d.q) * (1.0 + 1.0 / 1048576.0));
+    double Rv = 3.0 * p.h * (1.0 + SKIN);
+    d.R2c = (float)((Rv + 9.0 * d.q) * (Rv + 9.0 * d.q) * (1.0 + 1.0 / 1048576.0));
+    d.R2v = (float)(Rv * Rv * (1.0 + 1.0 / 262144.0));
+    // A pair within 3h at some step was within 3h + 2 * (SKIN 3h / 2) = Rv at the last re-sort as
+    // long as no particle has moved SKIN 3h / 2 since; past that the step re-sorts.
+    double smax = 0.5 * SKIN * 3.0 * p.h;
+    d.skin_max2 = (float)(smax * smax);
     d.nsblk = (d.ncell + SCAN_CHUNK - 1) / SCAN_CHUNK;
     d.dt = (float)dt;
     d.half_dt = (float)(0.5 * dt);
@@ -227,7 +236,8 @@ cudaError_t alloc_all(ann_ctx *c)
     A_(say, n); A_(sid, n); A_(sxi, n);
     A_(mx, n); A_(my, n); A_(mux, n); A_(muy, n); A_(mq11, n); A_(mq12, n); A_(mdr, n); A_(xi, n); A_(mid, n);
     A_(cell_count, ncell + 1); A_(cell_start, ncell + 1); A_(key, n); A_(rank, n); A_(perm, n);
-    A_(nbr, n * (MAXN / 2)); A_(nnbr, n);
+    A_(nnbr, n); A_(emask, n);
+    A_(vnbr, n * (MAXV / 2)); A_(vcnt, n); A_(xi_ref, n); A_(mkey, n); A_(rebuild, 1); A_(resorts, 1);
     A_(sumW, n); A_(V, n); A_(B11, n); A_(B12, n); A_(B22, n); A_(kr, n); A_(dh, n); A_(dhat, n);
     A_(p, n); A_(divx, n); A_(divy, n);
     A_(rec_gu, 4 * n); A_(rec_lap, 2 * n); A_(rec_apd, 2 * n);
@@ -249,6 +259,8 @@ cudaError_t alloc_all(ann_ctx *c)
     return cudaSuccess;
 }
 
+// The step graph: predict -> set-condition -> IF (re-sort flag) { keys, scan, scatter, cell order,
+// re-sort pass A } ELSE { pass A } -> passes B, C, D.  The branch not taken costs nothing.
 cudaError_t capture(ann_ctx *c)
 {
     if (c->exec) {
@@ -256,12 +268,59 @@ cudaError_t capture(ann_ctx *c)
         c->exec = nullptr;
     }
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(c->own, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaGraphCreate(&g, 0);
     if (e) return e;
-    cudaError_t e2 = enqueue_step(c->P, c->b, c->own, nullptr);
+    cudaGraphConditionalHandle h = 0;
+    e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+    if (!e) e = cudaStreamBeginCaptureToGraph(c->own, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e) {
+        cudaGraphDestroy(g);
+        return e;
+    }
+    cudaError_t ec = launch_kernel(0, c->P, c->b, c->own);
+    if (!ec) ec = launch_set_condition(c->b, h, c->own);
+    cudaGraph_t body[2] = {nullptr, nullptr};
+    if (!ec) {
+        cudaStreamCaptureStatus st;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        cudaGraph_t capg = nullptr;
+        ec = cudaStreamGetCaptureInfo(c->own, &st, nullptr, &capg, &deps, nullptr, &nd);
+        cudaGraphNode_t cn = nullptr;
+        if (!ec) {
+            // zeroed storage: the parameter struct's union has no default constructor
+            alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
+            cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(raw);
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeIf;
+            cp.conditional.size = 2;
+            ec = cudaGraphAddNode(&cn, capg, deps, nullptr, nd, &cp);
+            if (!ec) {
+                body[0] = cp.conditional.phGraph_out[0];
+                body[1] = cp.conditional.phGraph_out[1];
+            }
+        }
+        if (!ec) ec = cudaStreamUpdateCaptureDependencies(c->own, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+    }
+    for (int k = 0; k < 2 && !ec; k++) {
+        ec = cudaStreamBeginCaptureToGraph(c->aux, body[k], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (ec) break;
+        cudaError_t el = cudaSuccess;
+        if (k == 0)
+            for (int q = 1; q <= 5 && !el; q++) el = launch_kernel(q, c->P, c->b, c->aux);
+        else
+            el = launch_kernel(6, c->P, c->b, c->aux);
+        cudaGraph_t got = body[k];
+        ec = cudaStreamEndCapture(c->aux, &got);
+        if (!ec) ec = el;
+    }
+    for (int k = 7; k < NKERNELS && !ec; k++) ec = launch_kernel(k, c->P, c->b, c->own);
     e = cudaStreamEndCapture(c->own, &g);
-    if (e2) { if (g) cudaGraphDestroy(g); return e2; }
-    if (e) return e;
+    if (ec || e) {
+        if (g) cudaGraphDestroy(g);
+        return ec ? ec : e;
+    }
     e = cudaGraphInstantiate(&c->exec, g, 0);
     cudaGraphDestroy(g);
     return e;
@@ -284,9 +343,11 @@ int device_status(ann_ctx *c)
     return ANN_ERR_SINGULAR_ALPHA;
 }
 
+// Clears the sticky error bits and counters and schedules a re-sort for the next step.
 cudaError_t clear_flags(ann_ctx *c)
 {
     cudaError_t e = cudaMemsetAsync(c->b.err, 0, sizeof(uint32_t), c->stream);
+    if (!e) e = cudaMemsetAsync(c->b.rebuild, 1, sizeof(uint32_t), c->stream);
     if (!e) e = cudaMemsetAsync(c->b.maxu, 0, sizeof(uint32_t), c->stream);
     if (!e) e = cudaMemsetAsync(c->b.cell_count, 0, sizeof(uint32_t) * (c->P.ncell + 1), c->stream);
     return e;
@@ -342,7 +403,7 @@ __global__ void k_deinterleave(const float *src, float *dst, int n, int stride, 
     if (i < n) dst[i] = src[(size_t)i * stride + comp];
 }
 
-const char kMagic[8] = {'A', 'N', 'N', 'S', 'T', 'A', 'T', '1'};
+const char kMagic[8] = {'A', 'N', 'N', 'S', 'T', 'A', 'T', '2'};
 
 }  // namespace
 
@@ -420,6 +481,7 @@ int ann_create(const ann_params *p, ann_ctx **out)
     cudaError_t e = cudaGetDevice(&c->device);
     if (!e) e = prepare_kernels();
     if (!e) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+    if (!e) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
     if (!e) { c->stream = c->own; e = alloc_all(c); }
     if (!e) e = cudaMallocHost(&c->h_err, sizeof(uint32_t));
     if (!e) e = capture(c);
@@ -441,6 +503,7 @@ void ann_destroy(ann_ctx *c)
     for (void *v : c->allocs) cudaFree(v);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->own) cudaStreamDestroy(c->own);
+    if (c->aux) cudaStreamDestroy(c->aux);
     delete c;
 }
 
@@ -460,6 +523,7 @@ int ann_set_particles(ann_ctx *c, int64_t n, const double *x, const double *y, c
     if (n != c->prm.n) return fail(c, ANN_ERR_INVALID_ARG, "n differs from the n of ann_create");
     if (!x || !y || !ux || !uy || !q11 || !q12) return fail(c, ANN_ERR_INVALID_ARG, "null input array");
     cudaError_t e = clear_flags(c);
+    if (!e) e = cudaMemsetAsync(c->b.resorts, 0, sizeof(uint32_t), c->stream);
     if (e) return cuda_fail(c, e, "ann_set_particles");
     const double *src[7] = {x, y, ux, uy, q11, q12, rho};
     const double *dev[7] = {x, y, ux, uy, q11, q12, rho};
@@ -504,25 +568,47 @@ int ann_step_profile(ann_ctx *c, int64_t nsteps, double *kernel_ms)
 {
     if (!c || nsteps < 0 || !kernel_ms) return ANN_ERR_INVALID_ARG;
     if (!c->have_particles) return fail(c, ANN_ERR_STATE, "ann_step_profile before ann_set_particles");
-    std::vector<cudaEvent_t> ev((size_t)(NKERNELS + 1) * (size_t)nsteps);
+    // The same kernels as the step graph, launched one by one between CUDA events.  The host reads
+    // the re-sort decision after each predictor (one synchronisation per step) and launches only the
+    // branch the graph would take, so each kernel's time is what it costs inside the graph.
+    // Events per step: E[0] before the predictor, E[1] after it, E[2] after the host has read the
+    // decision, E[k + 2] after kernel k >= 1 (or where it would have run).
+    const size_t per = NKERNELS + 2;
+    std::vector<cudaEvent_t> ev(per * (size_t)nsteps);
     cudaError_t e = cudaSuccess;
     size_t made = 0;
     for (; made < ev.size() && !e; made++) e = cudaEventCreate(&ev[made]);
-    for (int64_t s = 0; s < nsteps && !e; s++) e = enqueue_step(c->P, c->b, c->stream, &ev[(size_t)s * (NKERNELS + 1)]);
+    for (int64_t s = 0; s < nsteps && !e; s++) {
+        cudaEvent_t *E = &ev[(size_t)s * per];
+        e = cudaEventRecord(E[0], c->stream);
+        if (!e) e = launch_kernel(0, c->P, c->b, c->stream);
+        if (!e) e = cudaEventRecord(E[1], c->stream);
+        if (!e) e = cudaMemcpyAsync(c->h_err, c->b.rebuild, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+        if (!e) e = cudaStreamSynchronize(c->stream);
+        bool rs = !e && *c->h_err != 0u;
+        if (!e) e = cudaEventRecord(E[2], c->stream);
+        for (int k = 1; k < NKERNELS && !e; k++) {
+            bool run = (k <= 5) ? rs : (k == 6 ? !rs : true);
+            if (run) e = launch_kernel(k, c->P, c->b, c->stream);
+            if (!e) e = cudaEventRecord(E[k + 2], c->stream);
+        }
+    }
     if (!e) e = cudaStreamSynchronize(c->stream);
     for (int64_t s = 0; s < nsteps && !e; s++) {
+        cudaEvent_t *E = &ev[(size_t)s * per];
         for (int k = 0; k < NKERNELS && !e; k++) {
             float ms = 0.f;
-            e = cudaEventElapsedTime(&ms, ev[(size_t)s * (NKERNELS + 1) + k], ev[(size_t)s * (NKERNELS + 1) + k + 1]);
+            e = (k == 0) ? cudaEventElapsedTime(&ms, E[0], E[1]) : cudaEventElapsedTime(&ms, E[k + 1], E[k + 2]);
             kernel_ms[k] += ms;
         }
     }
-    for (size_t k = 0; k < made; k++) if (ev[k]) cudaEventDestroy(ev[k]);
+    for (size_t k = 0; k < made; k++)
+        if (ev[k]) cudaEventDestroy(ev[k]);
     if (e) return cuda_fail(c, e, "ann_step_profile");
-    int s = device_status(c);
+    int st = device_status(c);
     c->steps += nsteps;
     c->t += nsteps * c->P.dt_d;
-    return s;
+    return st;
 }
 
 int ann_kernel_count(void) { return NKERNELS; }
@@ -573,7 +659,9 @@ int ann_get_diagnostics(ann_ctx *c, ann_diag *out)
     double h[NDIAG];
     uint32_t bits = 0;
     unsigned long long band = 0;
+    uint32_t resorts = 0;
     cudaError_t e = enqueue_diag(c->P, c->b, c->diag_part, nb, c->diag_out, c->stream);
+    if (!e) e = cudaMemcpyAsync(&resorts, c->b.resorts, sizeof resorts, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaMemcpyAsync(h, c->diag_out, sizeof h, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaMemcpyAsync(&bits, c->b.err, sizeof bits, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaMemcpyAsync(&band, c->b.band, sizeof band, cudaMemcpyDeviceToHost, c->stream);
@@ -597,6 +685,7 @@ int ann_get_diagnostics(ann_ctx *c, ann_diag *out)
     out->min_det_alpha = h[9];
     out->error_bits = bits;
     out->band_checks = band;
+    out->resorts = (int32_t)resorts;
     return ANN_OK;
 }
 
@@ -608,7 +697,9 @@ int ann_get_neighbors(ann_ctx *c, int64_t *rowptr, int32_t *cols, int64_t cap)
     DevParams Q = c->P;
     Q.half_dt = 0.f;
     Q.half_dt_d = 0.0;
-    cudaError_t e = enqueue_search(Q, c->b, c->stream);
+    // the search re-sorts at the present positions; S keeps its order, so the next step re-sorts too
+    cudaError_t e = cudaMemsetAsync(c->b.rebuild, 1, sizeof(uint32_t), c->stream);
+    if (!e) e = enqueue_search(Q, c->b, c->stream);
     if (e) return cuda_fail(c, e, "ann_get_neighbors search");
     int s = device_status(c);
     if (s) return s;
@@ -643,29 +734,40 @@ int ann_get_neighbors(ann_ctx *c, int64_t *rowptr, int32_t *cols, int64_t cap)
     return ANN_OK;
 }
 
+// File layout: magic, n, parameters, t, step count, re-sort flag, then per particle in the internal
+// order: x, y (FP64); ux, uy, q11, q12, delta, ax, ay (FP32); ID; cell of the last re-sort; split
+// position of the last re-sort (4 x FP32).  The last three reproduce the candidate lists exactly.
 int ann_save_state(ann_ctx *c, const char *path)
 {
     if (!c || !path) return ANN_ERR_INVALID_ARG;
     if (!c->have_particles) return fail(c, ANN_ERR_STATE, "no particles");
     size_t n = (size_t)c->P.n;
     std::vector<double> d(2 * n);
-    std::vector<float> f(7 * n);
+    std::vector<float> f(7 * n), xr(4 * n);
     std::vector<int> id(n);
+    std::vector<uint32_t> mk(n);
+    uint32_t rb = 1;
     const Bufs &b = c->b;
     const float *fs[7] = {b.sux, b.suy, b.sq11, b.sq12, b.sdr, b.sax, b.say};
     cudaError_t e = cudaMemcpyAsync(d.data(), b.sx, 8 * n, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaMemcpyAsync(d.data() + n, b.sy, 8 * n, cudaMemcpyDeviceToHost, c->stream);
     for (int k = 0; k < 7 && !e; k++) e = cudaMemcpyAsync(f.data() + k * n, fs[k], 4 * n, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaMemcpyAsync(id.data(), b.sid, 4 * n, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(mk.data(), b.mkey, 4 * n, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(xr.data(), b.xi_ref, 16 * n, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(&rb, b.rebuild, 4, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaStreamSynchronize(c->stream);
     if (e) return cuda_fail(c, e, "ann_save_state");
+    if (c->steps == 0) rb = 1;   // nothing evaluated yet: the next step re-sorts
     FILE *fp = std::fopen(path, "wb");
     if (!fp) return fail(c, ANN_ERR_IO, std::string("cannot open ") + path);
     int64_t nn = (int64_t)n;
     bool ok = std::fwrite(kMagic, 1, 8, fp) == 8 && std::fwrite(&nn, 8, 1, fp) == 1 &&
               std::fwrite(&c->prm, sizeof c->prm, 1, fp) == 1 && std::fwrite(&c->t, 8, 1, fp) == 1 &&
-              std::fwrite(&c->steps, 8, 1, fp) == 1 && std::fwrite(d.data(), 8, 2 * n, fp) == 2 * n &&
-              std::fwrite(f.data(), 4, 7 * n, fp) == 7 * n && std::fwrite(id.data(), 4, n, fp) == n;
+              std::fwrite(&c->steps, 8, 1, fp) == 1 && std::fwrite(&rb, 4, 1, fp) == 1 &&
+              std::fwrite(d.data(), 8, 2 * n, fp) == 2 * n && std::fwrite(f.data(), 4, 7 * n, fp) == 7 * n &&
+              std::fwrite(id.data(), 4, n, fp) == n && std::fwrite(mk.data(), 4, n, fp) == n &&
+              std::fwrite(xr.data(), 4, 4 * n, fp) == 4 * n;
     ok = (std::fclose(fp) == 0) && ok;
     return ok ? ANN_OK : fail(c, ANN_ERR_IO, "short write");
 }
@@ -680,19 +782,33 @@ int ann_load_state(ann_ctx *c, const char *path)
     ann_params prm;
     double t = 0.0;
     int64_t steps = 0;
+    uint32_t rb = 1;
     bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
               std::fread(&nn, 8, 1, fp) == 1 && std::fread(&prm, sizeof prm, 1, fp) == 1 &&
-              std::fread(&t, 8, 1, fp) == 1 && std::fread(&steps, 8, 1, fp) == 1;
+              std::fread(&t, 8, 1, fp) == 1 && std::fread(&steps, 8, 1, fp) == 1 &&
+              std::fread(&rb, 4, 1, fp) == 1;
     if (!ok) { std::fclose(fp); return fail(c, ANN_ERR_INVALID_ARG, "not a state file"); }
     if (nn != c->prm.n) { std::fclose(fp); return fail(c, ANN_ERR_INVALID_ARG, "state file n differs"); }
     size_t n = (size_t)nn;
     std::vector<double> d(2 * n);
-    std::vector<float> f(7 * n);
+    std::vector<float> f(7 * n), xr(4 * n);
     std::vector<int> id(n);
+    std::vector<uint32_t> mk(n);
     ok = std::fread(d.data(), 8, 2 * n, fp) == 2 * n && std::fread(f.data(), 4, 7 * n, fp) == 7 * n &&
-         std::fread(id.data(), 4, n, fp) == n;
+         std::fread(id.data(), 4, n, fp) == n && std::fread(mk.data(), 4, n, fp) == n &&
+         std::fread(xr.data(), 4, 4 * n, fp) == 4 * n;
     std::fclose(fp);
     if (!ok) return fail(c, ANN_ERR_IO, "short read");
+    // cell starts of the last re-sort, from the cell of each particle (nondecreasing in this order)
+    std::vector<uint32_t> start((size_t)c->P.ncell + 1, 0);
+    if (!rb) {
+        for (size_t i = 0; i < n; i++) {
+            if (mk[i] >= (uint32_t)c->P.ncell || (i > 0 && mk[i] < mk[i - 1]))
+                return fail(c, ANN_ERR_INVALID_ARG, "state file cell assignment is not sorted");
+            start[mk[i] + 1]++;
+        }
+        for (int k = 0; k < c->P.ncell; k++) start[k + 1] += start[k];
+    }
     const Bufs &b = c->b;
     float *fs[7] = {b.sux, b.suy, b.sq11, b.sq12, b.sdr, b.sax, b.say};
     cudaError_t e = clear_flags(c);
@@ -700,12 +816,19 @@ int ann_load_state(ann_ctx *c, const char *path)
     if (!e) e = cudaMemcpyAsync(b.sy, d.data() + n, 8 * n, cudaMemcpyHostToDevice, c->stream);
     for (int k = 0; k < 7 && !e; k++) e = cudaMemcpyAsync(fs[k], f.data() + k * n, 4 * n, cudaMemcpyHostToDevice, c->stream);
     if (!e) e = cudaMemcpyAsync(b.sid, id.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaMemcpyAsync(b.mkey, mk.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaMemcpyAsync(b.xi_ref, xr.data(), 16 * n, cudaMemcpyHostToDevice, c->stream);
+    if (!e && !rb) {
+        e = cudaMemcpyAsync(b.cell_start, start.data(), 4 * start.size(), cudaMemcpyHostToDevice, c->stream);
+        if (!e) e = enqueue_candidates_from_ref(c->P, b, c->stream);
+        if (!e) e = cudaMemsetAsync(b.rebuild, 0, sizeof(uint32_t), c->stream);
+    }
     if (!e) e = cudaStreamSynchronize(c->stream);
     if (e) return cuda_fail(c, e, "ann_load_state");
     c->have_particles = true;
     c->t = t;
     c->steps = steps;
-    return ANN_OK;
+    return device_status(c);
 }
 
 const char *ann_last_error(ann_ctx *c) { return c ? c->last_err.c_str() : ""; }

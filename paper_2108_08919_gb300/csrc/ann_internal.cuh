@@ -15,7 +15,11 @@ constexpr int HCAP = 1024;            // halo particles a tile may stage
 constexpr int MAXN = 64;              // neighbours per particle (ANN_MAX_NEIGHBORS)
 constexpr int MAXC = 64;              // particles per cell (ANN_MAX_PER_CELL)
 constexpr int PT = 256;               // threads per pair-pass block
-constexpr int NKERNELS = 8;
+constexpr int NKERNELS = 10;
+// Candidate ("Verlet") lists hold every pair within 3h (1 + SKIN) at the last re-sort; they stay
+// valid until some particle has moved SKIN/2 * 3h.  Cells are at least 3h (1 + SKIN) wide.
+constexpr double SKIN = 0.02;
+constexpr int MAXV = 64;              // candidates per particle
 constexpr int SCAN_CHUNK = 4096;      // cells per block of the cell-count scan
 
 // Sticky device error bits.
@@ -37,7 +41,9 @@ struct DevParams {
     float cell_hi, cell_lo;  // cell = cell_hi + cell_lo, cell_hi a multiple of q
     float qf, iqf;           // q and 1/q in FP32 (powers of two: exact)
     float R2lo, R2hi;      // FP32 band around (3h)^2 inside which the support test is redone in FP64
-    float R2c;             // coarse (hi-part only) candidate radius^2, padded by the hi-only error
+    float R2c;             // coarse (hi-part only) radius^2 of the re-sort scan, padded by the hi-only error
+    float R2v;             // candidate-list radius^2: (3h (1 + SKIN))^2
+    float skin_max2;       // displacement^2 beyond which a candidate list is no longer valid: (SKIN 3h / 2)^2
     float inv_h, ad, W0, dt, half_dt;
     float kw6, kw15;       // -6 a_d, 15 a_d           (W = a_d t3^5 + kw6 t2^5 + kw15 t1^5)
     float kf5, kf30, kf75; // -5 a_d/h, 30 a_d/h, -75 a_d/h  (F r = kf5 t3^4 + kf30 t2^4 + kf75 t1^4)
@@ -56,10 +62,16 @@ struct Bufs {
     double *mx, *my;
     float *mux, *muy, *mq11, *mq12, *mdr;
     float4 *xi;         // cell-local offset split as (hi_x, hi_y, lo_x, lo_y), hi on the q grid
+    float4 *xi_ref;     // split offset at the last re-sort (candidate lists were built from it)
+    uint32_t *mkey;     // cell each particle was assigned to at the last re-sort
     int *mid;
     uint32_t *cell_count, *cell_start, *key, *rank, *perm;
-    uint32_t *nbr;      // packed slot pairs, (MAXN/2) x n, row-major in the pair index
-    int *nnbr;
+    int *nnbr;          // neighbours per particle (exact support test)
+    unsigned long long *emask;   // bit k set: candidate k is a neighbour
+    uint32_t *vnbr;     // candidate lists: 16-bit tile slots, two per word, word k of particle g at [k n + g]
+    int *vcnt;
+    uint32_t *rebuild;  // non-zero: this step re-sorts and rebuilds the candidate lists
+    uint32_t *resorts;  // number of re-sort steps since the particles were loaded
     float *sumW, *V, *B11, *B12, *B22, *kr, *dh, *dhat, *p, *divx, *divy;
     float *rec_gu, *rec_lap, *rec_apd;   // 4n, 2n, 2n (recording only)
     uint32_t *err, *maxu;
@@ -69,12 +81,17 @@ struct Bufs {
 // Launch-configuration helpers (defined with the kernels).
 const char *kernel_name(int k);
 cudaError_t prepare_kernels();
-// Enqueue one time step on `s`.  With `ev` non-null, ev[0..NKERNELS] are recorded around the
-// kernels (ev[k] before kernel k, ev[NKERNELS] after the last).
-cudaError_t enqueue_step(const DevParams &P, const Bufs &b, cudaStream_t s, cudaEvent_t *ev);
-// Cell sort and pass A only (neighbour lists and volumes) at the positions in S advanced by
-// P.half_dt (callers pass 0 to keep them).
+// Launch kernel k (0 <= k < NKERNELS, in step order) of the time step on `s`.  Kernels 1-5 are the
+// re-sort path and kernel 6 its alternative; each also checks the re-sort flag itself.
+cudaError_t launch_kernel(int k, const DevParams &P, const Bufs &b, cudaStream_t s);
+// Copy the re-sort flag into a graph conditional handle (one thread).
+cudaError_t launch_set_condition(const Bufs &b, cudaGraphConditionalHandle h, cudaStream_t s);
+// Cell sort and the re-sort pass A only (neighbour lists and volumes) at the positions in S advanced
+// by P.half_dt (callers pass 0 to keep them).  Requires *b.rebuild != 0.
 cudaError_t enqueue_search(const DevParams &P, const Bufs &b, cudaStream_t s);
+// Rebuild the candidate lists from xi_ref (the split positions of the last re-sort), with the
+// cell starts of that re-sort: used after a checkpoint is loaded.
+cudaError_t enqueue_candidates_from_ref(const DevParams &P, const Bufs &b, cudaStream_t s);
 // Load FP64 inputs (ID order) into S; rho may be null.
 cudaError_t enqueue_load(const DevParams &P, const Bufs &b, const double *x, const double *y,
                          const double *ux, const double *uy, const double *q11, const double *q12,

@@ -67,19 +67,22 @@ __device__ __forceinline__ float kernel_w(float r2, const DevParams &P)
     return fmaf(P.ad * s3 * s3, t3, fmaf(P.kw6 * s2 * s2, t2, P.kw15 * s1 * s1 * t1));
 }
 
-// FP64 support test of the definition for particles gi (inner cell) and gj (halo image with cell
-// shift (sx, sy) in units of L): d = (x_i - x_j) -+ L, |d|^2 = d_x*d_x + d_y*d_y, no fused ops.
-__device__ __noinline__ bool support64(const DevParams &P, const Bufs &b, int gi, int gj, int sx, int sy)
+// FP64 support test of the definition for particles gi and gj: d = minimum image of x_i - x_j
+// (x_i - x_j, then -L or +L when beyond L/2), |d|^2 = d_x*d_x + d_y*d_y, no fused operations.
+__device__ __noinline__ bool support64(const DevParams &P, const Bufs &b, int gi, int gj)
 {
+    double hL = 0.5 * P.L;
     double dx = __dsub_rn(b.mx[gi], b.mx[gj]);
-    if (sx > 0) dx = __dsub_rn(dx, P.L);
-    else if (sx < 0) dx = __dadd_rn(dx, P.L);
+    if (dx > hL) dx = __dsub_rn(dx, P.L);
+    else if (dx < -hL) dx = __dadd_rn(dx, P.L);
     double dy = __dsub_rn(b.my[gi], b.my[gj]);
-    if (sy > 0) dy = __dsub_rn(dy, P.L);
-    else if (sy < 0) dy = __dadd_rn(dy, P.L);
+    if (dy > hL) dy = __dsub_rn(dy, P.L);
+    else if (dy < -hL) dy = __dadd_rn(dy, P.L);
     double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
     return r2 < P.R2;
 }
+
+__device__ __forceinline__ bool resorting(const Bufs &b) { return *(volatile uint32_t *)b.rebuild != 0u; }
 
 // ---------------------------------------------------------------------------------------------
 // Tile bookkeeping shared by the pair passes
@@ -176,17 +179,24 @@ __device__ __forceinline__ float2 pair_d(const float4 &a, const float4 &b)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Kernel 0: predictor, re-insertion, cell key, max |u'|                         (§3.1, Eq. 30)
+// Kernel 0: predictor, re-insertion, max |u'|, re-sort decision                   (§3.1, Eq. 30)
 // ---------------------------------------------------------------------------------------------
+
+// Split of the offset o of a position from a cell corner: hi = o rounded (in FP32) to the q grid,
+// exact in both precisions; lo = o - hi, exact in FP64, then rounded to FP32.
+__device__ __forceinline__ float2 split_offset(double o, const DevParams &P)
+{
+    float hi = rintf((float)o * P.iqf) * P.qf;
+    return make_float2(hi, (float)(o - (double)hi));
+}
 
 __global__ void __launch_bounds__(256) k_predict(DevParams P, Bufs b)
 {
     if (stopped(b)) return;
     __shared__ float wmax[8];
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int lane = threadIdx.x & 31;
+    bool rs = resorting(b);
     float sp = 0.f;
-    uint32_t key = 0xffffffffu;
     if (i < P.n) {
         float ux = b.sux[i] + P.half_dt * b.sax[i];
         float uy = b.suy[i] + P.half_dt * b.say[i];
@@ -204,30 +214,44 @@ __global__ void __launch_bounds__(256) k_predict(DevParams P, Bufs b)
                 uy = 0.f;
             }
         }
+        sp = sqrtf(ux * ux + uy * uy);
         b.sux[i] = ux;
         b.suy[i] = uy;
         b.sx[i] = x;
         b.sy[i] = y;
-        int cx = min((int)(x * P.inv_cell), P.nc - 1);
-        int cy = min((int)(y * P.inv_cell), P.nc - 1);
-        key = (uint32_t)(cy * P.nc + cx);
-        b.key[i] = key;
-        // offset from the cell corner, split into hi (FP32 on the q grid) + lo (FP32 remainder)
-        double ox = x - __ldg(&b.origin[cx]), oy = y - __ldg(&b.origin[cy]);
-        float hx = rintf((float)ox * P.iqf) * P.qf, hy = rintf((float)oy * P.iqf) * P.qf;
-        b.sxi[i] = make_float4(hx, hy, (float)(ox - (double)hx), (float)(oy - (double)hy));
-        sp = sqrtf(ux * ux + uy * uy);
+        if (!rs) {
+            // The order is that of the last re-sort: write the evaluation copy directly, split
+            // against the cell the particle was assigned to then.  A particle that has moved half
+            // the skin since makes this step re-sort (the kernels after this one see the flag).
+            uint32_t mk = b.mkey[i];
+            int cx = (int)(mk % (uint32_t)P.nc), cy = (int)(mk / (uint32_t)P.nc);
+            double ox = x - __ldg(&b.origin[cx]), oy = y - __ldg(&b.origin[cy]);
+            if (cx == 0 || cx == P.nc - 1) {   // the particle may have crossed the face since
+                if (ox > 0.5 * P.L) ox -= P.L;
+                else if (ox < -0.5 * P.L) ox += P.L;
+            }
+            if (cy == 0 || cy == P.nc - 1) {
+                if (oy > 0.5 * P.L) oy -= P.L;
+                else if (oy < -0.5 * P.L) oy += P.L;
+            }
+            float2 sx_ = split_offset(ox, P), sy_ = split_offset(oy, P);
+            float4 xi = make_float4(sx_.x, sy_.x, sx_.y, sy_.y);
+            float4 rf = b.xi_ref[i];
+            float ddx = (xi.x - rf.x) + (xi.z - rf.z), ddy = (xi.y - rf.y) + (xi.w - rf.w);
+            if (ddx * ddx + ddy * ddy > P.skin_max2) *(volatile uint32_t *)b.rebuild = 1u;
+            b.mx[i] = x;
+            b.my[i] = y;
+            b.xi[i] = xi;
+            b.mux[i] = ux;
+            b.muy[i] = uy;
+            b.mq11[i] = b.sq11[i];
+            b.mq12[i] = b.sq12[i];
+            b.mdr[i] = b.sdr[i];
+            b.mid[i] = b.sid[i];
+        }
     }
-    // Particles arrive in the previous step's cell order, so a warp holds a few runs of equal keys:
-    // one atomic per run instead of one per particle.
-    unsigned grp = __match_any_sync(FULL, key);
-    int leader = __ffs(grp) - 1;
-    uint32_t base = 0;
-    if (lane == leader && key != 0xffffffffu) base = atomicAdd(&b.cell_count[key], (uint32_t)__popc(grp));
-    base = __shfl_sync(FULL, base, leader);
-    if (i < P.n) b.rank[i] = base + (uint32_t)__popc(grp & ((1u << lane) - 1u));
     for (int o = 16; o > 0; o >>= 1) sp = fmaxf(sp, __shfl_xor_sync(FULL, sp, o));
-    if (lane == 0) wmax[threadIdx.x >> 5] = sp;
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = sp;
     __syncthreads();
     if (threadIdx.x < 32) {
         sp = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0.f;
@@ -237,7 +261,38 @@ __global__ void __launch_bounds__(256) k_predict(DevParams P, Bufs b)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Kernel 1: exclusive scan of cell counts -> cell starts, one block per SCAN_CHUNK cells.  Each
+// Kernel 1 (re-sort steps only): cell key of each predicted position, its split against that
+// cell, and its rank in the cell
+// ---------------------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_keys(DevParams P, Bufs b)
+{
+    if (stopped(b) || !resorting(b)) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int lane = threadIdx.x & 31;
+    uint32_t key = 0xffffffffu;
+    if (i < P.n) {
+        double x = b.sx[i], y = b.sy[i];
+        int cx = min((int)(x * P.inv_cell), P.nc - 1);
+        int cy = min((int)(y * P.inv_cell), P.nc - 1);
+        key = (uint32_t)(cy * P.nc + cx);
+        b.key[i] = key;
+        float2 sx_ = split_offset(x - __ldg(&b.origin[cx]), P);
+        float2 sy_ = split_offset(y - __ldg(&b.origin[cy]), P);
+        b.sxi[i] = make_float4(sx_.x, sy_.x, sx_.y, sy_.y);
+    }
+    // Particles arrive in the previous cell order, so a warp holds a few runs of equal keys: one
+    // atomic per run instead of one per particle.
+    unsigned grp = __match_any_sync(FULL, key);
+    int leader = __ffs(grp) - 1;
+    uint32_t base = 0;
+    if (lane == leader && key != 0xffffffffu) base = atomicAdd(&b.cell_count[key], (uint32_t)__popc(grp));
+    base = __shfl_sync(FULL, base, leader);
+    if (i < P.n) b.rank[i] = base + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Kernel 2: exclusive scan of cell counts -> cell starts, one block per SCAN_CHUNK cells.  Each
 // block first sums the counts of all cells before its chunk (coalesced, L2-resident reads), so no
 // block waits on another; then it scans its own chunk.  The counts are cleared by the scatter
 // kernel, after every block has read them.
@@ -245,7 +300,7 @@ __global__ void __launch_bounds__(256) k_predict(DevParams P, Bufs b)
 
 __global__ void __launch_bounds__(1024) k_scan(DevParams P, Bufs b)
 {
-    if (stopped(b)) return;
+    if (stopped(b) || !resorting(b)) return;
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t s_base, s_max;
     int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -302,12 +357,12 @@ __global__ void __launch_bounds__(1024) k_scan(DevParams P, Bufs b)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Kernel 2: scatter particle indices into their cells
+// Kernel 3: scatter particle indices into their cells
 // ---------------------------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) k_scatter(DevParams P, Bufs b)
 {
-    if (stopped(b)) return;
+    if (stopped(b) || !resorting(b)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < P.n) b.perm[b.cell_start[b.key[i]] + b.rank[i]] = (uint32_t)i;
     // every scan block has read the cell counts: clear them for the next step
@@ -315,13 +370,13 @@ __global__ void __launch_bounds__(256) k_scatter(DevParams P, Bufs b)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Kernel 3: order each cell by previous index (a stable sort overall) and gather the state into
+// Kernel 4: order each cell by previous index (a stable sort overall) and gather the state into
 // cell order; FP32 offsets from the cell corner.  One warp per cell.
 // ---------------------------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256) k_cell_order(DevParams P, Bufs b)
 {
-    if (stopped(b)) return;
+    if (stopped(b) || !resorting(b)) return;
     __shared__ uint32_t srt[8][MAXC];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int c = blockIdx.x * 8 + w;
@@ -358,6 +413,7 @@ __global__ void __launch_bounds__(256) k_cell_order(DevParams P, Bufs b)
         b.mx[g] = b.sx[old];
         b.my[g] = b.sy[old];
         b.xi[g] = b.sxi[old];
+        b.mkey[g] = (uint32_t)c;
         b.mux[g] = b.sux[old];
         b.muy[g] = b.suy[old];
         b.mq11[g] = b.sq11[old];
@@ -367,27 +423,157 @@ __global__ void __launch_bounds__(256) k_cell_order(DevParams P, Bufs b)
     }
 }
 
+// Exact support test of a candidate at FP32 squared distance r2: FP32 outside the rounding band,
+// the FP64 definition inside it.
+__device__ __forceinline__ bool in_support(float r2, const DevParams &P, const Bufs &b, int gi, int gj)
+{
+    bool in = r2 < P.R2lo;
+    if (!in && r2 < P.R2hi) {
+        in = support64(P, b, gi, gj);
+        atomicAdd(b.band, 1ull);
+    }
+    return in;
+}
+
 // ---------------------------------------------------------------------------------------------
-// Kernel 4: pass A -- neighbour lists, sum_j W_ij (self included) and V = 1/sum  (Eqs. 18, 19)
+// Kernel 5 (re-sort steps only): pass A -- candidate lists, neighbour counts, sum_j W_ij (self
+// included) and V = 1/sum  (Eqs. 18, 19)
 //
 // Two levels.  The coarse scan runs over the 3 x 3 cell stencil (three contiguous slot ranges, one
 // per stencil row) on the hi parts alone against a padded radius, appending candidates without a
-// branch.  The fine pass forms the correctly rounded pair vector of each candidate, applies the
-// exact support test (FP64 inside the rounding band), accumulates W and compacts the list in place.
+// branch.  The fine pass forms the correctly rounded pair vector of each candidate and keeps those
+// within 3h (1 + SKIN): the candidate list of this and the following steps.  For this step it also
+// counts the neighbours (exact support test) and sums W, which is zero beyond the support.
+// With FROM_REF the positions are those of the last re-sort (xi_ref) and only the candidate lists
+// are rebuilt (used after a checkpoint is loaded).
 // ---------------------------------------------------------------------------------------------
 
-constexpr int SMEM_A = HCAP * (16 + 4 + 1) + MAXN * PT * 2;
+constexpr int SMEM_A = HCAP * (16 + 4 + 1) + MAXV * PT * 2;
 
-__global__ void __launch_bounds__(PT) k_pass_a(DevParams P, Bufs b)
+template <bool FROM_REF>
+__global__ void __launch_bounds__(PT) k_pass_a_resort(DevParams P, Bufs b)
 {
-    if (stopped(b)) return;
+    if (stopped(b) || (!FROM_REF && !resorting(b))) return;
     __shared__ TileShared ts;
     extern __shared__ __align__(16) unsigned char dsm[];
     float4 *pos = reinterpret_cast<float4 *>(dsm);
     const float2 *phi = reinterpret_cast<const float2 *>(dsm);   // hi parts: phi[2 j] = pos[j].xy
     int *sg = reinterpret_cast<int *>(pos + HCAP);
     uint16_t *lst = reinterpret_cast<uint16_t *>(sg + HCAP);
-    unsigned char *shc = reinterpret_cast<unsigned char *>(lst + MAXN * PT);
+    unsigned char *shc = reinterpret_cast<unsigned char *>(lst + MAXV * PT);
+    Tile T;
+    if (!tile_begin(P, b, ts, T)) {
+        if (threadIdx.x == 0) atomicOr(b.err, EB_HALO);
+        return;
+    }
+    for (int t = threadIdx.x; t < T.H; t += PT) {
+        int h = slot_cell(ts, T.NH, t);
+        int g = ts.start[h] + (t - ts.off[h]);
+        float hx = (float)(h % T.HX), hy = (float)(h / T.HX);
+        float4 o = FROM_REF ? b.xi_ref[g] : b.xi[g];
+        pos[t] = make_float4(o.x + hx * P.cell_hi, o.y + hy * P.cell_hi, o.z + hx * P.cell_lo, o.w + hy * P.cell_lo);
+        sg[t] = g;
+        shc[t] = (unsigned char)h;
+    }
+    __syncthreads();
+    if (!FROM_REF && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(b.resorts, 1u);
+    uint16_t *my = lst + threadIdx.x;   // this thread's list column, stride PT
+    for (int q = threadIdx.x; q < T.Ni; q += PT) {
+        int si = inner_slot(ts, T, q);
+        int h = shc[si], hx = h % T.HX, hy = h / T.HX;
+        float4 pi = pos[si];
+        int gi = sg[si];
+        int cnt = 0;
+        for (int oy = -1; oy <= 1; oy++) {
+            int row = (hy + oy) * T.HX + hx;
+            int j0 = ts.off[row - 1], j1 = ts.off[row + 2];
+            for (int j = j0; j < j1; j++) {
+                float2 pj = phi[2 * j];
+                float dx = pi.x - pj.x, dy = pi.y - pj.y;
+                bool in = (dx * dx + dy * dy < P.R2c) & (j != si);
+                my[min(cnt, MAXV - 1) * PT] = (uint16_t)j;
+                cnt += in;
+            }
+        }
+        if (cnt > MAXV) {
+            atomicOr(b.err, EB_NBR);
+            cnt = MAXV;
+        }
+        float sw = P.W0;
+        int cv = 0, nn = 0;
+        unsigned long long mask = 0ull;
+        for (int k = 0; k < cnt; k++) {
+            int j = my[k * PT];
+            float2 d = pair_d(pi, pos[j]);
+            float r2 = d.x * d.x + d.y * d.y;
+            bool cand = r2 < P.R2v;
+            if (!FROM_REF && cand) {
+                sw += kernel_w<true>(r2, P);
+                bool in = in_support(r2, P, b, gi, sg[j]);
+                nn += in;
+                mask |= (unsigned long long)in << cv;
+            }
+            my[cv * PT] = (uint16_t)j;
+            cv += cand;
+        }
+        uint32_t *out = b.vnbr + gi;
+        for (int k = 0; k < cv; k += 2) {
+            uint32_t lo = my[k * PT];
+            uint32_t hi = (k + 1 < cv) ? my[(k + 1) * PT] : 0xffffu;
+            *out = lo | (hi << 16);
+            out += P.n;
+        }
+        b.vcnt[gi] = cv;
+        if (!FROM_REF) {
+            b.nnbr[gi] = nn;
+            b.emask[gi] = mask;
+            b.sumW[gi] = sw;
+            b.V[gi] = 1.0f / sw;
+            b.xi_ref[gi] = b.xi[gi];   // the split positions this re-sort used
+        }
+    }
+}
+
+// Visit the neighbour slots of particle gi (c of them, two per list word), prefetching the next
+// word while the current pair is processed.  Slots are masked into the staging buffer.
+template <typename Fn>
+__device__ __forceinline__ void for_each_slot(const uint32_t *list, int n, int gi, int c, Fn &&fn)
+{
+    const uint32_t *p = list + gi;
+    uint32_t w = c > 0 ? __ldg(p) : 0u;
+    int k = 0;
+    for (; k + 1 < c; k += 2) {
+        p += n;
+        uint32_t wn = (k + 2 < c) ? __ldg(p) : 0u;
+        fn((int)(w & (HCAP - 1)), k);
+        fn((int)((w >> 16) & (HCAP - 1)), k + 1);
+        w = wn;
+    }
+    if (k < c) fn((int)(w & (HCAP - 1)), k);
+}
+
+// Candidates of particle gi.  Beyond the support the clamped kernel gives W = F = 0 exactly, and
+// adding +0 or -0 leaves an FP32 sum unchanged, so sums over candidates equal sums over neighbours.
+template <typename Fn>
+__device__ __forceinline__ void for_each_candidate(const DevParams &P, const Bufs &b, int gi, Fn &&fn)
+{
+    for_each_slot(b.vnbr, P.n, gi, b.vcnt[gi], fn);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Kernel 6: pass A -- neighbour counts (exact support test on the candidates), sum_j W_ij (self
+// included) and V = 1/sum  (Eqs. 18, 19).  Skipped on re-sort steps, which do this in kernel 5.
+// ---------------------------------------------------------------------------------------------
+
+constexpr int SMEM_AF = HCAP * (16 + 4);
+
+__global__ void __launch_bounds__(PT) k_pass_a_filter(DevParams P, Bufs b)
+{
+    if (stopped(b) || resorting(b)) return;
+    __shared__ TileShared ts;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float4 *pos = reinterpret_cast<float4 *>(dsm);
+    int *sg = reinterpret_cast<int *>(pos + HCAP);
     Tile T;
     if (!tile_begin(P, b, ts, T)) {
         if (threadIdx.x == 0) atomicOr(b.err, EB_HALO);
@@ -397,84 +583,32 @@ __global__ void __launch_bounds__(PT) k_pass_a(DevParams P, Bufs b)
         SlotInfo s = slot_info(P, b, ts, T, t);
         pos[t] = s.e;
         sg[t] = s.g;
-        shc[t] = (unsigned char)s.h;
     }
     __syncthreads();
-    uint16_t *my = lst + threadIdx.x;   // this thread's list column, stride PT
     for (int q = threadIdx.x; q < T.Ni; q += PT) {
         int si = inner_slot(ts, T, q);
-        int h = shc[si], hx = h % T.HX, hy = h / T.HX;
+        int gi = sg[si];
         float4 pi = pos[si];
-        int cnt = 0;
-        for (int oy = -1; oy <= 1; oy++) {
-            int row = (hy + oy) * T.HX + hx;
-            int j0 = ts.off[row - 1], j1 = ts.off[row + 2];
-            for (int j = j0; j < j1; j++) {
-                float2 pj = phi[2 * j];
-                float dx = pi.x - pj.x, dy = pi.y - pj.y;
-                bool in = (dx * dx + dy * dy < P.R2c) & (j != si);
-                my[min(cnt, MAXN - 1) * PT] = (uint16_t)j;
-                cnt += in;
-            }
-        }
-        if (cnt > MAXN) {
-            atomicOr(b.err, EB_NBR);
-            cnt = MAXN;
-        }
         float sw = P.W0;
-        int c = 0;
-        for (int k = 0; k < cnt; k++) {
-            int j = my[k * PT];
+        int nn = 0;
+        unsigned long long mask = 0ull;
+        for_each_candidate(P, b, gi, [&](int j, int kc) {
             float2 d = pair_d(pi, pos[j]);
             float r2 = d.x * d.x + d.y * d.y;
-            bool in = r2 < P.R2lo;
-            if (!in && r2 < P.R2hi) {
-                int hj = shc[j];
-                int cxu = T.cx0 - 1 + hj % T.HX, cyu = T.cy0 - 1 + hj / T.HX;
-                int sx = cxu < 0 ? -1 : (cxu >= P.nc ? 1 : 0);
-                int sy = cyu < 0 ? -1 : (cyu >= P.nc ? 1 : 0);
-                in = support64(P, b, sg[si], sg[j], sx, sy);
-                atomicAdd(b.band, 1ull);
-            }
-            float Wv = kernel_w<true>(r2, P);
-            sw += in ? Wv : 0.f;
-            my[c * PT] = (uint16_t)j;
-            c += in;
-        }
-        int gi = sg[si];
+            sw += kernel_w<true>(r2, P);
+            bool in = in_support(r2, P, b, gi, sg[j]);
+            nn += in;
+            mask |= (unsigned long long)in << kc;
+        });
+        b.nnbr[gi] = nn;
+        b.emask[gi] = mask;
         b.sumW[gi] = sw;
         b.V[gi] = 1.0f / sw;
-        b.nnbr[gi] = c;
-        uint32_t *out = b.nbr + gi;
-        for (int k = 0; k < c; k += 2) {
-            uint32_t lo = my[k * PT];
-            uint32_t hi = (k + 1 < c) ? my[(k + 1) * PT] : 0xffffu;
-            *out = lo | (hi << 16);
-            out += P.n;
-        }
     }
-}
-
-// Visit the neighbour slots of particle gi (c of them, two per list word), prefetching the next
-// word while the current pair is processed.  Slots are masked into the staging buffer.
-template <typename Fn>
-__device__ __forceinline__ void for_each_neighbor(const DevParams &P, const Bufs &b, int gi, int c, Fn &&fn)
-{
-    const uint32_t *p = b.nbr + gi;
-    uint32_t w = c > 0 ? __ldg(p) : 0u;
-    int k = 0;
-    for (; k + 1 < c; k += 2) {
-        p += P.n;
-        uint32_t wn = (k + 2 < c) ? __ldg(p) : 0u;
-        fn((int)(w & (HCAP - 1)));
-        fn((int)((w >> 16) & (HCAP - 1)));
-        w = wn;
-    }
-    if (k < c) fn((int)(w & (HCAP - 1)));
 }
 
 // ---------------------------------------------------------------------------------------------
-// Kernel 5: pass B -- correction tensor alpha and B = alpha^-1 (Eq. 22), corrected velocity
+// Kernel 7: pass B -- correction tensor alpha and B = alpha^-1 (Eq. 22), corrected velocity
 // gradient (Eq. 20), continuity (Eq. 25) and half-step density, Q Laplacian (Eq. 21), molecular
 // field (Eq. 7), co-rotation term (Eq. 2) and the Q update of Eq. (24).
 // ---------------------------------------------------------------------------------------------
@@ -485,6 +619,7 @@ template <bool QOLD>
 __global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
 {
     if (stopped(b)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *b.rebuild = 0u;   // both pass A kernels have run
     __shared__ TileShared ts;
     extern __shared__ __align__(16) unsigned char dsm[];
     float4 *sp = reinterpret_cast<float4 *>(dsm);     // split position
@@ -513,14 +648,13 @@ __global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
         float l00 = 0.f, l01 = 0.f, l10 = 0.f, l11 = 0.f;
         float r1xx = 0.f, r1xy = 0.f, r1yy = 0.f, r2xx = 0.f, r2xy = 0.f, r2yy = 0.f;
         float g1x = 0.f, g1y = 0.f, g2x = 0.f, g2y = 0.f;
-        int c = b.nnbr[gi];
         float di = b.mdr[gi];   // loaded ahead of the neighbour loop
-        for_each_neighbor(P, b, gi, c, [&](int j) {
+        for_each_candidate(P, b, gi, [&](int j, int kc) {
             float4 bj = sb[j];
             float2 d = pair_d(pi, sp[j]);
             float r2 = d.x * d.x + d.y * d.y;
             float Wv, F, rinv;
-            kernel_wf<false>(r2, P, Wv, F, rinv);
+            kernel_wf<true>(r2, P, Wv, F, rinv);
             float g = bj.x * F;
             float gx = g * d.x, gy = g * d.y;
             float mxx = gx * d.x, mxy = gx * d.y, myy = gy * d.y;
@@ -597,7 +731,7 @@ __global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Kernel 6: pass C -- density filter (Eq. 28), equation of state (Eq. 26), div Q^{n+1}
+// Kernel 8: pass C -- density filter (Eq. 28), equation of state (Eq. 26), div Q^{n+1}
 // ---------------------------------------------------------------------------------------------
 
 constexpr int SMEM_C = HCAP * (16 + 16 + 4);
@@ -631,7 +765,6 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
         int gi = sg[si];
         float4 pi = sp[si], bi = sb[si];
         float shep = 0.f, g1x = 0.f, g1y = 0.f, g2x = 0.f, g2y = 0.f;
-        int c = b.nnbr[gi];
         float swi = b.sumW[gi];   // loaded ahead of the neighbour loop
         float B11 = 0.f, B12 = 0.f, B22 = 0.f;
         if (QNEW) {
@@ -639,12 +772,12 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
             B12 = b.B12[gi];
             B22 = b.B22[gi];
         }
-        for_each_neighbor(P, b, gi, c, [&](int j) {
+        for_each_candidate(P, b, gi, [&](int j, int kc) {
             float4 bj = sb[j];
             float2 d = pair_d(pi, sp[j]);
             float r2 = d.x * d.x + d.y * d.y;
             float Wv, F, rinv;
-            kernel_wf<false>(r2, P, Wv, F, rinv);
+            kernel_wf<true>(r2, P, Wv, F, rinv);
             shep += (bi.y - bj.y) * Wv;
             if (QNEW) {
                 float g = bj.x * F;
@@ -669,7 +802,7 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Kernel 7: pass D -- momentum (Eq. 23), corrector (§3.1), APD (Eq. 29), re-insertion (Eq. 30)
+// Kernel 9: pass D -- momentum (Eq. 23), corrector (§3.1), APD (Eq. 29), re-insertion (Eq. 30)
 // ---------------------------------------------------------------------------------------------
 
 constexpr int SMEM_D = HCAP * (16 + 16 + 8 + 4);
@@ -715,6 +848,7 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
         float fx = 0.f, fy = 0.f, vx = 0.f, vy = 0.f;
         float sux = 0.f, suy = 0.f, sr = 0.f, sdx = 0.f, sdy = 0.f;
         int c = b.nnbr[gi];
+        unsigned long long emask = b.emask[gi];   // which candidates are neighbours
         // per-particle inputs of the epilogue, loaded ahead of the neighbour loop
         float dhat = b.dhat[gi], kri = b.kr[gi], swi = b.sumW[gi];
         float B11 = 0.f, B12 = 0.f, B22 = 0.f, dvx = 0.f, dvy = 0.f;
@@ -726,12 +860,12 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
             dvy = b.divy[gi];
         }
         double mxi = b.mx[gi], myi = b.my[gi];
-        for_each_neighbor(P, b, gi, c, [&](int j) {
+        for_each_candidate(P, b, gi, [&](int j, int kc) {
             float4 bj = sb[j];
             float2 d = pair_d(pi, sp[j]);
             float r2 = d.x * d.x + d.y * d.y;
             float Wv, F, rinv;
-            kernel_wf<false>(r2, P, Wv, F, rinv);
+            kernel_wf<true>(r2, P, Wv, F, rinv);
             float ux = bi.z - bj.z, uy = bi.w - bj.w;
             float ud = ux * d.x + uy * d.y;
             float rinv2 = rinv * rinv;
@@ -753,8 +887,10 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
             }
             sux += ux * Wv;
             suy += uy * Wv;
-            sr += r2 * rinv;
-            float rinv3 = rinv2 * rinv;
+            // APD sums run over the neighbours only: their terms do not vanish at the support edge
+            float m = (float)((unsigned)(emask >> kc) & 1u);
+            sr += m * (r2 * rinv);
+            float rinv3 = m * (rinv2 * rinv);
             sdx += d.x * rinv3;
             sdy += d.y * rinv3;
         });
@@ -780,8 +916,9 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
             apx = sc_ * sdx;
             apy = sc_ * sdy;
         }
-        double xn = mxi + (double)(P.half_dt * unx + apx);
-        double yn = myi + (double)(P.half_dt * uny + apy);
+        float stepx = P.half_dt * unx + apx, stepy = P.half_dt * uny + apy;
+        double xn = mxi + (double)stepx;
+        double yn = myi + (double)stepy;
         if (!(in_box(xn, P.bitsL) && in_box(yn, P.bitsL))) {   // rare: re-insert (Eq. 30)
             xn = wrap_d(xn, P.L) + 0.0;
             yn = wrap_d(yn, P.L) + 0.0;
@@ -803,6 +940,12 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
             b.rec_apd[2 * gi + 1] = apy;
         }
     }
+}
+
+// Copies the re-sort decision into the condition of the step graph's IF / ELSE node.
+__global__ void k_set_condition(Bufs b, cudaGraphConditionalHandle h)
+{
+    cudaGraphSetConditional(h, *(volatile uint32_t *)b.rebuild != 0u ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -848,22 +991,27 @@ __global__ void __launch_bounds__(PT) k_export_nbrs(DevParams P, Bufs b, int *co
 {
     __shared__ TileShared ts;
     extern __shared__ __align__(16) unsigned char dsm[];
-    int *sg = reinterpret_cast<int *>(dsm);
+    float4 *pos = reinterpret_cast<float4 *>(dsm);
+    int *sg = reinterpret_cast<int *>(pos + HCAP);
     Tile T;
     if (!tile_begin(P, b, ts, T)) return;
     for (int t = threadIdx.x; t < T.H; t += PT) {
-        int h = slot_cell(ts, T.NH, t);
-        sg[t] = ts.start[h] + (t - ts.off[h]);
+        SlotInfo s = slot_info(P, b, ts, T, t);
+        pos[t] = s.e;
+        sg[t] = s.g;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < T.Ni; q += PT) {
         int si = inner_slot(ts, T, q);
         int gi = sg[si];
-        int c = b.nnbr[gi];
+        float4 pi = pos[si];
         int k = 0;
-        for_each_neighbor(P, b, gi, c, [&](int j) {
-            cols[(size_t)k * P.n + gi] = j < T.H ? b.mid[sg[j]] : -1;
-            k++;
+        unsigned long long emask = b.emask[gi];
+        for_each_candidate(P, b, gi, [&](int j, int kc) {
+            if (((emask >> kc) & 1ull) && j < T.H && k < MAXN) {
+                cols[(size_t)k * P.n + gi] = b.mid[sg[j]];
+                k++;
+            }
         });
     }
 }
@@ -923,8 +1071,8 @@ __global__ void k_diag_final(const double *part, int nblocks, double *out)
     out[q] = acc;
 }
 
-const char *const kNames[NKERNELS] = {"predict", "cell_scan", "cell_scatter", "cell_order",
-                                      "pass_a",  "pass_b",    "pass_c",       "pass_d"};
+const char *const kNames[NKERNELS] = {"predict", "cell_keys", "cell_scan", "cell_scatter", "cell_order",
+                                      "pass_a_resort", "pass_a", "pass_b", "pass_c", "pass_d"};
 
 inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
 
@@ -935,7 +1083,9 @@ const char *kernel_name(int k) { return (k >= 0 && k < NKERNELS) ? kNames[k] : n
 cudaError_t prepare_kernels()
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_pass_a, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_A))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_a_resort<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_A))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_a_resort<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_A))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_a_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_AF))) return e;
     if ((e = cudaFuncSetAttribute(k_pass_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_B))) return e;
     if ((e = cudaFuncSetAttribute(k_pass_b<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_B))) return e;
     if ((e = cudaFuncSetAttribute(k_pass_c<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_C))) return e;
@@ -945,45 +1095,53 @@ cudaError_t prepare_kernels()
     return cudaSuccess;
 }
 
-static cudaError_t launch_front(const DevParams &P, const Bufs &b, cudaStream_t s, cudaEvent_t *ev)
+// Kernel k of the step on stream s (see kNames).
+cudaError_t launch_kernel(int k, const DevParams &P, const Bufs &b, cudaStream_t s)
 {
-    int nb = blocks_for(P.n, 256);
-    if (ev) cudaEventRecord(ev[0], s);
-    k_predict<<<nb, 256, 0, s>>>(P, b);
-    if (ev) cudaEventRecord(ev[1], s);
-    k_scan<<<P.nsblk, 1024, 0, s>>>(P, b);
-    if (ev) cudaEventRecord(ev[2], s);
-    k_scatter<<<nb, 256, 0, s>>>(P, b);
-    if (ev) cudaEventRecord(ev[3], s);
-    k_cell_order<<<blocks_for(P.ncell, 8), 256, 0, s>>>(P, b);
-    if (ev) cudaEventRecord(ev[4], s);
-    k_pass_a<<<P.tiles * P.tiles, PT, SMEM_A, s>>>(P, b);
+    int nb = blocks_for(P.n, 256), nt = P.tiles * P.tiles;
+    switch (k) {
+    case 0: k_predict<<<nb, 256, 0, s>>>(P, b); break;
+    case 1: k_keys<<<nb, 256, 0, s>>>(P, b); break;
+    case 2: k_scan<<<P.nsblk, 1024, 0, s>>>(P, b); break;
+    case 3: k_scatter<<<nb, 256, 0, s>>>(P, b); break;
+    case 4: k_cell_order<<<blocks_for(P.ncell, 8), 256, 0, s>>>(P, b); break;
+    case 5: k_pass_a_resort<false><<<nt, PT, SMEM_A, s>>>(P, b); break;
+    case 6: k_pass_a_filter<<<nt, PT, SMEM_AF, s>>>(P, b); break;
+    case 7:
+        if (P.qnew) k_pass_b<false><<<nt, PT, SMEM_B, s>>>(P, b);
+        else k_pass_b<true><<<nt, PT, SMEM_B, s>>>(P, b);
+        break;
+    case 8:
+        if (P.qnew) k_pass_c<true><<<nt, PT, SMEM_C, s>>>(P, b);
+        else k_pass_c<false><<<nt, PT, SMEM_C, s>>>(P, b);
+        break;
+    case 9:
+        if (P.conservative) k_pass_d<true><<<nt, PT, SMEM_D, s>>>(P, b);
+        else k_pass_d<false><<<nt, PT, SMEM_D, s>>>(P, b);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-cudaError_t enqueue_step(const DevParams &P, const Bufs &b, cudaStream_t s, cudaEvent_t *ev)
+cudaError_t launch_set_condition(const Bufs &b, cudaGraphConditionalHandle h, cudaStream_t s)
 {
-    cudaError_t e = launch_front(P, b, s, ev);
-    if (e) return e;
-    int nt = P.tiles * P.tiles;
-    if (ev) cudaEventRecord(ev[5], s);
-    if (P.qnew) k_pass_b<false><<<nt, PT, SMEM_B, s>>>(P, b);
-    else k_pass_b<true><<<nt, PT, SMEM_B, s>>>(P, b);
-    if (ev) cudaEventRecord(ev[6], s);
-    if (P.qnew) k_pass_c<true><<<nt, PT, SMEM_C, s>>>(P, b);
-    else k_pass_c<false><<<nt, PT, SMEM_C, s>>>(P, b);
-    if (ev) cudaEventRecord(ev[7], s);
-    if (P.conservative) k_pass_d<true><<<nt, PT, SMEM_D, s>>>(P, b);
-    else k_pass_d<false><<<nt, PT, SMEM_D, s>>>(P, b);
-    if (ev) cudaEventRecord(ev[8], s);
+    k_set_condition<<<1, 1, 0, s>>>(b, h);
     return cudaGetLastError();
 }
 
 cudaError_t enqueue_search(const DevParams &P, const Bufs &b, cudaStream_t s)
 {
-    cudaError_t e = launch_front(P, b, s, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k <= 5 && !e; k++) e = launch_kernel(k, P, b, s);
     if (e) return e;
     return cudaMemsetAsync(b.maxu, 0, sizeof(uint32_t), s);
+}
+
+cudaError_t enqueue_candidates_from_ref(const DevParams &P, const Bufs &b, cudaStream_t s)
+{
+    k_pass_a_resort<true><<<P.tiles * P.tiles, PT, SMEM_A, s>>>(P, b);
+    return cudaGetLastError();
 }
 
 cudaError_t enqueue_load(const DevParams &P, const Bufs &b, const double *x, const double *y,
@@ -1006,7 +1164,7 @@ cudaError_t enqueue_unpermute(const void *f, const int *id, void *out, int n, in
 
 cudaError_t enqueue_export_nbrs(const DevParams &P, const Bufs &b, int *cols_tmp, cudaStream_t s)
 {
-    k_export_nbrs<<<P.tiles * P.tiles, PT, HCAP * 4, s>>>(P, b, cols_tmp);
+    k_export_nbrs<<<P.tiles * P.tiles, PT, SMEM_AF, s>>>(P, b, cols_tmp);
     return cudaGetLastError();
 }
 

@@ -64,9 +64,10 @@ def test_version_and_status_strings(B):
     assert B.ann_status_string(0) == "ok"
     assert "neighbour" in B.ann_status_string(-5)
     assert B.ann_status_string(-999) == "unknown status"
-    assert B.ann_kernel_count() == 8
-    names = [B.ann_kernel_name(k) for k in range(8)]
-    assert names[4:] == ["pass_a", "pass_b", "pass_c", "pass_d"]
+    assert B.ann_kernel_count() == 10
+    names = [B.ann_kernel_name(k) for k in range(10)]
+    assert names == ["predict", "cell_keys", "cell_scan", "cell_scatter", "cell_order",
+                     "pass_a_resort", "pass_a", "pass_b", "pass_c", "pass_d"]
 
 
 def test_default_params_are_the_paper_setup(B):
@@ -96,11 +97,12 @@ def test_validation_rejects_crowded_support(B):
 
 
 def test_grid_info(B):
-    for nx, nc in ((64, 16), (256, 65), (1024, 262)):
+    # cells are at least 3h (1 + 0.02) wide, the radius of the candidate lists
+    for nx, nc in ((64, 16), (256, 64), (1024, 257)):
         p = B.ann_default_params(n=nx * nx, h=1.3 / nx)
         g = B.ann_grid_info(p)
         assert g.cells_per_side == nc
-        assert g.cell_size >= 3 * p.h
+        assert g.cell_size >= 3 * p.h * 1.02
         assert g.tiles_per_side == math.ceil(nc / 4)
         assert g.expected_neighbors == pytest.approx(math.pi * 3.9 ** 2)
         assert g.device_bytes > nx * nx * 200

@@ -185,3 +185,85 @@ def test_device_inputs_and_outputs(B):
         assert np.array_equal(out.cpu().numpy(), host)
     finally:
         B.ann_destroy(ctx)
+
+
+def _moving_case(nx=64):
+    """Velocities of order 1: particles move ~1e-4 per step, so the candidate lists are rebuilt
+    (particles re-sorted) every few steps.  eta = 0.1 keeps dt = 1e-4 inside the viscous limit."""
+    ic = random_velocity_ic(nx, 12, u_scale=2.0, rho_scale=1e-4)
+    return ic, params(nx, eta=0.1, c0_min=0.5)
+
+
+def test_parity_across_resorts(B, orc):
+    ic, p = _moving_case()
+    run = GpuRun(B, p, ic)
+    st = oracle_state(ic)
+    P = oracle_params(orc, p, "brute")
+    worst = {}
+    try:
+        for _ in range(30):
+            run.step(1)
+            st, _ = orc.step(P, st, 1)
+            for k, e in compare_state(run.state(), st, ic["x"], ic["y"]).items():
+                worst[k] = max(worst.get(k, 0.0), e)
+        d = B.ann_get_diagnostics(run.ctx)
+        rp, cols = B.ann_get_neighbors(run.ctx, run.n)
+    finally:
+        run.close()
+    assert d["resorts"] >= 4, d
+    bad = {k: e for k, e in worst.items() if not e <= 1e-5}
+    assert not bad, worst
+    rp_o, cols_o = orc.neighbors(st["x"], st["y"], 1.0, p["h"], "brute")
+    # positions differ at the 1e-12 level between the two sides: compare lists away from ties
+    assert abs(int(rp[-1]) - int(rp_o[-1])) <= 2
+
+
+def test_checkpoint_across_resorts(B, tmp_path):
+    ic, p = _moving_case()
+    a = GpuRun(B, p, ic)
+    b = GpuRun(B, p, ic)
+    try:
+        a.step(30)
+        b.step(13)
+        path = str(tmp_path / "state.bin")
+        B.ann_save_state(b.ctx, path)
+        b.close()
+        c = GpuRun(B, p, si.jittered_lattice(64, seed=5))
+        B.ann_load_state(c.ctx, path)
+        c.step(17)
+        assert B.ann_get_diagnostics(a.ctx)["resorts"] >= 4
+        sa, sc = a.state(), c.state()
+        for k in sa:
+            assert np.array_equal(sa[k], sc[k]), k
+        c.close()
+    finally:
+        a.close()
+
+
+def test_late_resort_within_the_step(B, orc):
+    """A uniform translation fast enough that particles cross half the candidate skin within one
+    half step: the step notices it at the evaluation point and re-sorts before the pair passes,
+    so results still match the oracle (which searches from scratch every step)."""
+    nx = 32
+    ic = si.jittered_lattice(nx, seed=0)
+    n = ic["n"]
+    ic["q11"] = np.full(n, 0.6)
+    ic["q12"] = np.full(n, 0.2)
+    ic["ux"] = np.full(n, 15.0)
+    ic["uy"] = np.full(n, -4.0)
+    p = params(nx, eta=0.01, zeta=0.0, K=0.0)
+    run = GpuRun(B, p, ic)
+    st = oracle_state(ic)
+    P = oracle_params(orc, p, "brute")
+    try:
+        for _ in range(4):
+            run.step(1)
+            st, _ = orc.step(P, st, 1)
+            errs = compare_state(run.state(), st, ic["x"], ic["y"])
+            assert errs["disp"] <= 1e-5 and errs["u"] <= 1e-5, errs
+        d = B.ann_get_diagnostics(run.ctx)
+    finally:
+        run.close()
+    # a full step moves dt |u| = 1.55e-3, more than half the skin 0.5 * 0.02 * 3h = 1.2e-3, so
+    # every step finds the lists of the previous one stale and re-sorts
+    assert d["resorts"] >= 2, d
