@@ -40,6 +40,7 @@ class OrcParams(ctypes.Structure):
         ("c_shift", ctypes.c_double),
         ("apd", ctypes.c_int32), ("conservative", ctypes.c_int32),
         ("q_new_in_momentum", ctypes.c_int32), ("nbr_mode", ctypes.c_int32),
+        ("elastic", ctypes.c_int32),
     ]
 
 
@@ -52,7 +53,7 @@ class OrcRecord(ctypes.Structure):
 
 DEFAULTS = dict(L=1.0, h=1.3 / 64, dt=1e-4, rho0=1.0, eta=1.0, Gamma=0.34, lam=0.7, A=0.0,
                 B=0.0, C=1.0, K=0.04, zeta=0.05, gamma_eos=7.0, beta=1.0, c0_min=0.0,
-                c_shift=1.0 / 3.0, apd=1, conservative=0, q_new_in_momentum=1)
+                c_shift=1.0 / 3.0, apd=1, conservative=0, q_new_in_momentum=1, elastic=0)
 
 NBR_MODES = {"brute": 0, "ghost": 1, "cells": 2}
 
@@ -107,15 +108,18 @@ def lib() -> ctypes.CDLL:
                                      _lp, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
         L.orc_q_rate.restype = None
         L.orc_q_rate.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_double, ctypes.c_double,
-                                 _dp, _dp, _dp, _dp, _dp]
+                                 _dp, _dp, _dp, _dp, _dp, _dp]
+        L.orc_elastic_stress.restype = None
+        L.orc_elastic_stress.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_double, ctypes.c_double,
+                                         _dp, _dp]
         L.orc_momentum_paper.restype = None
         L.orc_momentum_paper.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_int64, _dp, _dp, _lp,
                                          _ip, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
-                                         _dp, _dp, _dp, _dp]
+                                         _dp, _dp, _dp, _dp, _dp]
         L.orc_momentum_conservative.restype = None
         L.orc_momentum_conservative.argtypes = [ctypes.POINTER(OrcParams), ctypes.c_int64, _dp,
                                                 _dp, _lp, _ip, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
-                                                _dp]
+                                                _dp, _dp]
         L.orc_apd.restype = None
         L.orc_apd.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_double, ctypes.c_double,
                               ctypes.c_double, _lp, _ip, _dp, _dp, _dp, _dp]
@@ -152,7 +156,8 @@ def make_params(**kw) -> OrcParams:
     return OrcParams(p["L"], p["h"], p["dt"], p["rho0"], p["eta"], p["Gamma"], p["lam"], p["A"],
                      p["B"], p["C"], p["K"], p["zeta"], p["gamma_eos"], p["beta"], p["c0_min"],
                      p["c_shift"], int(p["apd"]), int(p["conservative"]),
-                     int(p["q_new_in_momentum"]), NBR_MODES[mode] if isinstance(mode, str) else int(mode))
+                     int(p["q_new_in_momentum"]), NBR_MODES[mode] if isinstance(mode, str) else int(mode),
+                     int(p["elastic"]))
 
 
 def num_threads() -> int:
@@ -285,32 +290,46 @@ def continuity(nb: Nbrs, V, B, ux, uy, rho):
     return out
 
 
-def q_rate(params: OrcParams, q11, q12, D, lapQ):
-    """Eq. (24) for one particle: (m11, m12, trace of the unprojected m)."""
+def q_rate(params: OrcParams, q11, q12, D, lapQ, with_H=False):
+    """Eq. (24) for one particle: (m11, m12, trace of the unprojected m[, H as 2x2])."""
     D, Dp = _d(np.asarray(D, dtype=np.float64).reshape(4))
     lQ, lQp = _d(np.asarray(lapQ, dtype=np.float64).reshape(4))
     m11 = ctypes.c_double()
     m12 = ctypes.c_double()
     tr = ctypes.c_double()
+    H, Hp = _wd(4)
     lib().orc_q_rate(ctypes.byref(params), float(q11), float(q12), Dp, lQp, ctypes.byref(m11),
-                     ctypes.byref(m12), ctypes.byref(tr))
+                     ctypes.byref(m12), ctypes.byref(tr), Hp)
+    if with_H:
+        return m11.value, m12.value, tr.value, H.reshape(2, 2)
     return m11.value, m12.value, tr.value
 
 
-def momentum_paper(params: OrcParams, nb: Nbrs, V, B, rho, p, ux, uy, q11, q12):
-    """Eq. (23) with the active term scaled by -zeta/rho: (ax, ay, divQx, divQy)."""
+def elastic_stress(params: OrcParams, q11, q12, H):
+    """Eq. (12) without -p I, for one particle: Pi_el as 2x2."""
+    H, Hp = _d(np.asarray(H, dtype=np.float64).reshape(4))
+    out, op = _wd(4)
+    lib().orc_elastic_stress(ctypes.byref(params), float(q11), float(q12), Hp, op)
+    return out.reshape(2, 2)
+
+
+def momentum_paper(params: OrcParams, nb: Nbrs, V, B, rho, p, ux, uy, q11, q12, pel=None):
+    """Eq. (23) with the active term scaled by -zeta/rho: (ax, ay, divQx, divQy).  ``pel``: the
+    elastic stress per particle as (n, 3) = (11, 12, 22), used when params.elastic is set."""
     arrs = [_d(a) for a in (V, B[0], B[1], B[2], rho, p, ux, uy, q11, q12)]
     outs = [_wd(nb.n) for _ in range(4)]
+    pe = _d(np.zeros(3 * nb.n) if pel is None else np.asarray(pel, dtype=np.float64).reshape(-1))
     lib().orc_momentum_paper(ctypes.byref(params), nb.n, nb.xp, nb.yp, nb.rp, nb.cp,
-                             *[a[1] for a in arrs], *[o[1] for o in outs])
+                             *[a[1] for a in arrs], *[o[1] for o in outs], pe[1])
     return tuple(o[0] for o in outs)
 
 
-def momentum_conservative(params: OrcParams, nb: Nbrs, rho, p, ux, uy, q11, q12):
+def momentum_conservative(params: OrcParams, nb: Nbrs, rho, p, ux, uy, q11, q12, pel=None):
     arrs = [_d(a) for a in (rho, p, ux, uy, q11, q12)]
     outs = [_wd(nb.n) for _ in range(2)]
+    pe = _d(np.zeros(3 * nb.n) if pel is None else np.asarray(pel, dtype=np.float64).reshape(-1))
     lib().orc_momentum_conservative(ctypes.byref(params), nb.n, nb.xp, nb.yp, nb.rp, nb.cp,
-                                    *[a[1] for a in arrs], *[o[1] for o in outs])
+                                    *[a[1] for a in arrs], *[o[1] for o in outs], pe[1])
     return tuple(o[0] for o in outs)
 
 

@@ -38,7 +38,10 @@
  *   - momentum uses Q^{n+1} (text order of §3.1) unless q_new_in_momentum = 0;
  *   - corrector u^{n+1} = u^{n+1/2} + dt/2 a^{n+1/2}; rho^{n+1} = rho_hat + dt/2 k^{n+1/2};
  *   - c0 = max(10 max|u^{n+1/2}|, c0_min);
- *   - APD uses the midpoint pair data and u^{n+1/2}; r0 averages over the N_i neighbours.
+ *   - APD uses the midpoint pair data and u^{n+1/2}; r0 averages over the N_i neighbours;
+ *   - elastic stress (Eq. 12, off by default as in the paper): Pi_el = 2 lambda M (Q:H)
+ *     - lambda (H M + M H), M = Q + c I, from Q^n and the H of the Q rate; it enters the momentum
+ *     through the corrected divergence (paper mode) or the pair-antisymmetric form.
  */
 #include <math.h>
 #include <stdint.h>
@@ -76,6 +79,7 @@ typedef struct {
     int32_t conservative;      /* 1: pair-antisymmetric momentum with fixed masses */
     int32_t q_new_in_momentum; /* 1: Q^{n+1} in the active force, 0: Q^n */
     int32_t nbr_mode;          /* 0 brute force, 1 ghost layer, 2 cell grid */
+    int32_t elastic;           /* 1: add the elastic stress of Eq. (12) */
 } orc_params;
 
 /* Intermediates of the last step (each pointer may be NULL). */
@@ -502,7 +506,7 @@ static void mat_mul(const double A[2][2], const double B[2][2], double Cm[2][2])
  *   lapQ  : corrected Laplacian of each entry of Q (Eq. 21)
  * Writes the projected rate (m11, m12) and the trace of the unprojected m. */
 void orc_q_rate(const orc_params *P, double q11, double q12, const double D[2][2],
-                const double lapQ[2][2], double *m11, double *m12, double *trace_m)
+                const double lapQ[2][2], double *m11, double *m12, double *trace_m, double Hout[2][2])
 {
     double Q[2][2], I[2][2] = {{1.0, 0.0}, {0.0, 1.0}};
     q_tensor(q11, q12, Q);
@@ -537,6 +541,9 @@ void orc_q_rate(const orc_params *P, double q11, double q12, const double D[2][2
             H[a][b] = -P->A * Q[a][b] + P->B * (Q2[a][b] - I[a][b] / 3.0 * trQ2)
                       - P->C * Q[a][b] * trQ2 + P->K * lapQ[a][b];
 
+    if (Hout)
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2; b++) Hout[a][b] = H[a][b];
     double m[2][2];
     for (int a = 0; a < 2; a++)
         for (int b = 0; b < 2; b++) m[a][b] = S[a][b] + P->Gamma * H[a][b];
@@ -548,6 +555,25 @@ void orc_q_rate(const orc_params *P, double q11, double q12, const double D[2][2
         for (int b = 0; b < 2; b++) ms[a][b] = 0.5 * (m[a][b] + m[b][a]) - 0.5 * tr * I[a][b];
     *m11 = ms[0][0];
     *m12 = ms[0][1];
+}
+
+/* Eq. (12) without its -p I (the pressure enters separately):
+ * Pi_el = 2 lambda M (Q:H) - lambda H M - lambda M H with M = Q + c I. */
+void orc_elastic_stress(const orc_params *P, double q11, double q12, const double H[2][2],
+                        double Pi[2][2])
+{
+    double Q[2][2], M[2][2], HM[2][2], MH[2][2];
+    q_tensor(q11, q12, Q);
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++) M[a][b] = Q[a][b] + (a == b ? P->c_shift : 0.0);
+    double QH = 0.0;
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++) QH += Q[a][b] * H[a][b];
+    mat_mul(H, M, HM);
+    mat_mul(M, H, MH);
+    for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++)
+            Pi[a][b] = 2.0 * P->lambda * M[a][b] * QH - P->lambda * HM[a][b] - P->lambda * MH[a][b];
 }
 
 /* The active-force sum of Eq. (23): sum_j V_j (Q_j - Q_i) (B_i grad_i W_ij), a vector. */
@@ -575,7 +601,7 @@ void orc_momentum_paper(const orc_params *P, int64_t n, const double *x, const d
                         const double *B11, const double *B12, const double *B22,
                         const double *rho, const double *p, const double *ux, const double *uy,
                         const double *q11, const double *q12,
-                        double *ax, double *ay, double *divQx, double *divQy)
+                        double *ax, double *ay, double *divQx, double *divQy, const double *pel)
 {
     double L = P->L, h = P->h, nu = P->eta / P->rho0;
     #pragma omp parallel for schedule(static)
@@ -596,9 +622,22 @@ void orc_momentum_paper(const orc_params *P, int64_t n, const double *x, const d
         }
         double dq[2];
         active_sum(i, x, y, L, h, rowptr, cols, V, B, q11, q12, dq);
+        double del[2] = {0.0, 0.0};   /* sum_j V_j (Pi_j - Pi_i) . (B_i grad_i W_ij): div Pi_el */
+        if (P->elastic && pel) {
+            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+                int64_t j = cols[e];
+                pair_t pr = pair_of(x, y, i, j, L, h);
+                double Bg[2] = {B[0][0] * pr.gx + B[0][1] * pr.gy, B[1][0] * pr.gx + B[1][1] * pr.gy};
+                double Pj[2][2] = {{pel[3 * j], pel[3 * j + 1]}, {pel[3 * j + 1], pel[3 * j + 2]}};
+                double Pi[2][2] = {{pel[3 * i], pel[3 * i + 1]}, {pel[3 * i + 1], pel[3 * i + 2]}};
+                for (int a = 0; a < 2; a++)
+                    del[a] += V[j] * ((Pj[a][0] - Pi[a][0]) * Bg[0] + (Pj[a][1] - Pi[a][1]) * Bg[1]);
+            }
+        }
         double a_[2];
         for (int a = 0; a < 2; a++)
-            a_[a] = -rho[i] * fp[a] + 8.0 * nu * P->rho0 / rho[i] * fv[a] - P->zeta / rho[i] * dq[a];
+            a_[a] = -rho[i] * fp[a] + 8.0 * nu * P->rho0 / rho[i] * fv[a] - P->zeta / rho[i] * dq[a]
+                    + del[a] / rho[i];
         ax[i] = a_[0];
         ay[i] = a_[1];
         if (divQx) divQx[i] = dq[0];
@@ -614,7 +653,8 @@ void orc_momentum_paper(const orc_params *P, int64_t n, const double *x, const d
 void orc_momentum_conservative(const orc_params *P, int64_t n, const double *x, const double *y,
                                const int64_t *rowptr, const int32_t *cols, const double *rho,
                                const double *p, const double *ux, const double *uy,
-                               const double *q11, const double *q12, double *ax, double *ay)
+                               const double *q11, const double *q12, double *ax, double *ay,
+                               const double *pel)
 {
     double L = P->L, h = P->h, mass = P->rho0 * P->L * P->L / (double)n, mu = P->eta;
     #pragma omp parallel for schedule(static)
@@ -635,8 +675,15 @@ void orc_momentum_conservative(const orc_params *P, int64_t n, const double *x, 
                 double act = 0.0;
                 for (int b = 0; b < 2; b++)
                     act += (Qi[a][b] / (rho[i] * rho[i]) + Qj[a][b] / (rho[j] * rho[j])) * g[b];
+                double el = 0.0;   /* + sum_j m (Pi_i/rho_i^2 + Pi_j/rho_j^2) . grad_i W */
+                if (P->elastic && pel) {
+                    double Pi_[2][2] = {{pel[3 * i], pel[3 * i + 1]}, {pel[3 * i + 1], pel[3 * i + 2]}};
+                    double Pj_[2][2] = {{pel[3 * j], pel[3 * j + 1]}, {pel[3 * j + 1], pel[3 * j + 2]}};
+                    for (int b = 0; b < 2; b++)
+                        el += (Pi_[a][b] / (rho[i] * rho[i]) + Pj_[a][b] / (rho[j] * rho[j])) * g[b];
+                }
                 a_[a] += -mass * cp * g[a] + mass * 8.0 * mu / (rho[i] * rho[j]) * uijd / r2 * g[a]
-                         - P->zeta * mass * act;
+                         - P->zeta * mass * act + mass * el;
             }
         }
         ax[i] = a_[0];
@@ -695,12 +742,13 @@ int orc_step(const orc_params *P, int64_t n, double *x, double *y, double *ux, d
            *p = xalloc(nd), *gux = xalloc(2 * nd), *guy = xalloc(2 * nd), *lap = xalloc(4 * nd),
            *qn11 = xalloc(nd), *qn12 = xalloc(nd), *an_x = xalloc(nd), *an_y = xalloc(nd),
            *divx = xalloc(nd), *divy = xalloc(nd), *apx = xalloc(nd), *apy = xalloc(nd),
-           *trm = xalloc(nd), *f = xalloc(nd);
+           *trm = xalloc(nd), *f = xalloc(nd), *pel = xalloc(3 * nd);
     int64_t *rowptr = (int64_t *)xalloc(sizeof(int64_t) * (size_t)(n + 1));
     int32_t *cols = NULL;
     int rc = 0;
     if (!sumW || !V || !B11 || !B12 || !B22 || !k || !rh || !rhat || !p || !gux || !guy || !lap ||
-        !qn11 || !qn12 || !an_x || !an_y || !divx || !divy || !apx || !apy || !trm || !f || !rowptr) {
+        !qn11 || !qn12 || !an_x || !an_y || !divx || !divy || !apx || !apy || !trm || !f || !pel ||
+        !rowptr) {
         rc = -1;
         goto done;
     }
@@ -748,17 +796,21 @@ int orc_step(const orc_params *P, int64_t n, double *x, double *y, double *ux, d
         for (int64_t i = 0; i < n; i++) {
             double D[2][2] = {{gux[2 * i], gux[2 * i + 1]}, {guy[2 * i], guy[2 * i + 1]}};
             double lQ[2][2] = {{lap[i], lap[n + i]}, {lap[2 * n + i], lap[3 * n + i]}};
-            double m11, m12;
-            orc_q_rate(P, q11[i], q12[i], D, lQ, &m11, &m12, &trm[i]);
+            double m11, m12, H[2][2], Pe[2][2];
+            orc_q_rate(P, q11[i], q12[i], D, lQ, &m11, &m12, &trm[i], H);
             qn11[i] = q11[i] + dt * m11;
             qn12[i] = q12[i] + dt * m12;
+            orc_elastic_stress(P, q11[i], q12[i], H, Pe);
+            pel[3 * i] = Pe[0][0];
+            pel[3 * i + 1] = Pe[0][1];
+            pel[3 * i + 2] = Pe[1][1];
         }
 
         /* momentum at the midpoint */
         const double *qa = P->q_new_in_momentum ? qn11 : q11;
         const double *qb = P->q_new_in_momentum ? qn12 : q12;
         if (P->conservative) {
-            orc_momentum_conservative(P, n, x, y, rowptr, cols, rhat, p, ux, uy, qa, qb, an_x, an_y);
+            orc_momentum_conservative(P, n, x, y, rowptr, cols, rhat, p, ux, uy, qa, qb, an_x, an_y, pel);
             for (int64_t i = 0; i < n; i++) {
                 double B[2][2] = {{B11[i], B12[i]}, {B12[i], B22[i]}}, dq[2];
                 active_sum(i, x, y, L, h, rowptr, cols, V, B, qa, qb, dq);
@@ -767,7 +819,7 @@ int orc_step(const orc_params *P, int64_t n, double *x, double *y, double *ux, d
             }
         } else {
             orc_momentum_paper(P, n, x, y, rowptr, cols, V, B11, B12, B22, rhat, p, ux, uy, qa, qb,
-                               an_x, an_y, divx, divy);
+                               an_x, an_y, divx, divy, pel);
         }
 
         /* artificial particle displacement from the midpoint configuration */
@@ -824,7 +876,7 @@ int orc_step(const orc_params *P, int64_t n, double *x, double *y, double *ux, d
 done:
     free(sumW); free(V); free(B11); free(B12); free(B22); free(k); free(rh); free(rhat); free(p);
     free(gux); free(guy); free(lap); free(qn11); free(qn12); free(an_x); free(an_y);
-    free(divx); free(divy); free(apx); free(apy); free(trm); free(f); free(rowptr); free(cols);
+    free(divx); free(divy); free(apx); free(apy); free(trm); free(f); free(pel); free(rowptr); free(cols);
     return rc;
 }
 
