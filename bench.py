@@ -38,22 +38,34 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 KERNEL_SRC = os.path.join(ROOT, "paper_2108_08919_gb300", "csrc", "ann_kernels.cu")
 
 # FP32 flops per directed neighbour pair of each pass (FMA = 2), counted from the formulas:
-#   pair geometry and kernel value/derivative (d, |d|^2, 1/r, b, quintic pieces)   ~32
-#   pass A: geometry + W (24) + the cell-stencil candidate tests (5 flops x ~3.1 candidates/pair)
+#   pair geometry and kernel value/derivative (d, |d|^2, 1/r, b, quintic pieces)   ~24
+#   pass_a (candidate filter): geometry + W + the support test (3)                          = 27
+#   pass_a_resort: geometry + W + the cell-stencil candidate tests (5 x ~3.1 per pair)      = 39.5
 #   pass B: + alpha (6), velocity-gradient sums (10), Q-Laplacian sums (16), V F d (4)    = 70
 #   pass C: + Shepard sum (3), div Q sums (13)                                            = 48
 #   pass D: + pressure (7), viscous (12), APD sums (11)                                    = 62
-FLOPS_PER_PAIR = {"pass_a": 24 + 15.5, "pass_b": 70.0, "pass_c": 48.0, "pass_d": 62.0}
-# Compulsory DRAM bytes per particle of each kernel: every array it must read or write, once
-# (positions as the split float4, neighbour lists at 2 B per neighbour, 44 neighbours):
-#   predict     r, u, a in; r, u, key, rank, split position out                          80
-#   cell_order  permutation, state and split position in; the sorted copy out             116
-#   pass_a      split position in; sum W, V, count, lists out                             116
-#   pass_b      position, V, u, Q, delta, count, lists in; Q^{n+1}, B, k, delta_half out   160
-#   pass_c      position, V, delta_half, Q^{n+1}, count, sum W, B, lists in; 4 fields out  156
-#   pass_d      everything the momentum, corrector and APD read; the new state out        224
-BYTES_PER_PARTICLE = {"predict": 80, "cell_scan": 0.5, "cell_scatter": 16, "cell_order": 116,
-                      "pass_a": 116, "pass_b": 160, "pass_c": 156, "pass_d": 224}
+FLOPS_PER_PAIR = {"pass_a": 27.0, "pass_a_resort": 24 + 15.5, "pass_b": 70.0, "pass_c": 48.0,
+                  "pass_d": 62.0}
+# Compulsory DRAM bytes per particle of each kernel: every array it must read or write, once.
+# Candidate lists: 2 B per candidate, ~46 candidates (44 neighbours and the skin), + the count = 96.
+#   predict       u, a, r, Q, delta, id, cell key, reference split in (68); u, r, and the
+#                 evaluation copy (r, split r, u, Q, delta, id) out (80)                    148
+#   cell_order    permutation, state and split position in; the sorted copy out             116
+#   pass_a_resort split position in; candidate lists, count, mask, sum W, V, reference out  148
+#   pass_a        split position, candidate lists in; count, mask, sum W, V out             132
+#   pass_b        split position, V, u, Q, delta, lists in; Q^{n+1}, B, k, delta_half out   164
+#   pass_c        split position, V, delta_half, Q^{n+1}, sum W, B, lists in; 4 fields out 160
+#   pass_d        everything the momentum, corrector and APD read; the new state out        228
+BYTES_PER_PARTICLE = {"predict": 148, "cell_scan": 0.5, "cell_scatter": 16, "cell_order": 116,
+                      "pass_a_resort": 148, "pass_a": 132, "pass_b": 164, "pass_c": 160,
+                      "pass_d": 228}
+RESORT_BRANCH = ("cell_keys", "cell_scan", "cell_scatter", "cell_order", "pass_a_resort")
+
+
+def launches_in_steps(steps: int, resorts: int) -> int:
+    """Kernels the step graph launches: the predictor, the branch condition, then either the five
+    re-sort kernels or the candidate filter, then passes B, C and D."""
+    return 6 * steps + 4 * resorts
 
 
 def _rank_info():
@@ -277,6 +289,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    resorts0 = B.ann_get_diagnostics(ctx)["resorts"]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         with torch.cuda.stream(stream):
@@ -288,13 +301,21 @@ def run_ours(args):
         dist.barrier()
     ms_max = slowest(e0.elapsed_time(e1), dist, "cuda")
     diag = B.ann_get_diagnostics(ctx)
+    resorts_timed = diag["resorts"] - resorts0
     pairs_per_step = diag["nbr_mean"] * n
     value = job_throughput(ws, n, args.steps, ms_max * 1e-3)
 
     # per-kernel device times (CUDA events around each kernel launch, same stream, same state)
+    # (the re-sort branch runs in some steps, pass_a in the others: kernel_ms is the per-step
+    # average, avg_launch_ms the average over the launches that ran)
+    rp0 = B.ann_get_diagnostics(ctx)["resorts"]
     kprof = B.ann_step_profile(ctx, args.profile_steps)
+    rp = B.ann_get_diagnostics(ctx)["resorts"] - rp0
     kms = {k: v / args.profile_steps for k, v in kprof.items()}
+    klaunch = {k: (rp if k in RESORT_BRANCH else args.profile_steps - rp if k == "pass_a"
+                   else args.profile_steps) for k in kprof}
     dom = max(kms, key=kms.get)
+    dom_launch_ms = kprof[dom] / max(klaunch[dom], 1)
 
     # end to end through the C-ABI with host buffers: pinned inputs -> set_particles -> step ->
     # state fields back to pinned host arrays, every step
@@ -334,7 +355,7 @@ def run_ours(args):
     clocks = clk.summary()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     flops_launch = FLOPS_PER_PAIR.get(dom, 0.0) * pairs_per_step
-    achieved_tf = flops_launch / (kms[dom] * 1e-3) / 1e12 if kms[dom] > 0 else 0.0
+    achieved_tf = flops_launch / (dom_launch_ms * 1e-3) / 1e12 if dom_launch_ms > 0 else 0.0
     peak_tf = fp32_peak_tflops(sm_mhz)
     traffic, _ = _traffic_for(dom)
     bytes_launch = BYTES_PER_PARTICLE.get(dom, 0) * n
@@ -350,15 +371,17 @@ def run_ours(args):
                      "traffic": traffic,
                      "peak_source": f"FP32 152 SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz "
                                     f"(sm_max_mhz of MEASURED_PEAKS.json, {src})",
-                     "flops_per_launch": flops_launch, "avg_launch_ms": kms[dom],
-                     "hbm_achieved_gbs": bytes_launch / (kms[dom] * 1e-3) / 1e9,
+                     "flops_per_launch": flops_launch, "avg_launch_ms": dom_launch_ms,
+                     "hbm_achieved_gbs": bytes_launch / (dom_launch_ms * 1e-3) / 1e9,
                      "hbm_peak_gbs": peaks.get("hbm_gbs"),
-                     "hbm_frac": bytes_launch / (kms[dom] * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)},
+                     "hbm_frac": bytes_launch / (dom_launch_ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)},
         "kernel_ms": kms,
+        "kernel_launches": klaunch,
         "kernel_share": {k: v / sum(kms.values()) for k, v in kms.items()},
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
-        "gpu_launches": args.steps * B.ann_kernel_count(),
+        "gpu_launches": launches_in_steps(args.steps, resorts_timed),
+        "resorts": resorts_timed,
         "clocks": clocks,
         "diag": {"nbr_mean": diag["nbr_mean"], "error_bits": diag["error_bits"],
                  "band_checks": diag["band_checks"], "max_speed": diag["max_speed"]},

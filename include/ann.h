@@ -78,6 +78,10 @@ extern "C" {
  * c_shift: c in Q + c I of the co-rotation term (Eq. 2 prints 1/3).
  * q_new_in_momentum: 1 uses Q^{n+1} in the active force (text order of §3.1), 0 uses Q^n.
  * apd: 1 applies the artificial particle displacement of Eq. 29.
+ * elastic_stress: 1 adds the elastic stress of Eq. 12 (without its -p I),
+ *   Pi_el = 2 lambda M (Q:H) - lambda (H M + M H), M = Q + c_shift I, to the momentum through the
+ *   corrected divergence (paper mode) or the pair-antisymmetric form (conservative mode).  The
+ *   paper neglects it (text under Eq. 13); default 0.
  * Valid ranges (ann_validate_params): n >= 1, L > 0, 0 < h, 3h <= L/3 (at least three cells across
  * the box), dt > 0, rho0 > 0, eta >= 0, Gamma >= 0, gamma_eos > 0, 0 <= beta <= 1, c0_min >= 0, and
  * at most ANN_MAX_NEIGHBORS expected neighbours (pi (3h)^2 n / L^2 <= 0.85 ANN_MAX_NEIGHBORS).
@@ -91,7 +95,8 @@ typedef struct ann_params {
     int32_t momentum_mode;
     int32_t q_new_in_momentum;
     int32_t dt_mode;
-    int32_t reserved[4];
+    int32_t elastic_stress;
+    int32_t reserved[3];
 } ann_params;
 
 /* Cell grid and step size a parameter set implies (host computation, no GPU needed). */
@@ -193,7 +198,10 @@ int ann_step(ann_ctx *ctx, int64_t nsteps);
 
 /* Advance nsteps steps launching the kernels one by one with a CUDA event before and after each,
  * and add the total device time of each kernel (ms) to kernel_ms[ann_kernel_count()] (the caller
- * zeroes it).  Same physics and errors as ann_step. */
+ * zeroes it).  A step runs either the re-sort branch (kernels 1..5: cell_keys, cell_scan,
+ * cell_scatter, cell_order, pass_a_resort) or kernel 6 (pass_a, the candidate-list filter), as the
+ * step graph would; a kernel adds time only in the steps where it ran, and the step count of each
+ * branch follows from the change of ann_diag.resorts.  Same physics and errors as ann_step. */
 int ann_step_profile(ann_ctx *ctx, int64_t nsteps, double *kernel_ms);
 
 /* Number of kernels in one step, and the name of kernel k (static storage; NULL if out of range). */

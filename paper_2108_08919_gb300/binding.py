@@ -38,7 +38,8 @@ class ann_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64)] + [(k, ctypes.c_double) for k in (
         "L", "h", "dt", "rho0", "eta", "Gamma", "lambda_", "A", "B", "C", "K", "zeta", "gamma_eos",
         "beta", "c0_min", "c_shift")] + [(k, ctypes.c_int32) for k in (
-        "apd", "momentum_mode", "q_new_in_momentum", "dt_mode")] + [("reserved", ctypes.c_int32 * 4)]
+        "apd", "momentum_mode", "q_new_in_momentum", "dt_mode", "elastic_stress")] + [
+        ("reserved", ctypes.c_int32 * 3)]
 
 
 class ann_grid(ctypes.Structure):
@@ -148,8 +149,12 @@ def ann_status_string(status: int) -> str:
 def ann_default_params(**overrides) -> ann_params:
     p = ann_params()
     _check(lib().ann_default_params(ctypes.byref(p)), what="ann_default_params")
+    names = {f[0] for f in ann_params._fields_}
     for k, v in overrides.items():
-        setattr(p, "lambda_" if k == "lambda" else k, v)
+        k = "lambda_" if k == "lambda" else k
+        if k not in names or k == "reserved":
+            raise TypeError(f"ann_params has no field {k!r}")
+        setattr(p, k, v)
     return p
 
 

@@ -96,7 +96,8 @@ int64_t device_bytes(const ann_params &p)
                   + 4 + 8                     // neighbour counts, neighbour masks
                   + (MAXV / 2) * 4 + 4 + 16 + 4   // candidate lists, counts, split at re-sort, cell
                   + 11 * 4                    // intermediates
-                  + 8 * 4;                    // recording
+                  + 8 * 4                     // recording
+                  + 16 + 8;                   // elastic stress and its divergence
     int64_t tmp = std::max<int64_t>(7 * 8, MAXN * 4) * n;
     return per * n + tmp + 2 * 4 * (ncell + 1) + 4096;
 }
@@ -125,6 +126,7 @@ int validate(const ann_params *p, std::string &why)
     }
     if (p->q_new_in_momentum != 0 && p->q_new_in_momentum != 1) { why = "q_new_in_momentum must be 0 or 1"; return ANN_ERR_INVALID_ARG; }
     if (p->dt_mode != ANN_DT_FIXED && p->dt_mode != ANN_DT_STABLE) { why = "unknown dt_mode"; return ANN_ERR_INVALID_ARG; }
+    if (p->elastic_stress != 0 && p->elastic_stress != 1) { why = "elastic_stress must be 0 or 1"; return ANN_ERR_INVALID_ARG; }
     double R = 3.0 * p->h;
     double expected = M_PI * R * R * (double)p->n / (p->L * p->L);
     if (expected > 0.85 * MAXN) { why = "too many expected neighbours for the list capacity"; return ANN_ERR_INVALID_ARG; }
@@ -149,6 +151,7 @@ DevParams make_dev(const ann_params &p)
     d.conservative = p.momentum_mode == ANN_MOMENTUM_CONSERVATIVE;
     d.qnew = p.q_new_in_momentum;
     d.record = 0;
+    d.elastic = p.elastic_stress;
     d.L = p.L;
     d.cell = p.L / d.nc;
     d.inv_cell = (double)d.nc / p.L;
@@ -204,6 +207,7 @@ DevParams make_dev(const ann_params &p)
     d.Gamma = (float)p.Gamma;
     d.lambda = (float)p.lambda;
     d.A = (float)p.A;
+    d.Bl = (float)p.B;
     d.C = (float)p.C;
     d.K = (float)p.K;
     d.zeta = (float)p.zeta;
@@ -241,6 +245,7 @@ cudaError_t alloc_all(ann_ctx *c)
     A_(sumW, n); A_(V, n); A_(B11, n); A_(B12, n); A_(B22, n); A_(kr, n); A_(dh, n); A_(dhat, n);
     A_(p, n); A_(divx, n); A_(divy, n);
     A_(rec_gu, 4 * n); A_(rec_lap, 2 * n); A_(rec_apd, 2 * n);
+    A_(pel, n); A_(delx, n); A_(dely, n);
     A_(err, 1); A_(maxu, 1); A_(band, 1);
 #undef A_
     double *origin = nullptr;
@@ -575,6 +580,7 @@ int ann_step_profile(ann_ctx *c, int64_t nsteps, double *kernel_ms)
     // decision, E[k + 2] after kernel k >= 1 (or where it would have run).
     const size_t per = NKERNELS + 2;
     std::vector<cudaEvent_t> ev(per * (size_t)nsteps);
+    std::vector<char> resorted((size_t)nsteps, 0);
     cudaError_t e = cudaSuccess;
     size_t made = 0;
     for (; made < ev.size() && !e; made++) e = cudaEventCreate(&ev[made]);
@@ -586,6 +592,7 @@ int ann_step_profile(ann_ctx *c, int64_t nsteps, double *kernel_ms)
         if (!e) e = cudaMemcpyAsync(c->h_err, c->b.rebuild, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
         if (!e) e = cudaStreamSynchronize(c->stream);
         bool rs = !e && *c->h_err != 0u;
+        resorted[(size_t)s] = rs;
         if (!e) e = cudaEventRecord(E[2], c->stream);
         for (int k = 1; k < NKERNELS && !e; k++) {
             bool run = (k <= 5) ? rs : (k == 6 ? !rs : true);
@@ -596,7 +603,10 @@ int ann_step_profile(ann_ctx *c, int64_t nsteps, double *kernel_ms)
     if (!e) e = cudaStreamSynchronize(c->stream);
     for (int64_t s = 0; s < nsteps && !e; s++) {
         cudaEvent_t *E = &ev[(size_t)s * per];
+        bool rs = resorted[(size_t)s];
         for (int k = 0; k < NKERNELS && !e; k++) {
+            bool ran = (k >= 1 && k <= 5) ? rs : (k == 6 ? !rs : true);
+            if (!ran) continue;   // a skipped branch adds nothing (only the events' own gap)
             float ms = 0.f;
             e = (k == 0) ? cudaEventElapsedTime(&ms, E[0], E[1]) : cudaEventElapsedTime(&ms, E[k + 1], E[k + 2]);
             kernel_ms[k] += ms;

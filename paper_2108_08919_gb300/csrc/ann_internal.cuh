@@ -34,7 +34,7 @@ enum : uint32_t {
 // Parameters in the form the kernels use (FP64 where positions are involved).
 struct DevParams {
     int n, nc, ncell, tiles;
-    int apd, conservative, qnew, record;
+    int apd, conservative, qnew, record, elastic;
     double L, cell, inv_cell, R2, dt_d, half_dt_d;
     double q;              // power-of-two grid of the "hi" coordinate part: cell / q in [2^12, 2^13)
     long long bitsL;       // bit pattern of L: for x >= +0, x < L iff bits(x) < bits(L)
@@ -48,7 +48,7 @@ struct DevParams {
     float kw6, kw15;       // -6 a_d, 15 a_d           (W = a_d t3^5 + kw6 t2^5 + kw15 t1^5)
     float kf5, kf30, kf75; // -5 a_d/h, 30 a_d/h, -75 a_d/h  (F r = kf5 t3^4 + kf30 t2^4 + kf75 t1^4)
     int nsblk;             // blocks of SCAN_CHUNK cells (scan)
-    float rho0, nu, mu, Gamma, lambda, A, C, K, zeta, gamma_eos, beta, c0_min, c_shift, mass;
+    float rho0, nu, mu, Gamma, lambda, A, Bl, C, K, zeta, gamma_eos, beta, c0_min, c_shift, mass;
 };
 
 // Device buffers.  S: state at the end of a step, in the particle order of that step's evaluation.
@@ -74,6 +74,8 @@ struct Bufs {
     uint32_t *resorts;  // number of re-sort steps since the particles were loaded
     float *sumW, *V, *B11, *B12, *B22, *kr, *dh, *dhat, *p, *divx, *divy;
     float *rec_gu, *rec_lap, *rec_apd;   // 4n, 2n, 2n (recording only)
+    float4 *pel;        // elastic stress (11, 12, 22, -) of Eq. 12 (elastic_stress only)
+    float *delx, *dely; // its corrected divergence (paper momentum only)
     uint32_t *err, *maxu;
     unsigned long long *band;
 };

@@ -708,6 +708,19 @@ __global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
                    P.Gamma * (hb * q2 + P.K * lap2);
         b.sq11[gi] = q1 + P.dt * m1;
         b.sq12[gi] = q2 + P.dt * m2;
+        if (P.elastic) {
+            // Elastic stress of Eq. (12) without -p I: with H = H_tl + h0 I (h0 from the B term),
+            // M = Q + c I and the 2D identity A B + B A = (A:B) I for symmetric traceless A, B:
+            //   Pi = 2 lambda M (Q:H) - lambda [(Q:H) I + 2c H_tl + 2 h0 Q + 2c h0 I]
+            float h1 = hb * q1 + P.K * lap1, h2 = hb * q2 + P.K * lap2;
+            float h0 = P.Bl * trQ2 * (1.f / 6.f);
+            float c = P.c_shift, QH = 2.f * (q1 * h1 + q2 * h2);
+            float iso = QH + 2.f * c * h0;
+            float p11 = 2.f * lam * (q1 + c) * QH - lam * (iso + 2.f * c * h1 + 2.f * h0 * q1);
+            float p22 = 2.f * lam * (c - q1) * QH - lam * (iso - 2.f * c * h1 - 2.f * h0 * q1);
+            float p12 = 2.f * lam * q2 * QH - lam * (2.f * c * h2 + 2.f * h0 * q2);
+            b.pel[gi] = make_float4(p11, p12, p22, 0.f);
+        }
         b.B11[gi] = B11;
         b.B12[gi] = B12;
         b.B22[gi] = B22;
@@ -734,9 +747,10 @@ __global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
 // Kernel 8: pass C -- density filter (Eq. 28), equation of state (Eq. 26), div Q^{n+1}
 // ---------------------------------------------------------------------------------------------
 
-constexpr int SMEM_C = HCAP * (16 + 16 + 4);
+// the elastic stress tile exists only in the instantiations that read it
+constexpr int smem_c(bool el) { return HCAP * (16 + 16 + (el ? 16 : 0) + 4); }
 
-template <bool QNEW>
+template <bool QNEW, bool EL>
 __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
 {
     if (stopped(b)) return;
@@ -744,7 +758,8 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
     extern __shared__ __align__(16) unsigned char dsm[];
     float4 *sp = reinterpret_cast<float4 *>(dsm);      // split position
     float4 *sb = sp + HCAP;                            // (V, drho_half, q11^{n+1}, q12^{n+1})
-    int *sg = reinterpret_cast<int *>(sb + HCAP);
+    float4 *se = sb + HCAP;                            // elastic stress (11, 12, 22, -)
+    int *sg = reinterpret_cast<int *>(se + (EL ? HCAP : 0));
     Tile T;
     if (!tile_begin(P, b, ts, T)) {
         if (threadIdx.x == 0) atomicOr(b.err, EB_HALO);
@@ -755,6 +770,7 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
         sp[t] = s.e;
         sb[t] = QNEW ? make_float4(b.V[s.g], b.dh[s.g], b.sq11[s.g], b.sq12[s.g])
                      : make_float4(b.V[s.g], b.dh[s.g], 0.f, 0.f);
+        if (EL) se[t] = b.pel[s.g];
         sg[t] = s.g;
     }
     __syncthreads();
@@ -767,11 +783,13 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
         float shep = 0.f, g1x = 0.f, g1y = 0.f, g2x = 0.f, g2y = 0.f;
         float swi = b.sumW[gi];   // loaded ahead of the neighbour loop
         float B11 = 0.f, B12 = 0.f, B22 = 0.f;
-        if (QNEW) {
+        if (QNEW || EL) {
             B11 = b.B11[gi];
             B12 = b.B12[gi];
             B22 = b.B22[gi];
         }
+        float4 ei = EL ? se[si] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float e1x = 0.f, e1y = 0.f, e2x = 0.f, e2y = 0.f, e3x = 0.f, e3y = 0.f;
         for_each_candidate(P, b, gi, [&](int j, int kc) {
             float4 bj = sb[j];
             float2 d = pair_d(pi, sp[j]);
@@ -779,14 +797,26 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
             float Wv, F, rinv;
             kernel_wf<true>(r2, P, Wv, F, rinv);
             shep += (bi.y - bj.y) * Wv;
-            if (QNEW) {
+            if (QNEW || EL) {
                 float g = bj.x * F;
                 float gx = g * d.x, gy = g * d.y;
-                float dq1 = bj.z - bi.z, dq2 = bj.w - bi.w;
-                g1x += dq1 * gx;
-                g1y += dq1 * gy;
-                g2x += dq2 * gx;
-                g2y += dq2 * gy;
+                if (QNEW) {
+                    float dq1 = bj.z - bi.z, dq2 = bj.w - bi.w;
+                    g1x += dq1 * gx;
+                    g1y += dq1 * gy;
+                    g2x += dq2 * gx;
+                    g2y += dq2 * gy;
+                }
+                if (EL) {
+                    float4 ej = se[j];
+                    float d1 = ej.x - ei.x, d2 = ej.y - ei.y, d3 = ej.z - ei.z;
+                    e1x += d1 * gx;
+                    e1y += d1 * gy;
+                    e2x += d2 * gx;
+                    e2y += d2 * gy;
+                    e3x += d3 * gx;
+                    e3y += d3 * gy;
+                }
             }
         });
         float dhat = bi.y - P.beta * shep / swi;
@@ -798,6 +828,13 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
             b.divx[gi] = q1x + q2y;
             b.divy[gi] = q2x - q1y;
         }
+        if (EL) {   // div Pi = (d_x Pi11 + d_y Pi12, d_x Pi12 + d_y Pi22), corrected gradients
+            float p11x = e1x * B11 + e1y * B12;
+            float p12x = e2x * B11 + e2y * B12, p12y = e2x * B12 + e2y * B22;
+            float p22y = e3x * B12 + e3y * B22;
+            b.delx[gi] = p11x + p12y;
+            b.dely[gi] = p12x + p22y;
+        }
     }
 }
 
@@ -805,9 +842,9 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
 // Kernel 9: pass D -- momentum (Eq. 23), corrector (§3.1), APD (Eq. 29), re-insertion (Eq. 30)
 // ---------------------------------------------------------------------------------------------
 
-constexpr int SMEM_D = HCAP * (16 + 16 + 8 + 4);
+constexpr int smem_d(bool cons_el) { return HCAP * (16 + 16 + 8 + (cons_el ? 16 : 0) + 4); }
 
-template <bool CONS>
+template <bool CONS, bool EL>
 __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
 {
     if (stopped(b)) return;
@@ -816,7 +853,8 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
     float4 *sp = reinterpret_cast<float4 *>(dsm);       // split position
     float4 *sb = sp + HCAP;                             // paper: (V, p/rho^2, ux, uy)  cons: (p/rho^2, 1/rho, ux, uy)
     float2 *sc = reinterpret_cast<float2 *>(sb + HCAP); // cons: (q11/rho^2, q12/rho^2)
-    int *sg = reinterpret_cast<int *>(sc + HCAP);
+    float4 *se = reinterpret_cast<float4 *>(sc + HCAP); // cons + elastic: Pi/rho^2 (11, 12, 22, -)
+    int *sg = reinterpret_cast<int *>(se + ((CONS && EL) ? HCAP : 0));
     Tile T;
     if (!tile_begin(P, b, ts, T)) {
         if (threadIdx.x == 0) atomicOr(b.err, EB_HALO);
@@ -833,6 +871,11 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
             float q2 = P.qnew ? b.sq12[s.g] : b.mq12[s.g];
             sb[t] = make_float4(pr, irho, b.mux[s.g], b.muy[s.g]);
             sc[t] = make_float2(q1 * irho * irho, q2 * irho * irho);
+            if (EL) {
+                float4 pe = b.pel[s.g];
+                float ir2 = irho * irho;
+                se[t] = make_float4(pe.x * ir2, pe.y * ir2, pe.z * ir2, 0.f);
+            }
         } else {
             sb[t] = make_float4(b.V[s.g], pr, b.mux[s.g], b.muy[s.g]);
         }
@@ -845,6 +888,7 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
         int gi = sg[si];
         float4 pi = sp[si], bi = sb[si];
         float2 ci = CONS ? sc[si] : make_float2(0.f, 0.f);
+        float4 eci = (CONS && EL) ? se[si] : make_float4(0.f, 0.f, 0.f, 0.f);
         float fx = 0.f, fy = 0.f, vx = 0.f, vy = 0.f;
         float sux = 0.f, suy = 0.f, sr = 0.f, sdx = 0.f, sdy = 0.f;
         int c = b.nnbr[gi];
@@ -860,6 +904,11 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
             dvy = b.divy[gi];
         }
         double mxi = b.mx[gi], myi = b.my[gi];
+        float elx = 0.f, ely = 0.f;
+        if (EL && !CONS) {
+            elx = b.delx[gi];
+            ely = b.dely[gi];
+        }
         for_each_candidate(P, b, gi, [&](int j, int kc) {
             float4 bj = sb[j];
             float2 d = pair_d(pi, sp[j]);
@@ -877,6 +926,12 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
                 float qa = ci.x + cj.x, qb = ci.y + cj.y;
                 fx += (visc - cp) * gx - P.zeta * (qa * gx + qb * gy);
                 fy += (visc - cp) * gy - P.zeta * (qb * gx - qa * gy);
+                if (EL) {   // + sum_j m (Pi_i/rho_i^2 + Pi_j/rho_j^2) . grad_i W
+                    float4 ecj = se[j];
+                    float e11 = eci.x + ecj.x, e12 = eci.y + ecj.y, e22 = eci.z + ecj.z;
+                    fx += e11 * gx + e12 * gy;
+                    fy += e12 * gx + e22 * gy;
+                }
             } else {
                 float cp = bj.x * (bi.y + bj.y) * F;
                 fx += cp * d.x;
@@ -904,8 +959,8 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
             float vbx = B11 * vx + B12 * vy, vby = B12 * vx + B22 * vy;
             float irho = 1.f / rho;
             float kv = 8.f * P.nu * P.rho0 * irho;
-            ax = -rho * pbx + kv * vbx - P.zeta * irho * dvx;
-            ay = -rho * pby + kv * vby - P.zeta * irho * dvy;
+            ax = -rho * pbx + kv * vbx - P.zeta * irho * dvx + irho * elx;
+            ay = -rho * pby + kv * vby - P.zeta * irho * dvy + irho * ely;
         }
         float unx = bi.z + P.half_dt * ax, uny = bi.w + P.half_dt * ay;
         float apx = 0.f, apy = 0.f;
@@ -1088,10 +1143,14 @@ cudaError_t prepare_kernels()
     if ((e = cudaFuncSetAttribute(k_pass_a_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_AF))) return e;
     if ((e = cudaFuncSetAttribute(k_pass_b<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_B))) return e;
     if ((e = cudaFuncSetAttribute(k_pass_b<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_B))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_c<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_C))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_c<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_C))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_d<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_D))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_d<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_D))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_c<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c(false)))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_c<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c(false)))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_c<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c(true)))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_c<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c(true)))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_d<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_d(false)))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_d<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_d(false)))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_d<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_d(false)))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_d<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_d(true)))) return e;
     return cudaSuccess;
 }
 
@@ -1111,13 +1170,19 @@ cudaError_t launch_kernel(int k, const DevParams &P, const Bufs &b, cudaStream_t
         if (P.qnew) k_pass_b<false><<<nt, PT, SMEM_B, s>>>(P, b);
         else k_pass_b<true><<<nt, PT, SMEM_B, s>>>(P, b);
         break;
-    case 8:
-        if (P.qnew) k_pass_c<true><<<nt, PT, SMEM_C, s>>>(P, b);
-        else k_pass_c<false><<<nt, PT, SMEM_C, s>>>(P, b);
+    case 8: {
+        bool el = P.elastic && !P.conservative;   // the paper momentum takes div Pi from here
+        if (P.qnew && el) k_pass_c<true, true><<<nt, PT, smem_c(true), s>>>(P, b);
+        else if (P.qnew) k_pass_c<true, false><<<nt, PT, smem_c(false), s>>>(P, b);
+        else if (el) k_pass_c<false, true><<<nt, PT, smem_c(true), s>>>(P, b);
+        else k_pass_c<false, false><<<nt, PT, smem_c(false), s>>>(P, b);
         break;
+    }
     case 9:
-        if (P.conservative) k_pass_d<true><<<nt, PT, SMEM_D, s>>>(P, b);
-        else k_pass_d<false><<<nt, PT, SMEM_D, s>>>(P, b);
+        if (P.conservative && P.elastic) k_pass_d<true, true><<<nt, PT, smem_d(true), s>>>(P, b);
+        else if (P.conservative) k_pass_d<true, false><<<nt, PT, smem_d(false), s>>>(P, b);
+        else if (P.elastic) k_pass_d<false, true><<<nt, PT, smem_d(false), s>>>(P, b);
+        else k_pass_d<false, false><<<nt, PT, smem_d(false), s>>>(P, b);
         break;
     default: return cudaErrorInvalidValue;
     }

@@ -21,7 +21,7 @@ import sph_inputs as si
 # The paper's 2D set-up for the 64 x 64 and 256 x 256 lattices (dx = 1/nx, h = 1.3 dx).
 BASE = dict(L=1.0, dt=1e-4, rho0=1.0, eta=1.0, Gamma=0.34, lam=0.7, A=0.0, B=0.0, C=1.0, K=0.04,
             zeta=0.05, gamma_eos=7.0, beta=1.0, c0_min=0.0, c_shift=1.0 / 3.0, apd=1,
-            conservative=0, q_new_in_momentum=1)
+            conservative=0, q_new_in_momentum=1, elastic=0)
 
 STATE = ("x", "y", "ux", "uy", "q11", "q12", "drho", "ax", "ay")
 GPU_NAME = {"x": "X", "y": "Y", "ux": "UX", "uy": "UY", "q11": "Q11", "q12": "Q12",
@@ -57,7 +57,7 @@ def gpu_params(B, p, n):
         lambda_=p["lam"], A=p["A"], B=p["B"], C=p["C"], K=p["K"], zeta=p["zeta"],
         gamma_eos=p["gamma_eos"], beta=p["beta"], c0_min=p["c0_min"], c_shift=p["c_shift"],
         apd=p["apd"], momentum_mode=p["conservative"], q_new_in_momentum=p["q_new_in_momentum"],
-        dt_mode=0)
+        dt_mode=0, elastic_stress=p.get("elastic", 0))
 
 
 def relerr(a, b):

@@ -218,6 +218,37 @@ def test_parity_across_resorts(B, orc):
     assert abs(int(rp[-1]) - int(rp_o[-1])) <= 2
 
 
+def test_profiled_steps_match_graph_steps(B):
+    """ann_step_profile launches the same kernels one by one: same state bit for bit, and each
+    kernel is billed only in the steps where its branch ran."""
+    ic, p = _moving_case()
+    a = GpuRun(B, p, ic)
+    b = GpuRun(B, p, ic)
+    try:
+        a.step(30)
+        prof = B.ann_step_profile(b.ctx, 30)
+        ra = B.ann_get_diagnostics(a.ctx)["resorts"]
+        rb = B.ann_get_diagnostics(b.ctx)["resorts"]
+        sa, sb = a.state(), b.state()
+    finally:
+        a.close()
+        b.close()
+    assert ra == rb and 4 <= ra < 30, (ra, rb)
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    names = [B.ann_kernel_name(k) for k in range(B.ann_kernel_count())]
+    assert set(prof) == set(names)
+    assert all(v > 0.0 for v in prof.values()), prof
+    # one step of re-sort: the resort branch's kernels must not be billed for the other steps
+    c = GpuRun(B, p, ic)
+    try:
+        prof1 = B.ann_step_profile(c.ctx, 1)   # the first step after ann_set_particles re-sorts
+        assert B.ann_get_diagnostics(c.ctx)["resorts"] == 1
+    finally:
+        c.close()
+    assert prof1["pass_a"] == 0.0 and prof1["pass_a_resort"] > 0.0, prof1
+
+
 def test_checkpoint_across_resorts(B, tmp_path):
     ic, p = _moving_case()
     a = GpuRun(B, p, ic)
