@@ -19,6 +19,8 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libann.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+# extra nvcc arguments (e.g. -DANN_MINB_D=5 to try another occupancy hint); empty by default
+FLAGS += os.environ.get("ANN_NVCC_EXTRA", "").split()
 
 
 def _nvcc() -> str:

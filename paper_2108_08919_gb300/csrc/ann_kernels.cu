@@ -37,34 +37,78 @@ __device__ __forceinline__ int wrapc(int c, int nc) { return c < 0 ? c + nc : (c
 
 __device__ __forceinline__ bool stopped(const Bufs &b) { return *(volatile uint32_t *)b.err != 0u; }
 
+// Two-lane FP32 arithmetic (one instruction issues both lanes, each lane rounded as the scalar
+// operation).  The pair passes are issue-bound, and their x/y arithmetic pairs up naturally.
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, f2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// 1/sqrt(r2) by the hardware approximation (r2 is a squared pair distance: never subnormal
+// unless two particles coincide, where both forms give +inf).
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Quintic kernel of Eq. (18) in branch-free form: with t_k = max(k - b, 0),
 //   W = a_d [t3^5 - 6 t2^5 + 15 t1^5],   F = W'(b) / (h r) = a_d/h [-5 t3^4 + 30 t2^4 - 75 t1^4] / r,
 // so that grad_i W_ij = F d_ij.  The constants a_d, -6 a_d, ... are folded on the host.  For true
 // neighbours b < 3 up to FP32 rounding, and t3 needs no clamp (a rounding-negative t3 gives
-// |t3|^4 ~ 1e-28); `clamp3` keeps it for candidates that may lie beyond the support.
+// |t3|^4 ~ 1e-28); `clamp3` keeps it for candidates that may lie beyond the support, where it
+// makes W = F = 0 exactly.  (t3, t2) travel as one two-lane value.
+struct KernelPowers {
+    float2 t, q;     // (t3, t2), (t3^4, t2^4)
+    float t1, q1;    // t1, t1^4
+    float rinv;
+};
+
+template <bool clamp3>
+__device__ __forceinline__ KernelPowers kernel_powers(float r2, const DevParams &P)
+{
+    KernelPowers k;
+    k.rinv = rsqrt_approx(r2);
+    float bq = r2 * k.rinv * P.inv_h;
+    k.t = add2(f2(3.f, 2.f), bc(-bq));
+    if (clamp3) k.t.x = fmaxf(k.t.x, 0.f);
+    k.t.y = fmaxf(k.t.y, 0.f);
+    k.t1 = fmaxf(1.f - bq, 0.f);
+    float2 sq = mul2(k.t, k.t);
+    float s1 = k.t1 * k.t1;
+    k.q = mul2(sq, sq);
+    k.q1 = s1 * s1;
+    return k;
+}
+
+__device__ __forceinline__ float kernel_w_of(const KernelPowers &k, const DevParams &P)
+{
+    float2 w = mul2(k.q, k.t);   // (t3^5, t2^5)
+    return fmaf(P.ad, w.x, fmaf(P.kw6, w.y, P.kw15 * (k.q1 * k.t1)));
+}
+
+__device__ __forceinline__ float kernel_f_of(const KernelPowers &k, const DevParams &P)
+{
+    float2 f = mul2(f2(P.kf5, P.kf30), k.q);
+    return fmaf(P.kf75, k.q1, f.x + f.y) * k.rinv;
+}
+
 template <bool clamp3>
 __device__ __forceinline__ void kernel_wf(float r2, const DevParams &P, float &W, float &F, float &rinv)
 {
-    rinv = rsqrtf(r2);
-    float bq = r2 * rinv * P.inv_h;
-    float t3 = 3.f - bq;
-    if (clamp3) t3 = fmaxf(t3, 0.f);
-    float t2 = fmaxf(2.f - bq, 0.f), t1 = fmaxf(1.f - bq, 0.f);
-    float s3 = t3 * t3, s2 = t2 * t2, s1 = t1 * t1;
-    float q3 = s3 * s3, q2 = s2 * s2, q1 = s1 * s1;
-    W = fmaf(P.ad * q3, t3, fmaf(P.kw6 * q2, t2, P.kw15 * q1 * t1));
-    F = fmaf(P.kf5, q3, fmaf(P.kf30, q2, P.kf75 * q1)) * rinv;
+    KernelPowers k = kernel_powers<clamp3>(r2, P);
+    W = kernel_w_of(k, P);
+    F = kernel_f_of(k, P);
+    rinv = k.rinv;
 }
 
 template <bool clamp3>
 __device__ __forceinline__ float kernel_w(float r2, const DevParams &P)
 {
-    float bq = r2 * rsqrtf(r2) * P.inv_h;
-    float t3 = 3.f - bq;
-    if (clamp3) t3 = fmaxf(t3, 0.f);
-    float t2 = fmaxf(2.f - bq, 0.f), t1 = fmaxf(1.f - bq, 0.f);
-    float s3 = t3 * t3, s2 = t2 * t2, s1 = t1 * t1;
-    return fmaf(P.ad * s3 * s3, t3, fmaf(P.kw6 * s2 * s2, t2, P.kw15 * s1 * s1 * t1));
+    return kernel_w_of(kernel_powers<clamp3>(r2, P), P);
 }
 
 // FP64 support test of the definition for particles gi and gj: d = minimum image of x_i - x_j
@@ -172,10 +216,23 @@ __device__ __forceinline__ SlotInfo slot_info(const DevParams &P, const Bufs &b,
     return s;
 }
 
-// Pair vector d_ij from two split tile-local positions.
+// Pair vector d_ij from two split tile-local positions: (hi_i - hi_j) + (lo_i - lo_j) per lane.
 __device__ __forceinline__ float2 pair_d(const float4 &a, const float4 &b)
 {
-    return make_float2((a.x - b.x) + (a.z - b.z), (a.y - b.y) + (a.w - b.w));
+    return add2(sub2(f2(a.x, a.y), f2(b.x, b.y)), sub2(f2(a.z, a.w), f2(b.z, b.w)));
+}
+
+// Squared length, one rounding per product as the support-test band allows.
+__device__ __forceinline__ float len2(float2 d) { return fmaf(d.x, d.x, d.y * d.y); }
+
+// Element of a staged shared-memory array at byte offset o of a 16-byte slot (candidate lists
+// store o = 16 * slot): o / (16 / sizeof(T)) for narrower element types.
+template <typename T>
+__device__ __forceinline__ const T &slot_at(const T *base, int o)
+{
+    static_assert(sizeof(T) == 16 || sizeof(T) == 8 || sizeof(T) == 4, "staged element size");
+    constexpr int sh = sizeof(T) == 16 ? 0 : (sizeof(T) == 8 ? 1 : 2);
+    return *reinterpret_cast<const T *>(reinterpret_cast<const char *>(base) + (o >> sh));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -503,9 +560,9 @@ __global__ void __launch_bounds__(PT) k_pass_a_resort(DevParams P, Bufs b)
         int cv = 0, nn = 0;
         unsigned long long mask = 0ull;
         for (int k = 0; k < cnt; k++) {
-            int j = my[k * PT];
+            int j = my[k * PT];   // slot (the coarse scan stores slots)
             float2 d = pair_d(pi, pos[j]);
-            float r2 = d.x * d.x + d.y * d.y;
+            float r2 = len2(d);
             bool cand = r2 < P.R2v;
             if (!FROM_REF && cand) {
                 sw += kernel_w<true>(r2, P);
@@ -513,7 +570,7 @@ __global__ void __launch_bounds__(PT) k_pass_a_resort(DevParams P, Bufs b)
                 nn += in;
                 mask |= (unsigned long long)in << cv;
             }
-            my[cv * PT] = (uint16_t)j;
+            my[cv * PT] = (uint16_t)(j << 4);   // byte offset of the slot
             cv += cand;
         }
         uint32_t *out = b.vnbr + gi;
@@ -534,30 +591,93 @@ __global__ void __launch_bounds__(PT) k_pass_a_resort(DevParams P, Bufs b)
     }
 }
 
-// Visit the neighbour slots of particle gi (c of them, two per list word), prefetching the next
-// word while the current pair is processed.  Slots are masked into the staging buffer.
-template <typename Fn>
+// Occupancy hints of the pair passes (minimum resident blocks of PT threads per SM; 0 leaves the
+// register budget to the compiler) and the list-word prefetch distance of each (1 to 3 words).
+// The defaults are the measured best on GB300 at 1M particles: the register caps they imply
+// (32, 48, 40, 48) raise the resident warps to what the staged shared memory allows, which hides
+// the latency of the list and gather loads better than the instruction savings of more registers.
+#ifndef ANN_MINB_A
+#define ANN_MINB_A 8
+#endif
+#ifndef ANN_MINB_B
+#define ANN_MINB_B 5
+#endif
+#ifndef ANN_MINB_C
+#define ANN_MINB_C 6
+#endif
+#ifndef ANN_MINB_D
+#define ANN_MINB_D 5
+#endif
+#ifndef ANN_PF_A
+#define ANN_PF_A 1
+#endif
+#ifndef ANN_PF_B
+#define ANN_PF_B 2
+#endif
+#ifndef ANN_PF_C
+#define ANN_PF_C 2
+#endif
+#ifndef ANN_PF_D
+#define ANN_PF_D 2
+#endif
+#define ANN_BOUNDS(minb) __launch_bounds__(PT, (minb) > 0 ? (minb) : 1)
+#if ANN_MINB_A > 0
+#define BOUNDS_A ANN_BOUNDS(ANN_MINB_A)
+#else
+#define BOUNDS_A __launch_bounds__(PT)
+#endif
+#if ANN_MINB_B > 0
+#define BOUNDS_B ANN_BOUNDS(ANN_MINB_B)
+#else
+#define BOUNDS_B __launch_bounds__(PT)
+#endif
+#if ANN_MINB_C > 0
+#define BOUNDS_C ANN_BOUNDS(ANN_MINB_C)
+#else
+#define BOUNDS_C __launch_bounds__(PT)
+#endif
+#if ANN_MINB_D > 0
+#define BOUNDS_D ANN_BOUNDS(ANN_MINB_D)
+#else
+#define BOUNDS_D __launch_bounds__(PT)
+#endif
+
+// Candidate lists hold the byte offset 16 * slot of each candidate's 16-byte staging slot, two
+// 16-bit entries per word; the mask keeps every offset inside the HCAP staged slots.
+constexpr uint32_t SLOT_OFF_MASK = (HCAP - 1) << 4;
+static_assert(((HCAP - 1) << 4) <= 0xffff, "slot offsets must fit 16 bits");
+
+// Visit the candidates of particle gi (c of them, two per list word) in order, keeping the next
+// PF words in flight while the current pair is processed: fn(byte offset of the slot, candidate
+// index).  Word m (candidates 2m, 2m + 1) is loaded only when 2m < c.
+template <int PF, typename Fn>
 __device__ __forceinline__ void for_each_slot(const uint32_t *list, int n, int gi, int c, Fn &&fn)
 {
+    static_assert(PF >= 1 && PF <= 3, "prefetch distance");
     const uint32_t *p = list + gi;
-    uint32_t w = c > 0 ? __ldg(p) : 0u;
+    uint32_t r[PF + 1];   // r[0]: the current word, r[m]: word k/2 + m
+#pragma unroll
+    for (int m = 0; m <= PF; m++) r[m] = (2 * m < c) ? __ldg(p + (size_t)m * n) : 0u;
+    p += (size_t)(PF + 1) * n;
     int k = 0;
     for (; k + 1 < c; k += 2) {
+        uint32_t w = r[0];
+#pragma unroll
+        for (int m = 0; m < PF; m++) r[m] = r[m + 1];
+        r[PF] = (k + 2 * (PF + 1) < c) ? __ldg(p) : 0u;   // word k/2 + PF + 1
         p += n;
-        uint32_t wn = (k + 2 < c) ? __ldg(p) : 0u;
-        fn((int)(w & (HCAP - 1)), k);
-        fn((int)((w >> 16) & (HCAP - 1)), k + 1);
-        w = wn;
+        fn((int)(w & SLOT_OFF_MASK), k);
+        fn((int)((w >> 16) & SLOT_OFF_MASK), k + 1);
     }
-    if (k < c) fn((int)(w & (HCAP - 1)), k);
+    if (k < c) fn((int)(r[0] & SLOT_OFF_MASK), k);
 }
 
 // Candidates of particle gi.  Beyond the support the clamped kernel gives W = F = 0 exactly, and
 // adding +0 or -0 leaves an FP32 sum unchanged, so sums over candidates equal sums over neighbours.
-template <typename Fn>
+template <int PF, typename Fn>
 __device__ __forceinline__ void for_each_candidate(const DevParams &P, const Bufs &b, int gi, Fn &&fn)
 {
-    for_each_slot(b.vnbr, P.n, gi, b.vcnt[gi], fn);
+    for_each_slot<PF>(b.vnbr, P.n, gi, b.vcnt[gi], fn);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -567,7 +687,7 @@ __device__ __forceinline__ void for_each_candidate(const DevParams &P, const Buf
 
 constexpr int SMEM_AF = HCAP * (16 + 4);
 
-__global__ void __launch_bounds__(PT) k_pass_a_filter(DevParams P, Bufs b)
+__global__ void BOUNDS_A k_pass_a_filter(DevParams P, Bufs b)
 {
     if (stopped(b) || resorting(b)) return;
     __shared__ TileShared ts;
@@ -590,17 +710,20 @@ __global__ void __launch_bounds__(PT) k_pass_a_filter(DevParams P, Bufs b)
         int gi = sg[si];
         float4 pi = pos[si];
         float sw = P.W0;
-        int nn = 0;
-        unsigned long long mask = 0ull;
-        for_each_candidate(P, b, gi, [&](int j, int kc) {
-            float2 d = pair_d(pi, pos[j]);
-            float r2 = d.x * d.x + d.y * d.y;
+        int c = b.vcnt[gi];
+        // neighbour bits enter at the top of (mhi:mlo) and move down one place per candidate
+        uint32_t mlo = 0u, mhi = 0u;
+        for_each_slot<ANN_PF_A>(b.vnbr, P.n, gi, c, [&](int o, int kc) {
+            float2 d = pair_d(pi, slot_at(pos, o));
+            float r2 = len2(d);
             sw += kernel_w<true>(r2, P);
-            bool in = in_support(r2, P, b, gi, sg[j]);
-            nn += in;
-            mask |= (unsigned long long)in << kc;
+            uint32_t in = in_support(r2, P, b, gi, slot_at(sg, o));
+            mlo = __funnelshift_r(mlo, mhi, 1);
+            mhi = __funnelshift_r(mhi, in, 1);
         });
-        b.nnbr[gi] = nn;
+        unsigned long long mask = ((unsigned long long)mhi << 32) | mlo;
+        mask = c > 0 ? mask >> (64 - c) : 0ull;   // candidate k at bit k
+        b.nnbr[gi] = __popcll(mask);
         b.emask[gi] = mask;
         b.sumW[gi] = sw;
         b.V[gi] = 1.0f / sw;
@@ -616,7 +739,7 @@ __global__ void __launch_bounds__(PT) k_pass_a_filter(DevParams P, Bufs b)
 constexpr int SMEM_B = HCAP * (16 + 16 + 4 + 4);
 
 template <bool QOLD>
-__global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
+__global__ void BOUNDS_B k_pass_b(DevParams P, Bufs b)
 {
     if (stopped(b)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) *b.rebuild = 0u;   // both pass A kernels have run
@@ -644,44 +767,41 @@ __global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
         int gi = sg[si];
         float4 pi = sp[si], bi = sb[si];
         float q2i = sq[si];
-        float a11 = 0.f, a12 = 0.f, a22 = 0.f;
-        float l00 = 0.f, l01 = 0.f, l10 = 0.f, l11 = 0.f;
-        float r1xx = 0.f, r1xy = 0.f, r1yy = 0.f, r2xx = 0.f, r2xy = 0.f, r2yy = 0.f;
-        float g1x = 0.f, g1y = 0.f, g2x = 0.f, g2y = 0.f;
+        // two-lane accumulators: (a11, a12), a22; L rows (l00, l01), (l10, l11); Laplacian sums
+        // per tensor entry for (q11, q12): (r1xx, r2xx), (r1xy, r2xy), (r1yy, r2yy); div Q rows
+        float2 a1 = f2(0.f, 0.f), l0 = f2(0.f, 0.f), l1 = f2(0.f, 0.f);
+        float2 rxx = f2(0.f, 0.f), rxy = f2(0.f, 0.f), ryy = f2(0.f, 0.f);
+        float2 gq1 = f2(0.f, 0.f), gq2 = f2(0.f, 0.f);
+        float a22 = 0.f;
         float di = b.mdr[gi];   // loaded ahead of the neighbour loop
-        for_each_candidate(P, b, gi, [&](int j, int kc) {
-            float4 bj = sb[j];
-            float2 d = pair_d(pi, sp[j]);
-            float r2 = d.x * d.x + d.y * d.y;
-            float Wv, F, rinv;
-            kernel_wf<true>(r2, P, Wv, F, rinv);
-            float g = bj.x * F;
-            float gx = g * d.x, gy = g * d.y;
-            float mxx = gx * d.x, mxy = gx * d.y, myy = gy * d.y;
-            a11 -= mxx;
-            a12 -= mxy;
+        const float2 ui = f2(bi.y, bi.z), qi = f2(bi.w, q2i);
+        for_each_candidate<ANN_PF_B>(P, b, gi, [&](int o, int kc) {
+            float4 bj = slot_at(sb, o);
+            float2 d = pair_d(pi, slot_at(sp, o));
+            KernelPowers kp = kernel_powers<true>(len2(d), P);
+            float F = kernel_f_of(kp, P);
+            float2 g = mul2(bc(bj.x * F), d);            // V_j grad_i W = (gx, gy)
+            float2 mx = mul2(bc(g.x), d);                 // (mxx, mxy)
+            float myy = g.y * d.y;
+            a1 = sub2(a1, mx);
             a22 -= myy;
-            float dux = bj.y - bi.y, duy = bj.z - bi.z;
-            l00 += dux * gx;
-            l01 += dux * gy;
-            l10 += duy * gx;
-            l11 += duy * gy;
-            float dq1 = bj.w - bi.w, dq2 = sq[j] - q2i;
-            float rinv2 = rinv * rinv;
-            float e1 = -dq1 * rinv2, e2 = -dq2 * rinv2;
-            r1xx += e1 * mxx;
-            r1xy += e1 * mxy;
-            r1yy += e1 * myy;
-            r2xx += e2 * mxx;
-            r2xy += e2 * mxy;
-            r2yy += e2 * myy;
+            float2 du = sub2(f2(bj.y, bj.z), ui);         // u_j - u_i
+            l0 = fma2(bc(du.x), g, l0);
+            l1 = fma2(bc(du.y), g, l1);
+            float2 dq = sub2(f2(bj.w, slot_at(sq, o)), qi);   // Q_j - Q_i per component
+            float2 e = mul2(dq, bc(-(kp.rinv * kp.rinv)));
+            rxx = fma2(e, bc(mx.x), rxx);
+            rxy = fma2(e, bc(mx.y), rxy);
+            ryy = fma2(e, bc(myy), ryy);
             if (QOLD) {
-                g1x += dq1 * gx;
-                g1y += dq1 * gy;
-                g2x += dq2 * gx;
-                g2y += dq2 * gy;
+                gq1 = fma2(bc(dq.x), g, gq1);
+                gq2 = fma2(bc(dq.y), g, gq2);
             }
         });
+        float a11 = a1.x, a12 = a1.y;
+        float l00 = l0.x, l01 = l0.y, l10 = l1.x, l11 = l1.y;
+        float r1xx = rxx.x, r2xx = rxx.y, r1xy = rxy.x, r2xy = rxy.y, r1yy = ryy.x, r2yy = ryy.y;
+        float g1x = gq1.x, g1y = gq1.y, g2x = gq2.x, g2y = gq2.y;
         float det = a11 * a22 - a12 * a12;
         if (!(det > 0.f)) atomicOr(b.err, EB_SINGULAR);
         float idet = 1.f / det;
@@ -751,7 +871,7 @@ __global__ void __launch_bounds__(PT) k_pass_b(DevParams P, Bufs b)
 constexpr int smem_c(bool el) { return HCAP * (16 + 16 + (el ? 16 : 0) + 4); }
 
 template <bool QNEW, bool EL>
-__global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
+__global__ void BOUNDS_C k_pass_c(DevParams P, Bufs b)
 {
     if (stopped(b)) return;
     __shared__ TileShared ts;
@@ -780,7 +900,7 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
         int si = inner_slot(ts, T, q);
         int gi = sg[si];
         float4 pi = sp[si], bi = sb[si];
-        float shep = 0.f, g1x = 0.f, g1y = 0.f, g2x = 0.f, g2y = 0.f;
+        float shep = 0.f;
         float swi = b.sumW[gi];   // loaded ahead of the neighbour loop
         float B11 = 0.f, B12 = 0.f, B22 = 0.f;
         if (QNEW || EL) {
@@ -789,36 +909,33 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
             B22 = b.B22[gi];
         }
         float4 ei = EL ? se[si] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float e1x = 0.f, e1y = 0.f, e2x = 0.f, e2y = 0.f, e3x = 0.f, e3y = 0.f;
-        for_each_candidate(P, b, gi, [&](int j, int kc) {
-            float4 bj = sb[j];
-            float2 d = pair_d(pi, sp[j]);
-            float r2 = d.x * d.x + d.y * d.y;
-            float Wv, F, rinv;
-            kernel_wf<true>(r2, P, Wv, F, rinv);
+        // two-lane accumulators: corrected-gradient raw sums of q11, q12 and of Pi11, Pi12, Pi22
+        float2 gq1 = f2(0.f, 0.f), gq2 = f2(0.f, 0.f), ge1 = f2(0.f, 0.f), ge2 = f2(0.f, 0.f),
+               ge3 = f2(0.f, 0.f);
+        const float2 qi = f2(bi.z, bi.w);
+        for_each_candidate<ANN_PF_C>(P, b, gi, [&](int o, int kc) {
+            float4 bj = slot_at(sb, o);
+            float2 d = pair_d(pi, slot_at(sp, o));
+            KernelPowers kp = kernel_powers<true>(len2(d), P);
+            float Wv = kernel_w_of(kp, P);
             shep += (bi.y - bj.y) * Wv;
             if (QNEW || EL) {
-                float g = bj.x * F;
-                float gx = g * d.x, gy = g * d.y;
+                float2 g = mul2(bc(bj.x * kernel_f_of(kp, P)), d);
                 if (QNEW) {
-                    float dq1 = bj.z - bi.z, dq2 = bj.w - bi.w;
-                    g1x += dq1 * gx;
-                    g1y += dq1 * gy;
-                    g2x += dq2 * gx;
-                    g2y += dq2 * gy;
+                    float2 dq = sub2(f2(bj.z, bj.w), qi);
+                    gq1 = fma2(bc(dq.x), g, gq1);
+                    gq2 = fma2(bc(dq.y), g, gq2);
                 }
                 if (EL) {
-                    float4 ej = se[j];
-                    float d1 = ej.x - ei.x, d2 = ej.y - ei.y, d3 = ej.z - ei.z;
-                    e1x += d1 * gx;
-                    e1y += d1 * gy;
-                    e2x += d2 * gx;
-                    e2y += d2 * gy;
-                    e3x += d3 * gx;
-                    e3y += d3 * gy;
+                    float4 ej = slot_at(se, o);
+                    ge1 = fma2(bc(ej.x - ei.x), g, ge1);
+                    ge2 = fma2(bc(ej.y - ei.y), g, ge2);
+                    ge3 = fma2(bc(ej.z - ei.z), g, ge3);
                 }
             }
         });
+        float g1x = gq1.x, g1y = gq1.y, g2x = gq2.x, g2y = gq2.y;
+        float e1x = ge1.x, e1y = ge1.y, e2x = ge2.x, e2y = ge2.y, e3x = ge3.x, e3y = ge3.y;
         float dhat = bi.y - P.beta * shep / swi;
         b.dhat[gi] = dhat;
         b.p[gi] = pref * expm1f(P.gamma_eos * log1pf(dhat));
@@ -842,10 +959,11 @@ __global__ void __launch_bounds__(PT) k_pass_c(DevParams P, Bufs b)
 // Kernel 9: pass D -- momentum (Eq. 23), corrector (§3.1), APD (Eq. 29), re-insertion (Eq. 30)
 // ---------------------------------------------------------------------------------------------
 
-constexpr int smem_d(bool cons_el) { return HCAP * (16 + 16 + 8 + (cons_el ? 16 : 0) + 4); }
+// (the (q11, q12)/rho^2 tile exists in the conservative mode only, Pi/rho^2 with the elastic stress)
+constexpr int smem_d(bool cons, bool el) { return HCAP * (16 + 16 + (cons ? 8 : 0) + (cons && el ? 16 : 0) + 4); }
 
 template <bool CONS, bool EL>
-__global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
+__global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
 {
     if (stopped(b)) return;
     __shared__ TileShared ts;
@@ -853,7 +971,7 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
     float4 *sp = reinterpret_cast<float4 *>(dsm);       // split position
     float4 *sb = sp + HCAP;                             // paper: (V, p/rho^2, ux, uy)  cons: (p/rho^2, 1/rho, ux, uy)
     float2 *sc = reinterpret_cast<float2 *>(sb + HCAP); // cons: (q11/rho^2, q12/rho^2)
-    float4 *se = reinterpret_cast<float4 *>(sc + HCAP); // cons + elastic: Pi/rho^2 (11, 12, 22, -)
+    float4 *se = reinterpret_cast<float4 *>(sc + (CONS ? HCAP : 0)); // cons + elastic: Pi/rho^2
     int *sg = reinterpret_cast<int *>(se + ((CONS && EL) ? HCAP : 0));
     Tile T;
     if (!tile_begin(P, b, ts, T)) {
@@ -889,10 +1007,8 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
         float4 pi = sp[si], bi = sb[si];
         float2 ci = CONS ? sc[si] : make_float2(0.f, 0.f);
         float4 eci = (CONS && EL) ? se[si] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float fx = 0.f, fy = 0.f, vx = 0.f, vy = 0.f;
-        float sux = 0.f, suy = 0.f, sr = 0.f, sdx = 0.f, sdy = 0.f;
         int c = b.nnbr[gi];
-        unsigned long long emask = b.emask[gi];   // which candidates are neighbours
+        unsigned long long em = b.emask[gi];   // bit k: candidate k is a neighbour
         // per-particle inputs of the epilogue, loaded ahead of the neighbour loop
         float dhat = b.dhat[gi], kri = b.kr[gi], swi = b.sumW[gi];
         float B11 = 0.f, B12 = 0.f, B22 = 0.f, dvx = 0.f, dvy = 0.f;
@@ -909,59 +1025,63 @@ __global__ void __launch_bounds__(PT) k_pass_d(DevParams P, Bufs b)
             elx = b.delx[gi];
             ely = b.dely[gi];
         }
-        for_each_candidate(P, b, gi, [&](int j, int kc) {
-            float4 bj = sb[j];
-            float2 d = pair_d(pi, sp[j]);
-            float r2 = d.x * d.x + d.y * d.y;
-            float Wv, F, rinv;
-            kernel_wf<true>(r2, P, Wv, F, rinv);
-            float ux = bi.z - bj.z, uy = bi.w - bj.w;
-            float ud = ux * d.x + uy * d.y;
-            float rinv2 = rinv * rinv;
+        float rho = P.rho0 * (1.f + dhat);
+        // paper mode: pressure and viscous sums share grad_i W, so they accumulate as one vector
+        //   w = sum_j V_j F [ -rho_i (p_i/rho_i^2 + p_j/rho_j^2) + kv (u_ij . d) / r^2 ] d,
+        // with kv = 8 nu rho0 / rho_i, and a = B w + (active and elastic terms)
+        float irho = 1.f / rho;
+        float nrho = -rho, kv = 8.f * P.nu * P.rho0 * irho;
+        float k8 = 8.f * P.mu * bi.y;   // conservative: 8 mu / rho_i
+        const float2 ui = f2(bi.z, bi.w);
+        float2 w = f2(0.f, 0.f), su = f2(0.f, 0.f), sd = f2(0.f, 0.f);
+        float sr = 0.f;
+        for_each_candidate<ANN_PF_D>(P, b, gi, [&](int o, int kc) {
+            float4 bj = slot_at(sb, o);
+            float2 d = pair_d(pi, slot_at(sp, o));
+            float r2 = len2(d);
+            KernelPowers kp = kernel_powers<true>(r2, P);
+            float Wv = kernel_w_of(kp, P), F = kernel_f_of(kp, P);
+            float2 du = sub2(ui, f2(bj.z, bj.w));   // u_i - u_j
+            float ud = fmaf(du.x, d.x, du.y * d.y);
+            float rinv2 = kp.rinv * kp.rinv;
             if (CONS) {
-                float2 cj = sc[j];
-                float gx = F * d.x, gy = F * d.y;
-                float cp = bi.x + bj.x;
-                float visc = 8.f * P.mu * bi.y * bj.y * ud * rinv2;
-                float qa = ci.x + cj.x, qb = ci.y + cj.y;
-                fx += (visc - cp) * gx - P.zeta * (qa * gx + qb * gy);
-                fy += (visc - cp) * gy - P.zeta * (qb * gx - qa * gy);
+                float2 cj = slot_at(sc, o);
+                float2 g = mul2(bc(F), d);
+                float visc = k8 * bj.y * ud * rinv2;
+                w = fma2(bc(visc - (bi.x + bj.x)), g, w);
+                float2 qs = add2(ci, cj);   // (Q11_i/rho_i^2 + Q11_j/rho_j^2, same for Q12)
+                // Q.g = (qa gx + qb gy, qb gx - qa gy)
+                float2 act = fma2(qs, bc(g.x), mul2(f2(qs.y, -qs.x), bc(g.y)));
+                w = fma2(bc(-P.zeta), act, w);
                 if (EL) {   // + sum_j m (Pi_i/rho_i^2 + Pi_j/rho_j^2) . grad_i W
-                    float4 ecj = se[j];
-                    float e11 = eci.x + ecj.x, e12 = eci.y + ecj.y, e22 = eci.z + ecj.z;
-                    fx += e11 * gx + e12 * gy;
-                    fy += e12 * gx + e22 * gy;
+                    float4 ecj = slot_at(se, o);
+                    float2 e1 = add2(f2(eci.x, eci.y), f2(ecj.x, ecj.y));   // (Pi11, Pi12)
+                    float e22 = eci.z + ecj.z;
+                    w = fma2(e1, bc(g.x), fma2(f2(e1.y, e22), bc(g.y), w));
                 }
             } else {
-                float cp = bj.x * (bi.y + bj.y) * F;
-                fx += cp * d.x;
-                fy += cp * d.y;
-                float v = bj.x * ud * F * rinv2;
-                vx += v * d.x;
-                vy += v * d.y;
+                float coef = fmaf(kv, ud * rinv2, nrho * (bi.y + bj.y));
+                w = fma2(bc(bj.x * F * coef), d, w);
             }
-            sux += ux * Wv;
-            suy += uy * Wv;
-            // APD sums run over the neighbours only: their terms do not vanish at the support edge
-            float m = (float)((unsigned)(emask >> kc) & 1u);
-            sr += m * (r2 * rinv);
-            float rinv3 = m * (rinv2 * rinv);
-            sdx += d.x * rinv3;
-            sdy += d.y * rinv3;
+            su = fma2(du, bc(Wv), su);
+            // APD sums run over the neighbours only (their terms do not vanish at the support
+            // edge): candidate k is one iff bit k of the mask is set; the bits are consumed in order
+            bool in = (uint32_t)em & 1u;
+            em >>= 1;
+            if (in) {
+                sr += r2 * kp.rinv;
+                sd = fma2(d, bc(rinv2 * kp.rinv), sd);
+            }
         });
         float ax, ay;
-        float rho = P.rho0 * (1.f + dhat);
         if (CONS) {
-            ax = P.mass * fx;
-            ay = P.mass * fy;
+            ax = P.mass * w.x;
+            ay = P.mass * w.y;
         } else {
-            float pbx = B11 * fx + B12 * fy, pby = B12 * fx + B22 * fy;
-            float vbx = B11 * vx + B12 * vy, vby = B12 * vx + B22 * vy;
-            float irho = 1.f / rho;
-            float kv = 8.f * P.nu * P.rho0 * irho;
-            ax = -rho * pbx + kv * vbx - P.zeta * irho * dvx + irho * elx;
-            ay = -rho * pby + kv * vby - P.zeta * irho * dvy + irho * ely;
+            ax = fmaf(B11, w.x, B12 * w.y) - P.zeta * irho * dvx + irho * elx;
+            ay = fmaf(B12, w.x, B22 * w.y) - P.zeta * irho * dvy + irho * ely;
         }
+        float sux = su.x, suy = su.y, sdx = sd.x, sdy = sd.y;
         float unx = bi.z + P.half_dt * ax, uny = bi.w + P.half_dt * ay;
         float apx = 0.f, apy = 0.f;
         if (P.apd && c > 0) {
@@ -1059,10 +1179,10 @@ __global__ void __launch_bounds__(PT) k_export_nbrs(DevParams P, Bufs b, int *co
     for (int q = threadIdx.x; q < T.Ni; q += PT) {
         int si = inner_slot(ts, T, q);
         int gi = sg[si];
-        float4 pi = pos[si];
         int k = 0;
         unsigned long long emask = b.emask[gi];
-        for_each_candidate(P, b, gi, [&](int j, int kc) {
+        for_each_candidate<1>(P, b, gi, [&](int o, int kc) {
+            int j = o >> 4;
             if (((emask >> kc) & 1ull) && j < T.H && k < MAXN) {
                 cols[(size_t)k * P.n + gi] = b.mid[sg[j]];
                 k++;
@@ -1147,10 +1267,10 @@ cudaError_t prepare_kernels()
     if ((e = cudaFuncSetAttribute(k_pass_c<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c(false)))) return e;
     if ((e = cudaFuncSetAttribute(k_pass_c<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c(true)))) return e;
     if ((e = cudaFuncSetAttribute(k_pass_c<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c(true)))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_d<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_d(false)))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_d<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_d(false)))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_d<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_d(false)))) return e;
-    if ((e = cudaFuncSetAttribute(k_pass_d<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_d(true)))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_d<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_d(false, false)))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_d<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_d(true, false)))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_d<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_d(false, true)))) return e;
+    if ((e = cudaFuncSetAttribute(k_pass_d<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_d(true, true)))) return e;
     return cudaSuccess;
 }
 
@@ -1179,10 +1299,10 @@ cudaError_t launch_kernel(int k, const DevParams &P, const Bufs &b, cudaStream_t
         break;
     }
     case 9:
-        if (P.conservative && P.elastic) k_pass_d<true, true><<<nt, PT, smem_d(true), s>>>(P, b);
-        else if (P.conservative) k_pass_d<true, false><<<nt, PT, smem_d(false), s>>>(P, b);
-        else if (P.elastic) k_pass_d<false, true><<<nt, PT, smem_d(false), s>>>(P, b);
-        else k_pass_d<false, false><<<nt, PT, smem_d(false), s>>>(P, b);
+        if (P.conservative && P.elastic) k_pass_d<true, true><<<nt, PT, smem_d(true, true), s>>>(P, b);
+        else if (P.conservative) k_pass_d<true, false><<<nt, PT, smem_d(true, false), s>>>(P, b);
+        else if (P.elastic) k_pass_d<false, true><<<nt, PT, smem_d(false, true), s>>>(P, b);
+        else k_pass_d<false, false><<<nt, PT, smem_d(false, false), s>>>(P, b);
         break;
     default: return cudaErrorInvalidValue;
     }
