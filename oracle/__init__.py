@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sph_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "sph_diag.c")]
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liborc.so")
 _lock = threading.Lock()
@@ -59,14 +60,16 @@ NBR_MODES = {"brute": 0, "ghost": 1, "cells": 2}
 
 
 def build(force: bool = False) -> str:
-    """Compile ``sph_oracle.c`` into ``_lib/liborc.so`` with gcc (OpenMP, no FP contraction)."""
+    """Compile ``sph_oracle.c`` and ``sph_diag.c`` into ``_lib/liborc.so`` with gcc (OpenMP, no FP
+    contraction)."""
     with _lock:
-        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        if (not force and os.path.exists(_LIB)
+                and all(os.path.getmtime(_LIB) >= os.path.getmtime(p) for p in _SRCS)):
             return _LIB
         os.makedirs(_LIBDIR, exist_ok=True)
         tmp = _LIB + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-std=c99", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+               "-fPIC", "-shared", "-o", tmp, *_SRCS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
         return _LIB
