@@ -238,6 +238,83 @@ int ann_load_state(ann_ctx *ctx, const char *path);
 const char *ann_last_error(ann_ctx *ctx);
 
 /*
+ * Flow diagnostics of the results section (§5): the kinetic-energy spectrum (Eq. 31), the
+ * vorticity correlation and its length scale (Eq. 32), topological defects, the nematic order
+ * field, particle pathlines and mixing.  The paper names the quantities but not their
+ * discretisation; the readings taken are stated with each call.  They analyse the present state
+ * (after the last step) and never change it or the trajectory that follows.  Buffers they need are
+ * allocated on first use and kept for later calls.
+ *
+ * Gridded fields.  The state lives on particles; the spectrum, the correlation and the defects are
+ * computed on an M x M grid of nodes (ix L/M, iy L/M), M a power of two in [8, ANN_GRID_MAX], by
+ * Shepard interpolation with the method's kernel (Eq. 18): f(x_g) = sum_j f_j W_gj / sum_j W_gj
+ * over the particles with |x_g - x_j| < 3h (minimum image), FP32 sums, 0 where no particle is in
+ * reach.  Requires at least 5 cells per side (ann_grid.cells_per_side >= 5).
+ */
+#define ANN_GRID_MAX 2048
+#define ANN_MAX_COLORS 16
+#define ANN_MIX_BINS_MAX 4096
+
+/* The gridded present state: dst holds 5 M^2 doubles, fields ux, uy, q11, q12 and the weight
+ * sum sum_j W_gj, each row-major [iy][ix].  dst_is_device: 0 host, 1 device pointer.  Errors:
+ * INVALID_ARG (M, too few cells), STATE (no particles), CUDA, OOM. */
+int ann_grid_fields(ann_ctx *ctx, int32_t M, double *dst, int dst_is_device);
+
+/* Number of wavenumber shells of an M x M grid, round(M / sqrt 2) + 1 (host only; INVALID_ARG for
+ * a bad M). */
+int ann_spectrum_shells(int32_t M);
+
+/* Kinetic-energy spectrum of the gridded velocity (Eq. 31): with u_hat = FFT(u) / M^2 (FP64),
+ * E[n] = 1/2 sum |u_hat(k)|^2 over the integer wavevectors k whose |k| rounds to n, for
+ * n = 0 .. ann_spectrum_shells(M) - 1; wavenumber w_n = 2 pi n / L.  sum_n E[n] = 1/2 <|u|^2> of
+ * the grid (Parseval).  E: host array of at least nshell >= ann_spectrum_shells(M) doubles.
+ * Errors: as ann_grid_fields. */
+int ann_energy_spectrum(ann_ctx *ctx, int32_t M, double *E, int32_t nshell);
+
+/* Least-squares slope of log E[n] against log w_n over the shells with w1 <= w_n <= w2, n >= 1 and
+ * E[n] > 0 (the paper compares the spectrum with power laws w^-5/3, w^-4); NaN if fewer than two
+ * shells qualify.  Host only.  Errors: INVALID_ARG. */
+int ann_spectrum_slope(const double *E, int32_t nshell, double L, double w1, double w2, double *slope);
+
+/* Vorticity correlation (Eq. 32) along the horizontal centre line, row iy = M/2 of the grid, with
+ * the vorticity omega = d uy/dx - d ux/dy by periodic central differences of the gridded velocity.
+ * C[k] for r = k L/M, k = 0 .. M/2 (host array of M/2 + 1 doubles): all_origins = 0 takes the
+ * paper's single origin at the centre, C[k] = omega(M/2 + k) omega(M/2) / omega(M/2)^2;
+ * all_origins = 1 averages over every origin of the line (the box is periodic and homogeneous),
+ * C[k] = sum_i omega(i + k) omega(i) / sum_i omega(i)^2.  lengths (host, 2 doubles, may be NULL):
+ * the first r where C reaches 0, and where it falls to 0.2 max C (both length scales the paper
+ * names), linear between grid points, NaN if not reached.  Errors: as ann_grid_fields. */
+int ann_vorticity_correlation(ann_ctx *ctx, int32_t M, int32_t all_origins, double *C, double *lengths);
+
+/* Topological defects of the gridded Q: for each plaquette (ix, iy) -> (ix+1, iy) -> (ix+1, iy+1) ->
+ * (ix, iy+1) the winding number m of the vector (Q11, Q12) (the doubled director angle), counted
+ * exactly by signed crossings of the positive Q11 axis; the director defect there has charge m/2.
+ * counts (host, 3): plaquettes with m = +1 (+1/2 defects), m = -1 (-1/2), |m| >= 2.  map (host,
+ * M^2 int8, may be NULL): m of each plaquette, row-major by its lower-left node.  Defect density =
+ * (counts[0] + counts[1]) / L^2.  Errors: as ann_grid_fields. */
+int ann_defects(ann_ctx *ctx, int32_t M, int64_t *counts, int8_t *map);
+
+/* Colour of each particle by ID (n values in [0, ANN_MAX_COLORS), host or device), the marker of
+ * the paper's mixing experiment (particles coloured by their initial region).  Kept across
+ * ann_set_particles and in checkpoints; all 0 after ann_create.  Errors: INVALID_ARG (n, a colour
+ * out of range), CUDA. */
+int ann_set_colors(ann_ctx *ctx, const uint8_t *colors, int64_t n, int is_device);
+
+/* Mixing of the colours on a G x G grid of bins (1 <= G <= ANN_MIX_BINS_MAX; bin floor(x G / L),
+ * clamped): Danckwerts' intensity of segregation per colour s with overall fraction 0 < a_s < 1,
+ * I_s = mean over non-empty bins of (f_bs - a_s)^2 / (a_s (1 - a_s)), f_bs its fraction in bin b;
+ * *index = mean_s I_s (1: segregated at the bin scale, 0: uniformly mixed; 0 with one colour).
+ * per_species (host, ANN_MAX_COLORS doubles, may be NULL): I_s, NaN for absent or sole colours.
+ * Bin counts are exact integers.  Errors: INVALID_ARG, STATE, CUDA, OOM. */
+int ann_mixing_index(ann_ctx *ctx, int32_t G, double *index, double *per_species);
+
+/* Unwrapped positions of particles `ids` (host, k IDs in [0, n)) for pathlines: x + L i_x, y + L i_y
+ * with (i_x, i_y) the net periodic shifts of the particle since ann_set_particles (counted by the
+ * step kernels when they re-insert a particle, Eq. 30).  xy: host, 2k doubles (x0, y0, x1, ...).
+ * Errors: INVALID_ARG (an ID out of range), STATE, CUDA, OOM. */
+int ann_get_unwrapped(ann_ctx *ctx, const int64_t *ids, int64_t k, double *xy);
+
+/*
  * Velocity moments without any device allocation.  The paper has no counterpart: this is a
  * service entry point for callers that cannot call cudaMalloc -- a host framework that owns a fixed
  * device memory pool or a hard memory budget and forbids allocations after start-up, or a real-time

@@ -105,6 +105,16 @@ def lib() -> ctypes.CDLL:
         "ann_load_state": (i32, [vp, ctypes.c_char_p]),
         "ann_last_error": (ctypes.c_char_p, [vp]),
         "ann_velocity_moments_noalloc": (i32, [vp, vp, vp, ctypes.c_double, i64, vp, vp]),
+        "ann_grid_fields": (i32, [vp, i32, vp, i32]),
+        "ann_spectrum_shells": (i32, [i32]),
+        "ann_energy_spectrum": (i32, [vp, i32, _P(ctypes.c_double), i32]),
+        "ann_spectrum_slope": (i32, [_P(ctypes.c_double), i32, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, _P(ctypes.c_double)]),
+        "ann_vorticity_correlation": (i32, [vp, i32, i32, _P(ctypes.c_double), _P(ctypes.c_double)]),
+        "ann_defects": (i32, [vp, i32, _P(ctypes.c_int64), _P(ctypes.c_int8)]),
+        "ann_set_colors": (i32, [vp, vp, i64, i32]),
+        "ann_mixing_index": (i32, [vp, i32, _P(ctypes.c_double), _P(ctypes.c_double)]),
+        "ann_get_unwrapped": (i32, [vp, _P(ctypes.c_int64), i64, _P(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -284,3 +294,90 @@ def ann_velocity_moments_noalloc(ux, uy, out, mass=None, m0=1.0, stream=None) ->
         ctypes.c_void_p(mass.data_ptr()) if mass is not None else None, float(m0), int(ux.numel()),
         ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(int(handle) if handle else 0))
     _check(st, None, "ann_velocity_moments_noalloc")
+
+
+# ------------------------------------------------------------------ flow diagnostics (§5)
+
+GRID_MAX = 2048
+MAX_COLORS = 16
+_dptr = lambda a: a.ctypes.data_as(_P(ctypes.c_double))  # noqa: E731
+
+
+def ann_grid_fields(ctx, M: int, out=None):
+    """Gridded present state, shape (5, M, M): ux, uy, q11, q12, Shepard weight sum ([iy, ix]).
+    ``out``: optional float64 numpy array or CUDA tensor of 5 M^2 elements."""
+    if out is None:
+        out = np.empty((5, M, M), dtype=np.float64)
+    if hasattr(out, "data_ptr") and getattr(out, "is_cuda", False):
+        ptr, dev = out.data_ptr(), 1
+    else:
+        if out.dtype != np.float64 or out.size != 5 * M * M or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous float64 array of 5 M^2 elements")
+        ptr, dev = out.ctypes.data, 0
+    _check(lib().ann_grid_fields(ctx, int(M), ctypes.c_void_p(ptr), dev), ctx, "ann_grid_fields")
+    return out
+
+
+def ann_spectrum_shells(M: int) -> int:
+    return _check(lib().ann_spectrum_shells(int(M)), None, "ann_spectrum_shells")
+
+
+def ann_energy_spectrum(ctx, M: int):
+    """(w, E): wavenumbers 2 pi n / L and the shell energies of the gridded velocity."""
+    ns = ann_spectrum_shells(M)
+    E = np.zeros(ns)
+    _check(lib().ann_energy_spectrum(ctx, int(M), _dptr(E), ns), ctx, "ann_energy_spectrum")
+    return E
+
+
+def ann_spectrum_slope(E, L: float, w1: float, w2: float) -> float:
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    out = ctypes.c_double()
+    _check(lib().ann_spectrum_slope(_dptr(E), E.size, float(L), float(w1), float(w2), ctypes.byref(out)),
+           None, "ann_spectrum_slope")
+    return out.value
+
+
+def ann_vorticity_correlation(ctx, M: int, all_origins: bool = True):
+    """(C[0..M/2], (zero-crossing length, 0.2-max length))."""
+    C = np.zeros(M // 2 + 1)
+    lengths = np.zeros(2)
+    _check(lib().ann_vorticity_correlation(ctx, int(M), int(bool(all_origins)), _dptr(C), _dptr(lengths)), ctx,
+           "ann_vorticity_correlation")
+    return C, (float(lengths[0]), float(lengths[1]))
+
+
+def ann_defects(ctx, M: int, with_map: bool = False):
+    """(counts [m = +1, m = -1, |m| >= 2], winding map int8 [M, M] or None)."""
+    counts = np.zeros(3, dtype=np.int64)
+    m = np.zeros((M, M), dtype=np.int8) if with_map else None
+    _check(lib().ann_defects(ctx, int(M), counts.ctypes.data_as(_P(ctypes.c_int64)),
+                             m.ctypes.data_as(_P(ctypes.c_int8)) if with_map else None), ctx, "ann_defects")
+    return counts, m
+
+
+def ann_set_colors(ctx, colors) -> None:
+    """Colour of each particle by ID: uint8 numpy array or CUDA tensor of n values."""
+    if hasattr(colors, "data_ptr") and getattr(colors, "is_cuda", False):
+        ptr, dev, n = colors.data_ptr(), 1, colors.numel()
+    else:
+        colors = np.ascontiguousarray(colors, dtype=np.uint8)
+        ptr, dev, n = colors.ctypes.data, 0, colors.size
+    _check(lib().ann_set_colors(ctx, ctypes.c_void_p(ptr), int(n), dev), ctx, "ann_set_colors")
+
+
+def ann_mixing_index(ctx, G: int):
+    """(intensity of segregation I, per-colour I_s with NaN for absent or sole colours)."""
+    I = ctypes.c_double()
+    per = np.zeros(MAX_COLORS)
+    _check(lib().ann_mixing_index(ctx, int(G), ctypes.byref(I), _dptr(per)), ctx, "ann_mixing_index")
+    return I.value, per
+
+
+def ann_get_unwrapped(ctx, ids):
+    """Unwrapped positions (k, 2) of the particles with the given IDs."""
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    xy = np.zeros((ids.size, 2))
+    _check(lib().ann_get_unwrapped(ctx, ids.ctypes.data_as(_P(ctypes.c_int64)), ids.size, _dptr(xy)), ctx,
+           "ann_get_unwrapped")
+    return xy

@@ -30,6 +30,20 @@ struct ann_ctx {
     double *diag_part = nullptr;  // diag_blocks(n) x NDIAG
     double *diag_out = nullptr;   // NDIAG
     uint32_t *h_err = nullptr;    // pinned
+    // Which arrays hold the present state in the cell order of the last re-sort (the order the
+    // flow diagnostics need): S after a step or a load that kept the cell structure, the
+    // evaluation copy M after a neighbour export; neither after ann_set_particles.
+    bool s_sorted = false, m_current = false;
+    // flow diagnostics (allocated on first use, sized for the largest request so far)
+    unsigned char *colors = nullptr;   // by particle ID (n)
+    int ncolors = 1;                   // largest colour + 1
+    int *inv = nullptr;                // slot of each particle ID (n)
+    struct Scratch {
+        void *p = nullptr;
+        size_t bytes = 0;
+    } d_grid, d_off, d_fld, d_z, d_zt, d_tw, d_shoff, d_shmodes, d_out, d_map, d_cnt, d_ids;
+    int grid_M = 0, tw_M = 0, shell_M = 0;
+    int64_t grid_step = -1;            // step count of the gridded fields in d_grid (-1: none)
 };
 
 namespace {
@@ -245,7 +259,7 @@ cudaError_t alloc_all(ann_ctx *c)
     A_(sumW, n); A_(V, n); A_(B11, n); A_(B12, n); A_(B22, n); A_(kr, n); A_(dh, n); A_(dhat, n);
     A_(p, n); A_(divx, n); A_(divy, n);
     A_(rec_gu, 4 * n); A_(rec_lap, 2 * n); A_(rec_apd, 2 * n);
-    A_(pel, n); A_(delx, n); A_(dely, n);
+    A_(pel, n); A_(delx, n); A_(dely, n); A_(img, n);
     A_(err, 1); A_(maxu, 1); A_(band, 1);
 #undef A_
     double *origin = nullptr;
@@ -259,6 +273,8 @@ cudaError_t alloc_all(ann_ctx *c)
     unsigned char *tmp = nullptr;
     if ((e = dalloc(c, tmp, std::max<size_t>(7 * 8, MAXN * 4) * n))) return e;
     c->tmp = tmp;
+    if ((e = dalloc(c, c->colors, n))) return e;
+    if ((e = dalloc(c, c->inv, n))) return e;
     if ((e = dalloc(c, c->diag_part, (size_t)diag_blocks((int)n) * NDIAG))) return e;
     if ((e = dalloc(c, c->diag_out, NDIAG))) return e;
     return cudaSuccess;
@@ -408,7 +424,8 @@ __global__ void k_deinterleave(const float *src, float *dst, int n, int stride, 
     if (i < n) dst[i] = src[(size_t)i * stride + comp];
 }
 
-const char kMagic[8] = {'A', 'N', 'N', 'S', 'T', 'A', 'T', '2'};
+const char kMagic[8] = {'A', 'N', 'N', 'S', 'T', 'A', 'T', '3'};
+const char kMagicV2[8] = {'A', 'N', 'N', 'S', 'T', 'A', 'T', '2'};   // read: no image counts, colours
 
 }  // namespace
 
@@ -506,6 +523,9 @@ void ann_destroy(ann_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->exec) cudaGraphExecDestroy(c->exec);
     for (void *v : c->allocs) cudaFree(v);
+    for (ann_ctx::Scratch *sc : {&c->d_grid, &c->d_off, &c->d_fld, &c->d_z, &c->d_zt, &c->d_tw, &c->d_shoff,
+                                 &c->d_shmodes, &c->d_out, &c->d_map, &c->d_cnt, &c->d_ids})
+        if (sc->p) cudaFree(sc->p);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->own) cudaStreamDestroy(c->own);
     if (c->aux) cudaStreamDestroy(c->aux);
@@ -546,6 +566,8 @@ int ann_set_particles(ann_ctx *c, int64_t n, const double *x, const double *y, c
     c->have_particles = true;
     c->steps = 0;
     c->t = 0.0;
+    c->s_sorted = c->m_current = false;
+    c->grid_step = -1;
     int s = device_status(c);
     if (s) {
         c->have_particles = false;
@@ -566,6 +588,11 @@ int ann_step(ann_ctx *c, int64_t nsteps)
     int s = device_status(c);
     c->steps += nsteps;
     c->t += nsteps * c->P.dt_d;
+    if (nsteps > 0) {
+        c->s_sorted = true;
+        c->m_current = false;
+        c->grid_step = -1;
+    }
     return s;
 }
 
@@ -618,6 +645,11 @@ int ann_step_profile(ann_ctx *c, int64_t nsteps, double *kernel_ms)
     int st = device_status(c);
     c->steps += nsteps;
     c->t += nsteps * c->P.dt_d;
+    if (nsteps > 0) {
+        c->s_sorted = true;
+        c->m_current = false;
+        c->grid_step = -1;
+    }
     return st;
 }
 
@@ -713,6 +745,8 @@ int ann_get_neighbors(ann_ctx *c, int64_t *rowptr, int32_t *cols, int64_t cap)
     if (e) return cuda_fail(c, e, "ann_get_neighbors search");
     int s = device_status(c);
     if (s) return s;
+    c->s_sorted = false;   // the cell structure now follows M, which holds the present state
+    c->m_current = true;
     std::vector<int> nn(n), mid(n);
     e = cudaMemcpyAsync(nn.data(), c->b.nnbr, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaMemcpyAsync(mid.data(), c->b.mid, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream);
@@ -747,6 +781,8 @@ int ann_get_neighbors(ann_ctx *c, int64_t *rowptr, int32_t *cols, int64_t cap)
 // File layout: magic, n, parameters, t, step count, re-sort flag, then per particle in the internal
 // order: x, y (FP64); ux, uy, q11, q12, delta, ax, ay (FP32); ID; cell of the last re-sort; split
 // position of the last re-sort (4 x FP32).  The last three reproduce the candidate lists exactly.
+// Then per particle ID: periodic image counts (2 x int32) and colour (uint8).  Files of the
+// previous layout ("ANNSTAT2", without the last two) load with zero counts and colour 0.
 int ann_save_state(ann_ctx *c, const char *path)
 {
     if (!c || !path) return ANN_ERR_INVALID_ARG;
@@ -766,6 +802,10 @@ int ann_save_state(ann_ctx *c, const char *path)
     if (!e) e = cudaMemcpyAsync(mk.data(), b.mkey, 4 * n, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaMemcpyAsync(xr.data(), b.xi_ref, 16 * n, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaMemcpyAsync(&rb, b.rebuild, 4, cudaMemcpyDeviceToHost, c->stream);
+    std::vector<int> img(2 * n);
+    std::vector<unsigned char> col(n);
+    if (!e) e = cudaMemcpyAsync(img.data(), b.img, 8 * n, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(col.data(), c->colors, n, cudaMemcpyDeviceToHost, c->stream);
     if (!e) e = cudaStreamSynchronize(c->stream);
     if (e) return cuda_fail(c, e, "ann_save_state");
     if (c->steps == 0) rb = 1;   // nothing evaluated yet: the next step re-sorts
@@ -777,7 +817,8 @@ int ann_save_state(ann_ctx *c, const char *path)
               std::fwrite(&c->steps, 8, 1, fp) == 1 && std::fwrite(&rb, 4, 1, fp) == 1 &&
               std::fwrite(d.data(), 8, 2 * n, fp) == 2 * n && std::fwrite(f.data(), 4, 7 * n, fp) == 7 * n &&
               std::fwrite(id.data(), 4, n, fp) == n && std::fwrite(mk.data(), 4, n, fp) == n &&
-              std::fwrite(xr.data(), 4, 4 * n, fp) == 4 * n;
+              std::fwrite(xr.data(), 4, 4 * n, fp) == 4 * n && std::fwrite(img.data(), 4, 2 * n, fp) == 2 * n &&
+              std::fwrite(col.data(), 1, n, fp) == n;
     ok = (std::fclose(fp) == 0) && ok;
     return ok ? ANN_OK : fail(c, ANN_ERR_IO, "short write");
 }
@@ -793,7 +834,9 @@ int ann_load_state(ann_ctx *c, const char *path)
     double t = 0.0;
     int64_t steps = 0;
     uint32_t rb = 1;
-    bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+    bool ok = std::fread(magic, 1, 8, fp) == 8;
+    bool v3 = ok && std::memcmp(magic, kMagic, 8) == 0;
+    ok = ok && (v3 || std::memcmp(magic, kMagicV2, 8) == 0) &&
               std::fread(&nn, 8, 1, fp) == 1 && std::fread(&prm, sizeof prm, 1, fp) == 1 &&
               std::fread(&t, 8, 1, fp) == 1 && std::fread(&steps, 8, 1, fp) == 1 &&
               std::fread(&rb, 4, 1, fp) == 1;
@@ -807,7 +850,12 @@ int ann_load_state(ann_ctx *c, const char *path)
     ok = std::fread(d.data(), 8, 2 * n, fp) == 2 * n && std::fread(f.data(), 4, 7 * n, fp) == 7 * n &&
          std::fread(id.data(), 4, n, fp) == n && std::fread(mk.data(), 4, n, fp) == n &&
          std::fread(xr.data(), 4, 4 * n, fp) == 4 * n;
+    std::vector<int> img(2 * n, 0);
+    std::vector<unsigned char> col(n, 0);
+    if (ok && v3) ok = std::fread(img.data(), 4, 2 * n, fp) == 2 * n && std::fread(col.data(), 1, n, fp) == n;
     std::fclose(fp);
+    for (unsigned char v : col)
+        if (v >= ANN_MAX_COLORS) return fail(c, ANN_ERR_INVALID_ARG, "state file colour out of range");
     if (!ok) return fail(c, ANN_ERR_IO, "short read");
     // cell starts of the last re-sort, from the cell of each particle (nondecreasing in this order)
     std::vector<uint32_t> start((size_t)c->P.ncell + 1, 0);
@@ -828,6 +876,8 @@ int ann_load_state(ann_ctx *c, const char *path)
     if (!e) e = cudaMemcpyAsync(b.sid, id.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
     if (!e) e = cudaMemcpyAsync(b.mkey, mk.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
     if (!e) e = cudaMemcpyAsync(b.xi_ref, xr.data(), 16 * n, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaMemcpyAsync(b.img, img.data(), 8 * n, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaMemcpyAsync(c->colors, col.data(), n, cudaMemcpyHostToDevice, c->stream);
     if (!e && !rb) {
         e = cudaMemcpyAsync(b.cell_start, start.data(), 4 * start.size(), cudaMemcpyHostToDevice, c->stream);
         if (!e) e = enqueue_candidates_from_ref(c->P, b, c->stream);
@@ -838,9 +888,303 @@ int ann_load_state(ann_ctx *c, const char *path)
     c->have_particles = true;
     c->t = t;
     c->steps = steps;
+    c->s_sorted = !rb;
+    c->m_current = false;
+    c->grid_step = -1;
+    c->ncolors = 1;
+    for (unsigned char v : col) c->ncolors = std::max(c->ncolors, (int)v + 1);
     return device_status(c);
 }
 
 const char *ann_last_error(ann_ctx *c) { return c ? c->last_err.c_str() : ""; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// Flow diagnostics of the results section
+// ------------------------------------------------------------------------------------------------
+
+namespace {
+
+cudaError_t ensure(ann_ctx::Scratch &sc, size_t bytes)
+{
+    if (sc.bytes >= bytes) return cudaSuccess;
+    if (sc.p) cudaFree(sc.p);
+    sc.p = nullptr;
+    sc.bytes = 0;
+    cudaError_t e = cudaMalloc(&sc.p, std::max<size_t>(bytes, 16));
+    if (!e) sc.bytes = bytes;
+    return e;
+}
+
+bool grid_size_ok(int M) { return M >= 8 && M <= ANN_GRID_MAX && (M & (M - 1)) == 0; }
+
+int nshell_of(int M) { return (int)std::lround((double)M / std::sqrt(2.0)) + 1; }
+
+// The present state in the cell order of the last re-sort: S or M, else a search at the present
+// positions (the next step re-sorts in that case anyway, so the trajectory is unchanged).
+int diag_source(ann_ctx *c, DiagSrc &src)
+{
+    const Bufs &b = c->b;
+    if (!c->s_sorted && !c->m_current) {
+        DevParams Q = c->P;
+        Q.half_dt = 0.f;
+        Q.half_dt_d = 0.0;
+        cudaError_t e = cudaMemsetAsync(c->b.rebuild, 1, sizeof(uint32_t), c->stream);
+        if (!e) e = enqueue_search(Q, c->b, c->stream);
+        if (e) return cuda_fail(c, e, "diagnostics search");
+        int st = device_status(c);
+        if (st) return st;
+        c->m_current = true;
+    }
+    if (c->s_sorted) src = DiagSrc{b.sx, b.sy, b.sux, b.suy, b.sq11, b.sq12};
+    else src = DiagSrc{b.mx, b.my, b.mux, b.muy, b.mq11, b.mq12};
+    return ANN_OK;
+}
+
+// Gridded fields of the present state in d_grid (computed once per step and grid size).
+int diag_grid(ann_ctx *c, int M)
+{
+    if (!c->have_particles) return fail(c, ANN_ERR_STATE, "no particles");
+    if (!grid_size_ok(M)) return fail(c, ANN_ERR_INVALID_ARG, "grid size must be a power of two in [8, ANN_GRID_MAX]");
+    if (c->P.nc < 5) return fail(c, ANN_ERR_INVALID_ARG, "gridding needs at least 5 cells per side");
+    if (c->grid_M == M && c->grid_step == c->steps) return ANN_OK;
+    DiagSrc src;
+    int st = diag_source(c, src);
+    if (st) return st;
+    size_t n = (size_t)c->P.n, MM = (size_t)M * M;
+    cudaError_t e = ensure(c->d_grid, 5 * MM * sizeof(double));
+    if (!e) e = ensure(c->d_off, n * sizeof(float2));
+    if (!e) e = ensure(c->d_fld, n * sizeof(float4));
+    if (!e) e = enqueue_grid(c->P, c->b, src, M, (float2 *)c->d_off.p, (float4 *)c->d_fld.p, (double *)c->d_grid.p,
+                             c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "gridding");
+    c->grid_M = M;
+    c->grid_step = c->steps;
+    return ANN_OK;
+}
+
+// Shells of the FFT modes (index a M + b, a and b FFT indices): CSR in increasing mode index.
+cudaError_t shell_table(ann_ctx *c, int M)
+{
+    if (c->shell_M == M) return cudaSuccess;
+    int ns = nshell_of(M);
+    size_t MM = (size_t)M * M;
+    std::vector<int> cnt((size_t)ns + 1, 0), modes(MM), which(MM);
+    for (int a = 0; a < M; a++) {
+        long long ka = a < M / 2 ? a : a - M;
+        for (int bb = 0; bb < M; bb++) {
+            long long kb = bb < M / 2 ? bb : bb - M;
+            int sh = (int)std::llround(std::sqrt((double)(ka * ka + kb * kb)));
+            which[(size_t)a * M + bb] = sh;
+            cnt[(size_t)sh + 1]++;
+        }
+    }
+    for (int k = 0; k < ns; k++) cnt[(size_t)k + 1] += cnt[(size_t)k];
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (size_t i = 0; i < MM; i++) modes[(size_t)fill[(size_t)which[i]]++] = (int)i;
+    cudaError_t e = ensure(c->d_shoff, cnt.size() * sizeof(int));
+    if (!e) e = ensure(c->d_shmodes, MM * sizeof(int));
+    if (!e) e = cudaMemcpy(c->d_shoff.p, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(c->d_shmodes.p, modes.data(), MM * sizeof(int), cudaMemcpyHostToDevice);
+    if (!e) c->shell_M = M;
+    return e;
+}
+
+double crossing_length(const double *C, int M, double L, double level)
+{
+    for (int k = 0; k < M / 2; k++)
+        if (C[k] > level && level >= C[k + 1]) return (k + (C[k] - level) / (C[k] - C[k + 1])) * L / M;
+    return NAN;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ann_spectrum_shells(int32_t M) { return grid_size_ok(M) ? nshell_of(M) : ANN_ERR_INVALID_ARG; }
+
+int ann_grid_fields(ann_ctx *c, int32_t M, double *dst, int dst_is_device)
+{
+    if (!c || !dst) return ANN_ERR_INVALID_ARG;
+    int st = diag_grid(c, M);
+    if (st) return st;
+    cudaError_t e = cudaMemcpyAsync(dst, c->d_grid.p, 5 * (size_t)M * M * sizeof(double),
+                                    dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    return e ? cuda_fail(c, e, "ann_grid_fields") : ANN_OK;
+}
+
+int ann_energy_spectrum(ann_ctx *c, int32_t M, double *E, int32_t nshell)
+{
+    if (!c || !E) return ANN_ERR_INVALID_ARG;
+    int st = diag_grid(c, M);
+    if (st) return st;
+    int ns = nshell_of(M);
+    if (nshell < ns) return fail(c, ANN_ERR_INVALID_ARG, "E holds fewer than ann_spectrum_shells(M) values");
+    size_t MM = (size_t)M * M;
+    cudaError_t e = ensure(c->d_z, MM * sizeof(double2));
+    if (!e) e = ensure(c->d_zt, MM * sizeof(double2));
+    if (!e) e = ensure(c->d_tw, (size_t)(M / 2) * sizeof(double2));
+    if (!e) e = ensure(c->d_out, (size_t)std::max(ns, M / 2 + 1) * sizeof(double));
+    if (!e && c->tw_M != M) {
+        e = enqueue_twiddles(M, (double2 *)c->d_tw.p, c->stream);
+        if (!e) c->tw_M = M;
+    }
+    if (!e) e = shell_table(c, M);
+    if (!e) e = enqueue_spectrum(M, (const double *)c->d_grid.p, (double2 *)c->d_z.p, (double2 *)c->d_zt.p,
+                                 (const double2 *)c->d_tw.p, (const int *)c->d_shoff.p, (const int *)c->d_shmodes.p,
+                                 ns, (double *)c->d_out.p, c->stream);
+    if (!e) e = cudaMemcpyAsync(E, c->d_out.p, (size_t)ns * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    return e ? cuda_fail(c, e, "ann_energy_spectrum") : ANN_OK;
+}
+
+int ann_spectrum_slope(const double *E, int32_t nshell, double L, double w1, double w2, double *slope)
+{
+    if (!E || !slope || nshell < 1 || !(L > 0.0)) return ANN_ERR_INVALID_ARG;
+    double sx = 0, sy = 0, sxx = 0, sxy = 0;
+    int m = 0;
+    for (int k = 1; k < nshell; k++) {
+        double w = 2.0 * M_PI * k / L;
+        if (w < w1 || w > w2 || !(E[k] > 0.0)) continue;
+        double x = std::log(w), y = std::log(E[k]);
+        sx += x;
+        sy += y;
+        sxx += x * x;
+        sxy += x * y;
+        m++;
+    }
+    if (m < 2) {
+        *slope = NAN;
+        return ANN_OK;
+    }
+    *slope = (m * sxy - sx * sy) / (m * sxx - sx * sx);
+    return ANN_OK;
+}
+
+int ann_vorticity_correlation(ann_ctx *c, int32_t M, int32_t all_origins, double *C, double *lengths)
+{
+    if (!c || !C || (all_origins != 0 && all_origins != 1)) return ANN_ERR_INVALID_ARG;
+    int st = diag_grid(c, M);
+    if (st) return st;
+    cudaError_t e = ensure(c->d_out, (size_t)std::max(nshell_of(M), M / 2 + 1) * sizeof(double));
+    if (!e) e = enqueue_correlation(M, c->prm.L, (const double *)c->d_grid.p, all_origins, (double *)c->d_out.p,
+                                    c->stream);
+    if (!e) e = cudaMemcpyAsync(C, c->d_out.p, (size_t)(M / 2 + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "ann_vorticity_correlation");
+    if (lengths) {
+        double mx = C[0];
+        for (int k = 1; k <= M / 2; k++) mx = std::max(mx, C[k]);
+        lengths[0] = crossing_length(C, M, c->prm.L, 0.0);
+        lengths[1] = crossing_length(C, M, c->prm.L, 0.2 * mx);
+    }
+    return ANN_OK;
+}
+
+int ann_defects(ann_ctx *c, int32_t M, int64_t *counts, int8_t *map)
+{
+    if (!c || !counts) return ANN_ERR_INVALID_ARG;
+    int st = diag_grid(c, M);
+    if (st) return st;
+    size_t MM = (size_t)M * M;
+    unsigned long long h[3];
+    cudaError_t e = ensure(c->d_map, MM);
+    if (!e) e = ensure(c->d_cnt, std::max<size_t>(3 * sizeof(unsigned long long), c->d_cnt.bytes));
+    if (!e) e = enqueue_defects(M, (const double *)c->d_grid.p, (signed char *)c->d_map.p,
+                                (unsigned long long *)c->d_cnt.p, c->stream);
+    if (!e) e = cudaMemcpyAsync(h, c->d_cnt.p, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+    if (!e && map) e = cudaMemcpyAsync(map, c->d_map.p, MM, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "ann_defects");
+    for (int k = 0; k < 3; k++) counts[k] = (int64_t)h[k];
+    return ANN_OK;
+}
+
+int ann_set_colors(ann_ctx *c, const uint8_t *colors, int64_t n, int is_device)
+{
+    if (!c || !colors) return ANN_ERR_INVALID_ARG;
+    if (n != c->prm.n) return fail(c, ANN_ERR_INVALID_ARG, "n differs from the n of ann_create");
+    std::vector<uint8_t> h((size_t)n);
+    cudaError_t e = cudaMemcpyAsync(h.data(), colors, (size_t)n, is_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost,
+                                    c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "ann_set_colors");
+    int mx = 0;
+    for (uint8_t v : h) mx = std::max(mx, (int)v);
+    if (mx >= ANN_MAX_COLORS) return fail(c, ANN_ERR_INVALID_ARG, "colour beyond ANN_MAX_COLORS - 1");
+    e = cudaMemcpyAsync(c->colors, h.data(), (size_t)n, cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "ann_set_colors");
+    c->ncolors = mx + 1;
+    return ANN_OK;
+}
+
+int ann_mixing_index(ann_ctx *c, int32_t G, double *index, double *per_species)
+{
+    if (!c || !index || G < 1 || G > ANN_MIX_BINS_MAX) return ANN_ERR_INVALID_ARG;
+    if (!c->have_particles) return fail(c, ANN_ERR_STATE, "no particles");
+    int S = c->ncolors;
+    size_t nb = (size_t)G * G, bytes = nb * S * sizeof(unsigned);
+    cudaError_t e = ensure(c->d_cnt, std::max<size_t>(bytes, 3 * sizeof(unsigned long long)));
+    if (!e) e = enqueue_mixing(c->P, c->b, c->colors, G, S, (unsigned *)c->d_cnt.p, c->stream);
+    std::vector<unsigned> cnt(nb * S);
+    if (!e) e = cudaMemcpyAsync(cnt.data(), c->d_cnt.p, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "ann_mixing_index");
+    std::vector<double> Ns((size_t)S, 0.0);
+    std::vector<double> Nb(nb, 0.0);
+    double N = 0.0;
+    for (size_t k = 0; k < nb; k++)
+        for (int s2 = 0; s2 < S; s2++) {
+            double v = cnt[k * S + s2];
+            Ns[(size_t)s2] += v;
+            Nb[k] += v;
+            N += v;
+        }
+    double sum = 0.0;
+    int used = 0;
+    for (int s2 = 0; s2 < S; s2++) {
+        double a = N > 0 ? Ns[(size_t)s2] / N : 0.0, Is = NAN;
+        if (a > 0.0 && a < 1.0) {
+            double acc = 0.0;
+            int full = 0;
+            for (size_t k = 0; k < nb; k++) {
+                if (Nb[k] <= 0.0) continue;
+                double f = cnt[k * S + s2] / Nb[k] - a;
+                acc += f * f;
+                full++;
+            }
+            Is = acc / full / (a * (1.0 - a));
+            sum += Is;
+            used++;
+        }
+        if (per_species) per_species[s2] = Is;
+    }
+    if (per_species)
+        for (int s2 = S; s2 < ANN_MAX_COLORS; s2++) per_species[s2] = NAN;
+    *index = used ? sum / used : 0.0;
+    return ANN_OK;
+}
+
+int ann_get_unwrapped(ann_ctx *c, const int64_t *ids, int64_t k, double *xy)
+{
+    if (!c || (k > 0 && (!ids || !xy)) || k < 0 || k > c->prm.n) return ANN_ERR_INVALID_ARG;
+    if (!c->have_particles) return fail(c, ANN_ERR_STATE, "no particles");
+    for (int64_t t = 0; t < k; t++)
+        if (ids[t] < 0 || ids[t] >= c->prm.n) return fail(c, ANN_ERR_INVALID_ARG, "particle ID out of range");
+    if (k == 0) return ANN_OK;
+    size_t kk = (size_t)k;
+    cudaError_t e = ensure(c->d_ids, kk * (sizeof(long long) + 2 * sizeof(double)));
+    long long *dids = (long long *)c->d_ids.p;
+    double *dxy = (double *)(dids + kk);
+    if (!e) e = cudaMemcpyAsync(dids, ids, kk * sizeof(long long), cudaMemcpyHostToDevice, c->stream);
+    if (!e) e = enqueue_unwrapped(c->P, c->b, c->inv, dids, (int)k, dxy, c->stream);
+    if (!e) e = cudaMemcpyAsync(xy, dxy, 2 * kk * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    return e ? cuda_fail(c, e, "ann_get_unwrapped") : ANN_OK;
+}
 
 }  // extern "C"

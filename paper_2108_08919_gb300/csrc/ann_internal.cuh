@@ -76,6 +76,7 @@ struct Bufs {
     float *rec_gu, *rec_lap, *rec_apd;   // 4n, 2n, 2n (recording only)
     float4 *pel;        // elastic stress (11, 12, 22, -) of Eq. 12 (elastic_stress only)
     float *delx, *dely; // its corrected divergence (paper momentum only)
+    int2 *img;          // by particle ID: net periodic shifts (x, y) since ann_set_particles
     uint32_t *err, *maxu;
     unsigned long long *band;
 };
@@ -108,5 +109,24 @@ constexpr int NDIAG = 12;
 cudaError_t enqueue_diag(const DevParams &P, const Bufs &b, double *partials, int nblocks,
                          double *out, cudaStream_t s);
 int diag_blocks(int n);
+
+// Flow diagnostics (ann_diag.cu).  DiagSrc: the state the analysis reads, in the cell order of the
+// last re-sort (mkey, cell_start).
+struct DiagSrc {
+    const double *x, *y;
+    const float *ux, *uy, *q11, *q12;
+};
+// grid: 5 x M x M doubles (ux, uy, q11, q12, Shepard weight sum), [field][iy][ix]
+cudaError_t enqueue_grid(const DevParams &P, const Bufs &b, DiagSrc src, int M, float2 *off, float4 *fld,
+                         double *grid, cudaStream_t s);
+cudaError_t enqueue_twiddles(int M, double2 *tw, cudaStream_t s);
+cudaError_t enqueue_spectrum(int M, const double *grid, double2 *z, double2 *zt, const double2 *tw,
+                             const int *shell_off, const int *shell_modes, int nshell, double *E, cudaStream_t s);
+cudaError_t enqueue_correlation(int M, double L, const double *grid, int all_origins, double *C, cudaStream_t s);
+cudaError_t enqueue_defects(int M, const double *grid, signed char *map, unsigned long long *counts, cudaStream_t s);
+cudaError_t enqueue_mixing(const DevParams &P, const Bufs &b, const unsigned char *colors, int G, int S,
+                           unsigned *cnt, cudaStream_t s);
+cudaError_t enqueue_unwrapped(const DevParams &P, const Bufs &b, int *inv, const long long *ids, int k, double *xy,
+                              cudaStream_t s);
 
 }  // namespace ann

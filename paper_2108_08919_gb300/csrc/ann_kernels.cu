@@ -9,7 +9,7 @@
 // so d = (hi_i - hi_j) + (lo_i - lo_j) is the correctly rounded FP32 pair vector.  The support test
 // |d|^2 < (3h)^2 is decided in FP32 unless it falls within a rounding band of the cutoff, where it is
 // redone in FP64 from the FP64 positions exactly as the definition states.
-#include "ann_internal.cuh"
+#include "ann_device.cuh"
 
 #include <cmath>
 
@@ -18,98 +18,9 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-__device__ __forceinline__ double wrap_d(double a, double L)
-{
-    if (a < 0.0) a = a + L;
-    if (a >= L) a = a - L;
-    return a;
-}
-
-// x in [+0, L)?  Non-negative doubles order like their bit patterns, so two integer compares decide
-// it; negative values, -0, NaN and values >= L fail.
-__device__ __forceinline__ bool in_box(double x, long long bitsL)
-{
-    long long bx = __double_as_longlong(x);
-    return bx >= 0 && bx < bitsL;
-}
-
 __device__ __forceinline__ int wrapc(int c, int nc) { return c < 0 ? c + nc : (c >= nc ? c - nc : c); }
 
 __device__ __forceinline__ bool stopped(const Bufs &b) { return *(volatile uint32_t *)b.err != 0u; }
-
-// Two-lane FP32 arithmetic (one instruction issues both lanes, each lane rounded as the scalar
-// operation).  The pair passes are issue-bound, and their x/y arithmetic pairs up naturally.
-__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
-__device__ __forceinline__ float2 bc(float s) { return make_float2(s, s); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, f2(-b.x, -b.y)); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
-// 1/sqrt(r2) by the hardware approximation (r2 is a squared pair distance: never subnormal
-// unless two particles coincide, where both forms give +inf).
-__device__ __forceinline__ float rsqrt_approx(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Quintic kernel of Eq. (18) in branch-free form: with t_k = max(k - b, 0),
-//   W = a_d [t3^5 - 6 t2^5 + 15 t1^5],   F = W'(b) / (h r) = a_d/h [-5 t3^4 + 30 t2^4 - 75 t1^4] / r,
-// so that grad_i W_ij = F d_ij.  The constants a_d, -6 a_d, ... are folded on the host.  For true
-// neighbours b < 3 up to FP32 rounding, and t3 needs no clamp (a rounding-negative t3 gives
-// |t3|^4 ~ 1e-28); `clamp3` keeps it for candidates that may lie beyond the support, where it
-// makes W = F = 0 exactly.  (t3, t2) travel as one two-lane value.
-struct KernelPowers {
-    float2 t, q;     // (t3, t2), (t3^4, t2^4)
-    float t1, q1;    // t1, t1^4
-    float rinv;
-};
-
-template <bool clamp3>
-__device__ __forceinline__ KernelPowers kernel_powers(float r2, const DevParams &P)
-{
-    KernelPowers k;
-    k.rinv = rsqrt_approx(r2);
-    float bq = r2 * k.rinv * P.inv_h;
-    k.t = add2(f2(3.f, 2.f), bc(-bq));
-    if (clamp3) k.t.x = fmaxf(k.t.x, 0.f);
-    k.t.y = fmaxf(k.t.y, 0.f);
-    k.t1 = fmaxf(1.f - bq, 0.f);
-    float2 sq = mul2(k.t, k.t);
-    float s1 = k.t1 * k.t1;
-    k.q = mul2(sq, sq);
-    k.q1 = s1 * s1;
-    return k;
-}
-
-__device__ __forceinline__ float kernel_w_of(const KernelPowers &k, const DevParams &P)
-{
-    float2 w = mul2(k.q, k.t);   // (t3^5, t2^5)
-    return fmaf(P.ad, w.x, fmaf(P.kw6, w.y, P.kw15 * (k.q1 * k.t1)));
-}
-
-__device__ __forceinline__ float kernel_f_of(const KernelPowers &k, const DevParams &P)
-{
-    float2 f = mul2(f2(P.kf5, P.kf30), k.q);
-    return fmaf(P.kf75, k.q1, f.x + f.y) * k.rinv;
-}
-
-template <bool clamp3>
-__device__ __forceinline__ void kernel_wf(float r2, const DevParams &P, float &W, float &F, float &rinv)
-{
-    KernelPowers k = kernel_powers<clamp3>(r2, P);
-    W = kernel_w_of(k, P);
-    F = kernel_f_of(k, P);
-    rinv = k.rinv;
-}
-
-template <bool clamp3>
-__device__ __forceinline__ float kernel_w(float r2, const DevParams &P)
-{
-    return kernel_w_of(kernel_powers<clamp3>(r2, P), P);
-}
 
 // FP64 support test of the definition for particles gi and gj: d = minimum image of x_i - x_j
 // (x_i - x_j, then -L or +L when beyond L/2), |d|^2 = d_x*d_x + d_y*d_y, no fused operations.
@@ -222,8 +133,6 @@ __device__ __forceinline__ float2 pair_d(const float4 &a, const float4 &b)
     return add2(sub2(f2(a.x, a.y), f2(b.x, b.y)), sub2(f2(a.z, a.w), f2(b.z, b.w)));
 }
 
-// Squared length, one rounding per product as the support-test band allows.
-__device__ __forceinline__ float len2(float2 d) { return fmaf(d.x, d.x, d.y * d.y); }
 
 // Element of a staged shared-memory array at byte offset o of a 16-byte slot (candidate lists
 // store o = 16 * slot): o / (16 / sizeof(T)) for narrower element types.
@@ -261,8 +170,14 @@ __global__ void __launch_bounds__(256) k_predict(DevParams P, Bufs b)
         double x = b.sx[i] + (double)(P.half_dt * ux);
         double y = b.sy[i] + (double)(P.half_dt * uy);
         if (!(in_box(x, P.bitsL) && in_box(y, P.bitsL))) {   // rare: crossed a face, or not finite
-            x = wrap_d(x, P.L) + 0.0;
-            y = wrap_d(y, P.L) + 0.0;
+            int kx = wrap_count(x, P.L), ky = wrap_count(y, P.L);
+            x = x + 0.0;
+            y = y + 0.0;
+            if (kx | ky) {   // periodic image count of this particle (pathlines)
+                int2 &im = b.img[b.sid[i]];
+                im.x += kx;
+                im.y += ky;
+            }
             if (!(in_box(x, P.bitsL) && in_box(y, P.bitsL) && isfinite(ux) && isfinite(uy))) {
                 atomicOr(b.err, EB_NONFINITE);
                 x = 0.0;
@@ -1095,8 +1010,14 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
         double xn = mxi + (double)stepx;
         double yn = myi + (double)stepy;
         if (!(in_box(xn, P.bitsL) && in_box(yn, P.bitsL))) {   // rare: re-insert (Eq. 30)
-            xn = wrap_d(xn, P.L) + 0.0;
-            yn = wrap_d(yn, P.L) + 0.0;
+            int kx = wrap_count(xn, P.L), ky = wrap_count(yn, P.L);
+            xn = xn + 0.0;
+            yn = yn + 0.0;
+            if (kx | ky) {   // periodic image count of this particle (pathlines)
+                int2 &im = b.img[b.mid[gi]];
+                im.x += kx;
+                im.y += ky;
+            }
         }
         float dn = dhat + P.half_dt * kri;
         if (!(isfinite(unx) && isfinite(uny) && isfinite(dn) && in_box(xn, P.bitsL) &&
@@ -1153,6 +1074,7 @@ __global__ void k_load(DevParams P, Bufs b, const double *x, const double *y, co
     b.sax[i] = 0.f;
     b.say[i] = 0.f;
     b.sid[i] = i;
+    b.img[i] = make_int2(0, 0);   // pathlines start at the loaded (wrapped) positions
 }
 
 template <typename T>
@@ -1207,17 +1129,19 @@ __global__ void __launch_bounds__(256) k_diag_partial(DevParams P, Bufs b, doubl
         double m = P.conservative ? (double)P.mass : rho * (double)b.V[g];
         v[0] += m * ux;
         v[1] += m * uy;
-        v[2] += 0.5 * (ux * ux + uy * uy);
-        v[3] = fmax(v[3], sqrt(ux * ux + uy * uy));
+        double u2 = ux * ux + uy * uy;
+        v[2] += 0.5 * u2;
+        v[3] = fmax(v[3], u2);   // max |u|^2; the square root is taken once, at the end
         v[4] += m;
-        v[5] += sqrt((double)b.sq11[g] * b.sq11[g] + (double)b.sq12[g] * b.sq12[g]);
+        float q1 = b.sq11[g], q2 = b.sq12[g];
+        v[5] += (double)sqrtf(q1 * q1 + q2 * q2);   // FP32 state: q in FP32, summed in FP64
         double nn = (double)b.nnbr[g];
         v[6] += nn;
         v[7] = fmin(v[7], nn);
         v[8] = fmax(v[8], nn);
         double b11 = b.B11[g], b12 = b.B12[g], b22 = b.B22[g];
         double detb = b11 * b22 - b12 * b12;
-        v[9] = fmin(v[9], detb != 0.0 ? 1.0 / detb : 1e300);
+        v[9] = fmin(v[9], detb != 0.0 ? (double)(1.0f / (float)detb) : 1e300);
     }
     for (int q = 0; q < NDIAG; q++) {
         red[threadIdx.x] = v[q];
@@ -1234,16 +1158,27 @@ __global__ void __launch_bounds__(256) k_diag_partial(DevParams P, Bufs b, doubl
     }
 }
 
-__global__ void k_diag_final(const double *part, int nblocks, double *out)
+// One block per quantity: a strided pass over the block partials, then a fixed-order tree.
+__global__ void __launch_bounds__(256) k_diag_final(const double *part, int nblocks, double *out)
 {
-    int q = threadIdx.x;
-    if (q >= NDIAG) return;
-    double acc = (q == 7 || q == 9) ? 1e300 : ((q == 8) ? -1e300 : 0.0);
-    for (int k = 0; k < nblocks; k++) {
+    __shared__ double red[256];
+    int q = blockIdx.x;
+    bool mx = (q == 3 || q == 8), mn = (q == 7 || q == 9);
+    double acc = mn ? 1e300 : (mx ? -1e300 : 0.0);
+    for (int k = threadIdx.x; k < nblocks; k += blockDim.x) {
         double a = part[k * NDIAG + q];
-        acc = (q == 3 || q == 8) ? fmax(acc, a) : ((q == 7 || q == 9) ? fmin(acc, a) : acc + a);
+        acc = mx ? fmax(acc, a) : (mn ? fmin(acc, a) : acc + a);
     }
-    out[q] = acc;
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            double a = red[threadIdx.x], c = red[threadIdx.x + s];
+            red[threadIdx.x] = mx ? fmax(a, c) : (mn ? fmin(a, c) : a + c);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = (q == 3) ? sqrt(red[0]) : red[0];
 }
 
 const char *const kNames[NKERNELS] = {"predict", "cell_keys", "cell_scan", "cell_scatter", "cell_order",
@@ -1359,7 +1294,7 @@ cudaError_t enqueue_diag(const DevParams &P, const Bufs &b, double *partials, in
                          cudaStream_t s)
 {
     k_diag_partial<<<nblocks, 256, 0, s>>>(P, b, partials);
-    k_diag_final<<<1, 32, 0, s>>>(partials, nblocks, out);
+    k_diag_final<<<NDIAG, 256, 0, s>>>(partials, nblocks, out);
     return cudaGetLastError();
 }
 
