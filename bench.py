@@ -258,6 +258,52 @@ def _config(ws):
             "l2": "working set > L2 (no flush needed)"}
 
 
+DIAG_M = 1024          # grid nodes per side of the flow diagnostics (one node per particle)
+DIAG_TRACERS = 10000   # pathline particles
+
+
+def diagnostics_times(B, ctx, n, ic, reps=3):
+    """Wall time (ms, synchronised C-ABI calls) of the flow diagnostics on the present state:
+    gridding + FFT spectrum (first call after a step), then on the cached grid the correlation and
+    the defects; mixing on 64 x 64 bins; unwrapped positions of DIAG_TRACERS particles."""
+    import numpy as np
+
+    quad = ((ic["x"] >= 0.5).astype(np.uint8) + 2 * (ic["y"] >= 0.5).astype(np.uint8)).astype(np.uint8)
+    B.ann_set_colors(ctx, quad)
+    ids = np.arange(0, n, max(n // DIAG_TRACERS, 1))[:DIAG_TRACERS]
+    t = {"grid_and_spectrum_ms": [], "correlation_ms": [], "defects_ms": [], "mixing_ms": [],
+         "pathlines_ms": []}
+
+    def timed(key, fn):
+        t0 = time.perf_counter()
+        fn()
+        t[key].append(1e3 * (time.perf_counter() - t0))
+
+    for r in range(reps + 1):
+        B.ann_step(ctx, 1)   # a new state: the next call grids it afresh
+        timed("grid_and_spectrum_ms", lambda: B.ann_energy_spectrum(ctx, DIAG_M))
+        timed("correlation_ms", lambda: B.ann_vorticity_correlation(ctx, DIAG_M))
+        timed("defects_ms", lambda: B.ann_defects(ctx, DIAG_M))
+        timed("mixing_ms", lambda: B.ann_mixing_index(ctx, 64))
+        timed("pathlines_ms", lambda: B.ann_get_unwrapped(ctx, ids))
+    out = {k: min(v[1:]) for k, v in t.items()}   # the first round allocates and builds tables
+    out.update({"grid": DIAG_M, "tracers": int(ids.size), "mix_bins": 64,
+                "timing": "min of 3 synchronised calls, wall clock"})
+    return out
+
+
+def oracle_grid_ms(nx, M):
+    """The oracle's Shepard gridding (cell list, OpenMP) of the same workload's initial state."""
+    import oracle
+    from oracle import diagnostics as D
+    import sph_inputs as si
+
+    ic = si.jittered_lattice(nx, seed=0)
+    t0 = time.perf_counter()
+    D.grid_shepard(ic["x"], ic["y"], [ic["ux"], ic["uy"], ic["q11"], ic["q12"]], 1.0, 1.3 / nx, M)
+    return 1e3 * (time.perf_counter() - t0), oracle.num_threads()
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -343,6 +389,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_el = time.perf_counter() - t0
     e2e_value = job_throughput(ws, n, e2e_steps, slowest(e2e_el, dist, "cuda"))
+    diag_times = diagnostics_times(B, ctx, n, ic) if rank == 0 else None
     B.ann_destroy(ctx)
 
     if rank != 0:
@@ -386,8 +433,13 @@ def run_ours(args):
         "diag": {"nbr_mean": diag["nbr_mean"], "error_bits": diag["error_bits"],
                  "band_checks": diag["band_checks"], "max_speed": diag["max_speed"]},
     }
+    if diag_times is not None:
+        line["diagnostics"] = diag_times
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(NX)
+        ms, cores = oracle_grid_ms(NX, DIAG_M)
+        line["diagnostics"]["oracle_grid_ms"] = ms
+        line["diagnostics"]["oracle_cores"] = cores
     print(json.dumps(line))
     if dist:
         dist.barrier()
