@@ -111,7 +111,8 @@ int64_t device_bytes(const ann_params &p)
                   + (MAXV / 2) * 4 + 4 + 16 + 4   // candidate lists, counts, split at re-sort, cell
                   + 11 * 4                    // intermediates
                   + 8 * 4                     // recording
-                  + 16 + 8;                   // elastic stress and its divergence
+                  + 16 + 8                    // elastic stress and its divergence
+                  + 8 + 1 + 4;                // image counts, colour, inverse order (diagnostics)
     int64_t tmp = std::max<int64_t>(7 * 8, MAXN * 4) * n;
     return per * n + tmp + 2 * 4 * (ncell + 1) + 4096;
 }
@@ -255,7 +256,7 @@ cudaError_t alloc_all(ann_ctx *c)
     A_(mx, n); A_(my, n); A_(mux, n); A_(muy, n); A_(mq11, n); A_(mq12, n); A_(mdr, n); A_(xi, n); A_(mid, n);
     A_(cell_count, ncell + 1); A_(cell_start, ncell + 1); A_(key, n); A_(rank, n); A_(perm, n);
     A_(nnbr, n); A_(emask, n);
-    A_(vnbr, n * (MAXV / 2)); A_(vcnt, n); A_(xi_ref, n); A_(mkey, n); A_(rebuild, 1); A_(resorts, 1);
+    A_(vnbr, n * (MAXV / 4)); A_(vcnt, n); A_(xi_ref, n); A_(mkey, n); A_(rebuild, 1); A_(resorts, 1);
     A_(sumW, n); A_(V, n); A_(B11, n); A_(B12, n); A_(B22, n); A_(kr, n); A_(dh, n); A_(dhat, n);
     A_(p, n); A_(divx, n); A_(divy, n);
     A_(rec_gu, 4 * n); A_(rec_lap, 2 * n); A_(rec_apd, 2 * n);

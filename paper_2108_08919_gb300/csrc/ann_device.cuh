@@ -63,7 +63,7 @@ __device__ __forceinline__ float rsqrt_approx(float x)
 struct KernelPowers {
     float2 t, q;     // (t3, t2), (t3^4, t2^4)
     float t1, q1;    // t1, t1^4
-    float rinv;
+    float rinv, r;   // 1/|d| and |d|
 };
 
 template <bool clamp3>
@@ -71,7 +71,8 @@ __device__ __forceinline__ KernelPowers kernel_powers(float r2, const DevParams 
 {
     KernelPowers k;
     k.rinv = rsqrt_approx(r2);
-    float bq = r2 * k.rinv * P.inv_h;
+    k.r = r2 * k.rinv;
+    float bq = k.r * P.inv_h;
     k.t = add2(f2(3.f, 2.f), bc(-bq));
     if (clamp3) k.t.x = fmaxf(k.t.x, 0.f);
     k.t.y = fmaxf(k.t.y, 0.f);

@@ -68,7 +68,7 @@ struct Bufs {
     uint32_t *cell_count, *cell_start, *key, *rank, *perm;
     int *nnbr;          // neighbours per particle (exact support test)
     unsigned long long *emask;   // bit k set: candidate k is a neighbour
-    uint32_t *vnbr;     // candidate lists: 16-bit tile slots, two per word, word k of particle g at [k n + g]
+    uint2 *vnbr;        // candidate lists: 16-bit slot byte offsets, four per 64-bit word, word m of particle g at [m n + g]
     int *vcnt;
     uint32_t *rebuild;  // non-zero: this step re-sorts and rebuilds the candidate lists
     uint32_t *resorts;  // number of re-sort steps since the particles were loaded

@@ -488,11 +488,13 @@ __global__ void __launch_bounds__(PT) k_pass_a_resort(DevParams P, Bufs b)
             my[cv * PT] = (uint16_t)(j << 4);   // byte offset of the slot
             cv += cand;
         }
-        uint32_t *out = b.vnbr + gi;
-        for (int k = 0; k < cv; k += 2) {
-            uint32_t lo = my[k * PT];
-            uint32_t hi = (k + 1 < cv) ? my[(k + 1) * PT] : 0xffffu;
-            *out = lo | (hi << 16);
+        uint2 *out = b.vnbr + gi;
+        for (int k = 0; k < cv; k += 4) {
+            uint32_t s0 = my[k * PT];
+            uint32_t s1 = (k + 1 < cv) ? my[(k + 1) * PT] : 0u;
+            uint32_t s2 = (k + 2 < cv) ? my[(k + 2) * PT] : 0u;
+            uint32_t s3 = (k + 3 < cv) ? my[(k + 3) * PT] : 0u;
+            *out = make_uint2(s0 | (s1 << 16), s2 | (s3 << 16));
             out += P.n;
         }
         b.vcnt[gi] = cv;
@@ -507,7 +509,8 @@ __global__ void __launch_bounds__(PT) k_pass_a_resort(DevParams P, Bufs b)
 }
 
 // Occupancy hints of the pair passes (minimum resident blocks of PT threads per SM; 0 leaves the
-// register budget to the compiler) and the list-word prefetch distance of each (1 to 3 words).
+// register budget to the compiler) and the list-word prefetch distance of each (1 to 3 words of
+// four candidates).
 // The defaults are the measured best on GB300 at 1M particles: the register caps they imply
 // (32, 48, 40, 48) raise the resident warps to what the staged shared memory allows, which hides
 // the latency of the list and gather loads better than the instruction savings of more registers.
@@ -527,13 +530,13 @@ __global__ void __launch_bounds__(PT) k_pass_a_resort(DevParams P, Bufs b)
 #define ANN_PF_A 1
 #endif
 #ifndef ANN_PF_B
-#define ANN_PF_B 2
+#define ANN_PF_B 1
 #endif
 #ifndef ANN_PF_C
-#define ANN_PF_C 2
+#define ANN_PF_C 1
 #endif
 #ifndef ANN_PF_D
-#define ANN_PF_D 2
+#define ANN_PF_D 1
 #endif
 #define ANN_BOUNDS(minb) __launch_bounds__(PT, (minb) > 0 ? (minb) : 1)
 #if ANN_MINB_A > 0
@@ -562,37 +565,45 @@ __global__ void __launch_bounds__(PT) k_pass_a_resort(DevParams P, Bufs b)
 constexpr uint32_t SLOT_OFF_MASK = (HCAP - 1) << 4;
 static_assert(((HCAP - 1) << 4) <= 0xffff, "slot offsets must fit 16 bits");
 
-// Visit the candidates of particle gi (c of them, two per list word) in order, keeping the next
-// PF words in flight while the current pair is processed: fn(byte offset of the slot, candidate
-// index).  Word m (candidates 2m, 2m + 1) is loaded only when 2m < c.
+// Visit the candidates of particle gi (c of them, four per 64-bit list word) in order, keeping the
+// next PF words in flight while the current ones are processed: fn(byte offset of the slot,
+// candidate index, bit), bit = the candidate's bit of `em` (nonzero iff set; 0 when em = 0).
+// Word m (candidates 4m .. 4m + 3) is loaded only when 4m < c.
 template <int PF, typename Fn>
-__device__ __forceinline__ void for_each_slot(const uint32_t *list, int n, int gi, int c, Fn &&fn)
+__device__ __forceinline__ void for_each_slot(const uint2 *list, int n, int gi, int c, unsigned long long em, Fn &&fn)
 {
     static_assert(PF >= 1 && PF <= 3, "prefetch distance");
-    const uint32_t *p = list + gi;
-    uint32_t r[PF + 1];   // r[0]: the current word, r[m]: word k/2 + m
+    const uint2 *p = list + gi;
+    uint2 r[PF + 1];   // r[0]: the current word, r[m]: word k/4 + m
 #pragma unroll
-    for (int m = 0; m <= PF; m++) r[m] = (2 * m < c) ? __ldg(p + (size_t)m * n) : 0u;
+    for (int m = 0; m <= PF; m++) r[m] = (4 * m < c) ? __ldg(p + (size_t)m * n) : make_uint2(0u, 0u);
     p += (size_t)(PF + 1) * n;
     int k = 0;
-    for (; k + 1 < c; k += 2) {
-        uint32_t w = r[0];
+    for (; k + 3 < c; k += 4) {
+        uint2 w = r[0];
 #pragma unroll
         for (int m = 0; m < PF; m++) r[m] = r[m + 1];
-        r[PF] = (k + 2 * (PF + 1) < c) ? __ldg(p) : 0u;   // word k/2 + PF + 1
+        r[PF] = (k + 4 * (PF + 1) < c) ? __ldg(p) : make_uint2(0u, 0u);   // word k/4 + PF + 1
         p += n;
-        fn((int)(w & SLOT_OFF_MASK), k);
-        fn((int)((w >> 16) & SLOT_OFF_MASK), k + 1);
+        unsigned b4 = (unsigned)em;
+        em >>= 4;
+        fn((int)(w.x & SLOT_OFF_MASK), k, b4 & 1u);
+        fn((int)((w.x >> 16) & SLOT_OFF_MASK), k + 1, b4 & 2u);
+        fn((int)(w.y & SLOT_OFF_MASK), k + 2, b4 & 4u);
+        fn((int)((w.y >> 16) & SLOT_OFF_MASK), k + 3, b4 & 8u);
     }
-    if (k < c) fn((int)(r[0] & SLOT_OFF_MASK), k);
+    unsigned long long w64 = ((unsigned long long)r[0].y << 32) | r[0].x;
+    for (int t = 0; k < c; k++, t++)   // the last 0 to 3 candidates
+        fn((int)((unsigned)(w64 >> (16 * t)) & SLOT_OFF_MASK), k, (unsigned)(em >> t) & 1u);
 }
 
 // Candidates of particle gi.  Beyond the support the clamped kernel gives W = F = 0 exactly, and
 // adding +0 or -0 leaves an FP32 sum unchanged, so sums over candidates equal sums over neighbours.
 template <int PF, typename Fn>
-__device__ __forceinline__ void for_each_candidate(const DevParams &P, const Bufs &b, int gi, Fn &&fn)
+__device__ __forceinline__ void for_each_candidate(const DevParams &P, const Bufs &b, int gi, unsigned long long em,
+                                                   Fn &&fn)
 {
-    for_each_slot<PF>(b.vnbr, P.n, gi, b.vcnt[gi], fn);
+    for_each_slot<PF>(b.vnbr, P.n, gi, b.vcnt[gi], em, fn);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -628,7 +639,7 @@ __global__ void BOUNDS_A k_pass_a_filter(DevParams P, Bufs b)
         int c = b.vcnt[gi];
         // neighbour bits enter at the top of (mhi:mlo) and move down one place per candidate
         uint32_t mlo = 0u, mhi = 0u;
-        for_each_slot<ANN_PF_A>(b.vnbr, P.n, gi, c, [&](int o, int kc) {
+        for_each_slot<ANN_PF_A>(b.vnbr, P.n, gi, c, 0ull, [&](int o, int, unsigned) {
             float2 d = pair_d(pi, slot_at(pos, o));
             float r2 = len2(d);
             sw += kernel_w<true>(r2, P);
@@ -690,7 +701,7 @@ __global__ void BOUNDS_B k_pass_b(DevParams P, Bufs b)
         float a22 = 0.f;
         float di = b.mdr[gi];   // loaded ahead of the neighbour loop
         const float2 ui = f2(bi.y, bi.z), qi = f2(bi.w, q2i);
-        for_each_candidate<ANN_PF_B>(P, b, gi, [&](int o, int kc) {
+        for_each_candidate<ANN_PF_B>(P, b, gi, 0ull, [&](int o, int, unsigned) {
             float4 bj = slot_at(sb, o);
             float2 d = pair_d(pi, slot_at(sp, o));
             KernelPowers kp = kernel_powers<true>(len2(d), P);
@@ -828,7 +839,7 @@ __global__ void BOUNDS_C k_pass_c(DevParams P, Bufs b)
         float2 gq1 = f2(0.f, 0.f), gq2 = f2(0.f, 0.f), ge1 = f2(0.f, 0.f), ge2 = f2(0.f, 0.f),
                ge3 = f2(0.f, 0.f);
         const float2 qi = f2(bi.z, bi.w);
-        for_each_candidate<ANN_PF_C>(P, b, gi, [&](int o, int kc) {
+        for_each_candidate<ANN_PF_C>(P, b, gi, 0ull, [&](int o, int, unsigned) {
             float4 bj = slot_at(sb, o);
             float2 d = pair_d(pi, slot_at(sp, o));
             KernelPowers kp = kernel_powers<true>(len2(d), P);
@@ -946,11 +957,12 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
         // with kv = 8 nu rho0 / rho_i, and a = B w + (active and elastic terms)
         float irho = 1.f / rho;
         float nrho = -rho, kv = 8.f * P.nu * P.rho0 * irho;
+        float pci = nrho * bi.y;        // paper: -rho_i p_i / rho_i^2
         float k8 = 8.f * P.mu * bi.y;   // conservative: 8 mu / rho_i
         const float2 ui = f2(bi.z, bi.w);
         float2 w = f2(0.f, 0.f), su = f2(0.f, 0.f), sd = f2(0.f, 0.f);
         float sr = 0.f;
-        for_each_candidate<ANN_PF_D>(P, b, gi, [&](int o, int kc) {
+        for_each_candidate<ANN_PF_D>(P, b, gi, em, [&](int o, int, unsigned in) {
             float4 bj = slot_at(sb, o);
             float2 d = pair_d(pi, slot_at(sp, o));
             float r2 = len2(d);
@@ -975,16 +987,14 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
                     w = fma2(e1, bc(g.x), fma2(f2(e1.y, e22), bc(g.y), w));
                 }
             } else {
-                float coef = fmaf(kv, ud * rinv2, nrho * (bi.y + bj.y));
+                float coef = fmaf(kv, ud * rinv2, fmaf(nrho, bj.y, pci));
                 w = fma2(bc(bj.x * F * coef), d, w);
             }
             su = fma2(du, bc(Wv), su);
             // APD sums run over the neighbours only (their terms do not vanish at the support
-            // edge): candidate k is one iff bit k of the mask is set; the bits are consumed in order
-            bool in = (uint32_t)em & 1u;
-            em >>= 1;
+            // edge): `in` is the candidate's bit of the neighbour mask
             if (in) {
-                sr += r2 * kp.rinv;
+                sr += kp.r;
                 sd = fma2(d, bc(rinv2 * kp.rinv), sd);
             }
         });
@@ -1103,9 +1113,9 @@ __global__ void __launch_bounds__(PT) k_export_nbrs(DevParams P, Bufs b, int *co
         int gi = sg[si];
         int k = 0;
         unsigned long long emask = b.emask[gi];
-        for_each_candidate<1>(P, b, gi, [&](int o, int kc) {
+        for_each_candidate<1>(P, b, gi, emask, [&](int o, int, unsigned in) {
             int j = o >> 4;
-            if (((emask >> kc) & 1ull) && j < T.H && k < MAXN) {
+            if (in && j < T.H && k < MAXN) {
                 cols[(size_t)k * P.n + gi] = b.mid[sg[j]];
                 k++;
             }
