@@ -637,18 +637,28 @@ __global__ void BOUNDS_A k_pass_a_filter(DevParams P, Bufs b)
         float4 pi = pos[si];
         float sw = P.W0;
         int c = b.vcnt[gi];
-        // neighbour bits enter at the top of (mhi:mlo) and move down one place per candidate
+        // neighbour bits enter at the top of (mhi:mlo) and move down one place per candidate; the
+        // FP32 test decides outside the rounding band, and a candidate inside it (rare) is only
+        // noted here and decided in FP64 by the second walk below
         uint32_t mlo = 0u, mhi = 0u;
+        bool band = false;
         for_each_slot<ANN_PF_A>(b.vnbr, P.n, gi, c, 0ull, [&](int o, int, unsigned) {
             float2 d = pair_d(pi, slot_at(pos, o));
             float r2 = len2(d);
             sw += kernel_w<true>(r2, P);
-            uint32_t in = in_support(r2, P, b, gi, slot_at(sg, o));
+            uint32_t in = r2 < P.R2lo;
+            band |= (r2 >= P.R2lo) & (r2 < P.R2hi);
             mlo = __funnelshift_r(mlo, mhi, 1);
             mhi = __funnelshift_r(mhi, in, 1);
         });
         unsigned long long mask = ((unsigned long long)mhi << 32) | mlo;
         mask = c > 0 ? mask >> (64 - c) : 0ull;   // candidate k at bit k
+        if (band) {
+            for_each_slot<1>(b.vnbr, P.n, gi, c, 0ull, [&](int o, int kc, unsigned) {
+                float r2 = len2(pair_d(pi, slot_at(pos, o)));
+                if (r2 >= P.R2lo && in_support(r2, P, b, gi, slot_at(sg, o))) mask |= 1ull << kc;
+            });
+        }
         b.nnbr[gi] = __popcll(mask);
         b.emask[gi] = mask;
         b.sumW[gi] = sw;

@@ -298,3 +298,26 @@ def test_late_resort_within_the_step(B, orc):
     # a full step moves dt |u| = 1.55e-3, more than half the skin 0.5 * 0.02 * 3h = 1.2e-3, so
     # every step finds the lists of the previous one stale and re-sorts
     assert d["resorts"] >= 2, d
+
+
+def test_pairs_at_the_cutoff_take_the_fp64_band_test(B, orc):
+    """h = 4/3 dx on an unjittered lattice puts every particle's four lattice neighbours at
+    distance 4 dx = 3h exactly: each pair falls in the FP32 rounding band and is decided by the
+    FP64 definition, first in the re-sort pass, then (nothing moves) in the candidate filter of
+    the following steps.  Neighbour counts equal the oracle's bit for bit."""
+    nx = 64
+    ic = si.jittered_lattice(nx, seed=0, jitter=0.0)
+    p = params(nx, h=4.0 / (3.0 * nx), zeta=0.0)
+    run = GpuRun(B, p, ic)
+    st = oracle_state(ic)
+    P = oracle_params(orc, p, "brute")
+    try:
+        for _ in range(3):
+            run.step(1)
+            st, rec = orc.step(P, st, 1, record=True)
+            assert np.array_equal(run.field("NNBR"), rec["nnbr"])
+        d = B.ann_get_diagnostics(run.ctx)
+    finally:
+        run.close()
+    assert d["band_checks"] >= 3 * 4 * nx * nx, d
+    assert d["resorts"] == 1, d   # steps 2 and 3 ran the candidate filter
