@@ -682,9 +682,9 @@ __global__ void BOUNDS_B k_pass_b(DevParams P, Bufs b)
     __shared__ TileShared ts;
     extern __shared__ __align__(16) unsigned char dsm[];
     float4 *sp = reinterpret_cast<float4 *>(dsm);     // split position
-    float4 *sb = sp + HCAP;                           // (V, ux, uy, q11)
-    float *sq = reinterpret_cast<float *>(sb + HCAP); // q12
-    int *sg = reinterpret_cast<int *>(sq + HCAP);
+    float4 *sb = sp + HCAP;                           // (ux, uy, q11, q12): two-lane pairs in place
+    float *sv = reinterpret_cast<float *>(sb + HCAP); // V
+    int *sg = reinterpret_cast<int *>(sv + HCAP);
     Tile T;
     if (!tile_begin(P, b, ts, T)) {
         if (threadIdx.x == 0) atomicOr(b.err, EB_HALO);
@@ -693,8 +693,8 @@ __global__ void BOUNDS_B k_pass_b(DevParams P, Bufs b)
     for (int t = threadIdx.x; t < T.H; t += PT) {
         SlotInfo s = slot_info(P, b, ts, T, t);
         sp[t] = s.e;
-        sb[t] = make_float4(b.V[s.g], b.mux[s.g], b.muy[s.g], b.mq11[s.g]);
-        sq[t] = b.mq12[s.g];
+        sb[t] = make_float4(b.mux[s.g], b.muy[s.g], b.mq11[s.g], b.mq12[s.g]);
+        sv[t] = b.V[s.g];
         sg[t] = s.g;
     }
     __syncthreads();
@@ -702,7 +702,6 @@ __global__ void BOUNDS_B k_pass_b(DevParams P, Bufs b)
         int si = inner_slot(ts, T, q);
         int gi = sg[si];
         float4 pi = sp[si], bi = sb[si];
-        float q2i = sq[si];
         // two-lane accumulators: (a11, a12), a22; L rows (l00, l01), (l10, l11); Laplacian sums
         // per tensor entry for (q11, q12): (r1xx, r2xx), (r1xy, r2xy), (r1yy, r2yy); div Q rows
         float2 a1 = f2(0.f, 0.f), l0 = f2(0.f, 0.f), l1 = f2(0.f, 0.f);
@@ -710,21 +709,21 @@ __global__ void BOUNDS_B k_pass_b(DevParams P, Bufs b)
         float2 gq1 = f2(0.f, 0.f), gq2 = f2(0.f, 0.f);
         float a22 = 0.f;
         float di = b.mdr[gi];   // loaded ahead of the neighbour loop
-        const float2 ui = f2(bi.y, bi.z), qi = f2(bi.w, q2i);
+        const float2 ui = f2(bi.x, bi.y), qi = f2(bi.z, bi.w);
         for_each_candidate<ANN_PF_B>(P, b, gi, 0ull, [&](int o, int, unsigned) {
             float4 bj = slot_at(sb, o);
             float2 d = pair_d(pi, slot_at(sp, o));
             KernelPowers kp = kernel_powers<true>(len2(d), P);
             float F = kernel_f_of(kp, P);
-            float2 g = mul2(bc(bj.x * F), d);            // V_j grad_i W = (gx, gy)
+            float2 g = mul2(bc(slot_at(sv, o) * F), d);  // V_j grad_i W = (gx, gy)
             float2 mx = mul2(bc(g.x), d);                 // (mxx, mxy)
             float myy = g.y * d.y;
             a1 = sub2(a1, mx);
             a22 -= myy;
-            float2 du = sub2(f2(bj.y, bj.z), ui);         // u_j - u_i
+            float2 du = sub2(f2(bj.x, bj.y), ui);         // u_j - u_i
             l0 = fma2(bc(du.x), g, l0);
             l1 = fma2(bc(du.y), g, l1);
-            float2 dq = sub2(f2(bj.w, slot_at(sq, o)), qi);   // Q_j - Q_i per component
+            float2 dq = sub2(f2(bj.z, bj.w), qi);         // Q_j - Q_i per component
             float2 e = mul2(dq, bc(-(kp.rinv * kp.rinv)));
             rxx = fma2(e, bc(mx.x), rxx);
             rxy = fma2(e, bc(mx.y), rxy);
@@ -752,7 +751,7 @@ __global__ void BOUNDS_B k_pass_b(DevParams P, Bufs b)
         // Q rate, projected on symmetric traceless tensors.  With E = sym(D), w = (D10 - D01)/2:
         //   S_tl = lambda tr(E) Q + 2 c lambda E_tl + (Omega Q - Q Omega) - 2 lambda (Q:E) Q
         //   H_tl = -A Q - C tr(Q^2) Q + K lap Q        (the B term of Eq. 7 is isotropic in 2D)
-        float q1 = bi.w, q2 = q2i;
+        float q1 = bi.z, q2 = bi.w;
         float E12 = 0.5f * (D01 + D10), om = 0.5f * (D10 - D01);
         float QE = q1 * (D00 - D11) + 2.f * q2 * E12;
         float trQ2 = 2.f * (q1 * q1 + q2 * q2);
