@@ -315,6 +315,44 @@ int ann_mixing_index(ann_ctx *ctx, int32_t G, double *index, double *per_species
 int ann_get_unwrapped(ann_ctx *ctx, const int64_t *ids, int64_t k, double *xy);
 
 /*
+ * Batched ensemble: many independent runs (any mix of n and parameters, e.g. the (zeta, K) sweeps
+ * of the paper's results section) advanced together.  Each member is a full context; one
+ * ann_ensemble_step launches a single CUDA graph per step in which every member's step (with its
+ * own re-sort decision) is a branch, so the GPU overlaps the members and its block scheduler
+ * balances their uneven sizes.  Members are dealt round-robin to `groups` branches (members of a
+ * branch run one after the other); ann_ensemble_autotune times the groupings 1, 4, 16, ... and all
+ * members and keeps the fastest.  Every member advances exactly as ann_step would advance it alone
+ * (bit-identical results).
+ */
+#define ANN_ENSEMBLE_MAX 256
+typedef struct ann_ensemble ann_ensemble;
+
+/* Create `members` contexts from params[0 .. members) (each validated as by ann_create).  Errors:
+ * INVALID_ARG, OOM, CUDA, NOT_AVAILABLE; nothing is left allocated on error. */
+int ann_ensemble_create(const ann_params *params, int32_t members, ann_ensemble **out);
+void ann_ensemble_destroy(ann_ensemble *ens);
+
+/* Borrowed handle of member k: load it (ann_set_particles, ann_load_state), read fields and
+ * diagnostics, save it.  Do not destroy it; ann_step on it advances that member alone. */
+int ann_ensemble_member(ann_ensemble *ens, int32_t k, ann_ctx **ctx);
+
+/* Advance every member by nsteps steps (one graph launch per step) and synchronise.  All members
+ * must hold particles (STATE otherwise).  Returns the first member's error status, if any (text
+ * in ann_ensemble_last_error, naming the member); the other members still advanced. */
+int ann_ensemble_step(ann_ensemble *ens, int64_t nsteps);
+
+/* Rebuild the ensemble graph with members dealt to `groups` branches (1 .. members). */
+int ann_ensemble_set_groups(ann_ensemble *ens, int32_t groups);
+
+/* For each candidate grouping (1, 4, 16, ... and all members): one warm-up step, then
+ * trial_steps timed steps (CUDA events on the ensemble stream); keep the fastest.  The trial steps
+ * are real steps (the members advance by them).  groups_out, ms_per_step (may be NULL): the chosen
+ * grouping and its time per ensemble step.  Errors: as ann_ensemble_step, INVALID_ARG. */
+int ann_ensemble_autotune(ann_ensemble *ens, int32_t trial_steps, int32_t *groups_out, double *ms_per_step);
+
+const char *ann_ensemble_last_error(ann_ensemble *ens);
+
+/*
  * Velocity moments without any device allocation.  The paper has no counterpart: this is a
  * service entry point for callers that cannot call cudaMalloc -- a host framework that owns a fixed
  * device memory pool or a hard memory budget and forbids allocations after start-up, or a real-time

@@ -115,6 +115,13 @@ def lib() -> ctypes.CDLL:
         "ann_set_colors": (i32, [vp, vp, i64, i32]),
         "ann_mixing_index": (i32, [vp, i32, _P(ctypes.c_double), _P(ctypes.c_double)]),
         "ann_get_unwrapped": (i32, [vp, _P(ctypes.c_int64), i64, _P(ctypes.c_double)]),
+        "ann_ensemble_create": (i32, [_P(ann_params), i32, _P(vp)]),
+        "ann_ensemble_destroy": (None, [vp]),
+        "ann_ensemble_member": (i32, [vp, i32, _P(vp)]),
+        "ann_ensemble_step": (i32, [vp, i64]),
+        "ann_ensemble_set_groups": (i32, [vp, i32]),
+        "ann_ensemble_autotune": (i32, [vp, i32, _P(ctypes.c_int32), _P(ctypes.c_double)]),
+        "ann_ensemble_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -381,3 +388,55 @@ def ann_get_unwrapped(ctx, ids):
     _check(lib().ann_get_unwrapped(ctx, ids.ctypes.data_as(_P(ctypes.c_int64)), ids.size, _dptr(xy)), ctx,
            "ann_get_unwrapped")
     return xy
+
+
+# ------------------------------------------------------------------ batched ensemble
+
+ENSEMBLE_MAX = 256
+
+
+def _echeck(status: int, ens, what: str):
+    if status < 0:
+        detail = lib().ann_ensemble_last_error(ens).decode() if ens is not None else ""
+        text = lib().ann_status_string(status).decode()
+        raise AnnError(status, f"{what}: {text}" + (f" ({detail})" if detail else ""))
+    return status
+
+
+def ann_ensemble_create(params) -> ctypes.c_void_p:
+    """An ensemble of len(params) members (a list of ann_params)."""
+    arr = (ann_params * len(params))(*params)
+    ens = ctypes.c_void_p()
+    _echeck(lib().ann_ensemble_create(arr, len(params), ctypes.byref(ens)), None, "ann_ensemble_create")
+    return ens
+
+
+def ann_ensemble_destroy(ens) -> None:
+    lib().ann_ensemble_destroy(ens)
+
+
+def ann_ensemble_member(ens, k: int) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _echeck(lib().ann_ensemble_member(ens, int(k), ctypes.byref(ctx)), ens, "ann_ensemble_member")
+    return ctx
+
+
+def ann_ensemble_step(ens, nsteps: int) -> None:
+    _echeck(lib().ann_ensemble_step(ens, int(nsteps)), ens, "ann_ensemble_step")
+
+
+def ann_ensemble_set_groups(ens, groups: int) -> None:
+    _echeck(lib().ann_ensemble_set_groups(ens, int(groups)), ens, "ann_ensemble_set_groups")
+
+
+def ann_ensemble_autotune(ens, trial_steps: int):
+    """(chosen grouping, ms per ensemble step)."""
+    g = ctypes.c_int32()
+    ms = ctypes.c_double()
+    _echeck(lib().ann_ensemble_autotune(ens, int(trial_steps), ctypes.byref(g), ctypes.byref(ms)), ens,
+            "ann_ensemble_autotune")
+    return g.value, ms.value
+
+
+def ann_ensemble_last_error(ens) -> str:
+    return lib().ann_ensemble_last_error(ens).decode()

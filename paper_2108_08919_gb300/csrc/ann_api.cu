@@ -283,31 +283,22 @@ cudaError_t alloc_all(ann_ctx *c)
 
 // The step graph: predict -> set-condition -> IF (re-sort flag) { keys, scan, scatter, cell order,
 // re-sort pass A } ELSE { pass A } -> passes B, C, D.  The branch not taken costs nothing.
-cudaError_t capture(ann_ctx *c)
+// capture_step records one step of context c onto stream s, which is capturing into graph g (the
+// context's own graph, or an ensemble graph holding many contexts); the bodies of the conditional
+// node are captured on the context's aux stream.
+cudaError_t capture_step(ann_ctx *c, cudaStream_t s, cudaGraph_t g)
 {
-    if (c->exec) {
-        cudaGraphExecDestroy(c->exec);
-        c->exec = nullptr;
-    }
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaGraphCreate(&g, 0);
-    if (e) return e;
     cudaGraphConditionalHandle h = 0;
-    e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
-    if (!e) e = cudaStreamBeginCaptureToGraph(c->own, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e) {
-        cudaGraphDestroy(g);
-        return e;
-    }
-    cudaError_t ec = launch_kernel(0, c->P, c->b, c->own);
-    if (!ec) ec = launch_set_condition(c->b, h, c->own);
+    cudaError_t ec = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+    if (!ec) ec = launch_kernel(0, c->P, c->b, s);
+    if (!ec) ec = launch_set_condition(c->b, h, s);
     cudaGraph_t body[2] = {nullptr, nullptr};
     if (!ec) {
         cudaStreamCaptureStatus st;
         const cudaGraphNode_t *deps = nullptr;
         size_t nd = 0;
         cudaGraph_t capg = nullptr;
-        ec = cudaStreamGetCaptureInfo(c->own, &st, nullptr, &capg, &deps, nullptr, &nd);
+        ec = cudaStreamGetCaptureInfo(s, &st, nullptr, &capg, &deps, nullptr, &nd);
         cudaGraphNode_t cn = nullptr;
         if (!ec) {
             // zeroed storage: the parameter struct's union has no default constructor
@@ -323,7 +314,7 @@ cudaError_t capture(ann_ctx *c)
                 body[1] = cp.conditional.phGraph_out[1];
             }
         }
-        if (!ec) ec = cudaStreamUpdateCaptureDependencies(c->own, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (!ec) ec = cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
     }
     for (int k = 0; k < 2 && !ec; k++) {
         ec = cudaStreamBeginCaptureToGraph(c->aux, body[k], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
@@ -337,7 +328,25 @@ cudaError_t capture(ann_ctx *c)
         ec = cudaStreamEndCapture(c->aux, &got);
         if (!ec) ec = el;
     }
-    for (int k = 7; k < NKERNELS && !ec; k++) ec = launch_kernel(k, c->P, c->b, c->own);
+    for (int k = 7; k < NKERNELS && !ec; k++) ec = launch_kernel(k, c->P, c->b, s);
+    return ec;
+}
+
+cudaError_t capture(ann_ctx *c)
+{
+    if (c->exec) {
+        cudaGraphExecDestroy(c->exec);
+        c->exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e) return e;
+    e = cudaStreamBeginCaptureToGraph(c->own, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e) {
+        cudaGraphDestroy(g);
+        return e;
+    }
+    cudaError_t ec = capture_step(c, c->own, g);
     e = cudaStreamEndCapture(c->own, &g);
     if (ec || e) {
         if (g) cudaGraphDestroy(g);
@@ -1187,5 +1196,207 @@ int ann_get_unwrapped(ann_ctx *c, const int64_t *ids, int64_t k, double *xy)
     if (!e) e = cudaStreamSynchronize(c->stream);
     return e ? cuda_fail(c, e, "ann_get_unwrapped") : ANN_OK;
 }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// Batched ensemble: independent contexts stepped by one graph launch per step
+// ------------------------------------------------------------------------------------------------
+
+struct ann_ensemble {
+    std::vector<ann_ctx *> m;
+    cudaStream_t s0 = nullptr;                 // origin stream of the ensemble graph
+    std::vector<cudaStream_t> br;              // branch streams used while capturing
+    cudaGraphExec_t exec = nullptr;
+    int groups = 0;                            // members are dealt round-robin to this many branches
+    std::string last_err;
+};
+
+namespace {
+
+int efail(ann_ensemble *e, int code, const std::string &msg)
+{
+    if (e) e->last_err = msg;
+    return code;
+}
+
+// One graph: the origin forks `groups` branches; branch j steps members j, j + groups, ... one
+// after the other; the branches join the origin at the end.
+cudaError_t build_ensemble_graph(ann_ensemble *E, int groups)
+{
+    if (E->exec) {
+        cudaGraphExecDestroy(E->exec);
+        E->exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e) return e;
+    e = cudaStreamBeginCaptureToGraph(E->s0, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e) {
+        cudaGraphDestroy(g);
+        return e;
+    }
+    std::vector<cudaEvent_t> ev((size_t)groups + 1, nullptr);
+    cudaError_t ec = cudaSuccess;
+    for (auto &x : ev)
+        if (!ec) ec = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    if (!ec) ec = cudaEventRecord(ev[0], E->s0);
+    for (int j = 0; j < groups && !ec; j++) {
+        cudaStream_t s = E->br[(size_t)j];
+        ec = cudaStreamWaitEvent(s, ev[0], 0);
+        for (size_t k = (size_t)j; k < E->m.size() && !ec; k += (size_t)groups) ec = capture_step(E->m[k], s, g);
+        if (!ec) ec = cudaEventRecord(ev[(size_t)j + 1], s);
+        if (!ec) ec = cudaStreamWaitEvent(E->s0, ev[(size_t)j + 1], 0);
+    }
+    e = cudaStreamEndCapture(E->s0, &g);
+    for (auto &x : ev)
+        if (x) cudaEventDestroy(x);
+    if (ec || e) {
+        if (g) cudaGraphDestroy(g);
+        return ec ? ec : e;
+    }
+    e = cudaGraphInstantiate(&E->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (!e) E->groups = groups;
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ann_ensemble_create(const ann_params *params, int32_t members, ann_ensemble **out)
+{
+    if (!params || !out || members < 1 || members > ANN_ENSEMBLE_MAX) return ANN_ERR_INVALID_ARG;
+    *out = nullptr;
+    ann_ensemble *E = new (std::nothrow) ann_ensemble();
+    if (!E) return ANN_ERR_OOM;
+    int st = ANN_OK;
+    for (int k = 0; k < members && !st; k++) {
+        ann_ctx *c = nullptr;
+        st = ann_create(&params[k], &c);
+        if (!st) E->m.push_back(c);
+    }
+    cudaError_t e = cudaSuccess;
+    if (!st) e = cudaStreamCreateWithFlags(&E->s0, cudaStreamNonBlocking);
+    for (int k = 0; k < members && !st && !e; k++) {
+        cudaStream_t s = nullptr;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (!e) E->br.push_back(s);
+    }
+    if (!st && !e) e = build_ensemble_graph(E, members);
+    if (st || e) {
+        if (!st) st = e == cudaErrorMemoryAllocation ? ANN_ERR_OOM : ANN_ERR_CUDA;
+        ann_ensemble_destroy(E);
+        return st;
+    }
+    *out = E;
+    return ANN_OK;
+}
+
+void ann_ensemble_destroy(ann_ensemble *E)
+{
+    if (!E) return;
+    if (E->s0) cudaStreamSynchronize(E->s0);
+    if (E->exec) cudaGraphExecDestroy(E->exec);
+    for (cudaStream_t s : E->br) cudaStreamDestroy(s);
+    if (E->s0) cudaStreamDestroy(E->s0);
+    for (ann_ctx *c : E->m) ann_destroy(c);
+    delete E;
+}
+
+int ann_ensemble_member(ann_ensemble *E, int32_t k, ann_ctx **ctx)
+{
+    if (!E || !ctx || k < 0 || k >= (int32_t)E->m.size()) return ANN_ERR_INVALID_ARG;
+    *ctx = E->m[(size_t)k];
+    return ANN_OK;
+}
+
+int ann_ensemble_set_groups(ann_ensemble *E, int32_t groups)
+{
+    if (!E || groups < 1 || groups > (int32_t)E->m.size()) return ANN_ERR_INVALID_ARG;
+    if (groups == E->groups) return ANN_OK;
+    cudaError_t e = build_ensemble_graph(E, groups);
+    return e ? efail(E, ANN_ERR_CUDA, std::string("ensemble graph: ") + cudaGetErrorString(e)) : ANN_OK;
+}
+
+int ann_ensemble_step(ann_ensemble *E, int64_t nsteps)
+{
+    if (!E || nsteps < 0) return ANN_ERR_INVALID_ARG;
+    for (size_t k = 0; k < E->m.size(); k++)
+        if (!E->m[k]->have_particles)
+            return efail(E, ANN_ERR_STATE, "member " + std::to_string(k) + " has no particles");
+    for (int64_t s = 0; s < nsteps; s++) {
+        cudaError_t e = cudaGraphLaunch(E->exec, E->s0);
+        if (e) return efail(E, ANN_ERR_CUDA, std::string("ensemble graph launch: ") + cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaStreamSynchronize(E->s0);
+    if (e) return efail(E, ANN_ERR_CUDA, std::string("ensemble step: ") + cudaGetErrorString(e));
+    int first = ANN_OK;
+    for (size_t k = 0; k < E->m.size(); k++) {
+        ann_ctx *c = E->m[k];
+        int st = device_status(c);
+        c->steps += nsteps;
+        c->t += nsteps * c->P.dt_d;
+        if (nsteps > 0) {
+            c->s_sorted = true;
+            c->m_current = false;
+            c->grid_step = -1;
+        }
+        if (st && first == ANN_OK) {
+            first = st;
+            E->last_err = "member " + std::to_string(k) + ": " + c->last_err;
+        }
+    }
+    return first;
+}
+
+int ann_ensemble_autotune(ann_ensemble *E, int32_t trial_steps, int32_t *groups_out, double *ms_per_step)
+{
+    if (!E || trial_steps < 1) return ANN_ERR_INVALID_ARG;
+    int nm = (int)E->m.size();
+    std::vector<int> cand;
+    for (int g = 1; g < nm; g *= 4) cand.push_back(g);
+    cand.push_back(nm);
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (!e) e = cudaEventCreate(&b);
+    int best = E->groups;
+    float best_ms = -1.f;
+    int st = ANN_OK;
+    for (int g : cand) {
+        if (e || st) break;
+        e = build_ensemble_graph(E, g);
+        if (e) break;
+        st = ann_ensemble_step(E, 1);   // warm-up (and the first re-sort of fresh members)
+        if (st) break;
+        e = cudaEventRecord(a, E->s0);
+        for (int s2 = 0; s2 < trial_steps && !e; s2++) e = cudaGraphLaunch(E->exec, E->s0);
+        if (!e) e = cudaEventRecord(b, E->s0);
+        if (!e) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (!e) e = cudaEventElapsedTime(&ms, a, b);
+        if (!e) st = ann_ensemble_step(E, 0);   // status of the trial steps
+        for (ann_ctx *c : E->m) {
+            c->steps += trial_steps;
+            c->t += trial_steps * c->P.dt_d;
+        }
+        if (!e && (best_ms < 0.f || ms < best_ms)) {
+            best_ms = ms;
+            best = g;
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e) return efail(E, ANN_ERR_CUDA, std::string("ensemble autotune: ") + cudaGetErrorString(e));
+    if (st) return st;
+    e = build_ensemble_graph(E, best);
+    if (e) return efail(E, ANN_ERR_CUDA, std::string("ensemble graph: ") + cudaGetErrorString(e));
+    if (groups_out) *groups_out = best;
+    if (ms_per_step) *ms_per_step = best_ms / trial_steps;
+    return ANN_OK;
+}
+
+const char *ann_ensemble_last_error(ann_ensemble *E) { return E ? E->last_err.c_str() : ""; }
 
 }  // extern "C"
