@@ -304,6 +304,68 @@ def oracle_grid_ms(nx, M):
     return 1e3 * (time.perf_counter() - t0), oracle.num_threads()
 
 
+ENSEMBLE_MEMBERS = 64
+
+
+def ensemble_members(count=ENSEMBLE_MEMBERS, seed=2021):
+    """The batched-ensemble workload: side nx uniform in [128, 512] (n = nx^2, uneven), zeta
+    log-uniform in [0.01, 0.2], K uniform in [0.01, 0.08]; the other parameters as the 1M set-up."""
+    import math as _m
+
+    import sph_inputs as si
+
+    u = si.uniform53(seed, 3 * count).reshape(count, 3)
+    out = []
+    for k in range(count):
+        nx = int(round(128 + 384 * u[k, 0]))
+        zeta = _m.exp(_m.log(0.01) + u[k, 1] * (_m.log(0.2) - _m.log(0.01)))
+        K = 0.01 + 0.07 * u[k, 2]
+        out.append((nx, zeta, K))
+    return out
+
+
+def ensemble_bench(B, steps=100, trial_steps=10, solo_steps=20):
+    """Aggregate particle-steps/s of the ensemble (one graph launch per step, autotuned grouping)
+    against the same members stepped one after another through their own step graphs."""
+    import numpy as np  # noqa: F401
+
+    import sph_inputs as si
+
+    spec = ensemble_members()
+    plist = []
+    for nx, zeta, K in spec:
+        p = B.ann_default_params(n=nx * nx, h=1.3 / nx, zeta=zeta, K=K, dt_mode=1)
+        plist.append(p)
+    ens = B.ann_ensemble_create(plist)
+    try:
+        total = 0
+        for k, (nx, _, _) in enumerate(spec):
+            ic = si.jittered_lattice(nx, seed=100 + k)
+            B.ann_set_particles(B.ann_ensemble_member(ens, k), ic["x"], ic["y"], ic["ux"], ic["uy"],
+                                ic["q11"], ic["q12"], ic["rho"])
+            total += nx * nx
+        groups, _ = B.ann_ensemble_autotune(ens, trial_steps)
+        B.ann_ensemble_step(ens, 2)
+        t0 = time.perf_counter()
+        B.ann_ensemble_step(ens, steps)
+        el = time.perf_counter() - t0
+        seq = 0.0
+        for k in range(len(spec)):
+            ctx = B.ann_ensemble_member(ens, k)
+            B.ann_step(ctx, 1)
+            t1 = time.perf_counter()
+            B.ann_step(ctx, solo_steps)
+            seq += (time.perf_counter() - t1) / solo_steps
+    finally:
+        B.ann_ensemble_destroy(ens)
+    return {"members": len(spec), "particles": total, "groups": groups, "steps": steps,
+            "value": total * steps / el, "unit": METRIC, "ms_per_step": 1e3 * el / steps,
+            "sequential_value": total / seq, "sequential_ms_per_step": 1e3 * seq,
+            "speedup_vs_sequential": (total * steps / el) / (total / seq),
+            "workload": "64 members, side U[128, 512], zeta log-U[0.01, 0.2], K U[0.01, 0.08], stable dt",
+            "timing": "wall clock around synchronised calls"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -435,6 +497,8 @@ def run_ours(args):
     }
     if diag_times is not None:
         line["diagnostics"] = diag_times
+    if ws == 1 and not args.no_ensemble:
+        line["ensemble"] = ensemble_bench(B)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(NX)
         ms, cores = oracle_grid_ms(NX, DIAG_M)
@@ -455,6 +519,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--profile-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-member ensemble measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
