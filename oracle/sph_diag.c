@@ -166,3 +166,9 @@ void orc_defects(int32_t M, const double *q11, const double *q12, int8_t *m_out,
             else if (m != 0) counts[2]++;
         }
 }
+
+/* W(b_k) of Eq. (18) for an array of b = r/h (the surrogate oracle's neighbour weights). */
+void orc_W_array(int64_t n, const double *b, double h, double *out)
+{
+    for (int64_t k = 0; k < n; k++) out[k] = orc_W(b[k], h);
+}

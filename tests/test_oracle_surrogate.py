@@ -1,0 +1,101 @@
+"""Pins of the surrogate oracle: the hand-derived backward pass against central finite
+differences of the FP64 forward pass, the aggregation and its adjoint, and invariants."""
+import numpy as np
+import pytest
+
+import sph_inputs as si
+
+
+@pytest.fixture(scope="module")
+def S():
+    from oracle import surrogate
+
+    return surrogate
+
+
+def _graph(S, orc, nx=10, seed=3):
+    ic = si.jittered_lattice(nx, seed=seed, jitter=0.2)
+    h = 1.3 * ic["dx"]
+    rp, cols = orc.neighbors(ic["x"], ic["y"], 1.0, h)
+    return ic, S.Graph(ic["x"], ic["y"], 1.0, h, rp, cols)
+
+
+def test_aggregation_mean_and_adjoint(S, orc):
+    ic, G = _graph(S, orc)
+    n = G.n
+    assert np.abs(G.agg(np.full((n, 3), 2.5)) - 2.5).max() < 1e-14   # an SPH mean
+    rng = si.uniform53(5, 2 * 3 * n).reshape(2, n, 3) - 0.5
+    lhs = np.sum(G.agg(rng[0]) * rng[1])
+    rhs = np.sum(rng[0] * G.agg_T(rng[1]))
+    assert lhs == pytest.approx(rhs, rel=1e-13)
+    # each row's weights: W(r)/S with S = W(0) + sum W (Eq. 19's sum), positive, summing to 1
+    assert np.all(G.w > 0) and np.all(G.w_self > 0)
+    assert np.abs(G.w_self + np.bincount(G.rows, weights=G.w, minlength=n) - 1.0).max() < 1e-14
+
+
+def _random_problem(S, orc, seed=0):
+    ic, G = _graph(S, orc)
+    p = S.init_params(seed)
+    for k, b in (("b1", 0), ("b2", 1), ("b3", 2), ("bo", 3)):
+        p[k] = 0.2 * (si.uniform53(seed + 60 + b, p[k].size) - 0.5)
+    ux = 0.3 * (si.uniform53(seed + 50, G.n) - 0.5)
+    uy = 0.3 * (si.uniform53(seed + 70, G.n) - 0.5)
+    x = S.features(G, ic["q11"], ic["q12"], ux, uy, 0.1)
+    t = si.uniform53(seed + 80, 4 * G.n).reshape(G.n, 4) - 0.5
+    return G, p, x, t
+
+
+def test_backward_matches_finite_differences(S, orc):
+    G, p, x, t = _random_problem(S, orc)
+    y, c = S.forward(p, G, x)
+    g = S.backward(p, G, c, y, t)
+    eps = 1e-6
+    for ki, k in enumerate(S.ORDER):
+        flat = p[k].reshape(-1)
+        idx = np.unique((si.uniform53(300 + ki, 6) * flat.size).astype(int))
+        for i in idx:
+            old = flat[i]
+            flat[i] = old + eps
+            lp = S.loss(S.forward(p, G, x)[0], t)
+            flat[i] = old - eps
+            lm = S.loss(S.forward(p, G, x)[0], t)
+            flat[i] = old
+            fd = (lp - lm) / (2 * eps)
+            an = g[k].reshape(-1)[i]
+            assert abs(fd - an) <= 1e-6 * max(abs(fd), 1e-4), (k, i, fd, an)
+
+
+def test_zero_weights_give_the_bias_and_permutation_equivariance(S, orc):
+    G, p, x, t = _random_problem(S, orc, seed=1)
+    z = {k: np.zeros_like(v) for k, v in p.items()}
+    z["bo"] = np.array([0.1, -0.2, 0.3, 0.0])
+    y, _ = S.forward(z, G, x)
+    assert np.array_equal(y, np.tile(z["bo"], (G.n, 1)))
+    # relabel the particles: outputs follow the relabelling
+    ic, _ = _graph(S, orc)
+    perm = np.argsort(si.uniform53(9, G.n))
+    x2, y2 = ic["x"][perm], ic["y"][perm]
+    rp, cols = orc.neighbors(x2, y2, 1.0, 1.3 * ic["dx"])
+    G2 = S.Graph(x2, y2, 1.0, 1.3 * ic["dx"], rp, cols)
+    ya, _ = S.forward(p, G, x)
+    yb, _ = S.forward(p, G2, x[perm])
+    assert np.abs(yb - ya[perm]).max() < 1e-12
+
+
+def test_features_of_a_uniform_state(S, orc):
+    ic, G = _graph(S, orc)
+    n = G.n
+    x = S.features(G, np.full(n, 0.4), np.full(n, -0.1), np.full(n, 0.02), np.full(n, 0.01), 0.1)
+    assert np.abs(x[:, 4:8]).max() < 1e-15 and np.all(x[:, 8:] == 0.0)
+    assert np.allclose(x[:, :4], [0.4, -0.1, 0.2, 0.1], atol=1e-15)
+
+
+def test_first_adam_step_moves_by_the_learning_rate(S):
+    """Step 1: m = (1 - b1) g, v = (1 - b2) g^2, bias correction gives mh = g, vh = g^2, so every
+    parameter moves by lr g / (|g| + eps) = lr sign(g) (up to eps)."""
+    p = {"a": np.array([1.0, -2.0, 0.5])}
+    g = {"a": np.array([0.3, -1e-3, 4.0])}
+    m = {"a": np.zeros(3)}
+    v = {"a": np.zeros(3)}
+    S.adam_step(p, g, m, v, 1, lr=0.01)
+    assert np.allclose(p["a"], [1.0 - 0.01, -2.0 + 0.01, 0.5 - 0.01], rtol=0, atol=1e-7)
