@@ -315,6 +315,26 @@ int ann_mixing_index(ann_ctx *ctx, int32_t G, double *index, double *per_species
 int ann_get_unwrapped(ann_ctx *ctx, const int64_t *ids, int64_t k, double *xy);
 
 /*
+ * BF16 tensor-core GEMMs (5th-generation tensor cores) of the learned surrogate; the paper has no
+ * counterpart.  All pointers are device pointers; BF16 = 16-bit bfloat (1 sign, 8 exponent, 7
+ * mantissa bits); products accumulate in FP32.  The calls are synchronous on `stream` (a
+ * cudaStream_t, NULL for the legacy default stream).  Errors: INVALID_ARG (shapes below), CUDA
+ * (including a tensor-core completion that did not arrive within its bounded wait), OOM.
+ *
+ * ann_bf16_gemm: C[rows x N] = act([A1 | A2] . B^T + bias): A1 rows x K1 and A2 rows x K2 row-major
+ * BF16 (A2 NULL when K2 = 0; K1 + K2 = K), B N x K row-major BF16, bias N FP32 or NULL, act = relu
+ * (1) or identity (0); C rows x N row-major, BF16 (c_bf16 = 1) or FP32 (0; accumulate = 1 adds to
+ * it).  K1, K2 multiples of 16 (K2 may be 0), K in [16, 256]; N a multiple of 16 in [16, 256].
+ *
+ * ann_bf16_gemm_tn: C[K x N] += A^T . B over all rows: A rows x K, B rows x N row-major BF16, C
+ * K x N row-major FP32 (accumulated with atomics, so the order of the FP32 additions varies between
+ * runs).  K in [1, 256]; N a multiple of 16 in [16, 256].
+ */
+int ann_bf16_gemm(const void *A1, int32_t K1, const void *A2, int32_t K2, const void *B, int32_t N, int64_t rows,
+                  const float *bias, int32_t relu, void *C, int32_t c_bf16, int32_t accumulate, void *stream);
+int ann_bf16_gemm_tn(const void *A, int32_t K, const void *B, int32_t N, int64_t rows, float *C, void *stream);
+
+/*
  * Batched ensemble: many independent runs (any mix of n and parameters, e.g. the (zeta, K) sweeps
  * of the paper's results section) advanced together.  Each member is a full context; one
  * ann_ensemble_step launches a single CUDA graph per step in which every member's step (with its

@@ -115,6 +115,8 @@ def lib() -> ctypes.CDLL:
         "ann_set_colors": (i32, [vp, vp, i64, i32]),
         "ann_mixing_index": (i32, [vp, i32, _P(ctypes.c_double), _P(ctypes.c_double)]),
         "ann_get_unwrapped": (i32, [vp, _P(ctypes.c_int64), i64, _P(ctypes.c_double)]),
+        "ann_bf16_gemm": (i32, [vp, i32, vp, i32, vp, i32, i64, vp, i32, vp, i32, i32, vp]),
+        "ann_bf16_gemm_tn": (i32, [vp, i32, vp, i32, i64, vp, vp]),
         "ann_ensemble_create": (i32, [_P(ann_params), i32, _P(vp)]),
         "ann_ensemble_destroy": (None, [vp]),
         "ann_ensemble_member": (i32, [vp, i32, _P(vp)]),
@@ -440,3 +442,36 @@ def ann_ensemble_autotune(ens, trial_steps: int):
 
 def ann_ensemble_last_error(ens) -> str:
     return lib().ann_ensemble_last_error(ens).decode()
+
+
+# ------------------------------------------------------------------ BF16 tensor-core GEMMs
+
+
+def _dev(t):
+    if t is None:
+        return None
+    if not (hasattr(t, "data_ptr") and getattr(t, "is_cuda", False)):
+        raise ValueError("GEMM operands must be CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def ann_bf16_gemm(A1, B, C, A2=None, bias=None, relu=False, accumulate=False, stream=None) -> None:
+    """C = act([A1 | A2] B^T + bias) with bfloat16 CUDA tensors A1 (rows x K1), A2 (rows x K2),
+    B (N x K); C (rows x N) bfloat16 or float32 (accumulate adds to a float32 C)."""
+    rows, K1 = A1.shape
+    K2 = A2.shape[1] if A2 is not None else 0
+    N = B.shape[0]
+    c_bf16 = int(str(C.dtype).endswith("bfloat16"))
+    handle = getattr(stream, "cuda_stream", stream) if stream is not None else 0
+    st = lib().ann_bf16_gemm(_dev(A1), K1, _dev(A2), K2, _dev(B), N, rows, _dev(bias), int(bool(relu)), _dev(C),
+                             c_bf16, int(bool(accumulate)), ctypes.c_void_p(int(handle) if handle else 0))
+    _check(st, None, "ann_bf16_gemm")
+
+
+def ann_bf16_gemm_tn(A, B, C, stream=None) -> None:
+    """C += A^T B with bfloat16 CUDA tensors A (rows x K), B (rows x N) and float32 C (K x N)."""
+    rows, K = A.shape
+    N = B.shape[1]
+    handle = getattr(stream, "cuda_stream", stream) if stream is not None else 0
+    st = lib().ann_bf16_gemm_tn(_dev(A), K, _dev(B), N, rows, _dev(C), ctypes.c_void_p(int(handle) if handle else 0))
+    _check(st, None, "ann_bf16_gemm_tn")

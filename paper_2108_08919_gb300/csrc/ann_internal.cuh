@@ -126,6 +126,13 @@ cudaError_t enqueue_correlation(int M, double L, const double *grid, int all_ori
 cudaError_t enqueue_defects(int M, const double *grid, signed char *map, unsigned long long *counts, cudaStream_t s);
 cudaError_t enqueue_mixing(const DevParams &P, const Bufs &b, const unsigned char *colors, int G, int S,
                            unsigned *cnt, cudaStream_t s);
+// BF16 tensor-core GEMMs of the surrogate (ann_mlp.cu).  K, N multiples of 16 in [16, 256].
+bool gemm_shape_ok(int K, int N);
+cudaError_t enqueue_gemm_nt(const void *A1, int K1, const void *A2, int K2, const void *B, int N, int rows,
+                            const float *bias, int relu, void *C, int c_bf16, int accumulate, unsigned *err,
+                            int max_ctas, cudaStream_t s);
+cudaError_t enqueue_gemm_tn(const void *A, int K, const void *B, int N, int rows, float *C, unsigned *err,
+                            int max_ctas, cudaStream_t s);
 cudaError_t enqueue_unwrapped(const DevParams &P, const Bufs &b, int *inv, const long long *ids, int k, double *xy,
                               cudaStream_t s);
 
