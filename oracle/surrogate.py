@@ -12,7 +12,12 @@ Graph and weights.  N(i): the neighbours of particle i (|x_i - x_j| < 3h, as in 
 SPH weights normalised per row with the particle itself included (Eqs. 18, 19):
     w_ii = W(0) / S_i,  w_ij = W(|x_i - x_j|) / S_i,  S_i = W(0) + sum_{j in N(i)} W(|x_i - x_j|)
     agg(f)_i = w_ii f_i + sum_{j in N(i)} w_ij f_j          (an SPH mean; agg(const) = const)
-Features (16 per particle): r_i = (Q11, Q12, ux / us, uy / us); x_i = (r_i, agg(r)_i - r_i, 0 x 8).
+Features (16 per particle): r_i = (Q11, Q12, ux / us, uy / us) and the method's own tendencies at
+the last step, scaled to increments over the k steps the network spans:
+    x_i = (r_i, agg(r)_i - r_i, a_i k dt / ys_u, (lap Q)_i Gamma K k dt / ys_q, (grad u)_i k dt)
+with a the acceleration (Eq. 23), lap Q the corrected Laplacian of Q11, Q12 (Eq. 21) and grad u the
+corrected velocity gradient D_ab = du_a/dx_b in the order xx, xy, yx, yy (Eq. 20).  The network so
+learns the k-step increment as a correction on top of what the tendencies already predict.
 Layers (relu, width 128, messages of width 32):
     h1 = relu(W1 [x ; agg(x)] + b1)                 W1: 128 x 32
     z1 = P1 h1,  h2 = relu(W2 [h1 ; agg(z1)] + b2)  P1: 32 x 128, W2: 128 x 160
@@ -101,11 +106,16 @@ class Graph:
         return out
 
 
-def features(G: Graph, q11, q12, ux, uy, us):
+def features(G: Graph, q11, q12, ux, uy, tend, us, kdt, gamma_k, ys_q, ys_u):
+    """tend: (n, 8) = (ax, ay, lapQ11, lapQ12, D_xx, D_xy, D_yx, D_yy) of the last step."""
     r = np.stack([q11, q12, ux / us, uy / us], axis=1)
+    tend = np.asarray(tend, dtype=np.float64)
     x = np.zeros((G.n, F0))
     x[:, :4] = r
     x[:, 4:8] = G.agg(r) - r
+    x[:, 8:10] = tend[:, 0:2] * (kdt / ys_u)
+    x[:, 10:12] = tend[:, 2:4] * (gamma_k * kdt / ys_q)
+    x[:, 12:16] = tend[:, 4:8] * kdt
     return x
 
 

@@ -40,7 +40,8 @@ def _random_problem(S, orc, seed=0):
         p[k] = 0.2 * (si.uniform53(seed + 60 + b, p[k].size) - 0.5)
     ux = 0.3 * (si.uniform53(seed + 50, G.n) - 0.5)
     uy = 0.3 * (si.uniform53(seed + 70, G.n) - 0.5)
-    x = S.features(G, ic["q11"], ic["q12"], ux, uy, 0.1)
+    tend = si.uniform53(seed + 90, 8 * G.n).reshape(G.n, 8) - 0.5
+    x = S.features(G, ic["q11"], ic["q12"], ux, uy, tend, 0.1, 8e-4, 0.02, 0.01, 0.005)
     t = si.uniform53(seed + 80, 4 * G.n).reshape(G.n, 4) - 0.5
     return G, p, x, t
 
@@ -85,9 +86,15 @@ def test_zero_weights_give_the_bias_and_permutation_equivariance(S, orc):
 def test_features_of_a_uniform_state(S, orc):
     ic, G = _graph(S, orc)
     n = G.n
-    x = S.features(G, np.full(n, 0.4), np.full(n, -0.1), np.full(n, 0.02), np.full(n, 0.01), 0.1)
-    assert np.abs(x[:, 4:8]).max() < 1e-15 and np.all(x[:, 8:] == 0.0)
+    tend = np.tile([2.0, -1.0, 3.0, 4.0, 0.5, 0.25, -0.5, 1.0], (n, 1))
+    x = S.features(G, np.full(n, 0.4), np.full(n, -0.1), np.full(n, 0.02), np.full(n, 0.01), tend,
+                   0.1, 8e-4, 0.02, 0.01, 0.005)
+    assert np.abs(x[:, 4:8]).max() < 1e-15
     assert np.allclose(x[:, :4], [0.4, -0.1, 0.2, 0.1], atol=1e-15)
+    # tendencies scaled to increments over k dt: a k dt / ys_u, lap Q Gamma K k dt / ys_q, D k dt
+    want = [2 * 8e-4 / 0.005, -8e-4 / 0.005, 3 * 0.02 * 8e-4 / 0.01, 4 * 0.02 * 8e-4 / 0.01,
+            0.5 * 8e-4, 0.25 * 8e-4, -0.5 * 8e-4, 8e-4]
+    assert np.allclose(x[:, 8:], want, rtol=1e-14, atol=0)
 
 
 def test_first_adam_step_moves_by_the_learning_rate(S):
