@@ -48,7 +48,7 @@ class OrcParams(ctypes.Structure):
 class OrcRecord(ctypes.Structure):
     _fields_ = [(name, _dp) for name in (
         "sumW", "V", "B11", "B12", "B22", "gradu", "lapQ11", "lapQ12", "k", "rho_half", "rho_hat",
-        "p", "divQx", "divQy", "ax", "ay", "apdx", "apdy", "trace_m")] + [
+        "p", "divQx", "divQy", "ax", "ay", "apdx", "apdy", "trace_m", "qrate11", "qrate12")] + [
         ("nnbr", _ip), ("c0", _dp)]
 
 
@@ -352,7 +352,7 @@ def apd(nb: Nbrs, ux, uy, dt):
 
 STATE_FIELDS = ("x", "y", "ux", "uy", "q11", "q12", "rho", "ax", "ay")
 RECORD_FIELDS = ("sumW", "V", "B11", "B12", "B22", "gradu", "lapQ11", "lapQ12", "k", "rho_half",
-                 "rho_hat", "p", "divQx", "divQy", "ax", "ay", "apdx", "apdy", "trace_m")
+                 "rho_hat", "p", "divQx", "divQy", "ax", "ay", "apdx", "apdy", "trace_m", "qrate11", "qrate12")
 
 
 def step(params: OrcParams, state: dict, nsteps: int = 1, record: bool = False):

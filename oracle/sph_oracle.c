@@ -93,6 +93,7 @@ typedef struct {
     double *ax, *ay;
     double *apdx, *apdy;
     double *trace_m;        /* trace of m = S + Gamma H before projection */
+    double *qrate11, *qrate12;  /* the projected Q rate m of Eq. (24) (dQ/dt of the step) */
     int32_t *nnbr;
     double *c0;             /* scalar */
 } orc_record;
@@ -800,6 +801,8 @@ int orc_step(const orc_params *P, int64_t n, double *x, double *y, double *ux, d
             orc_q_rate(P, q11[i], q12[i], D, lQ, &m11, &m12, &trm[i], H);
             qn11[i] = q11[i] + dt * m11;
             qn12[i] = q12[i] + dt * m12;
+            if (rec && rec->qrate11) rec->qrate11[i] = m11;   /* the last step's values remain */
+            if (rec && rec->qrate12) rec->qrate12[i] = m12;
             orc_elastic_stress(P, q11[i], q12[i], H, Pe);
             pel[3 * i] = Pe[0][0];
             pel[3 * i + 1] = Pe[0][1];

@@ -13,18 +13,21 @@ SPH weights normalised per row with the particle itself included (Eqs. 18, 19):
     w_ii = W(0) / S_i,  w_ij = W(|x_i - x_j|) / S_i,  S_i = W(0) + sum_{j in N(i)} W(|x_i - x_j|)
     agg(f)_i = w_ii f_i + sum_{j in N(i)} w_ij f_j          (an SPH mean; agg(const) = const)
 Features (16 per particle): r_i = (Q11, Q12, ux / us, uy / us) and the method's own tendencies at
-the last step, scaled to increments over the k steps the network spans:
-    x_i = (r_i, agg(r)_i - r_i, a_i k dt / ys_u, (lap Q)_i Gamma K k dt / ys_q, (grad u)_i k dt)
-with a the acceleration (Eq. 23), lap Q the corrected Laplacian of Q11, Q12 (Eq. 21) and grad u the
-corrected velocity gradient D_ab = du_a/dx_b in the order xx, xy, yx, yy (Eq. 20).  The network so
-learns the k-step increment as a correction on top of what the tendencies already predict.
+the last step -- the acceleration a (Eq. 23), the projected Q rate m (Eq. 24), the corrected
+Laplacian of Q11, Q12 (Eq. 21), and from the corrected velocity gradient D (Eq. 20) the divergence
+D_xx + D_yy and the vorticity D_yx - D_xy -- scaled to increments over the k steps it spans:
+    x_i = (r_i, agg(r)_i - r_i, a k dt / ys_u, m k dt / ys_q, (lap Q) Gamma K k dt / ys_q,
+           (div u, vort u) k dt)
+Prediction: the explicit k-step Euler increment of the tendencies plus the network's correction,
+    (dQ11, dQ12, dux, duy) = k dt (m11, m12, ax, ay) + (ys_q y0, ys_q y1, ys_u y2, ys_u y3),
+so an untrained network (y = 0) reproduces the Euler macro-step and training learns what it misses.
 Layers (relu, width 128, messages of width 32):
     h1 = relu(W1 [x ; agg(x)] + b1)                 W1: 128 x 32
     z1 = P1 h1,  h2 = relu(W2 [h1 ; agg(z1)] + b2)  P1: 32 x 128, W2: 128 x 160
     z2 = P2 h2,  h3 = relu(W3 [h2 ; agg(z2)] + b3)  P2: 32 x 128, W3: 128 x 160
     y = Wo h3 + bo                                   Wo: 4 x 128
-Prediction: (dQ11, dQ12, dux, duy) = (ys_q y0, ys_q y1, ys_u y2, ys_u y3).
-Loss: mean over particles and the 4 outputs of (y - t)^2, t = the normalised true increments.
+Loss: mean over particles and the 4 outputs of (y - t)^2, t = the normalised residual
+(true increment - Euler increment) / ys.
 """
 from __future__ import annotations
 
@@ -106,17 +109,34 @@ class Graph:
         return out
 
 
+TENDENCIES = ("ax", "ay", "m11", "m12", "lapQ11", "lapQ12", "div_u", "vort_u")
+
+
 def features(G: Graph, q11, q12, ux, uy, tend, us, kdt, gamma_k, ys_q, ys_u):
-    """tend: (n, 8) = (ax, ay, lapQ11, lapQ12, D_xx, D_xy, D_yx, D_yy) of the last step."""
+    """tend: (n, 8) tendencies of the last step in the order of TENDENCIES."""
     r = np.stack([q11, q12, ux / us, uy / us], axis=1)
     tend = np.asarray(tend, dtype=np.float64)
     x = np.zeros((G.n, F0))
     x[:, :4] = r
     x[:, 4:8] = G.agg(r) - r
     x[:, 8:10] = tend[:, 0:2] * (kdt / ys_u)
-    x[:, 10:12] = tend[:, 2:4] * (gamma_k * kdt / ys_q)
-    x[:, 12:16] = tend[:, 4:8] * kdt
+    x[:, 10:12] = tend[:, 2:4] * (kdt / ys_q)
+    x[:, 12:14] = tend[:, 4:6] * (gamma_k * kdt / ys_q)
+    x[:, 14:16] = tend[:, 6:8] * kdt
     return x
+
+
+def euler_increment(tend, kdt):
+    """k dt (m11, m12, ax, ay): the explicit k-step increment the network corrects."""
+    tend = np.asarray(tend, dtype=np.float64)
+    return kdt * np.stack([tend[:, 2], tend[:, 3], tend[:, 0], tend[:, 1]], axis=1)
+
+
+def tendencies_from_record(rec):
+    """The 8 tendencies of TENDENCIES from an oracle step record (``step(..., record=True)``)."""
+    gu = rec["gradu"].reshape(-1, 4)
+    return np.stack([rec["ax"], rec["ay"], rec["qrate11"], rec["qrate12"], rec["lapQ11"], rec["lapQ12"],
+                     gu[:, 0] + gu[:, 3], gu[:, 2] - gu[:, 1]], axis=1)
 
 
 def relu(a):

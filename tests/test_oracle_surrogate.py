@@ -91,10 +91,28 @@ def test_features_of_a_uniform_state(S, orc):
                    0.1, 8e-4, 0.02, 0.01, 0.005)
     assert np.abs(x[:, 4:8]).max() < 1e-15
     assert np.allclose(x[:, :4], [0.4, -0.1, 0.2, 0.1], atol=1e-15)
-    # tendencies scaled to increments over k dt: a k dt / ys_u, lap Q Gamma K k dt / ys_q, D k dt
-    want = [2 * 8e-4 / 0.005, -8e-4 / 0.005, 3 * 0.02 * 8e-4 / 0.01, 4 * 0.02 * 8e-4 / 0.01,
-            0.5 * 8e-4, 0.25 * 8e-4, -0.5 * 8e-4, 8e-4]
+    # tendencies scaled to increments over k dt: a k dt / ys_u, m k dt / ys_q,
+    # lap Q Gamma K k dt / ys_q, (div u, vort u) k dt
+    want = [2 * 8e-4 / 0.005, -8e-4 / 0.005, 3 * 8e-4 / 0.01, 4 * 8e-4 / 0.01,
+            0.5 * 0.02 * 8e-4 / 0.01, 0.25 * 0.02 * 8e-4 / 0.01, -0.5 * 8e-4, 8e-4]
     assert np.allclose(x[:, 8:], want, rtol=1e-14, atol=0)
+    e = S.euler_increment(tend, 8e-4)
+    assert np.allclose(e, [3 * 8e-4, 4 * 8e-4, 2 * 8e-4, -8e-4], rtol=1e-15, atol=0)
+
+
+def test_recorded_q_rate_is_the_step_increment_over_dt(orc, S):
+    """The oracle's recorded Q rate (Eq. 24's m) equals (Q^{n+1} - Q^n) / dt of the step, and the
+    tendencies assembled from a record follow the velocity-gradient convention D_ab = du_a/dx_b."""
+    ic = si.jittered_lattice(16, seed=1)
+    P = orc.make_params(h=1.3 / 16)
+    st = {k: ic[k] for k in ("x", "y", "ux", "uy", "q11", "q12", "rho")}
+    out, rec = orc.step(P, st, 1, record=True)
+    for c in ("11", "12"):
+        m = (out["q" + c] - ic["q" + c]) / P.dt
+        assert np.abs(rec["qrate" + c] - m).max() <= 1e-11 * np.abs(m).max()
+    tnd = S.tendencies_from_record(rec)
+    gu = rec["gradu"].reshape(-1, 4)
+    assert np.array_equal(tnd[:, 6], gu[:, 0] + gu[:, 3]) and np.array_equal(tnd[:, 7], gu[:, 2] - gu[:, 1])
 
 
 def test_first_adam_step_moves_by_the_learning_rate(S):
