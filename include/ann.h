@@ -129,7 +129,7 @@ typedef struct ann_diag {
 
 /* Field identifiers for ann_get_field.  Element type: FP64 for ANN_FIELD_X/Y, int32 for
  * ANN_FIELD_NNBR, FP32 otherwise.  Fields after ANN_FIELD_AY are values of the last evaluated
- * step (at the midpoint configuration); the GRADU/LAPQ/APD ones need ann_set_record(ctx, 1). */
+ * step (at the midpoint configuration); the GRADU/LAPQ/APD/QRATE ones need ann_set_record(ctx, 1). */
 enum ann_field {
     ANN_FIELD_X = 0, ANN_FIELD_Y, ANN_FIELD_UX, ANN_FIELD_UY, ANN_FIELD_Q11, ANN_FIELD_Q12,
     ANN_FIELD_DRHO,        /* rho/rho0 - 1 */
@@ -144,6 +144,7 @@ enum ann_field {
     ANN_FIELD_GRADU_XX, ANN_FIELD_GRADU_XY, ANN_FIELD_GRADU_YX, ANN_FIELD_GRADU_YY, /* du_a/dx_b */
     ANN_FIELD_LAPQ11, ANN_FIELD_LAPQ12,
     ANN_FIELD_APDX, ANN_FIELD_APDY,
+    ANN_FIELD_QRATE11, ANN_FIELD_QRATE12,   /* the projected Q rate m of Eq. (24), dQ/dt of the step */
     ANN_FIELD_COUNT
 };
 
@@ -333,6 +334,67 @@ int ann_get_unwrapped(ann_ctx *ctx, const int64_t *ids, int64_t k, double *xy);
 int ann_bf16_gemm(const void *A1, int32_t K1, const void *A2, int32_t K2, const void *B, int32_t N, int64_t rows,
                   const float *bias, int32_t relu, void *C, int32_t c_bf16, int32_t accumulate, void *stream);
 int ann_bf16_gemm_tn(const void *A, int32_t K, const void *B, int32_t N, int64_t rows, float *C, void *stream);
+
+/*
+ * Learned coarse-step surrogate (the paper has no learned component; this is the project's).  A
+ * message-passing MLP over the SPH neighbour graph predicts the increments of Q and u over k
+ * steps; it is trained on the GPU by the project's own forward and backward kernels (BF16
+ * tensor-core GEMMs with FP32 accumulation, FP32 Adam on master weights).  Network, with N(i) the
+ * neighbours (|x_i - x_j| < 3h) and agg(f)_i = (W(0) f_i + sum_{j in N(i)} W_ij f_j) / S_i,
+ * S_i = W(0) + sum_j W_ij (Eqs. 18, 19):
+ *   x_i = (r_i, agg(r)_i - r_i, a k dt / ys_u, m k dt / ys_q, lapQ Gamma K k dt / ys_q,
+ *          (div u, vort u) k dt),  r = (Q11, Q12, ux / us, uy / us),
+ *   with the tendencies of the last step: the acceleration a (Eq. 23), the projected Q rate m
+ *   (Eq. 24), the corrected Laplacian of Q11, Q12 (Eq. 21), and the divergence D_xx + D_yy and
+ *   vorticity D_yx - D_xy of the corrected velocity gradient D (Eq. 20)
+ *   h1 = relu(W1 [x ; agg(x)] + b1),  z1 = P1 h1,  h2 = relu(W2 [h1 ; agg(z1)] + b2),
+ *   z2 = P2 h2,  h3 = relu(W3 [h2 ; agg(z2)] + b3),  y = Wo h3 + bo
+ * with W1 128 x 32, P1, P2 32 x 128, W2, W3 128 x 160, Wo 4 x 128.  Parameters are one FP32 array
+ * of ANN_SG_PARAMS values in the order W1, b1, P1, W2, b2, P2, W3, b3, Wo, bo (row-major).
+ * Prediction over k steps: the explicit increment plus the network's correction,
+ * dQ = k dt m + ys_q (y0, y1), du = k dt a + ys_u (y2, y3); positions advance by k dt (u + u') / 2.  Errors: INVALID_ARG, STATE (nothing loaded), OOM, CUDA (including a
+ * tensor-core wait that timed out), NOT_AVAILABLE.
+ */
+#define ANN_SG_PARAMS 54148
+typedef struct ann_surrogate ann_surrogate;
+
+/* A network for up to n_max particles (device buffers sized for it); parameters all 0. */
+int ann_surrogate_create(int64_t n_max, ann_surrogate **out);
+void ann_surrogate_destroy(ann_surrogate *sg);
+
+/* Host FP32 parameters in and out (ANN_SG_PARAMS values); setting them resets the optimiser. */
+int ann_surrogate_set_params(ann_surrogate *sg, const float *params);
+int ann_surrogate_get_params(ann_surrogate *sg, float *params);
+
+/* Velocity scale us of the inputs, increment scales ys_q, ys_u of the outputs (all > 0), and the
+ * number of steps k >= 1 the network spans (default 8). */
+int ann_surrogate_set_scales(ann_surrogate *sg, double us, double ys_q, double ys_u, int32_t k);
+
+/* Take the graph and the features of ctx's present state (a neighbour search at the present
+ * positions; afterwards the context's next step re-sorts).  tend: host n x 8 FP32, component-major
+ * (ax, ay, m11, m12, lapQ11, lapQ12, div u, vort u; component c of particle ID i at c n + i), or
+ * NULL to take them from the context's last step, which must have run with ann_set_record(ctx, 1)
+ * (STATE otherwise). */
+int ann_surrogate_load(ann_surrogate *sg, ann_ctx *ctx, const float *tend);
+
+/* Network outputs y of the loaded state: host n x 4 FP32, ID order (may be NULL). */
+int ann_surrogate_forward(ann_surrogate *sg, float *y);
+
+/* Forward and backward against targets t (host n x 4 FP32, ID order): *loss = mean (y - t)^2 over
+ * the n x 4 outputs; gradients kept for ann_surrogate_adam and copied to grads (host,
+ * ANN_SG_PARAMS FP32, may be NULL). */
+int ann_surrogate_gradients(ann_surrogate *sg, const float *target, double *loss, float *grads);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with the last gradients. */
+int ann_surrogate_adam(ann_surrogate *sg, double lr);
+
+/* Advance ctx by the network's k steps with one evaluation: load (tend as for ann_surrogate_load),
+ * forward, and replace the context's state by the prediction (t and the step count advance by k;
+ * accelerations restart from 0, so the next jump needs a recorded plain step first; periodic image
+ * counts follow the particles). */
+int ann_surrogate_jump(ann_surrogate *sg, ann_ctx *ctx, const float *tend);
+
+const char *ann_surrogate_last_error(ann_surrogate *sg);
 
 /*
  * Batched ensemble: many independent runs (any mix of n and parameters, e.g. the (zeta, K) sweeps

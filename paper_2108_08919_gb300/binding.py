@@ -22,7 +22,7 @@ DT_FIXED, DT_STABLE = 0, 1
 
 FIELDS = ["X", "Y", "UX", "UY", "Q11", "Q12", "DRHO", "AX", "AY", "SUMW", "V", "B11", "B12", "B22",
           "K", "DRHO_HALF", "DRHO_HAT", "P", "DIVQX", "DIVQY", "NNBR", "GRADU_XX", "GRADU_XY",
-          "GRADU_YX", "GRADU_YY", "LAPQ11", "LAPQ12", "APDX", "APDY"]
+          "GRADU_YX", "GRADU_YY", "LAPQ11", "LAPQ12", "APDX", "APDY", "QRATE11", "QRATE12"]
 FIELD_ID = {name: k for k, name in enumerate(FIELDS)}
 
 
@@ -117,6 +117,17 @@ def lib() -> ctypes.CDLL:
         "ann_get_unwrapped": (i32, [vp, _P(ctypes.c_int64), i64, _P(ctypes.c_double)]),
         "ann_bf16_gemm": (i32, [vp, i32, vp, i32, vp, i32, i64, vp, i32, vp, i32, i32, vp]),
         "ann_bf16_gemm_tn": (i32, [vp, i32, vp, i32, i64, vp, vp]),
+        "ann_surrogate_create": (i32, [i64, _P(vp)]),
+        "ann_surrogate_destroy": (None, [vp]),
+        "ann_surrogate_set_params": (i32, [vp, _P(ctypes.c_float)]),
+        "ann_surrogate_get_params": (i32, [vp, _P(ctypes.c_float)]),
+        "ann_surrogate_set_scales": (i32, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, i32]),
+        "ann_surrogate_load": (i32, [vp, vp, _P(ctypes.c_float)]),
+        "ann_surrogate_forward": (i32, [vp, _P(ctypes.c_float)]),
+        "ann_surrogate_gradients": (i32, [vp, _P(ctypes.c_float), _P(ctypes.c_double), _P(ctypes.c_float)]),
+        "ann_surrogate_adam": (i32, [vp, ctypes.c_double]),
+        "ann_surrogate_jump": (i32, [vp, vp, _P(ctypes.c_float)]),
+        "ann_surrogate_last_error": (ctypes.c_char_p, [vp]),
         "ann_ensemble_create": (i32, [_P(ann_params), i32, _P(vp)]),
         "ann_ensemble_destroy": (None, [vp]),
         "ann_ensemble_member": (i32, [vp, i32, _P(vp)]),
@@ -475,3 +486,87 @@ def ann_bf16_gemm_tn(A, B, C, stream=None) -> None:
     handle = getattr(stream, "cuda_stream", stream) if stream is not None else 0
     st = lib().ann_bf16_gemm_tn(_dev(A), K, _dev(B), N, rows, _dev(C), ctypes.c_void_p(int(handle) if handle else 0))
     _check(st, None, "ann_bf16_gemm_tn")
+
+
+# ------------------------------------------------------------------ learned surrogate
+
+SG_PARAMS = 54148
+_fp = lambda a: a.ctypes.data_as(_P(ctypes.c_float))  # noqa: E731
+
+
+def _scheck(status: int, sg, what: str):
+    if status < 0:
+        detail = lib().ann_surrogate_last_error(sg).decode() if sg is not None else ""
+        text = lib().ann_status_string(status).decode()
+        raise AnnError(status, f"{what}: {text}" + (f" ({detail})" if detail else ""))
+    return status
+
+
+def ann_surrogate_create(n_max: int) -> ctypes.c_void_p:
+    sg = ctypes.c_void_p()
+    _scheck(lib().ann_surrogate_create(int(n_max), ctypes.byref(sg)), None, "ann_surrogate_create")
+    return sg
+
+
+def ann_surrogate_destroy(sg) -> None:
+    lib().ann_surrogate_destroy(sg)
+
+
+def ann_surrogate_set_params(sg, params) -> None:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != SG_PARAMS:
+        raise ValueError(f"expected {SG_PARAMS} parameters")
+    _scheck(lib().ann_surrogate_set_params(sg, _fp(p)), sg, "ann_surrogate_set_params")
+
+
+def ann_surrogate_get_params(sg):
+    p = np.zeros(SG_PARAMS, dtype=np.float32)
+    _scheck(lib().ann_surrogate_get_params(sg, _fp(p)), sg, "ann_surrogate_get_params")
+    return p
+
+
+def ann_surrogate_set_scales(sg, us: float, ys_q: float, ys_u: float, k: int = 8) -> None:
+    _scheck(lib().ann_surrogate_set_scales(sg, float(us), float(ys_q), float(ys_u), int(k)), sg,
+            "ann_surrogate_set_scales")
+
+
+def _tend(tend):
+    if tend is None:
+        return None, None
+    t = np.ascontiguousarray(np.asarray(tend, dtype=np.float32).T if np.ndim(tend) == 2 and np.shape(tend)[1] == 8
+                             else tend, dtype=np.float32)
+    return _fp(t), t
+
+
+def ann_surrogate_load(sg, ctx, tend=None) -> None:
+    """tend: None (the context's last recorded step) or (n, 8) tendencies in ID order."""
+    ptr, keep = _tend(tend)
+    _scheck(lib().ann_surrogate_load(sg, ctx, ptr), sg, "ann_surrogate_load")
+
+
+def ann_surrogate_forward(sg, n: int):
+    y = np.zeros((n, 4), dtype=np.float32)
+    _scheck(lib().ann_surrogate_forward(sg, _fp(y)), sg, "ann_surrogate_forward")
+    return y
+
+
+def ann_surrogate_gradients(sg, target):
+    """(loss, gradients float32[SG_PARAMS]) against targets (n x 4)."""
+    t = np.ascontiguousarray(target, dtype=np.float32)
+    g = np.zeros(SG_PARAMS, dtype=np.float32)
+    loss = ctypes.c_double()
+    _scheck(lib().ann_surrogate_gradients(sg, _fp(t), ctypes.byref(loss), _fp(g)), sg, "ann_surrogate_gradients")
+    return loss.value, g
+
+
+def ann_surrogate_adam(sg, lr: float) -> None:
+    _scheck(lib().ann_surrogate_adam(sg, float(lr)), sg, "ann_surrogate_adam")
+
+
+def ann_surrogate_jump(sg, ctx, tend=None) -> None:
+    ptr, keep = _tend(tend)
+    _scheck(lib().ann_surrogate_jump(sg, ctx, ptr), sg, "ann_surrogate_jump")
+
+
+def ann_surrogate_last_error(sg) -> str:
+    return lib().ann_surrogate_last_error(sg).decode()

@@ -34,6 +34,7 @@ struct ann_ctx {
     // flow diagnostics need): S after a step or a load that kept the cell structure, the
     // evaluation copy M after a neighbour export; neither after ann_set_particles.
     bool s_sorted = false, m_current = false;
+    bool rec_valid = false;   // the last step ran with recording on (GRADU, LAPQ, APD and a are its values)
     // flow diagnostics (allocated on first use, sized for the largest request so far)
     unsigned char *colors = nullptr;   // by particle ID (n)
     int ncolors = 1;                   // largest colour + 1
@@ -110,7 +111,7 @@ int64_t device_bytes(const ann_params &p)
                   + 4 + 8                     // neighbour counts, neighbour masks
                   + (MAXV / 2) * 4 + 4 + 16 + 4   // candidate lists, counts, split at re-sort, cell
                   + 11 * 4                    // intermediates
-                  + 8 * 4                     // recording
+                  + 10 * 4                    // recording
                   + 16 + 8                    // elastic stress and its divergence
                   + 8 + 1 + 4;                // image counts, colour, inverse order (diagnostics)
     int64_t tmp = std::max<int64_t>(7 * 8, MAXN * 4) * n;
@@ -259,7 +260,7 @@ cudaError_t alloc_all(ann_ctx *c)
     A_(vnbr, n * (MAXV / 4)); A_(vcnt, n); A_(xi_ref, n); A_(mkey, n); A_(rebuild, 1); A_(resorts, 1);
     A_(sumW, n); A_(V, n); A_(B11, n); A_(B12, n); A_(B22, n); A_(kr, n); A_(dh, n); A_(dhat, n);
     A_(p, n); A_(divx, n); A_(divy, n);
-    A_(rec_gu, 4 * n); A_(rec_lap, 2 * n); A_(rec_apd, 2 * n);
+    A_(rec_gu, 4 * n); A_(rec_lap, 2 * n); A_(rec_apd, 2 * n); A_(rec_qrate, 2 * n);
     A_(pel, n); A_(delx, n); A_(dely, n); A_(img, n);
     A_(err, 1); A_(maxu, 1); A_(band, 1);
 #undef A_
@@ -424,6 +425,8 @@ bool field_of(ann_ctx *c, int f, Field &out)
         out = {b.rec_lap, 4, false, 2, f - ANN_FIELD_LAPQ11}; return true;
     case ANN_FIELD_APDX: case ANN_FIELD_APDY:
         out = {b.rec_apd, 4, false, 2, f - ANN_FIELD_APDX}; return true;
+    case ANN_FIELD_QRATE11: case ANN_FIELD_QRATE12:
+        out = {b.rec_qrate, 4, false, 2, f - ANN_FIELD_QRATE11}; return true;
     default: return false;
     }
 }
@@ -577,6 +580,7 @@ int ann_set_particles(ann_ctx *c, int64_t n, const double *x, const double *y, c
     c->steps = 0;
     c->t = 0.0;
     c->s_sorted = c->m_current = false;
+    c->rec_valid = false;
     c->grid_step = -1;
     int s = device_status(c);
     if (s) {
@@ -602,6 +606,7 @@ int ann_step(ann_ctx *c, int64_t nsteps)
         c->s_sorted = true;
         c->m_current = false;
         c->grid_step = -1;
+        c->rec_valid = c->P.record != 0;
     }
     return s;
 }
@@ -659,6 +664,7 @@ int ann_step_profile(ann_ctx *c, int64_t nsteps, double *kernel_ms)
         c->s_sorted = true;
         c->m_current = false;
         c->grid_step = -1;
+        c->rec_valid = c->P.record != 0;
     }
     return st;
 }
@@ -900,6 +906,7 @@ int ann_load_state(ann_ctx *c, const char *path)
     c->steps = steps;
     c->s_sorted = !rb;
     c->m_current = false;
+    c->rec_valid = false;
     c->grid_step = -1;
     c->ncolors = 1;
     for (unsigned char v : col) c->ncolors = std::max(c->ncolors, (int)v + 1);
@@ -1342,6 +1349,7 @@ int ann_ensemble_step(ann_ensemble *E, int64_t nsteps)
             c->s_sorted = true;
             c->m_current = false;
             c->grid_step = -1;
+            c->rec_valid = c->P.record != 0;
         }
         if (st && first == ANN_OK) {
             first = st;
@@ -1400,3 +1408,63 @@ int ann_ensemble_autotune(ann_ensemble *E, int32_t trial_steps, int32_t *groups_
 const char *ann_ensemble_last_error(ann_ensemble *E) { return E ? E->last_err.c_str() : ""; }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// Hooks for the learned surrogate
+// ------------------------------------------------------------------------------------------------
+
+namespace ann {
+
+int ctx_view(ann_ctx *c, CtxView *v)
+{
+    if (!c || !v) return ANN_ERR_INVALID_ARG;
+    if (!c->have_particles) return fail(c, ANN_ERR_STATE, "no particles");
+    v->P = c->P;
+    v->b = c->b;
+    v->stream = c->stream;
+    v->tmp = static_cast<double *>(c->tmp);
+    v->t = c->t;
+    v->steps = c->steps;
+    v->rec_valid = c->rec_valid;
+    return ANN_OK;
+}
+
+int ctx_search_present(ann_ctx *c)
+{
+    if (!c->have_particles) return fail(c, ANN_ERR_STATE, "no particles");
+    if (c->m_current) return ANN_OK;
+    DevParams Q = c->P;
+    Q.half_dt = 0.f;
+    Q.half_dt_d = 0.0;
+    cudaError_t e = cudaMemsetAsync(c->b.rebuild, 1, sizeof(uint32_t), c->stream);
+    if (!e) e = enqueue_search(Q, c->b, c->stream);
+    if (e) return cuda_fail(c, e, "search");
+    int st = device_status(c);
+    if (st) return st;
+    c->s_sorted = false;
+    c->m_current = true;
+    return ANN_OK;
+}
+
+// Replace the state by device arrays in ID order (as ann_set_particles), keeping t and the step
+// count, which advance by add_steps.  Accelerations restart from 0 and the next step re-sorts.
+int ctx_reload(ann_ctx *c, const double *dev7, int64_t add_steps)
+{
+    double t = c->t;
+    int64_t steps = c->steps;
+    size_t n = (size_t)c->P.n;
+    cudaError_t e = clear_flags(c);
+    if (!e) e = enqueue_load(c->P, c->b, dev7, dev7 + n, dev7 + 2 * n, dev7 + 3 * n, dev7 + 4 * n, dev7 + 5 * n,
+                             dev7 + 6 * n, c->stream, false);
+    if (e) return cuda_fail(c, e, "reload");
+    int st = device_status(c);
+    c->have_particles = (st == ANN_OK);
+    c->t = t + add_steps * c->P.dt_d;
+    c->steps = steps + add_steps;
+    c->s_sorted = c->m_current = false;
+    c->rec_valid = false;
+    c->grid_step = -1;
+    return st;
+}
+
+}  // namespace ann

@@ -1,6 +1,8 @@
 // Internal declarations shared by the kernels and the C-ABI of the SPH active-nematic solver.
 #pragma once
 
+#include "../../include/ann.h"
+
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -73,7 +75,7 @@ struct Bufs {
     uint32_t *rebuild;  // non-zero: this step re-sorts and rebuilds the candidate lists
     uint32_t *resorts;  // number of re-sort steps since the particles were loaded
     float *sumW, *V, *B11, *B12, *B22, *kr, *dh, *dhat, *p, *divx, *divy;
-    float *rec_gu, *rec_lap, *rec_apd;   // 4n, 2n, 2n (recording only)
+    float *rec_gu, *rec_lap, *rec_apd, *rec_qrate;   // 4n, 2n, 2n, 2n (recording only)
     float4 *pel;        // elastic stress (11, 12, 22, -) of Eq. 12 (elastic_stress only)
     float *delx, *dely; // its corrected divergence (paper momentum only)
     int2 *img;          // by particle ID: net periodic shifts (x, y) since ann_set_particles
@@ -98,7 +100,7 @@ cudaError_t enqueue_candidates_from_ref(const DevParams &P, const Bufs &b, cudaS
 // Load FP64 inputs (ID order) into S; rho may be null.
 cudaError_t enqueue_load(const DevParams &P, const Bufs &b, const double *x, const double *y,
                          const double *ux, const double *uy, const double *q11, const double *q12,
-                         const double *rho, cudaStream_t s);
+                         const double *rho, cudaStream_t s, bool reset_images = true);
 // Scatter field f (M or S order, element size es) into out[id[g]].
 cudaError_t enqueue_unpermute(const void *f, const int *id, void *out, int n, int es, cudaStream_t s);
 // Neighbour export: for each M-order particle g and k < nnbr[g], cols_tmp[k * n + g] = original ID
@@ -126,13 +128,41 @@ cudaError_t enqueue_correlation(int M, double L, const double *grid, int all_ori
 cudaError_t enqueue_defects(int M, const double *grid, signed char *map, unsigned long long *counts, cudaStream_t s);
 cudaError_t enqueue_mixing(const DevParams &P, const Bufs &b, const unsigned char *colors, int G, int S,
                            unsigned *cnt, cudaStream_t s);
+// Neighbour graph of the present positions in particle-ID order (ELL: entry k of row i at
+// k * n + i), for the learned surrogate.
+struct GraphOut {
+    int *nbr;        // MAXN x n neighbour IDs
+    float *W;        // MAXN x n kernel values W(|x_i - x_j|)
+    int *cnt;        // n
+    float *S;        // n: W(0) + sum_j W
+    double *x, *y;   // n: positions
+    float4 *u4;      // n: (ux, uy, q11, q12)
+    float *dr;       // n: rho / rho0 - 1
+};
+cudaError_t enqueue_export_graph(const DevParams &P, const Bufs &b, const GraphOut &o, cudaStream_t s);
+
+// Context hooks for the surrogate (implemented in ann_api.cu; the context itself stays opaque).
+struct CtxView {
+    DevParams P;
+    Bufs b;
+    cudaStream_t stream;
+    double *tmp;   // 7 n doubles of staging
+    double t;
+    int64_t steps;
+    bool rec_valid;   // the last step recorded grad u, lap Q and a
+};
+int ctx_view(ann_ctx *c, CtxView *v);
+int ctx_search_present(ann_ctx *c);                                  // search at the present positions
+int ctx_reload(ann_ctx *c, const double *dev7, int64_t add_steps);   // x, y, ux, uy, q11, q12, rho by ID
+
 // BF16 tensor-core GEMMs of the surrogate (ann_mlp.cu).  K, N multiples of 16 in [16, 256].
 bool gemm_shape_ok(int K, int N);
+// ldc: row stride of C in elements (0: N)
 cudaError_t enqueue_gemm_nt(const void *A1, int K1, const void *A2, int K2, const void *B, int N, int rows,
                             const float *bias, int relu, void *C, int c_bf16, int accumulate, unsigned *err,
-                            int max_ctas, cudaStream_t s);
+                            int max_ctas, cudaStream_t s, int ldc = 0);
 cudaError_t enqueue_gemm_tn(const void *A, int K, const void *B, int N, int rows, float *C, unsigned *err,
-                            int max_ctas, cudaStream_t s);
+                            int max_ctas, cudaStream_t s, int ldc = 0);
 cudaError_t enqueue_unwrapped(const DevParams &P, const Bufs &b, int *inv, const long long *ids, int k, double *xy,
                               cudaStream_t s);
 

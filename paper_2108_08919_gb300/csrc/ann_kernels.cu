@@ -794,6 +794,8 @@ __global__ void BOUNDS_B k_pass_b(DevParams P, Bufs b)
             b.rec_gu[4 * gi + 3] = D11;
             b.rec_lap[2 * gi + 0] = lap1;
             b.rec_lap[2 * gi + 1] = lap2;
+            b.rec_qrate[2 * gi + 0] = m1;
+            b.rec_qrate[2 * gi + 1] = m2;
         }
     }
 }
@@ -1068,7 +1070,8 @@ __global__ void k_set_condition(Bufs b, cudaGraphConditionalHandle h)
 // ---------------------------------------------------------------------------------------------
 
 __global__ void k_load(DevParams P, Bufs b, const double *x, const double *y, const double *ux,
-                       const double *uy, const double *q11, const double *q12, const double *rho)
+                       const double *uy, const double *q11, const double *q12, const double *rho,
+                       bool reset_images)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
@@ -1093,7 +1096,7 @@ __global__ void k_load(DevParams P, Bufs b, const double *x, const double *y, co
     b.sax[i] = 0.f;
     b.say[i] = 0.f;
     b.sid[i] = i;
-    b.img[i] = make_int2(0, 0);   // pathlines start at the loaded (wrapped) positions
+    if (reset_images) b.img[i] = make_int2(0, 0);   // pathlines start at the loaded (wrapped) positions
 }
 
 template <typename T>
@@ -1129,6 +1132,47 @@ __global__ void __launch_bounds__(PT) k_export_nbrs(DevParams P, Bufs b, int *co
                 k++;
             }
         });
+    }
+}
+
+// The neighbour graph of the present positions in particle-ID order, for the learned surrogate:
+// row id = mid[g] of particle g holds its neighbours' IDs and kernel values W(|d|) (the exact
+// support test's neighbours, from the mask), the count, and S = sum_j W + W(0) of the search;
+// the state is gathered by ID too.  Runs after a search at the present positions.
+__global__ void __launch_bounds__(PT) k_export_graph(DevParams P, Bufs b, GraphOut o)
+{
+    __shared__ TileShared ts;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float4 *pos = reinterpret_cast<float4 *>(dsm);
+    int *sg = reinterpret_cast<int *>(pos + HCAP);
+    Tile T;
+    if (!tile_begin(P, b, ts, T)) return;
+    for (int t = threadIdx.x; t < T.H; t += PT) {
+        SlotInfo s = slot_info(P, b, ts, T, t);
+        pos[t] = s.e;
+        sg[t] = s.g;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < T.Ni; q += PT) {
+        int si = inner_slot(ts, T, q);
+        int gi = sg[si];
+        float4 pi = pos[si];
+        int id = b.mid[gi], k = 0;
+        for_each_candidate<1>(P, b, gi, b.emask[gi], [&](int off, int, unsigned in) {
+            int j = off >> 4;
+            if (in && j < T.H && k < MAXN) {
+                float r2 = len2(pair_d(pi, slot_at(pos, off)));
+                o.nbr[(size_t)k * P.n + id] = b.mid[sg[j]];
+                o.W[(size_t)k * P.n + id] = kernel_w<true>(r2, P);
+                k++;
+            }
+        });
+        o.cnt[id] = k;
+        o.S[id] = b.sumW[gi];
+        o.x[id] = b.mx[gi];
+        o.y[id] = b.my[gi];
+        o.u4[id] = make_float4(b.mux[gi], b.muy[gi], b.mq11[gi], b.mq12[gi]);
+        o.dr[id] = b.mdr[gi];
     }
 }
 
@@ -1285,9 +1329,9 @@ cudaError_t enqueue_candidates_from_ref(const DevParams &P, const Bufs &b, cudaS
 
 cudaError_t enqueue_load(const DevParams &P, const Bufs &b, const double *x, const double *y,
                          const double *ux, const double *uy, const double *q11, const double *q12,
-                         const double *rho, cudaStream_t s)
+                         const double *rho, cudaStream_t s, bool reset_images)
 {
-    k_load<<<blocks_for(P.n, 256), 256, 0, s>>>(P, b, x, y, ux, uy, q11, q12, rho);
+    k_load<<<blocks_for(P.n, 256), 256, 0, s>>>(P, b, x, y, ux, uy, q11, q12, rho, reset_images);
     return cudaGetLastError();
 }
 
@@ -1298,6 +1342,12 @@ cudaError_t enqueue_unpermute(const void *f, const int *id, void *out, int n, in
             (const unsigned long long *)f, id, (unsigned long long *)out, n);
     else
         k_unpermute<uint32_t><<<blocks_for(n, 256), 256, 0, s>>>((const uint32_t *)f, id, (uint32_t *)out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_export_graph(const DevParams &P, const Bufs &b, const GraphOut &o, cudaStream_t s)
+{
+    k_export_graph<<<P.tiles * P.tiles, PT, SMEM_AF, s>>>(P, b, o);
     return cudaGetLastError();
 }
 

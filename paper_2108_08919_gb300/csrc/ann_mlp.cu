@@ -123,8 +123,8 @@ struct NtArgs {
     const __nv_bfloat16 *A1, *A2;   // rows x K1, rows x K2 (row-major), A2 may be null (K2 = 0)
     const __nv_bfloat16 *B;         // N x K (row-major: K-major)
     const float *bias;              // N or null
-    void *C;                        // rows x N: BF16 or FP32
-    int rows, K1, K2, N, relu, c_bf16, accumulate;
+    void *C;                        // rows x N (row stride ldc): BF16 or FP32
+    int rows, K1, K2, N, relu, c_bf16, accumulate, ldc;
     unsigned *err;
 };
 
@@ -198,12 +198,12 @@ __global__ void __launch_bounds__(128) k_gemm_nt(NtArgs a)
                     v[k] = x;
                 }
                 if (a.c_bf16) {
-                    __nv_bfloat16 *C = static_cast<__nv_bfloat16 *>(a.C) + (size_t)gr * N + c0;
+                    __nv_bfloat16 *C = static_cast<__nv_bfloat16 *>(a.C) + (size_t)gr * a.ldc + c0;
 #pragma unroll
                     for (int k = 0; k < 16; k += 2)
                         *reinterpret_cast<__nv_bfloat162 *>(C + k) = __floats2bfloat162_rn(v[k], v[k + 1]);
                 } else {
-                    float *C = static_cast<float *>(a.C) + (size_t)gr * N + c0;
+                    float *C = static_cast<float *>(a.C) + (size_t)gr * a.ldc + c0;
 #pragma unroll
                     for (int k = 0; k < 16; k++) C[k] = a.accumulate ? C[k] + v[k] : v[k];
                 }
@@ -229,8 +229,8 @@ __global__ void __launch_bounds__(128) k_gemm_nt(NtArgs a)
 struct TnArgs {
     const __nv_bfloat16 *A;   // rows x K
     const __nv_bfloat16 *B;   // rows x N
-    float *C;                 // K x N (FP32, accumulated)
-    int rows, K, N;
+    float *C;                 // K x N (FP32, accumulated, row stride ldc)
+    int rows, K, N, ldc;
     unsigned *err;
 };
 
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(128) k_gemm_tn(TnArgs a)
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
             if (f < a.K)
 #pragma unroll
-                for (int k = 0; k < 16; k++) atomicAdd(&a.C[(size_t)f * N + c0 + k], v[k]);
+                for (int k = 0; k < 16; k++) atomicAdd(&a.C[(size_t)f * a.ldc + c0 + k], v[k]);
         }
     }
     fence_before();
@@ -313,10 +313,11 @@ bool gemm_shape_ok(int K, int N) { return K >= 16 && K <= 256 && K % 16 == 0 && 
 
 cudaError_t enqueue_gemm_nt(const void *A1, int K1, const void *A2, int K2, const void *B, int N, int rows,
                             const float *bias, int relu, void *C, int c_bf16, int accumulate, unsigned *err,
-                            int max_ctas, cudaStream_t s)
+                            int max_ctas, cudaStream_t s, int ldc)
 {
     NtArgs a{static_cast<const __nv_bfloat16 *>(A1), static_cast<const __nv_bfloat16 *>(A2),
-             static_cast<const __nv_bfloat16 *>(B), bias, C, rows, K1, K2, N, relu, c_bf16, accumulate, err};
+             static_cast<const __nv_bfloat16 *>(B), bias, C, rows, K1, K2, N, relu, c_bf16, accumulate,
+             ldc > 0 ? ldc : N, err};
     int K = K1 + K2;
     size_t smem = (size_t)(N + MT) * K * 2;
     cudaError_t e = cudaFuncSetAttribute(k_gemm_nt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -329,9 +330,10 @@ cudaError_t enqueue_gemm_nt(const void *A1, int K1, const void *A2, int K2, cons
 }
 
 cudaError_t enqueue_gemm_tn(const void *A, int K, const void *B, int N, int rows, float *C, unsigned *err,
-                            int max_ctas, cudaStream_t s)
+                            int max_ctas, cudaStream_t s, int ldc)
 {
-    TnArgs a{static_cast<const __nv_bfloat16 *>(A), static_cast<const __nv_bfloat16 *>(B), C, rows, K, N, err};
+    TnArgs a{static_cast<const __nv_bfloat16 *>(A), static_cast<const __nv_bfloat16 *>(B), C, rows, K, N,
+             ldc > 0 ? ldc : N, err};
     size_t smem = (size_t)(MT + N) * MT * 2;
     cudaError_t e = cudaFuncSetAttribute(k_gemm_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;

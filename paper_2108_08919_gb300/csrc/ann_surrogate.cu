@@ -1,0 +1,614 @@
+// Learned coarse-step surrogate: a message-passing MLP over the SPH neighbour graph that predicts
+// the increments of Q and u over k steps, trained and evaluated on the GPU.  The paper has no
+// learned component; the network is the project's.
+//
+//   features  x_i = (r_i, agg(r)_i - r_i, a k dt / ys_u, m k dt / ys_q, lapQ Gamma K k dt / ys_q,
+//             (div u, vort u) k dt), r = (Q11, Q12, ux / us, uy / us), with the tendencies of the
+//             last recorded step: acceleration a, projected Q rate m, Laplacian of Q, and the
+//             divergence and vorticity of the corrected velocity gradient
+//   prediction  (dQ, du) = k dt (m, a) + (ys_q y0, ys_q y1, ys_u y2, ys_u y3)
+//   h1 = relu(W1 [x ; agg(x)] + b1),  z1 = P1 h1,  h2 = relu(W2 [h1 ; agg(z1)] + b2),
+//   z2 = P2 h2,  h3 = relu(W3 [h2 ; agg(z2)] + b3),  y = Wo h3 + bo
+//   agg(f)_i = (W(0) f_i + sum_j W_ij f_j) / S_i,  S_i = W(0) + sum_j W_ij   (an SPH mean, Eq. 19)
+//
+// Dense products run on the tensor cores (ann_mlp.cu: BF16 operands, FP32 accumulation);
+// activations are stored in BF16, gradients accumulate in FP32, the optimiser (Adam) keeps FP32
+// master weights.  Particles are in ID order throughout.
+#include "../../include/ann.h"
+#include "ann_internal.cuh"
+
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using bf16 = __nv_bfloat16;
+
+namespace ann {
+namespace {
+
+constexpr int F0 = 16, WIDTH = 128, MSG = 32, NOUT = 4, NOUTP = 16;
+// flat parameter layout: W1 b1 P1 W2 b2 P2 W3 b3 Wo bo
+constexpr int O_W1 = 0, O_B1 = O_W1 + WIDTH * 2 * F0, O_P1 = O_B1 + WIDTH, O_W2 = O_P1 + MSG * WIDTH,
+              O_B2 = O_W2 + WIDTH * (WIDTH + MSG), O_P2 = O_B2 + WIDTH, O_W3 = O_P2 + MSG * WIDTH,
+              O_B3 = O_W3 + WIDTH * (WIDTH + MSG), O_WO = O_B3 + WIDTH, O_BO = O_WO + NOUT * WIDTH,
+              NPARAM = O_BO + NOUT;
+static_assert(NPARAM == ANN_SG_PARAMS, "parameter count");
+
+struct GraphView {
+    const int *nbr;
+    const float *W;
+    const int *cnt;
+    const float *S;
+    int n;
+    float W0;
+};
+
+// tend: 8 x n (component-major, ID order): ax, ay, m11, m12, lapQ11, lapQ12, div u, vort u
+struct TendScales {
+    float a, m, lap, grad;
+};
+
+__global__ void k_sg_features(GraphView g, const float4 *u4, float inv_us, const float *tend, TendScales ts,
+                              bf16 *X)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    float4 s = u4[i];
+    float r[4] = {s.z, s.w, s.x * inv_us, s.y * inv_us};
+    float is = 1.f / g.S[i], a[4];
+    for (int c = 0; c < 4; c++) a[c] = g.W0 * is * r[c];
+    int m = g.cnt[i];
+    for (int k = 0; k < m; k++) {
+        int j = g.nbr[(size_t)k * g.n + i];
+        float w = g.W[(size_t)k * g.n + i] * is;
+        float4 t = u4[j];
+        a[0] += w * t.z;
+        a[1] += w * t.w;
+        a[2] += w * t.x * inv_us;
+        a[3] += w * t.y * inv_us;
+    }
+    bf16 *row = X + (size_t)i * F0;
+    for (int c = 0; c < 4; c++) {
+        row[c] = __float2bfloat16(r[c]);
+        row[4 + c] = __float2bfloat16(a[c] - r[c]);
+    }
+    for (int c = 0; c < 8; c++) {
+        float sc = c < 2 ? ts.a : (c < 4 ? ts.m : (c < 6 ? ts.lap : ts.grad));
+        row[8 + c] = __float2bfloat16(tend[(size_t)c * g.n + i] * sc);
+    }
+}
+
+// div u = D_xx + D_yy and vort u = D_yx - D_xy from the four gradient components (4 x n).
+__global__ void k_sg_div_vort(int n, const float *gu, float *tend)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    tend[6 * (size_t)n + i] = gu[i] + gu[3 * (size_t)n + i];
+    tend[7 * (size_t)n + i] = gu[2 * (size_t)n + i] - gu[(size_t)n + i];
+}
+
+// out[i][c] = agg(in)[i][c] for C channels (BF16 in and out, FP32 sums); thread per (i, c).
+template <int C>
+__global__ void k_sg_agg(GraphView g, const bf16 *in, bf16 *out)
+{
+    size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)g.n * C) return;
+    int i = (int)(t / C), c = (int)(t % C);
+    float is = 1.f / g.S[i];
+    float acc = g.W0 * is * __bfloat162float(in[(size_t)i * C + c]);
+    int m = g.cnt[i];
+    for (int k = 0; k < m; k++) {
+        int j = g.nbr[(size_t)k * g.n + i];
+        acc += g.W[(size_t)k * g.n + i] * is * __bfloat162float(in[(size_t)j * C + c]);
+    }
+    out[(size_t)i * C + c] = __float2bfloat16(acc);
+}
+
+// The adjoint of agg: out[j][c] = W(0)/S_j in[j][c] + sum_{i in N(j)} W_ij / S_i in[i][c]; the
+// neighbour relation is symmetric, so j's own row lists the i and W_ij.  in: FP32, row stride ld.
+template <int C>
+__global__ void k_sg_agg_T(GraphView g, const float *in, int ld, bf16 *out)
+{
+    size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)g.n * C) return;
+    int j = (int)(t / C), c = (int)(t % C);
+    float acc = g.W0 / g.S[j] * in[(size_t)j * ld + c];
+    int m = g.cnt[j];
+    for (int k = 0; k < m; k++) {
+        int i = g.nbr[(size_t)k * g.n + j];
+        acc += g.W[(size_t)k * g.n + j] / g.S[i] * in[(size_t)i * ld + c];
+    }
+    out[(size_t)j * C + c] = __float2bfloat16(acc);
+}
+
+// dY = 2 (y - t) / (4 n) on the 4 outputs (0 on the padding), and the sum of (y - t)^2.
+__global__ void k_sg_loss(int n, const float *Y, const float *T, bf16 *dY, double *loss)
+{
+    __shared__ double red[256];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (i < n) {
+        float sc = 2.f / (4.f * (float)n);
+        for (int c = 0; c < NOUTP; c++) {
+            float d = c < NOUT ? Y[(size_t)i * NOUTP + c] - T[(size_t)i * NOUT + c] : 0.f;
+            s += (double)d * d;
+            dY[(size_t)i * NOUTP + c] = __float2bfloat16(sc * d);
+        }
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, red[0]);
+}
+
+// dA = dH * (H > 0) (relu), dH FP32 with row stride ld, H and dA BF16 with C columns.
+__global__ void k_sg_relu_bwd(int n, int C, const float *dH, int ld, const bf16 *H, bf16 *dA)
+{
+    size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)n * C) return;
+    size_t i = t / C, c = t % C;
+    float h = __bfloat162float(H[t]);
+    dA[t] = __float2bfloat16(h > 0.f ? dH[i * ld + c] : 0.f);
+}
+
+// out[c] += sum_i in[i][c] (bias gradients); block: 256 threads over rows, one column per y.
+__global__ void k_sg_colsum(int n, int C, const bf16 *in, float *out)
+{
+    __shared__ float red[256];
+    int c = blockIdx.y;
+    float s = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        s += __bfloat162float(in[(size_t)i * C + c]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(&out[c], red[0]);
+}
+
+// BF16 copies of an R x C FP32 matrix: dst (R x C, rows padded to Rp with zeros) and its
+// transpose dstT (C x Rp).
+__global__ void k_sg_cast(const float *src, int R, int C, int Rp, bf16 *dst, bf16 *dstT)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= Rp * C) return;
+    int r = t / C, c = t % C;
+    float v = r < R ? src[r * C + c] : 0.f;
+    if (dst) dst[r * C + c] = __float2bfloat16(v);
+    if (dstT) dstT[c * Rp + r] = __float2bfloat16(v);
+}
+
+__global__ void k_sg_adam(float *p, const float *g, float *m, float *v, int count, float lr, float b1, float b2,
+                          float eps, float bc1, float bc2)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    float gg = g[t];
+    float mm = b1 * m[t] + (1.f - b1) * gg, vv = b2 * v[t] + (1.f - b2) * gg * gg;
+    m[t] = mm;
+    v[t] = vv;
+    p[t] -= lr * (mm / bc1) / (sqrtf(vv / bc2) + eps);
+}
+
+// The jump: u += k dt a + ys_u (y2, y3), Q += k dt m + ys_q (y0, y1), x += k dt (u + u') / 2
+// (trapezoid), wrapped with the periodic image count; out7 = x, y, ux, uy, q11, q12, rho (FP64, ID
+// order).
+__global__ void k_sg_jump(int n, const double *x, const double *y, const float4 *u4, const float *dr, const float *Y,
+                          const float *tend, float ysq, float ysu, double dtk, double L, float rho0, int2 *img,
+                          double *out7)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 s = u4[i];
+    const float *yi = Y + (size_t)i * NOUTP;
+    float kdt = (float)dtk;
+    float ux = s.x + (kdt * tend[i] + ysu * yi[2]), uy = s.y + (kdt * tend[(size_t)n + i] + ysu * yi[3]);
+    float q1 = s.z + (kdt * tend[2 * (size_t)n + i] + ysq * yi[0]);
+    float q2 = s.w + (kdt * tend[3 * (size_t)n + i] + ysq * yi[1]);
+    double xn = x[i] + dtk * 0.5 * ((double)s.x + (double)ux);
+    double yn = y[i] + dtk * 0.5 * ((double)s.y + (double)uy);
+    int kx = (int)floor(xn / L), ky = (int)floor(yn / L);
+    xn -= kx * L;
+    yn -= ky * L;
+    if (xn >= L) xn -= L;   // rounding at the face
+    if (yn >= L) yn -= L;
+    if (kx | ky) {
+        img[i].x += kx;
+        img[i].y += ky;
+    }
+    out7[i] = xn;
+    out7[(size_t)n + i] = yn;
+    out7[2 * (size_t)n + i] = ux;
+    out7[3 * (size_t)n + i] = uy;
+    out7[4 * (size_t)n + i] = q1;
+    out7[5 * (size_t)n + i] = q2;
+    out7[6 * (size_t)n + i] = (double)rho0 * (1.0 + (double)dr[i]);
+}
+
+inline unsigned nb(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+}  // namespace ann
+
+using namespace ann;
+
+struct ann_surrogate {
+    int64_t nmax = 0;
+    int n = 0;
+    double us = 1.0, ysq = 1.0, ysu = 1.0;
+    int k = 8;                  // steps the network spans
+    double gammaK = 0.0;        // Gamma K of the loaded context
+    cudaStream_t s = nullptr;
+    std::vector<void *> allocs;
+    std::string last_err;
+    // graph and state, ID order
+    int *nbr = nullptr, *cnt = nullptr;
+    float *W = nullptr, *S = nullptr, *dr = nullptr, *tend = nullptr;
+    double *x = nullptr, *y = nullptr;
+    float4 *u4 = nullptr;
+    float W0 = 0.f;
+    double L = 1.0, dt = 0.0;
+    float rho0 = 1.f;
+    bool loaded = false;
+    // activations (BF16) and outputs
+    bf16 *X0, *AX, *H1, *Z1, *AZ1, *H2, *Z2, *AZ2, *H3;
+    float *Y, *T;
+    // backward scratch
+    bf16 *dY, *dA, *dZ;
+    float *dH;   // n x 160
+    // parameters
+    float *p, *g, *m, *v;   // FP32 flat (NPARAM)
+    bf16 *W1b, *P1b, *W2b, *P2b, *W3b, *Wob, *W3T, *W2T, *P2T, *P1T, *WoT;
+    float *bop;             // bo padded to 16
+    double *loss;
+    unsigned *err;
+    int adam_t = 0;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t sg_alloc(ann_surrogate *S, T *&ptr, size_t count)
+{
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    if (e) return e;
+    S->allocs.push_back(p);
+    ptr = static_cast<T *>(p);
+    return cudaMemsetAsync(p, 0, std::max<size_t>(count, 1) * sizeof(T), S->s);
+}
+
+int sfail(ann_surrogate *S, int code, const std::string &msg)
+{
+    if (S) S->last_err = msg;
+    return code;
+}
+
+int scuda(ann_surrogate *S, cudaError_t e, const char *where)
+{
+    return sfail(S, e == cudaErrorMemoryAllocation ? ANN_ERR_OOM : ANN_ERR_CUDA,
+                 std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+GraphView view(const ann_surrogate *S) { return GraphView{S->nbr, S->W, S->cnt, S->S, S->n, S->W0}; }
+
+// BF16 copies (and transposes) of the weights for the next forward / backward pass.
+cudaError_t cast_weights(ann_surrogate *S)
+{
+    cudaStream_t s = S->s;
+    k_sg_cast<<<nb(WIDTH * 2 * F0), 256, 0, s>>>(S->p + O_W1, WIDTH, 2 * F0, WIDTH, S->W1b, nullptr);
+    k_sg_cast<<<nb(MSG * WIDTH), 256, 0, s>>>(S->p + O_P1, MSG, WIDTH, MSG, S->P1b, S->P1T);
+    k_sg_cast<<<nb(WIDTH * (WIDTH + MSG)), 256, 0, s>>>(S->p + O_W2, WIDTH, WIDTH + MSG, WIDTH, S->W2b, S->W2T);
+    k_sg_cast<<<nb(MSG * WIDTH), 256, 0, s>>>(S->p + O_P2, MSG, WIDTH, MSG, S->P2b, S->P2T);
+    k_sg_cast<<<nb(WIDTH * (WIDTH + MSG)), 256, 0, s>>>(S->p + O_W3, WIDTH, WIDTH + MSG, WIDTH, S->W3b, S->W3T);
+    k_sg_cast<<<nb(NOUTP * WIDTH), 256, 0, s>>>(S->p + O_WO, NOUT, WIDTH, NOUTP, S->Wob, S->WoT);
+    cudaError_t e = cudaMemsetAsync(S->bop, 0, NOUTP * sizeof(float), s);
+    if (!e) e = cudaMemcpyAsync(S->bop, S->p + O_BO, NOUT * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (!e) e = cudaGetLastError();
+    return e;
+}
+
+constexpr int GEMM_CTAS = 296;   // two persistent CTAs per SM
+
+cudaError_t forward(ann_surrogate *S)
+{
+    cudaStream_t s = S->s;
+    int n = S->n;
+    GraphView g = view(S);
+    unsigned *err = S->err;
+    k_sg_agg<F0><<<nb((size_t)n * F0), 256, 0, s>>>(g, S->X0, S->AX);
+    cudaError_t e = enqueue_gemm_nt(S->X0, F0, S->AX, F0, S->W1b, WIDTH, n, S->p + O_B1, 1, S->H1, 1, 0, err,
+                                    GEMM_CTAS, s);
+    if (!e) e = enqueue_gemm_nt(S->H1, WIDTH, nullptr, 0, S->P1b, MSG, n, nullptr, 0, S->Z1, 1, 0, err, GEMM_CTAS, s);
+    if (!e) {
+        k_sg_agg<MSG><<<nb((size_t)n * MSG), 256, 0, s>>>(g, S->Z1, S->AZ1);
+        e = enqueue_gemm_nt(S->H1, WIDTH, S->AZ1, MSG, S->W2b, WIDTH, n, S->p + O_B2, 1, S->H2, 1, 0, err, GEMM_CTAS, s);
+    }
+    if (!e) e = enqueue_gemm_nt(S->H2, WIDTH, nullptr, 0, S->P2b, MSG, n, nullptr, 0, S->Z2, 1, 0, err, GEMM_CTAS, s);
+    if (!e) {
+        k_sg_agg<MSG><<<nb((size_t)n * MSG), 256, 0, s>>>(g, S->Z2, S->AZ2);
+        e = enqueue_gemm_nt(S->H2, WIDTH, S->AZ2, MSG, S->W3b, WIDTH, n, S->p + O_B3, 1, S->H3, 1, 0, err, GEMM_CTAS, s);
+    }
+    if (!e) e = enqueue_gemm_nt(S->H3, WIDTH, nullptr, 0, S->Wob, NOUTP, n, S->bop, 0, S->Y, 0, 0, err, GEMM_CTAS, s);
+    return e ? e : cudaGetLastError();
+}
+
+// Gradients of the mean-squared loss against the targets in S->T (after forward).
+cudaError_t backward(ann_surrogate *S)
+{
+    cudaStream_t s = S->s;
+    int n = S->n;
+    GraphView g = view(S);
+    unsigned *err = S->err;
+    const int K2 = WIDTH + MSG;
+    float *gp = S->g;
+    cudaError_t e = cudaMemsetAsync(gp, 0, NPARAM * sizeof(float), s);
+    if (!e) e = cudaMemsetAsync(S->loss, 0, sizeof(double), s);
+    if (e) return e;
+    k_sg_loss<<<nb(n), 256, 0, s>>>(n, S->Y, S->T, S->dY, S->loss);
+    // output layer: gWo (rows 0..3 of the 16 x 128 product), gbo
+    float *gWo16 = S->dH;   // 16 x 128 scratch, copied below
+    e = cudaMemsetAsync(gWo16, 0, NOUTP * WIDTH * sizeof(float), s);
+    if (!e) e = enqueue_gemm_tn(S->dY, NOUTP, S->H3, WIDTH, n, gWo16, err, GEMM_CTAS, s);
+    if (!e) e = cudaMemcpyAsync(gp + O_WO, gWo16, NOUT * WIDTH * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e) return e;
+    {
+        dim3 gr(64, NOUT);
+        k_sg_colsum<<<gr, 256, 0, s>>>(n, NOUTP, S->dY, gp + O_BO);
+    }
+    // layer 3
+    e = enqueue_gemm_nt(S->dY, NOUTP, nullptr, 0, S->WoT, WIDTH, n, nullptr, 0, S->dH, 0, 0, err, GEMM_CTAS, s, K2);
+    if (e) return e;
+    k_sg_relu_bwd<<<nb((size_t)n * WIDTH), 256, 0, s>>>(n, WIDTH, S->dH, K2, S->H3, S->dA);
+    {
+        dim3 gr(64, WIDTH);
+        k_sg_colsum<<<gr, 256, 0, s>>>(n, WIDTH, S->dA, gp + O_B3);
+    }
+    e = enqueue_gemm_tn(S->dA, WIDTH, S->H2, WIDTH, n, gp + O_W3, err, GEMM_CTAS, s, K2);
+    if (!e) e = enqueue_gemm_tn(S->dA, WIDTH, S->AZ2, MSG, n, gp + O_W3 + WIDTH, err, GEMM_CTAS, s, K2);
+    if (!e) e = enqueue_gemm_nt(S->dA, WIDTH, nullptr, 0, S->W3T, K2, n, nullptr, 0, S->dH, 0, 0, err, GEMM_CTAS, s);
+    if (e) return e;
+    k_sg_agg_T<MSG><<<nb((size_t)n * MSG), 256, 0, s>>>(g, S->dH + WIDTH, K2, S->dZ);
+    e = enqueue_gemm_tn(S->dZ, MSG, S->H2, WIDTH, n, gp + O_P2, err, GEMM_CTAS, s);
+    if (!e) e = enqueue_gemm_nt(S->dZ, MSG, nullptr, 0, S->P2T, WIDTH, n, nullptr, 0, S->dH, 0, 1, err, GEMM_CTAS, s, K2);
+    if (e) return e;
+    // layer 2
+    k_sg_relu_bwd<<<nb((size_t)n * WIDTH), 256, 0, s>>>(n, WIDTH, S->dH, K2, S->H2, S->dA);
+    {
+        dim3 gr(64, WIDTH);
+        k_sg_colsum<<<gr, 256, 0, s>>>(n, WIDTH, S->dA, gp + O_B2);
+    }
+    e = enqueue_gemm_tn(S->dA, WIDTH, S->H1, WIDTH, n, gp + O_W2, err, GEMM_CTAS, s, K2);
+    if (!e) e = enqueue_gemm_tn(S->dA, WIDTH, S->AZ1, MSG, n, gp + O_W2 + WIDTH, err, GEMM_CTAS, s, K2);
+    if (!e) e = enqueue_gemm_nt(S->dA, WIDTH, nullptr, 0, S->W2T, K2, n, nullptr, 0, S->dH, 0, 0, err, GEMM_CTAS, s);
+    if (e) return e;
+    k_sg_agg_T<MSG><<<nb((size_t)n * MSG), 256, 0, s>>>(g, S->dH + WIDTH, K2, S->dZ);
+    e = enqueue_gemm_tn(S->dZ, MSG, S->H1, WIDTH, n, gp + O_P1, err, GEMM_CTAS, s);
+    if (!e) e = enqueue_gemm_nt(S->dZ, MSG, nullptr, 0, S->P1T, WIDTH, n, nullptr, 0, S->dH, 0, 1, err, GEMM_CTAS, s, K2);
+    if (e) return e;
+    // layer 1
+    k_sg_relu_bwd<<<nb((size_t)n * WIDTH), 256, 0, s>>>(n, WIDTH, S->dH, K2, S->H1, S->dA);
+    {
+        dim3 gr(64, WIDTH);
+        k_sg_colsum<<<gr, 256, 0, s>>>(n, WIDTH, S->dA, gp + O_B1);
+    }
+    e = enqueue_gemm_tn(S->dA, WIDTH, S->X0, F0, n, gp + O_W1, err, GEMM_CTAS, s, 2 * F0);
+    if (!e) e = enqueue_gemm_tn(S->dA, WIDTH, S->AX, F0, n, gp + O_W1 + F0, err, GEMM_CTAS, s, 2 * F0);
+    return e ? e : cudaGetLastError();
+}
+
+int check_err(ann_surrogate *S, const char *where)
+{
+    unsigned h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, S->err, sizeof h, cudaMemcpyDeviceToHost, S->s);
+    if (!e) e = cudaStreamSynchronize(S->s);
+    if (e) return scuda(S, e, where);
+    if (h) return sfail(S, ANN_ERR_CUDA, std::string(where) + ": a tensor-core wait timed out");
+    return ANN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ann_surrogate_create(int64_t n_max, ann_surrogate **out)
+{
+    if (!out || n_max < 1 || n_max > (1ll << 26)) return ANN_ERR_INVALID_ARG;
+    *out = nullptr;
+    int dev = 0;
+    if (cudaGetDeviceCount(&dev) != cudaSuccess || dev == 0) return ANN_ERR_NOT_AVAILABLE;
+    ann_surrogate *S = new (std::nothrow) ann_surrogate();
+    if (!S) return ANN_ERR_OOM;
+    S->nmax = n_max;
+    size_t n = (size_t)n_max, K2 = WIDTH + MSG;
+    cudaError_t e = cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking);
+#define SA_(p, c) if (!e) e = sg_alloc(S, S->p, c)
+    SA_(nbr, (size_t)MAXN * n); SA_(W, (size_t)MAXN * n); SA_(cnt, n); SA_(S, n); SA_(dr, n);
+    SA_(x, n); SA_(y, n); SA_(u4, n); SA_(tend, 8 * n);
+    SA_(X0, n * F0); SA_(AX, n * F0); SA_(H1, n * WIDTH); SA_(Z1, n * MSG); SA_(AZ1, n * MSG);
+    SA_(H2, n * WIDTH); SA_(Z2, n * MSG); SA_(AZ2, n * MSG); SA_(H3, n * WIDTH);
+    SA_(Y, n * NOUTP); SA_(T, n * NOUT); SA_(dY, n * NOUTP); SA_(dA, n * WIDTH); SA_(dZ, n * MSG);
+    SA_(dH, std::max(n * K2, (size_t)NOUTP * WIDTH));
+    SA_(p, NPARAM); SA_(g, NPARAM); SA_(m, NPARAM); SA_(v, NPARAM);
+    SA_(W1b, WIDTH * 2 * F0); SA_(P1b, MSG * WIDTH); SA_(W2b, WIDTH * K2); SA_(P2b, MSG * WIDTH);
+    SA_(W3b, WIDTH * K2); SA_(Wob, NOUTP * WIDTH); SA_(W3T, K2 * WIDTH); SA_(W2T, K2 * WIDTH);
+    SA_(P2T, WIDTH * MSG); SA_(P1T, WIDTH * MSG); SA_(WoT, WIDTH * NOUTP); SA_(bop, NOUTP);
+    SA_(loss, 1); SA_(err, 1);
+#undef SA_
+    if (!e) e = cudaStreamSynchronize(S->s);
+    if (e) {
+        int code = e == cudaErrorMemoryAllocation ? ANN_ERR_OOM : ANN_ERR_CUDA;
+        ann_surrogate_destroy(S);
+        return code;
+    }
+    *out = S;
+    return ANN_OK;
+}
+
+void ann_surrogate_destroy(ann_surrogate *S)
+{
+    if (!S) return;
+    if (S->s) cudaStreamSynchronize(S->s);
+    for (void *p : S->allocs) cudaFree(p);
+    if (S->s) cudaStreamDestroy(S->s);
+    delete S;
+}
+
+int ann_surrogate_set_params(ann_surrogate *S, const float *params)
+{
+    if (!S || !params) return ANN_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(S->p, params, NPARAM * sizeof(float), cudaMemcpyHostToDevice, S->s);
+    if (!e) e = cudaMemsetAsync(S->m, 0, NPARAM * sizeof(float), S->s);
+    if (!e) e = cudaMemsetAsync(S->v, 0, NPARAM * sizeof(float), S->s);
+    if (!e) e = cast_weights(S);
+    if (!e) e = cudaStreamSynchronize(S->s);
+    S->adam_t = 0;
+    return e ? scuda(S, e, "ann_surrogate_set_params") : ANN_OK;
+}
+
+int ann_surrogate_get_params(ann_surrogate *S, float *params)
+{
+    if (!S || !params) return ANN_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(params, S->p, NPARAM * sizeof(float), cudaMemcpyDeviceToHost, S->s);
+    if (!e) e = cudaStreamSynchronize(S->s);
+    return e ? scuda(S, e, "ann_surrogate_get_params") : ANN_OK;
+}
+
+int ann_surrogate_set_scales(ann_surrogate *S, double us, double ys_q, double ys_u, int32_t k)
+{
+    if (!S || !(us > 0.0) || !(ys_q > 0.0) || !(ys_u > 0.0) || !std::isfinite(us) || !std::isfinite(ys_q) ||
+        !std::isfinite(ys_u) || k < 1)
+        return ANN_ERR_INVALID_ARG;
+    S->us = us;
+    S->ysq = ys_q;
+    S->ysu = ys_u;
+    S->k = k;
+    return ANN_OK;
+}
+
+int ann_surrogate_load(ann_surrogate *S, ann_ctx *ctx, const float *tend)
+{
+    if (!S || !ctx) return ANN_ERR_INVALID_ARG;
+    CtxView v;
+    int st = ctx_view(ctx, &v);
+    if (st) return sfail(S, st, "ann_surrogate_load: context has no particles");
+    if (v.P.n > S->nmax) return sfail(S, ANN_ERR_INVALID_ARG, "context has more particles than n_max");
+    size_t n = (size_t)v.P.n;
+    if (tend) {
+        cudaError_t e = cudaMemcpyAsync(S->tend, tend, 8 * n * sizeof(float), cudaMemcpyHostToDevice, S->s);
+        if (!e) e = cudaStreamSynchronize(S->s);
+        if (e) return scuda(S, e, "ann_surrogate_load: tendencies");
+    } else {
+        if (!v.rec_valid)
+            return sfail(S, ANN_ERR_STATE, "the context's last step did not record its tendencies "
+                                          "(ann_set_record(ctx, 1), then ann_step)");
+        const int fields[6] = {ANN_FIELD_AX, ANN_FIELD_AY, ANN_FIELD_QRATE11, ANN_FIELD_QRATE12,
+                               ANN_FIELD_LAPQ11, ANN_FIELD_LAPQ12};
+        const int grads[4] = {ANN_FIELD_GRADU_XX, ANN_FIELD_GRADU_XY, ANN_FIELD_GRADU_YX, ANN_FIELD_GRADU_YY};
+        for (int c = 0; c < 6 && !st; c++)
+            st = ann_get_field(ctx, fields[c], S->tend + (size_t)c * n, (int64_t)(n * sizeof(float)), 1);
+        for (int c = 0; c < 4 && !st; c++)   // into the backward scratch, free outside training
+            st = ann_get_field(ctx, grads[c], S->dH + (size_t)c * n, (int64_t)(n * sizeof(float)), 1);
+        if (st) return sfail(S, st, "ann_surrogate_load: reading the tendencies");
+        k_sg_div_vort<<<nb(n), 256, 0, S->s>>>((int)n, S->dH, S->tend);
+        cudaError_t e = cudaGetLastError();
+        if (!e) e = cudaStreamSynchronize(S->s);
+        if (e) return scuda(S, e, "ann_surrogate_load: tendencies");
+    }
+    st = ctx_search_present(ctx);
+    if (st) return sfail(S, st, "ann_surrogate_load: search");
+    ctx_view(ctx, &v);
+    S->n = v.P.n;
+    S->W0 = v.P.W0;
+    S->L = v.P.L;
+    S->dt = v.P.dt_d;
+    S->rho0 = v.P.rho0;
+    S->gammaK = (double)v.P.Gamma * (double)v.P.K;
+    GraphOut o{S->nbr, S->W, S->cnt, S->S, S->x, S->y, S->u4, S->dr};
+    cudaError_t e = cudaStreamSynchronize(v.stream);
+    if (!e) e = enqueue_export_graph(v.P, v.b, o, S->s);
+    if (!e) {
+        double kdt = S->k * S->dt;
+        TendScales ts{(float)(kdt / S->ysu), (float)(kdt / S->ysq), (float)(S->gammaK * kdt / S->ysq), (float)kdt};
+        k_sg_features<<<nb(S->n), 256, 0, S->s>>>(view(S), S->u4, (float)(1.0 / S->us), S->tend, ts, S->X0);
+        e = cudaGetLastError();
+    }
+    if (!e) e = cudaStreamSynchronize(S->s);
+    if (e) return scuda(S, e, "ann_surrogate_load");
+    S->loaded = true;
+    return ANN_OK;
+}
+
+int ann_surrogate_forward(ann_surrogate *S, float *y)
+{
+    if (!S) return ANN_ERR_INVALID_ARG;
+    if (!S->loaded) return sfail(S, ANN_ERR_STATE, "no graph loaded");
+    cudaError_t e = cudaMemsetAsync(S->err, 0, sizeof(unsigned), S->s);
+    if (!e) e = forward(S);
+    if (!e && y)
+        e = cudaMemcpy2DAsync(y, NOUT * sizeof(float), S->Y, NOUTP * sizeof(float), NOUT * sizeof(float), S->n,
+                              cudaMemcpyDeviceToHost, S->s);
+    if (e) return scuda(S, e, "ann_surrogate_forward");
+    return check_err(S, "ann_surrogate_forward");
+}
+
+int ann_surrogate_gradients(ann_surrogate *S, const float *target, double *loss, float *grads)
+{
+    if (!S || !target) return ANN_ERR_INVALID_ARG;
+    if (!S->loaded) return sfail(S, ANN_ERR_STATE, "no graph loaded");
+    cudaError_t e = cudaMemsetAsync(S->err, 0, sizeof(unsigned), S->s);
+    if (!e) e = cudaMemcpyAsync(S->T, target, (size_t)S->n * NOUT * sizeof(float), cudaMemcpyHostToDevice, S->s);
+    if (!e) e = forward(S);
+    if (!e) e = backward(S);
+    double h = 0.0;
+    if (!e) e = cudaMemcpyAsync(&h, S->loss, sizeof h, cudaMemcpyDeviceToHost, S->s);
+    if (!e && grads) e = cudaMemcpyAsync(grads, S->g, NPARAM * sizeof(float), cudaMemcpyDeviceToHost, S->s);
+    if (e) return scuda(S, e, "ann_surrogate_gradients");
+    int st = check_err(S, "ann_surrogate_gradients");
+    if (loss) *loss = h / (4.0 * S->n);
+    return st;
+}
+
+int ann_surrogate_adam(ann_surrogate *S, double lr)
+{
+    if (!S || !(lr > 0.0)) return ANN_ERR_INVALID_ARG;
+    S->adam_t++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    float bc1 = 1.f - std::pow(b1, (float)S->adam_t), bc2 = 1.f - std::pow(b2, (float)S->adam_t);
+    k_sg_adam<<<nb(NPARAM), 256, 0, S->s>>>(S->p, S->g, S->m, S->v, NPARAM, (float)lr, b1, b2, 1e-8f, bc1, bc2);
+    cudaError_t e = cudaGetLastError();
+    if (!e) e = cast_weights(S);
+    if (!e) e = cudaStreamSynchronize(S->s);
+    return e ? scuda(S, e, "ann_surrogate_adam") : ANN_OK;
+}
+
+int ann_surrogate_jump(ann_surrogate *S, ann_ctx *ctx, const float *tend)
+{
+    if (!S || !ctx) return ANN_ERR_INVALID_ARG;
+    const int k = S->k;
+    int st = ann_surrogate_load(S, ctx, tend);
+    if (st) return st;
+    st = ann_surrogate_forward(S, nullptr);
+    if (st) return st;
+    CtxView v;
+    st = ctx_view(ctx, &v);
+    if (st) return st;
+    k_sg_jump<<<nb(S->n), 256, 0, S->s>>>(S->n, S->x, S->y, S->u4, S->dr, S->Y, S->tend, (float)S->ysq,
+                                          (float)S->ysu, S->dt * k, S->L, S->rho0, v.b.img, v.tmp);
+    cudaError_t e = cudaGetLastError();
+    if (!e) e = cudaStreamSynchronize(S->s);
+    if (e) return scuda(S, e, "ann_surrogate_jump");
+    return ctx_reload(ctx, v.tmp, k);
+}
+
+const char *ann_surrogate_last_error(ann_surrogate *S) { return S ? S->last_err.c_str() : ""; }
+
+}  // extern "C"
