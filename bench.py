@@ -366,6 +366,218 @@ def ensemble_bench(B, steps=100, trial_steps=10, solo_steps=20):
             "timing": "wall clock around synchronised calls"}
 
 
+SG_K = 8                    # steps one surrogate evaluation spans
+SG_TEND = ("AX", "AY", "QRATE11", "QRATE12", "LAPQ11", "LAPQ12", "GRADU_XX", "GRADU_XY", "GRADU_YX", "GRADU_YY")
+SG_STATE = ("X", "Y", "UX", "UY", "Q11", "Q12", "DRHO")
+
+
+def _sg_snapshot(B, ctx, n):
+    import numpy as np
+
+    f = {k: B.ann_get_field(ctx, k, n).astype(np.float64) for k in SG_STATE + SG_TEND}
+    f["tend"] = np.stack([f["AX"], f["AY"], f["QRATE11"], f["QRATE12"], f["LAPQ11"], f["LAPQ12"],
+                          f["GRADU_XX"] + f["GRADU_YY"], f["GRADU_YX"] - f["GRADU_XY"]], axis=1)
+    return f
+
+
+def _sg_trajectory(B, nx, zeta, K, seed, nsnap, spin, u0=0.0):
+    """Recorded plain-SPH snapshots every SG_K steps (ID order) and the context parameters."""
+    import numpy as np
+
+    import sph_inputs as si
+
+    n = nx * nx
+    p = B.ann_default_params(n=n, h=1.3 / nx, zeta=zeta, K=K, dt_mode=1, c0_min=0.5)
+    ctx = B.ann_create(p)
+    try:
+        ic = si.jittered_lattice(nx, seed=seed)
+        if u0 > 0:
+            r = si.uniform53(seed + 900, 2 * n).reshape(2, n) - 0.5
+            ic["ux"], ic["uy"] = u0 * r[0], u0 * r[1]
+        B.ann_set_particles(ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"], ic["rho"])
+        B.ann_set_record(ctx, 1)
+        B.ann_step(ctx, spin)
+        snaps = []
+        for _ in range(nsnap + 1):
+            snaps.append(_sg_snapshot(B, ctx, n))
+            B.ann_step(ctx, SG_K)
+        dt = B.ann_grid_info(p).dt_effective
+    finally:
+        B.ann_destroy(ctx)
+    return p, dt, snaps
+
+
+def _sg_pairs(snaps):
+    return list(zip(snaps[:-1], snaps[1:]))
+
+
+def _sg_residual(a, b, kdt):
+    import numpy as np
+
+    truth = np.stack([b["Q11"] - a["Q11"], b["Q12"] - a["Q12"], b["UX"] - a["UX"], b["UY"] - a["UY"]], axis=1)
+    euler = kdt * np.stack([a["tend"][:, 2], a["tend"][:, 3], a["tend"][:, 0], a["tend"][:, 1]], axis=1)
+    return truth, euler
+
+
+def _sg_train(B, sg, ctx, n, pairs, kdt, ys, iters, lr0):
+    import numpy as np
+
+    losses = []
+    for it in range(iters):
+        a, b = pairs[it % len(pairs)]
+        truth, euler = _sg_residual(a, b, kdt)
+        B.ann_set_particles(ctx, a["X"], a["Y"], a["UX"], a["UY"], a["Q11"], a["Q12"], 1.0 + a["DRHO"])
+        B.ann_surrogate_load(sg, ctx, a["tend"])
+        loss, _ = B.ann_surrogate_gradients(sg, (truth - euler) / ys)
+        B.ann_surrogate_adam(sg, lr0 if it < 0.7 * iters else 0.3 * lr0)
+        losses.append(loss)
+    return float(np.mean(losses[:10])), float(np.mean(losses[-10:]))
+
+
+def _sg_eval(B, sg, ctx, n, pairs, kdt, ys):
+    """Relative error of the surrogate's k-step increment, and of the explicit one, on held-out pairs."""
+    import numpy as np
+
+    en, ee = [], []
+    for a, b in pairs:
+        truth, euler = _sg_residual(a, b, kdt)
+        B.ann_set_particles(ctx, a["X"], a["Y"], a["UX"], a["UY"], a["Q11"], a["Q12"], 1.0 + a["DRHO"])
+        B.ann_surrogate_load(sg, ctx, a["tend"])
+        y = B.ann_surrogate_forward(sg, n)
+        scale = np.linalg.norm(truth)
+        en.append(np.linalg.norm(euler + y * ys - truth) / scale)
+        ee.append(np.linalg.norm(euler - truth) / scale)
+    return float(np.mean(en)), float(np.mean(ee))
+
+
+def surrogate_bench(B, max_err=0.05):
+    """The learned surrogate: pre-trained on 256 x 256 trajectories, fine-tuned and evaluated on the
+    1024 x 1024 workload; held-out k-step error, the speed of one recorded plain step plus a jump
+    against k + 1 plain steps, and a short rollout's defect density and spectrum slope against plain
+    SPH.  The jump is used only when its validation error is below max_err (else plain SPH)."""
+    import numpy as np
+
+    from oracle import surrogate as S_or
+
+    t_all = time.perf_counter()
+    out = {"k": SG_K, "max_err": max_err}
+    # pre-training at 256 x 256: 8 trajectories, zeta in [0.02, 0.1]
+    zetas = [0.02 + 0.08 * z for z in (0.0, 0.15, 0.3, 0.45, 0.6, 0.75, 0.9, 1.0)]
+    trs = [_sg_trajectory(B, 256, z, PARAMS["K"], 300 + s, 10, 200, u0=0.02) for s, z in enumerate(zetas)]
+    dt256 = trs[0][1]
+    kdt = SG_K * dt256
+    train = [pr for _, _, sn in trs[:7] for pr in _sg_pairs(sn)]
+    test = _sg_pairs(trs[7][2])
+    res = [_sg_residual(a, b, kdt) for a, b in train]
+    ys = np.array([np.std(np.concatenate([(t - e)[:, c] for t, e in res])) for c in (0, 0, 2, 2)])
+    ys[0] = ys[1] = np.std(np.concatenate([(t - e)[:, :2].ravel() for t, e in res]))
+    ys[2] = ys[3] = np.std(np.concatenate([(t - e)[:, 2:].ravel() for t, e in res]))
+    us = float(np.sqrt(np.mean(np.concatenate([np.r_[a["UX"], a["UY"]] for a, _ in train]) ** 2)))
+    n256 = 256 * 256
+    c256 = B.ann_create(trs[0][0])
+    sg = B.ann_surrogate_create(NX * NX)
+    try:
+        w0 = S_or.init_params(7)
+        B.ann_surrogate_set_params(sg, np.concatenate([w0[k].ravel() for k in S_or.ORDER]).astype(np.float32))
+        B.ann_surrogate_set_scales(sg, us, ys[0], ys[2], SG_K)
+        t0 = time.perf_counter()
+        l0, l1 = _sg_train(B, sg, c256, n256, train, kdt, ys, 600, 3e-3)
+        out["pretrain"] = {"resolution": 256, "trajectories": 7, "pairs": len(train), "iters": 600,
+                           "loss_first": l0, "loss_last": l1, "seconds": time.perf_counter() - t0}
+        e_net, e_eul = _sg_eval(B, sg, c256, n256, test, kdt, ys)
+        out["pretrain"].update({"heldout_err": e_net, "euler_err": e_eul})
+    finally:
+        B.ann_destroy(c256)
+    # fine-tuning and evaluation at 1024 x 1024 (the workload of the headline metric)
+    try:
+        n = NX * NX
+        p1, dt1, sn = _sg_trajectory(B, NX, PARAMS["zeta"], PARAMS["K"], 11, 14, 300, u0=0.02)
+        kdt1 = SG_K * dt1
+        pairs = _sg_pairs(sn)
+        tr1, te1 = pairs[:10], pairs[10:]
+        res1 = [_sg_residual(a, b, kdt1) for a, b in tr1]
+        ys1 = np.array([0.0] * 4)
+        ys1[0] = ys1[1] = np.std(np.concatenate([(t - e)[:, :2].ravel() for t, e in res1]))
+        ys1[2] = ys1[3] = np.std(np.concatenate([(t - e)[:, 2:].ravel() for t, e in res1]))
+        us1 = float(np.sqrt(np.mean(np.concatenate([np.r_[a["UX"], a["UY"]] for a, _ in tr1]) ** 2)))
+        B.ann_surrogate_set_scales(sg, us1, ys1[0], ys1[2], SG_K)
+        c1 = B.ann_create(p1)
+        try:
+            t0 = time.perf_counter()
+            l0, l1 = _sg_train(B, sg, c1, n, tr1, kdt1, ys1, 200, 1e-3)
+            e_net, e_eul = _sg_eval(B, sg, c1, n, te1, kdt1, ys1)
+            out["finetune"] = {"resolution": NX, "pairs": len(tr1), "iters": 200, "loss_first": l0,
+                               "loss_last": l1, "seconds": time.perf_counter() - t0, "heldout_err": e_net,
+                               "euler_err": e_eul}
+            use = e_net <= max_err
+            out["fallback"] = not use
+            # timing on the last held-out state: one recorded plain step + a jump vs k + 1 plain steps
+            a = te1[-1][0]
+
+            def load():
+                B.ann_set_particles(c1, a["X"], a["Y"], a["UX"], a["UY"], a["Q11"], a["Q12"], 1.0 + a["DRHO"])
+
+            load()
+            B.ann_set_record(c1, 1)
+            B.ann_step(c1, 3)
+            reps = 5
+            t_plain = []
+            for _ in range(reps):
+                t1 = time.perf_counter()
+                B.ann_step(c1, SG_K + 1)
+                t_plain.append(time.perf_counter() - t1)
+            t_cycle = []
+            for _ in range(reps):
+                t1 = time.perf_counter()
+                B.ann_step(c1, 1)
+                B.ann_surrogate_jump(sg, c1, None)
+                t_cycle.append(time.perf_counter() - t1)
+            tp, tc = min(t_plain), min(t_cycle)
+            out["timing"] = {"plain_ms_per_cycle": 1e3 * tp, "surrogate_ms_per_cycle": 1e3 * tc,
+                             "steps_per_cycle": SG_K + 1, "speedup": tp / tc,
+                             "speedup_used": tp / tc if use else 1.0,
+                             "clock": "wall, synchronised calls, min of 5"}
+            # rollout: 25 cycles from the same state, surrogate against plain SPH
+            cyc = 25
+            load()
+            B.ann_step(c1, 1)
+            for _ in range(cyc):
+                B.ann_step(c1, 1)
+                if use:
+                    B.ann_surrogate_jump(sg, c1, None)
+                else:
+                    B.ann_step(c1, SG_K)
+            s_counts, _ = B.ann_defects(c1, 256)
+            s_E = B.ann_energy_spectrum(c1, 256)
+            s_u = {f: B.ann_get_field(c1, f, n).astype(np.float64) for f in ("UX", "UY", "Q11", "Q12")}
+            load()
+            B.ann_step(c1, 1 + cyc * (SG_K + 1))
+            p_counts, _ = B.ann_defects(c1, 256)
+            p_E = B.ann_energy_spectrum(c1, 256)
+            p_u = {f: B.ann_get_field(c1, f, n).astype(np.float64) for f in ("UX", "UY", "Q11", "Q12")}
+            w = 2 * np.pi * np.arange(s_E.size)
+            sl_s = B.ann_spectrum_slope(s_E, 1.0, w[4], w[60])
+            sl_p = B.ann_spectrum_slope(p_E, 1.0, w[4], w[60])
+            dq = np.concatenate([s_u["Q11"] - p_u["Q11"], s_u["Q12"] - p_u["Q12"]])
+            qn = np.concatenate([p_u["Q11"] - a["Q11"], p_u["Q12"] - a["Q12"]])
+            du = np.concatenate([s_u["UX"] - p_u["UX"], s_u["UY"] - p_u["UY"]])
+            un = np.concatenate([p_u["UX"] - a["UX"], p_u["UY"] - a["UY"]])
+            out["rollout"] = {"cycles": cyc, "steps": cyc * (SG_K + 1) + 1, "surrogate_used": use,
+                              "defect_density": [float(s_counts[0] + s_counts[1]), float(p_counts[0] + p_counts[1])],
+                              "defect_density_rel_err": abs(float(s_counts[0] + s_counts[1] - p_counts[0] - p_counts[1]))
+                              / max(float(p_counts[0] + p_counts[1]), 1.0),
+                              "spectrum_slope": [sl_s, sl_p], "spectrum_slope_abs_err": abs(sl_s - sl_p),
+                              "q_increment_rel_err": float(np.linalg.norm(dq) / np.linalg.norm(qn)),
+                              "u_increment_rel_err": float(np.linalg.norm(du) / np.linalg.norm(un)),
+                              "grid": 256, "slope_range": "w in [2 pi 4, 2 pi 60]"}
+        finally:
+            B.ann_destroy(c1)
+    finally:
+        B.ann_surrogate_destroy(sg)
+    out["seconds"] = time.perf_counter() - t_all
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -499,6 +711,8 @@ def run_ours(args):
         line["diagnostics"] = diag_times
     if ws == 1 and not args.no_ensemble:
         line["ensemble"] = ensemble_bench(B)
+    if ws == 1 and not args.no_surrogate:
+        line["surrogate"] = surrogate_bench(B)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(NX)
         ms, cores = oracle_grid_ms(NX, DIAG_M)
@@ -520,6 +734,7 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-member ensemble measurement")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

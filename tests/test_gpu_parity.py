@@ -92,7 +92,7 @@ def test_one_step_intermediates(B, orc, kind):
         g = {k: run.field(k) for k in ("SUMW", "V", "B11", "B12", "B22", "K", "DRHO_HALF",
                                        "DRHO_HAT", "P", "DIVQX", "DIVQY", "AX", "AY", "LAPQ11",
                                        "LAPQ12", "GRADU_XX", "GRADU_XY", "GRADU_YX", "GRADU_YY",
-                                       "APDX", "APDY", "NNBR")}
+                                       "APDX", "APDY", "QRATE11", "QRATE12", "NNBR")}
     finally:
         run.close()
     _, r = _oracle_one_step(orc, p, ic)
@@ -111,6 +111,7 @@ def test_one_step_intermediates(B, orc, kind):
         "gradu": relerr_group([g["GRADU_XX"], g["GRADU_XY"], g["GRADU_YX"], g["GRADU_YY"]],
                               [r["gradu"][:, 0], r["gradu"][:, 1], r["gradu"][:, 2], r["gradu"][:, 3]]),
         "apd": relerr_group([g["APDX"], g["APDY"]], [r["apdx"], r["apdy"]]),
+        "qrate": relerr_group([g["QRATE11"], g["QRATE12"]], [r["qrate11"], r["qrate12"]]),
     }
     bad = {k: e for k, e in errs.items() if not e <= TOL}
     assert not bad, errs
