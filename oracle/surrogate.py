@@ -18,9 +18,12 @@ Laplacian of Q11, Q12 (Eq. 21), and from the corrected velocity gradient D (Eq. 
 D_xx + D_yy and the vorticity D_yx - D_xy -- scaled to increments over the k steps it spans:
     x_i = (r_i, agg(r)_i - r_i, a k dt / ys_u, m k dt / ys_q, (lap Q) Gamma K k dt / ys_q,
            (div u, vort u) k dt)
-Prediction: the explicit k-step Euler increment of the tendencies plus the network's correction,
-    (dQ11, dQ12, dux, duy) = k dt (m11, m12, ax, ay) + (ys_q y0, ys_q y1, ys_u y2, ys_u y3),
-so an untrained network (y = 0) reproduces the Euler macro-step and training learns what it misses.
+Prediction: the explicit k-step increment of the SPH-smoothed rates plus the network's correction,
+    (dQ11, dQ12, dux, duy) = k dt agg(m11, m12, ax, ay) + (ys_q y0, ys_q y1, ys_u y2, ys_u y3),
+so an untrained network (y = 0) reproduces the smoothed Euler macro-step and training learns what
+it misses.  The smoothing matters: k dt reaches k times the explicit viscous limit, where the plain
+Euler increment would amplify grid-scale modes by about 1 - k h^2 kappa^2 / 8 per jump; agg damps
+exactly those modes.
 Layers (relu, width 128, messages of width 32):
     h1 = relu(W1 [x ; agg(x)] + b1)                 W1: 128 x 32
     z1 = P1 h1,  h2 = relu(W2 [h1 ; agg(z1)] + b2)  P1: 32 x 128, W2: 128 x 160
@@ -126,10 +129,10 @@ def features(G: Graph, q11, q12, ux, uy, tend, us, kdt, gamma_k, ys_q, ys_u):
     return x
 
 
-def euler_increment(tend, kdt):
-    """k dt (m11, m12, ax, ay): the explicit k-step increment the network corrects."""
+def euler_increment(G: Graph, tend, kdt):
+    """k dt agg(m11, m12, ax, ay): the smoothed explicit k-step increment the network corrects."""
     tend = np.asarray(tend, dtype=np.float64)
-    return kdt * np.stack([tend[:, 2], tend[:, 3], tend[:, 0], tend[:, 1]], axis=1)
+    return kdt * G.agg(np.stack([tend[:, 2], tend[:, 3], tend[:, 0], tend[:, 1]], axis=1))
 
 
 def tendencies_from_record(rec):

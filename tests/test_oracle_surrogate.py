@@ -96,8 +96,26 @@ def test_features_of_a_uniform_state(S, orc):
     want = [2 * 8e-4 / 0.005, -8e-4 / 0.005, 3 * 8e-4 / 0.01, 4 * 8e-4 / 0.01,
             0.5 * 0.02 * 8e-4 / 0.01, 0.25 * 0.02 * 8e-4 / 0.01, -0.5 * 8e-4, 8e-4]
     assert np.allclose(x[:, 8:], want, rtol=1e-14, atol=0)
-    e = S.euler_increment(tend, 8e-4)
-    assert np.allclose(e, [3 * 8e-4, 4 * 8e-4, 2 * 8e-4, -8e-4], rtol=1e-15, atol=0)
+    e = S.euler_increment(G, tend, 8e-4)   # uniform rates: the SPH mean leaves them unchanged
+    assert np.allclose(e, [3 * 8e-4, 4 * 8e-4, 2 * 8e-4, -8e-4], rtol=1e-14, atol=0)
+
+
+def test_smoothed_increment_damps_the_grid_scale(S, orc):
+    """A checkerboard rate (the highest lattice wavenumber) is nearly removed by the SPH mean, while
+    a long wave passes almost unchanged: the explicit increment cannot amplify grid-scale modes."""
+    ic = si.jittered_lattice(24, seed=0, jitter=0.0)
+    h = 1.3 * ic["dx"]
+    rp, cols = orc.neighbors(ic["x"], ic["y"], 1.0, h)
+    G = S.Graph(ic["x"], ic["y"], 1.0, h, rp, cols)
+    ix = np.floor(ic["x"] * 24).astype(int)
+    iy = np.floor(ic["y"] * 24).astype(int)
+    checker = np.where((ix + iy) % 2 == 0, 1.0, -1.0)
+    wave = np.cos(2 * np.pi * ic["x"])
+    z = np.zeros(G.n)
+    for f, lo, hi in ((checker, 0.0, 0.1), (wave, 0.9, 1.0)):
+        tend = np.stack([f, z, z, z, z, z, z, z], axis=1)
+        ratio = np.linalg.norm(S.euler_increment(G, tend, 1.0)[:, 2]) / np.linalg.norm(f)
+        assert lo <= ratio <= hi, ratio
 
 
 def test_recorded_q_rate_is_the_step_increment_over_dt(orc, S):
