@@ -411,38 +411,57 @@ def _sg_pairs(snaps):
     return list(zip(snaps[:-1], snaps[1:]))
 
 
-def _sg_residual(a, b, kdt):
+def _sg_truth(a, b):
     import numpy as np
 
-    truth = np.stack([b["Q11"] - a["Q11"], b["Q12"] - a["Q12"], b["UX"] - a["UX"], b["UY"] - a["UY"]], axis=1)
-    euler = kdt * np.stack([a["tend"][:, 2], a["tend"][:, 3], a["tend"][:, 0], a["tend"][:, 1]], axis=1)
-    return truth, euler
+    return np.stack([b["Q11"] - a["Q11"], b["Q12"] - a["Q12"], b["UX"] - a["UX"], b["UY"] - a["UY"]], axis=1)
 
 
-def _sg_train(B, sg, ctx, n, pairs, kdt, ys, iters, lr0):
+def _sg_load(B, sg, ctx, a):
+    B.ann_set_particles(ctx, a["X"], a["Y"], a["UX"], a["UY"], a["Q11"], a["Q12"], 1.0 + a["DRHO"])
+    B.ann_surrogate_load(sg, ctx, a["tend"])
+
+
+def _sg_residuals(B, sg, ctx, n, pairs):
+    """(true increment, explicit increment of the library) of every pair."""
+    out = []
+    for a, b in pairs:
+        _sg_load(B, sg, ctx, a)
+        out.append((_sg_truth(a, b), B.ann_surrogate_euler(sg, n).astype("float64")))
+    return out
+
+
+def _sg_scales(res):
+    import numpy as np
+
+    ysq = np.std(np.concatenate([(t - e)[:, :2].ravel() for t, e in res]))
+    ysu = np.std(np.concatenate([(t - e)[:, 2:].ravel() for t, e in res]))
+    return np.array([ysq, ysq, ysu, ysu])
+
+
+def _sg_train(B, sg, ctx, n, pairs, res, ys, iters, lr0):
     import numpy as np
 
     losses = []
     for it in range(iters):
         a, b = pairs[it % len(pairs)]
-        truth, euler = _sg_residual(a, b, kdt)
-        B.ann_set_particles(ctx, a["X"], a["Y"], a["UX"], a["UY"], a["Q11"], a["Q12"], 1.0 + a["DRHO"])
-        B.ann_surrogate_load(sg, ctx, a["tend"])
+        truth, euler = res[it % len(pairs)]
+        _sg_load(B, sg, ctx, a)
         loss, _ = B.ann_surrogate_gradients(sg, (truth - euler) / ys)
         B.ann_surrogate_adam(sg, lr0 if it < 0.7 * iters else 0.3 * lr0)
         losses.append(loss)
     return float(np.mean(losses[:10])), float(np.mean(losses[-10:]))
 
 
-def _sg_eval(B, sg, ctx, n, pairs, kdt, ys):
+def _sg_eval(B, sg, ctx, n, pairs, ys):
     """Relative error of the surrogate's k-step increment, and of the explicit one, on held-out pairs."""
     import numpy as np
 
     en, ee = [], []
     for a, b in pairs:
-        truth, euler = _sg_residual(a, b, kdt)
-        B.ann_set_particles(ctx, a["X"], a["Y"], a["UX"], a["UY"], a["Q11"], a["Q12"], 1.0 + a["DRHO"])
-        B.ann_surrogate_load(sg, ctx, a["tend"])
+        truth = _sg_truth(a, b)
+        _sg_load(B, sg, ctx, a)
+        euler = B.ann_surrogate_euler(sg, n).astype(np.float64)
         y = B.ann_surrogate_forward(sg, n)
         scale = np.linalg.norm(truth)
         en.append(np.linalg.norm(euler + y * ys - truth) / scale)
@@ -457,34 +476,28 @@ def surrogate_bench(B, max_err=0.05):
     SPH.  The jump is used only when its validation error is below max_err (else plain SPH)."""
     import numpy as np
 
-    from oracle import surrogate as S_or
-
     t_all = time.perf_counter()
     out = {"k": SG_K, "max_err": max_err}
     # pre-training at 256 x 256: 8 trajectories, zeta in [0.02, 0.1]
     zetas = [0.02 + 0.08 * z for z in (0.0, 0.15, 0.3, 0.45, 0.6, 0.75, 0.9, 1.0)]
     trs = [_sg_trajectory(B, 256, z, PARAMS["K"], 300 + s, 10, 200, u0=0.02) for s, z in enumerate(zetas)]
-    dt256 = trs[0][1]
-    kdt = SG_K * dt256
     train = [pr for _, _, sn in trs[:7] for pr in _sg_pairs(sn)]
     test = _sg_pairs(trs[7][2])
-    res = [_sg_residual(a, b, kdt) for a, b in train]
-    ys = np.array([np.std(np.concatenate([(t - e)[:, c] for t, e in res])) for c in (0, 0, 2, 2)])
-    ys[0] = ys[1] = np.std(np.concatenate([(t - e)[:, :2].ravel() for t, e in res]))
-    ys[2] = ys[3] = np.std(np.concatenate([(t - e)[:, 2:].ravel() for t, e in res]))
     us = float(np.sqrt(np.mean(np.concatenate([np.r_[a["UX"], a["UY"]] for a, _ in train]) ** 2)))
     n256 = 256 * 256
     c256 = B.ann_create(trs[0][0])
     sg = B.ann_surrogate_create(NX * NX)
     try:
-        w0 = S_or.init_params(7)
-        B.ann_surrogate_set_params(sg, np.concatenate([w0[k].ravel() for k in S_or.ORDER]).astype(np.float32))
+        B.ann_surrogate_init(sg, 7)
+        B.ann_surrogate_set_scales(sg, us, 1.0, 1.0, SG_K)
+        res = _sg_residuals(B, sg, c256, n256, train)
+        ys = _sg_scales(res)
         B.ann_surrogate_set_scales(sg, us, ys[0], ys[2], SG_K)
         t0 = time.perf_counter()
-        l0, l1 = _sg_train(B, sg, c256, n256, train, kdt, ys, 600, 3e-3)
+        l0, l1 = _sg_train(B, sg, c256, n256, train, res, ys, 600, 3e-3)
         out["pretrain"] = {"resolution": 256, "trajectories": 7, "pairs": len(train), "iters": 600,
                            "loss_first": l0, "loss_last": l1, "seconds": time.perf_counter() - t0}
-        e_net, e_eul = _sg_eval(B, sg, c256, n256, test, kdt, ys)
+        e_net, e_eul = _sg_eval(B, sg, c256, n256, test, ys)
         out["pretrain"].update({"heldout_err": e_net, "euler_err": e_eul})
     finally:
         B.ann_destroy(c256)
@@ -492,20 +505,18 @@ def surrogate_bench(B, max_err=0.05):
     try:
         n = NX * NX
         p1, dt1, sn = _sg_trajectory(B, NX, PARAMS["zeta"], PARAMS["K"], 11, 14, 300, u0=0.02)
-        kdt1 = SG_K * dt1
         pairs = _sg_pairs(sn)
         tr1, te1 = pairs[:10], pairs[10:]
-        res1 = [_sg_residual(a, b, kdt1) for a, b in tr1]
-        ys1 = np.array([0.0] * 4)
-        ys1[0] = ys1[1] = np.std(np.concatenate([(t - e)[:, :2].ravel() for t, e in res1]))
-        ys1[2] = ys1[3] = np.std(np.concatenate([(t - e)[:, 2:].ravel() for t, e in res1]))
         us1 = float(np.sqrt(np.mean(np.concatenate([np.r_[a["UX"], a["UY"]] for a, _ in tr1]) ** 2)))
-        B.ann_surrogate_set_scales(sg, us1, ys1[0], ys1[2], SG_K)
         c1 = B.ann_create(p1)
         try:
+            B.ann_surrogate_set_scales(sg, us1, 1.0, 1.0, SG_K)
+            res1 = _sg_residuals(B, sg, c1, n, tr1)
+            ys1 = _sg_scales(res1)
+            B.ann_surrogate_set_scales(sg, us1, ys1[0], ys1[2], SG_K)
             t0 = time.perf_counter()
-            l0, l1 = _sg_train(B, sg, c1, n, tr1, kdt1, ys1, 200, 1e-3)
-            e_net, e_eul = _sg_eval(B, sg, c1, n, te1, kdt1, ys1)
+            l0, l1 = _sg_train(B, sg, c1, n, tr1, res1, ys1, 200, 1e-3)
+            e_net, e_eul = _sg_eval(B, sg, c1, n, te1, ys1)
             out["finetune"] = {"resolution": NX, "pairs": len(tr1), "iters": 200, "loss_first": l0,
                                "loss_last": l1, "seconds": time.perf_counter() - t0, "heldout_err": e_net,
                                "euler_err": e_eul}
@@ -541,12 +552,19 @@ def surrogate_bench(B, max_err=0.05):
             cyc = 25
             load()
             B.ann_step(c1, 1)
-            for _ in range(cyc):
-                B.ann_step(c1, 1)
-                if use:
-                    B.ann_surrogate_jump(sg, c1, None)
-                else:
-                    B.ann_step(c1, SG_K)
+            vmax = []
+            try:
+                for c in range(cyc):
+                    B.ann_step(c1, 1)
+                    if use:
+                        B.ann_surrogate_jump(sg, c1, None)
+                    else:
+                        B.ann_step(c1, SG_K)
+                    vmax.append(B.ann_get_diagnostics(c1)["max_speed"])
+            except B.AnnError as ex:
+                out["rollout"] = {"cycles": cyc, "failed_at_cycle": c, "error": str(ex)[:200],
+                                  "max_speed_per_cycle": vmax}
+                raise _SgRolloutFailed() from ex
             s_counts, _ = B.ann_defects(c1, 256)
             s_E = B.ann_energy_spectrum(c1, 256)
             s_u = {f: B.ann_get_field(c1, f, n).astype(np.float64) for f in ("UX", "UY", "Q11", "Q12")}
@@ -563,6 +581,7 @@ def surrogate_bench(B, max_err=0.05):
             du = np.concatenate([s_u["UX"] - p_u["UX"], s_u["UY"] - p_u["UY"]])
             un = np.concatenate([p_u["UX"] - a["UX"], p_u["UY"] - a["UY"]])
             out["rollout"] = {"cycles": cyc, "steps": cyc * (SG_K + 1) + 1, "surrogate_used": use,
+                              "max_speed_per_cycle": vmax,
                               "defect_density": [float(s_counts[0] + s_counts[1]), float(p_counts[0] + p_counts[1])],
                               "defect_density_rel_err": abs(float(s_counts[0] + s_counts[1] - p_counts[0] - p_counts[1]))
                               / max(float(p_counts[0] + p_counts[1]), 1.0),
@@ -570,12 +589,18 @@ def surrogate_bench(B, max_err=0.05):
                               "q_increment_rel_err": float(np.linalg.norm(dq) / np.linalg.norm(qn)),
                               "u_increment_rel_err": float(np.linalg.norm(du) / np.linalg.norm(un)),
                               "grid": 256, "slope_range": "w in [2 pi 4, 2 pi 60]"}
+        except _SgRolloutFailed:
+            pass
         finally:
             B.ann_destroy(c1)
     finally:
         B.ann_surrogate_destroy(sg)
     out["seconds"] = time.perf_counter() - t_all
     return out
+
+
+class _SgRolloutFailed(Exception):
+    pass
 
 
 def run_ours(args):

@@ -352,7 +352,10 @@ int ann_bf16_gemm_tn(const void *A, int32_t K, const void *B, int32_t N, int64_t
  * with W1 128 x 32, P1, P2 32 x 128, W2, W3 128 x 160, Wo 4 x 128.  Parameters are one FP32 array
  * of ANN_SG_PARAMS values in the order W1, b1, P1, W2, b2, P2, W3, b3, Wo, bo (row-major).
  * Prediction over k steps: the explicit increment plus the network's correction,
- * dQ = k dt m + ys_q (y0, y1), du = k dt a + ys_u (y2, y3); positions advance by k dt (u + u') / 2.  Errors: INVALID_ARG, STATE (nothing loaded), OOM, CUDA (including a
+ * dQ = k dt m + ys_q (y0, y1), du = k dt agg(agg(a)) + ys_u (y2, y3); the acceleration is
+ * SPH-smoothed twice (the mean removes the velocity modes that an explicit step k times beyond the
+ * viscous limit would amplify), the Q rate, mostly the particle-local bulk term, is not; positions
+ * advance by k dt (u + u') / 2.  Errors: INVALID_ARG, STATE (nothing loaded), OOM, CUDA (including a
  * tensor-core wait that timed out), NOT_AVAILABLE.
  */
 #define ANN_SG_PARAMS 54148
@@ -365,6 +368,10 @@ void ann_surrogate_destroy(ann_surrogate *sg);
 /* Host FP32 parameters in and out (ANN_SG_PARAMS values); setting them resets the optimiser. */
 int ann_surrogate_set_params(ann_surrogate *sg, const float *params);
 int ann_surrogate_get_params(ann_surrogate *sg, float *params);
+
+/* Seeded He initialisation: weights N(0, 2 / fan_in) (output layer half that standard deviation),
+ * biases 0, normals by Box-Muller from a counter-based SplitMix64 stream; resets the optimiser. */
+int ann_surrogate_init(ann_surrogate *sg, uint64_t seed);
 
 /* Velocity scale us of the inputs, increment scales ys_q, ys_u of the outputs (all > 0), and the
  * number of steps k >= 1 the network spans (default 8). */
@@ -379,6 +386,10 @@ int ann_surrogate_load(ann_surrogate *sg, ann_ctx *ctx, const float *tend);
 
 /* Network outputs y of the loaded state: host n x 4 FP32, ID order (may be NULL). */
 int ann_surrogate_forward(ann_surrogate *sg, float *y);
+
+/* The explicit increment k dt (m11, m12, agg(agg(a))) of the loaded state: host n x 4 FP32
+ * (dQ11, dQ12, dux, duy), ID order; training targets are (true increment - this) / ys. */
+int ann_surrogate_euler(ann_surrogate *sg, float *inc);
 
 /* Forward and backward against targets t (host n x 4 FP32, ID order): *loss = mean (y - t)^2 over
  * the n x 4 outputs; gradients kept for ann_surrogate_adam and copied to grads (host,

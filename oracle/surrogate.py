@@ -18,12 +18,18 @@ Laplacian of Q11, Q12 (Eq. 21), and from the corrected velocity gradient D (Eq. 
 D_xx + D_yy and the vorticity D_yx - D_xy -- scaled to increments over the k steps it spans:
     x_i = (r_i, agg(r)_i - r_i, a k dt / ys_u, m k dt / ys_q, (lap Q) Gamma K k dt / ys_q,
            (div u, vort u) k dt)
-Prediction: the explicit k-step increment of the SPH-smoothed rates plus the network's correction,
-    (dQ11, dQ12, dux, duy) = k dt agg(m11, m12, ax, ay) + (ys_q y0, ys_q y1, ys_u y2, ys_u y3),
-so an untrained network (y = 0) reproduces the smoothed Euler macro-step and training learns what
-it misses.  The smoothing matters: k dt reaches k times the explicit viscous limit, where the plain
-Euler increment would amplify grid-scale modes by about 1 - k h^2 kappa^2 / 8 per jump; agg damps
-exactly those modes.
+Prediction: an explicit k-step increment plus the network's correction,
+    (dQ11, dQ12, dux, duy) = k dt (m11, m12, agg(agg(a))) + (ys_q y0, ys_q y1, ys_u y2, ys_u y3),
+so an untrained network (y = 0) reproduces that macro-step and training learns what it misses.
+Only the velocity rate is smoothed.  The step's dt sits at the explicit viscous limit, so over k dt
+the plain Euler factor of a velocity mode, 1 - k dt lambda(kappa), falls well below -1 away from
+the longest waves; the compressive modes of the viscous term of Eq. 23 have about three times the
+lambda of the shear modes.  agg multiplies a mode by its SPH transform sigma(kappa), which falls
+from 1 at long waves to ~0 at the lattice scale; one pass still leaves compressive modes near a
+fifth of the lattice wavenumber at |1 - k dt lambda sigma| > 1, two passes (sigma^2) bring every
+lattice mode inside the unit circle once a plain step follows (a pin checks this on a lattice).
+The Q rate is dominated by the local bulk term of H (Eq. 25 with A, C) and by Gamma K lap Q, whose
+k dt is far from its own limit; smoothing it would erase the particle-local part of the rate.
 Layers (relu, width 128, messages of width 32):
     h1 = relu(W1 [x ; agg(x)] + b1)                 W1: 128 x 32
     z1 = P1 h1,  h2 = relu(W2 [h1 ; agg(z1)] + b2)  P1: 32 x 128, W2: 128 x 160
@@ -130,9 +136,9 @@ def features(G: Graph, q11, q12, ux, uy, tend, us, kdt, gamma_k, ys_q, ys_u):
 
 
 def euler_increment(G: Graph, tend, kdt):
-    """k dt agg(m11, m12, ax, ay): the smoothed explicit k-step increment the network corrects."""
+    """k dt (m11, m12, agg(agg(a))): the explicit k-step increment the network corrects."""
     tend = np.asarray(tend, dtype=np.float64)
-    return kdt * G.agg(np.stack([tend[:, 2], tend[:, 3], tend[:, 0], tend[:, 1]], axis=1))
+    return kdt * np.concatenate([tend[:, 2:4], G.agg(G.agg(tend[:, 0:2]))], axis=1)
 
 
 def tendencies_from_record(rec):

@@ -120,10 +120,12 @@ def lib() -> ctypes.CDLL:
         "ann_surrogate_create": (i32, [i64, _P(vp)]),
         "ann_surrogate_destroy": (None, [vp]),
         "ann_surrogate_set_params": (i32, [vp, _P(ctypes.c_float)]),
+        "ann_surrogate_init": (i32, [vp, ctypes.c_uint64]),
         "ann_surrogate_get_params": (i32, [vp, _P(ctypes.c_float)]),
         "ann_surrogate_set_scales": (i32, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, i32]),
         "ann_surrogate_load": (i32, [vp, vp, _P(ctypes.c_float)]),
         "ann_surrogate_forward": (i32, [vp, _P(ctypes.c_float)]),
+        "ann_surrogate_euler": (i32, [vp, _P(ctypes.c_float)]),
         "ann_surrogate_gradients": (i32, [vp, _P(ctypes.c_float), _P(ctypes.c_double), _P(ctypes.c_float)]),
         "ann_surrogate_adam": (i32, [vp, ctypes.c_double]),
         "ann_surrogate_jump": (i32, [vp, vp, _P(ctypes.c_float)]),
@@ -570,3 +572,14 @@ def ann_surrogate_jump(sg, ctx, tend=None) -> None:
 
 def ann_surrogate_last_error(sg) -> str:
     return lib().ann_surrogate_last_error(sg).decode()
+
+
+def ann_surrogate_init(sg, seed: int) -> None:
+    _scheck(lib().ann_surrogate_init(sg, int(seed)), sg, "ann_surrogate_init")
+
+
+def ann_surrogate_euler(sg, n: int):
+    """The explicit increment (n x 4: dQ11, dQ12, dux, duy; acceleration smoothed) of the loaded state."""
+    inc = np.zeros((n, 4), dtype=np.float32)
+    _scheck(lib().ann_surrogate_euler(sg, _fp(inc)), sg, "ann_surrogate_euler")
+    return inc

@@ -6,7 +6,10 @@
 //             (div u, vort u) k dt), r = (Q11, Q12, ux / us, uy / us), with the tendencies of the
 //             last recorded step: acceleration a, projected Q rate m, Laplacian of Q, and the
 //             divergence and vorticity of the corrected velocity gradient
-//   prediction  (dQ, du) = k dt (m, a) + (ys_q y0, ys_q y1, ys_u y2, ys_u y3)
+//   prediction  (dQ, du) = k dt (m, agg(agg(a))) + (ys_q y0, ys_q y1, ys_u y2, ys_u y3): the
+//               explicit increment, with the acceleration SPH-smoothed twice (the mean removes the
+//               velocity modes that k dt beyond the explicit viscous limit would amplify), plus
+//               the network's correction
 //   h1 = relu(W1 [x ; agg(x)] + b1),  z1 = P1 h1,  h2 = relu(W2 [h1 ; agg(z1)] + b2),
 //   z2 = P2 h2,  h3 = relu(W3 [h2 ; agg(z2)] + b3),  y = Wo h3 + bo
 //   agg(f)_i = (W(0) f_i + sum_j W_ij f_j) / S_i,  S_i = W(0) + sum_j W_ij   (an SPH mean, Eq. 19)
@@ -88,6 +91,39 @@ __global__ void k_sg_div_vort(int n, const float *gu, float *tend)
     if (i >= n) return;
     tend[6 * (size_t)n + i] = gu[i] + gu[3 * (size_t)n + i];
     tend[7 * (size_t)n + i] = gu[2 * (size_t)n + i] - gu[(size_t)n + i];
+}
+
+// out = agg(in) for two FP32 planes (component-major, n apart).
+__global__ void k_sg_mean2(GraphView g, const float *in, float *out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const float *fx = in, *fy = in + g.n;
+    float is = 1.f / g.S[i];
+    float sx = g.W0 * is * fx[i], sy = g.W0 * is * fy[i];
+    int m = g.cnt[i];
+    for (int k = 0; k < m; k++) {
+        int j = g.nbr[(size_t)k * g.n + i];
+        float w = g.W[(size_t)k * g.n + i] * is;
+        sx += w * fx[j];
+        sy += w * fy[j];
+    }
+    out[i] = sx;
+    out[(size_t)g.n + i] = sy;
+}
+
+// inc[i] = k dt (m11, m12, agg(agg(a))x, agg(agg(a))y)[i]: the explicit increment in the order of
+// the outputs (dQ11, dQ12, dux, duy); aa holds agg(agg(a)).  Only the acceleration is smoothed:
+// the viscous term is the stiff one at the step's dt, and two passes of the SPH mean take out the
+// velocity modes (compressive ones near a fifth of the lattice wavenumber the last to go) that
+// k dt would amplify; the Q rate is mostly the particle-local bulk term and is used as it is.
+__global__ void k_sg_euler(int n, const float *tend, const float *aa, float kdt, float *inc)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 r = make_float4(kdt * tend[(size_t)2 * n + i], kdt * tend[(size_t)3 * n + i], kdt * aa[i],
+                           kdt * aa[(size_t)n + i]);
+    *(float4 *)(inc + (size_t)i * NOUT) = r;
 }
 
 // out[i][c] = agg(in)[i][c] for C channels (BF16 in and out, FP32 sums); thread per (i, c).
@@ -198,21 +234,21 @@ __global__ void k_sg_adam(float *p, const float *g, float *m, float *v, int coun
     p[t] -= lr * (mm / bc1) / (sqrtf(vv / bc2) + eps);
 }
 
-// The jump: u += k dt a + ys_u (y2, y3), Q += k dt m + ys_q (y0, y1), x += k dt (u + u') / 2
+// The jump: (Q, u) += inc + (ys_q y0, ys_q y1, ys_u y2, ys_u y3), x += k dt (u + u') / 2
 // (trapezoid), wrapped with the periodic image count; out7 = x, y, ux, uy, q11, q12, rho (FP64, ID
 // order).
 __global__ void k_sg_jump(int n, const double *x, const double *y, const float4 *u4, const float *dr, const float *Y,
-                          const float *tend, float ysq, float ysu, double dtk, double L, float rho0, int2 *img,
+                          const float *inc, float ysq, float ysu, double dtk, double L, float rho0, int2 *img,
                           double *out7)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float4 s = u4[i];
     const float *yi = Y + (size_t)i * NOUTP;
-    float kdt = (float)dtk;
-    float ux = s.x + (kdt * tend[i] + ysu * yi[2]), uy = s.y + (kdt * tend[(size_t)n + i] + ysu * yi[3]);
-    float q1 = s.z + (kdt * tend[2 * (size_t)n + i] + ysq * yi[0]);
-    float q2 = s.w + (kdt * tend[3 * (size_t)n + i] + ysq * yi[1]);
+    const float *ci = inc + (size_t)i * NOUT;
+    float ux = s.x + (ci[2] + ysu * yi[2]), uy = s.y + (ci[3] + ysu * yi[3]);
+    float q1 = s.z + (ci[0] + ysq * yi[0]);
+    float q2 = s.w + (ci[1] + ysq * yi[1]);
     double xn = x[i] + dtk * 0.5 * ((double)s.x + (double)ux);
     double yn = y[i] + dtk * 0.5 * ((double)s.y + (double)uy);
     int kx = (int)floor(xn / L), ky = (int)floor(yn / L);
@@ -251,7 +287,7 @@ struct ann_surrogate {
     std::string last_err;
     // graph and state, ID order
     int *nbr = nullptr, *cnt = nullptr;
-    float *W = nullptr, *S = nullptr, *dr = nullptr, *tend = nullptr;
+    float *W = nullptr, *S = nullptr, *dr = nullptr, *tend = nullptr, *inc = nullptr;
     double *x = nullptr, *y = nullptr;
     float4 *u4 = nullptr;
     float W0 = 0.f;
@@ -432,7 +468,7 @@ int ann_surrogate_create(int64_t n_max, ann_surrogate **out)
     cudaError_t e = cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking);
 #define SA_(p, c) if (!e) e = sg_alloc(S, S->p, c)
     SA_(nbr, (size_t)MAXN * n); SA_(W, (size_t)MAXN * n); SA_(cnt, n); SA_(S, n); SA_(dr, n);
-    SA_(x, n); SA_(y, n); SA_(u4, n); SA_(tend, 8 * n);
+    SA_(x, n); SA_(y, n); SA_(u4, n); SA_(tend, 8 * n); SA_(inc, 4 * n);
     SA_(X0, n * F0); SA_(AX, n * F0); SA_(H1, n * WIDTH); SA_(Z1, n * MSG); SA_(AZ1, n * MSG);
     SA_(H2, n * WIDTH); SA_(Z2, n * MSG); SA_(AZ2, n * MSG); SA_(H3, n * WIDTH);
     SA_(Y, n * NOUTP); SA_(T, n * NOUT); SA_(dY, n * NOUTP); SA_(dA, n * WIDTH); SA_(dZ, n * MSG);
@@ -539,6 +575,10 @@ int ann_surrogate_load(ann_surrogate *S, ann_ctx *ctx, const float *tend)
         double kdt = S->k * S->dt;
         TendScales ts{(float)(kdt / S->ysu), (float)(kdt / S->ysq), (float)(S->gammaK * kdt / S->ysq), (float)kdt};
         k_sg_features<<<nb(S->n), 256, 0, S->s>>>(view(S), S->u4, (float)(1.0 / S->us), S->tend, ts, S->X0);
+        // dH is free between the gather above and the next backward pass
+        k_sg_mean2<<<nb(S->n), 256, 0, S->s>>>(view(S), S->tend, S->dH);
+        k_sg_mean2<<<nb(S->n), 256, 0, S->s>>>(view(S), S->dH, S->dH + 2 * (size_t)S->n);
+        k_sg_euler<<<nb(S->n), 256, 0, S->s>>>(S->n, S->tend, S->dH + 2 * (size_t)S->n, (float)kdt, S->inc);
         e = cudaGetLastError();
     }
     if (!e) e = cudaStreamSynchronize(S->s);
@@ -601,12 +641,51 @@ int ann_surrogate_jump(ann_surrogate *S, ann_ctx *ctx, const float *tend)
     CtxView v;
     st = ctx_view(ctx, &v);
     if (st) return st;
-    k_sg_jump<<<nb(S->n), 256, 0, S->s>>>(S->n, S->x, S->y, S->u4, S->dr, S->Y, S->tend, (float)S->ysq,
+    k_sg_jump<<<nb(S->n), 256, 0, S->s>>>(S->n, S->x, S->y, S->u4, S->dr, S->Y, S->inc, (float)S->ysq,
                                           (float)S->ysu, S->dt * k, S->L, S->rho0, v.b.img, v.tmp);
     cudaError_t e = cudaGetLastError();
     if (!e) e = cudaStreamSynchronize(S->s);
     if (e) return scuda(S, e, "ann_surrogate_jump");
     return ctx_reload(ctx, v.tmp, k);
+}
+
+// He initialisation: every weight matrix drawn N(0, 2 / fan_in) (the output layer at half that
+// standard deviation), biases 0.  Normals by Box-Muller from SplitMix64 (Steele, Lea and Flood
+// 2014) in counter form: value k of stream `seed` is the mix of seed + (k + 1) * 0x9E3779B97F4A7C15.
+int ann_surrogate_init(ann_surrogate *S, uint64_t seed)
+{
+    if (!S) return ANN_ERR_INVALID_ARG;
+    auto mix = [](uint64_t z) {
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    uint64_t ctr = 0;
+    auto uni = [&]() {   // uniform in (0, 1], 53 bits
+        uint64_t v = mix(seed + (++ctr) * 0x9E3779B97F4A7C15ull);
+        return ((v >> 11) + 1) * (1.0 / 9007199254740992.0);
+    };
+    std::vector<float> p(NPARAM, 0.f);
+    struct M { int off, rows, cols; double gain; };
+    const M ms[] = {{O_W1, WIDTH, 2 * F0, 1.0}, {O_P1, MSG, WIDTH, 1.0}, {O_W2, WIDTH, WIDTH + MSG, 1.0},
+                    {O_P2, MSG, WIDTH, 1.0}, {O_W3, WIDTH, WIDTH + MSG, 1.0}, {O_WO, NOUT, WIDTH, 0.5}};
+    for (const M &m : ms) {
+        double sd = m.gain * std::sqrt(2.0 / m.cols);
+        for (int k = 0; k < m.rows * m.cols; k++) {
+            double u1 = uni(), u2 = uni();
+            p[(size_t)m.off + k] = (float)(sd * std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2));
+        }
+    }
+    return ann_surrogate_set_params(S, p.data());
+}
+
+int ann_surrogate_euler(ann_surrogate *S, float *inc)
+{
+    if (!S || !inc) return ANN_ERR_INVALID_ARG;
+    if (!S->loaded) return sfail(S, ANN_ERR_STATE, "no graph loaded");
+    cudaError_t e = cudaMemcpyAsync(inc, S->inc, (size_t)S->n * NOUT * sizeof(float), cudaMemcpyDeviceToHost, S->s);
+    if (!e) e = cudaStreamSynchronize(S->s);
+    return e ? scuda(S, e, "ann_surrogate_euler") : ANN_OK;
 }
 
 const char *ann_surrogate_last_error(ann_surrogate *S) { return S ? S->last_err.c_str() : ""; }

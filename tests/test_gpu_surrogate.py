@@ -4,7 +4,7 @@
   and weights.  BF16 storage (unit roundoff 2^-9) of inputs, weights and activations through four
   layers and their backward pass bounds the normwise error near 2e-2; the tests allow 3e-2 for
   outputs and 6e-2 for gradients.
-* The jump applies the predicted increments (the explicit k dt (m, a) plus the network's correction)
+* The jump applies the predicted increments (the explicit k dt (m, agg(agg(a))) plus the network's correction)
   to Q and u and moves the particles by k dt (u + u')/2.
 * Trained on 8-step pairs the plain solver generates, the network predicts held-out increments
   better than persistence, than the explicit 8-step Euler increment of the tendencies (the
@@ -77,6 +77,7 @@ def test_forward_and_gradients_match_the_oracle(B, S, orc):
         tend = tend.astype(np.float32).astype(np.float64)
         B.ann_surrogate_load(sg, ctx, tend)
         y = B.ann_surrogate_forward(sg, ic["n"])
+        inc = B.ann_surrogate_euler(sg, ic["n"])
         t = si.uniform53(23, 4 * ic["n"]).reshape(-1, 4) - 0.5
         loss, g = B.ann_surrogate_gradients(sg, t)
     finally:
@@ -87,7 +88,9 @@ def test_forward_and_gradients_match_the_oracle(B, S, orc):
     x = S.features(G, ic["q11"], ic["q12"], ic["ux"], ic["uy"], tend, us, k * p["dt"], p["Gamma"] * p["K"], ysq, ysu)
     yo, c = S.forward(w, G, x)
     go = S.backward(w, G, c, yo, t)
-    errs = {"y": relerr(y, yo), "loss": abs(loss - S.loss(yo, t)) / S.loss(yo, t)}
+    errs = {"y": relerr(y, yo), "loss": abs(loss - S.loss(yo, t)) / S.loss(yo, t),
+            "euler": relerr(inc, S.euler_increment(G, tend, k * p["dt"]))}
+    assert errs["euler"] <= 1e-5, errs   # FP32 sums of the same SPH mean
     gg = _unflat(S, g)
     for k in S.ORDER:
         errs[k] = relerr(gg[k], go[k])
@@ -175,52 +178,53 @@ def test_training_gains_over_the_method_without_it(B, S):
     p = data[0][0]
     pairs = [(p_, a, b) for p_, sn in data for a, b in zip(sn[:-1], sn[1:])]
     train, test = pairs[:36], pairs[36:]
-    kdt = k * p["dt"]
-
-    def residual(a, b):
-        """true 8-step increment minus the explicit one, k dt (m, a), columns dQ11 dQ12 dux duy"""
-        truth = np.stack([b["Q11"] - a["Q11"], b["Q12"] - a["Q12"], b["UX"] - a["UX"], b["UY"] - a["UY"]], axis=1)
-        return truth, truth - S.euler_increment(a["tend"], kdt)
-
-    res = [residual(a, b)[1] for _, a, b in train]
-    ysq = float(np.std(np.concatenate([r[:, :2].ravel() for r in res])))
-    ysu = float(np.std(np.concatenate([r[:, 2:].ravel() for r in res])))
-    us = float(np.sqrt(np.mean(np.concatenate([np.r_[a["UX"], a["UY"]] for _, a, _ in train]) ** 2)))
     n = nx * nx
 
-    def target(a, b):
-        r = residual(a, b)[1]
-        return r / np.array([ysq, ysq, ysu, ysu])
+    def truth_of(a, b):
+        """the true 8-step increment, columns dQ11 dQ12 dux duy"""
+        return np.stack([b["Q11"] - a["Q11"], b["Q12"] - a["Q12"], b["UX"] - a["UX"], b["UY"] - a["UY"]], axis=1)
+
+    def as_ic(a):
+        return {"x": a["X"], "y": a["Y"], "ux": a["UX"], "uy": a["UY"], "q11": a["Q11"], "q12": a["Q12"],
+                "rho": 1.0 + a["DRHO"]}
 
     ctx = B.ann_create(gpu_params(B, p, n))
     sg = B.ann_surrogate_create(n)
     try:
         w = S.init_params(3)
         B.ann_surrogate_set_params(sg, _flat(S, w))
+        us = float(np.sqrt(np.mean(np.concatenate([np.r_[a["UX"], a["UY"]] for _, a, _ in train]) ** 2)))
+        B.ann_surrogate_set_scales(sg, us, 1.0, 1.0, k)
+        euler = []
+        for pp, a, b in train:   # the explicit increment of every training state
+            _load(B, ctx, as_ic(a))
+            B.ann_surrogate_load(sg, ctx, a["tend"])
+            euler.append(B.ann_surrogate_euler(sg, n).astype(np.float64))
+        res = [truth_of(a, b) - e for (_, a, b), e in zip(train, euler)]
+        ysq = float(np.std(np.concatenate([r[:, :2].ravel() for r in res])))
+        ysu = float(np.std(np.concatenate([r[:, 2:].ravel() for r in res])))
+        ys = np.array([ysq, ysq, ysu, ysu])
         B.ann_surrogate_set_scales(sg, us, ysq, ysu, k)
         losses = []
         for it in range(240):
-            pp, a, b = train[it % len(train)]
-            ic = {"x": a["X"], "y": a["Y"], "ux": a["UX"], "uy": a["UY"], "q11": a["Q11"], "q12": a["Q12"],
-                  "rho": 1.0 + a["DRHO"]}
-            _load(B, ctx, ic)
+            j = it % len(train)
+            pp, a, b = train[j]
+            _load(B, ctx, as_ic(a))
             B.ann_surrogate_load(sg, ctx, a["tend"])
-            loss, _ = B.ann_surrogate_gradients(sg, target(a, b))
+            loss, _ = B.ann_surrogate_gradients(sg, res[j] / ys)
             B.ann_surrogate_adam(sg, 3e-3 if it < 160 else 1e-3)
             losses.append(loss)
         first, last = np.mean(losses[:12]), np.mean(losses[-12:])
         errs = {"net": [], "persistence": [], "euler": [], "coarse_step": []}
         for pp, a, b in test:
-            ic = {"x": a["X"], "y": a["Y"], "ux": a["UX"], "uy": a["UY"], "q11": a["Q11"], "q12": a["Q12"],
-                  "rho": 1.0 + a["DRHO"]}
-            truth2, _ = residual(a, b)
-            truth = truth2.T.ravel()
+            ic = as_ic(a)
+            truth = truth_of(a, b).T.ravel()
             scale = np.linalg.norm(truth)
             _load(B, ctx, ic)
             B.ann_surrogate_load(sg, ctx, a["tend"])
             y = B.ann_surrogate_forward(sg, n)
-            eul = S.euler_increment(a["tend"], kdt)
-            pred = (eul + y * np.array([ysq, ysq, ysu, ysu])).T.ravel()
+            eul = B.ann_surrogate_euler(sg, n).astype(np.float64)
+            pred = (eul + y * ys).T.ravel()
             errs["net"].append(np.linalg.norm(pred - truth) / scale)
             errs["euler"].append(np.linalg.norm(eul.T.ravel() - truth) / scale)
             errs["persistence"].append(1.0)

@@ -101,8 +101,9 @@ def test_features_of_a_uniform_state(S, orc):
 
 
 def test_smoothed_increment_damps_the_grid_scale(S, orc):
-    """A checkerboard rate (the highest lattice wavenumber) is nearly removed by the SPH mean, while
-    a long wave passes almost unchanged: the explicit increment cannot amplify grid-scale modes."""
+    """A checkerboard acceleration (the highest lattice wavenumber) is nearly removed by the SPH
+    mean, while a long wave passes almost unchanged: the explicit velocity increment cannot amplify
+    grid-scale modes.  The Q rate is taken as it is, particle by particle."""
     ic = si.jittered_lattice(24, seed=0, jitter=0.0)
     h = 1.3 * ic["dx"]
     rp, cols = orc.neighbors(ic["x"], ic["y"], 1.0, h)
@@ -112,10 +113,50 @@ def test_smoothed_increment_damps_the_grid_scale(S, orc):
     checker = np.where((ix + iy) % 2 == 0, 1.0, -1.0)
     wave = np.cos(2 * np.pi * ic["x"])
     z = np.zeros(G.n)
-    for f, lo, hi in ((checker, 0.0, 0.1), (wave, 0.9, 1.0)):
-        tend = np.stack([f, z, z, z, z, z, z, z], axis=1)
-        ratio = np.linalg.norm(S.euler_increment(G, tend, 1.0)[:, 2]) / np.linalg.norm(f)
+    for f, lo, hi in ((checker, 0.0, 0.01), (wave, 0.8, 1.0)):
+        tend = np.stack([z, f, z, z, z, z, z, z], axis=1)
+        inc = S.euler_increment(G, tend, 1.0)
+        ratio = np.linalg.norm(inc[:, 3]) / np.linalg.norm(f)
         assert lo <= ratio <= hi, ratio
+        assert not inc[:, 2].any()
+        tend = np.stack([z, z, z, f, z, z, z, z], axis=1)
+        inc = S.euler_increment(G, tend, 0.5)
+        assert np.array_equal(inc[:, 1], 0.5 * f) and not inc[:, [0, 2, 3]].any()
+
+
+def test_jump_and_a_plain_step_damp_every_lattice_velocity_mode(S, orc):
+    """Stability of a surrogate cycle with an untrained network: for shear and compressive plane
+    waves of every lattice wavenumber along x and the diagonal, the acceleration of the method's
+    momentum equation (Eq. 23, zeta = 0, uniform density) gives the jump's velocity factor
+    1 + <du, u> / <u, u>; times the modified-Euler factor 1 - z + z^2 / 2 of the plain step that
+    follows (z = dt lambda), it stays inside the unit circle at dt = 0.125 h^2 / nu and k = 8."""
+    nx, k = 24, 8
+    dx = 1.0 / nx
+    h = 1.3 * dx
+    g = (np.arange(nx) + 0.5) * dx
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    x, y = X.ravel(), Y.ravel()
+    n = x.size
+    dt = 0.125 * h * h
+    P = orc.make_params(h=h, dt=dt, eta=1.0, zeta=0.0, c0_min=0.5)
+    nb = orc.Nbrs(x, y, 1.0, h, "cells")
+    _, V = orc.volumes(nb)
+    Bc = orc.correction(nb, V)[:3]
+    G = S.Graph(x, y, 1.0, h, nb.rowptr, nb.cols[:nb.rowptr[-1]])
+    one, z0 = np.ones(n), np.zeros(n)
+    worst = 0.0
+    for diag in (False, True):
+        for m in range(1, nx // 2 + 1):
+            f = np.cos(2 * np.pi * m * (x + y if diag else x))
+            for ux, uy in ((f, f) if diag else (f, z0), (f, -f) if diag else (z0, f)):
+                ax, ay, _, _ = orc.momentum_paper(P, nb, V, Bc, one, z0, ux, uy, z0, z0)
+                uu = np.dot(ux, ux) + np.dot(uy, uy)
+                zr = -dt * (np.dot(ax, ux) + np.dot(ay, uy)) / uu
+                tend = np.stack([ax, ay, z0, z0, z0, z0, z0, z0], axis=1)
+                inc = S.euler_increment(G, tend, k * dt)
+                jump = 1.0 + (np.dot(inc[:, 2], ux) + np.dot(inc[:, 3], uy)) / uu
+                worst = max(worst, abs(jump * (1.0 - zr + 0.5 * zr * zr)))
+    assert worst < 0.97, worst
 
 
 def test_recorded_q_rate_is_the_step_increment_over_dt(orc, S):
