@@ -325,7 +325,8 @@ int ann_get_unwrapped(ann_ctx *ctx, const int64_t *ids, int64_t k, double *xy);
  * ann_bf16_gemm: C[rows x N] = act([A1 | A2] . B^T + bias): A1 rows x K1 and A2 rows x K2 row-major
  * BF16 (A2 NULL when K2 = 0; K1 + K2 = K), B N x K row-major BF16, bias N FP32 or NULL, act = relu
  * (1) or identity (0); C rows x N row-major, BF16 (c_bf16 = 1) or FP32 (0; accumulate = 1 adds to
- * it).  K1, K2 multiples of 16 (K2 may be 0), K in [16, 256]; N a multiple of 16 in [16, 256].
+ * it).  K1, K2 multiples of 16 (K2 may be 0), K in [16, 256]; N a multiple of 16 in [16, 256];
+ * A1, A2, B and C 16-byte aligned.
  *
  * ann_bf16_gemm_tn: C[K x N] += A^T . B over all rows: A rows x K, B rows x N row-major BF16, C
  * K x N row-major FP32 (accumulated with atomics, so the order of the FP32 additions varies between

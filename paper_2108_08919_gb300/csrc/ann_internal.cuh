@@ -128,16 +128,17 @@ cudaError_t enqueue_correlation(int M, double L, const double *grid, int all_ori
 cudaError_t enqueue_defects(int M, const double *grid, signed char *map, unsigned long long *counts, cudaStream_t s);
 cudaError_t enqueue_mixing(const DevParams &P, const Bufs &b, const unsigned char *colors, int G, int S,
                            unsigned *cnt, cudaStream_t s);
-// Neighbour graph of the present positions in particle-ID order (ELL: entry k of row i at
-// k * n + i), for the learned surrogate.
+// Neighbour graph of the present positions in the cell-sorted order of the last search (ELL: entry
+// k of row g at k * n + g; neighbours as sorted indices), for the learned surrogate.
 struct GraphOut {
-    int *nbr;        // MAXN x n neighbour IDs
+    int *nbr;        // MAXN x n neighbour sorted indices
     float *W;        // MAXN x n kernel values W(|x_i - x_j|)
     int *cnt;        // n
     float *S;        // n: W(0) + sum_j W
     double *x, *y;   // n: positions
     float4 *u4;      // n: (ux, uy, q11, q12)
     float *dr;       // n: rho / rho0 - 1
+    int *ids;        // n: particle ID of sorted row g
 };
 cudaError_t enqueue_export_graph(const DevParams &P, const Bufs &b, const GraphOut &o, cudaStream_t s);
 

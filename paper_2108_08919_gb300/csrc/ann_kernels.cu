@@ -1157,22 +1157,23 @@ __global__ void __launch_bounds__(PT) k_export_graph(DevParams P, Bufs b, GraphO
         int si = inner_slot(ts, T, q);
         int gi = sg[si];
         float4 pi = pos[si];
-        int id = b.mid[gi], k = 0;
+        int k = 0;
         for_each_candidate<1>(P, b, gi, b.emask[gi], [&](int off, int, unsigned in) {
             int j = off >> 4;
             if (in && j < T.H && k < MAXN) {
                 float r2 = len2(pair_d(pi, slot_at(pos, off)));
-                o.nbr[(size_t)k * P.n + id] = b.mid[sg[j]];
-                o.W[(size_t)k * P.n + id] = kernel_w<true>(r2, P);
+                o.nbr[(size_t)k * P.n + gi] = sg[j];
+                o.W[(size_t)k * P.n + gi] = kernel_w<true>(r2, P);
                 k++;
             }
         });
-        o.cnt[id] = k;
-        o.S[id] = b.sumW[gi];
-        o.x[id] = b.mx[gi];
-        o.y[id] = b.my[gi];
-        o.u4[id] = make_float4(b.mux[gi], b.muy[gi], b.mq11[gi], b.mq12[gi]);
-        o.dr[id] = b.mdr[gi];
+        o.cnt[gi] = k;
+        o.S[gi] = b.sumW[gi];
+        o.x[gi] = b.mx[gi];
+        o.y[gi] = b.my[gi];
+        o.u4[gi] = make_float4(b.mux[gi], b.muy[gi], b.mq11[gi], b.mq12[gi]);
+        o.dr[gi] = b.mdr[gi];
+        o.ids[gi] = b.mid[gi];
     }
 }
 

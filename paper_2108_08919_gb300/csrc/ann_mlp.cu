@@ -115,6 +115,33 @@ __device__ __forceinline__ uint32_t kmaj_off(int row, int k, int Kt)
 
 __device__ __forceinline__ uint32_t ncols_for(int N) { return N <= 32 ? 32u : (N <= 64 ? 64u : (N <= 128 ? 128u : 256u)); }
 
+// Rows r0 .. r0 + 127 of [A1 | A2] (K = K1 + K2 columns, zero past `rows`) into the canonical layout
+// at sA, by the 128 threads of the CTA.  Thread t moves 16-byte chunks t, t + 128, ... of the tile
+// (consecutive threads read consecutive chunks of a row: coalesced), loading a batch of 8 chunks
+// into registers before storing any, so that 8 loads per thread are in flight at once.
+__device__ __forceinline__ void stage_rows(const __nv_bfloat16 *A1, int K1, const __nv_bfloat16 *A2, int K2, int r0,
+                                           int rows, unsigned char *sA, int tid)
+{
+    const int K = K1 + K2, kc = K / 8, c1 = K1 / 8;
+    for (int u0 = 0; u0 < kc; u0 += 8) {
+        uint4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            v[u] = make_uint4(0u, 0u, 0u, 0u);
+            const int e = tid + MT * (u0 + u), r = e / kc, c = e - r * kc, gr = r0 + r;
+            if (u0 + u < kc && gr < rows) {
+                const __nv_bfloat16 *src = c < c1 ? A1 + (size_t)gr * K1 + c * 8 : A2 + (size_t)gr * K2 + (c - c1) * 8;
+                v[u] = __ldcs(reinterpret_cast<const uint4 *>(src));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int e = tid + MT * (u0 + u), r = e / kc, c = e - r * kc;
+            if (u0 + u < kc) *reinterpret_cast<uint4 *>(sA + kmaj_off(r, c * 8, K)) = v[u];
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // nt: persistent CTAs keep B (N x K) in shared memory and walk 128-row tiles of A.
 // ------------------------------------------------------------------------------------------------
@@ -156,16 +183,7 @@ __global__ void __launch_bounds__(128) k_gemm_nt(NtArgs a)
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int r0 = t * MT;
-        for (int e = tid; e < MT * (K / 8); e += blockDim.x) {
-            int r = e / (K / 8), k8 = (e % (K / 8)) * 8;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            int gr = r0 + r;
-            if (gr < a.rows) {
-                if (k8 < a.K1) v = *reinterpret_cast<const uint4 *>(a.A1 + (size_t)gr * a.K1 + k8);
-                else v = *reinterpret_cast<const uint4 *>(a.A2 + (size_t)gr * a.K2 + (k8 - a.K1));
-            }
-            *reinterpret_cast<uint4 *>(sA + kmaj_off(r, k8, K)) = v;
-        }
+        stage_rows(a.A1, a.K1, a.A2, a.K2, r0, a.rows, sA, tid);
         fence_async_smem();
         fence_before();
         __syncthreads();
@@ -197,15 +215,28 @@ __global__ void __launch_bounds__(128) k_gemm_nt(NtArgs a)
                     if (a.relu) x = fmaxf(x, 0.f);
                     v[k] = x;
                 }
-                if (a.c_bf16) {
-                    __nv_bfloat16 *C = static_cast<__nv_bfloat16 *>(a.C) + (size_t)gr * a.ldc + c0;
+                if (a.c_bf16) {   // 32 bytes of the row: two 16-byte stores
+                    uint4 w[2];
+                    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(w);
 #pragma unroll
-                    for (int k = 0; k < 16; k += 2)
-                        *reinterpret_cast<__nv_bfloat162 *>(C + k) = __floats2bfloat162_rn(v[k], v[k + 1]);
-                } else {
-                    float *C = static_cast<float *>(a.C) + (size_t)gr * a.ldc + c0;
+                    for (int k = 0; k < 8; k++) h[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+                    uint4 *C = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.C) + (size_t)gr * a.ldc + c0);
+                    C[0] = w[0];
+                    C[1] = w[1];
+                } else {          // 64 bytes: four 16-byte stores
+                    float4 *C = reinterpret_cast<float4 *>(static_cast<float *>(a.C) + (size_t)gr * a.ldc + c0);
 #pragma unroll
-                    for (int k = 0; k < 16; k++) C[k] = a.accumulate ? C[k] + v[k] : v[k];
+                    for (int k = 0; k < 4; k++) {
+                        float4 o = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                        if (a.accumulate) {
+                            float4 c = C[k];
+                            o.x += c.x;
+                            o.y += c.y;
+                            o.z += c.z;
+                            o.w += c.w;
+                        }
+                        C[k] = o;
+                    }
                 }
             }
         }
@@ -225,6 +256,43 @@ __global__ void __launch_bounds__(128) k_gemm_nt(NtArgs a)
 // N x rows, both K-major in the rows) and reduced by 8 MMAs of K = 16 rows into TMEM; at the end
 // the CTA adds its 128 x N partial to C with FP32 atomics.
 // ------------------------------------------------------------------------------------------------
+
+// Columns f0 .. f0 + W - 1 (zero past K) of rows r0 .. r0 + 127 (zero past `rows`) of the row-major
+// X (rows x K), transposed into the canonical layout: element (column f, row r) at
+// kmaj_off(f - f0, r, 128).  Thread t owns row r0 + t and reads it in 16-byte chunks (batches of 8
+// in flight) when K is a multiple of 8 and X 16-byte aligned, element by element otherwise.
+__device__ __forceinline__ void stage_rows_T(const __nv_bfloat16 *X, int K, int f0, int r0, int rows, unsigned char *s,
+                                             int W, int tid)
+{
+    const int gr = r0 + tid;
+    const bool live = gr < rows;
+    if ((K & 7) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+        const uint4 *row = reinterpret_cast<const uint4 *>(X + (size_t)(live ? gr : 0) * K);
+        for (int c0 = 0; c0 < W / 8; c0 += 8) {
+            uint4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int f = f0 + (c0 + u) * 8;
+                v[u] = make_uint4(0u, 0u, 0u, 0u);
+                if (live && c0 + u < W / 8 && f < K) v[u] = __ldg(row + f / 8);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                if (c0 + u >= W / 8) break;
+                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&v[u]);
+#pragma unroll
+                for (int q = 0; q < 8; q++)
+                    *reinterpret_cast<__nv_bfloat16 *>(s + kmaj_off((c0 + u) * 8 + q, tid, MT)) = h[q];
+            }
+        }
+    } else {
+        for (int f = 0; f < W; f++) {
+            __nv_bfloat16 v = __float2bfloat16(0.f);
+            if (live && f0 + f < K) v = X[(size_t)gr * K + f0 + f];
+            *reinterpret_cast<__nv_bfloat16 *>(s + kmaj_off(f, tid, MT)) = v;
+        }
+    }
+}
 
 struct TnArgs {
     const __nv_bfloat16 *A;   // rows x K
@@ -257,18 +325,8 @@ __global__ void __launch_bounds__(128) k_gemm_tn(TnArgs a)
     for (int ch = blockIdx.x; ch < nchunks && ok; ch += gridDim.x) {
         const int r0 = ch * MT;
         // A^T: element (feature f, row r) at kmaj_off(f, r, 128); B^T: (n, r) at kmaj_off(n, r, 128)
-        for (int e = tid; e < MT * MT; e += blockDim.x) {
-            int r = e / MT, f = e % MT, gr = r0 + r, gf = f0 + f;
-            __nv_bfloat16 v = __float2bfloat16(0.f);
-            if (gr < a.rows && gf < a.K) v = a.A[(size_t)gr * a.K + gf];
-            *reinterpret_cast<__nv_bfloat16 *>(sA + kmaj_off(f, r, MT)) = v;
-        }
-        for (int e = tid; e < MT * N; e += blockDim.x) {
-            int r = e / N, n = e % N, gr = r0 + r;
-            __nv_bfloat16 v = __float2bfloat16(0.f);
-            if (gr < a.rows) v = a.B[(size_t)gr * N + n];
-            *reinterpret_cast<__nv_bfloat16 *>(sB + kmaj_off(n, r, MT)) = v;
-        }
+        stage_rows_T(a.A, a.K, f0, r0, a.rows, sA, MT, tid);
+        stage_rows_T(a.B, N, 0, r0, a.rows, sB, N, tid);
         fence_async_smem();
         fence_before();
         __syncthreads();
@@ -358,7 +416,9 @@ int ann_bf16_gemm(const void *A1, int32_t K1, const void *A2, int32_t K2, const 
 {
     if (!A1 || !B || !C || rows < 0 || rows > (1ll << 30) || K1 < 16 || K1 % 16 || K2 < 0 || K2 % 16 ||
         (K2 > 0 && !A2) || !ann::gemm_shape_ok(K1 + K2, N) || (relu != 0 && relu != 1) || (c_bf16 != 0 && c_bf16 != 1) ||
-        (accumulate != 0 && accumulate != 1) || (accumulate && c_bf16))
+        (accumulate != 0 && accumulate != 1) || (accumulate && c_bf16) ||
+        ((reinterpret_cast<uintptr_t>(A1) | reinterpret_cast<uintptr_t>(A2) | reinterpret_cast<uintptr_t>(B) |
+          reinterpret_cast<uintptr_t>(C)) & 15))
         return ANN_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned *err = nullptr, zero = 0, h = 0;

@@ -16,7 +16,9 @@
 //
 // Dense products run on the tensor cores (ann_mlp.cu: BF16 operands, FP32 accumulation);
 // activations are stored in BF16, gradients accumulate in FP32, the optimiser (Adam) keeps FP32
-// master weights.  Particles are in ID order throughout.
+// master weights.  On the device the particles are in the cell-sorted order of the context's last
+// search, so that neighbour rows gathered by the SPH mean sit close in memory; host inputs and
+// outputs are in ID order and are permuted on the way in or out.
 #include "../../include/ann.h"
 #include "ann_internal.cuh"
 
@@ -49,7 +51,7 @@ struct GraphView {
     float W0;
 };
 
-// tend: 8 x n (component-major, ID order): ax, ay, m11, m12, lapQ11, lapQ12, div u, vort u
+// tend: 8 x n (component-major, sorted order): ax, ay, m11, m12, lapQ11, lapQ12, div u, vort u
 struct TendScales {
     float a, m, lap, grad;
 };
@@ -64,10 +66,11 @@ __global__ void k_sg_features(GraphView g, const float4 *u4, float inv_us, const
     float is = 1.f / g.S[i], a[4];
     for (int c = 0; c < 4; c++) a[c] = g.W0 * is * r[c];
     int m = g.cnt[i];
+#pragma unroll 4
     for (int k = 0; k < m; k++) {
-        int j = g.nbr[(size_t)k * g.n + i];
-        float w = g.W[(size_t)k * g.n + i] * is;
-        float4 t = u4[j];
+        int j = __ldg(g.nbr + (size_t)k * g.n + i);
+        float w = __ldg(g.W + (size_t)k * g.n + i) * is;
+        float4 t = __ldg(u4 + j);
         a[0] += w * t.z;
         a[1] += w * t.w;
         a[2] += w * t.x * inv_us;
@@ -84,13 +87,51 @@ __global__ void k_sg_features(GraphView g, const float4 *u4, float inv_us, const
     }
 }
 
-// div u = D_xx + D_yy and vort u = D_yx - D_xy from the four gradient components (4 x n).
-__global__ void k_sg_div_vort(int n, const float *gu, float *tend)
+// The tendencies of the context's last recorded step, into ID order (8 x n, component-major):
+// the accelerations are held in the state order (slot g is particle sid[g]), the recorded Q rate
+// (2 per slot), Laplacian of Q (2) and velocity gradient (4: xx, xy, yx, yy) in the sorted order of
+// that step's search (slot g is particle mid[g]); div u = D_xx + D_yy, vort u = D_yx - D_xy.
+__global__ void k_sg_tend_from_ctx(int n, const int *sid, const int *mid, const float *sax, const float *say,
+                                   const float *qrate, const float *lap, const float *gu, float *tend)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    tend[6 * (size_t)n + i] = gu[i] + gu[3 * (size_t)n + i];
-    tend[7 * (size_t)n + i] = gu[2 * (size_t)n + i] - gu[(size_t)n + i];
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const size_t N = (size_t)n;
+    const int a = sid[g], m = mid[g];
+    tend[a] = sax[g];
+    tend[N + a] = say[g];
+    tend[2 * N + m] = qrate[2 * (size_t)g];
+    tend[3 * N + m] = qrate[2 * (size_t)g + 1];
+    tend[4 * N + m] = lap[2 * (size_t)g];
+    tend[5 * N + m] = lap[2 * (size_t)g + 1];
+    const float *d = gu + 4 * (size_t)g;
+    tend[6 * N + m] = d[0] + d[3];
+    tend[7 * N + m] = d[2] - d[1];
+}
+
+// dst[c n + g] = src[c n + ids[g]] for C planes: ID order into the graph's sorted order.
+__global__ void k_sg_gather_planes(int n, int C, const int *ids, const float *src, float *dst)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const int i = ids[g];
+    for (int c = 0; c < C; c++) dst[(size_t)c * n + g] = src[(size_t)c * n + i];
+}
+
+// Rows of 4 between the graph's sorted order and ID order: to_id: dst[ids[g]] = src[g] (src row
+// stride ld); from_id: dst[g] = src[ids[g]].
+__global__ void k_sg_rows_to_id(int n, const int *ids, const float *src, int ld, float *dst)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    reinterpret_cast<float4 *>(dst)[ids[g]] = *reinterpret_cast<const float4 *>(src + (size_t)g * ld);
+}
+
+__global__ void k_sg_rows_from_id(int n, const int *ids, const float *src, float *dst)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    reinterpret_cast<float4 *>(dst)[g] = reinterpret_cast<const float4 *>(src)[ids[g]];
 }
 
 // out = agg(in) for two FP32 planes (component-major, n apart).
@@ -102,11 +143,12 @@ __global__ void k_sg_mean2(GraphView g, const float *in, float *out)
     float is = 1.f / g.S[i];
     float sx = g.W0 * is * fx[i], sy = g.W0 * is * fy[i];
     int m = g.cnt[i];
+#pragma unroll 4
     for (int k = 0; k < m; k++) {
-        int j = g.nbr[(size_t)k * g.n + i];
-        float w = g.W[(size_t)k * g.n + i] * is;
-        sx += w * fx[j];
-        sy += w * fy[j];
+        int j = __ldg(g.nbr + (size_t)k * g.n + i);
+        float w = __ldg(g.W + (size_t)k * g.n + i) * is;
+        sx += w * __ldg(fx + j);
+        sy += w * __ldg(fy + j);
     }
     out[i] = sx;
     out[(size_t)g.n + i] = sy;
@@ -126,38 +168,98 @@ __global__ void k_sg_euler(int n, const float *tend, const float *aa, float kdt,
     *(float4 *)(inc + (size_t)i * NOUT) = r;
 }
 
-// out[i][c] = agg(in)[i][c] for C channels (BF16 in and out, FP32 sums); thread per (i, c).
-template <int C>
-__global__ void k_sg_agg(GraphView g, const bf16 *in, bf16 *out)
+__device__ __forceinline__ void fma8_bf16(float *acc, uint4 r, float w)
 {
-    size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (size_t)g.n * C) return;
-    int i = (int)(t / C), c = (int)(t % C);
-    float is = 1.f / g.S[i];
-    float acc = g.W0 * is * __bfloat162float(in[(size_t)i * C + c]);
-    int m = g.cnt[i];
-    for (int k = 0; k < m; k++) {
-        int j = g.nbr[(size_t)k * g.n + i];
-        acc += g.W[(size_t)k * g.n + i] * is * __bfloat162float(in[(size_t)j * C + c]);
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&r);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        float2 f = __bfloat1622float2(h[q]);
+        acc[2 * q] = fmaf(w, f.x, acc[2 * q]);
+        acc[2 * q + 1] = fmaf(w, f.y, acc[2 * q + 1]);
     }
-    out[(size_t)i * C + c] = __float2bfloat16(acc);
 }
 
-// The adjoint of agg: out[j][c] = W(0)/S_j in[j][c] + sum_{i in N(j)} W_ij / S_i in[i][c]; the
-// neighbour relation is symmetric, so j's own row lists the i and W_ij.  in: FP32, row stride ld.
-template <int C>
-__global__ void k_sg_agg_T(GraphView g, const float *in, int ld, bf16 *out)
+__device__ __forceinline__ uint4 pack8_bf16(const float *v, float s)
 {
-    size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (size_t)g.n * C) return;
-    int j = (int)(t / C), c = (int)(t % C);
-    float acc = g.W0 / g.S[j] * in[(size_t)j * ld + c];
-    int m = g.cnt[j];
-    for (int k = 0; k < m; k++) {
-        int i = g.nbr[(size_t)k * g.n + j];
-        acc += g.W[(size_t)k * g.n + j] / g.S[i] * in[(size_t)i * ld + c];
+    uint4 r;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&r);
+#pragma unroll
+    for (int q = 0; q < 4; q++) h[q] = __floats2bfloat162_rn(v[2 * q] * s, v[2 * q + 1] * s);
+    return r;
+}
+
+// out[i] = agg(in)[i] for rows of C BF16 channels (FP32 sums).  C / 8 lanes per particle, each
+// gathering 16 bytes (8 channels) of every neighbour row; neighbours are taken four at a time so
+// that four row loads per lane are in flight.
+template <int C>
+__global__ void __launch_bounds__(256) k_sg_agg(GraphView g, const bf16 *in, bf16 *out)
+{
+    constexpr int LP = C / 8;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(t / LP), q = (int)(t % LP);
+    if (i >= g.n) return;
+    const uint4 *src = reinterpret_cast<const uint4 *>(in) + q;
+    const size_t n = (size_t)g.n;
+    float acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) acc[c] = 0.f;
+    fma8_bf16(acc, __ldg(src + (size_t)i * LP), g.W0);
+    const int m = g.cnt[i];
+    const int *nb = g.nbr + i;
+    const float *wp = g.W + i;
+    int k = 0;
+    for (; k + 4 <= m; k += 4) {
+        int j[4];
+        float w[4];
+        uint4 r[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            j[u] = __ldg(nb + (k + u) * n);
+            w[u] = __ldg(wp + (k + u) * n);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) r[u] = __ldg(src + (size_t)j[u] * LP);
+#pragma unroll
+        for (int u = 0; u < 4; u++) fma8_bf16(acc, r[u], w[u]);
     }
-    out[(size_t)j * C + c] = __float2bfloat16(acc);
+    for (; k < m; k++) fma8_bf16(acc, __ldg(src + (size_t)__ldg(nb + k * n) * LP), __ldg(wp + k * n));
+    reinterpret_cast<uint4 *>(out)[(size_t)i * LP + q] = pack8_bf16(acc, 1.f / g.S[i]);
+}
+
+// The adjoint of agg: out[j] = W(0)/S_j in[j] + sum_{i in N(j)} W_ij / S_i in[i]; the neighbour
+// relation is symmetric, so j's own row lists the i and W_ij.  in: FP32 rows of C channels at row
+// stride ld (a multiple of 4, 16-byte aligned rows); C / 8 lanes per particle, 8 channels each.
+template <int C>
+__global__ void __launch_bounds__(256) k_sg_agg_T(GraphView g, const float *in, int ld, bf16 *out)
+{
+    constexpr int LP = C / 8;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = (int)(t / LP), q = (int)(t % LP);
+    if (j >= g.n) return;
+    const size_t n = (size_t)g.n;
+    float acc[8];
+    auto add = [&](int i, float w) {
+        const float4 *p = reinterpret_cast<const float4 *>(in + (size_t)i * ld) + 2 * q;
+        float4 a = __ldg(p), b = __ldg(p + 1);
+        acc[0] = fmaf(w, a.x, acc[0]);
+        acc[1] = fmaf(w, a.y, acc[1]);
+        acc[2] = fmaf(w, a.z, acc[2]);
+        acc[3] = fmaf(w, a.w, acc[3]);
+        acc[4] = fmaf(w, b.x, acc[4]);
+        acc[5] = fmaf(w, b.y, acc[5]);
+        acc[6] = fmaf(w, b.z, acc[6]);
+        acc[7] = fmaf(w, b.w, acc[7]);
+    };
+#pragma unroll
+    for (int c = 0; c < 8; c++) acc[c] = 0.f;
+    add(j, g.W0 / g.S[j]);
+    const int m = g.cnt[j];
+#pragma unroll 4
+    for (int k = 0; k < m; k++) {
+        const int i = __ldg(g.nbr + k * n + j);
+        add(i, __ldg(g.W + k * n + j) / __ldg(g.S + i));
+    }
+    reinterpret_cast<uint4 *>(out)[(size_t)j * LP + q] = pack8_bf16(acc, 1.f);
 }
 
 // dY = 2 (y - t) / (4 n) on the 4 outputs (0 on the padding), and the sum of (y - t)^2.
@@ -235,14 +337,15 @@ __global__ void k_sg_adam(float *p, const float *g, float *m, float *v, int coun
 }
 
 // The jump: (Q, u) += inc + (ys_q y0, ys_q y1, ys_u y2, ys_u y3), x += k dt (u + u') / 2
-// (trapezoid), wrapped with the periodic image count; out7 = x, y, ux, uy, q11, q12, rho (FP64, ID
-// order).
-__global__ void k_sg_jump(int n, const double *x, const double *y, const float4 *u4, const float *dr, const float *Y,
-                          const float *inc, float ysq, float ysu, double dtk, double L, float rho0, int2 *img,
-                          double *out7)
+// (trapezoid), wrapped with the periodic image count; row i is particle ids[i], and out7 = x, y, ux,
+// uy, q11, q12, rho (FP64) in ID order.
+__global__ void k_sg_jump(int n, const int *ids, const double *x, const double *y, const float4 *u4, const float *dr,
+                          const float *Y, const float *inc, float ysq, float ysu, double dtk, double L, float rho0,
+                          int2 *img, double *out7)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int id = ids[i];
     float4 s = u4[i];
     const float *yi = Y + (size_t)i * NOUTP;
     const float *ci = inc + (size_t)i * NOUT;
@@ -257,16 +360,16 @@ __global__ void k_sg_jump(int n, const double *x, const double *y, const float4 
     if (xn >= L) xn -= L;   // rounding at the face
     if (yn >= L) yn -= L;
     if (kx | ky) {
-        img[i].x += kx;
-        img[i].y += ky;
+        img[id].x += kx;
+        img[id].y += ky;
     }
-    out7[i] = xn;
-    out7[(size_t)n + i] = yn;
-    out7[2 * (size_t)n + i] = ux;
-    out7[3 * (size_t)n + i] = uy;
-    out7[4 * (size_t)n + i] = q1;
-    out7[5 * (size_t)n + i] = q2;
-    out7[6 * (size_t)n + i] = (double)rho0 * (1.0 + (double)dr[i]);
+    out7[id] = xn;
+    out7[(size_t)n + id] = yn;
+    out7[2 * (size_t)n + id] = ux;
+    out7[3 * (size_t)n + id] = uy;
+    out7[4 * (size_t)n + id] = q1;
+    out7[5 * (size_t)n + id] = q2;
+    out7[6 * (size_t)n + id] = (double)rho0 * (1.0 + (double)dr[i]);
 }
 
 inline unsigned nb(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -285,9 +388,11 @@ struct ann_surrogate {
     cudaStream_t s = nullptr;
     std::vector<void *> allocs;
     std::string last_err;
-    // graph and state, ID order
-    int *nbr = nullptr, *cnt = nullptr;
-    float *W = nullptr, *S = nullptr, *dr = nullptr, *tend = nullptr, *inc = nullptr;
+    // graph and state in the context's cell-sorted order (row g is particle ids[g]); tend_id and
+    // io4 hold ID-ordered tendencies and host rows on their way in or out
+    int *nbr = nullptr, *cnt = nullptr, *ids = nullptr;
+    float *W = nullptr, *S = nullptr, *dr = nullptr, *tend = nullptr, *inc = nullptr, *tend_id = nullptr,
+          *io4 = nullptr;
     double *x = nullptr, *y = nullptr;
     float4 *u4 = nullptr;
     float W0 = 0.f;
@@ -360,17 +465,17 @@ cudaError_t forward(ann_surrogate *S)
     int n = S->n;
     GraphView g = view(S);
     unsigned *err = S->err;
-    k_sg_agg<F0><<<nb((size_t)n * F0), 256, 0, s>>>(g, S->X0, S->AX);
+    k_sg_agg<F0><<<nb((size_t)n * (F0 / 8)), 256, 0, s>>>(g, S->X0, S->AX);
     cudaError_t e = enqueue_gemm_nt(S->X0, F0, S->AX, F0, S->W1b, WIDTH, n, S->p + O_B1, 1, S->H1, 1, 0, err,
                                     GEMM_CTAS, s);
     if (!e) e = enqueue_gemm_nt(S->H1, WIDTH, nullptr, 0, S->P1b, MSG, n, nullptr, 0, S->Z1, 1, 0, err, GEMM_CTAS, s);
     if (!e) {
-        k_sg_agg<MSG><<<nb((size_t)n * MSG), 256, 0, s>>>(g, S->Z1, S->AZ1);
+        k_sg_agg<MSG><<<nb((size_t)n * (MSG / 8)), 256, 0, s>>>(g, S->Z1, S->AZ1);
         e = enqueue_gemm_nt(S->H1, WIDTH, S->AZ1, MSG, S->W2b, WIDTH, n, S->p + O_B2, 1, S->H2, 1, 0, err, GEMM_CTAS, s);
     }
     if (!e) e = enqueue_gemm_nt(S->H2, WIDTH, nullptr, 0, S->P2b, MSG, n, nullptr, 0, S->Z2, 1, 0, err, GEMM_CTAS, s);
     if (!e) {
-        k_sg_agg<MSG><<<nb((size_t)n * MSG), 256, 0, s>>>(g, S->Z2, S->AZ2);
+        k_sg_agg<MSG><<<nb((size_t)n * (MSG / 8)), 256, 0, s>>>(g, S->Z2, S->AZ2);
         e = enqueue_gemm_nt(S->H2, WIDTH, S->AZ2, MSG, S->W3b, WIDTH, n, S->p + O_B3, 1, S->H3, 1, 0, err, GEMM_CTAS, s);
     }
     if (!e) e = enqueue_gemm_nt(S->H3, WIDTH, nullptr, 0, S->Wob, NOUTP, n, S->bop, 0, S->Y, 0, 0, err, GEMM_CTAS, s);
@@ -412,7 +517,7 @@ cudaError_t backward(ann_surrogate *S)
     if (!e) e = enqueue_gemm_tn(S->dA, WIDTH, S->AZ2, MSG, n, gp + O_W3 + WIDTH, err, GEMM_CTAS, s, K2);
     if (!e) e = enqueue_gemm_nt(S->dA, WIDTH, nullptr, 0, S->W3T, K2, n, nullptr, 0, S->dH, 0, 0, err, GEMM_CTAS, s);
     if (e) return e;
-    k_sg_agg_T<MSG><<<nb((size_t)n * MSG), 256, 0, s>>>(g, S->dH + WIDTH, K2, S->dZ);
+    k_sg_agg_T<MSG><<<nb((size_t)n * (MSG / 8)), 256, 0, s>>>(g, S->dH + WIDTH, K2, S->dZ);
     e = enqueue_gemm_tn(S->dZ, MSG, S->H2, WIDTH, n, gp + O_P2, err, GEMM_CTAS, s);
     if (!e) e = enqueue_gemm_nt(S->dZ, MSG, nullptr, 0, S->P2T, WIDTH, n, nullptr, 0, S->dH, 0, 1, err, GEMM_CTAS, s, K2);
     if (e) return e;
@@ -426,7 +531,7 @@ cudaError_t backward(ann_surrogate *S)
     if (!e) e = enqueue_gemm_tn(S->dA, WIDTH, S->AZ1, MSG, n, gp + O_W2 + WIDTH, err, GEMM_CTAS, s, K2);
     if (!e) e = enqueue_gemm_nt(S->dA, WIDTH, nullptr, 0, S->W2T, K2, n, nullptr, 0, S->dH, 0, 0, err, GEMM_CTAS, s);
     if (e) return e;
-    k_sg_agg_T<MSG><<<nb((size_t)n * MSG), 256, 0, s>>>(g, S->dH + WIDTH, K2, S->dZ);
+    k_sg_agg_T<MSG><<<nb((size_t)n * (MSG / 8)), 256, 0, s>>>(g, S->dH + WIDTH, K2, S->dZ);
     e = enqueue_gemm_tn(S->dZ, MSG, S->H1, WIDTH, n, gp + O_P1, err, GEMM_CTAS, s);
     if (!e) e = enqueue_gemm_nt(S->dZ, MSG, nullptr, 0, S->P1T, WIDTH, n, nullptr, 0, S->dH, 0, 1, err, GEMM_CTAS, s, K2);
     if (e) return e;
@@ -468,7 +573,8 @@ int ann_surrogate_create(int64_t n_max, ann_surrogate **out)
     cudaError_t e = cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking);
 #define SA_(p, c) if (!e) e = sg_alloc(S, S->p, c)
     SA_(nbr, (size_t)MAXN * n); SA_(W, (size_t)MAXN * n); SA_(cnt, n); SA_(S, n); SA_(dr, n);
-    SA_(x, n); SA_(y, n); SA_(u4, n); SA_(tend, 8 * n); SA_(inc, 4 * n);
+    SA_(x, n); SA_(y, n); SA_(u4, n); SA_(tend, 8 * n); SA_(inc, 4 * n); SA_(ids, n); SA_(tend_id, 8 * n);
+    SA_(io4, 4 * n);
     SA_(X0, n * F0); SA_(AX, n * F0); SA_(H1, n * WIDTH); SA_(Z1, n * MSG); SA_(AZ1, n * MSG);
     SA_(H2, n * WIDTH); SA_(Z2, n * MSG); SA_(AZ2, n * MSG); SA_(H3, n * WIDTH);
     SA_(Y, n * NOUTP); SA_(T, n * NOUT); SA_(dY, n * NOUTP); SA_(dA, n * WIDTH); SA_(dZ, n * MSG);
@@ -539,24 +645,17 @@ int ann_surrogate_load(ann_surrogate *S, ann_ctx *ctx, const float *tend)
     if (v.P.n > S->nmax) return sfail(S, ANN_ERR_INVALID_ARG, "context has more particles than n_max");
     size_t n = (size_t)v.P.n;
     if (tend) {
-        cudaError_t e = cudaMemcpyAsync(S->tend, tend, 8 * n * sizeof(float), cudaMemcpyHostToDevice, S->s);
+        cudaError_t e = cudaMemcpyAsync(S->tend_id, tend, 8 * n * sizeof(float), cudaMemcpyHostToDevice, S->s);
         if (!e) e = cudaStreamSynchronize(S->s);
         if (e) return scuda(S, e, "ann_surrogate_load: tendencies");
     } else {
         if (!v.rec_valid)
             return sfail(S, ANN_ERR_STATE, "the context's last step did not record its tendencies "
                                           "(ann_set_record(ctx, 1), then ann_step)");
-        const int fields[6] = {ANN_FIELD_AX, ANN_FIELD_AY, ANN_FIELD_QRATE11, ANN_FIELD_QRATE12,
-                               ANN_FIELD_LAPQ11, ANN_FIELD_LAPQ12};
-        const int grads[4] = {ANN_FIELD_GRADU_XX, ANN_FIELD_GRADU_XY, ANN_FIELD_GRADU_YX, ANN_FIELD_GRADU_YY};
-        for (int c = 0; c < 6 && !st; c++)
-            st = ann_get_field(ctx, fields[c], S->tend + (size_t)c * n, (int64_t)(n * sizeof(float)), 1);
-        for (int c = 0; c < 4 && !st; c++)   // into the backward scratch, free outside training
-            st = ann_get_field(ctx, grads[c], S->dH + (size_t)c * n, (int64_t)(n * sizeof(float)), 1);
-        if (st) return sfail(S, st, "ann_surrogate_load: reading the tendencies");
-        k_sg_div_vort<<<nb(n), 256, 0, S->s>>>((int)n, S->dH, S->tend);
+        // on the context's stream, ahead of the search that re-sorts the recorded arrays' order
+        k_sg_tend_from_ctx<<<nb(n), 256, 0, v.stream>>>((int)n, v.b.sid, v.b.mid, v.b.sax, v.b.say, v.b.rec_qrate,
+                                                        v.b.rec_lap, v.b.rec_gu, S->tend_id);
         cudaError_t e = cudaGetLastError();
-        if (!e) e = cudaStreamSynchronize(S->s);
         if (e) return scuda(S, e, "ann_surrogate_load: tendencies");
     }
     st = ctx_search_present(ctx);
@@ -568,10 +667,11 @@ int ann_surrogate_load(ann_surrogate *S, ann_ctx *ctx, const float *tend)
     S->dt = v.P.dt_d;
     S->rho0 = v.P.rho0;
     S->gammaK = (double)v.P.Gamma * (double)v.P.K;
-    GraphOut o{S->nbr, S->W, S->cnt, S->S, S->x, S->y, S->u4, S->dr};
+    GraphOut o{S->nbr, S->W, S->cnt, S->S, S->x, S->y, S->u4, S->dr, S->ids};
     cudaError_t e = cudaStreamSynchronize(v.stream);
     if (!e) e = enqueue_export_graph(v.P, v.b, o, S->s);
     if (!e) {
+        k_sg_gather_planes<<<nb(S->n), 256, 0, S->s>>>(S->n, 8, S->ids, S->tend_id, S->tend);
         double kdt = S->k * S->dt;
         TendScales ts{(float)(kdt / S->ysu), (float)(kdt / S->ysq), (float)(S->gammaK * kdt / S->ysq), (float)kdt};
         k_sg_features<<<nb(S->n), 256, 0, S->s>>>(view(S), S->u4, (float)(1.0 / S->us), S->tend, ts, S->X0);
@@ -593,9 +693,11 @@ int ann_surrogate_forward(ann_surrogate *S, float *y)
     if (!S->loaded) return sfail(S, ANN_ERR_STATE, "no graph loaded");
     cudaError_t e = cudaMemsetAsync(S->err, 0, sizeof(unsigned), S->s);
     if (!e) e = forward(S);
-    if (!e && y)
-        e = cudaMemcpy2DAsync(y, NOUT * sizeof(float), S->Y, NOUTP * sizeof(float), NOUT * sizeof(float), S->n,
-                              cudaMemcpyDeviceToHost, S->s);
+    if (!e && y) {
+        k_sg_rows_to_id<<<nb(S->n), 256, 0, S->s>>>(S->n, S->ids, S->Y, NOUTP, S->io4);
+        e = cudaGetLastError();
+        if (!e) e = cudaMemcpyAsync(y, S->io4, (size_t)S->n * NOUT * sizeof(float), cudaMemcpyDeviceToHost, S->s);
+    }
     if (e) return scuda(S, e, "ann_surrogate_forward");
     return check_err(S, "ann_surrogate_forward");
 }
@@ -605,7 +707,11 @@ int ann_surrogate_gradients(ann_surrogate *S, const float *target, double *loss,
     if (!S || !target) return ANN_ERR_INVALID_ARG;
     if (!S->loaded) return sfail(S, ANN_ERR_STATE, "no graph loaded");
     cudaError_t e = cudaMemsetAsync(S->err, 0, sizeof(unsigned), S->s);
-    if (!e) e = cudaMemcpyAsync(S->T, target, (size_t)S->n * NOUT * sizeof(float), cudaMemcpyHostToDevice, S->s);
+    if (!e) e = cudaMemcpyAsync(S->io4, target, (size_t)S->n * NOUT * sizeof(float), cudaMemcpyHostToDevice, S->s);
+    if (!e) {
+        k_sg_rows_from_id<<<nb(S->n), 256, 0, S->s>>>(S->n, S->ids, S->io4, S->T);
+        e = cudaGetLastError();
+    }
     if (!e) e = forward(S);
     if (!e) e = backward(S);
     double h = 0.0;
@@ -641,7 +747,7 @@ int ann_surrogate_jump(ann_surrogate *S, ann_ctx *ctx, const float *tend)
     CtxView v;
     st = ctx_view(ctx, &v);
     if (st) return st;
-    k_sg_jump<<<nb(S->n), 256, 0, S->s>>>(S->n, S->x, S->y, S->u4, S->dr, S->Y, S->inc, (float)S->ysq,
+    k_sg_jump<<<nb(S->n), 256, 0, S->s>>>(S->n, S->ids, S->x, S->y, S->u4, S->dr, S->Y, S->inc, (float)S->ysq,
                                           (float)S->ysu, S->dt * k, S->L, S->rho0, v.b.img, v.tmp);
     cudaError_t e = cudaGetLastError();
     if (!e) e = cudaStreamSynchronize(S->s);
@@ -683,7 +789,9 @@ int ann_surrogate_euler(ann_surrogate *S, float *inc)
 {
     if (!S || !inc) return ANN_ERR_INVALID_ARG;
     if (!S->loaded) return sfail(S, ANN_ERR_STATE, "no graph loaded");
-    cudaError_t e = cudaMemcpyAsync(inc, S->inc, (size_t)S->n * NOUT * sizeof(float), cudaMemcpyDeviceToHost, S->s);
+    k_sg_rows_to_id<<<nb(S->n), 256, 0, S->s>>>(S->n, S->ids, S->inc, NOUT, S->io4);
+    cudaError_t e = cudaGetLastError();
+    if (!e) e = cudaMemcpyAsync(inc, S->io4, (size_t)S->n * NOUT * sizeof(float), cudaMemcpyDeviceToHost, S->s);
     if (!e) e = cudaStreamSynchronize(S->s);
     return e ? scuda(S, e, "ann_surrogate_euler") : ANN_OK;
 }
