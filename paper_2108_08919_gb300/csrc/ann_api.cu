@@ -1436,8 +1436,8 @@ int ctx_search_present(ann_ctx *c)
     DevParams Q = c->P;
     Q.half_dt = 0.f;
     Q.half_dt_d = 0.0;
-    cudaError_t e = cudaMemsetAsync(c->b.rebuild, 1, sizeof(uint32_t), c->stream);
-    if (!e) e = enqueue_search(Q, c->b, c->stream);
+    // re-sorts only if the lists of the last re-sort no longer cover the present positions
+    cudaError_t e = enqueue_search_present(Q, c->b, c->stream);
     if (e) return cuda_fail(c, e, "search");
     int st = device_status(c);
     if (st) return st;

@@ -94,6 +94,10 @@ cudaError_t launch_set_condition(const Bufs &b, cudaGraphConditionalHandle h, cu
 // Cell sort and the re-sort pass A only (neighbour lists and volumes) at the positions in S advanced
 // by P.half_dt (callers pass 0 to keep them).  Requires *b.rebuild != 0.
 cudaError_t enqueue_search(const DevParams &P, const Bufs &b, cudaStream_t s);
+// Pass A at the positions in S advanced by P.half_dt, re-sorting only where the step would: when
+// *b.rebuild is set or a particle has moved past half the skin since the last re-sort; otherwise
+// the candidate lists of that re-sort are filtered at the new positions.
+cudaError_t enqueue_search_present(const DevParams &P, const Bufs &b, cudaStream_t s);
 // Rebuild the candidate lists from xi_ref (the split positions of the last re-sort), with the
 // cell starts of that re-sort: used after a checkpoint is loaded.
 cudaError_t enqueue_candidates_from_ref(const DevParams &P, const Bufs &b, cudaStream_t s);
@@ -164,6 +168,11 @@ cudaError_t enqueue_gemm_nt(const void *A1, int K1, const void *A2, int K2, cons
                             int max_ctas, cudaStream_t s, int ldc = 0);
 cudaError_t enqueue_gemm_tn(const void *A, int K, const void *B, int N, int rows, float *C, unsigned *err,
                             int max_ctas, cudaStream_t s, int ldc = 0);
+// One surrogate layer: h = relu([A1 | A2] W^T + bw) (128 wide; to H unless null), z = h P^T + bp
+// (Np wide, bp may be null; BF16 or FP32).  W 128 x (K1 + K2), P Np x 128, BF16, 16-byte aligned.
+cudaError_t enqueue_layer(const void *A1, int K1, const void *A2, int K2, const void *W, const float *bw,
+                          const void *P, const float *bp, int Np, void *H, void *Z, int z_bf16, int rows,
+                          unsigned *err, int max_ctas, cudaStream_t s);
 cudaError_t enqueue_unwrapped(const DevParams &P, const Bufs &b, int *inv, const long long *ids, int k, double *xy,
                               cudaStream_t s);
 

@@ -14,6 +14,9 @@
 #include "ann_internal.cuh"
 
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
 
 namespace ann {
 namespace {
@@ -33,6 +36,28 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;   // version
     return d;                 // base offset 0, layout SWIZZLE_NONE (0)
+}
+
+// Descriptor of a K-major operand in a swizzled layout: rows of `span` bytes (128, 64 or 32: one
+// TMA box row), 16-byte chunk j of row r stored at chunk j ^ ((r * span / 128) mod (span / 16)),
+// 8-row groups `8 span` bytes apart (SBO), the leading offset unused.  Atoms are 1024-byte aligned.
+__device__ __forceinline__ uint64_t smem_desc_sw(uint32_t addr, uint32_t span)
+{
+    const uint64_t mode = span == 128 ? 2u : (span == 64 ? 4u : 6u);   // SWIZZLE_128B / 64B / 32B
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                                  // LBO (unused): 16 bytes
+    d |= (uint64_t)(((8u * span) >> 4) & 0x3FFFu) << 32;     // SBO
+    d |= (uint64_t)1 << 46;                                  // version
+    d |= mode << 61;
+    return d;
+}
+
+// Byte offset of 16-byte chunk j of row r in a swizzled box with rows of `span` bytes.
+__device__ __forceinline__ uint32_t sw_off(int r, int j, uint32_t span)
+{
+    const int x = span == 128 ? (r & 7) : (span == 64 ? ((r >> 1) & 3) : ((r >> 2) & 1));
+    return (uint32_t)r * span + ((uint32_t)(j ^ x) << 4);
 }
 
 // Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, N >> 3, M >> 4.
@@ -106,6 +131,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
 #pragma unroll
     for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]);
 }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane, without waiting: the registers are valid
+// after tmem_ld_wait().
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t *r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Byte offset of element (row, k) of a K-major operand with Kt columns in the canonical layout.
 __device__ __forceinline__ uint32_t kmaj_off(int row, int k, int Kt)
@@ -251,6 +289,309 @@ __global__ void __launch_bounds__(128) k_gemm_nt(NtArgs a)
 }
 
 // ------------------------------------------------------------------------------------------------
+// layer: one message-passing layer per 128-row tile, two chained MMAs with the hidden activation
+// kept on chip:
+//   h = relu([A1 | A2] . W^T + bw)    (128 x 128 FP32 in TMEM; BF16 copy into shared memory as the
+//                                      next MMA's A operand, optionally stored to H)
+//   z = h . P^T (+ bp)                (128 x Np in TMEM; stored to Z, BF16 or FP32)
+// One persistent CTA per SM, warp-specialised: lane 0 of warp 8 loads A tiles by TMA into a ring
+// of `stages` buffers and issues the MMAs; warps 0-7 run the epilogues.  The accumulators are
+// double-buffered in TMEM (buffer b = tile mod 2 at columns 256 b: h at +0, z at +128), as is the
+// z staging tile in shared memory, so that the products of one tile overlap the epilogues of the
+// previous one; the h staging tile is single (its space buys a third A stage at K = 160, which
+// keeps two tiles' loads in flight).  Hand-offs are mbarriers:
+//   full[s]      TMA bytes of stage s landed          -> MMA of h
+//   empty[s]     MMA of h has read stage s            -> next TMA into s
+//   acc1_full[b] h accumulated                         -> epilogue 1
+//   h_full[b]    BF16 h written to shared memory       -> MMA of z
+//   acc2_full[b] z accumulated (h no longer read)      -> epilogue 2
+//   acc_empty[b] both accumulators of b read           -> MMA of h two tiles later
+// TMA boxes are 128 rows high and 128 bytes wide (64 columns), or the whole row where a part is
+// only 32 or 64 bytes wide, and land in the matching swizzled K-major layout (16-byte chunks of a
+// row XOR-permuted by the row within its 8-row group), which the MMA descriptors name; the epilogue
+// writes h and z in the same layouts and TMA stores them.  Rows past the end are zero-filled on
+// load and clipped on store.  Epilogue warp w reads TMEM lanes 32 (w mod 4) .. + 31 (tile rows) and half
+// of the columns.  Every wait is bounded; the epilogue warps take each wait's outcome together
+// (a barrier reduction), so a time-out ends all of them at the same tile.
+// ------------------------------------------------------------------------------------------------
+
+struct LayerMaps {
+    CUtensorMap a1, a2, h, z;   // A1 rows x K1, A2 rows x K2, H rows x 128, Z rows x Np
+};
+
+struct LayerArgs {
+    const __nv_bfloat16 *W;   // 128 x K
+    const float *bw;          // 128
+    const __nv_bfloat16 *P;   // Np x 128
+    const float *bp;          // Np or null
+    int rows, K1, K2, Np, z_bf16, store_h, stages;
+    unsigned *err;
+};
+
+constexpr int HW = 128;          // hidden width of a layer
+constexpr int EPI = 256;         // epilogue threads (warps 0-7)
+constexpr int LT = EPI + 32;     // + the TMA / MMA warp
+constexpr int NSMAX = 4;         // A stages at most
+
+// Row span in bytes of the boxes of a part of C BF16 columns (or FP32 when es = 4): 128 (boxes of
+// 64 columns) when C is a multiple of 64, else the whole row of 32 or 64 bytes.
+__host__ __device__ constexpr uint32_t part_span(int C, int es = 2)
+{
+    return (uint32_t)(C * es >= 128 ? 128 : C * es);
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, uint32_t src)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t *mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// AND of v over the 256 epilogue threads (named barrier 1); also a barrier among them.
+__device__ __forceinline__ bool epi_all(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// The A tile of rows r0.. into stage buffer sA, completing on `full`: part A1 then part A2, each as
+// boxes of 128 rows x span bytes (span / 2 columns), one after the other.
+__device__ __forceinline__ void layer_load(const LayerMaps &m, int K1, int K2, int r0, uint32_t sA, uint64_t *full)
+{
+    mbar_expect(full, (uint32_t)MT * (uint32_t)(K1 + K2) * 2u);
+    const uint32_t mb = smem_u32(full), s1 = part_span(K1), s2 = part_span(K2);
+    uint32_t d = sA;
+    for (int c = 0; c < K1; c += (int)s1 / 2, d += MT * s1) tma_load_2d(d, &m.a1, c, r0, mb);
+    for (int c = 0; c < K2; c += (int)s2 / 2, d += MT * s2) tma_load_2d(d, &m.a2, c, r0, mb);
+}
+
+__global__ void __launch_bounds__(LT, 1) k_layer(const __grid_constant__ LayerMaps maps, LayerArgs a)
+{
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    __shared__ uint64_t full[NSMAX], empty[NSMAX], acc1_full[2], acc2_full[2], h_full[2], acc_empty[2];
+    __shared__ uint32_t tbase;
+    __shared__ __align__(16) float sbw[HW], sbp[HW];
+    const int K = a.K1 + a.K2, Np = a.Np, NS = a.stages;
+    const uint32_t zspan = part_span(Np, a.z_bf16 ? 2 : 4);            // 64 bytes for the widths used here
+    const uint32_t zbytes = (uint32_t)MT * (uint32_t)Np * (a.z_bf16 ? 2u : 4u);
+    // swizzle atoms want 1024-byte alignment: the launch adds 1 KB of slack
+    unsigned char *sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
+    unsigned char *sW = sm;                                // 128 x K (no swizzle: LBO 128, SBO 128 K / 8)
+    unsigned char *sP = sW + (size_t)HW * K * 2;           // Np x 128 (no swizzle: LBO 128, SBO 2048)
+    unsigned char *sH = sP + (size_t)Np * HW * 2;          // 128 x 128: two 128-byte-span boxes
+    unsigned char *sZ0 = sH + (size_t)MT * HW * 2;         // 2 x (128 x Np)
+    unsigned char *sA0 = sZ0 + (size_t)2 * zbytes;         // NS x (128 x K)
+    const size_t abytes = (size_t)MT * K * 2;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntiles = (a.rows + MT - 1) / MT;
+    const int mine = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (warp == 0) tmem_alloc(&tbase, 512);
+    if (tid == 0) {
+        for (int q = 0; q < NS; q++) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&acc1_full[b], 1);
+            mbar_init(&acc2_full[b], 1);
+            mbar_init(&h_full[b], EPI);
+            mbar_init(&acc_empty[b], EPI);
+        }
+    }
+    for (int e = tid; e < HW * (K / 8); e += LT) {
+        int r = e / (K / 8), k8 = (e % (K / 8)) * 8;
+        *reinterpret_cast<uint4 *>(sW + kmaj_off(r, k8, K)) = *reinterpret_cast<const uint4 *>(a.W + (size_t)r * K + k8);
+    }
+    for (int e = tid; e < Np * (HW / 8); e += LT) {
+        int r = e / (HW / 8), k8 = (e % (HW / 8)) * 8;
+        *reinterpret_cast<uint4 *>(sP + kmaj_off(r, k8, HW)) = *reinterpret_cast<const uint4 *>(a.P + (size_t)r * HW + k8);
+    }
+    if (tid < HW) {
+        sbw[tid] = a.bw[tid];
+        sbp[tid] = (a.bp && tid < Np) ? a.bp[tid] : 0.f;
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tbase;
+    if (warp == EPI / 32) {
+        if (lane == 0) {
+            // TMA and MMA issue.  Order per step i: the product of h for tile i, the load of tile
+            // i + NS - 1 (into the stage of tile i - 1), the product of z for tile i - 1.
+            const uint32_t idesc1 = idesc_bf16(MT, HW), idesc2 = idesc_bf16(MT, Np);
+            const uint32_t sbo_w = (uint32_t)(K / 8) * 128, sbo_p = (uint32_t)(HW / 8) * 128;
+            int issued = 0, consumed = 0;
+            bool ok = true;
+            for (int q = 0; q < NS - 1 && q < mine; q++, issued++)
+                layer_load(maps, a.K1, a.K2, (blockIdx.x + q * gridDim.x) * MT, smem_u32(sA0 + (size_t)q * abytes),
+                           &full[q]);
+            for (int i = 0; i <= mine && ok; i++) {
+                if (i < mine) {
+                    const int st = i % NS, b = i & 1;
+                    ok = mbar_wait(&full[st], (uint32_t)(i / NS) & 1u);
+                    if (ok) consumed++;
+                    if (ok && i >= 2) ok = mbar_wait(&acc_empty[b], (uint32_t)((i - 2) / 2) & 1u);
+                    if (!ok) break;
+                    fence_after();
+                    // K steps of 16 columns (32 bytes): part A1's boxes, then A2's
+                    uint32_t box = smem_u32(sA0 + (size_t)st * abytes);
+                    int kk = 0;
+                    for (int part = 0; part < 2; part++) {
+                        const int C = part ? a.K2 : a.K1;
+                        const uint32_t span = part_span(C);
+                        for (int c = 0; c < C; c += 16, kk += 16) {
+                            const uint32_t in_box = (uint32_t)(c % ((int)span / 2)) * 2;
+                            mma_bf16(tmem + (uint32_t)b * 256u, smem_desc_sw(box + in_box, span),
+                                     smem_desc(smem_u32(sW) + (uint32_t)(kk / 8) * 128, 128, sbo_w), idesc1, kk > 0);
+                            if (in_box + 32 == span) box += MT * span;
+                        }
+                    }
+                    mma_commit(&empty[st]);
+                    mma_commit(&acc1_full[b]);
+                    const int j = i + NS - 1;
+                    if (j < mine) {
+                        const int sj = j % NS;
+                        if (i >= 1) ok = mbar_wait(&empty[sj], (uint32_t)((i - 1) / NS) & 1u);
+                        if (!ok) break;
+                        layer_load(maps, a.K1, a.K2, (blockIdx.x + j * gridDim.x) * MT,
+                                   smem_u32(sA0 + (size_t)sj * abytes), &full[sj]);
+                        issued++;
+                    }
+                }
+                if (i >= 1) {
+                    const int j = i - 1, b = j & 1;
+                    ok = mbar_wait(&h_full[b], (uint32_t)(j / 2) & 1u);
+                    if (!ok) break;
+                    fence_after();
+                    const uint32_t h0 = smem_u32(sH);
+                    for (int k = 0; k < HW / 16; k++)
+                        mma_bf16(tmem + (uint32_t)b * 256u + (uint32_t)HW,
+                                 smem_desc_sw(h0 + (uint32_t)(k / 4) * MT * 128 + (uint32_t)(k % 4) * 32, 128),
+                                 smem_desc(smem_u32(sP) + (uint32_t)k * 256, 128, sbo_p), idesc2, k > 0);
+                    mma_commit(&acc2_full[b]);
+                }
+            }
+            if (!ok) atomicOr(a.err, 4u);
+            // loads issued for tiles that were not reached (only after a failed wait) land before exit
+            for (int q = consumed; q < issued; q++) mbar_wait(&full[q % NS], (uint32_t)(q / NS) & 1u);
+        }
+        __syncwarp();
+    } else {
+        const int row = (warp & 3) * 32 + lane, half = warp >> 2;
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        const bool leader = tid == 0;
+        bool ok = true;
+        for (int i = 0; i < mine; i++) {
+            const int t = blockIdx.x + i * gridDim.x, b = i & 1;
+            unsigned char *sZ = sZ0 + (size_t)b * zbytes;
+            const uint32_t acc = tmem + (uint32_t)b * 256u + lane_base;
+            // stores commit two groups a tile, h then z: once at most the last (z of tile i - 1) is
+            // still reading, sH (stored from by tile i - 1) and sZ of buffer b (by tile i - 2) are free
+            if (leader && i >= 1) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            ok = epi_all(mbar_wait(&acc1_full[b], (uint32_t)(i / 2) & 1u));
+            if (!ok) break;
+            fence_after();
+            // h: bias, relu, BF16 into sH; 64 columns per warp, 32 at a time
+            for (int c0 = half * (HW / 2); c0 < (half + 1) * (HW / 2); c0 += 32) {
+                uint32_t r[32];
+                tmem_ld16_async(acc + (uint32_t)c0, r);
+                tmem_ld16_async(acc + (uint32_t)(c0 + 16), r + 16);
+                tmem_ld_wait();
+                uint4 w[4];
+                __nv_bfloat162 *h2 = reinterpret_cast<__nv_bfloat162 *>(w);
+#pragma unroll
+                for (int k = 0; k < 16; k++) {
+                    const float2 bb = *reinterpret_cast<const float2 *>(sbw + c0 + 2 * k);
+                    h2[k] = __floats2bfloat162_rn(fmaxf(__uint_as_float(r[2 * k]) + bb.x, 0.f),
+                                                  fmaxf(__uint_as_float(r[2 * k + 1]) + bb.y, 0.f));
+                }
+#pragma unroll
+                for (int q = 0; q < 4; q++) {   // chunk j of the 64-column box c0 / 64
+                    const int j = (c0 % 64) / 8 + q;
+                    *reinterpret_cast<uint4 *>(sH + (size_t)(c0 / 64) * MT * 128 + sw_off(row, j, 128)) = w[q];
+                }
+            }
+            fence_async_smem();
+            mbar_arrive(&h_full[b]);
+            epi_sync();
+            if (leader) {
+                if (a.store_h)
+                    for (int c = 0; c < HW / 64; c++)
+                        tma_store_2d(&maps.h, c * 64, t * MT, smem_u32(sH) + (uint32_t)c * MT * 128);
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            }
+            ok = epi_all(mbar_wait(&acc2_full[b], (uint32_t)(i / 2) & 1u));
+            if (!ok) break;
+            fence_after();
+            // z (+ bias) into sZ: BF16 blocks of 8 columns or FP32 blocks of 4
+            for (int c0 = half * 16; c0 < Np; c0 += 32) {
+                uint32_t r[16];
+                tmem_ld16_async(acc + (uint32_t)(HW + c0), r);
+                tmem_ld_wait();
+                float v[16];
+#pragma unroll
+                for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]) + sbp[c0 + k];
+                if (a.z_bf16) {
+                    uint4 w[2];
+                    __nv_bfloat162 *h2 = reinterpret_cast<__nv_bfloat162 *>(w);
+#pragma unroll
+                    for (int k = 0; k < 8; k++) h2[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+#pragma unroll
+                    for (int q = 0; q < 2; q++)
+                        *reinterpret_cast<uint4 *>(sZ + sw_off(row, c0 / 8 + q, zspan)) = w[q];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        *reinterpret_cast<float4 *>(sZ + sw_off(row, c0 / 4 + q, zspan)) =
+                            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                }
+            }
+            fence_async_smem();
+            fence_before();
+            mbar_arrive(&acc_empty[b]);
+            epi_sync();
+            if (leader) {
+                tma_store_2d(&maps.z, 0, t * MT, smem_u32(sZ));
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            }
+        }
+        if (!ok && leader) atomicOr(a.err, 4u);
+        if (leader) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// ------------------------------------------------------------------------------------------------
 // tn: C[K x N] += A^T B over all rows.  CTA (x, y): feature block y (128 features of A's K), row
 // chunks x, x + gridDim.x, ...; the chunk of 128 rows is staged transposed (features x rows and
 // N x rows, both K-major in the rows) and reduced by 8 MMAs of K = 16 rows into TMEM; at the end
@@ -384,6 +725,90 @@ cudaError_t enqueue_gemm_nt(const void *A1, int K1, const void *A2, int K2, cons
     int g = tiles < max_ctas ? tiles : max_ctas;
     if (g < 1) return cudaSuccess;
     k_gemm_nt<<<g, 128, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D map of a row-major rows x cols matrix with boxes of 128 rows x part_span(cols) bytes, in the
+// swizzle mode of that span.
+bool row_map(CUtensorMap *m, const void *base, int rows, int cols, bool fp32)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const int es = fp32 ? 4 : 2;
+    const uint32_t span = part_span(cols, es);
+    const CUtensorMapSwizzle sw = span == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : (span == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * es};
+    cuuint32_t box[2] = {span / (cuuint32_t)es, (cuuint32_t)MT};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base),
+               dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Widths a part of a tile may have: whole swizzle rows of 32 or 64 bytes, or 64-column boxes.
+bool part_ok(int C, int es = 2) { return C * es == 32 || C * es == 64 || (C * es) % 128 == 0; }
+
+}  // namespace
+
+cudaError_t enqueue_layer(const void *A1, int K1, const void *A2, int K2, const void *W, const float *bw,
+                          const void *P, const float *bp, int Np, void *H, void *Z, int z_bf16, int rows,
+                          unsigned *err, int max_ctas, cudaStream_t s)
+{
+    const int K = K1 + K2;
+    if (K < 16 || K > 256 || K % 16 || K1 % 16 || K1 < 16 || Np < 16 || Np > 128 || Np % 16 || rows < 0 ||
+        (K2 > 0 && !A2) || !part_ok(K1) || (K2 > 0 && !part_ok(K2)) || !part_ok(Np, z_bf16 ? 2 : 4) ||
+        (z_bf16 ? 2 : 4) * Np > 128)
+        return cudaErrorInvalidValue;
+    if (rows == 0) return cudaSuccess;
+    LayerMaps maps;
+    std::memset(&maps, 0, sizeof maps);
+    if (!row_map(&maps.a1, A1, rows, K1, false) || (K2 > 0 && !row_map(&maps.a2, A2, rows, K2, false)) ||
+        (H && !row_map(&maps.h, H, rows, HW, false)) || !row_map(&maps.z, Z, rows, Np, !z_bf16))
+        return cudaErrorInvalidValue;
+    LayerArgs a{static_cast<const __nv_bfloat16 *>(W), bw, static_cast<const __nv_bfloat16 *>(P), bp,
+                rows, K1, K2, Np, z_bf16, H ? 1 : 0, 2, err};
+    // W, P, an h tile, two z tiles and a ring of 2 to 4 A tiles in at most 216 KB; at least 116 KB,
+    // so that one CTA (all 512 TMEM columns) runs per SM
+    const size_t zbytes = (size_t)MT * Np * (z_bf16 ? 2 : 4);
+    const size_t fixed = ((size_t)HW * K + (size_t)Np * HW + (size_t)MT * HW) * 2 + 2 * zbytes,
+                 abytes = (size_t)MT * K * 2;
+    size_t room = 216 * 1024 > fixed ? 216 * 1024 - fixed : 0;
+    a.stages = (int)(room / abytes);
+    if (a.stages > NSMAX) a.stages = NSMAX;
+    if (a.stages < 2) a.stages = 2;
+    size_t smem = fixed + (size_t)a.stages * abytes + 1024;   // + alignment slack
+    if (smem < 116 * 1024) smem = 116 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e) return e;
+    }
+    int tiles = (rows + MT - 1) / MT;
+    int g = tiles < sms ? tiles : sms;
+    if (max_ctas > 0 && g > max_ctas) g = max_ctas;
+    k_layer<<<g, LT, smem, s>>>(maps, a);
     return cudaGetLastError();
 }
 

@@ -56,15 +56,19 @@ struct TendScales {
     float a, m, lap, grad;
 };
 
+// Features of every particle, and the first SPH mean of the acceleration (agg1 = agg(ax, ay), two
+// planes) from the same neighbour walk.
 __global__ void k_sg_features(GraphView g, const float4 *u4, float inv_us, const float *tend, TendScales ts,
-                              bf16 *X)
+                              bf16 *X, float *agg1)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
+    const float *ax = tend, *ay = tend + g.n;
     float4 s = u4[i];
     float r[4] = {s.z, s.w, s.x * inv_us, s.y * inv_us};
     float is = 1.f / g.S[i], a[4];
     for (int c = 0; c < 4; c++) a[c] = g.W0 * is * r[c];
+    float sx = g.W0 * is * ax[i], sy = g.W0 * is * ay[i];
     int m = g.cnt[i];
 #pragma unroll 4
     for (int k = 0; k < m; k++) {
@@ -75,7 +79,11 @@ __global__ void k_sg_features(GraphView g, const float4 *u4, float inv_us, const
         a[1] += w * t.w;
         a[2] += w * t.x * inv_us;
         a[3] += w * t.y * inv_us;
+        sx += w * __ldg(ax + j);
+        sy += w * __ldg(ay + j);
     }
+    agg1[i] = sx;
+    agg1[(size_t)g.n + i] = sy;
     bf16 *row = X + (size_t)i * F0;
     for (int c = 0; c < 4; c++) {
         row[c] = __float2bfloat16(r[c]);
@@ -459,26 +467,27 @@ cudaError_t cast_weights(ann_surrogate *S)
 
 constexpr int GEMM_CTAS = 296;   // two persistent CTAs per SM
 
-cudaError_t forward(ann_surrogate *S)
+// The three layers, each one fused kernel (both products of a layer on the tensor cores, h kept on
+// chip), with the SPH means in between; H3 is kept only for a backward pass.
+cudaError_t forward(ann_surrogate *S, bool keep_h3)
 {
     cudaStream_t s = S->s;
     int n = S->n;
     GraphView g = view(S);
     unsigned *err = S->err;
     k_sg_agg<F0><<<nb((size_t)n * (F0 / 8)), 256, 0, s>>>(g, S->X0, S->AX);
-    cudaError_t e = enqueue_gemm_nt(S->X0, F0, S->AX, F0, S->W1b, WIDTH, n, S->p + O_B1, 1, S->H1, 1, 0, err,
-                                    GEMM_CTAS, s);
-    if (!e) e = enqueue_gemm_nt(S->H1, WIDTH, nullptr, 0, S->P1b, MSG, n, nullptr, 0, S->Z1, 1, 0, err, GEMM_CTAS, s);
+    cudaError_t e = enqueue_layer(S->X0, F0, S->AX, F0, S->W1b, S->p + O_B1, S->P1b, nullptr, MSG, S->H1, S->Z1, 1,
+                                  n, err, GEMM_CTAS, s);
     if (!e) {
         k_sg_agg<MSG><<<nb((size_t)n * (MSG / 8)), 256, 0, s>>>(g, S->Z1, S->AZ1);
-        e = enqueue_gemm_nt(S->H1, WIDTH, S->AZ1, MSG, S->W2b, WIDTH, n, S->p + O_B2, 1, S->H2, 1, 0, err, GEMM_CTAS, s);
+        e = enqueue_layer(S->H1, WIDTH, S->AZ1, MSG, S->W2b, S->p + O_B2, S->P2b, nullptr, MSG, S->H2, S->Z2, 1, n,
+                          err, GEMM_CTAS, s);
     }
-    if (!e) e = enqueue_gemm_nt(S->H2, WIDTH, nullptr, 0, S->P2b, MSG, n, nullptr, 0, S->Z2, 1, 0, err, GEMM_CTAS, s);
     if (!e) {
         k_sg_agg<MSG><<<nb((size_t)n * (MSG / 8)), 256, 0, s>>>(g, S->Z2, S->AZ2);
-        e = enqueue_gemm_nt(S->H2, WIDTH, S->AZ2, MSG, S->W3b, WIDTH, n, S->p + O_B3, 1, S->H3, 1, 0, err, GEMM_CTAS, s);
+        e = enqueue_layer(S->H2, WIDTH, S->AZ2, MSG, S->W3b, S->p + O_B3, S->Wob, S->bop, NOUTP,
+                          keep_h3 ? S->H3 : nullptr, S->Y, 0, n, err, GEMM_CTAS, s);
     }
-    if (!e) e = enqueue_gemm_nt(S->H3, WIDTH, nullptr, 0, S->Wob, NOUTP, n, S->bop, 0, S->Y, 0, 0, err, GEMM_CTAS, s);
     return e ? e : cudaGetLastError();
 }
 
@@ -674,9 +683,8 @@ int ann_surrogate_load(ann_surrogate *S, ann_ctx *ctx, const float *tend)
         k_sg_gather_planes<<<nb(S->n), 256, 0, S->s>>>(S->n, 8, S->ids, S->tend_id, S->tend);
         double kdt = S->k * S->dt;
         TendScales ts{(float)(kdt / S->ysu), (float)(kdt / S->ysq), (float)(S->gammaK * kdt / S->ysq), (float)kdt};
-        k_sg_features<<<nb(S->n), 256, 0, S->s>>>(view(S), S->u4, (float)(1.0 / S->us), S->tend, ts, S->X0);
-        // dH is free between the gather above and the next backward pass
-        k_sg_mean2<<<nb(S->n), 256, 0, S->s>>>(view(S), S->tend, S->dH);
+        // dH is scratch between here and the next backward pass
+        k_sg_features<<<nb(S->n), 256, 0, S->s>>>(view(S), S->u4, (float)(1.0 / S->us), S->tend, ts, S->X0, S->dH);
         k_sg_mean2<<<nb(S->n), 256, 0, S->s>>>(view(S), S->dH, S->dH + 2 * (size_t)S->n);
         k_sg_euler<<<nb(S->n), 256, 0, S->s>>>(S->n, S->tend, S->dH + 2 * (size_t)S->n, (float)kdt, S->inc);
         e = cudaGetLastError();
@@ -692,7 +700,7 @@ int ann_surrogate_forward(ann_surrogate *S, float *y)
     if (!S) return ANN_ERR_INVALID_ARG;
     if (!S->loaded) return sfail(S, ANN_ERR_STATE, "no graph loaded");
     cudaError_t e = cudaMemsetAsync(S->err, 0, sizeof(unsigned), S->s);
-    if (!e) e = forward(S);
+    if (!e) e = forward(S, false);
     if (!e && y) {
         k_sg_rows_to_id<<<nb(S->n), 256, 0, S->s>>>(S->n, S->ids, S->Y, NOUTP, S->io4);
         e = cudaGetLastError();
@@ -712,7 +720,7 @@ int ann_surrogate_gradients(ann_surrogate *S, const float *target, double *loss,
         k_sg_rows_from_id<<<nb(S->n), 256, 0, S->s>>>(S->n, S->ids, S->io4, S->T);
         e = cudaGetLastError();
     }
-    if (!e) e = forward(S);
+    if (!e) e = forward(S, true);
     if (!e) e = backward(S);
     double h = 0.0;
     if (!e) e = cudaMemcpyAsync(&h, S->loss, sizeof h, cudaMemcpyDeviceToHost, S->s);
