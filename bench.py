@@ -380,31 +380,87 @@ def _sg_snapshot(B, ctx, n):
     return f
 
 
-def _sg_trajectory(B, nx, zeta, K, seed, nsnap, spin, u0=0.0):
-    """Recorded plain-SPH snapshots every SG_K steps (ID order) and the context parameters."""
-    import numpy as np
+def _sg_params(B, nx, zeta, K):
+    return B.ann_default_params(n=nx * nx, h=1.3 / nx, zeta=zeta, K=K, dt_mode=1, c0_min=0.5)
 
+
+def _sg_run(B, ctx, nx, seed, nsnap, spin, u0):
+    """Recorded plain-SPH snapshots every SG_K steps (ID order) of a seeded run on context ctx."""
     import sph_inputs as si
 
     n = nx * nx
-    p = B.ann_default_params(n=n, h=1.3 / nx, zeta=zeta, K=K, dt_mode=1, c0_min=0.5)
+    ic = si.jittered_lattice(nx, seed=seed)
+    if u0 > 0:
+        r = si.uniform53(seed + 900, 2 * n).reshape(2, n) - 0.5
+        ic["ux"], ic["uy"] = u0 * r[0], u0 * r[1]
+    B.ann_set_particles(ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"], ic["rho"])
+    B.ann_set_record(ctx, 1)
+    B.ann_step(ctx, spin)
+    snaps = []
+    for _ in range(nsnap + 1):
+        snaps.append(_sg_snapshot(B, ctx, n))
+        B.ann_step(ctx, SG_K)
+    return snaps
+
+
+def _sg_trajectory(B, nx, zeta, K, seed, nsnap, spin, u0=0.0):
+    """Recorded plain-SPH snapshots every SG_K steps (ID order) and the context parameters."""
+    p = _sg_params(B, nx, zeta, K)
     ctx = B.ann_create(p)
     try:
-        ic = si.jittered_lattice(nx, seed=seed)
-        if u0 > 0:
-            r = si.uniform53(seed + 900, 2 * n).reshape(2, n) - 0.5
-            ic["ux"], ic["uy"] = u0 * r[0], u0 * r[1]
-        B.ann_set_particles(ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"], ic["rho"])
-        B.ann_set_record(ctx, 1)
-        B.ann_step(ctx, spin)
-        snaps = []
-        for _ in range(nsnap + 1):
-            snaps.append(_sg_snapshot(B, ctx, n))
-            B.ann_step(ctx, SG_K)
+        snaps = _sg_run(B, ctx, nx, seed, nsnap, spin, u0)
         dt = B.ann_grid_info(p).dt_effective
     finally:
         B.ann_destroy(ctx)
     return p, dt, snaps
+
+
+SG_PRE_TRAJ = 200     # seeded 256 x 256 pre-training trajectories
+SG_PRE_ZETAS = 8      # activities in [0.02, 0.1], one context each
+
+
+def _sg_pretrain(B, sg, nx=256, n_traj=SG_PRE_TRAJ, seed0=300, spin=120, nsnap=2, passes=3, lr0=3e-3):
+    """Online pre-training on n_traj seeded trajectories at nx^2: trajectory s has activity
+    zeta_(s mod 8) and seed seed0 + s, starts from a lattice with random velocities, runs `spin`
+    plain steps and gives nsnap pairs of states SG_K steps apart; each pair is used `passes` times
+    as it arrives (Adam, the rate dropping to 0.3 lr0 for the last 30 % of the trajectories).  The
+    velocity and residual scales come from the first 8 trajectories; a 201st is held out."""
+    import numpy as np
+
+    zetas = [0.02 + 0.08 * q / (SG_PRE_ZETAS - 1) for q in range(SG_PRE_ZETAS)]
+    ctxs = [B.ann_create(_sg_params(B, nx, z, PARAMS["K"])) for z in zetas]
+    n = nx * nx
+    try:
+        def pairs_of(s):
+            return _sg_pairs(_sg_run(B, ctxs[s % SG_PRE_ZETAS], nx, seed0 + s, nsnap, spin, 0.02))
+
+        first = [pairs_of(s) for s in range(8)]
+        flat = [pr for prs in first for pr in prs]
+        us = float(np.sqrt(np.mean(np.concatenate([np.r_[a["UX"], a["UY"]] for a, _ in flat]) ** 2)))
+        B.ann_surrogate_set_scales(sg, us, 1.0, 1.0, SG_K)
+        ys = _sg_scales(_sg_residuals(B, sg, ctxs[0], n, flat))
+        B.ann_surrogate_set_scales(sg, us, ys[0], ys[2], SG_K)
+        losses, iters = [], 0
+        for s in range(n_traj):
+            prs = first[s] if s < 8 else pairs_of(s)
+            ctx = ctxs[s % SG_PRE_ZETAS]
+            lr = lr0 if s < 0.7 * n_traj else 0.3 * lr0
+            for _ in range(passes):
+                for a, b in prs:
+                    _sg_load(B, sg, ctx, a)
+                    e = B.ann_surrogate_euler(sg, n).astype(np.float64)
+                    loss, _ = B.ann_surrogate_gradients(sg, (_sg_truth(a, b) - e) / ys)
+                    B.ann_surrogate_adam(sg, lr)
+                    losses.append(loss)
+                    iters += 1
+        held = pairs_of(n_traj)
+        e_net, e_eul = _sg_eval(B, sg, ctxs[n_traj % SG_PRE_ZETAS], n, held, ys)
+    finally:
+        for c in ctxs:
+            B.ann_destroy(c)
+    return {"resolution": nx, "trajectories": n_traj, "pairs": n_traj * nsnap, "iters": iters,
+            "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:])),
+            "heldout_err": e_net, "euler_err": e_eul, "us": us, "ys": [float(ys[0]), float(ys[2])]}
 
 
 def _sg_pairs(snaps):
@@ -453,20 +509,27 @@ def _sg_train(B, sg, ctx, n, pairs, res, ys, iters, lr0):
     return float(np.mean(losses[:10])), float(np.mean(losses[-10:]))
 
 
-def _sg_eval(B, sg, ctx, n, pairs, ys):
-    """Relative error of the surrogate's k-step increment, and of the explicit one, on held-out pairs."""
+def _sg_eval(B, sg, ctx, n, pairs, ys, parts=False):
+    """Relative error of the surrogate's k-step increment, and of the explicit one, on held-out pairs;
+    with parts, also each for the Q and the u increments alone."""
     import numpy as np
 
-    en, ee = [], []
+    en, ee, pq, pu = [], [], [], []
     for a, b in pairs:
         truth = _sg_truth(a, b)
         _sg_load(B, sg, ctx, a)
         euler = B.ann_surrogate_euler(sg, n).astype(np.float64)
-        y = B.ann_surrogate_forward(sg, n)
+        pred = euler + B.ann_surrogate_forward(sg, n) * ys
         scale = np.linalg.norm(truth)
-        en.append(np.linalg.norm(euler + y * ys - truth) / scale)
+        en.append(np.linalg.norm(pred - truth) / scale)
         ee.append(np.linalg.norm(euler - truth) / scale)
-    return float(np.mean(en)), float(np.mean(ee))
+        for acc, cs in ((pq, slice(0, 2)), (pu, slice(2, 4))):
+            t = np.linalg.norm(truth[:, cs])
+            acc.append((np.linalg.norm(pred[:, cs] - truth[:, cs]) / t, np.linalg.norm(euler[:, cs] - truth[:, cs]) / t))
+    if not parts:
+        return float(np.mean(en)), float(np.mean(ee))
+    return (float(np.mean(en)), float(np.mean(ee)), [float(v) for v in np.mean(pq, axis=0)],
+            [float(v) for v in np.mean(pu, axis=0)])
 
 
 def surrogate_bench(B, max_err=0.05):
@@ -478,29 +541,16 @@ def surrogate_bench(B, max_err=0.05):
 
     t_all = time.perf_counter()
     out = {"k": SG_K, "max_err": max_err}
-    # pre-training at 256 x 256: 8 trajectories, zeta in [0.02, 0.1]
-    zetas = [0.02 + 0.08 * z for z in (0.0, 0.15, 0.3, 0.45, 0.6, 0.75, 0.9, 1.0)]
-    trs = [_sg_trajectory(B, 256, z, PARAMS["K"], 300 + s, 10, 200, u0=0.02) for s, z in enumerate(zetas)]
-    train = [pr for _, _, sn in trs[:7] for pr in _sg_pairs(sn)]
-    test = _sg_pairs(trs[7][2])
-    us = float(np.sqrt(np.mean(np.concatenate([np.r_[a["UX"], a["UY"]] for a, _ in train]) ** 2)))
-    n256 = 256 * 256
-    c256 = B.ann_create(trs[0][0])
+    # pre-training: 200 seeded 256 x 256 trajectories, zeta in [0.02, 0.1], streamed
     sg = B.ann_surrogate_create(NX * NX)
     try:
         B.ann_surrogate_init(sg, 7)
-        B.ann_surrogate_set_scales(sg, us, 1.0, 1.0, SG_K)
-        res = _sg_residuals(B, sg, c256, n256, train)
-        ys = _sg_scales(res)
-        B.ann_surrogate_set_scales(sg, us, ys[0], ys[2], SG_K)
         t0 = time.perf_counter()
-        l0, l1 = _sg_train(B, sg, c256, n256, train, res, ys, 600, 3e-3)
-        out["pretrain"] = {"resolution": 256, "trajectories": 7, "pairs": len(train), "iters": 600,
-                           "loss_first": l0, "loss_last": l1, "seconds": time.perf_counter() - t0}
-        e_net, e_eul = _sg_eval(B, sg, c256, n256, test, ys)
-        out["pretrain"].update({"heldout_err": e_net, "euler_err": e_eul})
-    finally:
-        B.ann_destroy(c256)
+        out["pretrain"] = _sg_pretrain(B, sg)
+        out["pretrain"]["seconds"] = time.perf_counter() - t0
+    except BaseException:
+        B.ann_surrogate_destroy(sg)
+        raise
     # fine-tuning and evaluation at 1024 x 1024 (the workload of the headline metric)
     try:
         n = NX * NX
@@ -516,10 +566,11 @@ def surrogate_bench(B, max_err=0.05):
             B.ann_surrogate_set_scales(sg, us1, ys1[0], ys1[2], SG_K)
             t0 = time.perf_counter()
             l0, l1 = _sg_train(B, sg, c1, n, tr1, res1, ys1, 200, 1e-3)
-            e_net, e_eul = _sg_eval(B, sg, c1, n, te1, ys1)
+            e_net, e_eul, e_q, e_u = _sg_eval(B, sg, c1, n, te1, ys1, parts=True)
             out["finetune"] = {"resolution": NX, "pairs": len(tr1), "iters": 200, "loss_first": l0,
                                "loss_last": l1, "seconds": time.perf_counter() - t0, "heldout_err": e_net,
-                               "euler_err": e_eul}
+                               "euler_err": e_eul, "heldout_q_err_net_euler": e_q,
+                               "heldout_u_err_net_euler": e_u, "velocity_correction": False}
             use = e_net <= max_err
             out["fallback"] = not use
             # timing on the last held-out state: one recorded plain step + a jump vs k + 1 plain steps
@@ -531,7 +582,7 @@ def surrogate_bench(B, max_err=0.05):
             load()
             B.ann_set_record(c1, 1)
             B.ann_step(c1, 3)
-            reps = 5
+            reps = 20
             t_plain = []
             for _ in range(reps):
                 t1 = time.perf_counter()
@@ -547,7 +598,7 @@ def surrogate_bench(B, max_err=0.05):
             out["timing"] = {"plain_ms_per_cycle": 1e3 * tp, "surrogate_ms_per_cycle": 1e3 * tc,
                              "steps_per_cycle": SG_K + 1, "speedup": tp / tc,
                              "speedup_used": tp / tc if use else 1.0,
-                             "clock": "wall, synchronised calls, min of 5"}
+                             "clock": "wall, synchronised calls, min of 20"}
             # rollout: 25 cycles from the same state, surrogate against plain SPH
             cyc = 25
             load()

@@ -403,8 +403,15 @@ int ann_surrogate_adam(ann_surrogate *sg, double lr);
 /* Advance ctx by the network's k steps with one evaluation: load (tend as for ann_surrogate_load),
  * forward, and replace the context's state by the prediction (t and the step count advance by k;
  * accelerations restart from 0, so the next jump needs a recorded plain step first; periodic image
- * counts follow the particles). */
+ * counts follow the particles).  Q takes the explicit increment plus the network's correction; u
+ * takes the explicit increment alone unless the velocity correction is switched on (below). */
 int ann_surrogate_jump(ann_surrogate *sg, ann_ctx *ctx, const float *tend);
+
+/* Whether the jump adds the network's velocity correction ys_u (y2, y3) (on = 1) or not (0, the
+ * default).  In the viscous regime of the paper's runs u follows Q almost instantly: the
+ * correction gains little on a single jump and, fed back over many jumps, grows a mode of its own,
+ * so rollouts leave it off.  Errors: INVALID_ARG. */
+int ann_surrogate_set_velocity_correction(ann_surrogate *sg, int32_t on);
 
 const char *ann_surrogate_last_error(ann_surrogate *sg);
 

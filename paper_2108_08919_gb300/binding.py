@@ -129,6 +129,7 @@ def lib() -> ctypes.CDLL:
         "ann_surrogate_gradients": (i32, [vp, _P(ctypes.c_float), _P(ctypes.c_double), _P(ctypes.c_float)]),
         "ann_surrogate_adam": (i32, [vp, ctypes.c_double]),
         "ann_surrogate_jump": (i32, [vp, vp, _P(ctypes.c_float)]),
+        "ann_surrogate_set_velocity_correction": (i32, [vp, i32]),
         "ann_surrogate_last_error": (ctypes.c_char_p, [vp]),
         "ann_ensemble_create": (i32, [_P(ann_params), i32, _P(vp)]),
         "ann_ensemble_destroy": (None, [vp]),
@@ -568,6 +569,11 @@ def ann_surrogate_adam(sg, lr: float) -> None:
 def ann_surrogate_jump(sg, ctx, tend=None) -> None:
     ptr, keep = _tend(tend)
     _scheck(lib().ann_surrogate_jump(sg, ctx, ptr), sg, "ann_surrogate_jump")
+
+
+def ann_surrogate_set_velocity_correction(sg, on) -> None:
+    _scheck(lib().ann_surrogate_set_velocity_correction(sg, int(on)), sg,
+            "ann_surrogate_set_velocity_correction")
 
 
 def ann_surrogate_last_error(sg) -> str:

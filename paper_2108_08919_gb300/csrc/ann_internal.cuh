@@ -133,12 +133,15 @@ cudaError_t enqueue_defects(int M, const double *grid, signed char *map, unsigne
 cudaError_t enqueue_mixing(const DevParams &P, const Bufs &b, const unsigned char *colors, int G, int S,
                            unsigned *cnt, cudaStream_t s);
 // Neighbour graph of the present positions in the cell-sorted order of the last search (ELL: entry
-// k of row g at k * n + g; neighbours as sorted indices), for the learned surrogate.
+// k of row g at k * n + g; neighbours as sorted indices), for the learned surrogate.  A row lists
+// the cnt2 neighbours closer than 2h (the network's graph) first, then the rest of the support (3h).
 struct GraphOut {
     int *nbr;        // MAXN x n neighbour sorted indices
     float *W;        // MAXN x n kernel values W(|x_i - x_j|)
-    int *cnt;        // n
-    float *S;        // n: W(0) + sum_j W
+    int *cnt;        // n: neighbours in the support
+    int *cnt2;       // n: of which closer than 2h
+    float *S;        // n: W(0) + sum_j W over the support
+    float *S2;       // n: W(0) + sum_j W over the 2h neighbours
     double *x, *y;   // n: positions
     float4 *u4;      // n: (ux, uy, q11, q12)
     float *dr;       // n: rho / rho0 - 1

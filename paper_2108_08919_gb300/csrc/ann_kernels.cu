@@ -1157,18 +1157,31 @@ __global__ void __launch_bounds__(PT) k_export_graph(DevParams P, Bufs b, GraphO
         int si = inner_slot(ts, T, q);
         int gi = sg[si];
         float4 pi = pos[si];
+        // neighbours inside the network radius (2h) first (a walk of their own), then the rest of
+        // the support
+        const float r2net = 4.f / (P.inv_h * P.inv_h);
+        const unsigned long long em = b.emask[gi];
         int k = 0;
-        for_each_candidate<1>(P, b, gi, b.emask[gi], [&](int off, int, unsigned in) {
-            int j = off >> 4;
-            if (in && j < T.H && k < MAXN) {
-                float r2 = len2(pair_d(pi, slot_at(pos, off)));
-                o.nbr[(size_t)k * P.n + gi] = sg[j];
-                o.W[(size_t)k * P.n + gi] = kernel_w<true>(r2, P);
-                k++;
-            }
-        });
+        float s2 = P.W0;
+        for (int pass = 0; pass < 2; pass++) {
+            for_each_candidate<1>(P, b, gi, em, [&](int off, int, unsigned in) {
+                int j = off >> 4;
+                if (in && j < T.H && k < MAXN) {
+                    float r2 = len2(pair_d(pi, slot_at(pos, off)));
+                    if ((r2 < r2net) == (pass == 0)) {
+                        float w = kernel_w<true>(r2, P);
+                        o.nbr[(size_t)k * P.n + gi] = sg[j];
+                        o.W[(size_t)k * P.n + gi] = w;
+                        if (pass == 0) s2 += w;
+                        k++;
+                    }
+                }
+            });
+            if (pass == 0) o.cnt2[gi] = k;
+        }
         o.cnt[gi] = k;
         o.S[gi] = b.sumW[gi];
+        o.S2[gi] = s2;
         o.x[gi] = b.mx[gi];
         o.y[gi] = b.my[gi];
         o.u4[gi] = make_float4(b.mux[gi], b.muy[gi], b.mq11[gi], b.mq12[gi]);

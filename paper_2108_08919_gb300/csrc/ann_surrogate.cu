@@ -56,43 +56,61 @@ struct TendScales {
     float a, m, lap, grad;
 };
 
+// Entry q of row i of the ELL.
+__device__ __forceinline__ size_t support_entry(const GraphView &g, int i, int q) { return (size_t)q * g.n + i; }
+
+constexpr int SL = 4;   // lanes per particle in the support means
+
 // Features of every particle, and the first SPH mean of the acceleration (agg1 = agg(ax, ay), two
-// planes) from the same neighbour walk.
-__global__ void k_sg_features(GraphView g, const float4 *u4, float inv_us, const float *tend, TendScales ts,
-                              bf16 *X, float *agg1)
+// planes) from the same neighbour walk, on the 3h support.  SL lanes per particle take every SL-th
+// neighbour; the partial sums meet by shuffles.
+__global__ void __launch_bounds__(256) k_sg_features(GraphView g, const float4 *u4, float inv_us,
+                                                     const float *tend, TendScales ts, bf16 *X, float *agg1)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(t / SL), sub = (int)(t % SL);
+    const bool live = i < g.n;
+    const int ii = live ? i : 0;
     const float *ax = tend, *ay = tend + g.n;
-    float4 s = u4[i];
-    float r[4] = {s.z, s.w, s.x * inv_us, s.y * inv_us};
-    float is = 1.f / g.S[i], a[4];
-    for (int c = 0; c < 4; c++) a[c] = g.W0 * is * r[c];
-    float sx = g.W0 * is * ax[i], sy = g.W0 * is * ay[i];
-    int m = g.cnt[i];
-#pragma unroll 4
-    for (int k = 0; k < m; k++) {
-        int j = __ldg(g.nbr + (size_t)k * g.n + i);
-        float w = __ldg(g.W + (size_t)k * g.n + i) * is;
-        float4 t = __ldg(u4 + j);
-        a[0] += w * t.z;
-        a[1] += w * t.w;
-        a[2] += w * t.x * inv_us;
-        a[3] += w * t.y * inv_us;
-        sx += w * __ldg(ax + j);
-        sy += w * __ldg(ay + j);
+    float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // Q11, Q12, ux, uy, ax, ay
+    if (live) {
+        const int m = g.cnt[ii];
+#pragma unroll 2
+        for (int q = sub; q < m; q += SL) {
+            const size_t e = support_entry(g, ii, q);
+            const int j = __ldg(g.nbr + e);
+            const float w = __ldg(g.W + e);
+            const float4 u = __ldg(u4 + j);
+            a[0] += w * u.z;
+            a[1] += w * u.w;
+            a[2] += w * u.x;
+            a[3] += w * u.y;
+            a[4] += w * __ldg(ax + j);
+            a[5] += w * __ldg(ay + j);
+        }
     }
-    agg1[i] = sx;
-    agg1[(size_t)g.n + i] = sy;
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+        a[c] += __shfl_xor_sync(0xFFFFFFFFu, a[c], 1);
+        a[c] += __shfl_xor_sync(0xFFFFFFFFu, a[c], 2);
+    }
+    if (!live || sub != 0) return;
+    const float4 s = u4[i];
+    const float is = 1.f / g.S[i];
+    const float r[4] = {s.z, s.w, s.x * inv_us, s.y * inv_us};
+    const float self[4] = {s.z, s.w, s.x, s.y};
     bf16 *row = X + (size_t)i * F0;
     for (int c = 0; c < 4; c++) {
+        const float mean = (g.W0 * self[c] + a[c]) * is * (c < 2 ? 1.f : inv_us);
         row[c] = __float2bfloat16(r[c]);
-        row[4 + c] = __float2bfloat16(a[c] - r[c]);
+        row[4 + c] = __float2bfloat16(mean - r[c]);
     }
     for (int c = 0; c < 8; c++) {
         float sc = c < 2 ? ts.a : (c < 4 ? ts.m : (c < 6 ? ts.lap : ts.grad));
         row[8 + c] = __float2bfloat16(tend[(size_t)c * g.n + i] * sc);
     }
+    agg1[i] = (g.W0 * ax[i] + a[4]) * is;
+    agg1[(size_t)g.n + i] = (g.W0 * ay[i] + a[5]) * is;
 }
 
 // The tendencies of the context's last recorded step, into ID order (8 x n, component-major):
@@ -142,24 +160,35 @@ __global__ void k_sg_rows_from_id(int n, const int *ids, const float *src, float
     reinterpret_cast<float4 *>(dst)[g] = reinterpret_cast<const float4 *>(src)[ids[g]];
 }
 
-// out = agg(in) for two FP32 planes (component-major, n apart).
-__global__ void k_sg_mean2(GraphView g, const float *in, float *out)
+// out = agg(in) on the 3h support for two FP32 planes (component-major, n apart); SL lanes per
+// particle as in the features.
+__global__ void __launch_bounds__(256) k_sg_mean2(GraphView g, const float *in, float *out)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(t / SL), sub = (int)(t % SL);
+    const bool live = i < g.n;
+    const int ii = live ? i : 0;
     const float *fx = in, *fy = in + g.n;
-    float is = 1.f / g.S[i];
-    float sx = g.W0 * is * fx[i], sy = g.W0 * is * fy[i];
-    int m = g.cnt[i];
-#pragma unroll 4
-    for (int k = 0; k < m; k++) {
-        int j = __ldg(g.nbr + (size_t)k * g.n + i);
-        float w = __ldg(g.W + (size_t)k * g.n + i) * is;
-        sx += w * __ldg(fx + j);
-        sy += w * __ldg(fy + j);
+    float sx = 0.f, sy = 0.f;
+    if (live) {
+        const int m = g.cnt[ii];
+#pragma unroll 2
+        for (int q = sub; q < m; q += SL) {
+            const size_t e = support_entry(g, ii, q);
+            const int j = __ldg(g.nbr + e);
+            const float w = __ldg(g.W + e);
+            sx += w * __ldg(fx + j);
+            sy += w * __ldg(fy + j);
+        }
     }
-    out[i] = sx;
-    out[(size_t)g.n + i] = sy;
+    sx += __shfl_xor_sync(0xFFFFFFFFu, sx, 1);
+    sx += __shfl_xor_sync(0xFFFFFFFFu, sx, 2);
+    sy += __shfl_xor_sync(0xFFFFFFFFu, sy, 1);
+    sy += __shfl_xor_sync(0xFFFFFFFFu, sy, 2);
+    if (!live || sub != 0) return;
+    const float is = 1.f / g.S[i];
+    out[i] = (g.W0 * fx[i] + sx) * is;
+    out[(size_t)g.n + i] = (g.W0 * fy[i] + sy) * is;
 }
 
 // inc[i] = k dt (m11, m12, agg(agg(a))x, agg(agg(a))y)[i]: the explicit increment in the order of
@@ -392,14 +421,15 @@ struct ann_surrogate {
     int n = 0;
     double us = 1.0, ysq = 1.0, ysu = 1.0;
     int k = 8;                  // steps the network spans
+    int vel_corr = 0;           // the jump adds the network's velocity correction
     double gammaK = 0.0;        // Gamma K of the loaded context
     cudaStream_t s = nullptr;
     std::vector<void *> allocs;
     std::string last_err;
     // graph and state in the context's cell-sorted order (row g is particle ids[g]); tend_id and
     // io4 hold ID-ordered tendencies and host rows on their way in or out
-    int *nbr = nullptr, *cnt = nullptr, *ids = nullptr;
-    float *W = nullptr, *S = nullptr, *dr = nullptr, *tend = nullptr, *inc = nullptr, *tend_id = nullptr,
+    int *nbr = nullptr, *cnt = nullptr, *cnt2 = nullptr, *ids = nullptr;
+    float *W = nullptr, *S = nullptr, *S2 = nullptr, *dr = nullptr, *tend = nullptr, *inc = nullptr, *tend_id = nullptr,
           *io4 = nullptr;
     double *x = nullptr, *y = nullptr;
     float4 *u4 = nullptr;
@@ -447,7 +477,10 @@ int scuda(ann_surrogate *S, cudaError_t e, const char *where)
                  std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// The SPH support (3h): the features' mean and the explicit increment.
 GraphView view(const ann_surrogate *S) { return GraphView{S->nbr, S->W, S->cnt, S->S, S->n, S->W0}; }
+// The network's graph (neighbours closer than 2h, the first cnt2 entries of each row).
+GraphView view_net(const ann_surrogate *S) { return GraphView{S->nbr, S->W, S->cnt2, S->S2, S->n, S->W0}; }
 
 // BF16 copies (and transposes) of the weights for the next forward / backward pass.
 cudaError_t cast_weights(ann_surrogate *S)
@@ -473,7 +506,7 @@ cudaError_t forward(ann_surrogate *S, bool keep_h3)
 {
     cudaStream_t s = S->s;
     int n = S->n;
-    GraphView g = view(S);
+    GraphView g = view_net(S);
     unsigned *err = S->err;
     k_sg_agg<F0><<<nb((size_t)n * (F0 / 8)), 256, 0, s>>>(g, S->X0, S->AX);
     cudaError_t e = enqueue_layer(S->X0, F0, S->AX, F0, S->W1b, S->p + O_B1, S->P1b, nullptr, MSG, S->H1, S->Z1, 1,
@@ -496,7 +529,7 @@ cudaError_t backward(ann_surrogate *S)
 {
     cudaStream_t s = S->s;
     int n = S->n;
-    GraphView g = view(S);
+    GraphView g = view_net(S);
     unsigned *err = S->err;
     const int K2 = WIDTH + MSG;
     float *gp = S->g;
@@ -582,6 +615,7 @@ int ann_surrogate_create(int64_t n_max, ann_surrogate **out)
     cudaError_t e = cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking);
 #define SA_(p, c) if (!e) e = sg_alloc(S, S->p, c)
     SA_(nbr, (size_t)MAXN * n); SA_(W, (size_t)MAXN * n); SA_(cnt, n); SA_(S, n); SA_(dr, n);
+    SA_(cnt2, n); SA_(S2, n);
     SA_(x, n); SA_(y, n); SA_(u4, n); SA_(tend, 8 * n); SA_(inc, 4 * n); SA_(ids, n); SA_(tend_id, 8 * n);
     SA_(io4, 4 * n);
     SA_(X0, n * F0); SA_(AX, n * F0); SA_(H1, n * WIDTH); SA_(Z1, n * MSG); SA_(AZ1, n * MSG);
@@ -676,7 +710,7 @@ int ann_surrogate_load(ann_surrogate *S, ann_ctx *ctx, const float *tend)
     S->dt = v.P.dt_d;
     S->rho0 = v.P.rho0;
     S->gammaK = (double)v.P.Gamma * (double)v.P.K;
-    GraphOut o{S->nbr, S->W, S->cnt, S->S, S->x, S->y, S->u4, S->dr, S->ids};
+    GraphOut o{S->nbr, S->W, S->cnt, S->cnt2, S->S, S->S2, S->x, S->y, S->u4, S->dr, S->ids};
     cudaError_t e = cudaStreamSynchronize(v.stream);
     if (!e) e = enqueue_export_graph(v.P, v.b, o, S->s);
     if (!e) {
@@ -684,8 +718,9 @@ int ann_surrogate_load(ann_surrogate *S, ann_ctx *ctx, const float *tend)
         double kdt = S->k * S->dt;
         TendScales ts{(float)(kdt / S->ysu), (float)(kdt / S->ysq), (float)(S->gammaK * kdt / S->ysq), (float)kdt};
         // dH is scratch between here and the next backward pass
-        k_sg_features<<<nb(S->n), 256, 0, S->s>>>(view(S), S->u4, (float)(1.0 / S->us), S->tend, ts, S->X0, S->dH);
-        k_sg_mean2<<<nb(S->n), 256, 0, S->s>>>(view(S), S->dH, S->dH + 2 * (size_t)S->n);
+        k_sg_features<<<nb((size_t)S->n * SL), 256, 0, S->s>>>(view(S), S->u4, (float)(1.0 / S->us), S->tend,
+                                                               ts, S->X0, S->dH);
+        k_sg_mean2<<<nb((size_t)S->n * SL), 256, 0, S->s>>>(view(S), S->dH, S->dH + 2 * (size_t)S->n);
         k_sg_euler<<<nb(S->n), 256, 0, S->s>>>(S->n, S->tend, S->dH + 2 * (size_t)S->n, (float)kdt, S->inc);
         e = cudaGetLastError();
     }
@@ -756,7 +791,8 @@ int ann_surrogate_jump(ann_surrogate *S, ann_ctx *ctx, const float *tend)
     st = ctx_view(ctx, &v);
     if (st) return st;
     k_sg_jump<<<nb(S->n), 256, 0, S->s>>>(S->n, S->ids, S->x, S->y, S->u4, S->dr, S->Y, S->inc, (float)S->ysq,
-                                          (float)S->ysu, S->dt * k, S->L, S->rho0, v.b.img, v.tmp);
+                                          S->vel_corr ? (float)S->ysu : 0.f, S->dt * k, S->L, S->rho0, v.b.img,
+                                          v.tmp);
     cudaError_t e = cudaGetLastError();
     if (!e) e = cudaStreamSynchronize(S->s);
     if (e) return scuda(S, e, "ann_surrogate_jump");
@@ -802,6 +838,13 @@ int ann_surrogate_euler(ann_surrogate *S, float *inc)
     if (!e) e = cudaMemcpyAsync(inc, S->io4, (size_t)S->n * NOUT * sizeof(float), cudaMemcpyDeviceToHost, S->s);
     if (!e) e = cudaStreamSynchronize(S->s);
     return e ? scuda(S, e, "ann_surrogate_euler") : ANN_OK;
+}
+
+int ann_surrogate_set_velocity_correction(ann_surrogate *S, int32_t on)
+{
+    if (!S || (on != 0 && on != 1)) return ANN_ERR_INVALID_ARG;
+    S->vel_corr = on;
+    return ANN_OK;
 }
 
 const char *ann_surrogate_last_error(ann_surrogate *S) { return S ? S->last_err.c_str() : ""; }

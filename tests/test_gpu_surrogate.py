@@ -4,8 +4,8 @@
   and weights.  BF16 storage (unit roundoff 2^-9) of inputs, weights and activations through four
   layers and their backward pass bounds the normwise error near 2e-2; the tests allow 3e-2 for
   outputs and 6e-2 for gradients.
-* The jump applies the predicted increments (the explicit k dt (m, agg(agg(a))) plus the network's correction)
-  to Q and u and moves the particles by k dt (u + u')/2.
+* The jump applies the predicted increments (the explicit k dt (m, agg(agg(a))) plus the network's correction,
+  to u only when the velocity correction is switched on) and moves the particles by k dt (u + u')/2.
 * Trained on 8-step pairs the plain solver generates, the network predicts held-out increments
   better than persistence, than the explicit 8-step Euler increment of the tendencies (the
   untrained network), and than the plain method taking one step of 8 dt.
@@ -84,10 +84,11 @@ def test_forward_and_gradients_match_the_oracle(B, S, orc):
         B.ann_surrogate_destroy(sg)
         B.ann_destroy(ctx)
     rp, cols = orc.neighbors(ic["x"], ic["y"], 1.0, p["h"])
-    G = S.Graph(ic["x"], ic["y"], 1.0, p["h"], rp, cols)
+    G = S.Graph(ic["x"], ic["y"], 1.0, p["h"], rp, cols)               # the support: features, increment
+    Gn = S.Graph(ic["x"], ic["y"], 1.0, p["h"], rp, cols, radius=2.0)  # the network's graph
     x = S.features(G, ic["q11"], ic["q12"], ic["ux"], ic["uy"], tend, us, k * p["dt"], p["Gamma"] * p["K"], ysq, ysu)
-    yo, c = S.forward(w, G, x)
-    go = S.backward(w, G, c, yo, t)
+    yo, c = S.forward(w, Gn, x)
+    go = S.backward(w, Gn, c, yo, t)
     errs = {"y": relerr(y, yo), "loss": abs(loss - S.loss(yo, t)) / S.loss(yo, t),
             "euler": relerr(inc, S.euler_increment(G, tend, k * p["dt"]))}
     assert errs["euler"] <= 1e-5, errs   # FP32 sums of the same SPH mean
@@ -117,6 +118,13 @@ def test_jump_applies_the_increments(B, S):
         ysq, ysu = 0.5, 0.01
         B.ann_surrogate_set_scales(sg, 1.0, ysq, ysu, k)
         tend = np.tile([0.5, -0.25, 1.0, -2.0, 7.0, 3.0, 0.1, 0.2], (ic["n"], 1))
+        # by default u takes the explicit increment alone
+        B.ann_surrogate_jump(sg, ctx, tend)
+        u_off = {f: B.ann_get_field(ctx, f, ic["n"]).astype(np.float64) for f in ("UX", "UY")}
+        _load(B, ctx, ic)
+        with pytest.raises(B.AnnError):
+            B.ann_surrogate_set_velocity_correction(sg, 2)
+        B.ann_surrogate_set_velocity_correction(sg, True)
         B.ann_surrogate_jump(sg, ctx, tend)
         got = {f: B.ann_get_field(ctx, f, ic["n"]).astype(np.float64) for f in ("X", "Y", "UX", "UY", "Q11", "Q12")}
         unw = B.ann_get_unwrapped(ctx, np.arange(ic["n"]))
@@ -127,6 +135,8 @@ def test_jump_applies_the_increments(B, S):
     f32 = lambda v: np.float32(v).astype(np.float64)  # noqa: E731
     dt = p["dt"]
     kdt = k * dt
+    assert np.abs(u_off["UX"] - (f32(ic["ux"]) + kdt * 0.5)).max() < 1e-6
+    assert np.abs(u_off["UY"] - (f32(ic["uy"]) - kdt * 0.25)).max() < 1e-6
     ux1 = f32(ic["ux"]) + kdt * 0.5 + ysu * float(bo[2])
     uy1 = f32(ic["uy"]) - kdt * 0.25 + ysu * float(bo[3])
     assert np.abs(got["UX"] - ux1).max() < 1e-6 and np.abs(got["UY"] - uy1).max() < 1e-6

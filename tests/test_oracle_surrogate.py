@@ -13,11 +13,29 @@ def S():
     return surrogate
 
 
-def _graph(S, orc, nx=10, seed=3):
+def _graph(S, orc, nx=10, seed=3, radius=3.0):
     ic = si.jittered_lattice(nx, seed=seed, jitter=0.2)
     h = 1.3 * ic["dx"]
     rp, cols = orc.neighbors(ic["x"], ic["y"], 1.0, h)
-    return ic, S.Graph(ic["x"], ic["y"], 1.0, h, rp, cols)
+    return ic, S.Graph(ic["x"], ic["y"], 1.0, h, rp, cols, radius=radius)
+
+
+def test_network_graph_is_the_2h_part_of_the_support(S, orc):
+    """The 2h graph keeps exactly the support pairs closer than 2h (brute force over all pairs),
+    is symmetric, and is still an SPH mean."""
+    ic, G2 = _graph(S, orc, radius=2.0)
+    _, G3 = _graph(S, orc)
+    h, n = 1.3 * ic["dx"], G2.n
+    dx = ic["x"][:, None] - ic["x"][None, :]
+    dy = ic["y"][:, None] - ic["y"][None, :]
+    dx -= np.round(dx)
+    dy -= np.round(dy)
+    r = np.sqrt(dx * dx + dy * dy)
+    want = {(i, j) for i, j in zip(*np.nonzero((r < 2 * h) & ~np.eye(n, dtype=bool)))}
+    got = set(zip(G2.rows.tolist(), G2.cols.tolist()))
+    assert got == want and {(j, i) for i, j in got} == got
+    assert len(G3.rows) > 2 * len(G2.rows)
+    assert np.abs(G2.agg(np.full((n, 2), -1.5)) + 1.5).max() < 1e-14
 
 
 def test_aggregation_mean_and_adjoint(S, orc):
@@ -34,7 +52,7 @@ def test_aggregation_mean_and_adjoint(S, orc):
 
 
 def _random_problem(S, orc, seed=0):
-    ic, G = _graph(S, orc)
+    ic, G = _graph(S, orc, radius=2.0)
     p = S.init_params(seed)
     for k, b in (("b1", 0), ("b2", 1), ("b3", 2), ("bo", 3)):
         p[k] = 0.2 * (si.uniform53(seed + 60 + b, p[k].size) - 0.5)
@@ -77,7 +95,7 @@ def test_zero_weights_give_the_bias_and_permutation_equivariance(S, orc):
     perm = np.argsort(si.uniform53(9, G.n))
     x2, y2 = ic["x"][perm], ic["y"][perm]
     rp, cols = orc.neighbors(x2, y2, 1.0, 1.3 * ic["dx"])
-    G2 = S.Graph(x2, y2, 1.0, 1.3 * ic["dx"], rp, cols)
+    G2 = S.Graph(x2, y2, 1.0, 1.3 * ic["dx"], rp, cols, radius=2.0)
     ya, _ = S.forward(p, G, x)
     yb, _ = S.forward(p, G2, x[perm])
     assert np.abs(yb - ya[perm]).max() < 1e-12
