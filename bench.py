@@ -532,6 +532,36 @@ def _sg_eval(B, sg, ctx, n, pairs, ys, parts=False):
             [float(v) for v in np.mean(pu, axis=0)])
 
 
+def surrogate_cycles(cycles):
+    """Cycles of one recorded plain step and one jump on the 1024^2 workload with the library's
+    He-initialised weights; prints the mean wall time of a cycle (synchronised calls)."""
+    import sph_inputs as si
+    from paper_2108_08919_gb300 import binding as B, build
+
+    build.build()
+    n = NX * NX
+    p = _sg_params(B, NX, PARAMS["zeta"], PARAMS["K"])
+    ctx = B.ann_create(p)
+    sg = B.ann_surrogate_create(n)
+    try:
+        ic = si.jittered_lattice(NX, seed=3)
+        B.ann_set_particles(ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"], ic["rho"])
+        B.ann_set_record(ctx, 1)
+        B.ann_surrogate_init(sg, 7)
+        B.ann_surrogate_set_scales(sg, 1e-3, 1e-3, 1e-5, SG_K)
+        B.ann_step(ctx, 2)
+        t0 = time.perf_counter()
+        for _ in range(cycles):
+            B.ann_step(ctx, 1)
+            B.ann_surrogate_jump(sg, ctx, None)
+        ms = 1e3 * (time.perf_counter() - t0) / cycles
+    finally:
+        B.ann_surrogate_destroy(sg)
+        B.ann_destroy(ctx)
+    print(json.dumps({"surrogate_cycles": cycles, "ms_per_cycle": ms, "particles": n}))
+    return 0
+
+
 def surrogate_bench(B, max_err=0.05):
     """The learned surrogate: pre-trained on 256 x 256 trajectories, fine-tuned and evaluated on the
     1024 x 1024 workload; held-out k-step error, the speed of one recorded plain step plus a jump
@@ -811,9 +841,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-member ensemble measurement")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
+    ap.add_argument("--surrogate-cycles", type=int, default=0,
+                    help="only run this many surrogate cycles (recorded step + jump) at the headline size, "
+                         "untrained weights, and print their wall time (for launch lists and profiles)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.surrogate_cycles > 0:
+        return surrogate_cycles(args.surrogate_cycles)
     return run_ours(args)
 
 
