@@ -20,7 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sph_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "sph_diag.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "sph_diag.c"), os.path.join(_HERE, "sph_oracle3d.c")]
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liborc.so")
 _lock = threading.Lock()
@@ -60,7 +60,7 @@ NBR_MODES = {"brute": 0, "ghost": 1, "cells": 2}
 
 
 def build(force: bool = False) -> str:
-    """Compile ``sph_oracle.c`` and ``sph_diag.c`` into ``_lib/liborc.so`` with gcc (OpenMP, no FP
+    """Compile ``sph_oracle.c``, ``sph_diag.c`` and ``sph_oracle3d.c`` into ``_lib/liborc.so`` with gcc (OpenMP, no FP
     contraction)."""
     with _lock:
         if (not force and os.path.exists(_LIB)

@@ -19,6 +19,9 @@ zero initial velocity and a slightly perturbed nematic orientation):
   ``Q12 = q sin(2 theta) + g12`` (2D: Q = 2q(nn - I/2), §2).  Velocity is zero, density is rho0.
 * ``uniform_random``: ``n`` positions uniform in the box (irregular cell occupancy, ragged sizes).
 * ``hex_lattice``: a triangular lattice patch (used by operator pins that need isotropic moments).
+* ``jittered_lattice3``: the 3D variant, an ``nx^3`` cubic lattice (ID ``ix + nx (iy + nx iz)``),
+  eight uniforms per particle in ID order: jitter ``jx, jy, jz``, a director uniform on the sphere
+  (``cos(polar)``, azimuth) for a uniaxial ``Q = s0 (d d - I/3)``, and optional velocities.
 """
 from __future__ import annotations
 
@@ -30,6 +33,7 @@ __all__ = [
     "splitmix64",
     "uniform53",
     "jittered_lattice",
+    "jittered_lattice3",
     "uniform_random",
     "hex_lattice",
     "wrap_positions",
@@ -99,6 +103,35 @@ def jittered_lattice(nx: int, ny: int | None = None, *, L: float = 1.0, seed: in
         "rho": np.full(n, rho0),
         "id": ids.astype(np.int32),
     }
+
+
+def jittered_lattice3(nx: int, *, L: float = 1.0, seed: int = 0, jitter: float = 0.05, s0: float = 0.5,
+                      u_scale: float = 0.0, rho0: float = 1.0) -> dict:
+    """Jittered cubic lattice of nx^3 particles (spacing dx = L / nx, particle ID = ix + nx (iy + nx iz))
+    with a uniaxial Q = s0 (d d - I/3) about a random direction d per particle (uniform on the
+    sphere) and, if u_scale > 0, velocities uniform in [-u_scale/2, u_scale/2]^3.
+
+    Returns float64 arrays ``x, y, z, rho`` (n), ``u`` (n, 3), ``q`` (n, 5) = (Q11, Q12, Q13, Q22, Q23),
+    and the scalars ``dx`` and ``n``.
+    """
+    n = nx ** 3
+    dx = L / nx
+    u = uniform53(seed, 8 * n).reshape(n, 8) if n > 0 else np.zeros((0, 8))
+    ids = np.arange(n, dtype=np.int64)
+    ix = (ids % nx).astype(np.float64)
+    iy = ((ids // nx) % nx).astype(np.float64)
+    iz = (ids // (nx * nx)).astype(np.float64)
+    pos = [wrap_positions((i + 0.5) * dx + (u[:, c] - 0.5) * (2.0 * jitter) * dx, L)
+           for c, i in enumerate((ix, iy, iz))]
+    cz = 2.0 * u[:, 3] - 1.0
+    ph = 2.0 * math.pi * u[:, 4]
+    sz = np.sqrt(np.maximum(1.0 - cz * cz, 0.0))
+    d = np.stack([sz * np.cos(ph), sz * np.sin(ph), cz], axis=1)
+    q = s0 * np.stack([d[:, 0] * d[:, 0] - 1.0 / 3.0, d[:, 0] * d[:, 1], d[:, 0] * d[:, 2],
+                       d[:, 1] * d[:, 1] - 1.0 / 3.0, d[:, 1] * d[:, 2]], axis=1)
+    vel = u_scale * (u[:, 5:8] - 0.5) if u_scale > 0 else np.zeros((n, 3))
+    return {"n": n, "dx": dx, "x": pos[0], "y": pos[1], "z": pos[2], "u": vel, "q": q,
+            "rho": np.full(n, rho0)}
 
 
 def uniform_random(n: int, *, L: float = 1.0, seed: int = 0, q_scale: float = 1.0,
