@@ -481,6 +481,74 @@ const char *ann_ensemble_last_error(ann_ensemble *ens);
 int ann_velocity_moments_noalloc(const float *ux, const float *uy, const float *mass, double m0,
                                  int64_t n, double *out, void *stream);
 
+/*
+ * Three-dimensional variant of the step (§3 with d = 3; the paper's runs are 2D, its equations are
+ * written for any dimension and Eq. (18) gives the 3D kernel constant a_d = 3 / (359 pi h^3)).
+ * Q is the symmetric traceless 3x3 tensor, stored as five components (Q11, Q12, Q13, Q22, Q23),
+ * Q33 = -Q11 - Q22; the molecular field keeps the B term (Q^2 - tr(Q^2) I / 3) of Eq. (7); the
+ * corrected Laplacian is the scalar form with factor 2 per component; the viscous term of Eq. (23)
+ * carries 2 (d + 2) nu = 10 nu.  Paper momentum mode only, no elastic stress.  A periodic cube of
+ * side L; cells of side >= 3h, at least 3 per side.  Neighbour lists hold at most
+ * ANN3_MAX_NEIGHBORS particles (~250 at h = 1.3 dx).  FP64 positions; pair differences are taken
+ * in FP64 and everything else runs in FP32.  The step order is that of the 2D step (modified
+ * Euler predictor, search, volumes, correction tensor, continuity, density filter and equation of
+ * state, velocity gradient, Laplacian of Q, Q rate, momentum, artificial displacement, corrector).
+ */
+#define ANN3_MAX_NEIGHBORS 448
+
+typedef struct ann3_ctx ann3_ctx;
+
+typedef struct {
+    int64_t n;
+    double L, h, dt, rho0, eta, Gamma, lambda_, A, B, C, K, zeta, gamma_eos, beta, c0_min, c_shift;
+    int32_t apd;
+    int32_t reserved[3];
+} ann3_params;
+
+/* Fields of ann3_get_field: components per particle in brackets. */
+enum {
+    ANN3_FIELD_POS = 0,    /* x, y, z [3] */
+    ANN3_FIELD_U = 1,      /* velocity [3] */
+    ANN3_FIELD_Q = 2,      /* Q11, Q12, Q13, Q22, Q23 [5] */
+    ANN3_FIELD_RHO = 3,    /* density [1] */
+    ANN3_FIELD_A = 4,      /* acceleration of the last step [3] */
+    ANN3_FIELD_SUMW = 5,   /* W(0) + sum_j W_ij of the last step [1] */
+    ANN3_FIELD_GRADU = 6,  /* corrected velocity gradient du_a/dx_b, row-major [9] */
+    ANN3_FIELD_LAPQ = 7,   /* corrected Laplacian of the five Q components [5] */
+    ANN3_FIELD_QRATE = 8,  /* projected Q rate m of Eq. (24) [5] */
+    ANN3_FIELD_P = 9,      /* pressure [1] */
+    ANN3_FIELD_NNBR = 10,  /* neighbours [1] */
+    ANN3_FIELD_COUNT = 11
+};
+
+/* Defaults: L 1, h 1.3 / 32, dt 1e-4, rho0 1, eta 1, Gamma 0.34, lambda 0.7, A 0, B 0, C 1, K 0.04,
+ * zeta 0.05, gamma 7, beta 1, c0_min 0, c_shift 1/3, apd 1; n 32^3. */
+int ann3_default_params(ann3_params *p);
+
+/* Device buffers for n particles.  Errors: INVALID_ARG (n < 1, h or L not positive, fewer than 3
+ * cells per side), NOT_AVAILABLE, OOM, CUDA. */
+int ann3_create(const ann3_params *p, ann3_ctx **out);
+void ann3_destroy(ann3_ctx *c);
+
+/* Load the state, ID order, host FP64: x, y, z (n each, in [0, L)), u (3n: ux, uy, uz per particle),
+ * q (5n), rho (n, or NULL for rho0); accelerations restart from 0.  Errors: INVALID_ARG (n differs
+ * from the context's, a NULL array, a non-finite value or a position outside [0, L)), CUDA. */
+int ann3_set_particles(ann3_ctx *c, int64_t n, const double *x, const double *y, const double *z,
+                       const double *u, const double *q, const double *rho);
+
+/* Advance by nsteps steps.  Errors: STATE (no particles), NBR_OVERFLOW, CELL_OVERFLOW,
+ * NONFINITE, SINGULAR_ALPHA (sticky device flags set by the kernels' own checks), CUDA. */
+int ann3_step(ann3_ctx *c, int64_t nsteps);
+
+/* A field in ID order into host FP64 dst (n x components, interleaved per particle).  Errors:
+ * INVALID_ARG (unknown field, NULL dst), STATE, CUDA. */
+int ann3_get_field(ann3_ctx *c, int32_t field, double *dst);
+
+/* Steps taken, and the device error bits (1 cell overflow, 4 neighbours, 8 non-finite, 16 alpha). */
+int ann3_get_status(ann3_ctx *c, int64_t *steps, uint32_t *error_bits);
+
+const char *ann3_last_error(ann3_ctx *c);
+
 #ifdef __cplusplus
 }
 #endif

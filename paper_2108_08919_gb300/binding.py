@@ -63,6 +63,16 @@ class ann_diag(ctypes.Structure):
         return d
 
 
+class ann3_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64)] + [(k, ctypes.c_double) for k in (
+        "L", "h", "dt", "rho0", "eta", "Gamma", "lambda_", "A", "B", "C", "K", "zeta", "gamma_eos",
+        "beta", "c0_min", "c_shift")] + [("apd", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+FIELDS3 = {"POS": (0, 3), "U": (1, 3), "Q": (2, 5), "RHO": (3, 1), "A": (4, 3), "SUMW": (5, 1),
+           "GRADU": (6, 9), "LAPQ": (7, 5), "QRATE": (8, 5), "P": (9, 1), "NNBR": (10, 1)}
+
+
 class AnnError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{msg} (status {status})")
@@ -138,6 +148,14 @@ def lib() -> ctypes.CDLL:
         "ann_ensemble_set_groups": (i32, [vp, i32]),
         "ann_ensemble_autotune": (i32, [vp, i32, _P(ctypes.c_int32), _P(ctypes.c_double)]),
         "ann_ensemble_last_error": (ctypes.c_char_p, [vp]),
+        "ann3_default_params": (i32, [_P(ann3_params)]),
+        "ann3_create": (i32, [_P(ann3_params), _P(vp)]),
+        "ann3_destroy": (None, [vp]),
+        "ann3_set_particles": (i32, [vp, i64, dp, dp, dp, dp, dp, dp]),
+        "ann3_step": (i32, [vp, i64]),
+        "ann3_get_field": (i32, [vp, i32, dp]),
+        "ann3_get_status": (i32, [vp, _P(ctypes.c_int64), _P(ctypes.c_uint32)]),
+        "ann3_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -589,3 +607,71 @@ def ann_surrogate_euler(sg, n: int):
     inc = np.zeros((n, 4), dtype=np.float32)
     _scheck(lib().ann_surrogate_euler(sg, _fp(inc)), sg, "ann_surrogate_euler")
     return inc
+
+
+# ---------------------------------------------------------------------------------------------
+# three-dimensional variant
+# ---------------------------------------------------------------------------------------------
+
+def _check3(status: int, ctx, what: str):
+    if status < 0:
+        detail = lib().ann3_last_error(ctx).decode() if ctx is not None else ""
+        text = lib().ann_status_string(status).decode()
+        raise AnnError(status, f"{what}: {text}" + (f" ({detail})" if detail else ""))
+    return status
+
+
+def ann3_default_params(**overrides) -> ann3_params:
+    p = ann3_params()
+    _check(lib().ann3_default_params(ctypes.byref(p)), what="ann3_default_params")
+    names = {f[0] for f in ann3_params._fields_}
+    for k, v in overrides.items():
+        k = "lambda_" if k == "lambda" else k
+        if k not in names or k == "reserved":
+            raise TypeError(f"ann3_params has no field {k!r}")
+        setattr(p, k, v)
+    return p
+
+
+def ann3_create(p: ann3_params) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(lib().ann3_create(ctypes.byref(p), ctypes.byref(ctx)), what="ann3_create")
+    return ctx
+
+
+def ann3_destroy(ctx) -> None:
+    if ctx:
+        lib().ann3_destroy(ctx)
+
+
+def ann3_set_particles(ctx, x, y, z, u, q, rho=None) -> None:
+    """Host FP64 state in ID order: x, y, z (n), u (n, 3), q (n, 5), rho (n) or None."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in (x, y, z, u, q)]
+    r = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
+    n = arrs[0].size
+    ptrs = [a.ctypes.data_as(ctypes.c_void_p) for a in arrs]
+    _check3(lib().ann3_set_particles(ctx, n, *ptrs, None if r is None else r.ctypes.data_as(ctypes.c_void_p)),
+            ctx, "ann3_set_particles")
+
+
+def ann3_step(ctx, nsteps: int = 1) -> None:
+    _check3(lib().ann3_step(ctx, int(nsteps)), ctx, "ann3_step")
+
+
+def ann3_get_field(ctx, name: str, n: int) -> np.ndarray:
+    """Field `name` (a key of FIELDS3) in ID order as an (n, components) FP64 array."""
+    fid, comps = FIELDS3[name]
+    out = np.zeros(n * comps, dtype=np.float64)
+    _check3(lib().ann3_get_field(ctx, fid, out.ctypes.data_as(ctypes.c_void_p)), ctx, "ann3_get_field")
+    return out.reshape(n, comps)
+
+
+def ann3_get_status(ctx):
+    steps = ctypes.c_int64()
+    bits = ctypes.c_uint32()
+    _check3(lib().ann3_get_status(ctx, ctypes.byref(steps), ctypes.byref(bits)), ctx, "ann3_get_status")
+    return steps.value, bits.value
+
+
+def ann3_last_error(ctx) -> str:
+    return lib().ann3_last_error(ctx).decode()

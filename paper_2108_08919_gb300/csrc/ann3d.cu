@@ -1,0 +1,807 @@
+// Three-dimensional variant of the SPH active-nematic step (the paper's equations for d = 3):
+// a periodic cube, Q as the symmetric traceless 3x3 tensor (Q11, Q12, Q13, Q22, Q23), the corrected
+// SPH operators with a 3x3 correction tensor, the viscous term with 2 (d + 2) nu = 10 nu.
+//
+// One step (modified Euler, §3.1), all on the device, one thread per particle:
+//   predict     u += dt/2 a, r += dt/2 u (wrap), max |u|, cell of each particle, cell counts
+//   scan        cell starts (one block)
+//   scatter     particle order by cell; each cell's slots sorted by particle ID (deterministic)
+//   gather      state into the new order (buffer set M)
+//   neighbours  lists of j with |r_i - r_j| < 3h from the 27 surrounding cells (FP64 differences),
+//               sum W, V = 1 / sum W (Eq. 19)
+//   correction  alpha (Eq. 22) and B = alpha^-1
+//   pass 1      continuity k (Eq. 25), rho_half, corrected velocity gradient (Eq. 20), corrected
+//               Laplacian of Q (Eq. 21), Q rate m (Eqs. 2, 7, 24), Q^{n+1}
+//   pass 2      density filter (Eq. 28), equation of state (Eq. 26) with c0 = max(10 max|u|, c0_min)
+//   pass 3      momentum (Eq. 23), artificial displacement (Eq. 29), corrector; the new state is
+//               written into buffer set S in the new order
+// The state lives in S between steps, in the cell order of the last step.  Errors are sticky bits
+// set by the kernels' own checks (neighbour overflow, non-finite state, singular alpha).
+#include "../../include/ann.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace {
+
+constexpr int MAXN3 = ANN3_MAX_NEIGHBORS;
+constexpr uint32_t E3_NBR = 4u, E3_NONFINITE = 8u, E3_ALPHA = 16u;
+
+struct P3 {
+    int n, nc, ncell;
+    double L, inv_cell, R2d, half_dt_d;
+    float h, inv_h, ad, W0, dt, half_dt;
+    float rho0, nu, Gamma, lambda, A, B, C, K, zeta, gamma_eos, beta, c0_min, c_shift;
+    int apd;
+};
+
+struct Set3 {   // one buffer set of the state
+    double *x, *y, *z;
+    float *u[3], *q[5], *dr, *a[3];   // dr: density deviation rho / rho0 - 1 (FP32 keeps its digits)
+    int *id;
+};
+
+struct Work3 {
+    int *key, *slot, *perm, *count, *start, *nbr, *nnbr;
+    float *sumW, *V, *B, *k, *dh, *dhat, *p, *qn, *an, *gu, *lap, *m;   // dh, dhat: deviations of rho_half, rho_hat
+    unsigned *umax, *err;
+};
+
+__device__ __forceinline__ double min_image(double d, double L)
+{
+    if (d > 0.5 * L) d -= L;
+    else if (d < -0.5 * L) d += L;
+    return d;
+}
+
+__device__ __forceinline__ double wrap(double v, double L)
+{
+    double w = v - L * floor(v / L);
+    if (w >= L) w -= L;
+    if (w < 0.0) w = 0.0;
+    return w;
+}
+
+// Quintic kernel (Eq. 18) and its derivative in b = r / h, times the 3D constant.
+__device__ __forceinline__ float w_of(float b, float ad)
+{
+    float t3 = fmaxf(3.f - b, 0.f), t2 = fmaxf(2.f - b, 0.f), t1 = fmaxf(1.f - b, 0.f);
+    float t3_2 = t3 * t3, t2_2 = t2 * t2, t1_2 = t1 * t1;
+    return ad * (t3_2 * t3_2 * t3 - 6.f * t2_2 * t2_2 * t2 + 15.f * t1_2 * t1_2 * t1);
+}
+
+__device__ __forceinline__ float dw_of(float b, float ad)
+{
+    float t3 = fmaxf(3.f - b, 0.f), t2 = fmaxf(2.f - b, 0.f), t1 = fmaxf(1.f - b, 0.f);
+    float t3_2 = t3 * t3, t2_2 = t2 * t2, t1_2 = t1 * t1;
+    return ad * (-5.f * t3_2 * t3_2 + 30.f * t2_2 * t2_2 - 75.f * t1_2 * t1_2);
+}
+
+// Pair data of i and j: d = r_i - r_j (FP64 minimum image, then FP32), r, W, grad_i W.
+struct Pair3 {
+    float d[3], r, W, g[3];
+};
+
+__device__ __forceinline__ Pair3 pair_of(const P3 &P, const Set3 &S, int i, int j)
+{
+    Pair3 p;
+    p.d[0] = (float)min_image(S.x[i] - S.x[j], P.L);
+    p.d[1] = (float)min_image(S.y[i] - S.y[j], P.L);
+    p.d[2] = (float)min_image(S.z[i] - S.z[j], P.L);
+    p.r = sqrtf(p.d[0] * p.d[0] + p.d[1] * p.d[1] + p.d[2] * p.d[2]);
+    float b = p.r * P.inv_h;
+    p.W = w_of(b, P.ad);
+    float f = dw_of(b, P.ad) * P.inv_h / p.r;
+    for (int c = 0; c < 3; c++) p.g[c] = f * p.d[c];
+    return p;
+}
+
+__device__ __forceinline__ void bg_of(const float *B, const float g[3], float out[3])
+{
+    for (int a = 0; a < 3; a++) out[a] = B[3 * a] * g[0] + B[3 * a + 1] * g[1] + B[3 * a + 2] * g[2];
+}
+
+__device__ __forceinline__ int cell_of(const P3 &P, double x, double y, double z)
+{
+    int cx = min((int)(x * P.inv_cell), P.nc - 1), cy = min((int)(y * P.inv_cell), P.nc - 1),
+        cz = min((int)(z * P.inv_cell), P.nc - 1);
+    return (cz * P.nc + cy) * P.nc + max(cx, 0);
+}
+
+// ---- predictor, cell counts --------------------------------------------------------------------
+
+__global__ void k3_predict(P3 P, Set3 S, Work3 w)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float sp = 0.f;
+    if (i < P.n) {
+        float u[3];
+        for (int c = 0; c < 3; c++) {
+            u[c] = S.u[c][i] + P.half_dt * S.a[c][i];
+            S.u[c][i] = u[c];
+        }
+        double x = wrap(S.x[i] + P.half_dt_d * (double)u[0], P.L);
+        double y = wrap(S.y[i] + P.half_dt_d * (double)u[1], P.L);
+        double z = wrap(S.z[i] + P.half_dt_d * (double)u[2], P.L);
+        if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]))) {
+            atomicOr(w.err, E3_NONFINITE);
+            x = y = z = 0.0;
+        }
+        S.x[i] = x;
+        S.y[i] = y;
+        S.z[i] = z;
+        sp = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        if (!isfinite(sp)) sp = 0.f;
+        int c = cell_of(P, x, y, z);
+        w.key[i] = c;
+        w.slot[i] = atomicAdd(&w.count[c], 1);
+    }
+    for (int o = 16; o > 0; o >>= 1) sp = fmaxf(sp, __shfl_xor_sync(0xFFFFFFFFu, sp, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(w.umax, __float_as_uint(sp));   // sp >= 0: bits order as values
+}
+
+// Exclusive scan of the cell counts by one block of 1024 threads (chunks of 1024 cells).
+__global__ void __launch_bounds__(1024) k3_scan(int ncell, const int *count, int *start)
+{
+    __shared__ int s[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < ncell; base += 1024) {
+        int c = base + threadIdx.x;
+        int v = c < ncell ? count[c] : 0;
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            int t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+            __syncthreads();
+            s[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (c < ncell) start[c] = carry + s[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += s[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) start[ncell] = carry;
+}
+
+__global__ void k3_scatter(P3 P, Work3 w)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P.n) w.perm[w.start[w.key[i]] + w.slot[i]] = i;
+}
+
+// The slots of each cell in particle-ID order (insertion sort; cells hold tens of particles).
+__global__ void k3_cellsort(P3 P, const Set3 S, Work3 w)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= P.ncell) return;
+    int b = w.start[c], e = w.start[c + 1];
+    for (int s = b + 1; s < e; s++) {
+        int v = w.perm[s], iv = S.id[v], t = s - 1;
+        while (t >= b && S.id[w.perm[t]] > iv) {
+            w.perm[t + 1] = w.perm[t];
+            t--;
+        }
+        w.perm[t + 1] = v;
+    }
+}
+
+__global__ void k3_gather(P3 P, const Set3 S, Set3 M, Work3 w)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= P.n) return;
+    int i = w.perm[g];
+    M.x[g] = S.x[i];
+    M.y[g] = S.y[i];
+    M.z[g] = S.z[i];
+    for (int c = 0; c < 3; c++) {
+        M.u[c][g] = S.u[c][i];
+        M.a[c][g] = S.a[c][i];
+    }
+    for (int c = 0; c < 5; c++) M.q[c][g] = S.q[c][i];
+    M.dr[g] = S.dr[i];
+    M.id[g] = S.id[i];
+    w.key[g] = cell_of(P, M.x[g], M.y[g], M.z[g]);
+}
+
+// ---- neighbours, volumes, correction -------------------------------------------------------------
+
+__global__ void k3_neighbours(P3 P, const Set3 M, Work3 w)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    int c = w.key[i];
+    int cx = c % P.nc, cy = (c / P.nc) % P.nc, cz = c / (P.nc * P.nc);
+    double xi = M.x[i], yi = M.y[i], zi = M.z[i];
+    int k = 0;
+    float s = P.W0;
+    bool over = false;
+    for (int oz = -1; oz <= 1; oz++)
+        for (int oy = -1; oy <= 1; oy++)
+            for (int ox = -1; ox <= 1; ox++) {
+                int qx = cx + ox, qy = cy + oy, qz = cz + oz;
+                qx += qx < 0 ? P.nc : (qx >= P.nc ? -P.nc : 0);
+                qy += qy < 0 ? P.nc : (qy >= P.nc ? -P.nc : 0);
+                qz += qz < 0 ? P.nc : (qz >= P.nc ? -P.nc : 0);
+                int q = (qz * P.nc + qy) * P.nc + qx;
+                for (int j = w.start[q]; j < w.start[q + 1]; j++) {
+                    if (j == i) continue;
+                    double dx = min_image(xi - M.x[j], P.L), dy = min_image(yi - M.y[j], P.L),
+                           dz = min_image(zi - M.z[j], P.L);
+                    double r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 < P.R2d) {
+                        if (k < MAXN3) {
+                            w.nbr[(size_t)k * P.n + i] = j;
+                            s += w_of(sqrtf((float)r2) * P.inv_h, P.ad);
+                            k++;
+                        } else {
+                            over = true;
+                        }
+                    }
+                }
+            }
+    if (over) atomicOr(w.err, E3_NBR);
+    w.nnbr[i] = k;
+    w.sumW[i] = s;
+    w.V[i] = 1.f / s;
+}
+
+__global__ void k3_correction(P3 P, const Set3 M, Work3 w)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    float a[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    int m = w.nnbr[i];
+    for (int k = 0; k < m; k++) {
+        int j = w.nbr[(size_t)k * P.n + i];
+        Pair3 p = pair_of(P, M, i, j);
+        float vj = w.V[j];
+        for (int s = 0; s < 3; s++)
+            for (int l = 0; l < 3; l++) a[s][l] += -p.d[s] * vj * p.g[l];
+    }
+    float det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+                a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+    if (!(det > 0.f)) atomicOr(w.err, E3_ALPHA);
+    float id = 1.f / det, *B = w.B + 9 * (size_t)i;
+    B[0] = (a[1][1] * a[2][2] - a[1][2] * a[2][1]) * id;
+    B[1] = (a[0][2] * a[2][1] - a[0][1] * a[2][2]) * id;
+    B[2] = (a[0][1] * a[1][2] - a[0][2] * a[1][1]) * id;
+    B[3] = (a[1][2] * a[2][0] - a[1][0] * a[2][2]) * id;
+    B[4] = (a[0][0] * a[2][2] - a[0][2] * a[2][0]) * id;
+    B[5] = (a[0][2] * a[1][0] - a[0][0] * a[1][2]) * id;
+    B[6] = (a[1][0] * a[2][1] - a[1][1] * a[2][0]) * id;
+    B[7] = (a[0][1] * a[2][0] - a[0][0] * a[2][1]) * id;
+    B[8] = (a[0][0] * a[1][1] - a[0][1] * a[1][0]) * id;
+}
+
+// ---- pass 1: continuity, velocity gradient, Laplacian of Q, Q rate ----------------------------------
+
+__device__ __forceinline__ void full_q(const float *q, float Q[3][3])
+{
+    Q[0][0] = q[0]; Q[0][1] = q[1]; Q[0][2] = q[2];
+    Q[1][0] = q[1]; Q[1][1] = q[3]; Q[1][2] = q[4];
+    Q[2][0] = q[2]; Q[2][1] = q[4]; Q[2][2] = -q[0] - q[3];
+}
+
+// Eq. (24) with Eqs. (2) and (7): m = S + Gamma H, projected onto the symmetric traceless part.
+__device__ void q_rate3(const P3 &P, const float *q, const float D[3][3], const float *lq, float *m5)
+{
+    float Q[3][3], LQ[3][3], M[3][3], E[3][3], Om[3][3];
+    full_q(q, Q);
+    full_q(lq, LQ);
+    float QD = 0.f;
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            E[a][b] = 0.5f * (D[a][b] + D[b][a]);
+            Om[a][b] = 0.5f * (D[a][b] - D[b][a]);
+            M[a][b] = Q[a][b] + (a == b ? P.c_shift : 0.f);
+            QD += Q[a][b] * D[a][b];
+        }
+    float trQ2 = 0.f, Q2[3][3];
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            Q2[a][b] = Q[a][0] * Q[0][b] + Q[a][1] * Q[1][b] + Q[a][2] * Q[2][b];
+        }
+    trQ2 = Q2[0][0] + Q2[1][1] + Q2[2][2];
+    float m[3][3];
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            // (lambda E + Omega) M + M (lambda E - Omega) - 2 lambda M (Q : grad u)
+            float s = 0.f;
+            for (int c = 0; c < 3; c++)
+                s += (P.lambda * E[a][c] + Om[a][c]) * M[c][b] + M[a][c] * (P.lambda * E[c][b] - Om[c][b]);
+            s -= 2.f * P.lambda * M[a][b] * QD;
+            float H = -P.A * Q[a][b] + P.B * (Q2[a][b] - (a == b ? trQ2 / 3.f : 0.f)) - P.C * Q[a][b] * trQ2 +
+                      P.K * LQ[a][b];
+            m[a][b] = s + P.Gamma * H;
+        }
+    float tr = m[0][0] + m[1][1] + m[2][2];
+    m5[0] = m[0][0] - tr / 3.f;
+    m5[1] = 0.5f * (m[0][1] + m[1][0]);
+    m5[2] = 0.5f * (m[0][2] + m[2][0]);
+    m5[3] = m[1][1] - tr / 3.f;
+    m5[4] = 0.5f * (m[1][2] + m[2][1]);
+}
+
+__global__ void k3_pass1(P3 P, const Set3 M, Work3 w)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const float *B = w.B + 9 * (size_t)i;
+    float ui[3] = {M.u[0][i], M.u[1][i], M.u[2][i]}, qi[5];
+    for (int c = 0; c < 5; c++) qi[c] = M.q[c][i];
+    float rhs[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, lap[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, kc = 0.f;
+    int m = w.nnbr[i];
+    for (int k = 0; k < m; k++) {
+        int j = w.nbr[(size_t)k * P.n + i];
+        Pair3 p = pair_of(P, M, i, j);
+        float bg[3], vj = w.V[j];
+        bg_of(B, p.g, bg);
+        float du[3] = {ui[0] - M.u[0][j], ui[1] - M.u[1][j], ui[2] - M.u[2][j]};
+        kc += vj * (du[0] * bg[0] + du[1] * bg[1] + du[2] * bg[2]);
+        for (int c = 0; c < 3; c++)
+            for (int l = 0; l < 3; l++) rhs[c][l] += vj * (-du[c]) * p.g[l];
+        float f = vj * (p.d[0] * bg[0] + p.d[1] * bg[1] + p.d[2] * bg[2]) / (p.r * p.r);
+        for (int c = 0; c < 5; c++) lap[c] += f * (qi[c] - M.q[c][j]);
+    }
+    float D[3][3];
+    for (int c = 0; c < 3; c++)
+        for (int b = 0; b < 3; b++) D[c][b] = rhs[c][0] * B[b] + rhs[c][1] * B[3 + b] + rhs[c][2] * B[6 + b];
+    for (int c = 0; c < 5; c++) lap[c] *= 2.f;
+    float k_i = P.rho0 * (1.f + M.dr[i]) * kc;
+    w.k[i] = k_i;
+    w.dh[i] = M.dr[i] + P.half_dt * k_i / P.rho0;
+    float m5[5];
+    q_rate3(P, qi, D, lap, m5);
+    for (int c = 0; c < 5; c++) {
+        w.m[(size_t)c * P.n + i] = m5[c];
+        w.lap[(size_t)c * P.n + i] = lap[c];
+        w.qn[(size_t)c * P.n + i] = qi[c] + P.dt * m5[c];
+    }
+    for (int c = 0; c < 9; c++) w.gu[(size_t)c * P.n + i] = D[c / 3][c % 3];
+}
+
+// ---- pass 2: density filter, equation of state ------------------------------------------------------
+
+__global__ void k3_pass2(P3 P, const Set3 M, Work3 w)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    // Eq. (28) on the deviations (rho0 factors out of the filter)
+    float di = w.dh[i], num = 0.f, den = P.W0;
+    int m = w.nnbr[i];
+    for (int k = 0; k < m; k++) {
+        int j = w.nbr[(size_t)k * P.n + i];
+        Pair3 p = pair_of(P, M, i, j);
+        num += (di - w.dh[j]) * p.W;
+        den += p.W;
+    }
+    float dhat = di - P.beta * num / den;
+    w.dhat[i] = dhat;
+    // Eq. (26): (rho / rho0)^gamma - 1 = expm1(gamma log1p(delta)), accurate for small delta
+    float c0 = fmaxf(10.f * __uint_as_float(*w.umax), P.c0_min);
+    w.p[i] = P.rho0 * c0 * c0 / P.gamma_eos * expm1f(P.gamma_eos * log1pf(dhat));
+}
+
+// ---- pass 3: momentum, artificial displacement, corrector --------------------------------------------
+
+__global__ void k3_pass3(P3 P, const Set3 M, Set3 S, Work3 w)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const float *B = w.B + 9 * (size_t)i;
+    float ri = P.rho0 * (1.f + w.dhat[i]), pri = w.p[i] / (ri * ri);
+    float ui[3] = {M.u[0][i], M.u[1][i], M.u[2][i]}, qi[5];
+    for (int c = 0; c < 5; c++) qi[c] = w.qn[(size_t)c * P.n + i];
+    float Qi[3][3];
+    full_q(qi, Qi);
+    float fp[3] = {0.f, 0.f, 0.f}, fv[3] = {0.f, 0.f, 0.f}, dq[3] = {0.f, 0.f, 0.f};
+    float su[3] = {0.f, 0.f, 0.f}, sw = P.W0, sr = 0.f, sd[3] = {0.f, 0.f, 0.f};
+    int m = w.nnbr[i];
+    for (int k = 0; k < m; k++) {
+        int j = w.nbr[(size_t)k * P.n + i];
+        Pair3 p = pair_of(P, M, i, j);
+        float bg[3], vj = w.V[j];
+        bg_of(B, p.g, bg);
+        float rj = P.rho0 * (1.f + w.dhat[j]);
+        float cp = pri + w.p[j] / (rj * rj);
+        float du[3] = {ui[0] - M.u[0][j], ui[1] - M.u[1][j], ui[2] - M.u[2][j]};
+        float ud = du[0] * p.d[0] + du[1] * p.d[1] + du[2] * p.d[2];
+        float r2 = p.r * p.r;
+        float qj[5];
+        for (int c = 0; c < 5; c++) qj[c] = w.qn[(size_t)c * P.n + j];
+        float Qj[3][3];
+        full_q(qj, Qj);
+        for (int c = 0; c < 3; c++) {
+            fp[c] += vj * cp * bg[c];
+            fv[c] += vj * ud / r2 * bg[c];
+            dq[c] += vj * ((Qj[c][0] - Qi[c][0]) * bg[0] + (Qj[c][1] - Qi[c][1]) * bg[1] + (Qj[c][2] - Qi[c][2]) * bg[2]);
+            su[c] += du[c] * p.W;
+            sd[c] += p.d[c] / (r2 * p.r);
+        }
+        sw += p.W;
+        sr += p.r;
+    }
+    float an[3], apd[3] = {0.f, 0.f, 0.f};
+    for (int c = 0; c < 3; c++)
+        an[c] = -ri * fp[c] + 10.f * P.nu * P.rho0 / ri * fv[c] - P.zeta / ri * dq[c];
+    if (P.apd) {
+        float uv = sqrtf(su[0] * su[0] + su[1] * su[1] + su[2] * su[2]) / sw;
+        float r0 = m > 0 ? sr / (float)m : 0.f;
+        for (int c = 0; c < 3; c++) apd[c] = sd[c] * r0 * r0 * uv * P.dt;
+    }
+    // corrector into S (the new cell order)
+    float un[3];
+    for (int c = 0; c < 3; c++) {
+        un[c] = ui[c] + P.half_dt * an[c];
+        S.u[c][i] = un[c];
+        S.a[c][i] = an[c];
+    }
+    double x = wrap(M.x[i] + P.half_dt_d * (double)un[0] + (double)apd[0], P.L);
+    double y = wrap(M.y[i] + P.half_dt_d * (double)un[1] + (double)apd[1], P.L);
+    double z = wrap(M.z[i] + P.half_dt_d * (double)un[2] + (double)apd[2], P.L);
+    float dr = w.dhat[i] + P.half_dt * w.k[i] / P.rho0;
+    bool ok = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(un[0]) && isfinite(un[1]) && isfinite(un[2]) &&
+              isfinite(dr);
+    for (int c = 0; c < 5; c++) ok = ok && isfinite(qi[c]);
+    if (!ok) {
+        atomicOr(w.err, E3_NONFINITE);
+        x = y = z = 0.0;
+    }
+    S.x[i] = x;
+    S.y[i] = y;
+    S.z[i] = z;
+    S.dr[i] = dr;
+    for (int c = 0; c < 5; c++) S.q[c][i] = qi[c];
+    S.id[i] = M.id[i];
+}
+
+// dst[id[g] * nc + c] = planes[c][g] (ID order, interleaved, FP64)
+__global__ void k3_to_id(int n, int ncomp, const float *const *planes, const int *id, double *dst)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    for (int c = 0; c < ncomp; c++) dst[(size_t)id[g] * ncomp + c] = (double)planes[c][g];
+}
+
+__global__ void k3_pos_to_id(int n, const double *x, const double *y, const double *z, const int *id, double *dst)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    dst[3 * (size_t)id[g]] = x[g];
+    dst[3 * (size_t)id[g] + 1] = y[g];
+    dst[3 * (size_t)id[g] + 2] = z[g];
+}
+
+__global__ void k3_int_to_id(int n, const int *v, const int *id, double *dst)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) dst[id[g]] = (double)v[g];
+}
+
+inline unsigned nb3(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+struct ann3_ctx {
+    ann3_params prm;
+    P3 P;
+    Set3 S, M;
+    Work3 w;
+    std::vector<void *> allocs;
+    cudaStream_t s = nullptr;
+    bool have = false;
+    int64_t steps = 0;
+    std::string last_err;
+    double *tmp = nullptr;         // device staging for ann3_get_field (9n doubles)
+    const float **planes = nullptr;   // device array of plane pointers
+};
+
+namespace {
+
+template <typename T>
+cudaError_t alloc3(ann3_ctx *c, T *&p, size_t count)
+{
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(T));
+    if (e) return e;
+    c->allocs.push_back(v);
+    p = static_cast<T *>(v);
+    return cudaMemsetAsync(v, 0, std::max<size_t>(count, 1) * sizeof(T), c->s);
+}
+
+cudaError_t alloc_set(ann3_ctx *c, Set3 &S, size_t n)
+{
+    cudaError_t e = alloc3(c, S.x, n);
+    if (!e) e = alloc3(c, S.y, n);
+    if (!e) e = alloc3(c, S.z, n);
+    for (int k = 0; k < 3 && !e; k++) e = alloc3(c, S.u[k], n);
+    for (int k = 0; k < 3 && !e; k++) e = alloc3(c, S.a[k], n);
+    for (int k = 0; k < 5 && !e; k++) e = alloc3(c, S.q[k], n);
+    if (!e) e = alloc3(c, S.dr, n);
+    if (!e) e = alloc3(c, S.id, n);
+    return e;
+}
+
+int fail3(ann3_ctx *c, int code, const std::string &m)
+{
+    if (c) c->last_err = m;
+    return code;
+}
+
+int cuda3(ann3_ctx *c, cudaError_t e, const char *where)
+{
+    return fail3(c, e == cudaErrorMemoryAllocation ? ANN_ERR_OOM : ANN_ERR_CUDA, std::string(where) + ": " +
+                                                                                  cudaGetErrorString(e));
+}
+
+// The first cause wins: truncated neighbour lists can make alpha singular and the state non-finite.
+int status_of_bits(uint32_t b)
+{
+    if (b & E3_NBR) return ANN_ERR_NBR_OVERFLOW;
+    if (b & E3_ALPHA) return ANN_ERR_SINGULAR_ALPHA;
+    if (b & E3_NONFINITE) return ANN_ERR_NONFINITE;
+    return ANN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ann3_default_params(ann3_params *p)
+{
+    if (!p) return ANN_ERR_INVALID_ARG;
+    std::memset(p, 0, sizeof *p);
+    p->n = 32 * 32 * 32;
+    p->L = 1.0;
+    p->h = 1.3 / 32;
+    p->dt = 1e-4;
+    p->rho0 = 1.0;
+    p->eta = 1.0;
+    p->Gamma = 0.34;
+    p->lambda_ = 0.7;
+    p->A = 0.0;
+    p->B = 0.0;
+    p->C = 1.0;
+    p->K = 0.04;
+    p->zeta = 0.05;
+    p->gamma_eos = 7.0;
+    p->beta = 1.0;
+    p->c0_min = 0.0;
+    p->c_shift = 1.0 / 3.0;
+    p->apd = 1;
+    return ANN_OK;
+}
+
+int ann3_create(const ann3_params *p, ann3_ctx **out)
+{
+    if (!p || !out) return ANN_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (p->n < 1 || p->n > (1ll << 26) || !(p->L > 0.0) || !(p->h > 0.0) || !(p->dt > 0.0) || !(p->rho0 > 0.0) ||
+        !(p->gamma_eos > 0.0))
+        return ANN_ERR_INVALID_ARG;
+    int nc = (int)std::floor(p->L / (3.0 * p->h));
+    if (nc < 3 || (int64_t)nc * nc * nc > (1ll << 28)) return ANN_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDeviceCount(&dev) != cudaSuccess || dev == 0) return ANN_ERR_NOT_AVAILABLE;
+    ann3_ctx *c = new (std::nothrow) ann3_ctx();
+    if (!c) return ANN_ERR_OOM;
+    c->prm = *p;
+    P3 &P = c->P;
+    P.n = (int)p->n;
+    P.nc = nc;
+    P.ncell = nc * nc * nc;
+    P.L = p->L;
+    P.inv_cell = nc / p->L;
+    P.R2d = 9.0 * p->h * p->h;
+    P.half_dt_d = 0.5 * p->dt;
+    P.h = (float)p->h;
+    P.inv_h = (float)(1.0 / p->h);
+    P.ad = (float)(3.0 / (359.0 * 3.14159265358979323846 * p->h * p->h * p->h));   // Eq. (18), d = 3
+    P.W0 = P.ad * 66.f;                                           // W(0) = a_d (3^5 - 6 2^5 + 15)
+    P.dt = (float)p->dt;
+    P.half_dt = (float)(0.5 * p->dt);
+    P.rho0 = (float)p->rho0;
+    P.nu = (float)(p->eta / p->rho0);
+    P.Gamma = (float)p->Gamma;
+    P.lambda = (float)p->lambda_;
+    P.A = (float)p->A;
+    P.B = (float)p->B;
+    P.C = (float)p->C;
+    P.K = (float)p->K;
+    P.zeta = (float)p->zeta;
+    P.gamma_eos = (float)p->gamma_eos;
+    P.beta = (float)p->beta;
+    P.c0_min = (float)p->c0_min;
+    P.c_shift = (float)p->c_shift;
+    P.apd = p->apd;
+    size_t n = (size_t)p->n;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking);
+    if (!e) e = alloc_set(c, c->S, n);
+    if (!e) e = alloc_set(c, c->M, n);
+    Work3 &w = c->w;
+    if (!e) e = alloc3(c, w.key, n);
+    if (!e) e = alloc3(c, w.slot, n);
+    if (!e) e = alloc3(c, w.perm, n);
+    if (!e) e = alloc3(c, w.count, (size_t)P.ncell);
+    if (!e) e = alloc3(c, w.start, (size_t)P.ncell + 1);
+    if (!e) e = alloc3(c, w.nbr, (size_t)MAXN3 * n);
+    if (!e) e = alloc3(c, w.nnbr, n);
+    if (!e) e = alloc3(c, w.sumW, n);
+    if (!e) e = alloc3(c, w.V, n);
+    if (!e) e = alloc3(c, w.B, 9 * n);
+    if (!e) e = alloc3(c, w.k, n);
+    if (!e) e = alloc3(c, w.dh, n);
+    if (!e) e = alloc3(c, w.dhat, n);
+    if (!e) e = alloc3(c, w.p, n);
+    if (!e) e = alloc3(c, w.qn, 5 * n);
+    if (!e) e = alloc3(c, w.an, 3 * n);
+    if (!e) e = alloc3(c, w.gu, 9 * n);
+    if (!e) e = alloc3(c, w.lap, 5 * n);
+    if (!e) e = alloc3(c, w.m, 5 * n);
+    if (!e) e = alloc3(c, w.umax, 1);
+    if (!e) e = alloc3(c, w.err, 1);
+    if (!e) e = alloc3(c, c->tmp, 9 * n);
+    if (!e) e = alloc3(c, c->planes, 9);
+    if (!e) e = cudaStreamSynchronize(c->s);
+    if (e) {
+        int code = e == cudaErrorMemoryAllocation ? ANN_ERR_OOM : ANN_ERR_CUDA;
+        ann3_destroy(c);
+        return code;
+    }
+    *out = c;
+    return ANN_OK;
+}
+
+void ann3_destroy(ann3_ctx *c)
+{
+    if (!c) return;
+    if (c->s) cudaStreamSynchronize(c->s);
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->s) cudaStreamDestroy(c->s);
+    delete c;
+}
+
+int ann3_set_particles(ann3_ctx *c, int64_t n, const double *x, const double *y, const double *z, const double *u,
+                       const double *q, const double *rho)
+{
+    if (!c) return ANN_ERR_INVALID_ARG;
+    if (n != c->prm.n || !x || !y || !z || !u || !q) return fail3(c, ANN_ERR_INVALID_ARG, "bad arguments");
+    const double L = c->prm.L;
+    for (int64_t i = 0; i < n; i++) {
+        const double r[3] = {x[i], y[i], z[i]};
+        for (double v : r)
+            if (!(v >= 0.0 && v < L)) return fail3(c, ANN_ERR_INVALID_ARG, "position outside [0, L)");
+        for (int k = 0; k < 3; k++)
+            if (!std::isfinite(u[3 * i + k])) return fail3(c, ANN_ERR_INVALID_ARG, "non-finite velocity");
+        for (int k = 0; k < 5; k++)
+            if (!std::isfinite(q[5 * i + k])) return fail3(c, ANN_ERR_INVALID_ARG, "non-finite Q");
+        if (rho && !(std::isfinite(rho[i]) && rho[i] > 0.0)) return fail3(c, ANN_ERR_INVALID_ARG, "bad density");
+    }
+    size_t nn = (size_t)n;
+    std::vector<float> f(nn);
+    std::vector<int> id(nn);
+    cudaError_t e = cudaMemcpyAsync(c->S.x, x, nn * 8, cudaMemcpyHostToDevice, c->s);
+    if (!e) e = cudaMemcpyAsync(c->S.y, y, nn * 8, cudaMemcpyHostToDevice, c->s);
+    if (!e) e = cudaMemcpyAsync(c->S.z, z, nn * 8, cudaMemcpyHostToDevice, c->s);
+    auto plane = [&](float *dst, const double *src, int stride, int comp, double dflt) -> cudaError_t {
+        for (size_t i = 0; i < nn; i++) f[i] = (float)(src ? src[i * stride + comp] : dflt);
+        if (dst == c->S.dr)   // the deviation, taken in FP64
+            for (size_t i = 0; i < nn; i++) f[i] = (float)(src ? src[i] / c->prm.rho0 - 1.0 : 0.0);
+        cudaError_t r = cudaMemcpyAsync(dst, f.data(), nn * 4, cudaMemcpyHostToDevice, c->s);
+        if (!r) r = cudaStreamSynchronize(c->s);   // f is reused
+        return r;
+    };
+    for (int k = 0; k < 3 && !e; k++) e = plane(c->S.u[k], u, 3, k, 0.0);
+    for (int k = 0; k < 5 && !e; k++) e = plane(c->S.q[k], q, 5, k, 0.0);
+    if (!e) e = plane(c->S.dr, rho, 1, 0, c->prm.rho0);
+    for (int k = 0; k < 3 && !e; k++) e = cudaMemsetAsync(c->S.a[k], 0, nn * 4, c->s);
+    for (size_t i = 0; i < nn; i++) id[i] = (int)i;
+    if (!e) e = cudaMemcpyAsync(c->S.id, id.data(), nn * 4, cudaMemcpyHostToDevice, c->s);
+    if (!e) e = cudaMemsetAsync(c->w.err, 0, 4, c->s);
+    if (!e) e = cudaStreamSynchronize(c->s);
+    if (e) return cuda3(c, e, "ann3_set_particles");
+    c->have = true;
+    c->steps = 0;
+    return ANN_OK;
+}
+
+int ann3_step(ann3_ctx *c, int64_t nsteps)
+{
+    if (!c || nsteps < 0) return ANN_ERR_INVALID_ARG;
+    if (!c->have) return fail3(c, ANN_ERR_STATE, "ann3_step before ann3_set_particles");
+    const P3 &P = c->P;
+    cudaStream_t s = c->s;
+    const unsigned g = nb3((size_t)P.n);
+    cudaError_t e = cudaSuccess;
+    for (int64_t t = 0; t < nsteps && !e; t++) {
+        e = cudaMemsetAsync(c->w.count, 0, sizeof(int) * (size_t)P.ncell, s);
+        if (!e) e = cudaMemsetAsync(c->w.umax, 0, 4, s);
+        if (e) break;
+        k3_predict<<<g, 256, 0, s>>>(P, c->S, c->w);
+        k3_scan<<<1, 1024, 0, s>>>(P.ncell, c->w.count, c->w.start);
+        k3_scatter<<<g, 256, 0, s>>>(P, c->w);
+        k3_cellsort<<<nb3((size_t)P.ncell), 256, 0, s>>>(P, c->S, c->w);
+        k3_gather<<<g, 256, 0, s>>>(P, c->S, c->M, c->w);
+        k3_neighbours<<<g, 256, 0, s>>>(P, c->M, c->w);
+        k3_correction<<<g, 256, 0, s>>>(P, c->M, c->w);
+        k3_pass1<<<g, 256, 0, s>>>(P, c->M, c->w);
+        k3_pass2<<<g, 256, 0, s>>>(P, c->M, c->w);
+        k3_pass3<<<g, 256, 0, s>>>(P, c->M, c->S, c->w);
+        e = cudaGetLastError();
+    }
+    uint32_t bits = 0;
+    if (!e) e = cudaMemcpyAsync(&bits, c->w.err, 4, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda3(c, e, "ann3_step");
+    c->steps += nsteps;
+    int st = status_of_bits(bits);
+    if (st) return fail3(c, st, "ann3_step: device error bits " + std::to_string(bits));
+    return ANN_OK;
+}
+
+int ann3_get_field(ann3_ctx *c, int32_t field, double *dst)
+{
+    if (!c || !dst || field < 0 || field >= ANN3_FIELD_COUNT) return ANN_ERR_INVALID_ARG;
+    if (!c->have) return fail3(c, ANN_ERR_STATE, "no particles");
+    const int n = c->P.n;
+    const Work3 &w = c->w;
+    const float *pl[9];
+    int nc = 0;
+    cudaError_t e = cudaSuccess;
+    switch (field) {
+    case ANN3_FIELD_POS:
+        k3_pos_to_id<<<nb3(n), 256, 0, c->s>>>(n, c->S.x, c->S.y, c->S.z, c->S.id, c->tmp);
+        nc = -3;
+        break;
+    case ANN3_FIELD_NNBR:
+        k3_int_to_id<<<nb3(n), 256, 0, c->s>>>(n, w.nnbr, c->S.id, c->tmp);
+        nc = -1;
+        break;
+    case ANN3_FIELD_U: for (int k = 0; k < 3; k++) pl[k] = c->S.u[k]; nc = 3; break;
+    case ANN3_FIELD_Q: for (int k = 0; k < 5; k++) pl[k] = c->S.q[k]; nc = 5; break;
+    case ANN3_FIELD_RHO: pl[0] = c->S.dr; nc = 1; break;
+    case ANN3_FIELD_A: for (int k = 0; k < 3; k++) pl[k] = c->S.a[k]; nc = 3; break;
+    case ANN3_FIELD_SUMW: pl[0] = w.sumW; nc = 1; break;
+    case ANN3_FIELD_GRADU: for (int k = 0; k < 9; k++) pl[k] = w.gu + (size_t)k * n; nc = 9; break;
+    case ANN3_FIELD_LAPQ: for (int k = 0; k < 5; k++) pl[k] = w.lap + (size_t)k * n; nc = 5; break;
+    case ANN3_FIELD_QRATE: for (int k = 0; k < 5; k++) pl[k] = w.m + (size_t)k * n; nc = 5; break;
+    case ANN3_FIELD_P: pl[0] = w.p; nc = 1; break;
+    default: return ANN_ERR_INVALID_ARG;
+    }
+    int comps = nc < 0 ? -nc : nc;
+    if (nc > 0) {
+        e = cudaMemcpyAsync(c->planes, pl, sizeof(float *) * (size_t)nc, cudaMemcpyHostToDevice, c->s);
+        if (!e) k3_to_id<<<nb3(n), 256, 0, c->s>>>(n, nc, c->planes, c->S.id, c->tmp);
+    }
+    if (!e) e = cudaGetLastError();
+    if (!e) e = cudaMemcpyAsync(dst, c->tmp, sizeof(double) * (size_t)n * comps, cudaMemcpyDeviceToHost, c->s);
+    if (!e) e = cudaStreamSynchronize(c->s);
+    if (e) return cuda3(c, e, "ann3_get_field");
+    if (field == ANN3_FIELD_RHO)
+        for (int i = 0; i < n; i++) dst[i] = c->prm.rho0 * (1.0 + dst[i]);
+    return ANN_OK;
+}
+
+int ann3_get_status(ann3_ctx *c, int64_t *steps, uint32_t *error_bits)
+{
+    if (!c) return ANN_ERR_INVALID_ARG;
+    uint32_t b = 0;
+    cudaError_t e = cudaMemcpyAsync(&b, c->w.err, 4, cudaMemcpyDeviceToHost, c->s);
+    if (!e) e = cudaStreamSynchronize(c->s);
+    if (e) return cuda3(c, e, "ann3_get_status");
+    if (steps) *steps = c->steps;
+    if (error_bits) *error_bits = b;
+    return ANN_OK;
+}
+
+const char *ann3_last_error(ann3_ctx *c) { return c ? c->last_err.c_str() : ""; }
+
+}  // extern "C"

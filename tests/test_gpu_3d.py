@@ -1,0 +1,165 @@
+"""The three-dimensional step through the C-ABI against the FP64 3D oracle.
+
+Parity measure as in 2D: the normwise relative error of a whole field (all components together);
+positions through the displacement from the start.  FP32 pair arithmetic over ~250 neighbours per
+particle, FP64 positions and differences: the tests allow 2e-5 on the state after a few steps and
+on the intermediates of the last step, and require identical neighbour counts."""
+import numpy as np
+import pytest
+
+import sph_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_08919_gb300 import binding, build
+
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle3d
+
+    return oracle3d
+
+
+def relerr(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _params(nx, **kw):
+    p = dict(L=1.0, h=1.3 / nx, dt=2e-4, rho0=1.0, eta=0.2, Gamma=0.34, lam=0.7, A=0.05, B=0.3, C=1.0,
+             K=0.04, zeta=0.3, gamma_eos=7.0, beta=1.0, c0_min=0.5, c_shift=1.0 / 3.0, apd=1)
+    p.update(kw)
+    return p
+
+
+def _gpu_params(B, p, n):
+    q = {("lambda_" if k == "lam" else k): v for k, v in p.items()}
+    return B.ann3_default_params(n=n, **q)
+
+
+def _run_both(B, O, ic, p, steps):
+    n = ic["n"]
+    st = {"x": ic["x"], "y": ic["y"], "z": ic["z"], "u": ic["u"], "q": ic["q"], "rho": ic["rho"]}
+    want, rec = O.step(O.make_params(**p), st, steps, record=True)
+    ctx = B.ann3_create(_gpu_params(B, p, n))
+    try:
+        B.ann3_set_particles(ctx, ic["x"], ic["y"], ic["z"], ic["u"], ic["q"], ic["rho"])
+        B.ann3_step(ctx, steps)
+        got = {k: B.ann3_get_field(ctx, k, n) for k in B.FIELDS3}
+    finally:
+        B.ann3_destroy(ctx)
+    return got, want, rec
+
+
+def _disp(pos, x0, L=1.0):
+    d = pos - x0
+    return d - L * np.round(d / L)
+
+
+@pytest.mark.parametrize("kind", ["lattice", "random"])
+def test_steps_match_the_oracle(B, O, kind):
+    nx = 12
+    if kind == "lattice":
+        ic = si.jittered_lattice3(nx, seed=11, jitter=0.2, u_scale=0.2)
+    else:   # uniform random positions: ragged cell occupancy and neighbour counts
+        ic = si.jittered_lattice3(nx, seed=12, jitter=0.0, u_scale=0.2)
+        r = si.uniform53(99, 3 * ic["n"]).reshape(3, -1)
+        ic["x"], ic["y"], ic["z"] = r[0], r[1], r[2]
+    p = _params(nx)
+    got, want, rec = _run_both(B, O, ic, p, 3)
+    x0 = np.stack([ic["x"], ic["y"], ic["z"]], axis=1)
+    wpos = np.stack([want["x"], want["y"], want["z"]], axis=1)
+    errs = {
+        "disp": relerr(_disp(got["POS"], x0), _disp(wpos, x0)),
+        "u": relerr(got["U"], want["u"]),
+        "q": relerr(got["Q"], want["q"]),
+        "rho-1": relerr(got["RHO"][:, 0] - 1.0, want["rho"] - 1.0),
+        "a": relerr(got["A"], want["a"]),
+        "sumW": relerr(got["SUMW"][:, 0], rec["sumW"]),
+        "gradu": relerr(got["GRADU"], rec["gradu"]),
+        "lapQ": relerr(got["LAPQ"], rec["lapQ"]),
+        "qrate": relerr(got["QRATE"], rec["qrate"]),
+        "p": relerr(got["P"][:, 0], rec["p"]),
+    }
+    print(kind, {k: f"{v:.2e}" for k, v in errs.items()})
+    assert np.array_equal(got["NNBR"][:, 0].astype(np.int64), rec["nnbr"])
+    assert max(errs.values()) < 2e-5, errs
+
+
+def test_uniform_state_at_64_cubed(B, O):
+    """A property that holds at any size: uniform Q at rest relaxes by the bulk term alone and
+    nothing moves (262,144 particles, 5 steps)."""
+    nx = 64
+    ic = si.jittered_lattice3(nx, seed=13, jitter=0.2)
+    n = ic["n"]
+    q5 = np.array([0.2, -0.1, 0.05, -0.15, 0.08])
+    p = _params(nx, dt=1e-4)
+    ctx = B.ann3_create(_gpu_params(B, p, n))
+    try:
+        B.ann3_set_particles(ctx, ic["x"], ic["y"], ic["z"], np.zeros((n, 3)), np.tile(q5, (n, 1)), None)
+        B.ann3_step(ctx, 5)
+        q = B.ann3_get_field(ctx, "Q", n)
+        u = B.ann3_get_field(ctx, "U", n)
+        pos = B.ann3_get_field(ctx, "POS", n)
+        nn = B.ann3_get_field(ctx, "NNBR", n)
+    finally:
+        B.ann3_destroy(ctx)
+    st = {"x": ic["x"][:1728], "y": ic["y"][:1728], "z": ic["z"][:1728], "u": np.zeros((1728, 3)),
+          "q": np.tile(q5, (1728, 1)), "rho": np.ones(1728)}
+    qq = q5.copy()
+    P = O.make_params(**p)
+    for _ in range(5):   # the bulk relaxation alone, in FP64
+        m, _ = O.q_rate(P, qq, np.zeros((3, 3)), np.zeros(5))
+        qq = qq + p["dt"] * m
+    assert np.abs(q - qq).max() < 1e-6
+    assert np.abs(u).max() < 1e-6
+    x0 = np.stack([ic["x"], ic["y"], ic["z"]], axis=1)
+    assert np.abs(_disp(pos, x0)).max() < 1e-9
+    assert 200 < nn.mean() < 300
+
+
+def test_errors_are_reported(B):
+    nx = 12
+    p = _params(nx)
+    ic = si.jittered_lattice3(nx, seed=1)
+    n = ic["n"]
+    with pytest.raises(B.AnnError):   # fewer than 3 cells per side
+        B.ann3_create(_gpu_params(B, _params(8), 512))
+    ctx = B.ann3_create(_gpu_params(B, p, n))
+    try:
+        with pytest.raises(B.AnnError):
+            B.ann3_step(ctx, 1)   # no particles yet
+        bad = ic["x"].copy()
+        bad[5] = 1.0
+        with pytest.raises(B.AnnError):
+            B.ann3_set_particles(ctx, bad, ic["y"], ic["z"], ic["u"], ic["q"])
+        with pytest.raises(B.AnnError):
+            B.ann3_set_particles(ctx, ic["x"][:-1], ic["y"][:-1], ic["z"][:-1], ic["u"][:-1], ic["q"][:-1])
+        B.ann3_set_particles(ctx, ic["x"], ic["y"], ic["z"], ic["u"], ic["q"])
+        B.ann3_step(ctx, 2)
+        assert B.ann3_get_status(ctx) == (2, 0)
+    finally:
+        B.ann3_destroy(ctx)
+    # more neighbours than the lists hold: reported, not written past the end
+    nx = 16
+    p = _params(nx, h=1.6 / nx)
+    ic = si.jittered_lattice3(nx, seed=2)
+    ctx = B.ann3_create(_gpu_params(B, p, ic["n"]))
+    try:
+        B.ann3_set_particles(ctx, ic["x"], ic["y"], ic["z"], ic["u"], ic["q"])
+        with pytest.raises(B.AnnError) as e:
+            B.ann3_step(ctx, 1)
+        assert e.value.status == -5
+    finally:
+        B.ann3_destroy(ctx)
