@@ -532,6 +532,57 @@ def _sg_eval(B, sg, ctx, n, pairs, ys, parts=False):
             [float(v) for v in np.mean(pu, axis=0)])
 
 
+NX3 = 96   # the 3D variant's measured size: 96^3 = 884,736 particles
+
+
+def _params3(B, nx):
+    return B.ann3_default_params(n=nx ** 3, h=1.3 / nx, dt=1e-4, eta=0.2, A=0.05, B=0.3, zeta=0.3, c0_min=0.5)
+
+
+def three_d_bench(B, nx=NX3, warmup=3, steps=20):
+    """The 3D variant on an nx^3 jittered cubic lattice with random directors and small random
+    velocities: wall time of `steps` steps in one call (one synchronisation), after `warmup`."""
+    import numpy as np
+
+    import sph_inputs as si
+
+    n = nx ** 3
+    ic = si.jittered_lattice3(nx, seed=5, jitter=0.1, u_scale=0.02)
+    ctx = B.ann3_create(_params3(B, nx))
+    try:
+        B.ann3_set_particles(ctx, ic["x"], ic["y"], ic["z"], ic["u"], ic["q"], ic["rho"])
+        B.ann3_step(ctx, warmup)
+        t0 = time.perf_counter()
+        B.ann3_step(ctx, steps)
+        dt = time.perf_counter() - t0
+        nn = B.ann3_get_field(ctx, "NNBR", n)
+    finally:
+        B.ann3_destroy(ctx)
+    ms = 1e3 * dt / steps
+    return {"workload": f"sph_active_nematic_3d_{nx}cubed", "particles": n, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms, "value": n / (ms * 1e-3), "unit": "particle-steps/s",
+            "pair_interactions_per_s": float(nn.sum()) / (ms * 1e-3), "nbr_mean": float(nn.mean()),
+            "clock": "wall around one synchronised call of `steps` steps"}
+
+
+def oracle3d_baseline(nx=24, steps=1):
+    """The FP64 3D oracle, as it stands, on the host cores: `steps` whole steps of a 24^3 lattice (the
+    same set-up as three_d_bench, smaller: the per-particle work is the same)."""
+    import oracle
+    import sph_inputs as si
+    from oracle import oracle3d as O3
+
+    ic = si.jittered_lattice3(nx, seed=5, jitter=0.1, u_scale=0.02)
+    P = O3.make_params(h=1.3 / nx, dt=1e-4, eta=0.2, A=0.05, B=0.3, zeta=0.3, c0_min=0.5)
+    st = {"x": ic["x"], "y": ic["y"], "z": ic["z"], "u": ic["u"], "q": ic["q"], "rho": ic["rho"]}
+    t0 = time.perf_counter()
+    O3.step(P, st, steps)
+    dt = time.perf_counter() - t0
+    n = nx ** 3
+    return {"value": n * steps / dt, "unit": "particle-steps/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{steps} whole FP64 3D oracle step(s) of a {nx}^3 lattice, {dt:.1f} s"}
+
+
 def surrogate_cycles(cycles):
     """Cycles of one recorded plain step and one jump on the 1024^2 workload with the library's
     He-initialised weights; prints the mean wall time of a cycle (synchronised calls)."""
@@ -819,11 +870,15 @@ def run_ours(args):
         line["ensemble"] = ensemble_bench(B)
     if ws == 1 and not args.no_surrogate:
         line["surrogate"] = surrogate_bench(B)
+    if ws == 1 and not args.no_3d:
+        line["three_d"] = three_d_bench(B, nx=args.nx3)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(NX)
         ms, cores = oracle_grid_ms(NX, DIAG_M)
         line["diagnostics"]["oracle_grid_ms"] = ms
         line["diagnostics"]["oracle_cores"] = cores
+        if "three_d" in line:
+            line["three_d"]["cpu_baseline"] = oracle3d_baseline()
     print(json.dumps(line))
     if dist:
         dist.barrier()
@@ -841,6 +896,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-member ensemble measurement")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
+    ap.add_argument("--no-3d", action="store_true", help="skip the three-dimensional variant's measurement")
+    ap.add_argument("--nx3", type=int, default=NX3, help="side of the 3D variant's cubic lattice")
     ap.add_argument("--surrogate-cycles", type=int, default=0,
                     help="only run this many surrogate cycles (recorded step + jump) at the headline size, "
                          "untrained weights, and print their wall time (for launch lists and profiles)")

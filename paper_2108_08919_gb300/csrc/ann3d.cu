@@ -34,8 +34,8 @@ constexpr uint32_t E3_NBR = 4u, E3_NONFINITE = 8u, E3_ALPHA = 16u;
 
 struct P3 {
     int n, nc, ncell;
-    double L, inv_cell, R2d, half_dt_d;
-    float h, inv_h, ad, W0, dt, half_dt;
+    double L, inv_cell, cell, R2d, half_dt_d;
+    float h, inv_h, ad, W0, dt, half_dt, cell_f, R2lo, R2hi;
     float rho0, nu, Gamma, lambda, A, B, C, K, zeta, gamma_eos, beta, c0_min, c_shift;
     int apd;
 };
@@ -44,6 +44,8 @@ struct Set3 {   // one buffer set of the state
     double *x, *y, *z;
     float *u[3], *q[5], *dr, *a[3];   // dr: density deviation rho / rho0 - 1 (FP32 keeps its digits)
     int *id;
+    float4 *xi;   // (gathered set only) position relative to the corner of the particle's cell, FP32
+    int *cxyz;    // (gathered set only) cell coordinates cx | cy << 10 | cz << 20
 };
 
 struct Work3 {
@@ -82,17 +84,40 @@ __device__ __forceinline__ float dw_of(float b, float ad)
     return ad * (-5.f * t3_2 * t3_2 + 30.f * t2_2 * t2_2 - 75.f * t1_2 * t1_2);
 }
 
-// Pair data of i and j: d = r_i - r_j (FP64 minimum image, then FP32), r, W, grad_i W.
+// Pair data of i and j: d = r_i - r_j, r, W, grad_i W.  d is taken from the FP32 positions
+// relative to each particle's cell corner and the (periodic) cell offset, which is -1, 0 or 1
+// cell per axis for neighbours: d = xi_i - xi_j + (c_i - c_j) cell.  The cell-local offsets carry
+// the FP64 positions to about 1e-9 (cells of side ~0.04 L), so d is good to ~1e-7 relative.
 struct Pair3 {
     float d[3], r, W, g[3];
 };
 
-__device__ __forceinline__ Pair3 pair_of(const P3 &P, const Set3 &S, int i, int j)
+__device__ __forceinline__ int cell_step(int dc, int nc) { return dc > 1 ? dc - nc : (dc < -1 ? dc + nc : dc); }
+
+struct Here3 {   // particle i's own data for its pair loop
+    float4 xi;
+    int cx, cy, cz;
+};
+
+__device__ __forceinline__ Here3 here_of(const Set3 &M, int i)
+{
+    Here3 h;
+    h.xi = M.xi[i];
+    int c = M.cxyz[i];
+    h.cx = c & 1023;
+    h.cy = (c >> 10) & 1023;
+    h.cz = c >> 20;
+    return h;
+}
+
+__device__ __forceinline__ Pair3 pair_of(const P3 &P, const Set3 &M, const Here3 &h, int j)
 {
     Pair3 p;
-    p.d[0] = (float)min_image(S.x[i] - S.x[j], P.L);
-    p.d[1] = (float)min_image(S.y[i] - S.y[j], P.L);
-    p.d[2] = (float)min_image(S.z[i] - S.z[j], P.L);
+    const float4 xj = __ldg(M.xi + j);
+    const int cj = __ldg(M.cxyz + j);
+    p.d[0] = (h.xi.x - xj.x) + (float)cell_step(h.cx - (cj & 1023), P.nc) * P.cell_f;
+    p.d[1] = (h.xi.y - xj.y) + (float)cell_step(h.cy - ((cj >> 10) & 1023), P.nc) * P.cell_f;
+    p.d[2] = (h.xi.z - xj.z) + (float)cell_step(h.cz - (cj >> 20), P.nc) * P.cell_f;
     p.r = sqrtf(p.d[0] * p.d[0] + p.d[1] * p.d[1] + p.d[2] * p.d[2]);
     float b = p.r * P.inv_h;
     p.W = w_of(b, P.ad);
@@ -208,7 +233,12 @@ __global__ void k3_gather(P3 P, const Set3 S, Set3 M, Work3 w)
     for (int c = 0; c < 5; c++) M.q[c][g] = S.q[c][i];
     M.dr[g] = S.dr[i];
     M.id[g] = S.id[i];
-    w.key[g] = cell_of(P, M.x[g], M.y[g], M.z[g]);
+    const double x = S.x[i], y = S.y[i], z = S.z[i];
+    const int c = cell_of(P, x, y, z);
+    const int cx = c % P.nc, cy = (c / P.nc) % P.nc, cz = c / (P.nc * P.nc);
+    w.key[g] = c;
+    M.cxyz[g] = cx | (cy << 10) | (cz << 20);
+    M.xi[g] = make_float4((float)(x - cx * P.cell), (float)(y - cy * P.cell), (float)(z - cz * P.cell), 0.f);
 }
 
 // ---- neighbours, volumes, correction -------------------------------------------------------------
@@ -217,29 +247,37 @@ __global__ void k3_neighbours(P3 P, const Set3 M, Work3 w)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
-    int c = w.key[i];
-    int cx = c % P.nc, cy = (c / P.nc) % P.nc, cz = c / (P.nc * P.nc);
-    double xi = M.x[i], yi = M.y[i], zi = M.z[i];
+    const Here3 h = here_of(M, i);
     int k = 0;
     float s = P.W0;
     bool over = false;
     for (int oz = -1; oz <= 1; oz++)
         for (int oy = -1; oy <= 1; oy++)
             for (int ox = -1; ox <= 1; ox++) {
-                int qx = cx + ox, qy = cy + oy, qz = cz + oz;
+                int qx = h.cx + ox, qy = h.cy + oy, qz = h.cz + oz;
                 qx += qx < 0 ? P.nc : (qx >= P.nc ? -P.nc : 0);
                 qy += qy < 0 ? P.nc : (qy >= P.nc ? -P.nc : 0);
                 qz += qz < 0 ? P.nc : (qz >= P.nc ? -P.nc : 0);
-                int q = (qz * P.nc + qy) * P.nc + qx;
-                for (int j = w.start[q]; j < w.start[q + 1]; j++) {
+                const int q = (qz * P.nc + qy) * P.nc + qx;
+                // d = xi_i - xi_j - (offset of cell q) cell
+                const float sx = h.xi.x - (float)ox * P.cell_f, sy = h.xi.y - (float)oy * P.cell_f,
+                            sz = h.xi.z - (float)oz * P.cell_f;
+                const int e = w.start[q + 1];
+                for (int j = w.start[q]; j < e; j++) {
                     if (j == i) continue;
-                    double dx = min_image(xi - M.x[j], P.L), dy = min_image(yi - M.y[j], P.L),
-                           dz = min_image(zi - M.z[j], P.L);
-                    double r2 = dx * dx + dy * dy + dz * dz;
-                    if (r2 < P.R2d) {
+                    const float4 xj = __ldg(M.xi + j);
+                    const float dx = sx - xj.x, dy = sy - xj.y, dz = sz - xj.z;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    bool in = r2 < P.R2lo;
+                    if (!in && r2 < P.R2hi) {   // near 3h: decide in FP64 as the oracle does
+                        double ex = min_image(M.x[i] - M.x[j], P.L), ey = min_image(M.y[i] - M.y[j], P.L),
+                               ez = min_image(M.z[i] - M.z[j], P.L);
+                        in = ex * ex + ey * ey + ez * ez < P.R2d;
+                    }
+                    if (in) {
                         if (k < MAXN3) {
                             w.nbr[(size_t)k * P.n + i] = j;
-                            s += w_of(sqrtf((float)r2) * P.inv_h, P.ad);
+                            s += w_of(sqrtf(r2) * P.inv_h, P.ad);
                             k++;
                         } else {
                             over = true;
@@ -257,11 +295,12 @@ __global__ void k3_correction(P3 P, const Set3 M, Work3 w)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
+    const Here3 hi = here_of(M, i);
     float a[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     int m = w.nnbr[i];
     for (int k = 0; k < m; k++) {
         int j = w.nbr[(size_t)k * P.n + i];
-        Pair3 p = pair_of(P, M, i, j);
+        Pair3 p = pair_of(P, M, hi, j);
         float vj = w.V[j];
         for (int s = 0; s < 3; s++)
             for (int l = 0; l < 3; l++) a[s][l] += -p.d[s] * vj * p.g[l];
@@ -334,6 +373,7 @@ __global__ void k3_pass1(P3 P, const Set3 M, Work3 w)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
+    const Here3 hi = here_of(M, i);
     const float *B = w.B + 9 * (size_t)i;
     float ui[3] = {M.u[0][i], M.u[1][i], M.u[2][i]}, qi[5];
     for (int c = 0; c < 5; c++) qi[c] = M.q[c][i];
@@ -341,7 +381,7 @@ __global__ void k3_pass1(P3 P, const Set3 M, Work3 w)
     int m = w.nnbr[i];
     for (int k = 0; k < m; k++) {
         int j = w.nbr[(size_t)k * P.n + i];
-        Pair3 p = pair_of(P, M, i, j);
+        Pair3 p = pair_of(P, M, hi, j);
         float bg[3], vj = w.V[j];
         bg_of(B, p.g, bg);
         float du[3] = {ui[0] - M.u[0][j], ui[1] - M.u[1][j], ui[2] - M.u[2][j]};
@@ -374,12 +414,13 @@ __global__ void k3_pass2(P3 P, const Set3 M, Work3 w)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
+    const Here3 hi = here_of(M, i);
     // Eq. (28) on the deviations (rho0 factors out of the filter)
     float di = w.dh[i], num = 0.f, den = P.W0;
     int m = w.nnbr[i];
     for (int k = 0; k < m; k++) {
         int j = w.nbr[(size_t)k * P.n + i];
-        Pair3 p = pair_of(P, M, i, j);
+        Pair3 p = pair_of(P, M, hi, j);
         num += (di - w.dh[j]) * p.W;
         den += p.W;
     }
@@ -396,6 +437,7 @@ __global__ void k3_pass3(P3 P, const Set3 M, Set3 S, Work3 w)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
+    const Here3 hi = here_of(M, i);
     const float *B = w.B + 9 * (size_t)i;
     float ri = P.rho0 * (1.f + w.dhat[i]), pri = w.p[i] / (ri * ri);
     float ui[3] = {M.u[0][i], M.u[1][i], M.u[2][i]}, qi[5];
@@ -407,7 +449,7 @@ __global__ void k3_pass3(P3 P, const Set3 M, Set3 S, Work3 w)
     int m = w.nnbr[i];
     for (int k = 0; k < m; k++) {
         int j = w.nbr[(size_t)k * P.n + i];
-        Pair3 p = pair_of(P, M, i, j);
+        Pair3 p = pair_of(P, M, hi, j);
         float bg[3], vj = w.V[j];
         bg_of(B, p.g, bg);
         float rj = P.rho0 * (1.f + w.dhat[j]);
@@ -527,6 +569,8 @@ cudaError_t alloc_set(ann3_ctx *c, Set3 &S, size_t n)
     for (int k = 0; k < 5 && !e; k++) e = alloc3(c, S.q[k], n);
     if (!e) e = alloc3(c, S.dr, n);
     if (!e) e = alloc3(c, S.id, n);
+    if (!e) e = alloc3(c, S.xi, n);
+    if (!e) e = alloc3(c, S.cxyz, n);
     return e;
 }
 
@@ -600,7 +644,11 @@ int ann3_create(const ann3_params *p, ann3_ctx **out)
     P.ncell = nc * nc * nc;
     P.L = p->L;
     P.inv_cell = nc / p->L;
+    P.cell = p->L / nc;
+    P.cell_f = (float)P.cell;
     P.R2d = 9.0 * p->h * p->h;
+    P.R2lo = (float)(P.R2d * (1.0 - 4e-6));   // FP32 r^2 of a pair is good to ~1e-6 relative
+    P.R2hi = (float)(P.R2d * (1.0 + 4e-6));
     P.half_dt_d = 0.5 * p->dt;
     P.h = (float)p->h;
     P.inv_h = (float)(1.0 / p->h);
