@@ -488,8 +488,10 @@ int ann_velocity_moments_noalloc(const float *ux, const float *uy, const float *
  * Q33 = -Q11 - Q22; the molecular field keeps the B term (Q^2 - tr(Q^2) I / 3) of Eq. (7); the
  * corrected Laplacian is the scalar form with factor 2 per component; the viscous term of Eq. (23)
  * carries 2 (d + 2) nu = 10 nu.  Paper momentum mode only, no elastic stress.  A periodic cube of
- * side L; cells of side >= 3h, at least 3 per side.  Neighbour lists hold at most
- * ANN3_MAX_NEIGHBORS particles (~250 at h = 1.3 dx).  FP64 positions; pair differences are taken
+ * side L; cells of side >= 3h (1 + 0.05), at least 3 per side (L >= 9.45 h: 13 particles a side at
+ * h = 1.3 dx).  Candidate lists (every j within 3h (1 + 0.05), rebuilt with a re-sort when a
+ * particle has moved 0.05 x 3h / 2) hold at most 576, neighbour lists ANN3_MAX_NEIGHBORS (~250 at
+ * h = 1.3 dx).  FP64 positions; pair differences are taken
  * in FP64 and everything else runs in FP32.  The step order is that of the 2D step (modified
  * Euler predictor, search, volumes, correction tensor, continuity, density filter and equation of
  * state, velocity gradient, Laplacian of Q, Q rate, momentum, artificial displacement, corrector).
@@ -544,8 +546,9 @@ int ann3_step(ann3_ctx *c, int64_t nsteps);
  * INVALID_ARG (unknown field, NULL dst), STATE, CUDA. */
 int ann3_get_field(ann3_ctx *c, int32_t field, double *dst);
 
-/* Steps taken, and the device error bits (1 cell overflow, 4 neighbours, 8 non-finite, 16 alpha). */
-int ann3_get_status(ann3_ctx *c, int64_t *steps, uint32_t *error_bits);
+/* Steps taken, the device error bits (4 neighbours, 8 non-finite, 16 alpha) and the number of steps
+ * that re-sorted and rebuilt the candidate lists since ann3_set_particles (each pointer may be NULL). */
+int ann3_get_status(ann3_ctx *c, int64_t *steps, uint32_t *error_bits, int64_t *resorts);
 
 const char *ann3_last_error(ann3_ctx *c);
 

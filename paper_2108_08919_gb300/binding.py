@@ -154,7 +154,7 @@ def lib() -> ctypes.CDLL:
         "ann3_set_particles": (i32, [vp, i64, dp, dp, dp, dp, dp, dp]),
         "ann3_step": (i32, [vp, i64]),
         "ann3_get_field": (i32, [vp, i32, dp]),
-        "ann3_get_status": (i32, [vp, _P(ctypes.c_int64), _P(ctypes.c_uint32)]),
+        "ann3_get_status": (i32, [vp, _P(ctypes.c_int64), _P(ctypes.c_uint32), _P(ctypes.c_int64)]),
         "ann3_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -667,10 +667,13 @@ def ann3_get_field(ctx, name: str, n: int) -> np.ndarray:
 
 
 def ann3_get_status(ctx):
+    """(steps, error bits, re-sorting steps) since the particles were loaded."""
     steps = ctypes.c_int64()
     bits = ctypes.c_uint32()
-    _check3(lib().ann3_get_status(ctx, ctypes.byref(steps), ctypes.byref(bits)), ctx, "ann3_get_status")
-    return steps.value, bits.value
+    rs = ctypes.c_int64()
+    _check3(lib().ann3_get_status(ctx, ctypes.byref(steps), ctypes.byref(bits), ctypes.byref(rs)), ctx,
+            "ann3_get_status")
+    return steps.value, bits.value, rs.value
 
 
 def ann3_last_error(ctx) -> str:

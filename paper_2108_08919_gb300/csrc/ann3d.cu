@@ -30,12 +30,15 @@
 namespace {
 
 constexpr int MAXN3 = ANN3_MAX_NEIGHBORS;
+constexpr int MAXC3 = 576;          // candidates: neighbours within 3h (1 + SKIN3) at the last re-sort
+constexpr double SKIN3 = 0.05;      // candidate lists stay valid while no particle moves SKIN3 3h / 2
 constexpr uint32_t E3_NBR = 4u, E3_NONFINITE = 8u, E3_ALPHA = 16u;
 
 struct P3 {
     int n, nc, ncell;
     double L, inv_cell, cell, R2d, half_dt_d;
-    float h, inv_h, ad, W0, dt, half_dt, cell_f, R2lo, R2hi;
+    float h, inv_h, ad, W0, dt, half_dt, cell_f, R2lo, R2hi, R2c;
+    double skin_max2;
     float rho0, nu, Gamma, lambda, A, B, C, K, zeta, gamma_eos, beta, c0_min, c_shift;
     int apd;
 };
@@ -49,7 +52,10 @@ struct Set3 {   // one buffer set of the state
 };
 
 struct Work3 {
-    int *key, *slot, *perm, *count, *start, *nbr, *nnbr;
+    int *key, *slot, *perm, *count, *start, *nbr, *nnbr, *cand, *ncand;
+    double *xr, *yr, *zr;   // positions at the last re-sort (sorted order)
+    unsigned *flag;         // non-zero: this step re-sorts and rebuilds the candidate lists
+    unsigned *rebuilds;
     float *sumW, *V, *B, *k, *dh, *dhat, *p, *qn, *an, *gu, *lap, *m;   // dh, dhat: deviations of rho_half, rho_hat
     unsigned *umax, *err;
 };
@@ -140,15 +146,22 @@ __device__ __forceinline__ int cell_of(const P3 &P, double x, double y, double z
 
 // ---- predictor, cell counts --------------------------------------------------------------------
 
-__global__ void k3_predict(P3 P, Set3 S, Work3 w)
+__device__ __forceinline__ bool resorting(const Work3 &w) { return *(volatile unsigned *)w.flag != 0u; }
+
+// Predictor on S (in place) and a copy into M in the same order (the order of the last re-sort),
+// with the FP32 offset to the particle's assigned cell; a particle that has moved SKIN3 3h / 2 since
+// the last re-sort makes this step re-sort (the gated kernels after this one see the flag).
+__global__ void k3_predict(P3 P, Set3 S, Set3 M, Work3 w)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float sp = 0.f;
+    const bool rs = resorting(w);
     if (i < P.n) {
         float u[3];
         for (int c = 0; c < 3; c++) {
             u[c] = S.u[c][i] + P.half_dt * S.a[c][i];
             S.u[c][i] = u[c];
+            M.u[c][i] = u[c];
         }
         double x = wrap(S.x[i] + P.half_dt_d * (double)u[0], P.L);
         double y = wrap(S.y[i] + P.half_dt_d * (double)u[1], P.L);
@@ -162,17 +175,40 @@ __global__ void k3_predict(P3 P, Set3 S, Work3 w)
         S.z[i] = z;
         sp = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
         if (!isfinite(sp)) sp = 0.f;
-        int c = cell_of(P, x, y, z);
-        w.key[i] = c;
-        w.slot[i] = atomicAdd(&w.count[c], 1);
+        if (!rs) {
+            double ex = min_image(x - w.xr[i], P.L), ey = min_image(y - w.yr[i], P.L), ez = min_image(z - w.zr[i], P.L);
+            if (ex * ex + ey * ey + ez * ez > P.skin_max2) *(volatile unsigned *)w.flag = 1u;
+            M.x[i] = x;
+            M.y[i] = y;
+            M.z[i] = z;
+            for (int c = 0; c < 5; c++) M.q[c][i] = S.q[c][i];
+            M.dr[i] = S.dr[i];
+            M.id[i] = S.id[i];
+            int cc = M.cxyz[i];
+            int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = cc >> 20;
+            M.xi[i] = make_float4((float)min_image(x - cx * P.cell, P.L), (float)min_image(y - cy * P.cell, P.L),
+                                  (float)min_image(z - cz * P.cell, P.L), 0.f);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) sp = fmaxf(sp, __shfl_xor_sync(0xFFFFFFFFu, sp, o));
     if ((threadIdx.x & 31) == 0) atomicMax(w.umax, __float_as_uint(sp));   // sp >= 0: bits order as values
 }
 
-// Exclusive scan of the cell counts by one block of 1024 threads (chunks of 1024 cells).
-__global__ void __launch_bounds__(1024) k3_scan(int ncell, const int *count, int *start)
+// Cell of each particle and the cell counts (re-sort steps only).
+__global__ void k3_keys(P3 P, const Set3 S, Work3 w)
 {
+    if (!resorting(w)) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    int c = cell_of(P, S.x[i], S.y[i], S.z[i]);
+    w.key[i] = c;
+    w.slot[i] = atomicAdd(&w.count[c], 1);
+}
+
+// Exclusive scan of the cell counts by one block of 1024 threads (chunks of 1024 cells).
+__global__ void __launch_bounds__(1024) k3_scan(Work3 w, int ncell, const int *count, int *start)
+{
+    if (!resorting(w)) return;
     __shared__ int s[1024];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
@@ -198,6 +234,7 @@ __global__ void __launch_bounds__(1024) k3_scan(int ncell, const int *count, int
 
 __global__ void k3_scatter(P3 P, Work3 w)
 {
+    if (!resorting(w)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < P.n) w.perm[w.start[w.key[i]] + w.slot[i]] = i;
 }
@@ -205,6 +242,7 @@ __global__ void k3_scatter(P3 P, Work3 w)
 // The slots of each cell in particle-ID order (insertion sort; cells hold tens of particles).
 __global__ void k3_cellsort(P3 P, const Set3 S, Work3 w)
 {
+    if (!resorting(w)) return;
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= P.ncell) return;
     int b = w.start[c], e = w.start[c + 1];
@@ -220,6 +258,7 @@ __global__ void k3_cellsort(P3 P, const Set3 S, Work3 w)
 
 __global__ void k3_gather(P3 P, const Set3 S, Set3 M, Work3 w)
 {
+    if (!resorting(w)) return;
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= P.n) return;
     int i = w.perm[g];
@@ -243,13 +282,16 @@ __global__ void k3_gather(P3 P, const Set3 S, Set3 M, Work3 w)
 
 // ---- neighbours, volumes, correction -------------------------------------------------------------
 
-__global__ void k3_neighbours(P3 P, const Set3 M, Work3 w)
+// Candidate lists (re-sort steps only): every j within 3h (1 + SKIN3) from the 27 surrounding
+// cells, and the positions they were taken at.
+__global__ void k3_candidates(P3 P, const Set3 M, Work3 w)
 {
+    if (!resorting(w)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
+    if (i == 0) atomicAdd(w.rebuilds, 1u);
     const Here3 h = here_of(M, i);
     int k = 0;
-    float s = P.W0;
     bool over = false;
     for (int oz = -1; oz <= 1; oz++)
         for (int oy = -1; oy <= 1; oy++)
@@ -267,24 +309,51 @@ __global__ void k3_neighbours(P3 P, const Set3 M, Work3 w)
                     if (j == i) continue;
                     const float4 xj = __ldg(M.xi + j);
                     const float dx = sx - xj.x, dy = sy - xj.y, dz = sz - xj.z;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    bool in = r2 < P.R2lo;
-                    if (!in && r2 < P.R2hi) {   // near 3h: decide in FP64 as the oracle does
-                        double ex = min_image(M.x[i] - M.x[j], P.L), ey = min_image(M.y[i] - M.y[j], P.L),
-                               ez = min_image(M.z[i] - M.z[j], P.L);
-                        in = ex * ex + ey * ey + ez * ez < P.R2d;
-                    }
-                    if (in) {
-                        if (k < MAXN3) {
-                            w.nbr[(size_t)k * P.n + i] = j;
-                            s += w_of(sqrtf(r2) * P.inv_h, P.ad);
-                            k++;
-                        } else {
-                            over = true;
-                        }
+                    if (dx * dx + dy * dy + dz * dz < P.R2c) {
+                        if (k < MAXC3) w.cand[(size_t)k++ * P.n + i] = j;
+                        else over = true;
                     }
                 }
             }
+    if (over) atomicOr(w.err, E3_NBR);
+    w.ncand[i] = k;
+    w.xr[i] = M.x[i];
+    w.yr[i] = M.y[i];
+    w.zr[i] = M.z[i];
+}
+
+// Every step: the neighbours (|r_i - r_j| < 3h; FP32 test, FP64 near 3h as the oracle decides)
+// among the candidates, sum W and V = 1 / sum W (Eq. 19).  Clears the re-sort flag: the gated
+// kernels of this step have run.
+__global__ void k3_filter(P3 P, const Set3 M, Work3 w)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *(volatile unsigned *)w.flag = 0u;
+    if (i >= P.n) return;
+    const Here3 hi = here_of(M, i);
+    int k = 0;
+    float s = P.W0;
+    bool over = false;
+    const int m = w.ncand[i];
+    for (int q = 0; q < m; q++) {
+        const int j = w.cand[(size_t)q * P.n + i];
+        const Pair3 p = pair_of(P, M, hi, j);
+        const float r2 = p.r * p.r;
+        bool in = r2 < P.R2lo;
+        if (!in && r2 < P.R2hi) {
+            double ex = min_image(M.x[i] - M.x[j], P.L), ey = min_image(M.y[i] - M.y[j], P.L),
+                   ez = min_image(M.z[i] - M.z[j], P.L);
+            in = ex * ex + ey * ey + ez * ez < P.R2d;
+        }
+        if (in) {
+            if (k < MAXN3) {
+                w.nbr[(size_t)k++ * P.n + i] = j;
+                s += p.W;
+            } else {
+                over = true;
+            }
+        }
+    }
     if (over) atomicOr(w.err, E3_NBR);
     w.nnbr[i] = k;
     w.sumW[i] = s;
@@ -446,6 +515,9 @@ __global__ void k3_pass3(P3 P, const Set3 M, Set3 S, Work3 w)
     full_q(qi, Qi);
     float fp[3] = {0.f, 0.f, 0.f}, fv[3] = {0.f, 0.f, 0.f}, dq[3] = {0.f, 0.f, 0.f};
     float su[3] = {0.f, 0.f, 0.f}, sw = P.W0, sr = 0.f, sd[3] = {0.f, 0.f, 0.f};
+    // sum_j d / r^3 of Eq. (29) nearly cancels (terms ~1/r^2, sum ~ their imbalance): compensated
+    // (Kahan) summation keeps it to FP32 rounding of the sum rather than of the terms
+    float sdc[3] = {0.f, 0.f, 0.f};
     int m = w.nnbr[i];
     for (int k = 0; k < m; k++) {
         int j = w.nbr[(size_t)k * P.n + i];
@@ -466,7 +538,10 @@ __global__ void k3_pass3(P3 P, const Set3 M, Set3 S, Work3 w)
             fv[c] += vj * ud / r2 * bg[c];
             dq[c] += vj * ((Qj[c][0] - Qi[c][0]) * bg[0] + (Qj[c][1] - Qi[c][1]) * bg[1] + (Qj[c][2] - Qi[c][2]) * bg[2]);
             su[c] += du[c] * p.W;
-            sd[c] += p.d[c] / (r2 * p.r);
+            const float y = p.d[c] / (r2 * p.r) - sdc[c];
+            const float t = sd[c] + y;
+            sdc[c] = (t - sd[c]) - y;
+            sd[c] = t;
         }
         sw += p.W;
         sr += p.r;
@@ -631,7 +706,7 @@ int ann3_create(const ann3_params *p, ann3_ctx **out)
     if (p->n < 1 || p->n > (1ll << 26) || !(p->L > 0.0) || !(p->h > 0.0) || !(p->dt > 0.0) || !(p->rho0 > 0.0) ||
         !(p->gamma_eos > 0.0))
         return ANN_ERR_INVALID_ARG;
-    int nc = (int)std::floor(p->L / (3.0 * p->h));
+    int nc = (int)std::floor(p->L / (3.0 * p->h * (1.0 + SKIN3)));
     if (nc < 3 || (int64_t)nc * nc * nc > (1ll << 28)) return ANN_ERR_INVALID_ARG;
     int dev = 0;
     if (cudaGetDeviceCount(&dev) != cudaSuccess || dev == 0) return ANN_ERR_NOT_AVAILABLE;
@@ -649,6 +724,8 @@ int ann3_create(const ann3_params *p, ann3_ctx **out)
     P.R2d = 9.0 * p->h * p->h;
     P.R2lo = (float)(P.R2d * (1.0 - 4e-6));   // FP32 r^2 of a pair is good to ~1e-6 relative
     P.R2hi = (float)(P.R2d * (1.0 + 4e-6));
+    P.R2c = (float)(P.R2d * (1.0 + SKIN3) * (1.0 + SKIN3) * (1.0 + 1e-5));   // padded for FP32 rounding
+    P.skin_max2 = (0.5 * SKIN3 * 3.0 * p->h) * (0.5 * SKIN3 * 3.0 * p->h);
     P.half_dt_d = 0.5 * p->dt;
     P.h = (float)p->h;
     P.inv_h = (float)(1.0 / p->h);
@@ -681,6 +758,13 @@ int ann3_create(const ann3_params *p, ann3_ctx **out)
     if (!e) e = alloc3(c, w.count, (size_t)P.ncell);
     if (!e) e = alloc3(c, w.start, (size_t)P.ncell + 1);
     if (!e) e = alloc3(c, w.nbr, (size_t)MAXN3 * n);
+    if (!e) e = alloc3(c, w.cand, (size_t)MAXC3 * n);
+    if (!e) e = alloc3(c, w.ncand, n);
+    if (!e) e = alloc3(c, w.xr, n);
+    if (!e) e = alloc3(c, w.yr, n);
+    if (!e) e = alloc3(c, w.zr, n);
+    if (!e) e = alloc3(c, w.flag, 1);
+    if (!e) e = alloc3(c, w.rebuilds, 1);
     if (!e) e = alloc3(c, w.nnbr, n);
     if (!e) e = alloc3(c, w.sumW, n);
     if (!e) e = alloc3(c, w.V, n);
@@ -754,6 +838,9 @@ int ann3_set_particles(ann3_ctx *c, int64_t n, const double *x, const double *y,
     for (size_t i = 0; i < nn; i++) id[i] = (int)i;
     if (!e) e = cudaMemcpyAsync(c->S.id, id.data(), nn * 4, cudaMemcpyHostToDevice, c->s);
     if (!e) e = cudaMemsetAsync(c->w.err, 0, 4, c->s);
+    const unsigned one = 1u;   // the first step re-sorts
+    if (!e) e = cudaMemcpyAsync(c->w.flag, &one, 4, cudaMemcpyHostToDevice, c->s);
+    if (!e) e = cudaMemsetAsync(c->w.rebuilds, 0, 4, c->s);
     if (!e) e = cudaStreamSynchronize(c->s);
     if (e) return cuda3(c, e, "ann3_set_particles");
     c->have = true;
@@ -773,12 +860,15 @@ int ann3_step(ann3_ctx *c, int64_t nsteps)
         e = cudaMemsetAsync(c->w.count, 0, sizeof(int) * (size_t)P.ncell, s);
         if (!e) e = cudaMemsetAsync(c->w.umax, 0, 4, s);
         if (e) break;
-        k3_predict<<<g, 256, 0, s>>>(P, c->S, c->w);
-        k3_scan<<<1, 1024, 0, s>>>(P.ncell, c->w.count, c->w.start);
+        k3_predict<<<g, 256, 0, s>>>(P, c->S, c->M, c->w);
+        // re-sort and candidate rebuild: each kernel returns at once unless the flag is set
+        k3_keys<<<g, 256, 0, s>>>(P, c->S, c->w);
+        k3_scan<<<1, 1024, 0, s>>>(c->w, P.ncell, c->w.count, c->w.start);
         k3_scatter<<<g, 256, 0, s>>>(P, c->w);
         k3_cellsort<<<nb3((size_t)P.ncell), 256, 0, s>>>(P, c->S, c->w);
         k3_gather<<<g, 256, 0, s>>>(P, c->S, c->M, c->w);
-        k3_neighbours<<<g, 256, 0, s>>>(P, c->M, c->w);
+        k3_candidates<<<g, 256, 0, s>>>(P, c->M, c->w);
+        k3_filter<<<g, 256, 0, s>>>(P, c->M, c->w);
         k3_correction<<<g, 256, 0, s>>>(P, c->M, c->w);
         k3_pass1<<<g, 256, 0, s>>>(P, c->M, c->w);
         k3_pass2<<<g, 256, 0, s>>>(P, c->M, c->w);
@@ -838,15 +928,17 @@ int ann3_get_field(ann3_ctx *c, int32_t field, double *dst)
     return ANN_OK;
 }
 
-int ann3_get_status(ann3_ctx *c, int64_t *steps, uint32_t *error_bits)
+int ann3_get_status(ann3_ctx *c, int64_t *steps, uint32_t *error_bits, int64_t *resorts)
 {
     if (!c) return ANN_ERR_INVALID_ARG;
-    uint32_t b = 0;
+    uint32_t b = 0, r = 0;
     cudaError_t e = cudaMemcpyAsync(&b, c->w.err, 4, cudaMemcpyDeviceToHost, c->s);
+    if (!e) e = cudaMemcpyAsync(&r, c->w.rebuilds, 4, cudaMemcpyDeviceToHost, c->s);
     if (!e) e = cudaStreamSynchronize(c->s);
     if (e) return cuda3(c, e, "ann3_get_status");
     if (steps) *steps = c->steps;
     if (error_bits) *error_bits = b;
+    if (resorts) *resorts = r;
     return ANN_OK;
 }
 

@@ -57,6 +57,7 @@ def _run_both(B, O, ic, p, steps):
         B.ann3_set_particles(ctx, ic["x"], ic["y"], ic["z"], ic["u"], ic["q"], ic["rho"])
         B.ann3_step(ctx, steps)
         got = {k: B.ann3_get_field(ctx, k, n) for k in B.FIELDS3}
+        got["status"] = B.ann3_get_status(ctx)
     finally:
         B.ann3_destroy(ctx)
     return got, want, rec
@@ -67,17 +68,32 @@ def _disp(pos, x0, L=1.0):
     return d - L * np.round(d / L)
 
 
-@pytest.mark.parametrize("kind", ["lattice", "random"])
+@pytest.mark.parametrize("kind", ["lattice", "random", "fast"])
 def test_steps_match_the_oracle(B, O, kind):
-    nx = 12
+    """lattice: one re-sort, the later steps filter the candidate lists; fast: particles cross half
+    the skin every few steps, so the run re-sorts several times."""
+    nx = 13
+    steps = 4
+    p = _params(nx)
     if kind == "lattice":
         ic = si.jittered_lattice3(nx, seed=11, jitter=0.2, u_scale=0.2)
-    else:   # uniform random positions: ragged cell occupancy and neighbour counts
+    elif kind == "random":   # uniform random positions: ragged cell occupancy and neighbour counts
         ic = si.jittered_lattice3(nx, seed=12, jitter=0.0, u_scale=0.2)
         r = si.uniform53(99, 3 * ic["n"]).reshape(3, -1)
         ic["x"], ic["y"], ic["z"] = r[0], r[1], r[2]
-    p = _params(nx)
-    got, want, rec = _run_both(B, O, ic, p, 3)
+    else:
+        # a uniform drift of |u| = 18.7 on top of small random velocities: particles cross half the
+        # skin every 4 steps or so, without the chaotic separation of FP32 and FP64 trajectories
+        # that large random velocities at the particle scale bring
+        ic = si.jittered_lattice3(nx, seed=14, jitter=0.2, u_scale=0.2)
+        ic["u"] = ic["u"] + np.array([15.0, -10.0, 5.0])
+        p = _params(nx, dt=1e-4)
+        steps = 12
+    got, want, rec = _run_both(B, O, ic, p, steps)
+    resorts = got.pop("status")[2]
+    # the lattice moves little; random positions are pushed apart by the displacement of Eq. (29)
+    # and may re-sort again; fast particles re-sort every few steps
+    assert {"lattice": resorts == 1, "random": resorts >= 1, "fast": resorts >= 3}[kind], resorts
     x0 = np.stack([ic["x"], ic["y"], ic["z"]], axis=1)
     wpos = np.stack([want["x"], want["y"], want["z"]], axis=1)
     errs = {
@@ -94,6 +110,13 @@ def test_steps_match_the_oracle(B, O, kind):
     }
     print(kind, {k: f"{v:.2e}" for k, v in errs.items()})
     assert np.array_equal(got["NNBR"][:, 0].astype(np.int64), rec["nnbr"])
+    if kind == "fast":
+        # u is FP32 and carries the drift: the velocity differences that feed grad u, a, the Q rate,
+        # the density and the pressure keep log2(|U| / |u - U|) ~ 7 fewer bits than in the other
+        # cases, so those fields get 2^7 x the bound
+        loose = {"gradu", "a", "qrate", "rho-1", "p"}
+        assert max(v for k, v in errs.items() if k in loose) < 2e-5 * 2 ** 7, errs
+        errs = {k: v for k, v in errs.items() if k not in loose}
     assert max(errs.values()) < 2e-5, errs
 
 
@@ -130,7 +153,7 @@ def test_uniform_state_at_64_cubed(B, O):
 
 
 def test_errors_are_reported(B):
-    nx = 12
+    nx = 13
     p = _params(nx)
     ic = si.jittered_lattice3(nx, seed=1)
     n = ic["n"]
@@ -148,7 +171,7 @@ def test_errors_are_reported(B):
             B.ann3_set_particles(ctx, ic["x"][:-1], ic["y"][:-1], ic["z"][:-1], ic["u"][:-1], ic["q"][:-1])
         B.ann3_set_particles(ctx, ic["x"], ic["y"], ic["z"], ic["u"], ic["q"])
         B.ann3_step(ctx, 2)
-        assert B.ann3_get_status(ctx) == (2, 0)
+        assert B.ann3_get_status(ctx) == (2, 0, 1)   # slow particles: only the first step re-sorts
     finally:
         B.ann3_destroy(ctx)
     # more neighbours than the lists hold: reported, not written past the end
