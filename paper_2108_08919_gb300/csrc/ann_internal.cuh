@@ -4,6 +4,7 @@
 #include "../../include/ann.h"
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace ann {
@@ -132,22 +133,29 @@ cudaError_t enqueue_correlation(int M, double L, const double *grid, int all_ori
 cudaError_t enqueue_defects(int M, const double *grid, signed char *map, unsigned long long *counts, cudaStream_t s);
 cudaError_t enqueue_mixing(const DevParams &P, const Bufs &b, const unsigned char *colors, int G, int S,
                            unsigned *cnt, cudaStream_t s);
-// Neighbour graph of the present positions in the cell-sorted order of the last search (ELL: entry
-// k of row g at k * n + g; neighbours as sorted indices), for the learned surrogate.  A row lists
-// the cnt2 neighbours closer than 2h (the network's graph) first, then the rest of the support (3h).
+// Neighbour graph of the present positions in the cell-sorted order of the last search, for the
+// learned surrogate (row g is particle ids[g]): the neighbours closer than 2h as ELL rows (entry k
+// of row g at k * n + g, neighbours as sorted indices) with W and S2 = W(0) + sum W; and over the
+// support (3h) the SPH means of (ux, uy, Q11, Q12) and of the recorded acceleration, and from them
+// the network's input rows.
 struct GraphOut {
-    int *nbr;        // MAXN x n neighbour sorted indices
-    float *W;        // MAXN x n kernel values W(|x_i - x_j|)
-    int *cnt;        // n: neighbours in the support
-    int *cnt2;       // n: of which closer than 2h
-    float *S;        // n: W(0) + sum_j W over the support
-    float *S2;       // n: W(0) + sum_j W over the 2h neighbours
-    double *x, *y;   // n: positions
-    float4 *u4;      // n: (ux, uy, q11, q12)
-    float *dr;       // n: rho / rho0 - 1
-    int *ids;        // n: particle ID of sorted row g
+    int *nbr;               // MAXN x n neighbour sorted indices (2h)
+    float *W;               // MAXN x n kernel values W(|x_i - x_j|)
+    int *cnt2;              // n: neighbours closer than 2h
+    float *S2;              // n: W(0) + sum_j W over them
+    double *x, *y;          // n: positions
+    float4 *u4;             // n: (ux, uy, q11, q12)
+    float *dr;              // n: rho / rho0 - 1
+    int *ids;               // n: particle ID of sorted row g
+    float *agg1;            // 2 x n: SPH mean of (ax, ay) over the support
+    const float *tend_id;   // 8 x n tendencies by particle ID (ax, ay, m11, m12, lapQ, div, vort)
+    __nv_bfloat16 *X;       // n x 16: the network's input rows (BF16)
+    float inv_us;           // 1 / velocity scale
+    float scale[4];         // tendency scales per pair of channels (a, m, lap Q, div / vort)
 };
-cudaError_t enqueue_export_graph(const DevParams &P, const Bufs &b, const GraphOut &o, cudaStream_t s);
+// The export, then inc (n x 4, sorted order) = kdt (m11, m12, agg(agg1)) with a second walk.
+cudaError_t enqueue_export_graph(const DevParams &P, const Bufs &b, const GraphOut &o, float kdt, float *inc,
+                                 cudaStream_t s);
 
 // Context hooks for the surrogate (implemented in ann_api.cu; the context itself stays opaque).
 struct CtxView {

@@ -1139,54 +1139,135 @@ __global__ void __launch_bounds__(PT) k_export_nbrs(DevParams P, Bufs b, int *co
 // row id = mid[g] of particle g holds its neighbours' IDs and kernel values W(|d|) (the exact
 // support test's neighbours, from the mask), the count, and S = sum_j W + W(0) of the search;
 // the state is gathered by ID too.  Runs after a search at the present positions.
+constexpr int SMEM_EX = HCAP * (16 + 4 + 16 + 8);   // position, slot, (u, Q), a
+
+// Graph export for the surrogate, one walk of each particle's candidates at the present
+// positions: the neighbours closer than 2h (the network's graph) into the ELL rows with W and their
+// normalisation S2, and over the whole support (3h) the SPH means (Eq. 19 weights W / sum W, self
+// term included) of (ux, uy, Q11, Q12) and of the recorded acceleration (o.tend_id planes 0, 1 by
+// particle ID).
 __global__ void __launch_bounds__(PT) k_export_graph(DevParams P, Bufs b, GraphOut o)
 {
     __shared__ TileShared ts;
     extern __shared__ __align__(16) unsigned char dsm[];
     float4 *pos = reinterpret_cast<float4 *>(dsm);
-    int *sg = reinterpret_cast<int *>(pos + HCAP);
+    float4 *su = pos + HCAP;                                  // (ux, uy, q11, q12)
+    float2 *sa = reinterpret_cast<float2 *>(su + HCAP);       // (ax, ay)
+    int *sg = reinterpret_cast<int *>(sa + HCAP);
     Tile T;
     if (!tile_begin(P, b, ts, T)) return;
     for (int t = threadIdx.x; t < T.H; t += PT) {
         SlotInfo s = slot_info(P, b, ts, T, t);
         pos[t] = s.e;
         sg[t] = s.g;
+        su[t] = make_float4(b.mux[s.g], b.muy[s.g], b.mq11[s.g], b.mq12[s.g]);
+        const int id = b.mid[s.g];
+        sa[t] = make_float2(o.tend_id[id], o.tend_id[(size_t)P.n + id]);
+    }
+    __syncthreads();
+    const float r2net = 4.f / (P.inv_h * P.inv_h);
+    for (int q = threadIdx.x; q < T.Ni; q += PT) {
+        int si = inner_slot(ts, T, q);
+        int gi = sg[si];
+        float4 pi = pos[si], ui = su[si];
+        float2 ai = sa[si];
+        int k = 0;
+        float s2 = P.W0;
+        float4 m4 = make_float4(P.W0 * ui.x, P.W0 * ui.y, P.W0 * ui.z, P.W0 * ui.w);
+        float2 m2 = make_float2(P.W0 * ai.x, P.W0 * ai.y);
+        for_each_candidate<1>(P, b, gi, b.emask[gi], [&](int off, int, unsigned in) {
+            int j = off >> 4;
+            if (in && j < T.H) {
+                float r2 = len2(pair_d(pi, slot_at(pos, off)));
+                float w = kernel_w<true>(r2, P);
+                float4 uj = slot_at(su, off);
+                float2 aj = slot_at(sa, off);
+                m4.x = fmaf(w, uj.x, m4.x);
+                m4.y = fmaf(w, uj.y, m4.y);
+                m4.z = fmaf(w, uj.z, m4.z);
+                m4.w = fmaf(w, uj.w, m4.w);
+                m2.x = fmaf(w, aj.x, m2.x);
+                m2.y = fmaf(w, aj.y, m2.y);
+                if (r2 < r2net && k < MAXN) {
+                    o.nbr[(size_t)k * P.n + gi] = sg[j];
+                    o.W[(size_t)k * P.n + gi] = w;
+                    s2 += w;
+                    k++;
+                }
+            }
+        });
+        const float is = 1.f / b.sumW[gi];
+        o.cnt2[gi] = k;
+        o.S2[gi] = s2;
+        o.agg1[gi] = m2.x * is;
+        o.agg1[(size_t)P.n + gi] = m2.y * is;
+        // the network's input row (16 BF16): (Q11, Q12, ux/us, uy/us), their deviation from the
+        // support mean, and the 8 tendencies scaled to increments over k dt
+        {
+            const int id = b.mid[gi];
+            const float r[4] = {ui.z, ui.w, ui.x * o.inv_us, ui.y * o.inv_us};
+            const float mr[4] = {m4.z * is, m4.w * is, m4.x * is * o.inv_us, m4.y * is * o.inv_us};
+            float f[16];
+            for (int c = 0; c < 4; c++) {
+                f[c] = r[c];
+                f[4 + c] = mr[c] - r[c];
+            }
+            for (int c = 0; c < 8; c++) f[8 + c] = o.tend_id[(size_t)c * P.n + id] * o.scale[c >> 1];
+            uint4 w[2];
+            __nv_bfloat162 *h2 = reinterpret_cast<__nv_bfloat162 *>(w);
+            for (int c = 0; c < 8; c++) h2[c] = __floats2bfloat162_rn(f[2 * c], f[2 * c + 1]);
+            uint4 *row = reinterpret_cast<uint4 *>(o.X + 16 * (size_t)gi);
+            row[0] = w[0];
+            row[1] = w[1];
+        }
+        o.x[gi] = b.mx[gi];
+        o.y[gi] = b.my[gi];
+        o.u4[gi] = make_float4(ui.x, ui.y, ui.z, ui.w);
+        o.dr[gi] = b.mdr[gi];
+        o.ids[gi] = b.mid[gi];
+    }
+}
+
+// The second support mean of the acceleration and the explicit increment of the surrogate:
+// inc[g] = kdt (m11, m12, agg(agg1)x, agg(agg1)y), with m the recorded Q rate (tend_id planes 2, 3
+// by particle ID); the same walk as the export (run right after it, on the same candidate lists).
+__global__ void __launch_bounds__(PT) k_export_increment(DevParams P, Bufs b, const float *agg1,
+                                                         const float *tend_id, float kdt, float *inc)
+{
+    __shared__ TileShared ts;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float4 *pos = reinterpret_cast<float4 *>(dsm);
+    float2 *sa = reinterpret_cast<float2 *>(pos + HCAP);
+    int *sg = reinterpret_cast<int *>(sa + HCAP);
+    Tile T;
+    if (!tile_begin(P, b, ts, T)) return;
+    for (int t = threadIdx.x; t < T.H; t += PT) {
+        SlotInfo s = slot_info(P, b, ts, T, t);
+        pos[t] = s.e;
+        sg[t] = s.g;
+        sa[t] = make_float2(agg1[s.g], agg1[(size_t)P.n + s.g]);
     }
     __syncthreads();
     for (int q = threadIdx.x; q < T.Ni; q += PT) {
         int si = inner_slot(ts, T, q);
         int gi = sg[si];
         float4 pi = pos[si];
-        // neighbours inside the network radius (2h) first (a walk of their own), then the rest of
-        // the support
-        const float r2net = 4.f / (P.inv_h * P.inv_h);
-        const unsigned long long em = b.emask[gi];
-        int k = 0;
-        float s2 = P.W0;
-        for (int pass = 0; pass < 2; pass++) {
-            for_each_candidate<1>(P, b, gi, em, [&](int off, int, unsigned in) {
-                int j = off >> 4;
-                if (in && j < T.H && k < MAXN) {
-                    float r2 = len2(pair_d(pi, slot_at(pos, off)));
-                    if ((r2 < r2net) == (pass == 0)) {
-                        float w = kernel_w<true>(r2, P);
-                        o.nbr[(size_t)k * P.n + gi] = sg[j];
-                        o.W[(size_t)k * P.n + gi] = w;
-                        if (pass == 0) s2 += w;
-                        k++;
-                    }
-                }
-            });
-            if (pass == 0) o.cnt2[gi] = k;
-        }
-        o.cnt[gi] = k;
-        o.S[gi] = b.sumW[gi];
-        o.S2[gi] = s2;
-        o.x[gi] = b.mx[gi];
-        o.y[gi] = b.my[gi];
-        o.u4[gi] = make_float4(b.mux[gi], b.muy[gi], b.mq11[gi], b.mq12[gi]);
-        o.dr[gi] = b.mdr[gi];
-        o.ids[gi] = b.mid[gi];
+        float2 ai = sa[si];
+        float2 m2 = make_float2(P.W0 * ai.x, P.W0 * ai.y);
+        for_each_candidate<1>(P, b, gi, b.emask[gi], [&](int off, int, unsigned in) {
+            int j = off >> 4;
+            if (in && j < T.H) {
+                float w = kernel_w<true>(len2(pair_d(pi, slot_at(pos, off))), P);
+                float2 aj = slot_at(sa, off);
+                m2.x = fmaf(w, aj.x, m2.x);
+                m2.y = fmaf(w, aj.y, m2.y);
+            }
+        });
+        const float is = 1.f / b.sumW[gi];
+        const int id = b.mid[gi];
+        *reinterpret_cast<float4 *>(inc + 4 * (size_t)gi) =
+            make_float4(kdt * tend_id[2 * (size_t)P.n + id], kdt * tend_id[3 * (size_t)P.n + id], kdt * m2.x * is,
+                        kdt * m2.y * is);
     }
 }
 
@@ -1367,9 +1448,14 @@ cudaError_t enqueue_unpermute(const void *f, const int *id, void *out, int n, in
     return cudaGetLastError();
 }
 
-cudaError_t enqueue_export_graph(const DevParams &P, const Bufs &b, const GraphOut &o, cudaStream_t s)
+cudaError_t enqueue_export_graph(const DevParams &P, const Bufs &b, const GraphOut &o, float kdt, float *inc,
+                                 cudaStream_t s)
 {
-    k_export_graph<<<P.tiles * P.tiles, PT, SMEM_AF, s>>>(P, b, o);
+    cudaError_t e = cudaFuncSetAttribute(k_export_graph, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_EX);
+    if (!e) e = cudaFuncSetAttribute(k_export_increment, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_EX);
+    if (e) return e;
+    k_export_graph<<<P.tiles * P.tiles, PT, SMEM_EX, s>>>(P, b, o);
+    k_export_increment<<<P.tiles * P.tiles, PT, HCAP * (16 + 8 + 4), s>>>(P, b, o.agg1, o.tend_id, kdt, inc);
     return cudaGetLastError();
 }
 

@@ -51,68 +51,6 @@ struct GraphView {
     float W0;
 };
 
-// tend: 8 x n (component-major, sorted order): ax, ay, m11, m12, lapQ11, lapQ12, div u, vort u
-struct TendScales {
-    float a, m, lap, grad;
-};
-
-// Entry q of row i of the ELL.
-__device__ __forceinline__ size_t support_entry(const GraphView &g, int i, int q) { return (size_t)q * g.n + i; }
-
-constexpr int SL = 4;   // lanes per particle in the support means
-
-// Features of every particle, and the first SPH mean of the acceleration (agg1 = agg(ax, ay), two
-// planes) from the same neighbour walk, on the 3h support.  SL lanes per particle take every SL-th
-// neighbour; the partial sums meet by shuffles.
-__global__ void __launch_bounds__(256) k_sg_features(GraphView g, const float4 *u4, float inv_us,
-                                                     const float *tend, TendScales ts, bf16 *X, float *agg1)
-{
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = (int)(t / SL), sub = (int)(t % SL);
-    const bool live = i < g.n;
-    const int ii = live ? i : 0;
-    const float *ax = tend, *ay = tend + g.n;
-    float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // Q11, Q12, ux, uy, ax, ay
-    if (live) {
-        const int m = g.cnt[ii];
-#pragma unroll 2
-        for (int q = sub; q < m; q += SL) {
-            const size_t e = support_entry(g, ii, q);
-            const int j = __ldg(g.nbr + e);
-            const float w = __ldg(g.W + e);
-            const float4 u = __ldg(u4 + j);
-            a[0] += w * u.z;
-            a[1] += w * u.w;
-            a[2] += w * u.x;
-            a[3] += w * u.y;
-            a[4] += w * __ldg(ax + j);
-            a[5] += w * __ldg(ay + j);
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 6; c++) {
-        a[c] += __shfl_xor_sync(0xFFFFFFFFu, a[c], 1);
-        a[c] += __shfl_xor_sync(0xFFFFFFFFu, a[c], 2);
-    }
-    if (!live || sub != 0) return;
-    const float4 s = u4[i];
-    const float is = 1.f / g.S[i];
-    const float r[4] = {s.z, s.w, s.x * inv_us, s.y * inv_us};
-    const float self[4] = {s.z, s.w, s.x, s.y};
-    bf16 *row = X + (size_t)i * F0;
-    for (int c = 0; c < 4; c++) {
-        const float mean = (g.W0 * self[c] + a[c]) * is * (c < 2 ? 1.f : inv_us);
-        row[c] = __float2bfloat16(r[c]);
-        row[4 + c] = __float2bfloat16(mean - r[c]);
-    }
-    for (int c = 0; c < 8; c++) {
-        float sc = c < 2 ? ts.a : (c < 4 ? ts.m : (c < 6 ? ts.lap : ts.grad));
-        row[8 + c] = __float2bfloat16(tend[(size_t)c * g.n + i] * sc);
-    }
-    agg1[i] = (g.W0 * ax[i] + a[4]) * is;
-    agg1[(size_t)g.n + i] = (g.W0 * ay[i] + a[5]) * is;
-}
-
 // The tendencies of the context's last recorded step, into ID order (8 x n, component-major):
 // the accelerations are held in the state order (slot g is particle sid[g]), the recorded Q rate
 // (2 per slot), Laplacian of Q (2) and velocity gradient (4: xx, xy, yx, yy) in the sorted order of
@@ -135,15 +73,6 @@ __global__ void k_sg_tend_from_ctx(int n, const int *sid, const int *mid, const 
     tend[7 * N + m] = d[2] - d[1];
 }
 
-// dst[c n + g] = src[c n + ids[g]] for C planes: ID order into the graph's sorted order.
-__global__ void k_sg_gather_planes(int n, int C, const int *ids, const float *src, float *dst)
-{
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
-    const int i = ids[g];
-    for (int c = 0; c < C; c++) dst[(size_t)c * n + g] = src[(size_t)c * n + i];
-}
-
 // Rows of 4 between the graph's sorted order and ID order: to_id: dst[ids[g]] = src[g] (src row
 // stride ld); from_id: dst[g] = src[ids[g]].
 __global__ void k_sg_rows_to_id(int n, const int *ids, const float *src, int ld, float *dst)
@@ -158,51 +87,6 @@ __global__ void k_sg_rows_from_id(int n, const int *ids, const float *src, float
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
     reinterpret_cast<float4 *>(dst)[g] = reinterpret_cast<const float4 *>(src)[ids[g]];
-}
-
-// out = agg(in) on the 3h support for two FP32 planes (component-major, n apart); SL lanes per
-// particle as in the features.
-__global__ void __launch_bounds__(256) k_sg_mean2(GraphView g, const float *in, float *out)
-{
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = (int)(t / SL), sub = (int)(t % SL);
-    const bool live = i < g.n;
-    const int ii = live ? i : 0;
-    const float *fx = in, *fy = in + g.n;
-    float sx = 0.f, sy = 0.f;
-    if (live) {
-        const int m = g.cnt[ii];
-#pragma unroll 2
-        for (int q = sub; q < m; q += SL) {
-            const size_t e = support_entry(g, ii, q);
-            const int j = __ldg(g.nbr + e);
-            const float w = __ldg(g.W + e);
-            sx += w * __ldg(fx + j);
-            sy += w * __ldg(fy + j);
-        }
-    }
-    sx += __shfl_xor_sync(0xFFFFFFFFu, sx, 1);
-    sx += __shfl_xor_sync(0xFFFFFFFFu, sx, 2);
-    sy += __shfl_xor_sync(0xFFFFFFFFu, sy, 1);
-    sy += __shfl_xor_sync(0xFFFFFFFFu, sy, 2);
-    if (!live || sub != 0) return;
-    const float is = 1.f / g.S[i];
-    out[i] = (g.W0 * fx[i] + sx) * is;
-    out[(size_t)g.n + i] = (g.W0 * fy[i] + sy) * is;
-}
-
-// inc[i] = k dt (m11, m12, agg(agg(a))x, agg(agg(a))y)[i]: the explicit increment in the order of
-// the outputs (dQ11, dQ12, dux, duy); aa holds agg(agg(a)).  Only the acceleration is smoothed:
-// the viscous term is the stiff one at the step's dt, and two passes of the SPH mean take out the
-// velocity modes (compressive ones near a fifth of the lattice wavenumber the last to go) that
-// k dt would amplify; the Q rate is mostly the particle-local bulk term and is used as it is.
-__global__ void k_sg_euler(int n, const float *tend, const float *aa, float kdt, float *inc)
-{
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float4 r = make_float4(kdt * tend[(size_t)2 * n + i], kdt * tend[(size_t)3 * n + i], kdt * aa[i],
-                           kdt * aa[(size_t)n + i]);
-    *(float4 *)(inc + (size_t)i * NOUT) = r;
 }
 
 __device__ __forceinline__ void fma8_bf16(float *acc, uint4 r, float w)
@@ -428,9 +312,9 @@ struct ann_surrogate {
     std::string last_err;
     // graph and state in the context's cell-sorted order (row g is particle ids[g]); tend_id and
     // io4 hold ID-ordered tendencies and host rows on their way in or out
-    int *nbr = nullptr, *cnt = nullptr, *cnt2 = nullptr, *ids = nullptr;
-    float *W = nullptr, *S = nullptr, *S2 = nullptr, *dr = nullptr, *tend = nullptr, *inc = nullptr, *tend_id = nullptr,
-          *io4 = nullptr;
+    int *nbr = nullptr, *cnt2 = nullptr, *ids = nullptr;
+    float *W = nullptr, *S2 = nullptr, *dr = nullptr, *inc = nullptr, *tend_id = nullptr, *io4 = nullptr,
+          *agg1 = nullptr;
     double *x = nullptr, *y = nullptr;
     float4 *u4 = nullptr;
     float W0 = 0.f;
@@ -477,8 +361,6 @@ int scuda(ann_surrogate *S, cudaError_t e, const char *where)
                  std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-// The SPH support (3h): the features' mean and the explicit increment.
-GraphView view(const ann_surrogate *S) { return GraphView{S->nbr, S->W, S->cnt, S->S, S->n, S->W0}; }
 // The network's graph (neighbours closer than 2h, the first cnt2 entries of each row).
 GraphView view_net(const ann_surrogate *S) { return GraphView{S->nbr, S->W, S->cnt2, S->S2, S->n, S->W0}; }
 
@@ -614,9 +496,9 @@ int ann_surrogate_create(int64_t n_max, ann_surrogate **out)
     size_t n = (size_t)n_max, K2 = WIDTH + MSG;
     cudaError_t e = cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking);
 #define SA_(p, c) if (!e) e = sg_alloc(S, S->p, c)
-    SA_(nbr, (size_t)MAXN * n); SA_(W, (size_t)MAXN * n); SA_(cnt, n); SA_(S, n); SA_(dr, n);
-    SA_(cnt2, n); SA_(S2, n);
-    SA_(x, n); SA_(y, n); SA_(u4, n); SA_(tend, 8 * n); SA_(inc, 4 * n); SA_(ids, n); SA_(tend_id, 8 * n);
+    SA_(nbr, (size_t)MAXN * n); SA_(W, (size_t)MAXN * n); SA_(dr, n); SA_(cnt2, n); SA_(S2, n);
+    SA_(agg1, 2 * n);
+    SA_(x, n); SA_(y, n); SA_(u4, n); SA_(inc, 4 * n); SA_(ids, n); SA_(tend_id, 8 * n);
     SA_(io4, 4 * n);
     SA_(X0, n * F0); SA_(AX, n * F0); SA_(H1, n * WIDTH); SA_(Z1, n * MSG); SA_(AZ1, n * MSG);
     SA_(H2, n * WIDTH); SA_(Z2, n * MSG); SA_(AZ2, n * MSG); SA_(H3, n * WIDTH);
@@ -710,20 +592,14 @@ int ann_surrogate_load(ann_surrogate *S, ann_ctx *ctx, const float *tend)
     S->dt = v.P.dt_d;
     S->rho0 = v.P.rho0;
     S->gammaK = (double)v.P.Gamma * (double)v.P.K;
-    GraphOut o{S->nbr, S->W, S->cnt, S->cnt2, S->S, S->S2, S->x, S->y, S->u4, S->dr, S->ids};
+    const double kdt = S->k * S->dt;
+    GraphOut o{S->nbr, S->W, S->cnt2, S->S2, S->x, S->y, S->u4, S->dr, S->ids, S->agg1, S->tend_id, S->X0,
+               (float)(1.0 / S->us),
+               {(float)(kdt / S->ysu), (float)(kdt / S->ysq), (float)(S->gammaK * kdt / S->ysq), (float)kdt}};
+    // the export forms the support means of (u, Q) and a and the network's input rows; its second
+    // walk gives the explicit increment k dt (m11, m12, agg(agg(a)))
     cudaError_t e = cudaStreamSynchronize(v.stream);
-    if (!e) e = enqueue_export_graph(v.P, v.b, o, S->s);
-    if (!e) {
-        k_sg_gather_planes<<<nb(S->n), 256, 0, S->s>>>(S->n, 8, S->ids, S->tend_id, S->tend);
-        double kdt = S->k * S->dt;
-        TendScales ts{(float)(kdt / S->ysu), (float)(kdt / S->ysq), (float)(S->gammaK * kdt / S->ysq), (float)kdt};
-        // dH is scratch between here and the next backward pass
-        k_sg_features<<<nb((size_t)S->n * SL), 256, 0, S->s>>>(view(S), S->u4, (float)(1.0 / S->us), S->tend,
-                                                               ts, S->X0, S->dH);
-        k_sg_mean2<<<nb((size_t)S->n * SL), 256, 0, S->s>>>(view(S), S->dH, S->dH + 2 * (size_t)S->n);
-        k_sg_euler<<<nb(S->n), 256, 0, S->s>>>(S->n, S->tend, S->dH + 2 * (size_t)S->n, (float)kdt, S->inc);
-        e = cudaGetLastError();
-    }
+    if (!e) e = enqueue_export_graph(v.P, v.b, o, (float)kdt, S->inc, S->s);
     if (!e) e = cudaStreamSynchronize(S->s);
     if (e) return scuda(S, e, "ann_surrogate_load");
     S->loaded = true;
