@@ -366,6 +366,37 @@ def ensemble_bench(B, steps=100, trial_steps=10, solo_steps=20):
             "timing": "wall clock around synchronised calls"}
 
 
+def sweep_bench(B, nx=256, zetas=(-0.08, -0.04, 0.04, 0.08, 0.12), Ks=(0.02, 0.04), chunks=3, chunk=1000,
+                M=256):
+    """The activity and elastic-constant sweep of the results section (contractile zeta < 0 and
+    extensile zeta > 0 against K), run as one ensemble of nx^2 members from the same seeded lattice:
+    after every `chunk` steps, each member's defect count (grid M) and mean |Q| (the q field)."""
+    import sph_inputs as si
+
+    spec = [(z, K) for K in Ks for z in zetas]
+    ens = B.ann_ensemble_create([B.ann_default_params(n=nx * nx, h=1.3 / nx, zeta=z, K=K, dt_mode=1) for z, K in spec])
+    rows = [{"zeta": z, "K": K, "defects": [], "mean_q": []} for z, K in spec]
+    try:
+        ic = si.jittered_lattice(nx, seed=77)
+        for k in range(len(spec)):
+            B.ann_set_particles(B.ann_ensemble_member(ens, k), ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"],
+                                ic["q12"], ic["rho"])
+        t0 = time.perf_counter()
+        for c in range(chunks + 1):
+            if c:
+                B.ann_ensemble_step(ens, chunk)
+            for k in range(len(spec)):
+                ctx = B.ann_ensemble_member(ens, k)
+                counts, _ = B.ann_defects(ctx, M)
+                rows[k]["defects"].append(int(counts[0] + counts[1]))
+                rows[k]["mean_q"].append(B.ann_get_diagnostics(ctx)["mean_q"])
+        el = time.perf_counter() - t0
+    finally:
+        B.ann_ensemble_destroy(ens)
+    return {"members": rows, "particles_per_member": nx * nx, "steps": chunks * chunk, "every": chunk, "grid": M,
+            "seconds": el, "workload": f"{len(spec)} members of {nx}^2, zeta x K grid, one ensemble"}
+
+
 SG_K = 8                    # steps one surrogate evaluation spans
 SG_TEND = ("AX", "AY", "QRATE11", "QRATE12", "LAPQ11", "LAPQ12", "GRADU_XX", "GRADU_XY", "GRADU_YX", "GRADU_YY")
 SG_STATE = ("X", "Y", "UX", "UY", "Q11", "Q12", "DRHO")
@@ -872,6 +903,8 @@ def run_ours(args):
         line["surrogate"] = surrogate_bench(B)
     if ws == 1 and not args.no_3d:
         line["three_d"] = three_d_bench(B, nx=args.nx3)
+    if ws == 1 and not args.no_sweep:
+        line["sweep"] = sweep_bench(B)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(NX)
         ms, cores = oracle_grid_ms(NX, DIAG_M)
@@ -897,6 +930,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 64-member ensemble measurement")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
     ap.add_argument("--no-3d", action="store_true", help="skip the three-dimensional variant's measurement")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the activity / elastic-constant sweep")
     ap.add_argument("--nx3", type=int, default=NX3, help="side of the 3D variant's cubic lattice")
     ap.add_argument("--surrogate-cycles", type=int, default=0,
                     help="only run this many surrogate cycles (recorded step + jump) at the headline size, "
