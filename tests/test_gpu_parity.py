@@ -156,14 +156,16 @@ def test_ten_steps_256(B, orc, zeta):
 
 
 @pytest.mark.parametrize("variant", ["conservative", "q_old", "c_half", "no_apd", "beta_half",
-                                     "landau_A", "elastic", "elastic_conservative"])
+                                     "landau_A", "elastic", "elastic_conservative", "contractile"])
 def test_variants_five_steps(B, orc, variant):
     kw = {"conservative": dict(conservative=1, c0_min=0.05), "q_old": dict(q_new_in_momentum=0),
           "c_half": dict(c_shift=0.5), "no_apd": dict(apd=0), "beta_half": dict(beta=0.5),
           "landau_A": dict(A=0.3, C=0.5),
           # Eq. (12) elastic stress, with a B term so that its isotropic part of H enters too
           "elastic": dict(elastic=1, A=0.3, B=0.2, C=0.5),
-          "elastic_conservative": dict(elastic=1, conservative=1, c0_min=0.05, A=0.3, B=0.2, C=0.5)}[variant]
+          "elastic_conservative": dict(elastic=1, conservative=1, c0_min=0.05, A=0.3, B=0.2, C=0.5),
+          # contractile activity (zeta < 0) with a larger elastic constant: the sweeps' other half
+          "contractile": dict(zeta=-0.1, K=0.08)}[variant]
     ic = random_velocity_ic(48, 9, rho_scale=1e-4)
     worst = _ten_steps(B, orc, 48, params(48, **kw), ic, "brute", nsteps=5)
     bad = {k: e for k, e in worst.items() if not e <= TOL}
