@@ -671,6 +671,7 @@ int ann_surrogate_jump(ann_surrogate *S, ann_ctx *ctx, const float *tend)
                                           v.tmp);
     cudaError_t e = cudaGetLastError();
     if (!e) e = cudaStreamSynchronize(S->s);
+    S->loaded = false;   // the context moves on: the next forward needs a new load
     if (e) return scuda(S, e, "ann_surrogate_jump");
     return ctx_reload(ctx, v.tmp, k);
 }

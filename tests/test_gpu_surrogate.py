@@ -264,3 +264,40 @@ def test_training_gains_over_the_method_without_it(B, S):
     assert last < 0.5 * first
     assert summary["net"] < 0.8 * summary["persistence"]
     assert summary["net"] < summary["euler"] and summary["net"] < summary["coarse_step"]
+
+
+def test_jump_applies_the_public_forward(B):
+    """A jump equals what the public calls give on the same state: Q moves by the explicit increment
+    plus ys_q times the forward output (to the FP32 rounding of Q), u by the increment alone, and
+    the loaded graph is consumed."""
+    nx, k = 48, 8
+    ic = si.jittered_lattice(nx, seed=8)
+    r = si.uniform53(18, 2 * ic["n"]).reshape(2, -1) - 0.5
+    ic["ux"], ic["uy"] = 0.02 * r[0], 0.02 * r[1]
+    p = params(nx)
+    p["dt"] = stable_dt(p)
+    n = ic["n"]
+    ctx = B.ann_create(gpu_params(B, p, n))
+    sg = B.ann_surrogate_create(n)
+    try:
+        _load(B, ctx, ic)
+        B.ann_set_record(ctx, 1)
+        B.ann_step(ctx, 2)
+        s0 = {f: B.ann_get_field(ctx, f, n).astype(np.float64) for f in ("Q11", "Q12", "UX", "UY")}
+        B.ann_surrogate_init(sg, 5)
+        ysq, ysu = 1e-3, 1e-5
+        B.ann_surrogate_set_scales(sg, 0.01, ysq, ysu, k)
+        B.ann_surrogate_load(sg, ctx, None)
+        y = B.ann_surrogate_forward(sg, n).astype(np.float64)
+        inc = B.ann_surrogate_euler(sg, n).astype(np.float64)
+        B.ann_surrogate_jump(sg, ctx, None)
+        s1 = {f: B.ann_get_field(ctx, f, n).astype(np.float64) for f in ("Q11", "Q12", "UX", "UY")}
+        with pytest.raises(B.AnnError):
+            B.ann_surrogate_forward(sg, n)
+    finally:
+        B.ann_surrogate_destroy(sg)
+        B.ann_destroy(ctx)
+    ulp = 2.0 ** -23 * max(np.abs(s1["Q11"]).max(), np.abs(s1["Q12"]).max())
+    corr = np.stack([s1["Q11"] - s0["Q11"] - inc[:, 0], s1["Q12"] - s0["Q12"] - inc[:, 1]], axis=1)
+    assert np.abs(corr - ysq * y[:, :2]).max() < 4 * ulp
+    assert np.abs(s1["UX"] - s0["UX"] - inc[:, 2]).max() < 1e-7 and np.abs(s1["UY"] - s0["UY"] - inc[:, 3]).max() < 1e-7
