@@ -3,12 +3,13 @@
 // SPH operators with a 3x3 correction tensor, the viscous term with 2 (d + 2) nu = 10 nu.
 //
 // One step (modified Euler, §3.1), all on the device, one thread per particle:
-//   predict     u += dt/2 a, r += dt/2 u (wrap), max |u|, cell of each particle, cell counts
-//   scan        cell starts (one block)
-//   scatter     particle order by cell; each cell's slots sorted by particle ID (deterministic)
-//   gather      state into the new order (buffer set M)
-//   neighbours  lists of j with |r_i - r_j| < 3h from the 27 surrounding cells (FP64 differences),
-//               sum W, V = 1 / sum W (Eq. 19)
+//   predict     u += dt/2 a, r += dt/2 u (wrap), max |u|; the re-sort test (a particle has moved
+//               half the skin since the last re-sort)
+//   re-sort only: cell keys and counts, scan (one block), scatter, each cell's slots sorted by
+//               particle ID (deterministic), gather into the new order (buffer set M), candidate
+//               lists: every j within 3h (1 + skin) in the 27 surrounding cells
+//   filter      neighbour lists (|r_i - r_j| < 3h among the candidates; FP32 test, FP64 in a band
+//               around 3h), sum W, V = 1 / sum W (Eq. 19)
 //   correction  alpha (Eq. 22) and B = alpha^-1
 //   pass 1      continuity k (Eq. 25), rho_half, corrected velocity gradient (Eq. 20), corrected
 //               Laplacian of Q (Eq. 21), Q rate m (Eqs. 2, 7, 24), Q^{n+1}
@@ -16,7 +17,9 @@
 //   pass 3      momentum (Eq. 23), artificial displacement (Eq. 29), corrector; the new state is
 //               written into buffer set S in the new order
 // The state lives in S between steps, in the cell order of the last step.  Errors are sticky bits
-// set by the kernels' own checks (neighbour overflow, non-finite state, singular alpha).
+// set by the kernels' own checks (neighbour overflow, non-finite state, singular alpha).  The pair
+// loops read each neighbour through a few 16-byte loads of packed per-particle records, written by
+// the kernel that produces them.
 #include "../../include/ann.h"
 
 #include <cuda_runtime.h>
@@ -31,13 +34,14 @@ namespace {
 
 constexpr int MAXN3 = ANN3_MAX_NEIGHBORS;
 constexpr int MAXC3 = 576;          // candidates: neighbours within 3h (1 + SKIN3) at the last re-sort
+static_assert(MAXN3 % 4 == 0 && MAXC3 % 4 == 0, "lists are whole int4 words");
 constexpr double SKIN3 = 0.05;      // candidate lists stay valid while no particle moves SKIN3 3h / 2
 constexpr uint32_t E3_NBR = 4u, E3_NONFINITE = 8u, E3_ALPHA = 16u;
 
 struct P3 {
     int n, nc, ncell;
     double L, inv_cell, cell, R2d, half_dt_d;
-    float h, inv_h, ad, W0, dt, half_dt, cell_f, R2lo, R2hi, R2c;
+    float h, inv_h, ad, adh, W0, dt, half_dt, cell_f, R2lo, R2hi, R2c;
     double skin_max2;
     float rho0, nu, Gamma, lambda, A, B, C, K, zeta, gamma_eos, beta, c0_min, c_shift;
     int apd;
@@ -47,16 +51,26 @@ struct Set3 {   // one buffer set of the state
     double *x, *y, *z;
     float *u[3], *q[5], *dr, *a[3];   // dr: density deviation rho / rho0 - 1 (FP32 keeps its digits)
     int *id;
-    float4 *xi;   // (gathered set only) position relative to the corner of the particle's cell, FP32
+    float4 *xi;   // (gathered set only) position relative to the corner of the particle's cell, FP32;
+                  // w holds the bits of cxyz, so one load gives a neighbour's geometry
     int *cxyz;    // (gathered set only) cell coordinates cx | cy << 10 | cz << 20
 };
 
+// Neighbour and candidate lists: entry k of particle i is component k % 4 of the int4 word
+// list[(k / 4) n + i], so a warp reads 32 consecutive words per load and a thread four entries.
 struct Work3 {
-    int *key, *slot, *perm, *count, *start, *nbr, *nnbr, *cand, *ncand;
+    int *key, *slot, *perm, *count, *start, *nnbr, *ncand;
+    int4 *nbr, *cand;
     double *xr, *yr, *zr;   // positions at the last re-sort (sorted order)
     unsigned *flag;         // non-zero: this step re-sorts and rebuilds the candidate lists
     unsigned *rebuilds;
     float *sumW, *V, *B, *k, *dh, *dhat, *p, *qn, *an, *gu, *lap, *m;   // dh, dhat: deviations of rho_half, rho_hat
+    // what the pair loops read of a neighbour j, packed so that one 16-byte load brings four values:
+    float4 *vu;    // (V, u) at the midpoint                                     written by the filter
+    float4 *q4;    // (Q11, Q12, Q13, Q22) of the midpoint state (Q23: M.q[4])   written by the filter
+    float4 *vpu;   // (V, p / rho_hat^2, u_x, u_y)                               written by pass 2
+    float4 *uqn;   // (u_z, Q^{n+1}_11, Q^{n+1}_12, Q^{n+1}_13)                   written by pass 1
+    float2 *qn2;   // (Q^{n+1}_22, Q^{n+1}_23)                                   written by pass 1
     unsigned *umax, *err;
 };
 
@@ -74,29 +88,6 @@ __device__ __forceinline__ double wrap(double v, double L)
     if (w < 0.0) w = 0.0;
     return w;
 }
-
-// Quintic kernel (Eq. 18) and its derivative in b = r / h, times the 3D constant.
-__device__ __forceinline__ float w_of(float b, float ad)
-{
-    float t3 = fmaxf(3.f - b, 0.f), t2 = fmaxf(2.f - b, 0.f), t1 = fmaxf(1.f - b, 0.f);
-    float t3_2 = t3 * t3, t2_2 = t2 * t2, t1_2 = t1 * t1;
-    return ad * (t3_2 * t3_2 * t3 - 6.f * t2_2 * t2_2 * t2 + 15.f * t1_2 * t1_2 * t1);
-}
-
-__device__ __forceinline__ float dw_of(float b, float ad)
-{
-    float t3 = fmaxf(3.f - b, 0.f), t2 = fmaxf(2.f - b, 0.f), t1 = fmaxf(1.f - b, 0.f);
-    float t3_2 = t3 * t3, t2_2 = t2 * t2, t1_2 = t1 * t1;
-    return ad * (-5.f * t3_2 * t3_2 + 30.f * t2_2 * t2_2 - 75.f * t1_2 * t1_2);
-}
-
-// Pair data of i and j: d = r_i - r_j, r, W, grad_i W.  d is taken from the FP32 positions
-// relative to each particle's cell corner and the (periodic) cell offset, which is -1, 0 or 1
-// cell per axis for neighbours: d = xi_i - xi_j + (c_i - c_j) cell.  The cell-local offsets carry
-// the FP64 positions to about 1e-9 (cells of side ~0.04 L), so d is good to ~1e-7 relative.
-struct Pair3 {
-    float d[3], r, W, g[3];
-};
 
 __device__ __forceinline__ int cell_step(int dc, int nc) { return dc > 1 ? dc - nc : (dc < -1 ? dc + nc : dc); }
 
@@ -116,26 +107,133 @@ __device__ __forceinline__ Here3 here_of(const Set3 &M, int i)
     return h;
 }
 
-__device__ __forceinline__ Pair3 pair_of(const P3 &P, const Set3 &M, const Here3 &h, int j)
+// Pair geometry of i and j: d = r_i - r_j, |d|^2, 1/|d| and |d|.  d is taken from the FP32
+// positions relative to each particle's cell corner and the (periodic) cell offset, which is -1, 0
+// or 1 cell per axis for neighbours: d = xi_i - xi_j + (c_i - c_j) cell.  The cell-local offsets
+// carry the FP64 positions to about 1e-9 (cells of side ~0.04 L), so d is good to ~1e-7 relative.
+struct Geo3 {
+    float d[3], r2, rinv, r;
+};
+
+__device__ __forceinline__ Geo3 geo_of(const P3 &P, const Here3 &h, const float4 xj)
 {
-    Pair3 p;
-    const float4 xj = __ldg(M.xi + j);
-    const int cj = __ldg(M.cxyz + j);
-    p.d[0] = (h.xi.x - xj.x) + (float)cell_step(h.cx - (cj & 1023), P.nc) * P.cell_f;
-    p.d[1] = (h.xi.y - xj.y) + (float)cell_step(h.cy - ((cj >> 10) & 1023), P.nc) * P.cell_f;
-    p.d[2] = (h.xi.z - xj.z) + (float)cell_step(h.cz - (cj >> 20), P.nc) * P.cell_f;
-    p.r = sqrtf(p.d[0] * p.d[0] + p.d[1] * p.d[1] + p.d[2] * p.d[2]);
-    float b = p.r * P.inv_h;
-    p.W = w_of(b, P.ad);
-    float f = dw_of(b, P.ad) * P.inv_h / p.r;
-    for (int c = 0; c < 3; c++) p.g[c] = f * p.d[c];
-    return p;
+    Geo3 g;
+    const int cj = __float_as_int(xj.w);
+    g.d[0] = (h.xi.x - xj.x) + (float)cell_step(h.cx - (cj & 1023), P.nc) * P.cell_f;
+    g.d[1] = (h.xi.y - xj.y) + (float)cell_step(h.cy - ((cj >> 10) & 1023), P.nc) * P.cell_f;
+    g.d[2] = (h.xi.z - xj.z) + (float)cell_step(h.cz - (cj >> 20), P.nc) * P.cell_f;
+    g.r2 = g.d[0] * g.d[0] + g.d[1] * g.d[1] + g.d[2] * g.d[2];
+    g.rinv = rsqrtf(g.r2);
+    g.r = g.r2 * g.rinv;
+    return g;
 }
 
-__device__ __forceinline__ void bg_of(const float *B, const float g[3], float out[3])
+// Quintic kernel (Eq. 18) times the 3D constant: W(r), and F with grad_i W = F d (F = W'(r) / r).
+__device__ __forceinline__ float w3(const P3 &P, const Geo3 &g)
 {
-    for (int a = 0; a < 3; a++) out[a] = B[3 * a] * g[0] + B[3 * a + 1] * g[1] + B[3 * a + 2] * g[2];
+    const float b = g.r * P.inv_h;
+    const float t3 = fmaxf(3.f - b, 0.f), t2 = fmaxf(2.f - b, 0.f), t1 = fmaxf(1.f - b, 0.f);
+    const float s3 = t3 * t3, s2 = t2 * t2, s1 = t1 * t1;
+    return P.ad * (s3 * s3 * t3 - 6.f * s2 * s2 * t2 + 15.f * s1 * s1 * t1);
 }
+
+__device__ __forceinline__ float f3(const P3 &P, const Geo3 &g)
+{
+    const float b = g.r * P.inv_h;
+    const float t3 = fmaxf(3.f - b, 0.f), t2 = fmaxf(2.f - b, 0.f), t1 = fmaxf(1.f - b, 0.f);
+    const float s3 = t3 * t3, s2 = t2 * t2, s1 = t1 * t1;
+    return P.adh * (30.f * s2 * s2 - 5.f * s3 * s3 - 75.f * s1 * s1) * g.rinv;
+}
+
+__device__ __forceinline__ void wf3(const P3 &P, const Geo3 &g, float &W, float &F)
+{
+    const float b = g.r * P.inv_h;
+    const float t3 = fmaxf(3.f - b, 0.f), t2 = fmaxf(2.f - b, 0.f), t1 = fmaxf(1.f - b, 0.f);
+    const float s3 = t3 * t3, s2 = t2 * t2, s1 = t1 * t1;
+    const float q3 = s3 * s3, q2 = s2 * s2, q1 = s1 * s1;
+    W = P.ad * (q3 * t3 - 6.f * q2 * t2 + 15.f * q1 * t1);
+    F = P.adh * (30.f * q2 - 5.f * q3 - 75.f * q1) * g.rinv;
+}
+
+// out = B d (B row-major, held in registers)
+__device__ __forceinline__ void bd_of(const float B[9], const float d[3], float out[3])
+{
+    for (int a = 0; a < 3; a++) out[a] = B[3 * a] * d[0] + B[3 * a + 1] * d[1] + B[3 * a + 2] * d[2];
+}
+
+__device__ __forceinline__ void load_b(const Work3 &w, int i, float B[9])
+{
+    const float *p = w.B + 9 * (size_t)i;
+    for (int c = 0; c < 9; c++) B[c] = p[c];
+}
+
+// Occupancy hints of the pair kernels (minimum resident blocks of 256 threads per SM; 0 leaves the
+// register budget to the compiler) and the list-word prefetch distance (words of four entries).
+// The defaults are the measured best on GB300 at 96^3: passes 1 and 3 keep ~125 registers (two
+// blocks per SM), because the four independent neighbours of a list word, loaded together, hide
+// the gather latency better than more resident warps with fewer registers each would.
+#ifndef ANN3_MINB_F
+#define ANN3_MINB_F 4
+#endif
+#ifndef ANN3_MINB_1
+#define ANN3_MINB_1 2
+#endif
+#ifndef ANN3_MINB_3
+#define ANN3_MINB_3 2
+#endif
+#ifndef ANN3_PF
+#define ANN3_PF 1
+#endif
+#define ANN3_BOUNDS(minb) __launch_bounds__(256, (minb) > 0 ? (minb) : 1)
+
+// Visit entries 0 .. m - 1 of particle i's list in order, fn(entry, k), keeping the next ANN3_PF
+// words in flight while the current one is processed; word w is loaded only when 4 w < m.
+template <typename Fn>
+__device__ __forceinline__ void for_each_entry(const int4 *list, int n, int i, int m, Fn &&fn)
+{
+    constexpr int PF = ANN3_PF;
+    static_assert(PF >= 1 && PF <= 3, "prefetch distance");
+    const int4 *p = list + i;
+    int4 r[PF + 1];
+#pragma unroll
+    for (int t = 0; t <= PF; t++) r[t] = (4 * t < m) ? __ldg(p + (size_t)t * n) : make_int4(0, 0, 0, 0);
+    p += (size_t)(PF + 1) * n;
+    int k = 0;
+    for (; k + 3 < m; k += 4) {
+        const int4 e = r[0];
+#pragma unroll
+        for (int t = 0; t < PF; t++) r[t] = r[t + 1];
+        r[PF] = (k + 4 * (PF + 1) < m) ? __ldg(p) : make_int4(0, 0, 0, 0);
+        p += n;
+        fn(e.x, k);
+        fn(e.y, k + 1);
+        fn(e.z, k + 2);
+        fn(e.w, k + 3);
+    }
+    if (k < m) fn(r[0].x, k);
+    if (k + 1 < m) fn(r[0].y, k + 1);
+    if (k + 2 < m) fn(r[0].z, k + 2);
+}
+
+// Builds a list in the int4 layout one entry at a time: four entries are written as one word.
+struct ListWriter {
+    int4 *list;
+    int n, i, k = 0;
+    int4 acc = make_int4(0, 0, 0, 0);
+    __device__ ListWriter(int4 *l, int n_, int i_) : list(l), n(n_), i(i_) {}
+    __device__ __forceinline__ void push(int j)
+    {
+        acc = make_int4(acc.y, acc.z, acc.w, j);
+        if ((++k & 3) == 0) list[(size_t)(k / 4 - 1) * n + i] = acc;
+    }
+    __device__ __forceinline__ void finish()   // writes the last, partial word (unused entries 0)
+    {
+        if (k & 3) {
+            for (int t = k & 3; t < 4; t++) acc = make_int4(acc.y, acc.z, acc.w, 0);
+            list[(size_t)(k / 4) * n + i] = acc;
+        }
+    }
+};
 
 __device__ __forceinline__ int cell_of(const P3 &P, double x, double y, double z)
 {
@@ -187,7 +285,7 @@ __global__ void k3_predict(P3 P, Set3 S, Set3 M, Work3 w)
             int cc = M.cxyz[i];
             int cx = cc & 1023, cy = (cc >> 10) & 1023, cz = cc >> 20;
             M.xi[i] = make_float4((float)min_image(x - cx * P.cell, P.L), (float)min_image(y - cy * P.cell, P.L),
-                                  (float)min_image(z - cz * P.cell, P.L), 0.f);
+                                  (float)min_image(z - cz * P.cell, P.L), __int_as_float(cc));
         }
     }
     for (int o = 16; o > 0; o >>= 1) sp = fmaxf(sp, __shfl_xor_sync(0xFFFFFFFFu, sp, o));
@@ -277,7 +375,8 @@ __global__ void k3_gather(P3 P, const Set3 S, Set3 M, Work3 w)
     const int cx = c % P.nc, cy = (c / P.nc) % P.nc, cz = c / (P.nc * P.nc);
     w.key[g] = c;
     M.cxyz[g] = cx | (cy << 10) | (cz << 20);
-    M.xi[g] = make_float4((float)(x - cx * P.cell), (float)(y - cy * P.cell), (float)(z - cz * P.cell), 0.f);
+    M.xi[g] = make_float4((float)(x - cx * P.cell), (float)(y - cy * P.cell), (float)(z - cz * P.cell),
+                          __int_as_float(M.cxyz[g]));
 }
 
 // ---- neighbours, volumes, correction -------------------------------------------------------------
@@ -291,7 +390,7 @@ __global__ void k3_candidates(P3 P, const Set3 M, Work3 w)
     if (i >= P.n) return;
     if (i == 0) atomicAdd(w.rebuilds, 1u);
     const Here3 h = here_of(M, i);
-    int k = 0;
+    ListWriter out(w.cand, P.n, i);
     bool over = false;
     for (int oz = -1; oz <= 1; oz++)
         for (int oy = -1; oy <= 1; oy++)
@@ -310,13 +409,14 @@ __global__ void k3_candidates(P3 P, const Set3 M, Work3 w)
                     const float4 xj = __ldg(M.xi + j);
                     const float dx = sx - xj.x, dy = sy - xj.y, dz = sz - xj.z;
                     if (dx * dx + dy * dy + dz * dz < P.R2c) {
-                        if (k < MAXC3) w.cand[(size_t)k++ * P.n + i] = j;
+                        if (out.k < MAXC3) out.push(j);
                         else over = true;
                     }
                 }
             }
+    out.finish();
     if (over) atomicOr(w.err, E3_NBR);
-    w.ncand[i] = k;
+    w.ncand[i] = out.k;
     w.xr[i] = M.x[i];
     w.yr[i] = M.y[i];
     w.zr[i] = M.z[i];
@@ -325,39 +425,40 @@ __global__ void k3_candidates(P3 P, const Set3 M, Work3 w)
 // Every step: the neighbours (|r_i - r_j| < 3h; FP32 test, FP64 near 3h as the oracle decides)
 // among the candidates, sum W and V = 1 / sum W (Eq. 19).  Clears the re-sort flag: the gated
 // kernels of this step have run.
-__global__ void k3_filter(P3 P, const Set3 M, Work3 w)
+__global__ void ANN3_BOUNDS(ANN3_MINB_F) k3_filter(P3 P, const Set3 M, Work3 w)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (blockIdx.x == 0 && threadIdx.x == 0) *(volatile unsigned *)w.flag = 0u;
     if (i >= P.n) return;
     const Here3 hi = here_of(M, i);
-    int k = 0;
+    ListWriter out(w.nbr, P.n, i);
     float s = P.W0;
     bool over = false;
-    const int m = w.ncand[i];
-    for (int q = 0; q < m; q++) {
-        const int j = w.cand[(size_t)q * P.n + i];
-        const Pair3 p = pair_of(P, M, hi, j);
-        const float r2 = p.r * p.r;
-        bool in = r2 < P.R2lo;
-        if (!in && r2 < P.R2hi) {
+    for_each_entry(w.cand, P.n, i, w.ncand[i], [&](int j, int) {
+        const Geo3 g = geo_of(P, hi, __ldg(M.xi + j));
+        bool in = g.r2 < P.R2lo;
+        if (!in && g.r2 < P.R2hi) {
             double ex = min_image(M.x[i] - M.x[j], P.L), ey = min_image(M.y[i] - M.y[j], P.L),
                    ez = min_image(M.z[i] - M.z[j], P.L);
             in = ex * ex + ey * ey + ez * ez < P.R2d;
         }
         if (in) {
-            if (k < MAXN3) {
-                w.nbr[(size_t)k++ * P.n + i] = j;
-                s += p.W;
+            if (out.k < MAXN3) {
+                out.push(j);
+                s += w3(P, g);
             } else {
                 over = true;
             }
         }
-    }
+    });
+    out.finish();
     if (over) atomicOr(w.err, E3_NBR);
-    w.nnbr[i] = k;
+    w.nnbr[i] = out.k;
     w.sumW[i] = s;
-    w.V[i] = 1.f / s;
+    const float v = 1.f / s;
+    w.V[i] = v;
+    w.vu[i] = make_float4(v, M.u[0][i], M.u[1][i], M.u[2][i]);
+    w.q4[i] = make_float4(M.q[0][i], M.q[1][i], M.q[2][i], M.q[3][i]);
 }
 
 __global__ void k3_correction(P3 P, const Set3 M, Work3 w)
@@ -365,15 +466,20 @@ __global__ void k3_correction(P3 P, const Set3 M, Work3 w)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
     const Here3 hi = here_of(M, i);
-    float a[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-    int m = w.nnbr[i];
-    for (int k = 0; k < m; k++) {
-        int j = w.nbr[(size_t)k * P.n + i];
-        Pair3 p = pair_of(P, M, hi, j);
-        float vj = w.V[j];
-        for (int s = 0; s < 3; s++)
-            for (int l = 0; l < 3; l++) a[s][l] += -p.d[s] * vj * p.g[l];
-    }
+    // alpha^{sl} = sum_j V_j (-d^s) F d^l is symmetric: six sums
+    float a00 = 0.f, a01 = 0.f, a02 = 0.f, a11 = 0.f, a12 = 0.f, a22 = 0.f;
+    for_each_entry(w.nbr, P.n, i, w.nnbr[i], [&](int j, int) {
+        const Geo3 g = geo_of(P, hi, __ldg(M.xi + j));
+        const float c = -__ldg(w.V + j) * f3(P, g);
+        const float e0 = c * g.d[0], e1 = c * g.d[1], e2 = c * g.d[2];
+        a00 = fmaf(e0, g.d[0], a00);
+        a01 = fmaf(e0, g.d[1], a01);
+        a02 = fmaf(e0, g.d[2], a02);
+        a11 = fmaf(e1, g.d[1], a11);
+        a12 = fmaf(e1, g.d[2], a12);
+        a22 = fmaf(e2, g.d[2], a22);
+    });
+    const float a[3][3] = {{a00, a01, a02}, {a01, a11, a12}, {a02, a12, a22}};
     float det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
                 a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
     if (!(det > 0.f)) atomicOr(w.err, E3_ALPHA);
@@ -438,28 +544,33 @@ __device__ void q_rate3(const P3 &P, const float *q, const float D[3][3], const 
     m5[4] = 0.5f * (m[1][2] + m[2][1]);
 }
 
-__global__ void k3_pass1(P3 P, const Set3 M, Work3 w)
+__global__ void ANN3_BOUNDS(ANN3_MINB_1) k3_pass1(P3 P, const Set3 M, Work3 w)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
     const Here3 hi = here_of(M, i);
-    const float *B = w.B + 9 * (size_t)i;
+    float B[9];
+    load_b(w, i, B);
     float ui[3] = {M.u[0][i], M.u[1][i], M.u[2][i]}, qi[5];
     for (int c = 0; c < 5; c++) qi[c] = M.q[c][i];
+    // rhs[c][l] = sum_j V_j (u_j - u_i)_c F d_l;  grad u = rhs B (Eq. 20)
     float rhs[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, lap[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, kc = 0.f;
-    int m = w.nnbr[i];
-    for (int k = 0; k < m; k++) {
-        int j = w.nbr[(size_t)k * P.n + i];
-        Pair3 p = pair_of(P, M, hi, j);
-        float bg[3], vj = w.V[j];
-        bg_of(B, p.g, bg);
-        float du[3] = {ui[0] - M.u[0][j], ui[1] - M.u[1][j], ui[2] - M.u[2][j]};
-        kc += vj * (du[0] * bg[0] + du[1] * bg[1] + du[2] * bg[2]);
-        for (int c = 0; c < 3; c++)
-            for (int l = 0; l < 3; l++) rhs[c][l] += vj * (-du[c]) * p.g[l];
-        float f = vj * (p.d[0] * bg[0] + p.d[1] * bg[1] + p.d[2] * bg[2]) / (p.r * p.r);
-        for (int c = 0; c < 5; c++) lap[c] += f * (qi[c] - M.q[c][j]);
-    }
+    for_each_entry(w.nbr, P.n, i, w.nnbr[i], [&](int j, int) {
+        const Geo3 g = geo_of(P, hi, __ldg(M.xi + j));
+        const float4 vu = __ldg(w.vu + j), qa = __ldg(w.q4 + j);
+        const float qj[5] = {qa.x, qa.y, qa.z, qa.w, __ldg(M.q[4] + j)};
+        const float vf = vu.x * f3(P, g);   // V_j F
+        float bd[3];
+        bd_of(B, g.d, bd);
+        const float du[3] = {ui[0] - vu.y, ui[1] - vu.z, ui[2] - vu.w};
+        kc = fmaf(vf, du[0] * bd[0] + du[1] * bd[1] + du[2] * bd[2], kc);
+        for (int c = 0; c < 3; c++) {
+            const float e = -vf * du[c];
+            for (int l = 0; l < 3; l++) rhs[c][l] = fmaf(e, g.d[l], rhs[c][l]);
+        }
+        const float f = vf * (g.d[0] * bd[0] + g.d[1] * bd[1] + g.d[2] * bd[2]) * (g.rinv * g.rinv);
+        for (int c = 0; c < 5; c++) lap[c] = fmaf(f, qi[c] - qj[c], lap[c]);
+    });
     float D[3][3];
     for (int c = 0; c < 3; c++)
         for (int b = 0; b < 3; b++) D[c][b] = rhs[c][0] * B[b] + rhs[c][1] * B[3 + b] + rhs[c][2] * B[6 + b];
@@ -467,13 +578,16 @@ __global__ void k3_pass1(P3 P, const Set3 M, Work3 w)
     float k_i = P.rho0 * (1.f + M.dr[i]) * kc;
     w.k[i] = k_i;
     w.dh[i] = M.dr[i] + P.half_dt * k_i / P.rho0;
-    float m5[5];
+    float m5[5], qn[5];
     q_rate3(P, qi, D, lap, m5);
     for (int c = 0; c < 5; c++) {
+        qn[c] = qi[c] + P.dt * m5[c];
         w.m[(size_t)c * P.n + i] = m5[c];
         w.lap[(size_t)c * P.n + i] = lap[c];
-        w.qn[(size_t)c * P.n + i] = qi[c] + P.dt * m5[c];
+        w.qn[(size_t)c * P.n + i] = qn[c];
     }
+    w.uqn[i] = make_float4(ui[2], qn[0], qn[1], qn[2]);
+    w.qn2[i] = make_float2(qn[3], qn[4]);
     for (int c = 0; c < 9; c++) w.gu[(size_t)c * P.n + i] = D[c / 3][c % 3];
 }
 
@@ -486,69 +600,76 @@ __global__ void k3_pass2(P3 P, const Set3 M, Work3 w)
     const Here3 hi = here_of(M, i);
     // Eq. (28) on the deviations (rho0 factors out of the filter)
     float di = w.dh[i], num = 0.f, den = P.W0;
-    int m = w.nnbr[i];
-    for (int k = 0; k < m; k++) {
-        int j = w.nbr[(size_t)k * P.n + i];
-        Pair3 p = pair_of(P, M, hi, j);
-        num += (di - w.dh[j]) * p.W;
-        den += p.W;
-    }
+    for_each_entry(w.nbr, P.n, i, w.nnbr[i], [&](int j, int) {
+        const float W = w3(P, geo_of(P, hi, __ldg(M.xi + j)));
+        num = fmaf(di - __ldg(w.dh + j), W, num);
+        den += W;
+    });
     float dhat = di - P.beta * num / den;
     w.dhat[i] = dhat;
     // Eq. (26): (rho / rho0)^gamma - 1 = expm1(gamma log1p(delta)), accurate for small delta
     float c0 = fmaxf(10.f * __uint_as_float(*w.umax), P.c0_min);
-    w.p[i] = P.rho0 * c0 * c0 / P.gamma_eos * expm1f(P.gamma_eos * log1pf(dhat));
+    const float p = P.rho0 * c0 * c0 / P.gamma_eos * expm1f(P.gamma_eos * log1pf(dhat));
+    const float rho = P.rho0 * (1.f + dhat);
+    w.p[i] = p;
+    w.vpu[i] = make_float4(w.V[i], p / (rho * rho), M.u[0][i], M.u[1][i]);
 }
 
 // ---- pass 3: momentum, artificial displacement, corrector --------------------------------------------
 
-__global__ void k3_pass3(P3 P, const Set3 M, Set3 S, Work3 w)
+__global__ void ANN3_BOUNDS(ANN3_MINB_3) k3_pass3(P3 P, const Set3 M, Set3 S, Work3 w)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
     const Here3 hi = here_of(M, i);
-    const float *B = w.B + 9 * (size_t)i;
+    float B[9];
+    load_b(w, i, B);
     float ri = P.rho0 * (1.f + w.dhat[i]), pri = w.p[i] / (ri * ri);
     float ui[3] = {M.u[0][i], M.u[1][i], M.u[2][i]}, qi[5];
     for (int c = 0; c < 5; c++) qi[c] = w.qn[(size_t)c * P.n + i];
     float Qi[3][3];
     full_q(qi, Qi);
-    float fp[3] = {0.f, 0.f, 0.f}, fv[3] = {0.f, 0.f, 0.f}, dq[3] = {0.f, 0.f, 0.f};
+    // pressure and viscous terms share B grad_i W = F B d:
+    //   fw = sum_j V_j F [ -rho_i (p_i/rho_i^2 + p_j/rho_j^2) + kv (u_ij . d) / r^2 ] B d,  kv = 10 nu rho0 / rho_i
+    const float kv = 10.f * P.nu * P.rho0 / ri;
+    float fw[3] = {0.f, 0.f, 0.f}, dq[3] = {0.f, 0.f, 0.f};
     float su[3] = {0.f, 0.f, 0.f}, sw = P.W0, sr = 0.f, sd[3] = {0.f, 0.f, 0.f};
     // sum_j d / r^3 of Eq. (29) nearly cancels (terms ~1/r^2, sum ~ their imbalance): compensated
     // (Kahan) summation keeps it to FP32 rounding of the sum rather than of the terms
     float sdc[3] = {0.f, 0.f, 0.f};
-    int m = w.nnbr[i];
-    for (int k = 0; k < m; k++) {
-        int j = w.nbr[(size_t)k * P.n + i];
-        Pair3 p = pair_of(P, M, hi, j);
-        float bg[3], vj = w.V[j];
-        bg_of(B, p.g, bg);
-        float rj = P.rho0 * (1.f + w.dhat[j]);
-        float cp = pri + w.p[j] / (rj * rj);
-        float du[3] = {ui[0] - M.u[0][j], ui[1] - M.u[1][j], ui[2] - M.u[2][j]};
-        float ud = du[0] * p.d[0] + du[1] * p.d[1] + du[2] * p.d[2];
-        float r2 = p.r * p.r;
-        float qj[5];
-        for (int c = 0; c < 5; c++) qj[c] = w.qn[(size_t)c * P.n + j];
+    const int m = w.nnbr[i];
+    for_each_entry(w.nbr, P.n, i, m, [&](int j, int) {
+        const Geo3 g = geo_of(P, hi, __ldg(M.xi + j));
+        const float4 vp = __ldg(w.vpu + j), uq = __ldg(w.uqn + j);
+        const float2 q2 = __ldg(w.qn2 + j);
+        float W, F;
+        wf3(P, g, W, F);
+        const float vf = vp.x * F;   // V_j F
+        float bd[3];
+        bd_of(B, g.d, bd);
+        const float du[3] = {ui[0] - vp.z, ui[1] - vp.w, ui[2] - uq.x};
+        const float ud = du[0] * g.d[0] + du[1] * g.d[1] + du[2] * g.d[2];
+        const float rinv2 = g.rinv * g.rinv;
+        const float coef = vf * fmaf(kv, ud * rinv2, -ri * (pri + vp.y));
+        const float qj[5] = {uq.y, uq.z, uq.w, q2.x, q2.y};
         float Qj[3][3];
         full_q(qj, Qj);
+        const float rinv3 = rinv2 * g.rinv;
         for (int c = 0; c < 3; c++) {
-            fp[c] += vj * cp * bg[c];
-            fv[c] += vj * ud / r2 * bg[c];
-            dq[c] += vj * ((Qj[c][0] - Qi[c][0]) * bg[0] + (Qj[c][1] - Qi[c][1]) * bg[1] + (Qj[c][2] - Qi[c][2]) * bg[2]);
-            su[c] += du[c] * p.W;
-            const float y = p.d[c] / (r2 * p.r) - sdc[c];
+            fw[c] = fmaf(coef, bd[c], fw[c]);
+            dq[c] = fmaf(vf, (Qj[c][0] - Qi[c][0]) * bd[0] + (Qj[c][1] - Qi[c][1]) * bd[1] + (Qj[c][2] - Qi[c][2]) * bd[2],
+                         dq[c]);
+            su[c] = fmaf(du[c], W, su[c]);
+            const float y = g.d[c] * rinv3 - sdc[c];
             const float t = sd[c] + y;
             sdc[c] = (t - sd[c]) - y;
             sd[c] = t;
         }
-        sw += p.W;
-        sr += p.r;
-    }
+        sw += W;
+        sr += g.r;
+    });
     float an[3], apd[3] = {0.f, 0.f, 0.f};
-    for (int c = 0; c < 3; c++)
-        an[c] = -ri * fp[c] + 10.f * P.nu * P.rho0 / ri * fv[c] - P.zeta / ri * dq[c];
+    for (int c = 0; c < 3; c++) an[c] = fw[c] - P.zeta / ri * dq[c];
     if (P.apd) {
         float uv = sqrtf(su[0] * su[0] + su[1] * su[1] + su[2] * su[2]) / sw;
         float r0 = m > 0 ? sr / (float)m : 0.f;
@@ -730,6 +851,7 @@ int ann3_create(const ann3_params *p, ann3_ctx **out)
     P.h = (float)p->h;
     P.inv_h = (float)(1.0 / p->h);
     P.ad = (float)(3.0 / (359.0 * 3.14159265358979323846 * p->h * p->h * p->h));   // Eq. (18), d = 3
+    P.adh = P.ad * P.inv_h;
     P.W0 = P.ad * 66.f;                                           // W(0) = a_d (3^5 - 6 2^5 + 15)
     P.dt = (float)p->dt;
     P.half_dt = (float)(0.5 * p->dt);
@@ -757,8 +879,8 @@ int ann3_create(const ann3_params *p, ann3_ctx **out)
     if (!e) e = alloc3(c, w.perm, n);
     if (!e) e = alloc3(c, w.count, (size_t)P.ncell);
     if (!e) e = alloc3(c, w.start, (size_t)P.ncell + 1);
-    if (!e) e = alloc3(c, w.nbr, (size_t)MAXN3 * n);
-    if (!e) e = alloc3(c, w.cand, (size_t)MAXC3 * n);
+    if (!e) e = alloc3(c, w.nbr, (size_t)(MAXN3 / 4) * n);
+    if (!e) e = alloc3(c, w.cand, (size_t)(MAXC3 / 4) * n);
     if (!e) e = alloc3(c, w.ncand, n);
     if (!e) e = alloc3(c, w.xr, n);
     if (!e) e = alloc3(c, w.yr, n);
@@ -778,6 +900,11 @@ int ann3_create(const ann3_params *p, ann3_ctx **out)
     if (!e) e = alloc3(c, w.gu, 9 * n);
     if (!e) e = alloc3(c, w.lap, 5 * n);
     if (!e) e = alloc3(c, w.m, 5 * n);
+    if (!e) e = alloc3(c, w.vu, n);
+    if (!e) e = alloc3(c, w.q4, n);
+    if (!e) e = alloc3(c, w.vpu, n);
+    if (!e) e = alloc3(c, w.uqn, n);
+    if (!e) e = alloc3(c, w.qn2, n);
     if (!e) e = alloc3(c, w.umax, 1);
     if (!e) e = alloc3(c, w.err, 1);
     if (!e) e = alloc3(c, c->tmp, 9 * n);
