@@ -35,6 +35,7 @@
 #ifndef ANN_H
 #define ANN_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -56,6 +57,9 @@ extern "C" {
 #define ANN_ERR_STATE (-9)           /* call out of order (e.g. ann_step before ann_set_particles) */
 #define ANN_ERR_NOT_AVAILABLE (-10)  /* no CUDA device */
 #define ANN_ERR_TOO_LARGE (-11)      /* size beyond the fixed scratch of ann_velocity_moments_noalloc */
+#define ANN_ERR_TIMEOUT (-12)        /* a bounded device wait (a tensor-core completion) expired; the kernel
+                                        returned without its result and the context stays usable */
+#define ANN_ERR_CFL_VIOLATION (-13)  /* dt_mode ANN_DT_CHECK: the step's dt exceeded a stability limit */
 
 /* Limits of the device kernels. */
 #define ANN_MAX_NEIGHBORS 64         /* neighbours per particle */
@@ -68,6 +72,9 @@ extern "C" {
 /* dt_mode */
 #define ANN_DT_FIXED 0               /* dt as given */
 #define ANN_DT_STABLE 1              /* dt = min(dt, 0.125 h^2/nu, 0.125 h^2/(Gamma K), 0.25 h/c0_min), fixed at create */
+#define ANN_DT_CHECK 2               /* dt as given; a step whose dt exceeds min(0.125 h^2/nu,
+                                        0.125 h^2/(Gamma K), 0.25 h/(c0 + max|u|)), with c0 and max|u| of
+                                        that step's midpoint, fails with ANN_ERR_CFL_VIOLATION */
 
 /*
  * Parameters (plain data).  Names follow the paper: rho0 reference density, eta dynamic viscosity
@@ -174,6 +181,24 @@ int ann_grid_info(const ann_params *p, ann_grid *out);
  * Errors: INVALID_ARG, OOM, CUDA, NOT_AVAILABLE. */
 int ann_create(const ann_params *p, ann_ctx **out);
 
+/* Device memory provider for a context, in place of cudaMalloc / cudaFree (for example a host
+ * framework's caching allocator).  alloc returns a device pointer to at least `bytes` bytes on the
+ * current device, 16-byte aligned, or NULL on failure; release frees a pointer alloc returned,
+ * with the same byte count.  `stream` is the context's own stream (a cudaStream_t): memory is used
+ * on it, and a context synchronises it before it releases anything.  Both are called on the
+ * calling thread, from ann_create_with_allocator, ann_destroy and the calls that grow the flow
+ * diagnostics' scratch; `user` is passed through. */
+typedef struct ann_allocator {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*release)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} ann_allocator;
+
+/* ann_create with every device buffer of the context (state, lists, scratch) taken from *a
+ * (NULL: cudaMalloc, the same as ann_create).  Errors: as ann_create; INVALID_ARG if a callback is
+ * NULL or alloc returns a pointer that is not 16-byte aligned; OOM if alloc returns NULL. */
+int ann_create_with_allocator(const ann_params *p, const ann_allocator *a, ann_ctx **out);
+
 /* Free all device memory of ctx.  NULL is ignored. */
 void ann_destroy(ann_ctx *ctx);
 
@@ -191,7 +216,7 @@ int ann_set_particles(ann_ctx *ctx, int64_t n, const double *x, const double *y,
                       int is_device);
 
 /* Advance nsteps >= 0 steps (one CUDA-graph launch per step) and synchronise.  Errors:
- * STATE (no particles), CELL_OVERFLOW, NBR_OVERFLOW, NONFINITE, SINGULAR_ALPHA (device error
+ * STATE (no particles), CELL_OVERFLOW, NBR_OVERFLOW, NONFINITE, SINGULAR_ALPHA, CFL_VIOLATION (device error
  * bits; once one is raised the remaining kernels of the call return without work, so the state is
  * that of the failing step, partly updated; ann_get_diagnostics reports the bits; ann_set_particles
  * or ann_load_state clears them), CUDA. */
@@ -319,8 +344,8 @@ int ann_get_unwrapped(ann_ctx *ctx, const int64_t *ids, int64_t k, double *xy);
  * BF16 tensor-core GEMMs (5th-generation tensor cores) of the learned surrogate; the paper has no
  * counterpart.  All pointers are device pointers; BF16 = 16-bit bfloat (1 sign, 8 exponent, 7
  * mantissa bits); products accumulate in FP32.  The calls are synchronous on `stream` (a
- * cudaStream_t, NULL for the legacy default stream).  Errors: INVALID_ARG (shapes below), CUDA
- * (including a tensor-core completion that did not arrive within its bounded wait), OOM.
+ * cudaStream_t, NULL for the legacy default stream).  Errors: INVALID_ARG (shapes below), CUDA, OOM,
+ * TIMEOUT (a tensor-core completion did not arrive within its bounded wait).
  *
  * ann_bf16_gemm: C[rows x N] = act([A1 | A2] . B^T + bias): A1 rows x K1 and A2 rows x K2 row-major
  * BF16 (A2 NULL when K2 = 0; K1 + K2 = K), B N x K row-major BF16, bias N FP32 or NULL, act = relu
@@ -335,6 +360,14 @@ int ann_get_unwrapped(ann_ctx *ctx, const int64_t *ids, int64_t k, double *xy);
 int ann_bf16_gemm(const void *A1, int32_t K1, const void *A2, int32_t K2, const void *B, int32_t N, int64_t rows,
                   const float *bias, int32_t relu, void *C, int32_t c_bf16, int32_t accumulate, void *stream);
 int ann_bf16_gemm_tn(const void *A, int32_t K, const void *B, int32_t N, int64_t rows, float *C, void *stream);
+
+/* Self-test of the bounded waits of the tensor-core kernels: one device thread polls a
+ * shared-memory mbarrier that nothing completes, gives up after spin_limit polls (1 .. 2^20) and
+ * raises a device flag the way an expired wait of ann_bf16_gemm or the surrogate does; the call
+ * reads the flag and returns ANN_ERR_TIMEOUT, its expected result.  Nothing faults or hangs, and
+ * the device stays usable.  Synchronous on the legacy default stream.  Errors: INVALID_ARG,
+ * NOT_AVAILABLE, CUDA (ANN_OK would mean the wait completed, which is a defect). */
+int ann_check_bounded_wait(uint32_t spin_limit);
 
 /*
  * Learned coarse-step surrogate (the paper has no learned component; this is the project's).  A
@@ -356,8 +389,8 @@ int ann_bf16_gemm_tn(const void *A, int32_t K, const void *B, int32_t N, int64_t
  * dQ = k dt m + ys_q (y0, y1), du = k dt agg(agg(a)) + ys_u (y2, y3); the acceleration is
  * SPH-smoothed twice (the mean removes the velocity modes that an explicit step k times beyond the
  * viscous limit would amplify), the Q rate, mostly the particle-local bulk term, is not; positions
- * advance by k dt (u + u') / 2.  Errors: INVALID_ARG, STATE (nothing loaded), OOM, CUDA (including a
- * tensor-core wait that timed out), NOT_AVAILABLE.
+ * advance by k dt (u + u') / 2.  Errors: INVALID_ARG, STATE (nothing loaded), OOM, CUDA, TIMEOUT (a
+ * tensor-core wait that did not complete within its bound), NOT_AVAILABLE.
  */
 #define ANN_SG_PARAMS 54148
 typedef struct ann_surrogate ann_surrogate;

@@ -73,6 +73,14 @@ FIELDS3 = {"POS": (0, 3), "U": (1, 3), "Q": (2, 5), "RHO": (3, 1), "A": (4, 3), 
            "GRADU": (6, 9), "LAPQ": (7, 5), "QRATE": (8, 5), "P": (9, 1), "NNBR": (10, 1)}
 
 
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class ann_allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("release", _RELEASE_FN), ("user", ctypes.c_void_p)]
+
+
 class AnnError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{msg} (status {status})")
@@ -100,6 +108,8 @@ def lib() -> ctypes.CDLL:
         "ann_validate_params": (i32, [_P(ann_params)]),
         "ann_grid_info": (i32, [_P(ann_params), _P(ann_grid)]),
         "ann_create": (i32, [_P(ann_params), _P(vp)]),
+        "ann_create_with_allocator": (i32, [_P(ann_params), _P(ann_allocator), _P(vp)]),
+        "ann_check_bounded_wait": (i32, [ctypes.c_uint32]),
         "ann_destroy": (None, [vp]),
         "ann_set_stream": (i32, [vp, vp]),
         "ann_set_particles": (i32, [vp, i64, dp, dp, dp, dp, dp, dp, dp, i32]),
@@ -225,9 +235,42 @@ def ann_create(p: ann_params) -> ctypes.c_void_p:
     return ctx
 
 
+# allocators handed to ann_create_with_allocator, kept alive (with their ctypes callbacks) until
+# the context that uses them is destroyed
+_ctx_allocators = {}
+
+
+def ann_create_with_allocator(p: ann_params, a) -> ctypes.c_void_p:
+    """``a``: an ann_allocator (see torch_allocator), or None for cudaMalloc."""
+    ctx = ctypes.c_void_p()
+    _check(lib().ann_create_with_allocator(ctypes.byref(p), ctypes.byref(a) if a is not None else None,
+                                           ctypes.byref(ctx)), what="ann_create_with_allocator")
+    if a is not None:
+        _ctx_allocators[ctx.value] = a
+    return ctx
+
+
+def torch_allocator() -> ann_allocator:
+    """An ann_allocator that takes device memory from PyTorch's CUDA caching allocator, on the
+    context's own stream (memory then counts in torch.cuda.memory_allocated)."""
+    import torch
+
+    def alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except RuntimeError:
+            return None
+
+    def release(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return ann_allocator(_ALLOC_FN(alloc), _RELEASE_FN(release), None)
+
+
 def ann_destroy(ctx) -> None:
     if ctx:
         lib().ann_destroy(ctx)
+        _ctx_allocators.pop(getattr(ctx, "value", ctx), None)
 
 
 def ann_set_stream(ctx, stream) -> None:
@@ -507,6 +550,11 @@ def ann_bf16_gemm_tn(A, B, C, stream=None) -> None:
     handle = getattr(stream, "cuda_stream", stream) if stream is not None else 0
     st = lib().ann_bf16_gemm_tn(_dev(A), K, _dev(B), N, rows, _dev(C), ctypes.c_void_p(int(handle) if handle else 0))
     _check(st, None, "ann_bf16_gemm_tn")
+
+
+def ann_check_bounded_wait(spin_limit: int = 4096) -> int:
+    """Status of the bounded-wait self-test: ANN_ERR_TIMEOUT (-12) is the expected result."""
+    return lib().ann_check_bounded_wait(spin_limit)
 
 
 # ------------------------------------------------------------------ learned surrogate

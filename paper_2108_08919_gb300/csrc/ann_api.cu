@@ -25,7 +25,9 @@ struct ann_ctx {
     int64_t steps = 0;
     double t = 0.0;
     std::string last_err;
-    std::vector<void *> allocs;
+    ann_allocator al{};           // device memory provider (alloc == nullptr: cudaMalloc / cudaFree)
+    bool al_misaligned = false;   // the provider returned a pointer that is not 16-byte aligned
+    std::vector<std::pair<void *, size_t>> allocs;
     void *tmp = nullptr;          // staging: max(7 n doubles, MAXN n ints)
     double *diag_part = nullptr;  // diag_blocks(n) x NDIAG
     double *diag_out = nullptr;   // NDIAG
@@ -66,6 +68,8 @@ const char *status_text(int s)
     case ANN_ERR_STATE: return "call out of order";
     case ANN_ERR_NOT_AVAILABLE: return "no CUDA device";
     case ANN_ERR_TOO_LARGE: return "size beyond the fixed scratch of a no-allocation entry point";
+    case ANN_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case ANN_ERR_CFL_VIOLATION: return "dt above a stability limit (CFL)";
     default: return "unknown status";
     }
 }
@@ -141,7 +145,10 @@ int validate(const ann_params *p, std::string &why)
         return ANN_ERR_INVALID_ARG;
     }
     if (p->q_new_in_momentum != 0 && p->q_new_in_momentum != 1) { why = "q_new_in_momentum must be 0 or 1"; return ANN_ERR_INVALID_ARG; }
-    if (p->dt_mode != ANN_DT_FIXED && p->dt_mode != ANN_DT_STABLE) { why = "unknown dt_mode"; return ANN_ERR_INVALID_ARG; }
+    if (p->dt_mode != ANN_DT_FIXED && p->dt_mode != ANN_DT_STABLE && p->dt_mode != ANN_DT_CHECK) {
+        why = "unknown dt_mode";
+        return ANN_ERR_INVALID_ARG;
+    }
     if (p->elastic_stress != 0 && p->elastic_stress != 1) { why = "elastic_stress must be 0 or 1"; return ANN_ERR_INVALID_ARG; }
     double R = 3.0 * p->h;
     double expected = M_PI * R * R * (double)p->n / (p->L * p->L);
@@ -232,18 +239,49 @@ DevParams make_dev(const ann_params &p)
     d.c0_min = (float)p.c0_min;
     d.c_shift = (float)p.c_shift;
     d.mass = (float)(p.rho0 * p.L * p.L / (double)p.n);
+    d.dt_check = p.dt_mode == ANN_DT_CHECK;
+    {
+        double lim = INFINITY, nu = p.eta / p.rho0;
+        if (nu > 0.0) lim = std::min(lim, 0.125 * p.h * p.h / nu);
+        if (p.Gamma * p.K > 0.0) lim = std::min(lim, 0.125 * p.h * p.h / (p.Gamma * p.K));
+        d.dt_static = (float)lim;
+    }
     return d;
+}
+
+// Device memory of a context: from its ann_allocator when it has one, else cudaMalloc.
+cudaError_t dev_alloc(ann_ctx *c, void **v, size_t bytes)
+{
+    *v = nullptr;
+    if (!c->al.alloc) return cudaMalloc(v, bytes);
+    void *p = c->al.alloc(bytes, (void *)c->own, c->al.user);
+    if (!p) return cudaErrorMemoryAllocation;
+    if ((uintptr_t)p & 15u) {
+        c->al.release(p, bytes, (void *)c->own, c->al.user);
+        c->al_misaligned = true;
+        return cudaErrorInvalidValue;
+    }
+    *v = p;
+    return cudaSuccess;
+}
+
+void dev_free(ann_ctx *c, void *v, size_t bytes)
+{
+    if (!v) return;
+    if (c->al.release) c->al.release(v, bytes, (void *)c->own, c->al.user);
+    else cudaFree(v);
 }
 
 template <typename T>
 cudaError_t dalloc(ann_ctx *c, T *&ptr, size_t count)
 {
     void *v = nullptr;
-    cudaError_t e = cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(T));
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = dev_alloc(c, &v, bytes);
     if (e) return e;
-    c->allocs.push_back(v);
+    c->allocs.emplace_back(v, bytes);
     ptr = static_cast<T *>(v);
-    return cudaMemset(v, 0, std::max<size_t>(count, 1) * sizeof(T));
+    return cudaMemset(v, 0, bytes);
 }
 
 cudaError_t alloc_all(ann_ctx *c)
@@ -367,11 +405,13 @@ int device_status(ann_ctx *c)
     uint32_t bits = *c->h_err;
     if (!bits) return ANN_OK;
     char buf[160];
-    std::snprintf(buf, sizeof buf, "device error bits 0x%x (1 cell, 2 halo, 4 neighbours, 8 non-finite, 16 alpha)", bits);
+    std::snprintf(buf, sizeof buf,
+                  "device error bits 0x%x (1 cell, 2 halo, 4 neighbours, 8 non-finite, 16 alpha, 32 CFL)", bits);
     c->last_err = buf;
     if (bits & EB_NONFINITE) return ANN_ERR_NONFINITE;
     if (bits & (EB_CELL | EB_HALO)) return ANN_ERR_CELL_OVERFLOW;
     if (bits & EB_NBR) return ANN_ERR_NBR_OVERFLOW;
+    if (bits & EB_CFL) return ANN_ERR_CFL_VIOLATION;
     return ANN_ERR_SINGULAR_ALPHA;
 }
 
@@ -497,13 +537,16 @@ int ann_grid_info(const ann_params *p, ann_grid *out)
     return ANN_OK;
 }
 
-int ann_create(const ann_params *p, ann_ctx **out)
+int ann_create(const ann_params *p, ann_ctx **out) { return ann_create_with_allocator(p, nullptr, out); }
+
+int ann_create_with_allocator(const ann_params *p, const ann_allocator *a, ann_ctx **out)
 {
     if (!out) return ANN_ERR_INVALID_ARG;
     *out = nullptr;
     std::string why;
     int s = validate(p, why);
     if (s) return s;
+    if (a && (!a->alloc || !a->release)) return ANN_ERR_INVALID_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -513,6 +556,7 @@ int ann_create(const ann_params *p, ann_ctx **out)
     if (!c) return ANN_ERR_OOM;
     c->prm = *p;
     c->P = make_dev(*p);
+    if (a) c->al = *a;
     cudaError_t e = cudaGetDevice(&c->device);
     if (!e) e = prepare_kernels();
     if (!e) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
@@ -522,7 +566,8 @@ int ann_create(const ann_params *p, ann_ctx **out)
     if (!e) e = capture(c);
     if (!e) e = cudaStreamSynchronize(c->own);
     if (e) {
-        int code = cuda_fail(c, e, "ann_create");
+        int code = c->al_misaligned ? fail(c, ANN_ERR_INVALID_ARG, "ann_create: allocator returned a misaligned pointer")
+                                    : cuda_fail(c, e, "ann_create");
         ann_destroy(c);
         return code;
     }
@@ -535,10 +580,10 @@ void ann_destroy(ann_ctx *c)
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->exec) cudaGraphExecDestroy(c->exec);
-    for (void *v : c->allocs) cudaFree(v);
+    for (auto &v : c->allocs) dev_free(c, v.first, v.second);
     for (ann_ctx::Scratch *sc : {&c->d_grid, &c->d_off, &c->d_fld, &c->d_z, &c->d_zt, &c->d_tw, &c->d_shoff,
                                  &c->d_shmodes, &c->d_out, &c->d_map, &c->d_cnt, &c->d_ids})
-        if (sc->p) cudaFree(sc->p);
+        dev_free(c, sc->p, sc->bytes);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->own) cudaStreamDestroy(c->own);
     if (c->aux) cudaStreamDestroy(c->aux);
@@ -923,14 +968,21 @@ const char *ann_last_error(ann_ctx *c) { return c ? c->last_err.c_str() : ""; }
 
 namespace {
 
-cudaError_t ensure(ann_ctx::Scratch &sc, size_t bytes)
+// Grows a scratch buffer to at least `bytes` (contents are not kept).  The context's stream is
+// synchronised before an old buffer is released.
+cudaError_t ensure(ann_ctx *c, ann_ctx::Scratch &sc, size_t bytes)
 {
-    if (sc.bytes >= bytes) return cudaSuccess;
-    if (sc.p) cudaFree(sc.p);
+    if (sc.p && sc.bytes >= bytes) return cudaSuccess;
+    if (sc.p) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e) return e;
+        dev_free(c, sc.p, sc.bytes);
+    }
     sc.p = nullptr;
     sc.bytes = 0;
-    cudaError_t e = cudaMalloc(&sc.p, std::max<size_t>(bytes, 16));
-    if (!e) sc.bytes = bytes;
+    const size_t cap = std::max<size_t>(bytes, 16);
+    cudaError_t e = dev_alloc(c, &sc.p, cap);
+    if (!e) sc.bytes = cap;
     return e;
 }
 
@@ -970,9 +1022,9 @@ int diag_grid(ann_ctx *c, int M)
     int st = diag_source(c, src);
     if (st) return st;
     size_t n = (size_t)c->P.n, MM = (size_t)M * M;
-    cudaError_t e = ensure(c->d_grid, 5 * MM * sizeof(double));
-    if (!e) e = ensure(c->d_off, n * sizeof(float2));
-    if (!e) e = ensure(c->d_fld, n * sizeof(float4));
+    cudaError_t e = ensure(c, c->d_grid, 5 * MM * sizeof(double));
+    if (!e) e = ensure(c, c->d_off, n * sizeof(float2));
+    if (!e) e = ensure(c, c->d_fld, n * sizeof(float4));
     if (!e) e = enqueue_grid(c->P, c->b, src, M, (float2 *)c->d_off.p, (float4 *)c->d_fld.p, (double *)c->d_grid.p,
                              c->stream);
     if (!e) e = cudaStreamSynchronize(c->stream);
@@ -1001,8 +1053,8 @@ cudaError_t shell_table(ann_ctx *c, int M)
     for (int k = 0; k < ns; k++) cnt[(size_t)k + 1] += cnt[(size_t)k];
     std::vector<int> fill(cnt.begin(), cnt.end() - 1);
     for (size_t i = 0; i < MM; i++) modes[(size_t)fill[(size_t)which[i]]++] = (int)i;
-    cudaError_t e = ensure(c->d_shoff, cnt.size() * sizeof(int));
-    if (!e) e = ensure(c->d_shmodes, MM * sizeof(int));
+    cudaError_t e = ensure(c, c->d_shoff, cnt.size() * sizeof(int));
+    if (!e) e = ensure(c, c->d_shmodes, MM * sizeof(int));
     if (!e) e = cudaMemcpy(c->d_shoff.p, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (!e) e = cudaMemcpy(c->d_shmodes.p, modes.data(), MM * sizeof(int), cudaMemcpyHostToDevice);
     if (!e) c->shell_M = M;
@@ -1041,10 +1093,10 @@ int ann_energy_spectrum(ann_ctx *c, int32_t M, double *E, int32_t nshell)
     int ns = nshell_of(M);
     if (nshell < ns) return fail(c, ANN_ERR_INVALID_ARG, "E holds fewer than ann_spectrum_shells(M) values");
     size_t MM = (size_t)M * M;
-    cudaError_t e = ensure(c->d_z, MM * sizeof(double2));
-    if (!e) e = ensure(c->d_zt, MM * sizeof(double2));
-    if (!e) e = ensure(c->d_tw, (size_t)(M / 2) * sizeof(double2));
-    if (!e) e = ensure(c->d_out, (size_t)std::max(ns, M / 2 + 1) * sizeof(double));
+    cudaError_t e = ensure(c, c->d_z, MM * sizeof(double2));
+    if (!e) e = ensure(c, c->d_zt, MM * sizeof(double2));
+    if (!e) e = ensure(c, c->d_tw, (size_t)(M / 2) * sizeof(double2));
+    if (!e) e = ensure(c, c->d_out, (size_t)std::max(ns, M / 2 + 1) * sizeof(double));
     if (!e && c->tw_M != M) {
         e = enqueue_twiddles(M, (double2 *)c->d_tw.p, c->stream);
         if (!e) c->tw_M = M;
@@ -1086,7 +1138,7 @@ int ann_vorticity_correlation(ann_ctx *c, int32_t M, int32_t all_origins, double
     if (!c || !C || (all_origins != 0 && all_origins != 1)) return ANN_ERR_INVALID_ARG;
     int st = diag_grid(c, M);
     if (st) return st;
-    cudaError_t e = ensure(c->d_out, (size_t)std::max(nshell_of(M), M / 2 + 1) * sizeof(double));
+    cudaError_t e = ensure(c, c->d_out, (size_t)std::max(nshell_of(M), M / 2 + 1) * sizeof(double));
     if (!e) e = enqueue_correlation(M, c->prm.L, (const double *)c->d_grid.p, all_origins, (double *)c->d_out.p,
                                     c->stream);
     if (!e) e = cudaMemcpyAsync(C, c->d_out.p, (size_t)(M / 2 + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
@@ -1108,8 +1160,8 @@ int ann_defects(ann_ctx *c, int32_t M, int64_t *counts, int8_t *map)
     if (st) return st;
     size_t MM = (size_t)M * M;
     unsigned long long h[3];
-    cudaError_t e = ensure(c->d_map, MM);
-    if (!e) e = ensure(c->d_cnt, std::max<size_t>(3 * sizeof(unsigned long long), c->d_cnt.bytes));
+    cudaError_t e = ensure(c, c->d_map, MM);
+    if (!e) e = ensure(c, c->d_cnt, std::max<size_t>(3 * sizeof(unsigned long long), c->d_cnt.bytes));
     if (!e) e = enqueue_defects(M, (const double *)c->d_grid.p, (signed char *)c->d_map.p,
                                 (unsigned long long *)c->d_cnt.p, c->stream);
     if (!e) e = cudaMemcpyAsync(h, c->d_cnt.p, sizeof h, cudaMemcpyDeviceToHost, c->stream);
@@ -1145,7 +1197,7 @@ int ann_mixing_index(ann_ctx *c, int32_t G, double *index, double *per_species)
     if (!c->have_particles) return fail(c, ANN_ERR_STATE, "no particles");
     int S = c->ncolors;
     size_t nb = (size_t)G * G, bytes = nb * S * sizeof(unsigned);
-    cudaError_t e = ensure(c->d_cnt, std::max<size_t>(bytes, 3 * sizeof(unsigned long long)));
+    cudaError_t e = ensure(c, c->d_cnt, std::max<size_t>(bytes, 3 * sizeof(unsigned long long)));
     if (!e) e = enqueue_mixing(c->P, c->b, c->colors, G, S, (unsigned *)c->d_cnt.p, c->stream);
     std::vector<unsigned> cnt(nb * S);
     if (!e) e = cudaMemcpyAsync(cnt.data(), c->d_cnt.p, bytes, cudaMemcpyDeviceToHost, c->stream);
@@ -1194,7 +1246,7 @@ int ann_get_unwrapped(ann_ctx *c, const int64_t *ids, int64_t k, double *xy)
         if (ids[t] < 0 || ids[t] >= c->prm.n) return fail(c, ANN_ERR_INVALID_ARG, "particle ID out of range");
     if (k == 0) return ANN_OK;
     size_t kk = (size_t)k;
-    cudaError_t e = ensure(c->d_ids, kk * (sizeof(long long) + 2 * sizeof(double)));
+    cudaError_t e = ensure(c, c->d_ids, kk * (sizeof(long long) + 2 * sizeof(double)));
     long long *dids = (long long *)c->d_ids.p;
     double *dxy = (double *)(dids + kk);
     if (!e) e = cudaMemcpyAsync(dids, ids, kk * sizeof(long long), cudaMemcpyHostToDevice, c->stream);

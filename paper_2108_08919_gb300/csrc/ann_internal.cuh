@@ -32,6 +32,7 @@ enum : uint32_t {
     EB_NBR = 4u,         // a particle had more than MAXN neighbours
     EB_NONFINITE = 8u,   // NaN / infinity in the state
     EB_SINGULAR = 16u,   // det(alpha) <= 0
+    EB_CFL = 32u,        // dt above a stability limit of the step (dt_mode ANN_DT_CHECK)
 };
 
 // Parameters in the form the kernels use (FP64 where positions are involved).
@@ -52,6 +53,8 @@ struct DevParams {
     float kf5, kf30, kf75; // -5 a_d/h, 30 a_d/h, -75 a_d/h  (F r = kf5 t3^4 + kf30 t2^4 + kf75 t1^4)
     int nsblk;             // blocks of SCAN_CHUNK cells (scan)
     float rho0, nu, mu, Gamma, lambda, A, Bl, C, K, zeta, gamma_eos, beta, c0_min, c_shift, mass;
+    int dt_check;          // ANN_DT_CHECK: pass C tests dt against dt_static and 0.25 h / (c0 + max|u|)
+    float dt_static;       // min(0.125 h^2 / nu, 0.125 h^2 / (Gamma K)) (infinity where a rate is 0)
 };
 
 // Device buffers.  S: state at the end of a step, in the particle order of that step's evaluation.

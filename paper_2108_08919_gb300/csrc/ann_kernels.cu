@@ -831,8 +831,13 @@ __global__ void BOUNDS_C k_pass_c(DevParams P, Bufs b)
         sg[t] = s.g;
     }
     __syncthreads();
-    float c0 = fmaxf(10.f * __uint_as_float(*b.maxu), P.c0_min);
+    const float umax = __uint_as_float(*b.maxu);
+    float c0 = fmaxf(10.f * umax, P.c0_min);
     float pref = P.rho0 * c0 * c0 / P.gamma_eos;
+    // stability limits of this step's dt (a zero speed gives an infinite limit); pass D then stops
+    if (P.dt_check && blockIdx.x == 0 && threadIdx.x == 0 &&
+        (P.dt > P.dt_static || P.dt * (c0 + umax) * P.inv_h > 0.25f))
+        atomicOr(b.err, EB_CFL);
     for (int q = threadIdx.x; q < T.Ni; q += PT) {
         int si = inner_slot(ts, T, q);
         int gi = sg[si];

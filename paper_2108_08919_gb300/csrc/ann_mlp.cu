@@ -103,10 +103,10 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count)
 }
 
 // Bounded wait for the phase `parity` of the mbarrier to complete; false on time-out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, unsigned limit = SPIN_LIMIT)
 {
     uint32_t a = smem_u32(mbar);
-    for (unsigned it = 0; it < SPIN_LIMIT; it++) {
+    for (unsigned it = 0; it < limit; it++) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
@@ -706,7 +706,24 @@ __global__ void __launch_bounds__(128) k_gemm_tn(TnArgs a)
     if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
+// Self-test of the bounded wait: one thread polls an mbarrier that nothing completes (a fresh
+// barrier's phase 0 never finishes) and, after `limit` polls, raises the flag exactly as an
+// expired wait of the tensor-core kernels does.
+__global__ void k_wait_probe(unsigned limit, unsigned *err)
+{
+    __shared__ uint64_t mbar;
+    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&mbar, 0u, limit)) atomicOr(err, 1u);
+}
+
 }  // namespace
+
+cudaError_t enqueue_wait_probe(unsigned limit, unsigned *err, cudaStream_t s)
+{
+    k_wait_probe<<<1, 32, 0, s>>>(limit, err);
+    return cudaGetLastError();
+}
 
 bool gemm_shape_ok(int K, int N) { return K >= 16 && K <= 256 && K % 16 == 0 && N >= 16 && N <= 256 && N % 16 == 0; }
 
@@ -831,10 +848,28 @@ cudaError_t enqueue_gemm_tn(const void *A, int K, const void *B, int N, int rows
 }  // namespace ann
 
 namespace {
-__device__ unsigned g_gemm_err;   // time-out flags of the stand-alone GEMM entry points
+__device__ unsigned g_gemm_err;    // time-out flags of the stand-alone GEMM entry points
+__device__ unsigned g_probe_err;   // flag of ann_check_bounded_wait
 }
 
 extern "C" {
+
+int ann_check_bounded_wait(uint32_t spin_limit)
+{
+    if (spin_limit < 1 || spin_limit > (1u << 20)) return ANN_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return ANN_ERR_NOT_AVAILABLE;
+    }
+    unsigned *err = nullptr, zero = 0, h = 0;
+    cudaError_t e = cudaGetSymbolAddress((void **)&err, g_probe_err);
+    if (!e) e = cudaMemcpy(err, &zero, sizeof zero, cudaMemcpyHostToDevice);
+    if (!e) e = ann::enqueue_wait_probe(spin_limit, err, nullptr);
+    if (!e) e = cudaMemcpy(&h, err, sizeof h, cudaMemcpyDeviceToHost);
+    if (e) return ANN_ERR_CUDA;
+    return h ? ANN_ERR_TIMEOUT : ANN_OK;
+}
 
 int ann_bf16_gemm(const void *A1, int32_t K1, const void *A2, int32_t K2, const void *B, int32_t N, int64_t rows,
                   const float *bias, int32_t relu, void *C, int32_t c_bf16, int32_t accumulate, void *stream)
@@ -853,7 +888,7 @@ int ann_bf16_gemm(const void *A1, int32_t K1, const void *A2, int32_t K2, const 
     if (!e) e = cudaMemcpyAsync(&h, err, sizeof h, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return e == cudaErrorMemoryAllocation ? ANN_ERR_OOM : ANN_ERR_CUDA;
-    return h ? ANN_ERR_CUDA : ANN_OK;
+    return h ? ANN_ERR_TIMEOUT : ANN_OK;
 }
 
 int ann_bf16_gemm_tn(const void *A, int32_t K, const void *B, int32_t N, int64_t rows, float *C, void *stream)
@@ -868,7 +903,7 @@ int ann_bf16_gemm_tn(const void *A, int32_t K, const void *B, int32_t N, int64_t
     if (!e) e = cudaMemcpyAsync(&h, err, sizeof h, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) return e == cudaErrorMemoryAllocation ? ANN_ERR_OOM : ANN_ERR_CUDA;
-    return h ? ANN_ERR_CUDA : ANN_OK;
+    return h ? ANN_ERR_TIMEOUT : ANN_OK;
 }
 
 }  // extern "C"

@@ -476,7 +476,7 @@ int check_err(ann_surrogate *S, const char *where)
     cudaError_t e = cudaMemcpyAsync(&h, S->err, sizeof h, cudaMemcpyDeviceToHost, S->s);
     if (!e) e = cudaStreamSynchronize(S->s);
     if (e) return scuda(S, e, where);
-    if (h) return sfail(S, ANN_ERR_CUDA, std::string(where) + ": a tensor-core wait timed out");
+    if (h) return sfail(S, ANN_ERR_TIMEOUT, std::string(where) + ": a tensor-core wait timed out");
     return ANN_OK;
 }
 

@@ -39,7 +39,8 @@ def test_every_declared_symbol_is_exported(B):
 def test_struct_layouts_match_header(B, tmp_path):
     """ctypes mirrors of the header structs have the C compiler's sizes and field offsets."""
     import subprocess
-    structs = {"ann_params": B.ann_params, "ann_grid": B.ann_grid, "ann_diag": B.ann_diag}
+    structs = {"ann_params": B.ann_params, "ann_grid": B.ann_grid, "ann_diag": B.ann_diag,
+               "ann_allocator": B.ann_allocator}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ann.h"', "int main(void) {"]
     for sname, cls in structs.items():
         lines.append(f'printf("{sname} sizeof %zu\\n", sizeof({sname}));')
@@ -114,6 +115,29 @@ def test_stable_dt(B):
     assert g.dt_effective == pytest.approx(0.125 * (1.3 / 256) ** 2 / 1.0)
     p.dt_mode = 0
     assert B.ann_grid_info(p).dt_effective == 1e-4
+
+
+def test_dt_check_mode_and_new_status_codes(B):
+    p = B.ann_default_params(dt_mode=2)   # ANN_DT_CHECK: dt as given, checked every step
+    assert B.ann_validate_params(p) == 0
+    assert B.ann_grid_info(p).dt_effective == p.dt
+    assert "timed out" in B.ann_status_string(-12)
+    assert "CFL" in B.ann_status_string(-13)
+
+
+def test_allocator_callbacks_are_validated_before_any_device_call(B):
+    a = B.ann_allocator()   # both callbacks NULL
+    with pytest.raises(B.AnnError) as e:
+        B.ann_create_with_allocator(B.ann_default_params(), a)
+    assert e.value.status == -1
+    with pytest.raises(B.AnnError) as e:   # bad parameters are reported first
+        B.ann_create_with_allocator(B.ann_default_params(n=0), None)
+    assert e.value.status == -1
+
+
+def test_bounded_wait_self_test_rejects_bad_limits(B):
+    assert B.ann_check_bounded_wait(0) == -1
+    assert B.ann_check_bounded_wait(1 << 21) == -1
 
 
 def test_create_without_gpu_reports_not_available(B):

@@ -1,6 +1,7 @@
 """BF16 tensor-core GEMMs (tcgen05) against an FP64 matmul of the same BF16-rounded operands:
 ragged row counts, two-source K, bias and relu, BF16 and FP32 outputs, accumulation, and the
-row-reduction form A^T B used for weight gradients.  FP32 accumulation of K <= 256 products:
+row-reduction form A^T B used for weight gradients, and the time-out status of the bounded waits.
+FP32 accumulation of K <= 256 products:
 relative error <= 1e-5 before the output is rounded (BF16 output: half an ulp, 2^-9)."""
 import numpy as np
 import pytest
@@ -71,3 +72,18 @@ def test_gemm_rejects_bad_shapes(env):
     C = torch.zeros(10, 16, dtype=torch.float32, device="cuda")
     with pytest.raises(B.AnnError):
         B.ann_bf16_gemm(A, W, C)   # K = 24 is not a multiple of 16
+
+
+def test_an_expired_wait_is_a_status_not_a_hang(env):
+    """The bounded mbarrier wait the tensor-core kernels use: waiting on a barrier nothing
+    completes gives up after its poll limit and the host reads ANN_ERR_TIMEOUT; the device then
+    runs a GEMM correctly."""
+    B, torch = env
+    assert B.ann_check_bounded_wait(4096) == -12
+    assert B.ann_check_bounded_wait(1) == -12
+    A = _bf16(torch, (300, 32), 21)
+    W = _bf16(torch, (16, 32), 22)
+    C = torch.zeros(300, 16, dtype=torch.float32, device="cuda")
+    B.ann_bf16_gemm(A.cuda(), W.cuda(), C)
+    ref = A.double() @ W.double().T
+    assert (C.double().cpu() - ref).abs().max().item() <= 1e-5 * ref.abs().max().item() + 1e-6

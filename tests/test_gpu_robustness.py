@@ -321,3 +321,65 @@ def test_pairs_at_the_cutoff_take_the_fp64_band_test(B, orc):
         run.close()
     assert d["band_checks"] >= 3 * 4 * nx * nx, d
     assert d["resorts"] == 1, d   # steps 2 and 3 ran the candidate filter
+
+
+def test_dt_check_mode_reports_cfl_violations(B):
+    """dt_mode ANN_DT_CHECK: a step whose dt exceeds the viscous limit 0.125 h^2 / nu, or
+    0.25 h / (c0 + max|u|) with c0 = 10 max|u| of its midpoint, fails with CFL_VIOLATION (the bit
+    stays set); below both limits it runs."""
+    nx = 64
+    ic = random_velocity_ic(nx, 21, u_scale=1.0)
+    h = 1.3 / nx
+
+    def run(**kw):
+        gp = gpu_params(B, params(nx, **kw), ic["n"])
+        gp.dt_mode = 2
+        ctx = B.ann_create(gp)
+        try:
+            B.ann_set_particles(ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"], ic["rho"])
+            try:
+                B.ann_step(ctx, 3)
+                status = 0
+            except B.AnnError as e:
+                status = e.status
+            return status, B.ann_get_diagnostics(ctx)["error_bits"]
+        finally:
+            B.ann_destroy(ctx)
+
+    assert 0.125 * h * h < 1e-4          # eta = 1: the viscous limit is below dt = 1e-4
+    assert run(dt=1e-4) == (-13, 32)
+    umax = float(np.hypot(ic["ux"], ic["uy"]).max())
+    lim = 0.25 * h / (11.0 * umax)      # the first midpoint velocity is u itself (a^0 = 0)
+    assert lim < 0.125 * h * h / (0.34 * 0.04) and lim < 0.125 * h * h / 1e-3
+    assert run(dt=2.0 * lim, eta=1e-3) == (-13, 32)
+    assert run(dt=0.4 * lim, eta=1e-3) == (0, 0)
+
+
+def test_context_on_the_torch_caching_allocator(B):
+    """Every device buffer of a context made by ann_create_with_allocator comes from the given
+    allocator (here PyTorch's caching allocator) and goes back to it on destroy; the steps and the
+    flow diagnostics are bit-identical to a context on cudaMalloc."""
+    import torch
+
+    ic = random_velocity_ic(96, 5)
+    p = params(96, c0_min=0.05)
+    p["dt"] = stable_dt(p)
+    gp = gpu_params(B, p, ic["n"])
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    ctx = B.ann_create_with_allocator(gp, B.torch_allocator())
+    ref = GpuRun(B, p, ic)
+    try:
+        held = torch.cuda.memory_allocated() - base
+        assert held >= 0.8 * B.ann_grid_info(gp).device_bytes
+        B.ann_set_particles(ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"], ic["rho"])
+        B.ann_step(ctx, 15)
+        ref.step(15)
+        for f in ("X", "Y", "UX", "UY", "Q11", "Q12", "DRHO"):
+            assert np.array_equal(B.ann_get_field(ctx, f, ref.n), B.ann_get_field(ref.ctx, f, ref.n)), f
+        assert np.array_equal(B.ann_energy_spectrum(ctx, 64), B.ann_energy_spectrum(ref.ctx, 64))
+        assert torch.cuda.memory_allocated() - base > held   # the spectrum's scratch
+    finally:
+        B.ann_destroy(ctx)
+        ref.close()
+    assert torch.cuda.memory_allocated() == base
