@@ -10,9 +10,9 @@
 //               lists: every j within 3h (1 + skin) in the 27 surrounding cells
 //   filter      neighbour lists (|r_i - r_j| < 3h among the candidates; FP32 test, FP64 in a band
 //               around 3h), sum W, V = 1 / sum W (Eq. 19)
-//   correction  alpha (Eq. 22) and B = alpha^-1
-//   pass 1      continuity k (Eq. 25), rho_half, corrected velocity gradient (Eq. 20), corrected
-//               Laplacian of Q (Eq. 21), Q rate m (Eqs. 2, 7, 24), Q^{n+1}
+//   pass 1      alpha (Eq. 22) and B = alpha^-1, continuity k (Eq. 25), rho_half, corrected
+//               velocity gradient (Eq. 20), corrected Laplacian of Q (Eq. 21), Q rate m (Eqs. 2, 7,
+//               24), Q^{n+1}: one walk of the neighbours, B applied to the sums afterwards
 //   pass 2      density filter (Eq. 28), equation of state (Eq. 26) with c0 = max(10 max|u|, c0_min)
 //   pass 3      momentum (Eq. 23), artificial displacement (Eq. 29), corrector; the new state is
 //               written into buffer set S in the new order
@@ -461,29 +461,13 @@ __global__ void ANN3_BOUNDS(ANN3_MINB_F) k3_filter(P3 P, const Set3 M, Work3 w)
     w.q4[i] = make_float4(M.q[0][i], M.q[1][i], M.q[2][i], M.q[3][i]);
 }
 
-__global__ void k3_correction(P3 P, const Set3 M, Work3 w)
+// B = alpha^-1 of a symmetric alpha (Eq. 22); flags a non-positive determinant.
+__device__ __forceinline__ void invert_alpha(const float a[3][3], float *B, unsigned *err)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
-    const Here3 hi = here_of(M, i);
-    // alpha^{sl} = sum_j V_j (-d^s) F d^l is symmetric: six sums
-    float a00 = 0.f, a01 = 0.f, a02 = 0.f, a11 = 0.f, a12 = 0.f, a22 = 0.f;
-    for_each_entry(w.nbr, P.n, i, w.nnbr[i], [&](int j, int) {
-        const Geo3 g = geo_of(P, hi, __ldg(M.xi + j));
-        const float c = -__ldg(w.V + j) * f3(P, g);
-        const float e0 = c * g.d[0], e1 = c * g.d[1], e2 = c * g.d[2];
-        a00 = fmaf(e0, g.d[0], a00);
-        a01 = fmaf(e0, g.d[1], a01);
-        a02 = fmaf(e0, g.d[2], a02);
-        a11 = fmaf(e1, g.d[1], a11);
-        a12 = fmaf(e1, g.d[2], a12);
-        a22 = fmaf(e2, g.d[2], a22);
-    });
-    const float a[3][3] = {{a00, a01, a02}, {a01, a11, a12}, {a02, a12, a22}};
     float det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
                 a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
-    if (!(det > 0.f)) atomicOr(w.err, E3_ALPHA);
-    float id = 1.f / det, *B = w.B + 9 * (size_t)i;
+    if (!(det > 0.f)) atomicOr(err, E3_ALPHA);
+    float id = 1.f / det;
     B[0] = (a[1][1] * a[2][2] - a[1][2] * a[2][1]) * id;
     B[1] = (a[0][2] * a[2][1] - a[0][1] * a[2][2]) * id;
     B[2] = (a[0][1] * a[1][2] - a[0][2] * a[1][1]) * id;
@@ -544,37 +528,59 @@ __device__ void q_rate3(const P3 &P, const float *q, const float D[3][3], const 
     m5[4] = 0.5f * (m[1][2] + m[2][1]);
 }
 
+// One walk of the neighbours gives alpha and every raw sum of pass 1; B enters after the walk,
+// since each corrected quantity is a contraction of B with a sum that does not involve it:
+//   alpha_ab = -sum_j V_j F d_a d_b                                                   (Eq. 22)
+//   grad u   = rhs B,  rhs_cl = sum_j V_j (u_j - u_i)_c F d_l                         (Eq. 20)
+//   k / rho  = sum_j V_j F (u_i - u_j) . B d = -sum_ab B_ab rhs_ab                    (Eq. 25)
+//   lap Q_c  = 2 sum_j V_j F (Q_i - Q_j)_c (d . B d) / r^2 = 2 sum_ab B_ab L_c,ab,
+//              L_c,ab = sum_j V_j F d_a d_b (Q_i - Q_j)_c / r^2 (symmetric in ab)     (Eq. 21)
 __global__ void ANN3_BOUNDS(ANN3_MINB_1) k3_pass1(P3 P, const Set3 M, Work3 w)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
     const Here3 hi = here_of(M, i);
-    float B[9];
-    load_b(w, i, B);
     float ui[3] = {M.u[0][i], M.u[1][i], M.u[2][i]}, qi[5];
     for (int c = 0; c < 5; c++) qi[c] = M.q[c][i];
-    // rhs[c][l] = sum_j V_j (u_j - u_i)_c F d_l;  grad u = rhs B (Eq. 20)
-    float rhs[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, lap[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, kc = 0.f;
+    float al[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // (00, 01, 02, 11, 12, 22) of sum_j V_j F d_a d_b
+    float rhs[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float L[5][6] = {};
     for_each_entry(w.nbr, P.n, i, w.nnbr[i], [&](int j, int) {
         const Geo3 g = geo_of(P, hi, __ldg(M.xi + j));
         const float4 vu = __ldg(w.vu + j), qa = __ldg(w.q4 + j);
         const float qj[5] = {qa.x, qa.y, qa.z, qa.w, __ldg(M.q[4] + j)};
         const float vf = vu.x * f3(P, g);   // V_j F
-        float bd[3];
-        bd_of(B, g.d, bd);
-        const float du[3] = {ui[0] - vu.y, ui[1] - vu.z, ui[2] - vu.w};
-        kc = fmaf(vf, du[0] * bd[0] + du[1] * bd[1] + du[2] * bd[2], kc);
-        for (int c = 0; c < 3; c++) {
-            const float e = -vf * du[c];
-            for (int l = 0; l < 3; l++) rhs[c][l] = fmaf(e, g.d[l], rhs[c][l]);
+        const float e0 = vf * g.d[0], e1 = vf * g.d[1], e2 = vf * g.d[2];
+        const float pab[6] = {e0 * g.d[0], e0 * g.d[1], e0 * g.d[2], e1 * g.d[1], e1 * g.d[2], e2 * g.d[2]};
+        for (int k = 0; k < 6; k++) al[k] += pab[k];
+        const float du[3] = {vu.y - ui[0], vu.z - ui[1], vu.w - ui[2]};   // u_j - u_i
+        const float ev[3] = {e0, e1, e2};
+        for (int c = 0; c < 3; c++)
+            for (int l = 0; l < 3; l++) rhs[c][l] = fmaf(du[c], ev[l], rhs[c][l]);
+        const float ir2 = g.rinv * g.rinv;
+        for (int c = 0; c < 5; c++) {
+            const float dq = (qi[c] - qj[c]) * ir2;
+            for (int k = 0; k < 6; k++) L[c][k] = fmaf(pab[k], dq, L[c][k]);
         }
-        const float f = vf * (g.d[0] * bd[0] + g.d[1] * bd[1] + g.d[2] * bd[2]) * (g.rinv * g.rinv);
-        for (int c = 0; c < 5; c++) lap[c] = fmaf(f, qi[c] - qj[c], lap[c]);
     });
+    const float a[3][3] = {{-al[0], -al[1], -al[2]}, {-al[1], -al[3], -al[4]}, {-al[2], -al[4], -al[5]}};
+    float B[9];
+    invert_alpha(a, B, w.err);
+    for (int c = 0; c < 9; c++) w.B[9 * (size_t)i + c] = B[c];
     float D[3][3];
     for (int c = 0; c < 3; c++)
         for (int b = 0; b < 3; b++) D[c][b] = rhs[c][0] * B[b] + rhs[c][1] * B[3 + b] + rhs[c][2] * B[6 + b];
-    for (int c = 0; c < 5; c++) lap[c] *= 2.f;
+    float kc = 0.f;
+    for (int a_ = 0; a_ < 3; a_++)
+        for (int b = 0; b < 3; b++) kc -= B[3 * a_ + b] * rhs[a_][b];
+    // B_ab + B_ba weights of the off-diagonal pairs of the symmetric L
+    const float bw[6] = {B[0], B[1] + B[3], B[2] + B[6], B[4], B[5] + B[7], B[8]};
+    float lap[5];
+    for (int c = 0; c < 5; c++) {
+        float sl = 0.f;
+        for (int k = 0; k < 6; k++) sl = fmaf(bw[k], L[c][k], sl);
+        lap[c] = 2.f * sl;
+    }
     float k_i = P.rho0 * (1.f + M.dr[i]) * kc;
     w.k[i] = k_i;
     w.dh[i] = M.dr[i] + P.half_dt * k_i / P.rho0;
@@ -996,7 +1002,6 @@ int ann3_step(ann3_ctx *c, int64_t nsteps)
         k3_gather<<<g, 256, 0, s>>>(P, c->S, c->M, c->w);
         k3_candidates<<<g, 256, 0, s>>>(P, c->M, c->w);
         k3_filter<<<g, 256, 0, s>>>(P, c->M, c->w);
-        k3_correction<<<g, 256, 0, s>>>(P, c->M, c->w);
         k3_pass1<<<g, 256, 0, s>>>(P, c->M, c->w);
         k3_pass2<<<g, 256, 0, s>>>(P, c->M, c->w);
         k3_pass3<<<g, 256, 0, s>>>(P, c->M, c->S, c->w);
