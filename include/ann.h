@@ -437,7 +437,10 @@ int ann_surrogate_adam(ann_surrogate *sg, double lr);
  * forward, and replace the context's state by the prediction (t and the step count advance by k;
  * accelerations restart from 0, so the next jump needs a recorded plain step first; periodic image
  * counts follow the particles).  Q takes the explicit increment plus the network's correction; u
- * takes the explicit increment alone unless the velocity correction is switched on (below). */
+ * takes the explicit increment alone unless the velocity correction is switched on (below).  The
+ * context keeps its cell structure and candidate lists (the next step re-sorts only if a particle
+ * has moved half the skin since the last re-sort).  Errors: as ann_surrogate_forward; NONFINITE if
+ * the prediction is not finite (the context's error bit is then set, as a failed step sets it). */
 int ann_surrogate_jump(ann_surrogate *sg, ann_ctx *ctx, const float *tend);
 
 /* Whether the jump adds the network's velocity correction ys_u (y2, y3) (on = 1) or not (0, the

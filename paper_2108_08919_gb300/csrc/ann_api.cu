@@ -1498,22 +1498,16 @@ int ctx_search_present(ann_ctx *c)
     return ANN_OK;
 }
 
-// Replace the state by device arrays in ID order (as ann_set_particles), keeping t and the step
-// count, which advance by add_steps.  Accelerations restart from 0 and the next step re-sorts.
-int ctx_reload(ann_ctx *c, const double *dev7, int64_t add_steps)
+// The state arrays S were rewritten in place, in the order of the evaluation copy M (the order of
+// the last re-sort), with accelerations 0: t and the step count advance by add_steps.  The cell
+// structure is kept: the next step re-sorts only if a particle has moved half the skin since the
+// last re-sort, as after any step.
+int ctx_commit_in_place(ann_ctx *c, int64_t add_steps)
 {
-    double t = c->t;
-    int64_t steps = c->steps;
-    size_t n = (size_t)c->P.n;
-    cudaError_t e = clear_flags(c);
-    if (!e) e = enqueue_load(c->P, c->b, dev7, dev7 + n, dev7 + 2 * n, dev7 + 3 * n, dev7 + 4 * n, dev7 + 5 * n,
-                             dev7 + 6 * n, c->stream, false);
-    if (e) return cuda_fail(c, e, "reload");
     int st = device_status(c);
-    c->have_particles = (st == ANN_OK);
-    c->t = t + add_steps * c->P.dt_d;
-    c->steps = steps + add_steps;
-    c->s_sorted = c->m_current = false;
+    c->t += add_steps * c->P.dt_d;
+    c->steps += add_steps;
+    c->s_sorted = c->m_current = false;   // diagnostics search the present positions first
     c->rec_valid = false;
     c->grid_step = -1;
     return st;

@@ -172,7 +172,7 @@ struct CtxView {
 };
 int ctx_view(ann_ctx *c, CtxView *v);
 int ctx_search_present(ann_ctx *c);                                  // search at the present positions
-int ctx_reload(ann_ctx *c, const double *dev7, int64_t add_steps);   // x, y, ux, uy, q11, q12, rho by ID
+int ctx_commit_in_place(ann_ctx *c, int64_t add_steps);              // S was rewritten in the order of M
 
 // BF16 tensor-core GEMMs of the surrogate (ann_mlp.cu).  K, N multiples of 16 in [16, 256].
 bool gemm_shape_ok(int K, int N);

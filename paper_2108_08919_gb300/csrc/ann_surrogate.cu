@@ -258,11 +258,12 @@ __global__ void k_sg_adam(float *p, const float *g, float *m, float *v, int coun
 }
 
 // The jump: (Q, u) += inc + (ys_q y0, ys_q y1, ys_u y2, ys_u y3), x += k dt (u + u') / 2
-// (trapezoid), wrapped with the periodic image count; row i is particle ids[i], and out7 = x, y, ux,
-// uy, q11, q12, rho (FP64) in ID order.
+// (trapezoid), wrapped with the periodic image count.  Row i is slot i of the context's evaluation
+// copy (particle ids[i]); the new state goes straight into the context's state arrays at the same
+// slot, with the density unchanged and the accelerations restarting from 0, so the context keeps
+// its cell structure and candidate lists.
 __global__ void k_sg_jump(int n, const int *ids, const double *x, const double *y, const float4 *u4, const float *dr,
-                          const float *Y, const float *inc, float ysq, float ysu, double dtk, double L, float rho0,
-                          int2 *img, double *out7)
+                          const float *Y, const float *inc, float ysq, float ysu, double dtk, double L, Bufs b)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -280,17 +281,26 @@ __global__ void k_sg_jump(int n, const int *ids, const double *x, const double *
     yn -= ky * L;
     if (xn >= L) xn -= L;   // rounding at the face
     if (yn >= L) yn -= L;
-    if (kx | ky) {
-        img[id].x += kx;
-        img[id].y += ky;
+    if (!(xn >= 0.0 && xn < L && yn >= 0.0 && yn < L && isfinite(ux) && isfinite(uy) && isfinite(q1) &&
+          isfinite(q2))) {
+        atomicOr(b.err, EB_NONFINITE);
+        xn = yn = 0.0;
+        kx = ky = 0;
     }
-    out7[id] = xn;
-    out7[(size_t)n + id] = yn;
-    out7[2 * (size_t)n + id] = ux;
-    out7[3 * (size_t)n + id] = uy;
-    out7[4 * (size_t)n + id] = q1;
-    out7[5 * (size_t)n + id] = q2;
-    out7[6 * (size_t)n + id] = (double)rho0 * (1.0 + (double)dr[i]);
+    if (kx | ky) {
+        b.img[id].x += kx;
+        b.img[id].y += ky;
+    }
+    b.sx[i] = xn;
+    b.sy[i] = yn;
+    b.sux[i] = ux;
+    b.suy[i] = uy;
+    b.sq11[i] = q1;
+    b.sq12[i] = q2;
+    b.sdr[i] = dr[i];
+    b.sax[i] = 0.f;
+    b.say[i] = 0.f;
+    b.sid[i] = id;
 }
 
 inline unsigned nb(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -667,13 +677,12 @@ int ann_surrogate_jump(ann_surrogate *S, ann_ctx *ctx, const float *tend)
     st = ctx_view(ctx, &v);
     if (st) return st;
     k_sg_jump<<<nb(S->n), 256, 0, S->s>>>(S->n, S->ids, S->x, S->y, S->u4, S->dr, S->Y, S->inc, (float)S->ysq,
-                                          S->vel_corr ? (float)S->ysu : 0.f, S->dt * k, S->L, S->rho0, v.b.img,
-                                          v.tmp);
+                                          S->vel_corr ? (float)S->ysu : 0.f, S->dt * k, S->L, v.b);
     cudaError_t e = cudaGetLastError();
     if (!e) e = cudaStreamSynchronize(S->s);
     S->loaded = false;   // the context moves on: the next forward needs a new load
     if (e) return scuda(S, e, "ann_surrogate_jump");
-    return ctx_reload(ctx, v.tmp, k);
+    return ctx_commit_in_place(ctx, k);
 }
 
 // He initialisation: every weight matrix drawn N(0, 2 / fan_in) (the output layer at half that
