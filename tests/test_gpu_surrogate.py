@@ -14,7 +14,8 @@ import numpy as np
 import pytest
 
 import sph_inputs as si
-from _sph import gpu_params, params, relerr, stable_dt
+from _sph import (GpuRun, compare_state, gpu_params, oracle_params, params, random_velocity_ic, relerr,
+                  stable_dt)
 
 pytestmark = pytest.mark.gpu
 
@@ -301,3 +302,36 @@ def test_jump_applies_the_public_forward(B):
     corr = np.stack([s1["Q11"] - s0["Q11"] - inc[:, 0], s1["Q12"] - s0["Q12"] - inc[:, 1]], axis=1)
     assert np.abs(corr - ysq * y[:, :2]).max() < 4 * ulp
     assert np.abs(s1["UX"] - s0["UX"] - inc[:, 2]).max() < 1e-7 and np.abs(s1["UY"] - s0["UY"] - inc[:, 3]).max() < 1e-7
+
+
+def test_plain_steps_continue_from_a_jump_in_place(B, orc):
+    """The jump writes the new state into the context's own arrays, in the cell order of its last
+    re-sort: the plain steps after it match the FP64 oracle started from the jumped state (read back
+    by particle ID), and a slow flow keeps the candidate lists (no re-sort)."""
+    nx, k = 64, 8
+    ic = random_velocity_ic(nx, 31)
+    p = params(nx)
+    p["dt"] = stable_dt(p)
+    run = GpuRun(B, p, ic)
+    sg = B.ann_surrogate_create(run.n)
+    try:
+        B.ann_set_record(run.ctx, 1)
+        run.step(2)
+        B.ann_surrogate_init(sg, 5)
+        B.ann_surrogate_set_scales(sg, 0.01, 1e-3, 1e-5, k)
+        B.ann_surrogate_jump(sg, run.ctx, None)
+        r0 = B.ann_get_diagnostics(run.ctx)["resorts"]
+        s = run.state()
+        assert not s["ax"].any() and not s["ay"].any()   # accelerations restart from 0
+        st = {"x": s["x"], "y": s["y"], "ux": s["ux"], "uy": s["uy"], "q11": s["q11"], "q12": s["q12"],
+              "rho": 1.0 + s["drho"]}
+        P = oracle_params(orc, p, "cells")
+        for _ in range(2):
+            run.step(1)
+            st, _ = orc.step(P, st, 1, record=True)
+            errs = compare_state(run.state(), st, s["x"], s["y"])
+            assert all(e <= 1e-5 for e in errs.values()), errs
+        assert B.ann_get_diagnostics(run.ctx)["resorts"] == r0
+    finally:
+        B.ann_surrogate_destroy(sg)
+        run.close()
