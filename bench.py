@@ -840,8 +840,7 @@ def run_ours(args):
     def e2e_iter():
         B.ann_set_particles(ctx, pin["x"], pin["y"], pin["ux"], pin["uy"], pin["q11"], pin["q12"], pin["rho"])
         B.ann_step(ctx, 1)
-        for k in outs:
-            B.ann_get_field(ctx, k, n, out=pout[k])
+        B.ann_get_state(ctx, n, out=pout)
 
     e2e_iter()
     torch.cuda.synchronize()

@@ -243,6 +243,12 @@ int ann_set_record(ann_ctx *ctx, int on);
  * (unknown field, short buffer), STATE (no particles), CUDA. */
 int ann_get_field(ann_ctx *ctx, int field, void *dst, int64_t bytes, int dst_is_device);
 
+/* The state (x, y FP64; ux, uy, q11, q12 and drho = rho/rho0 - 1 FP32; n each, particle-ID order)
+ * in one call with one synchronisation: the same values as ann_get_field of ANN_FIELD_X ... _DRHO.
+ * A NULL destination is skipped.  dst_is_device as for ann_get_field.  Errors: STATE, CUDA. */
+int ann_get_state(ann_ctx *ctx, double *x, double *y, float *ux, float *uy, float *q11, float *q12,
+                  float *drho, int dst_is_device);
+
 /* FP64 diagnostics of the current state.  Errors: STATE, CUDA. */
 int ann_get_diagnostics(ann_ctx *ctx, ann_diag *out);
 

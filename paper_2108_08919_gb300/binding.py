@@ -119,6 +119,7 @@ def lib() -> ctypes.CDLL:
         "ann_kernel_name": (ctypes.c_char_p, [i32]),
         "ann_set_record": (i32, [vp, i32]),
         "ann_get_field": (i32, [vp, i32, vp, i64, i32]),
+        "ann_get_state": (i32, [vp, vp, vp, vp, vp, vp, vp, vp, i32]),
         "ann_get_diagnostics": (i32, [vp, _P(ann_diag)]),
         "ann_get_neighbors": (i32, [vp, _P(ctypes.c_int64), _P(ctypes.c_int32), i64]),
         "ann_save_state": (i32, [vp, ctypes.c_char_p]),
@@ -328,6 +329,38 @@ def ann_get_field(ctx, field: str, n: int, out=None):
         ptr, dev, nbytes = out.ctypes.data, 0, out.nbytes
     _check(lib().ann_get_field(ctx, FIELD_ID[field], ctypes.c_void_p(ptr), nbytes, dev), ctx,
            f"ann_get_field({field})")
+    return out
+
+
+STATE_FIELDS = ("X", "Y", "UX", "UY", "Q11", "Q12", "DRHO")
+
+
+def ann_get_state(ctx, n: int, out=None) -> dict:
+    """The state fields X, Y (float64) and UX, UY, Q11, Q12, DRHO (float32) in particle-ID order,
+    in one call: new numpy arrays, or written into ``out`` (a dict of numpy arrays, or of CUDA
+    tensors, with some or all of those names)."""
+    if out is None:
+        out = {f: np.empty(n, dtype=field_dtype(f)) for f in STATE_FIELDS}
+    ptrs, dev = [], None
+    for f in STATE_FIELDS:
+        a = out.get(f)
+        if a is None:
+            ptrs.append(None)
+            continue
+        is_dev = bool(getattr(a, "is_cuda", False))
+        if dev is None:
+            dev = is_dev
+        if is_dev != dev:
+            raise ValueError("out must be all host arrays or all CUDA tensors")
+        if is_dev:
+            if a.numel() < n or a.element_size() != np.dtype(field_dtype(f)).itemsize:
+                raise ValueError(f"out[{f!r}] must hold n values of the field's dtype")
+            ptrs.append(ctypes.c_void_p(a.data_ptr()))
+        else:
+            if a.dtype != field_dtype(f) or not a.flags.c_contiguous or a.size < n:
+                raise ValueError(f"out[{f!r}] must be a contiguous {np.dtype(field_dtype(f)).name} array of n values")
+            ptrs.append(ctypes.c_void_p(a.ctypes.data))
+    _check(lib().ann_get_state(ctx, *ptrs, 1 if dev else 0), ctx, "ann_get_state")
     return out
 
 

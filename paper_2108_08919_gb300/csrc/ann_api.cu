@@ -754,6 +754,33 @@ int ann_get_field(ann_ctx *c, int field, void *dst, int64_t bytes, int dst_is_de
     return ANN_OK;
 }
 
+int ann_get_state(ann_ctx *c, double *x, double *y, float *ux, float *uy, float *q11, float *q12, float *drho,
+                  int dst_is_device)
+{
+    if (!c) return ANN_ERR_INVALID_ARG;
+    if (!c->have_particles) return fail(c, ANN_ERR_STATE, "no particles");
+    const size_t n = (size_t)c->P.n;
+    const Bufs &b = c->b;
+    // each field is un-permuted into its own part of the staging buffer (36 bytes per particle of
+    // the >= 56 it holds), so all copies are in flight before the one synchronisation
+    unsigned char *tmp = static_cast<unsigned char *>(c->tmp);
+    struct Part { const void *src; void *dst; int es; } parts[7] = {
+        {b.sx, x, 8}, {b.sy, y, 8}, {b.sux, ux, 4}, {b.suy, uy, 4}, {b.sq11, q11, 4}, {b.sq12, q12, 4}, {b.sdr, drho, 4}};
+    const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaSuccess;
+    size_t off = 0;
+    for (const Part &p : parts) {
+        unsigned char *stage = tmp + off;
+        off += (size_t)p.es * n;
+        if (!p.dst) continue;
+        e = enqueue_unpermute(p.src, b.sid, stage, (int)n, p.es, c->stream);
+        if (!e) e = cudaMemcpyAsync(p.dst, stage, (size_t)p.es * n, kind, c->stream);
+        if (e) break;
+    }
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    return e ? cuda_fail(c, e, "ann_get_state") : ANN_OK;
+}
+
 int ann_get_diagnostics(ann_ctx *c, ann_diag *out)
 {
     if (!c || !out) return ANN_ERR_INVALID_ARG;

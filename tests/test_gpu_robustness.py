@@ -383,3 +383,27 @@ def test_context_on_the_torch_caching_allocator(B):
         B.ann_destroy(ctx)
         ref.close()
     assert torch.cuda.memory_allocated() == base
+
+
+def test_get_state_equals_the_field_reads(B):
+    """ann_get_state returns, in one call, exactly what ann_get_field returns field by field, to
+    host arrays and to device tensors, and skips the fields it is not given."""
+    import torch
+
+    ic = random_velocity_ic(64, 9)
+    p = params(64, c0_min=0.05)
+    p["dt"] = stable_dt(p)
+    run = GpuRun(B, p, ic)
+    try:
+        run.step(7)
+        ref = {f: B.ann_get_field(run.ctx, f, run.n) for f in B.STATE_FIELDS}
+        host = B.ann_get_state(run.ctx, run.n)
+        dev = {f: torch.zeros(run.n, dtype=torch.float64 if f in ("X", "Y") else torch.float32, device="cuda")
+               for f in B.STATE_FIELDS if f not in ("UY", "Q12")}
+        B.ann_get_state(run.ctx, run.n, out=dev)
+        for f in B.STATE_FIELDS:
+            assert np.array_equal(host[f], ref[f]), f
+            if f in dev:
+                assert np.array_equal(dev[f].cpu().numpy(), ref[f]), f
+    finally:
+        run.close()
