@@ -825,10 +825,12 @@ def run_ours(args):
     dom = max(kms, key=kms.get)
     dom_launch_ms = kprof[dom] / max(klaunch[dom], 1)
 
-    # end to end through the C-ABI with host buffers: pinned inputs -> set_particles -> step ->
-    # state fields back to pinned host arrays, every step
-    pin = {k: torch.from_numpy(np.ascontiguousarray(ic[k], dtype=np.float64)).pin_memory().numpy()
-           for k in ("x", "y", "ux", "uy", "q11", "q12", "rho")}
+    # end to end through the C-ABI with host buffers: the state in pinned host arrays, in the
+    # precision the library keeps it -> ann_set_state -> step -> ann_get_state back, every step
+    src = {"X": ic["x"], "Y": ic["y"], "UX": ic["ux"], "UY": ic["uy"], "Q11": ic["q11"], "Q12": ic["q12"],
+           "DRHO": np.asarray(ic["rho"]) / p.rho0 - 1.0}
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v, dtype=B.field_dtype(k))).pin_memory().numpy()
+           for k, v in src.items()}
     outs = {"X": np.float64, "Y": np.float64, "UX": np.float32, "UY": np.float32, "Q11": np.float32,
             "Q12": np.float32, "DRHO": np.float32}
     pout = {k: torch.empty(n, dtype=torch.float64 if dt == np.float64 else torch.float32).pin_memory().numpy()
@@ -838,7 +840,7 @@ def run_ours(args):
     e2e_steps = max(5, min(50, args.steps // 20))
 
     def e2e_iter():
-        B.ann_set_particles(ctx, pin["x"], pin["y"], pin["ux"], pin["uy"], pin["q11"], pin["q12"], pin["rho"])
+        B.ann_set_state(ctx, pin)
         B.ann_step(ctx, 1)
         B.ann_get_state(ctx, n, out=pout)
 

@@ -215,6 +215,14 @@ int ann_set_particles(ann_ctx *ctx, int64_t n, const double *x, const double *y,
                       const double *uy, const double *q11, const double *q12, const double *rho,
                       int is_device);
 
+/* Load the state in the precision the context keeps it, as ann_get_state returns it: x, y FP64;
+ * ux, uy, q11, q12 FP32; drho = rho/rho0 - 1 FP32 (NULL: 0); n each, particle-ID order.
+ * Otherwise as ann_set_particles (positions re-inserted, a^0 = 0, t and the step count 0, the next
+ * step re-sorts): the same state as ann_set_particles of the same values.  Errors: INVALID_ARG,
+ * NONFINITE (also drho <= -1), CUDA. */
+int ann_set_state(ann_ctx *ctx, int64_t n, const double *x, const double *y, const float *ux, const float *uy,
+                  const float *q11, const float *q12, const float *drho, int is_device);
+
 /* Advance nsteps >= 0 steps (one CUDA-graph launch per step) and synchronise.  Errors:
  * STATE (no particles), CELL_OVERFLOW, NBR_OVERFLOW, NONFINITE, SINGULAR_ALPHA, CFL_VIOLATION (device error
  * bits; once one is raised the remaining kernels of the call return without work, so the state is

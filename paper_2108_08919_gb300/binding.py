@@ -120,6 +120,7 @@ def lib() -> ctypes.CDLL:
         "ann_set_record": (i32, [vp, i32]),
         "ann_get_field": (i32, [vp, i32, vp, i64, i32]),
         "ann_get_state": (i32, [vp, vp, vp, vp, vp, vp, vp, vp, i32]),
+        "ann_set_state": (i32, [vp, i64, vp, vp, vp, vp, vp, vp, vp, i32]),
         "ann_get_diagnostics": (i32, [vp, _P(ann_diag)]),
         "ann_get_neighbors": (i32, [vp, _P(ctypes.c_int64), _P(ctypes.c_int32), i64]),
         "ann_save_state": (i32, [vp, ctypes.c_char_p]),
@@ -289,6 +290,35 @@ def ann_set_particles(ctx, x, y, ux, uy, q11, q12, rho=None) -> None:
     n = int(len(arrs[0][2]) if not hasattr(arrs[0][2], "numel") else arrs[0][2].numel())
     _check(lib().ann_set_particles(ctx, n, *[a[0] for a in arrs], int(dev.pop())), ctx,
            "ann_set_particles")
+
+
+def ann_set_state(ctx, state: dict) -> None:
+    """Load the state as ann_get_state returns it: a dict with X, Y (float64) and UX, UY, Q11, Q12
+    and optionally DRHO (float32), all numpy arrays or all CUDA tensors, in particle-ID order."""
+    ptrs, dev, n = [], None, None
+    for f in STATE_FIELDS:
+        a = state.get(f)
+        if a is None:
+            if f != "DRHO":
+                raise ValueError(f"state[{f!r}] is required")
+            ptrs.append(None)
+            continue
+        is_dev = bool(getattr(a, "is_cuda", False))
+        dev = is_dev if dev is None else dev
+        if is_dev != dev:
+            raise ValueError("state must be all host arrays or all CUDA tensors")
+        size = a.numel() if is_dev else a.size
+        n = size if n is None else n
+        want = np.dtype(field_dtype(f))
+        if is_dev:
+            if a.element_size() != want.itemsize or size != n or not a.is_contiguous():
+                raise ValueError(f"state[{f!r}] must be a contiguous {want.name} tensor of n values")
+            ptrs.append(ctypes.c_void_p(a.data_ptr()))
+        else:
+            if a.dtype != want or size != n or not a.flags.c_contiguous:
+                raise ValueError(f"state[{f!r}] must be a contiguous {want.name} array of n values")
+            ptrs.append(ctypes.c_void_p(a.ctypes.data))
+    _check(lib().ann_set_state(ctx, n, *ptrs, 1 if dev else 0), ctx, "ann_set_state")
 
 
 def ann_step(ctx, nsteps: int) -> None:

@@ -471,6 +471,40 @@ bool field_of(ann_ctx *c, int f, Field &out)
     }
 }
 
+// ann_set_state's load: the state as the context stores it (FP64 positions, FP32 fields, the
+// density as its deviation), re-inserted into the box as ann_set_particles does.
+__global__ void k_load_state(DevParams P, Bufs b, const double *x, const double *y, const float *ux,
+                             const float *uy, const float *q11, const float *q12, const float *drho)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    double xx = x[i], yy = y[i];
+    const float d = drho ? drho[i] : 0.f;
+    if (!(isfinite(xx) && isfinite(yy) && isfinite(ux[i]) && isfinite(uy[i]) && isfinite(q11[i]) &&
+          isfinite(q12[i]) && isfinite(d) && d > -1.f)) {
+        atomicOr(b.err, EB_NONFINITE);
+        xx = 0.0;
+        yy = 0.0;
+    }
+    if (xx < -P.L || xx >= 2.0 * P.L) xx = xx - floor(xx / P.L) * P.L;
+    if (yy < -P.L || yy >= 2.0 * P.L) yy = yy - floor(yy / P.L) * P.L;
+    if (xx < 0.0) xx += P.L;
+    if (xx >= P.L) xx -= P.L;
+    if (yy < 0.0) yy += P.L;
+    if (yy >= P.L) yy -= P.L;
+    b.sx[i] = xx + 0.0;
+    b.sy[i] = yy + 0.0;
+    b.sux[i] = ux[i];
+    b.suy[i] = uy[i];
+    b.sq11[i] = q11[i];
+    b.sq12[i] = q12[i];
+    b.sdr[i] = d;
+    b.sax[i] = 0.f;
+    b.say[i] = 0.f;
+    b.sid[i] = i;
+    b.img[i] = make_int2(0, 0);
+}
+
 __global__ void k_deinterleave(const float *src, float *dst, int n, int stride, int comp)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -621,6 +655,49 @@ int ann_set_particles(ann_ctx *c, int64_t n, const double *x, const double *y, c
     }
     e = enqueue_load(c->P, c->b, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5], dev[6], c->stream);
     if (e) return cuda_fail(c, e, "ann_set_particles load");
+    c->have_particles = true;
+    c->steps = 0;
+    c->t = 0.0;
+    c->s_sorted = c->m_current = false;
+    c->rec_valid = false;
+    c->grid_step = -1;
+    int s = device_status(c);
+    if (s) {
+        c->have_particles = false;
+        clear_flags(c);
+        cudaStreamSynchronize(c->stream);
+    }
+    return s;
+}
+
+int ann_set_state(ann_ctx *c, int64_t n, const double *x, const double *y, const float *ux, const float *uy,
+                  const float *q11, const float *q12, const float *drho, int is_device)
+{
+    if (!c) return ANN_ERR_INVALID_ARG;
+    if (n != c->prm.n) return fail(c, ANN_ERR_INVALID_ARG, "n differs from the n of ann_create");
+    if (!x || !y || !ux || !uy || !q11 || !q12) return fail(c, ANN_ERR_INVALID_ARG, "null input array");
+    cudaError_t e = clear_flags(c);
+    if (!e) e = cudaMemsetAsync(c->b.resorts, 0, sizeof(uint32_t), c->stream);
+    if (e) return cuda_fail(c, e, "ann_set_state");
+    const void *dev[7] = {x, y, ux, uy, q11, q12, drho};
+    if (!is_device) {
+        unsigned char *t = static_cast<unsigned char *>(c->tmp);   // 36 of its >= 56 bytes per particle
+        size_t off = 0;
+        for (int k = 0; k < 7; k++) {
+            const size_t bytes = (k < 2 ? 8 : 4) * (size_t)n;
+            if (dev[k]) {
+                e = cudaMemcpyAsync(t + off, dev[k], bytes, cudaMemcpyHostToDevice, c->stream);
+                if (e) return cuda_fail(c, e, "ann_set_state copy");
+                dev[k] = t + off;
+            }
+            off += bytes;
+        }
+    }
+    k_load_state<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+        c->P, c->b, (const double *)dev[0], (const double *)dev[1], (const float *)dev[2], (const float *)dev[3],
+        (const float *)dev[4], (const float *)dev[5], (const float *)dev[6]);
+    e = cudaGetLastError();
+    if (e) return cuda_fail(c, e, "ann_set_state load");
     c->have_particles = true;
     c->steps = 0;
     c->t = 0.0;

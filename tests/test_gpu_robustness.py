@@ -407,3 +407,43 @@ def test_get_state_equals_the_field_reads(B):
                 assert np.array_equal(dev[f].cpu().numpy(), ref[f]), f
     finally:
         run.close()
+
+
+def test_set_state_is_set_particles_in_native_precision(B):
+    """ann_set_state of a state read with ann_get_state loads the same state as ann_set_particles of
+    the same values in FP64: the steps after it are bit-identical (host arrays and device tensors);
+    a density deviation <= -1 is rejected."""
+    import torch
+
+    ic = random_velocity_ic(64, 13, rho_scale=1e-3)
+    p = params(64, c0_min=0.05)
+    p["dt"] = stable_dt(p)
+    src = GpuRun(B, p, ic)
+    a, b = GpuRun(B, p, ic), GpuRun(B, p, ic)
+    try:
+        src.step(4)
+        st = B.ann_get_state(src.ctx, src.n)
+        B.ann_set_particles(a.ctx, st["X"], st["Y"], st["UX"].astype(np.float64), st["UY"].astype(np.float64),
+                            st["Q11"].astype(np.float64), st["Q12"].astype(np.float64),
+                            1.0 + st["DRHO"].astype(np.float64))
+        B.ann_set_state(b.ctx, {k: torch.from_numpy(v).cuda() for k, v in st.items()})
+        assert np.array_equal(B.ann_get_state(b.ctx, b.n)["DRHO"], st["DRHO"])
+        a.step(6)
+        b.step(6)
+        sa, sb = B.ann_get_state(a.ctx, a.n), B.ann_get_state(b.ctx, b.n)
+        for f in B.STATE_FIELDS:
+            assert np.array_equal(sa[f], sb[f]), f
+        B.ann_set_state(b.ctx, st)   # host arrays
+        b.step(6)
+        sh = B.ann_get_state(b.ctx, b.n)
+        for f in B.STATE_FIELDS:
+            assert np.array_equal(sa[f], sh[f]), f
+        bad = dict(st)
+        bad["DRHO"] = st["DRHO"].copy()
+        bad["DRHO"][7] = -1.0
+        with pytest.raises(B.AnnError) as e:
+            B.ann_set_state(b.ctx, bad)
+        assert e.value.status == -6
+    finally:
+        for r in (src, a, b):
+            r.close()
