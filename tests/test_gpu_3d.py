@@ -120,6 +120,35 @@ def test_steps_match_the_oracle(B, O, kind):
     assert max(errs.values()) < 2e-5, errs
 
 
+def test_full_size_two_steps(B, O):
+    """The benchmark's 3D workload at its full size (96^3 = 884,736 particles, ~250 neighbours, the
+    same parameters and launch configuration): two steps, the first re-sorting and building the
+    candidate lists, the second filtering them, against the FP64 oracle on every particle."""
+    nx = 96
+    p = _params(nx, dt=1e-4)
+    ic = si.jittered_lattice3(nx, seed=5, jitter=0.1, u_scale=0.02)
+    got, want, rec = _run_both(B, O, ic, p, 2)
+    steps, bits, resorts = got.pop("status")
+    assert (steps, bits, resorts) == (2, 0, 1)
+    x0 = np.stack([ic["x"], ic["y"], ic["z"]], axis=1)
+    wpos = np.stack([want["x"], want["y"], want["z"]], axis=1)
+    errs = {
+        "disp": relerr(_disp(got["POS"], x0), _disp(wpos, x0)),
+        "u": relerr(got["U"], want["u"]),
+        "q": relerr(got["Q"], want["q"]),
+        "rho-1": relerr(got["RHO"][:, 0] - 1.0, want["rho"] - 1.0),
+        "a": relerr(got["A"], want["a"]),
+        "sumW": relerr(got["SUMW"][:, 0], rec["sumW"]),
+        "gradu": relerr(got["GRADU"], rec["gradu"]),
+        "lapQ": relerr(got["LAPQ"], rec["lapQ"]),
+        "qrate": relerr(got["QRATE"], rec["qrate"]),
+        "p": relerr(got["P"][:, 0], rec["p"]),
+    }
+    print("96^3", {k: f"{v:.2e}" for k, v in errs.items()})
+    assert np.array_equal(got["NNBR"][:, 0].astype(np.int64), rec["nnbr"])
+    assert max(errs.values()) < 2e-5, errs
+
+
 def test_uniform_state_at_64_cubed(B, O):
     """A property that holds at any size: uniform Q at rest relaxes by the bulk term alone and
     nothing moves (262,144 particles, 5 steps)."""
