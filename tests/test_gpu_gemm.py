@@ -28,8 +28,10 @@ def _bf16(torch, shape, seed, scale=1.0):
     return torch.tensor(v, dtype=torch.float32).to(torch.bfloat16)
 
 
+# 200,003 rows: 1,563 row tiles, several for every persistent CTA, and a ragged last tile
 @pytest.mark.parametrize("rows,K1,K2,N", [(1, 16, 0, 16), (128, 16, 16, 128), (300, 128, 32, 128),
-                                          (1000, 32, 0, 32), (127, 128, 32, 160), (4099, 128, 0, 16)])
+                                          (1000, 32, 0, 32), (127, 128, 32, 160), (4099, 128, 0, 16),
+                                          (200003, 128, 32, 128)])
 def test_gemm_nt(env, rows, K1, K2, N):
     B, torch = env
     A1 = _bf16(torch, (rows, K1), 1)
@@ -53,7 +55,8 @@ def test_gemm_nt(env, rows, K1, K2, N):
         2e-5 * ref.abs().max().item() + 1e-6
 
 
-@pytest.mark.parametrize("rows,K,N", [(5, 16, 16), (128, 128, 32), (1000, 160, 128), (4099, 32, 16)])
+@pytest.mark.parametrize("rows,K,N", [(5, 16, 16), (128, 128, 32), (1000, 160, 128), (4099, 32, 16),
+                                      (200003, 160, 128)])
 def test_gemm_tn(env, rows, K, N):
     B, torch = env
     A = _bf16(torch, (rows, K), 11)

@@ -56,8 +56,11 @@ def _load(B, ctx, ic):
     B.ann_set_particles(ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"], ic.get("rho"))
 
 
-def test_forward_and_gradients_match_the_oracle(B, S, orc):
-    nx, us = 32, 0.01
+@pytest.mark.parametrize("nx", [32, 400])
+def test_forward_and_gradients_match_the_oracle(B, S, orc, nx):
+    """nx = 400 (160,000 rows, 1,250 row tiles): every persistent layer and GEMM CTA runs several
+    tiles, so the stage ring and the TMEM double buffer go through many phases."""
+    us = 0.01
     ic = si.jittered_lattice(nx, seed=21)
     r = si.uniform53(22, 2 * ic["n"]).reshape(2, -1) - 0.5
     ic["ux"], ic["uy"] = 0.02 * r[0], 0.02 * r[1]
