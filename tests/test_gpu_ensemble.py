@@ -116,3 +116,41 @@ def test_failing_member_is_named_and_others_advance(B):
         assert steps == [4, 2, 4], steps
     finally:
         B.ann_ensemble_destroy(ens)
+
+
+def test_benchmark_ensemble_members_match_solo_runs(B):
+    """The benchmark's 64-member ensemble (sides uniform in [128, 512], 7.4M particles, autotuned
+    grouping) after a few steps: sampled members, the smallest and the largest among them, are
+    bit-identical to the same members stepped alone."""
+    import math
+
+    import sph_inputs as si
+
+    u = si.uniform53(2021, 3 * 64).reshape(64, 3)   # the benchmark's member recipe
+    spec = [(int(round(128 + 384 * u[k, 0])), math.exp(math.log(0.01) + u[k, 1] * (math.log(0.2) - math.log(0.01))),
+             0.01 + 0.07 * u[k, 2]) for k in range(64)]
+    plist = [B.ann_default_params(n=nx * nx, h=1.3 / nx, zeta=z, K=K, dt_mode=1) for nx, z, K in spec]
+    ics = [si.jittered_lattice(nx, seed=100 + k) for k, (nx, _, _) in enumerate(spec)]
+    ens = B.ann_ensemble_create(plist)
+    try:
+        for k, ic in enumerate(ics):
+            _load(B, B.ann_ensemble_member(ens, k), ic)
+        B.ann_ensemble_autotune(ens, 2)
+        B.ann_ensemble_step(ens, 3)
+        sides = [s[0] for s in spec]
+        sample = sorted({sides.index(min(sides)), sides.index(max(sides)), 0, 17, 33, 50, 63})
+        for k in sample:
+            ctx = B.ann_ensemble_member(ens, k)
+            steps = B.ann_get_diagnostics(ctx)["step"]
+            got = _state(B, ctx, ics[k]["n"])
+            solo = B.ann_create(plist[k])
+            try:
+                _load(B, solo, ics[k])
+                B.ann_step(solo, steps)
+                want = _state(B, solo, ics[k]["n"])
+            finally:
+                B.ann_destroy(solo)
+            for f in got:
+                assert np.array_equal(got[f], want[f]), (k, f)
+    finally:
+        B.ann_ensemble_destroy(ens)
