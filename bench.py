@@ -825,24 +825,23 @@ def run_ours(args):
     dom = max(kms, key=kms.get)
     dom_launch_ms = kprof[dom] / max(klaunch[dom], 1)
 
-    # end to end through the C-ABI with host buffers: the state in pinned host arrays, in the
-    # precision the library keeps it -> ann_set_state -> step -> ann_get_state back, every step
+    # end to end through the C-ABI with host buffers: the host holds the state between steps, in
+    # pinned arrays and in the precision the library keeps it (with the last acceleration);
+    # every step uploads it (ann_update_state), advances one step and reads it back (ann_get_state)
     src = {"X": ic["x"], "Y": ic["y"], "UX": ic["ux"], "UY": ic["uy"], "Q11": ic["q11"], "Q12": ic["q12"],
-           "DRHO": np.asarray(ic["rho"]) / p.rho0 - 1.0}
+           "DRHO": np.asarray(ic["rho"]) / p.rho0 - 1.0, "AX": np.zeros(n), "AY": np.zeros(n)}
     pin = {k: torch.from_numpy(np.ascontiguousarray(v, dtype=B.field_dtype(k))).pin_memory().numpy()
            for k, v in src.items()}
-    outs = {"X": np.float64, "Y": np.float64, "UX": np.float32, "UY": np.float32, "Q11": np.float32,
-            "Q12": np.float32, "DRHO": np.float32}
-    pout = {k: torch.empty(n, dtype=torch.float64 if dt == np.float64 else torch.float32).pin_memory().numpy()
-            for k, dt in outs.items()}
-    h2d = sum(a.nbytes for a in pin.values())
-    d2h = sum(a.nbytes for a in pout.values())
+    B.ann_set_state(ctx, pin)
+    B.ann_step(ctx, 1)
+    B.ann_get_state(ctx, n, out=pin)
+    h2d = d2h = sum(a.nbytes for a in pin.values())
     e2e_steps = max(5, min(50, args.steps // 20))
 
     def e2e_iter():
-        B.ann_set_state(ctx, pin)
+        B.ann_update_state(ctx, pin)
         B.ann_step(ctx, 1)
-        B.ann_get_state(ctx, n, out=pout)
+        B.ann_get_state(ctx, n, out=pin)
 
     e2e_iter()
     torch.cuda.synchronize()

@@ -251,11 +251,22 @@ int ann_set_record(ann_ctx *ctx, int on);
  * (unknown field, short buffer), STATE (no particles), CUDA. */
 int ann_get_field(ann_ctx *ctx, int field, void *dst, int64_t bytes, int dst_is_device);
 
-/* The state (x, y FP64; ux, uy, q11, q12 and drho = rho/rho0 - 1 FP32; n each, particle-ID order)
- * in one call with one synchronisation: the same values as ann_get_field of ANN_FIELD_X ... _DRHO.
- * A NULL destination is skipped.  dst_is_device as for ann_get_field.  Errors: STATE, CUDA. */
+/* The state (x, y FP64; ux, uy, q11, q12, drho = rho/rho0 - 1 and the last step's acceleration
+ * ax, ay FP32; n each, particle-ID order) in one call with one synchronisation: the same values as
+ * ann_get_field of ANN_FIELD_X ... _DRHO, _AX, _AY.  A NULL destination is skipped.  dst_is_device
+ * as for ann_get_field.  Errors: STATE, CUDA. */
 int ann_get_state(ann_ctx *ctx, double *x, double *y, float *ux, float *uy, float *q11, float *q12,
-                  float *drho, int dst_is_device);
+                  float *drho, float *ax, float *ay, int dst_is_device);
+
+/* Replace the present state of a loaded context by the arrays (particle-ID order, the layout of
+ * ann_get_state; drho, ax, ay NULL: 0), keeping t, the step count, the periodic image counts and
+ * the cell structure: each particle keeps its slot, and the next step re-sorts only if some
+ * particle is half the candidate skin away from where the last re-sort put it, as after any step.
+ * ann_get_state followed by ann_update_state of the same arrays leaves the trajectory
+ * bit-identical.  Errors: INVALID_ARG, STATE (nothing loaded), NONFINITE (also drho <= -1), CUDA. */
+int ann_update_state(ann_ctx *ctx, const double *x, const double *y, const float *ux, const float *uy,
+                     const float *q11, const float *q12, const float *drho, const float *ax, const float *ay,
+                     int is_device);
 
 /* FP64 diagnostics of the current state.  Errors: STATE, CUDA. */
 int ann_get_diagnostics(ann_ctx *ctx, ann_diag *out);

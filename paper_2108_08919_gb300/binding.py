@@ -119,7 +119,8 @@ def lib() -> ctypes.CDLL:
         "ann_kernel_name": (ctypes.c_char_p, [i32]),
         "ann_set_record": (i32, [vp, i32]),
         "ann_get_field": (i32, [vp, i32, vp, i64, i32]),
-        "ann_get_state": (i32, [vp, vp, vp, vp, vp, vp, vp, vp, i32]),
+        "ann_get_state": (i32, [vp] * 10 + [i32]),
+        "ann_update_state": (i32, [vp] * 10 + [i32]),
         "ann_set_state": (i32, [vp, i64, vp, vp, vp, vp, vp, vp, vp, i32]),
         "ann_get_diagnostics": (i32, [vp, _P(ann_diag)]),
         "ann_get_neighbors": (i32, [vp, _P(ctypes.c_int64), _P(ctypes.c_int32), i64]),
@@ -295,29 +296,7 @@ def ann_set_particles(ctx, x, y, ux, uy, q11, q12, rho=None) -> None:
 def ann_set_state(ctx, state: dict) -> None:
     """Load the state as ann_get_state returns it: a dict with X, Y (float64) and UX, UY, Q11, Q12
     and optionally DRHO (float32), all numpy arrays or all CUDA tensors, in particle-ID order."""
-    ptrs, dev, n = [], None, None
-    for f in STATE_FIELDS:
-        a = state.get(f)
-        if a is None:
-            if f != "DRHO":
-                raise ValueError(f"state[{f!r}] is required")
-            ptrs.append(None)
-            continue
-        is_dev = bool(getattr(a, "is_cuda", False))
-        dev = is_dev if dev is None else dev
-        if is_dev != dev:
-            raise ValueError("state must be all host arrays or all CUDA tensors")
-        size = a.numel() if is_dev else a.size
-        n = size if n is None else n
-        want = np.dtype(field_dtype(f))
-        if is_dev:
-            if a.element_size() != want.itemsize or size != n or not a.is_contiguous():
-                raise ValueError(f"state[{f!r}] must be a contiguous {want.name} tensor of n values")
-            ptrs.append(ctypes.c_void_p(a.data_ptr()))
-        else:
-            if a.dtype != want or size != n or not a.flags.c_contiguous:
-                raise ValueError(f"state[{f!r}] must be a contiguous {want.name} array of n values")
-            ptrs.append(ctypes.c_void_p(a.ctypes.data))
+    ptrs, dev, n = _state_ptrs(state, STATE_FIELDS, ("X", "Y", "UX", "UY", "Q11", "Q12"), "state")
     _check(lib().ann_set_state(ctx, n, *ptrs, 1 if dev else 0), ctx, "ann_set_state")
 
 
@@ -363,35 +342,57 @@ def ann_get_field(ctx, field: str, n: int, out=None):
 
 
 STATE_FIELDS = ("X", "Y", "UX", "UY", "Q11", "Q12", "DRHO")
+FULL_STATE = STATE_FIELDS + ("AX", "AY")   # with the last step's acceleration
 
 
-def ann_get_state(ctx, n: int, out=None) -> dict:
-    """The state fields X, Y (float64) and UX, UY, Q11, Q12, DRHO (float32) in particle-ID order,
-    in one call: new numpy arrays, or written into ``out`` (a dict of numpy arrays, or of CUDA
-    tensors, with some or all of those names)."""
-    if out is None:
-        out = {f: np.empty(n, dtype=field_dtype(f)) for f in STATE_FIELDS}
-    ptrs, dev = [], None
-    for f in STATE_FIELDS:
-        a = out.get(f)
+def _state_ptrs(arrays: dict, names, required, what: str):
+    """Pointers (None where absent) of host arrays or CUDA tensors of the fields' dtypes, and whether
+    they are on the device; every array holds the same number of values, which is returned."""
+    ptrs, dev, n = [], None, None
+    for f in names:
+        a = arrays.get(f)
         if a is None:
+            if f in required:
+                raise ValueError(f"{what}[{f!r}] is required")
             ptrs.append(None)
             continue
         is_dev = bool(getattr(a, "is_cuda", False))
-        if dev is None:
-            dev = is_dev
+        dev = is_dev if dev is None else dev
         if is_dev != dev:
-            raise ValueError("out must be all host arrays or all CUDA tensors")
+            raise ValueError(f"{what} must be all host arrays or all CUDA tensors")
+        size = a.numel() if is_dev else a.size
+        n = size if n is None else n
+        want = np.dtype(field_dtype(f))
         if is_dev:
-            if a.numel() < n or a.element_size() != np.dtype(field_dtype(f)).itemsize:
-                raise ValueError(f"out[{f!r}] must hold n values of the field's dtype")
+            if a.element_size() != want.itemsize or size != n or not a.is_contiguous():
+                raise ValueError(f"{what}[{f!r}] must be a contiguous {want.name} tensor of n values")
             ptrs.append(ctypes.c_void_p(a.data_ptr()))
         else:
-            if a.dtype != field_dtype(f) or not a.flags.c_contiguous or a.size < n:
-                raise ValueError(f"out[{f!r}] must be a contiguous {np.dtype(field_dtype(f)).name} array of n values")
+            if a.dtype != want or size != n or not a.flags.c_contiguous:
+                raise ValueError(f"{what}[{f!r}] must be a contiguous {want.name} array of n values")
             ptrs.append(ctypes.c_void_p(a.ctypes.data))
+    return ptrs, bool(dev), n
+
+
+def ann_get_state(ctx, n: int, out=None) -> dict:
+    """The state fields X, Y (float64), UX, UY, Q11, Q12, DRHO and the last step's AX, AY (float32)
+    in particle-ID order, in one call: new numpy arrays, or written into ``out`` (a dict of numpy
+    arrays, or of CUDA tensors, with some or all of those names)."""
+    if out is None:
+        out = {f: np.empty(n, dtype=field_dtype(f)) for f in FULL_STATE}
+    ptrs, dev, m = _state_ptrs(out, FULL_STATE, (), "out")
+    if m is not None and m < n:
+        raise ValueError("out arrays must hold n values")
     _check(lib().ann_get_state(ctx, *ptrs, 1 if dev else 0), ctx, "ann_get_state")
     return out
+
+
+def ann_update_state(ctx, state: dict) -> None:
+    """Replace the present state, keeping the step count and the cell structure (see the header): a
+    dict with the names of ann_get_state (DRHO, AX, AY optional), all numpy arrays or all CUDA
+    tensors, in particle-ID order."""
+    ptrs, dev, _ = _state_ptrs(state, FULL_STATE, ("X", "Y", "UX", "UY", "Q11", "Q12"), "state")
+    _check(lib().ann_update_state(ctx, *ptrs, 1 if dev else 0), ctx, "ann_update_state")
 
 
 def ann_get_diagnostics(ctx) -> dict:

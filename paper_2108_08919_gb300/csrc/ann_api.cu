@@ -505,6 +505,41 @@ __global__ void k_load_state(DevParams P, Bufs b, const double *x, const double 
     b.img[i] = make_int2(0, 0);
 }
 
+// ann_update_state: slot g of the state takes particle ids[g]'s values (ids: the particle at each
+// slot in the order of the last re-sort), so the cell structure and candidate lists stay valid.
+__global__ void k_update_state(DevParams P, Bufs b, const int *ids, const double *x, const double *y,
+                               const float *ux, const float *uy, const float *q11, const float *q12,
+                               const float *drho, const float *ax, const float *ay)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= P.n) return;
+    const int id = ids[g];
+    double xx = x[id], yy = y[id];
+    const float d = drho ? drho[id] : 0.f, a0 = ax ? ax[id] : 0.f, a1 = ay ? ay[id] : 0.f;
+    if (!(isfinite(xx) && isfinite(yy) && isfinite(ux[id]) && isfinite(uy[id]) && isfinite(q11[id]) &&
+          isfinite(q12[id]) && isfinite(d) && d > -1.f && isfinite(a0) && isfinite(a1))) {
+        atomicOr(b.err, EB_NONFINITE);
+        xx = 0.0;
+        yy = 0.0;
+    }
+    if (xx < -P.L || xx >= 2.0 * P.L) xx = xx - floor(xx / P.L) * P.L;
+    if (yy < -P.L || yy >= 2.0 * P.L) yy = yy - floor(yy / P.L) * P.L;
+    if (xx < 0.0) xx += P.L;
+    if (xx >= P.L) xx -= P.L;
+    if (yy < 0.0) yy += P.L;
+    if (yy >= P.L) yy -= P.L;
+    b.sx[g] = xx + 0.0;
+    b.sy[g] = yy + 0.0;
+    b.sux[g] = ux[id];
+    b.suy[g] = uy[id];
+    b.sq11[g] = q11[id];
+    b.sq12[g] = q12[id];
+    b.sdr[g] = d;
+    b.sax[g] = a0;
+    b.say[g] = a1;
+    b.sid[g] = id;
+}
+
 __global__ void k_deinterleave(const float *src, float *dst, int n, int stride, int comp)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -713,6 +748,44 @@ int ann_set_state(ann_ctx *c, int64_t n, const double *x, const double *y, const
     return s;
 }
 
+int ann_update_state(ann_ctx *c, const double *x, const double *y, const float *ux, const float *uy,
+                     const float *q11, const float *q12, const float *drho, const float *ax, const float *ay,
+                     int is_device)
+{
+    if (!c) return ANN_ERR_INVALID_ARG;
+    if (!c->have_particles) return fail(c, ANN_ERR_STATE, "ann_update_state before ann_set_particles");
+    if (!x || !y || !ux || !uy || !q11 || !q12) return fail(c, ANN_ERR_INVALID_ARG, "null input array");
+    const size_t n = (size_t)c->P.n;
+    const void *dev[9] = {x, y, ux, uy, q11, q12, drho, ax, ay};
+    cudaError_t e = cudaSuccess;
+    if (!is_device) {
+        unsigned char *t = static_cast<unsigned char *>(c->tmp);   // 44 of its >= 56 bytes per particle
+        size_t off = 0;
+        for (int k = 0; k < 9 && !e; k++) {
+            const size_t bytes = (k < 2 ? 8 : 4) * n;
+            if (dev[k]) {
+                e = cudaMemcpyAsync(t + off, dev[k], bytes, cudaMemcpyHostToDevice, c->stream);
+                dev[k] = t + off;
+            }
+            off += bytes;
+        }
+        if (e) return cuda_fail(c, e, "ann_update_state copy");
+    }
+    // the particle at each slot of the last re-sort: M's order when M holds the present state (a
+    // search may have re-sorted into it), else S's
+    const int *ids = c->m_current ? c->b.mid : c->b.sid;
+    k_update_state<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+        c->P, c->b, ids, (const double *)dev[0], (const double *)dev[1], (const float *)dev[2], (const float *)dev[3],
+        (const float *)dev[4], (const float *)dev[5], (const float *)dev[6], (const float *)dev[7],
+        (const float *)dev[8]);
+    e = cudaGetLastError();
+    if (e) return cuda_fail(c, e, "ann_update_state");
+    c->s_sorted = c->m_current = false;
+    c->rec_valid = false;
+    c->grid_step = -1;
+    return device_status(c);
+}
+
 int ann_step(ann_ctx *c, int64_t nsteps)
 {
     if (!c || nsteps < 0) return ANN_ERR_INVALID_ARG;
@@ -832,17 +905,18 @@ int ann_get_field(ann_ctx *c, int field, void *dst, int64_t bytes, int dst_is_de
 }
 
 int ann_get_state(ann_ctx *c, double *x, double *y, float *ux, float *uy, float *q11, float *q12, float *drho,
-                  int dst_is_device)
+                  float *ax, float *ay, int dst_is_device)
 {
     if (!c) return ANN_ERR_INVALID_ARG;
     if (!c->have_particles) return fail(c, ANN_ERR_STATE, "no particles");
     const size_t n = (size_t)c->P.n;
     const Bufs &b = c->b;
-    // each field is un-permuted into its own part of the staging buffer (36 bytes per particle of
+    // each field is un-permuted into its own part of the staging buffer (44 bytes per particle of
     // the >= 56 it holds), so all copies are in flight before the one synchronisation
     unsigned char *tmp = static_cast<unsigned char *>(c->tmp);
-    struct Part { const void *src; void *dst; int es; } parts[7] = {
-        {b.sx, x, 8}, {b.sy, y, 8}, {b.sux, ux, 4}, {b.suy, uy, 4}, {b.sq11, q11, 4}, {b.sq12, q12, 4}, {b.sdr, drho, 4}};
+    struct Part { const void *src; void *dst; int es; } parts[9] = {
+        {b.sx, x, 8}, {b.sy, y, 8}, {b.sux, ux, 4}, {b.suy, uy, 4}, {b.sq11, q11, 4}, {b.sq12, q12, 4}, {b.sdr, drho, 4},
+        {b.sax, ax, 4}, {b.say, ay, 4}};
     const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     cudaError_t e = cudaSuccess;
     size_t off = 0;
