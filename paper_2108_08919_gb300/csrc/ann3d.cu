@@ -23,6 +23,7 @@
 #include "../../include/ann.h"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstring>
@@ -732,6 +733,14 @@ __global__ void k3_int_to_id(int n, const int *v, const int *id, double *dst)
 
 inline unsigned nb3(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// A named NVTX range for the lifetime of the object (profilers show the library's calls).
+struct Range3 {
+    explicit Range3(const char *name) { nvtxRangePushA(name); }
+    ~Range3() { nvtxRangePop(); }
+    Range3(const Range3 &) = delete;
+    Range3 &operator=(const Range3 &) = delete;
+};
+
 }  // namespace
 
 struct ann3_ctx {
@@ -983,6 +992,7 @@ int ann3_set_particles(ann3_ctx *c, int64_t n, const double *x, const double *y,
 
 int ann3_step(ann3_ctx *c, int64_t nsteps)
 {
+    Range3 range("ann3_step");
     if (!c || nsteps < 0) return ANN_ERR_INVALID_ARG;
     if (!c->have) return fail3(c, ANN_ERR_STATE, "ann3_step before ann3_set_particles");
     const P3 &P = c->P;

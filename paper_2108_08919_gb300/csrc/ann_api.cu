@@ -671,6 +671,7 @@ int ann_set_particles(ann_ctx *c, int64_t n, const double *x, const double *y, c
                       const double *uy, const double *q11, const double *q12, const double *rho,
                       int is_device)
 {
+    NvtxRange range("ann_set_particles");
     if (!c) return ANN_ERR_INVALID_ARG;
     if (n != c->prm.n) return fail(c, ANN_ERR_INVALID_ARG, "n differs from the n of ann_create");
     if (!x || !y || !ux || !uy || !q11 || !q12) return fail(c, ANN_ERR_INVALID_ARG, "null input array");
@@ -708,6 +709,7 @@ int ann_set_particles(ann_ctx *c, int64_t n, const double *x, const double *y, c
 int ann_set_state(ann_ctx *c, int64_t n, const double *x, const double *y, const float *ux, const float *uy,
                   const float *q11, const float *q12, const float *drho, int is_device)
 {
+    NvtxRange range("ann_set_state");
     if (!c) return ANN_ERR_INVALID_ARG;
     if (n != c->prm.n) return fail(c, ANN_ERR_INVALID_ARG, "n differs from the n of ann_create");
     if (!x || !y || !ux || !uy || !q11 || !q12) return fail(c, ANN_ERR_INVALID_ARG, "null input array");
@@ -752,6 +754,7 @@ int ann_update_state(ann_ctx *c, const double *x, const double *y, const float *
                      const float *q11, const float *q12, const float *drho, const float *ax, const float *ay,
                      int is_device)
 {
+    NvtxRange range("ann_update_state");
     if (!c) return ANN_ERR_INVALID_ARG;
     if (!c->have_particles) return fail(c, ANN_ERR_STATE, "ann_update_state before ann_set_particles");
     if (!x || !y || !ux || !uy || !q11 || !q12) return fail(c, ANN_ERR_INVALID_ARG, "null input array");
@@ -788,6 +791,7 @@ int ann_update_state(ann_ctx *c, const double *x, const double *y, const float *
 
 int ann_step(ann_ctx *c, int64_t nsteps)
 {
+    NvtxRange range("ann_step");
     if (!c || nsteps < 0) return ANN_ERR_INVALID_ARG;
     if (!c->have_particles) return fail(c, ANN_ERR_STATE, "ann_step before ann_set_particles");
     for (int64_t s = 0; s < nsteps; s++) {
@@ -808,6 +812,7 @@ int ann_step(ann_ctx *c, int64_t nsteps)
 
 int ann_step_profile(ann_ctx *c, int64_t nsteps, double *kernel_ms)
 {
+    NvtxRange range("ann_step_profile");
     if (!c || nsteps < 0 || !kernel_ms) return ANN_ERR_INVALID_ARG;
     if (!c->have_particles) return fail(c, ANN_ERR_STATE, "ann_step_profile before ann_set_particles");
     // The same kernels as the step graph, launched one by one between CUDA events.  The host reads
@@ -833,7 +838,10 @@ int ann_step_profile(ann_ctx *c, int64_t nsteps, double *kernel_ms)
         if (!e) e = cudaEventRecord(E[2], c->stream);
         for (int k = 1; k < NKERNELS && !e; k++) {
             bool run = (k <= 5) ? rs : (k == 6 ? !rs : true);
-            if (run) e = launch_kernel(k, c->P, c->b, c->stream);
+            if (run) {
+                NvtxRange r(kernel_name(k));
+                e = launch_kernel(k, c->P, c->b, c->stream);
+            }
             if (!e) e = cudaEventRecord(E[k + 2], c->stream);
         }
     }
@@ -907,6 +915,7 @@ int ann_get_field(ann_ctx *c, int field, void *dst, int64_t bytes, int dst_is_de
 int ann_get_state(ann_ctx *c, double *x, double *y, float *ux, float *uy, float *q11, float *q12, float *drho,
                   float *ax, float *ay, int dst_is_device)
 {
+    NvtxRange range("ann_get_state");
     if (!c) return ANN_ERR_INVALID_ARG;
     if (!c->have_particles) return fail(c, ANN_ERR_STATE, "no particles");
     const size_t n = (size_t)c->P.n;
@@ -1559,6 +1568,7 @@ int ann_ensemble_set_groups(ann_ensemble *E, int32_t groups)
 
 int ann_ensemble_step(ann_ensemble *E, int64_t nsteps)
 {
+    ann::NvtxRange range("ann_ensemble_step");
     if (!E || nsteps < 0) return ANN_ERR_INVALID_ARG;
     for (size_t k = 0; k < E->m.size(); k++)
         if (!E->m[k]->have_particles)

@@ -6,8 +6,19 @@
 #include <cstdint>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace ann {
+
+// A named NVTX range for the lifetime of the object: profilers (Nsight Systems and the like) show
+// the library's calls and, in the profiled step, each pass; without a profiler attached it costs
+// a check of a function pointer.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Tiling of the pair passes: one CUDA block per TILE x TILE cells; it stages the particles of the
 // (TILE+2) x (TILE+2) cells around them (periodic images included) in shared memory.

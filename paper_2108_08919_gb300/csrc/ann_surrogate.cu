@@ -573,6 +573,7 @@ int ann_surrogate_set_scales(ann_surrogate *S, double us, double ys_q, double ys
 
 int ann_surrogate_load(ann_surrogate *S, ann_ctx *ctx, const float *tend)
 {
+    ann::NvtxRange range("ann_surrogate_load");
     if (!S || !ctx) return ANN_ERR_INVALID_ARG;
     CtxView v;
     int st = ctx_view(ctx, &v);
@@ -667,6 +668,7 @@ int ann_surrogate_adam(ann_surrogate *S, double lr)
 
 int ann_surrogate_jump(ann_surrogate *S, ann_ctx *ctx, const float *tend)
 {
+    ann::NvtxRange range("ann_surrogate_jump");
     if (!S || !ctx) return ANN_ERR_INVALID_ARG;
     const int k = S->k;
     int st = ann_surrogate_load(S, ctx, tend);
