@@ -490,3 +490,34 @@ def test_update_state_round_trip_and_moved_particles(B, orc):
     finally:
         a.close()
         b.close()
+
+
+def test_isolated_particle_is_a_singular_correction_tensor(B, orc):
+    """The method's degenerate case: a particle with no neighbour within 3h has alpha = 0 (Eq. 22
+    cannot be inverted).  The step reports SINGULAR_ALPHA instead of producing infinities, and the
+    context stays usable.  The ring of particles pushed out to make the gap keeps full supports."""
+    nx = 64
+    ic = si.jittered_lattice(nx, seed=6)
+    h = 1.3 / nx
+    x, y = ic["x"].copy(), ic["y"].copy()
+    cx = cy = 0.5
+    dx, dy = x - cx, y - cy
+    r = np.hypot(dx, dy)
+    inside = r < 4.0 * h
+    k0 = int(np.argmin(r))
+    scale = np.where(inside, 4.0 * h / np.maximum(r, 1e-12), 1.0)
+    x, y = cx + dx * scale, cy + dy * scale
+    x[k0], y[k0] = cx, cy                       # the isolated particle
+    rp, cols = orc.neighbors(x, y, 1.0, h)
+    assert rp[k0 + 1] == rp[k0]                 # no neighbour within 3h
+    ctx = B.ann_create(gpu_params(B, params(nx), nx * nx))
+    try:
+        B.ann_set_particles(ctx, x, y, ic["ux"], ic["uy"], ic["q11"], ic["q12"])
+        with pytest.raises(B.AnnError) as e:
+            B.ann_step(ctx, 1)
+        assert e.value.status == -7
+        assert B.ann_get_diagnostics(ctx)["error_bits"] & 16
+        B.ann_set_particles(ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"])
+        B.ann_step(ctx, 1)
+    finally:
+        B.ann_destroy(ctx)
