@@ -199,9 +199,25 @@ def cpu_baseline(nx: int, budget_s: float = 10.0, max_steps: int = 6):
         if time.perf_counter() - t0 >= budget_s:
             break
     el = time.perf_counter() - t0
-    return {"value": nx * nx * steps / el, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # one core: one step of a 256 x 256 box with the same dx, h and parameters (the same work per
+    # particle, a bounded sample)
+    n1 = 256
+    ic1 = si.jittered_lattice(n1, L=n1 / nx, seed=0)
+    P1 = oracle.make_params(L=n1 / nx, h=h, dt=dt, zeta=PARAMS["zeta"], K=PARAMS["K"], nbr_mode="cells")
+    oracle.set_num_threads(1)
+    try:
+        t1 = time.perf_counter()
+        oracle.step(P1, {k: ic1[k] for k in ("x", "y", "ux", "uy", "q11", "q12", "rho")}, 1)
+        el1 = time.perf_counter() - t1
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": nx * nx * steps / el, "unit": METRIC, "cores": cores, "kind": "oracle",
             "sample": f"{steps} whole FP64 oracle step(s) of the {nx}x{nx} workload (cell-grid search, "
-                      f"OpenMP over particles), {el:.1f} s"}
+                      f"OpenMP over particles), {el:.1f} s",
+            "single_core_value": n1 * n1 / el1,
+            "single_core_sample": f"1 step of a {n1}x{n1} periodic sub-box (same dx, h, parameters) on 1 core, "
+                                  f"{el1:.1f} s"}
 
 
 def run_reference(args):
