@@ -1676,8 +1676,14 @@ int ctx_search_present(ann_ctx *c)
     DevParams Q = c->P;
     Q.half_dt = 0.f;
     Q.half_dt_d = 0.0;
-    // re-sorts only if the lists of the last re-sort no longer cover the present positions
-    cudaError_t e = enqueue_search_present(Q, c->b, c->stream);
+    // re-sorts only if the lists of the last re-sort no longer cover the present positions: the
+    // host reads the predictor's decision and launches only the branch that does work
+    cudaError_t e = launch_kernel(0, Q, c->b, c->stream);
+    if (!e) e = cudaMemcpyAsync(c->h_err, c->b.rebuild, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    const bool rs = !e && *c->h_err != 0u;
+    for (int k = rs ? 1 : 6; k <= (rs ? 5 : 6) && !e; k++) e = launch_kernel(k, Q, c->b, c->stream);
+    if (!e) e = cudaMemsetAsync(c->b.maxu, 0, sizeof(uint32_t), c->stream);
     if (e) return cuda_fail(c, e, "search");
     int st = device_status(c);
     if (st) return st;

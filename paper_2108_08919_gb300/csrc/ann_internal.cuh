@@ -109,10 +109,6 @@ cudaError_t launch_set_condition(const Bufs &b, cudaGraphConditionalHandle h, cu
 // Cell sort and the re-sort pass A only (neighbour lists and volumes) at the positions in S advanced
 // by P.half_dt (callers pass 0 to keep them).  Requires *b.rebuild != 0.
 cudaError_t enqueue_search(const DevParams &P, const Bufs &b, cudaStream_t s);
-// Pass A at the positions in S advanced by P.half_dt, re-sorting only where the step would: when
-// *b.rebuild is set or a particle has moved past half the skin since the last re-sort; otherwise
-// the candidate lists of that re-sort are filtered at the new positions.
-cudaError_t enqueue_search_present(const DevParams &P, const Bufs &b, cudaStream_t s);
 // Rebuild the candidate lists from xi_ref (the split positions of the last re-sort), with the
 // cell starts of that re-sort: used after a checkpoint is loaded.
 cudaError_t enqueue_candidates_from_ref(const DevParams &P, const Bufs &b, cudaStream_t s);

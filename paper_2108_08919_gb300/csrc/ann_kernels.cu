@@ -1421,14 +1421,6 @@ cudaError_t enqueue_search(const DevParams &P, const Bufs &b, cudaStream_t s)
     return cudaMemsetAsync(b.maxu, 0, sizeof(uint32_t), s);
 }
 
-cudaError_t enqueue_search_present(const DevParams &P, const Bufs &b, cudaStream_t s)
-{
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k <= 6 && !e; k++) e = launch_kernel(k, P, b, s);
-    if (e) return e;
-    return cudaMemsetAsync(b.maxu, 0, sizeof(uint32_t), s);
-}
-
 cudaError_t enqueue_candidates_from_ref(const DevParams &P, const Bufs &b, cudaStream_t s)
 {
     k_pass_a_resort<true><<<P.tiles * P.tiles, PT, SMEM_A, s>>>(P, b);
