@@ -172,7 +172,7 @@ struct CtxView {
     DevParams P;
     Bufs b;
     cudaStream_t stream;
-    double *tmp;   // 7 n doubles of staging
+    double *tmp;   // staging of at least 7 n doubles
     double t;
     int64_t steps;
     bool rec_valid;   // the last step recorded grad u, lap Q and a
