@@ -150,3 +150,21 @@ def test_create_without_gpu_reports_not_available(B):
     with pytest.raises(B.AnnError) as e:
         B.ann_create(B.ann_default_params())
     assert e.value.status == -10
+
+
+def test_state_transfer_arguments_are_checked_on_the_host(B):
+    """The binding rejects state arrays of the wrong dtype, length or mixture before any call."""
+    import numpy as np
+
+    n = 16
+    good = {"X": np.zeros(n), "Y": np.zeros(n), "UX": np.zeros(n, np.float32), "UY": np.zeros(n, np.float32),
+            "Q11": np.zeros(n, np.float32), "Q12": np.zeros(n, np.float32)}
+    for bad in ({**good, "UX": np.zeros(n)},                     # float64 where float32 is kept
+                {**good, "Q12": np.zeros(n - 1, np.float32)},   # short
+                {k: v for k, v in good.items() if k != "Y"}):   # a required field missing
+        with pytest.raises(ValueError):
+            B.ann_update_state(None, bad)
+        with pytest.raises(ValueError):
+            B.ann_set_state(None, bad)
+    with pytest.raises(ValueError):
+        B.ann_get_state(None, n, out={"X": np.zeros(n, np.float32)})
