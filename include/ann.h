@@ -182,7 +182,7 @@ int ann_grid_info(const ann_params *p, ann_grid *out);
 int ann_create(const ann_params *p, ann_ctx **out);
 
 /* Device memory provider for a context, in place of cudaMalloc / cudaFree (for example a host
- * framework's caching allocator).  alloc returns a device pointer to at least `bytes` bytes on the
+ * framework's caching allocator); the paper has no counterpart.  alloc returns a device pointer to at least `bytes` bytes on the
  * current device, 16-byte aligned, or NULL on failure; release frees a pointer alloc returned,
  * with the same byte count.  `stream` is the context's own stream (a cudaStream_t): memory is used
  * on it, and a context synchronises it before it releases anything.  Both are called on the
@@ -215,7 +215,8 @@ int ann_set_particles(ann_ctx *ctx, int64_t n, const double *x, const double *y,
                       const double *uy, const double *q11, const double *q12, const double *rho,
                       int is_device);
 
-/* Load the state in the precision the context keeps it, as ann_get_state returns it: x, y FP64;
+/* Load the state of §3.1 (initial conditions, as ann_set_particles) in the precision the context
+ * keeps it, as ann_get_state returns it: x, y FP64;
  * ux, uy, q11, q12 FP32; drho = rho/rho0 - 1 FP32 (NULL: 0); n each, particle-ID order.
  * Otherwise as ann_set_particles (positions re-inserted, a^0 = 0, t and the step count 0, the next
  * step re-sorts): the same state as ann_set_particles of the same values.  Errors: INVALID_ARG,
@@ -251,14 +252,16 @@ int ann_set_record(ann_ctx *ctx, int on);
  * (unknown field, short buffer), STATE (no particles), CUDA. */
 int ann_get_field(ann_ctx *ctx, int field, void *dst, int64_t bytes, int dst_is_device);
 
-/* The state (x, y FP64; ux, uy, q11, q12, drho = rho/rho0 - 1 and the last step's acceleration
- * ax, ay FP32; n each, particle-ID order) in one call with one synchronisation: the same values as
+/* The state the time integration of §3.1 carries from step to step (positions, velocity, Q,
+ * density and the acceleration a^{n-1/2} the predictor uses): x, y FP64; ux, uy, q11, q12,
+ * drho = rho/rho0 - 1 and ax, ay FP32; n each, particle-ID order, in one call with one
+ * synchronisation: the same values as
  * ann_get_field of ANN_FIELD_X ... _DRHO, _AX, _AY.  A NULL destination is skipped.  dst_is_device
  * as for ann_get_field.  Errors: STATE, CUDA. */
 int ann_get_state(ann_ctx *ctx, double *x, double *y, float *ux, float *uy, float *q11, float *q12,
                   float *drho, float *ax, float *ay, int dst_is_device);
 
-/* Replace the present state of a loaded context by the arrays (particle-ID order, the layout of
+/* Replace the present state of §3.1 of a loaded context by the arrays (particle-ID order, the layout of
  * ann_get_state; drho, ax, ay NULL: 0), keeping t, the step count, the periodic image counts and
  * the cell structure: each particle keeps its slot, and the next step re-sorts only if some
  * particle is half the candidate skin away from where the last re-sort put it, as after any step.
@@ -386,10 +389,10 @@ int ann_bf16_gemm(const void *A1, int32_t K1, const void *A2, int32_t K2, const 
                   const float *bias, int32_t relu, void *C, int32_t c_bf16, int32_t accumulate, void *stream);
 int ann_bf16_gemm_tn(const void *A, int32_t K, const void *B, int32_t N, int64_t rows, float *C, void *stream);
 
-/* Self-test of the bounded waits of the tensor-core kernels: one device thread polls a
- * shared-memory mbarrier that nothing completes, gives up after spin_limit polls (1 .. 2^20) and
- * raises a device flag the way an expired wait of ann_bf16_gemm or the surrogate does; the call
- * reads the flag and returns ANN_ERR_TIMEOUT, its expected result.  Nothing faults or hangs, and
+/* Self-test of the bounded waits of the tensor-core kernels (the paper has no counterpart): one
+ * device thread polls a shared-memory mbarrier that nothing completes, gives up after spin_limit
+ * polls (1 .. 2^20) and raises a device flag the way an expired wait of ann_bf16_gemm or the
+ * surrogate does; the call reads the flag and returns ANN_ERR_TIMEOUT, its expected result.  Nothing faults or hangs, and
  * the device stays usable.  Synchronous on the legacy default stream.  Errors: INVALID_ARG,
  * NOT_AVAILABLE, CUDA (ANN_OK would mean the wait completed, which is a defect). */
 int ann_check_bounded_wait(uint32_t spin_limit);
