@@ -526,7 +526,7 @@ const char *ann_ensemble_last_error(ann_ensemble *ens);
  * Computes, for a velocity field already on the device (FP32 arrays ux, uy of length n, any
  * particle order), in FP64 with a fixed reduction order (deterministic):
  *   out[0], out[1] = sum_i m_i u_i (momentum), m_i = mass[i], or m0 for every particle if mass is NULL
- *   out[2]         = 1/2 <|u|^2>, the mean over the n particles (the paper's Eq. 31)
+ *   out[2]         = 1/2 <|u|^2>, the mean over the n particles (the kinetic_energy of ann_diag)
  *   out[3]         = max_i |u_i|
  * the same quantities ann_get_diagnostics reports for a context's state.  `out` is a device pointer
  * to 4 doubles; the call is asynchronous on `stream` (a cudaStream_t, NULL for the legacy default
@@ -538,8 +538,10 @@ const char *ann_ensemble_last_error(ann_ensemble *ens);
  * first call on a device looks up the array's device address (cudaGetSymbolAddress, with that
  * device current) and caches it; make that first call before any stream capture.  All calls share
  * the one array: calls whose kernels overlap on the GPU (different streams, or different host
- * threads on one device) race on it and must be serialised by the caller.  Errors: INVALID_ARG
- * (NULL pointer, n < 1), TOO_LARGE, CUDA.
+ * threads on one device) race on it and must be serialised by the caller.  Every pointer must be
+ * device memory of the current device (a pointer to host memory or to another GPU's memory returns
+ * INVALID_ARG before any launch).  Errors: INVALID_ARG (NULL pointer, n < 1, a pointer that is not
+ * memory of the current device), TOO_LARGE, CUDA.
  */
 #define ANN_NOALLOC_MAX_N 2097152
 int ann_velocity_moments_noalloc(const float *ux, const float *uy, const float *mass, double m0,

@@ -432,15 +432,33 @@ NOALLOC_MAX_N = 2097152
 def ann_velocity_moments_noalloc(ux, uy, out, mass=None, m0=1.0, stream=None) -> None:
     """Momentum, mean kinetic energy and peak speed of a device velocity field, written into the
     CUDA tensor ``out`` (4 float64) without any device allocation; ``ux``, ``uy`` (and ``mass``)
-    are float32 CUDA tensors.  Asynchronous on ``stream`` (default: the legacy default stream)."""
-    for a in (ux, uy, out) + ((mass,) if mass is not None else ()):
-        if not (hasattr(a, "data_ptr") and getattr(a, "is_cuda", False)):
-            raise ValueError("ux, uy, out and mass must be CUDA tensors")
+    are contiguous float32 CUDA tensors of one length n, all on one device.  Asynchronous on
+    ``stream`` (default: the legacy default stream).  The arguments are checked here, before any
+    C call: a shorter ``uy`` or ``mass`` or a smaller ``out`` would make the kernel read or write
+    past the end of an allocation."""
+    import torch
+
+    named = [("ux", ux), ("uy", uy), ("out", out)] + ([("mass", mass)] if mass is not None else [])
+    for name, a in named:
+        if not (isinstance(a, torch.Tensor) and a.is_cuda):
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if not a.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    n = ux.numel()
+    for name, a in named:
+        if name == "out":
+            if a.dtype != torch.float64 or a.numel() < 4:
+                raise ValueError("out must be a float64 tensor of at least 4 elements")
+        elif a.dtype != torch.float32 or a.numel() != n:
+            raise ValueError(f"{name} must be a float32 tensor of {n} elements (the length of ux)")
+    if len({a.device for _, a in named}) != 1:
+        raise ValueError("ux, uy, out and mass must be on one device")
     handle = getattr(stream, "cuda_stream", stream) if stream is not None else 0
-    st = lib().ann_velocity_moments_noalloc(
-        ctypes.c_void_p(ux.data_ptr()), ctypes.c_void_p(uy.data_ptr()),
-        ctypes.c_void_p(mass.data_ptr()) if mass is not None else None, float(m0), int(ux.numel()),
-        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(int(handle) if handle else 0))
+    with torch.cuda.device(ux.device):
+        st = lib().ann_velocity_moments_noalloc(
+            ctypes.c_void_p(ux.data_ptr()), ctypes.c_void_p(uy.data_ptr()),
+            ctypes.c_void_p(mass.data_ptr()) if mass is not None else None, float(m0), int(n),
+            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(int(handle) if handle else 0))
     _check(st, None, "ann_velocity_moments_noalloc")
 
 
@@ -471,7 +489,8 @@ def ann_spectrum_shells(M: int) -> int:
 
 
 def ann_energy_spectrum(ctx, M: int):
-    """(w, E): wavenumbers 2 pi n / L and the shell energies of the gridded velocity."""
+    """Shell energies E_n of the gridded velocity, n = 0 .. shells - 1; shell n is the wavenumber
+    w_n = 2 pi n / L."""
     ns = ann_spectrum_shells(M)
     E = np.zeros(ns)
     _check(lib().ann_energy_spectrum(ctx, int(M), _dptr(E), ns), ctx, "ann_energy_spectrum")

@@ -91,6 +91,18 @@ __global__ void __launch_bounds__(kThreads) k_moments_noalloc(const float *ux, c
     }
 }
 
+// True when p is device (or managed) memory of device dev: the kernel runs on dev and must not be
+// handed host memory or another GPU's memory.
+bool on_device(const void *p, int dev)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
 }  // namespace
 
 extern "C" int ann_velocity_moments_noalloc(const float *ux, const float *uy, const float *mass, double m0,
@@ -103,6 +115,8 @@ extern "C" int ann_velocity_moments_noalloc(const float *ux, const float *uy, co
         cudaGetLastError();
         return ANN_ERR_CUDA;
     }
+    if (!on_device(ux, dev) || !on_device(uy, dev) || !on_device(out, dev) || (mass && !on_device(mass, dev)))
+        return ANN_ERR_INVALID_ARG;
     unsigned char *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_setup_mutex);
