@@ -175,3 +175,123 @@ def test_step_records_and_zero_velocity_start(orc):
     want_ax = -0.05 * rec["divQx"] / rec["rho_hat"]
     assert np.abs(rec["ax"] - want_ax).max() <= 1e-15 * np.abs(want_ax).max()
     assert np.abs(out["ux"] - 0.5 * 1e-4 * rec["ax"]).max() <= 1e-18 + 1e-15 * np.abs(out["ux"]).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# Time integration (§3.1) with the corrector read as u^{n+1} = u^{n+1/2} + dt/2 a^{n+1/2}, the
+# positions r^{n+1} = r^{n+1/2} + dt/2 u^{n+1}, the density rho^{n+1} = rho_hat + dt/2 k, and
+# c0 = 10 max |u^{n+1/2}| (readings R11, R12).
+# ---------------------------------------------------------------------------------------------
+
+def _shear_wave(orc, nx, nsteps, literal=False):
+    # u_x = U sin(2 pi y) on a square lattice, zeta = 0: momentum is purely viscous.  On a perfect
+    # lattice the discrete operator maps the mode to itself, a = -lam_d u, and lam_d -> nu k^2
+    # (k = 2 pi) as h -> 0 (the "8 nu" form of Eq. 23 is nu lap u for div u = 0).  Returns
+    # (lam_d from the first step's midpoint acceleration, the decay rate over nsteps, nu k^2).
+    U, nu, dt = 1e-3, 0.05, 2e-3 * (32.0 / nx) ** 2
+    ic = si.jittered_lattice(nx, seed=0, jitter=0.0)
+    h = 1.3 * ic["dx"]
+    st = {k: ic[k] for k in ("x", "y", "uy", "q11", "q12", "rho")}
+    st["ux"] = U * np.sin(2 * np.pi * ic["y"])
+    P = orc.make_params(h=h, dt=dt, eta=nu, rho0=1.0, zeta=0.0, A=0.0, C=0.0, K=0.0, apd=0,
+                        nbr_mode="cells")
+    mode = np.sin(2 * np.pi * ic["y"])
+    amp = lambda v: 2.0 * np.dot(v, mode) / ic["n"]   # noqa: E731
+    a0 = amp(st["ux"])
+    _, rec = orc.step(P, st, 1, record=True)
+    lam = -amp(rec["ax"]) / a0
+    if nsteps == 0:
+        return lam, None, nu * (2 * np.pi) ** 2
+    if not literal:
+        out, _ = orc.step(P, st, nsteps)
+    else:
+        # the corrector as printed, u^{n+1} = u^n + dt/2 a^{n+1/2}: the test rewrites u after each
+        # oracle step from the step's recorded a^{n+1/2}
+        for _ in range(nsteps):
+            out, rec = orc.step(P, st, 1, record=True)
+            out["ux"] = st["ux"] + 0.5 * dt * rec["ax"]
+            out["uy"] = st["uy"] + 0.5 * dt * rec["ay"]
+            st = out
+    return lam, -math.log(amp(out["ux"]) / a0) / (nsteps * dt), nu * (2 * np.pi) ** 2
+
+
+def test_shear_wave_decays_at_the_viscous_rate(orc):
+    lam, rate, exact = _shear_wave(orc, 32, 500)
+    # the time integration decays the mode at the operator's rate (O(lam dt) = 0.4 % apart) ...
+    assert rate == pytest.approx(lam, rel=0.01)
+    # ... which is nu k^2 up to the square lattice's anisotropic fourth moments (a fixed ~6 % at
+    # h = 1.3 dx; the vector form is exact for quadratics only on the triangular lattice)
+    assert lam == pytest.approx(exact, rel=0.08)
+
+
+def test_literal_corrector_fails_the_shear_wave_decay(orc):
+    # the printed corrector starts from u^n and takes only half of the step's acceleration: the
+    # wave decays at about half the rate, so the decay pin above tells the two readings apart
+    lam, rate, _ = _shear_wave(orc, 32, 500, literal=True)
+    assert rate == pytest.approx(0.5 * lam, rel=0.01)
+    assert abs(rate / lam - 1.0) > 0.4
+
+
+def test_uniform_translation_advances_positions_and_sets_c0(orc):
+    # uniform u0 with a given a^0 on a jittered lattice, zeta = 0: every pair difference vanishes,
+    # so the midpoint acceleration, k and the APD are zero; u^{1/2} = u0 + dt/2 a0 = u^1 and
+    # r^1 = r^0 + dt u^{1/2}; c0 = 10 |u^{1/2}| (not 10 |u^0|)
+    ic = si.jittered_lattice(24, seed=4)
+    h = 1.3 * ic["dx"]
+    dt = 1e-3
+    u0, a0 = np.array([0.31, -0.17]), np.array([40.0, 25.0])
+    st = {k: ic[k] for k in ("x", "y", "q11", "q12", "rho")}
+    n = ic["n"]
+    st["ux"], st["uy"] = np.full(n, u0[0]), np.full(n, u0[1])
+    st["ax"], st["ay"] = np.full(n, a0[0]), np.full(n, a0[1])
+    P = orc.make_params(h=h, dt=dt, zeta=0.0, c0_min=0.0)
+    out, rec = orc.step(P, st, 1, record=True)
+    uh = u0 + 0.5 * dt * a0
+    assert rec["c0"] == pytest.approx(10.0 * math.hypot(*uh), rel=1e-15)
+    assert np.abs(rec["ax"]).max() <= 1e-9 and np.abs(rec["apdx"]).max() == 0.0
+    for k, c in (("x", 0), ("y", 1)):
+        moved = (out[k] - ic[k] - dt * uh[c] + 0.5) % 1.0 - 0.5
+        assert np.abs(moved).max() <= 1e-14
+    assert np.abs(out["ux"] - uh[0]).max() <= 1e-12 and np.abs(out["uy"] - uh[1]).max() <= 1e-12
+    # then many steps: positions advance by n dt u exactly (to rounding), c0 stays 10 |u|
+    out2, rec2 = orc.step(P, out, 40, record=True)
+    assert rec2["c0"] == pytest.approx(10.0 * math.hypot(*uh), rel=1e-12)
+    moved = (out2["x"] - ic["x"] - 41 * dt * uh[0] + 0.5) % 1.0 - 0.5
+    assert np.abs(moved).max() <= 1e-13
+
+
+def test_density_update_takes_a_whole_step_of_continuity(orc):
+    # compressive wave u_x = U sin(2 pi x) from rho = rho0: rho^1 = rho_hat + dt/2 k, with
+    # rho_hat the filtered rho0 + dt/2 k, so rho^1 - rho0 = dt k (1 + f)/2 where f ~ 1 - O((kh)^2)
+    # is the filter's attenuation of the mode and k = -rho0 U 2 pi cos(2 pi x) up to the SPH
+    # gradient's O((kh)^2).  Dropping the corrector's half gives about half of that.
+    ic = si.jittered_lattice(32, seed=0, jitter=0.0)
+    h = 1.3 * ic["dx"]
+    U, dt = 1e-3, 1e-4
+    st = {k: ic[k] for k in ("x", "y", "uy", "q11", "q12", "rho")}
+    st["ux"] = U * np.sin(2 * np.pi * ic["x"])
+    P = orc.make_params(h=h, dt=dt, zeta=0.0, apd=0, c0_min=0.0)
+    out, _ = orc.step(P, st, 1)
+    mode = np.cos(2 * np.pi * ic["x"])
+    amp = 2.0 * np.dot(out["rho"] - 1.0, mode) / ic["n"]
+    ratio = amp / (-dt * U * 2 * np.pi)
+    assert 0.95 < ratio < 1.005, ratio
+
+
+def test_position_update_is_the_trapezoid_of_the_half_step_velocities(orc):
+    # r^{1} = r^0 + dt/2 u^{1/2} + dt/2 u^{1}: with a viscous shear wave (a != 0, APD off) the
+    # position increment is the mean of the predicted and the corrected velocity, which differ by
+    # dt/2 a^{1/2}; a position update from u^{1/2} alone is off by dt^2 a / 4 (~2e-12 here)
+    ic = si.jittered_lattice(32, seed=0, jitter=0.0)
+    h = 1.3 * ic["dx"]
+    dt = 2e-3
+    st = {k: ic[k] for k in ("x", "y", "uy", "q11", "q12", "rho")}
+    st["ux"] = 1e-3 * np.sin(2 * np.pi * ic["y"])
+    st["ax"] = -2e-3 * np.sin(2 * np.pi * ic["y"])
+    P = orc.make_params(h=h, dt=dt, eta=0.05, zeta=0.0, A=0.0, C=0.0, K=0.0, apd=0)
+    out, rec = orc.step(P, st, 1, record=True)
+    uh = st["ux"] + 0.5 * dt * st["ax"]
+    assert np.abs(out["ux"] - (uh + 0.5 * dt * rec["ax"])).max() <= 1e-18
+    assert np.abs(rec["ax"]).max() > 1e-3
+    moved = (out["x"] - ic["x"] + 0.5) % 1.0 - 0.5
+    assert np.abs(moved - 0.5 * dt * (uh + out["ux"])).max() <= 1e-15   # FP64 ulps of positions

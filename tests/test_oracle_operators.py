@@ -223,3 +223,91 @@ def test_correction_tensor_isotropic_on_lattices(orc, square, hexa):
         b11, b12, b22 = B
         assert np.abs(b11[m] - b22[m]).max() < 1e-12 * np.abs(b11[m]).max()
         assert np.abs(b12[m]).max() < 1e-12 * np.abs(b11[m]).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# APD magnitude (Eq. 29): delta r_i = dt u_v r0^2 sum_j d_ij / |d_ij|^3 with
+# u_v = |sum_j (u_i - u_j) W_ij| / sum_j W_ij (self term in the denominator) and r0 the mean
+# neighbour distance.  Pinned by closed forms of two- and three-particle configurations and by the
+# scaling laws the formula fixes.
+# ---------------------------------------------------------------------------------------------
+
+def _apd_of(orc, pts, u, h, dt, L=1.0):
+    pts = np.asarray(pts, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    nb = orc.Nbrs(pts[:, 0], pts[:, 1], L, h)
+    return np.stack(orc.apd(nb, u[:, 0], u[:, 1], dt), axis=1)
+
+
+@pytest.mark.parametrize("b", [0.3, 1.2, 2.1, 2.9])
+def test_apd_two_particles_closed_form(orc, b):
+    # particle 1 at distance r = b h from particle 0, along a direction e; only particle 1 moves.
+    # For particle 0: u_v = |u_1| W / (W(0) + W), r0 = r, sum d/r^3 = -e / r^2, so
+    # delta r_0 = -dt |u_1| W / (W(0) + W) e; particle 1 gets the opposite displacement.
+    h, dt = 0.04, 3e-3
+    W0, Wr = orc.W([0.0, b], h)
+    for e in ((1.0, 0.0), (0.6, -0.8)):
+        e = np.array(e)
+        p0 = np.array([0.31, 0.57])
+        pts = [p0, p0 + b * h * e]
+        u = [[0.0, 0.0], [0.7, -2.4]]          # |u_1| = 2.5
+        got = _apd_of(orc, pts, u, h, dt)
+        mag = dt * 2.5 * Wr / (W0 + Wr)
+        assert np.abs(got[0] + mag * e).max() <= 1e-14 * mag
+        assert np.abs(got[1] - mag * e).max() <= 1e-14 * mag
+
+
+def test_apd_two_particles_across_the_periodic_face(orc):
+    # the pair vector is the minimum image: particle 1 sits just across x = 0 from particle 0
+    h, dt, b = 0.04, 3e-3, 1.7
+    W0, Wr = orc.W([0.0, b], h)
+    pts = [[0.01, 0.5], [1.0 + 0.01 - b * h, 0.5]]    # x_0 - x_1 = +b h by minimum image
+    got = _apd_of(orc, pts, [[0.0, 0.0], [0.0, 1.5]], h, dt)
+    mag = dt * 1.5 * Wr / (W0 + Wr)
+    assert got[0, 0] == pytest.approx(mag, rel=1e-12) and abs(got[0, 1]) <= 1e-14 * mag
+    assert got[1, 0] == pytest.approx(-mag, rel=1e-12)
+
+
+def test_apd_three_particles_closed_form(orc):
+    # particle 0 with neighbours 1 (at +r1 along x) and 2 (at +r2 along y), r1^2 + r2^2 > (3h)^2 so
+    # 1 and 2 do not see each other; only particle 1 moves, with speed U along x.
+    #   particle 0: u_v = U W(r1) / (W(0) + W(r1) + W(r2)), r0 = (r1 + r2)/2,
+    #               delta r_0 = dt u_v r0^2 (-1/r1^2, -1/r2^2)
+    #   particle 1: delta r_1 = dt U W(r1) / (W(0) + W(r1)) (1, 0);  particle 2: 0
+    h, dt, U = 0.05, 2e-3, 0.9
+    b1, b2 = 2.5, 2.0
+    r1, r2 = b1 * h, b2 * h
+    W0, W1, W2 = orc.W([0.0, b1, b2], h)
+    pts = [[0.5, 0.5], [0.5 + r1, 0.5], [0.5, 0.5 + r2]]
+    got = _apd_of(orc, pts, [[0.0, 0.0], [U, 0.0], [0.0, 0.0]], h, dt)
+    uv = U * W1 / (W0 + W1 + W2)
+    r0 = 0.5 * (r1 + r2)
+    want0 = dt * uv * r0 * r0 * np.array([-1.0 / r1**2, -1.0 / r2**2])
+    want1 = dt * U * W1 / (W0 + W1) * np.array([1.0, 0.0])
+    assert np.abs(got[0] - want0).max() <= 1e-14 * np.abs(want0).max()
+    assert np.abs(got[1] - want1).max() <= 1e-14 * np.abs(want1).max()
+    assert np.abs(got[2]).max() == 0.0
+
+
+def test_apd_scaling_laws(orc):
+    # delta r is linear in dt and in the amplitude of the velocity differences (even in its sign),
+    # and unchanged when positions, h and L scale by s with u fixed (r0^2 ~ s^2, sum d/r^3 ~ s^-2,
+    # u_v ~ s^0 since W scales out of the ratio).  A dropped square on r0, a d/r^2 for d/r^3, a u_v
+    # without its division by sum W, or a missing dt breaks one of these.
+    ic = si.jittered_lattice(24, seed=9, jitter=0.3)
+    h = 1.3 * ic["dx"]
+    r = si.uniform53(31, 2 * ic["n"]).reshape(2, ic["n"]) - 0.5
+    nb = orc.Nbrs(ic["x"], ic["y"], 1.0, h)
+    base = np.stack(orc.apd(nb, r[0], r[1], 1e-3), axis=1)
+    scale = np.abs(base).max()
+    assert scale > 0.0
+    twice_dt = np.stack(orc.apd(nb, r[0], r[1], 2e-3), axis=1)
+    assert np.abs(twice_dt - 2.0 * base).max() <= 1e-13 * scale
+    for a in (3.0, -2.0):
+        amp = np.stack(orc.apd(nb, a * r[0] + 0.4, a * r[1] - 0.1, 1e-3), axis=1)   # offsets cancel
+        assert np.abs(amp - abs(a) * base).max() <= 1e-12 * abs(a) * scale
+    s = 2.5
+    nbs = orc.Nbrs(s * ic["x"], s * ic["y"], s, s * h)
+    assert np.array_equal(nbs.rowptr, nb.rowptr) and np.array_equal(nbs.cols, nb.cols)
+    scaled = np.stack(orc.apd(nbs, r[0], r[1], 1e-3), axis=1)
+    assert np.abs(scaled - base).max() <= 1e-12 * scale
