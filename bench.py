@@ -63,9 +63,9 @@ RESORT_BRANCH = ("cell_keys", "cell_scan", "cell_scatter", "cell_order", "pass_a
 
 
 def launches_in_steps(steps: int, resorts: int) -> int:
-    """Kernels the step graph launches: the predictor, the branch condition, then either the five
-    re-sort kernels or the candidate filter, then passes B, C and D."""
-    return 6 * steps + 4 * resorts
+    """Kernels the step graph launches: the commit of the previous step, the predictor, the branch
+    condition, then either the five re-sort kernels or the candidate filter, then passes B, C and D."""
+    return 7 * steps + 4 * resorts
 
 
 def _rank_info():

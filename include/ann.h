@@ -226,9 +226,14 @@ int ann_set_state(ann_ctx *ctx, int64_t n, const double *x, const double *y, con
 
 /* Advance nsteps >= 0 steps (one CUDA-graph launch per step) and synchronise.  Errors:
  * STATE (no particles), CELL_OVERFLOW, NBR_OVERFLOW, NONFINITE, SINGULAR_ALPHA, CFL_VIOLATION (device error
- * bits; once one is raised the remaining kernels of the call return without work, so the state is
- * that of the failing step, partly updated; ann_get_diagnostics reports the bits; ann_set_particles
- * or ann_load_state clears them), CUDA. */
+ * bits; once one is raised the remaining kernels of the call return without work), CUDA.
+ * A failed step leaves the state at the last completed step: the context keeps two copies of the
+ * state, a step reads the committed one and writes the other, and only a step that ends with no
+ * error raised is committed.  After a failure ann_get_field, ann_get_state, ann_get_unwrapped and
+ * ann_save_state see the state after the last completed step (ann_diag.step and .t count only the
+ * completed steps; the periodic image counts the failed step changed are restored), and the next
+ * step re-sorts.  The error bits stay set (ann_get_diagnostics reports them) until
+ * ann_set_particles, ann_set_state or ann_load_state clears them. */
 int ann_step(ann_ctx *ctx, int64_t nsteps);
 
 /* Advance nsteps steps launching the kernels one by one with a CUDA event before and after each,

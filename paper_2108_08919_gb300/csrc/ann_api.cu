@@ -32,6 +32,8 @@ struct ann_ctx {
     double *diag_part = nullptr;  // diag_blocks(n) x NDIAG
     double *diag_out = nullptr;   // NDIAG
     uint32_t *h_err = nullptr;    // pinned
+    uint32_t *h_ctl = nullptr;    // pinned: step control words and the error word read back, words to write
+    int cur = 0;                  // the state set the host view (b.sx, ...) points at: the committed one
     // Which arrays hold the present state in the cell order of the last re-sort (the order the
     // flow diagnostics need): S after a step or a load that kept the cell structure, the
     // evaluation copy M after a neighbour export; neither after ann_set_particles.
@@ -117,7 +119,9 @@ int64_t device_bytes(const ann_params &p)
                   + 11 * 4                    // intermediates
                   + 10 * 4                    // recording
                   + 16 + 8                    // elastic stress and its divergence
-                  + 8 + 1 + 4;                // image counts, colour, inverse order (diagnostics)
+                  + 8 + 1 + 4                 // image counts, colour, inverse order (diagnostics)
+                  + 2 * 8 + 7 * 4 + 4         // the second state set (a step writes it, rollback keeps the first)
+                  + 2;                        // crossing log (n/8 entries of 16 bytes)
     int64_t tmp = std::max<int64_t>(7 * 8, MAXN * 4) * n;
     return per * n + tmp + 2 * 4 * (ncell + 1) + 4096;
 }
@@ -301,6 +305,13 @@ cudaError_t alloc_all(ann_ctx *c)
     A_(rec_gu, 4 * n); A_(rec_lap, 2 * n); A_(rec_apd, 2 * n); A_(rec_qrate, 2 * n);
     A_(pel, n); A_(delx, n); A_(dely, n); A_(img, n);
     A_(err, 1); A_(maxu, 1); A_(band, 1);
+    // the state sets: st[0] is the storage the host view starts on, st[1] the step's other copy
+    b.st[0] = StateSet{b.sx, b.sy, b.sux, b.suy, b.sq11, b.sq12, b.sdr, b.sax, b.say, b.sid};
+    A_(st[1].x, n); A_(st[1].y, n); A_(st[1].ux, n); A_(st[1].uy, n); A_(st[1].q11, n); A_(st[1].q12, n);
+    A_(st[1].dr, n); A_(st[1].ax, n); A_(st[1].ay, n); A_(st[1].id, n);
+    A_(ctl, CTL_WORDS);
+    b.xlog_cap = (int)std::max<size_t>(1024, n / 8);
+    A_(xlog, (size_t)b.xlog_cap);
 #undef A_
     double *origin = nullptr;
     if ((e = dalloc(c, origin, (size_t)c->P.nc))) return e;
@@ -329,6 +340,7 @@ cudaError_t capture_step(ann_ctx *c, cudaStream_t s, cudaGraph_t g)
 {
     cudaGraphConditionalHandle h = 0;
     cudaError_t ec = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+    if (!ec) ec = launch_commit(c->b, s);
     if (!ec) ec = launch_kernel(0, c->P, c->b, s);
     if (!ec) ec = launch_set_condition(c->b, h, s);
     cudaGraph_t body[2] = {nullptr, nullptr};
@@ -422,7 +434,77 @@ cudaError_t clear_flags(ann_ctx *c)
     if (!e) e = cudaMemsetAsync(c->b.rebuild, 1, sizeof(uint32_t), c->stream);
     if (!e) e = cudaMemsetAsync(c->b.maxu, 0, sizeof(uint32_t), c->stream);
     if (!e) e = cudaMemsetAsync(c->b.cell_count, 0, sizeof(uint32_t) * (c->P.ncell + 1), c->stream);
+    // no step pending, counters cleared; the committed set (ctl[CTL_CUR]) stays the host view's
+    if (!e) e = cudaMemsetAsync(c->b.ctl + CTL_PENDING, 0, sizeof(uint32_t) * (CTL_WORDS - CTL_PENDING), c->stream);
     return e;
+}
+
+// Point the host view of the state (b.sx, ...) at state set k.
+void set_view(ann_ctx *c, int k)
+{
+    c->cur = k;
+    const StateSet &t = c->b.st[k];
+    Bufs &b = c->b;
+    b.sx = t.x;
+    b.sy = t.y;
+    b.sux = t.ux;
+    b.suy = t.uy;
+    b.sq11 = t.q11;
+    b.sq12 = t.q12;
+    b.sdr = t.dr;
+    b.sax = t.ax;
+    b.say = t.ay;
+    b.sid = t.id;
+}
+
+// After a batch of `launched` steps (graph replays or the profiled loop): with no error raised the
+// last step is committed here (the next step's k_commit would do it); after an error the failed
+// step is rolled back -- its output set is dropped, so the committed set is the state of the last
+// completed step, the image counts it changed are restored from its crossing log, and the next
+// step re-sorts, as the failed step may have re-sorted the cell structure.  Adds the completed
+// steps to the step count and time; returns the status of the device error word.
+int settle_steps(ann_ctx *c, int64_t launched)
+{
+    uint32_t *h = c->h_ctl;   // [0, CTL_WORDS) read back, [CTL_WORDS] the error word, then the words to write
+    cudaError_t e = cudaMemcpyAsync(h, c->b.ctl, sizeof(uint32_t) * CTL_WORDS, cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaMemcpyAsync(h + CTL_WORDS, c->b.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_fail(c, e, "reading the step status");
+    const bool failed = h[CTL_WORDS] != 0u;
+    uint32_t cur = h[CTL_CUR] & 1u;
+    int64_t done = launched;
+    bool log_lost = false;
+    if (!failed) {
+        if (h[CTL_PENDING]) cur ^= 1u;
+    } else {
+        done = std::min<int64_t>(launched, h[CTL_COMMITS]);
+        const uint32_t nlog = h[CTL_XLOG];
+        log_lost = nlog > (uint32_t)c->b.xlog_cap;
+        e = enqueue_undo_crossings(c->b, (int)std::min<uint32_t>(nlog, (uint32_t)c->b.xlog_cap), c->stream);
+        if (!e) e = cudaMemsetAsync(c->b.rebuild, 1, sizeof(uint32_t), c->stream);
+    }
+    uint32_t *w = h + CTL_WORDS + 1;
+    w[CTL_CUR] = cur;
+    w[CTL_PENDING] = 0u;
+    w[CTL_COMMITS] = 0u;
+    w[CTL_XLOG] = 0u;
+    if (!e) e = cudaMemcpyAsync(c->b.ctl, w, sizeof(uint32_t) * CTL_WORDS, cudaMemcpyHostToDevice, c->stream);
+    if (e) return cuda_fail(c, e, "settling the steps");
+    set_view(c, (int)cur);
+    c->steps += done;
+    c->t += done * c->P.dt_d;
+    if (done > 0 || failed) {
+        c->s_sorted = !failed;   // after a rollback the cell structure may not follow the state
+        c->m_current = false;
+        c->grid_step = -1;
+        c->rec_valid = !failed && c->P.record != 0;
+    }
+    int st = device_status(c);   // synchronises: the words above are written when this returns
+    if (failed) {
+        c->last_err += "; the state is that of the last completed step (" + std::to_string(c->steps) + ")";
+        if (log_lost) c->last_err += "; more crossings than the log holds: image counts not restored";
+    }
+    return st;
 }
 
 struct Field {
@@ -632,6 +714,7 @@ int ann_create_with_allocator(const ann_params *p, const ann_allocator *a, ann_c
     if (!e) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
     if (!e) { c->stream = c->own; e = alloc_all(c); }
     if (!e) e = cudaMallocHost(&c->h_err, sizeof(uint32_t));
+    if (!e) e = cudaMallocHost(&c->h_ctl, sizeof(uint32_t) * (2 * CTL_WORDS + 1));
     if (!e) e = capture(c);
     if (!e) e = cudaStreamSynchronize(c->own);
     if (e) {
@@ -654,6 +737,7 @@ void ann_destroy(ann_ctx *c)
                                  &c->d_shmodes, &c->d_out, &c->d_map, &c->d_cnt, &c->d_ids})
         dev_free(c, sc->p, sc->bytes);
     if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->h_ctl) cudaFreeHost(c->h_ctl);
     if (c->own) cudaStreamDestroy(c->own);
     if (c->aux) cudaStreamDestroy(c->aux);
     delete c;
@@ -798,16 +882,7 @@ int ann_step(ann_ctx *c, int64_t nsteps)
         cudaError_t e = cudaGraphLaunch(c->exec, c->stream);
         if (e) return cuda_fail(c, e, "ann_step graph launch");
     }
-    int s = device_status(c);
-    c->steps += nsteps;
-    c->t += nsteps * c->P.dt_d;
-    if (nsteps > 0) {
-        c->s_sorted = true;
-        c->m_current = false;
-        c->grid_step = -1;
-        c->rec_valid = c->P.record != 0;
-    }
-    return s;
+    return settle_steps(c, nsteps);
 }
 
 int ann_step_profile(ann_ctx *c, int64_t nsteps, double *kernel_ms)
@@ -828,7 +903,8 @@ int ann_step_profile(ann_ctx *c, int64_t nsteps, double *kernel_ms)
     for (; made < ev.size() && !e; made++) e = cudaEventCreate(&ev[made]);
     for (int64_t s = 0; s < nsteps && !e; s++) {
         cudaEvent_t *E = &ev[(size_t)s * per];
-        e = cudaEventRecord(E[0], c->stream);
+        e = launch_commit(c->b, c->stream);   // as the graph's first node (not timed)
+        if (!e) e = cudaEventRecord(E[0], c->stream);
         if (!e) e = launch_kernel(0, c->P, c->b, c->stream);
         if (!e) e = cudaEventRecord(E[1], c->stream);
         if (!e) e = cudaMemcpyAsync(c->h_err, c->b.rebuild, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
@@ -860,16 +936,7 @@ int ann_step_profile(ann_ctx *c, int64_t nsteps, double *kernel_ms)
     for (size_t k = 0; k < made; k++)
         if (ev[k]) cudaEventDestroy(ev[k]);
     if (e) return cuda_fail(c, e, "ann_step_profile");
-    int st = device_status(c);
-    c->steps += nsteps;
-    c->t += nsteps * c->P.dt_d;
-    if (nsteps > 0) {
-        c->s_sorted = true;
-        c->m_current = false;
-        c->grid_step = -1;
-        c->rec_valid = c->P.record != 0;
-    }
-    return st;
+    return settle_steps(c, nsteps);
 }
 
 int ann_kernel_count(void) { return NKERNELS; }
@@ -1558,6 +1625,22 @@ int ann_ensemble_member(ann_ensemble *E, int32_t k, ann_ctx **ctx)
     return ANN_OK;
 }
 
+// Settle every member after a batch of ensemble steps (settle_steps); the first failing member's
+// status is returned and named.
+static int ensemble_settle(ann_ensemble *E, int64_t launched)
+{
+    int first = ANN_OK;
+    for (size_t k = 0; k < E->m.size(); k++) {
+        ann_ctx *c = E->m[k];
+        int st = settle_steps(c, launched);
+        if (st && first == ANN_OK) {
+            first = st;
+            E->last_err = "member " + std::to_string(k) + ": " + c->last_err;
+        }
+    }
+    return first;
+}
+
 int ann_ensemble_set_groups(ann_ensemble *E, int32_t groups)
 {
     if (!E || groups < 1 || groups > (int32_t)E->m.size()) return ANN_ERR_INVALID_ARG;
@@ -1579,24 +1662,7 @@ int ann_ensemble_step(ann_ensemble *E, int64_t nsteps)
     }
     cudaError_t e = cudaStreamSynchronize(E->s0);
     if (e) return efail(E, ANN_ERR_CUDA, std::string("ensemble step: ") + cudaGetErrorString(e));
-    int first = ANN_OK;
-    for (size_t k = 0; k < E->m.size(); k++) {
-        ann_ctx *c = E->m[k];
-        int st = device_status(c);
-        c->steps += nsteps;
-        c->t += nsteps * c->P.dt_d;
-        if (nsteps > 0) {
-            c->s_sorted = true;
-            c->m_current = false;
-            c->grid_step = -1;
-            c->rec_valid = c->P.record != 0;
-        }
-        if (st && first == ANN_OK) {
-            first = st;
-            E->last_err = "member " + std::to_string(k) + ": " + c->last_err;
-        }
-    }
-    return first;
+    return ensemble_settle(E, nsteps);
 }
 
 int ann_ensemble_autotune(ann_ensemble *E, int32_t trial_steps, int32_t *groups_out, double *ms_per_step)
@@ -1624,11 +1690,7 @@ int ann_ensemble_autotune(ann_ensemble *E, int32_t trial_steps, int32_t *groups_
         if (!e) e = cudaEventSynchronize(b);
         float ms = 0.f;
         if (!e) e = cudaEventElapsedTime(&ms, a, b);
-        if (!e) st = ann_ensemble_step(E, 0);   // status of the trial steps
-        for (ann_ctx *c : E->m) {
-            c->steps += trial_steps;
-            c->t += trial_steps * c->P.dt_d;
-        }
+        if (!e) st = ensemble_settle(E, trial_steps);   // commit (or roll back) the trial steps
         if (!e && (best_ms < 0.f || ms < best_ms)) {
             best_ms = ms;
             best = g;

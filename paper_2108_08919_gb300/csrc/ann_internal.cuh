@@ -68,8 +68,30 @@ struct DevParams {
     float dt_static;       // min(0.125 h^2 / nu, 0.125 h^2 / (Gamma K)) (infinity where a rate is 0)
 };
 
-// Device buffers.  S: state at the end of a step, in the particle order of that step's evaluation.
-// M: the current step's cell-sorted copy.  Per-particle intermediates are in M order.
+// One copy of the state of §3.1 at the end of a step, in the particle order of that step's
+// evaluation (slot g holds particle id[g]).
+struct StateSet {
+    double *x, *y;
+    float *ux, *uy, *q11, *q12, *dr, *ax, *ay;
+    int *id;
+};
+
+// Step control words (ctl[]).  The state lives in two StateSets: st[ctl[CTL_CUR]] holds the last
+// committed step, and a step writes the other one.  A step commits when the next step begins with
+// no error raised (k_commit) or, for the last step of a call, when the host finds no error after it;
+// a failed step is never committed, so its input -- the last completed step -- stays intact.
+enum : int {
+    CTL_CUR = 0,       // index of the committed state set
+    CTL_PENDING = 1,   // 1: a step has written st[CUR ^ 1] and is not yet committed
+    CTL_COMMITS = 2,   // steps committed on the device (counts up; the host takes differences)
+    CTL_XLOG = 3,      // entries in the crossing log of the step in flight
+    CTL_WORDS = 4,
+};
+
+// Device buffers.  S: the host's view of the committed state (the StateSet st[CUR]: the kernels
+// outside the step read and write the state through it).  The step kernels take their input and
+// output sets from st[] and ctl[] instead.  M: the current step's cell-sorted copy.  Per-particle
+// intermediates are in M order.
 struct Bufs {
     double *sx, *sy;
     float *sux, *suy, *sq11, *sq12, *sdr, *sax, *say;
@@ -96,7 +118,32 @@ struct Bufs {
     int2 *img;          // by particle ID: net periodic shifts (x, y) since ann_set_particles
     uint32_t *err, *maxu;
     unsigned long long *band;
+    StateSet st[2];     // the two state sets (st[0] is the host view's storage at creation)
+    uint32_t *ctl;      // CTL_WORDS step control words
+    int4 *xlog;         // crossings of the step in flight: (particle ID, dx, dy, -), undone if it fails
+    int xlog_cap;       // entries of xlog
 };
+
+// Input and output state sets of a step kernel (the step reads the committed set and writes the
+// other).  Only the step kernels use these; ctl[CUR] does not change while a step runs.
+__device__ __forceinline__ StateSet pick_set(const Bufs &b, bool one)
+{
+    StateSet s;
+    s.x = one ? b.st[1].x : b.st[0].x;
+    s.y = one ? b.st[1].y : b.st[0].y;
+    s.ux = one ? b.st[1].ux : b.st[0].ux;
+    s.uy = one ? b.st[1].uy : b.st[0].uy;
+    s.q11 = one ? b.st[1].q11 : b.st[0].q11;
+    s.q12 = one ? b.st[1].q12 : b.st[0].q12;
+    s.dr = one ? b.st[1].dr : b.st[0].dr;
+    s.ax = one ? b.st[1].ax : b.st[0].ax;
+    s.ay = one ? b.st[1].ay : b.st[0].ay;
+    s.id = one ? b.st[1].id : b.st[0].id;
+    return s;
+}
+__device__ __forceinline__ bool cur_set(const Bufs &b) { return (*(volatile uint32_t *)(b.ctl + CTL_CUR)) != 0u; }
+__device__ __forceinline__ StateSet state_in(const Bufs &b) { return pick_set(b, cur_set(b)); }
+__device__ __forceinline__ StateSet state_out(const Bufs &b) { return pick_set(b, !cur_set(b)); }
 
 // Launch-configuration helpers (defined with the kernels).
 const char *kernel_name(int k);
@@ -106,6 +153,10 @@ cudaError_t prepare_kernels();
 cudaError_t launch_kernel(int k, const DevParams &P, const Bufs &b, cudaStream_t s);
 // Copy the re-sort flag into a graph conditional handle (one thread).
 cudaError_t launch_set_condition(const Bufs &b, cudaGraphConditionalHandle h, cudaStream_t s);
+// The first node of every step: commits the previous step if no error was raised since (one thread).
+cudaError_t launch_commit(const Bufs &b, cudaStream_t s);
+// Undo the crossings logged by a failed step in the image counts (img), n_log entries.
+cudaError_t enqueue_undo_crossings(const Bufs &b, int n_log, cudaStream_t s);
 // Cell sort and the re-sort pass A only (neighbour lists and volumes) at the positions in S advanced
 // by P.half_dt (callers pass 0 to keep them).  Requires *b.rebuild != 0.
 cudaError_t enqueue_search(const DevParams &P, const Bufs &b, cudaStream_t s);

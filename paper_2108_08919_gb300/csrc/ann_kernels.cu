@@ -39,6 +39,17 @@ __device__ __noinline__ bool support64(const DevParams &P, const Bufs &b, int gi
 
 __device__ __forceinline__ bool resorting(const Bufs &b) { return *(volatile uint32_t *)b.rebuild != 0u; }
 
+// A particle crossed the box (Eq. 30): update its periodic image count (one thread per particle)
+// and log the crossing, so that the host can undo it if this step fails.  Crossings are rare.
+__device__ __forceinline__ void add_crossing(const Bufs &b, int id, int kx, int ky)
+{
+    int2 &im = b.img[id];
+    im.x += kx;
+    im.y += ky;
+    const unsigned k = atomicAdd(b.ctl + CTL_XLOG, 1u);
+    if (k < (unsigned)b.xlog_cap) b.xlog[k] = make_int4(id, kx, ky, 0);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Tile bookkeeping shared by the pair passes
 // ---------------------------------------------------------------------------------------------
@@ -164,20 +175,18 @@ __global__ void __launch_bounds__(256) k_predict(DevParams P, Bufs b)
     bool rs = resorting(b);
     float sp = 0.f;
     if (i < P.n) {
-        float ux = b.sux[i] + P.half_dt * b.sax[i];
-        float uy = b.suy[i] + P.half_dt * b.say[i];
+        // the committed state in, the predicted positions and velocities into the other set
+        const StateSet in = state_in(b), out = state_out(b);
+        float ux = in.ux[i] + P.half_dt * in.ax[i];
+        float uy = in.uy[i] + P.half_dt * in.ay[i];
         // FP64 work is kept to what the positions need: GB300 issues FP64 at 1/64 of FP32.
-        double x = b.sx[i] + (double)(P.half_dt * ux);
-        double y = b.sy[i] + (double)(P.half_dt * uy);
+        double x = in.x[i] + (double)(P.half_dt * ux);
+        double y = in.y[i] + (double)(P.half_dt * uy);
         if (!(in_box(x, P.bitsL) && in_box(y, P.bitsL))) {   // rare: crossed a face, or not finite
             int kx = wrap_count(x, P.L), ky = wrap_count(y, P.L);
             x = x + 0.0;
             y = y + 0.0;
-            if (kx | ky) {   // periodic image count of this particle (pathlines)
-                int2 &im = b.img[b.sid[i]];
-                im.x += kx;
-                im.y += ky;
-            }
+            if (kx | ky) add_crossing(b, in.id[i], kx, ky);   // periodic image count (pathlines)
             if (!(in_box(x, P.bitsL) && in_box(y, P.bitsL) && isfinite(ux) && isfinite(uy))) {
                 atomicOr(b.err, EB_NONFINITE);
                 x = 0.0;
@@ -187,10 +196,10 @@ __global__ void __launch_bounds__(256) k_predict(DevParams P, Bufs b)
             }
         }
         sp = sqrtf(ux * ux + uy * uy);
-        b.sux[i] = ux;
-        b.suy[i] = uy;
-        b.sx[i] = x;
-        b.sy[i] = y;
+        out.ux[i] = ux;
+        out.uy[i] = uy;
+        out.x[i] = x;
+        out.y[i] = y;
         if (!rs) {
             // The order is that of the last re-sort: write the evaluation copy directly, split
             // against the cell the particle was assigned to then.  A particle that has moved half
@@ -216,10 +225,10 @@ __global__ void __launch_bounds__(256) k_predict(DevParams P, Bufs b)
             b.xi[i] = xi;
             b.mux[i] = ux;
             b.muy[i] = uy;
-            b.mq11[i] = b.sq11[i];
-            b.mq12[i] = b.sq12[i];
-            b.mdr[i] = b.sdr[i];
-            b.mid[i] = b.sid[i];
+            b.mq11[i] = in.q11[i];
+            b.mq12[i] = in.q12[i];
+            b.mdr[i] = in.dr[i];
+            b.mid[i] = in.id[i];
         }
     }
     for (int o = 16; o > 0; o >>= 1) sp = fmaxf(sp, __shfl_xor_sync(FULL, sp, o));
@@ -244,7 +253,8 @@ __global__ void __launch_bounds__(256) k_keys(DevParams P, Bufs b)
     int lane = threadIdx.x & 31;
     uint32_t key = 0xffffffffu;
     if (i < P.n) {
-        double x = b.sx[i], y = b.sy[i];
+        const StateSet out = state_out(b);   // the predicted positions
+        double x = out.x[i], y = out.y[i];
         int cx = min((int)(x * P.inv_cell), P.nc - 1);
         int cy = min((int)(y * P.inv_cell), P.nc - 1);
         key = (uint32_t)(cy * P.nc + cx);
@@ -380,18 +390,20 @@ __global__ void __launch_bounds__(256) k_cell_order(DevParams P, Bufs b)
     if (lane < cnt) srt[w][r0] = v0;
     if (lane + 32 < cnt) srt[w][r1] = v1;
     __syncwarp();
+    // predicted positions and velocities from the output set, the rest of the state from the input
+    const StateSet in = state_in(b), out = state_out(b);
     for (int s = lane; s < cnt; s += 32) {
         uint32_t old = srt[w][s], g = start + (uint32_t)s;
-        b.mx[g] = b.sx[old];
-        b.my[g] = b.sy[old];
+        b.mx[g] = out.x[old];
+        b.my[g] = out.y[old];
         b.xi[g] = b.sxi[old];
         b.mkey[g] = (uint32_t)c;
-        b.mux[g] = b.sux[old];
-        b.muy[g] = b.suy[old];
-        b.mq11[g] = b.sq11[old];
-        b.mq12[g] = b.sq12[old];
-        b.mdr[g] = b.sdr[old];
-        b.mid[g] = b.sid[old];
+        b.mux[g] = out.ux[old];
+        b.muy[g] = out.uy[old];
+        b.mq11[g] = in.q11[old];
+        b.mq12[g] = in.q12[old];
+        b.mdr[g] = in.dr[old];
+        b.mid[g] = in.id[old];
     }
 }
 
@@ -761,8 +773,11 @@ __global__ void BOUNDS_B k_pass_b(DevParams P, Bufs b)
                    P.Gamma * (hb * q1 + P.K * lap1);
         float m2 = lam * divu * q2 + 2.f * cl * E12 + 2.f * om * q1 - 2.f * lam * QE * q2 +
                    P.Gamma * (hb * q2 + P.K * lap2);
-        b.sq11[gi] = q1 + P.dt * m1;
-        b.sq12[gi] = q2 + P.dt * m2;
+        {
+            const StateSet out = state_out(b);   // Q^{n+1} into the step's output set
+            out.q11[gi] = q1 + P.dt * m1;
+            out.q12[gi] = q2 + P.dt * m2;
+        }
         if (P.elastic) {
             // Elastic stress of Eq. (12) without -p I: with H = H_tl + h0 I (h0 from the B term),
             // M = Q + c I and the 2D identity A B + B A = (A:B) I for symmetric traceless A, B:
@@ -822,10 +837,11 @@ __global__ void BOUNDS_C k_pass_c(DevParams P, Bufs b)
         if (threadIdx.x == 0) atomicOr(b.err, EB_HALO);
         return;
     }
+    const StateSet out = state_out(b);   // Q^{n+1} (pass B)
     for (int t = threadIdx.x; t < T.H; t += PT) {
         SlotInfo s = slot_info(P, b, ts, T, t);
         sp[t] = s.e;
-        sb[t] = QNEW ? make_float4(b.V[s.g], b.dh[s.g], b.sq11[s.g], b.sq12[s.g])
+        sb[t] = QNEW ? make_float4(b.V[s.g], b.dh[s.g], out.q11[s.g], out.q12[s.g])
                      : make_float4(b.V[s.g], b.dh[s.g], 0.f, 0.f);
         if (EL) se[t] = b.pel[s.g];
         sg[t] = s.g;
@@ -915,11 +931,15 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
     float2 *sc = reinterpret_cast<float2 *>(sb + HCAP); // cons: (q11/rho^2, q12/rho^2)
     float4 *se = reinterpret_cast<float4 *>(sc + (CONS ? HCAP : 0)); // cons + elastic: Pi/rho^2
     int *sg = reinterpret_cast<int *>(se + ((CONS && EL) ? HCAP : 0));
+    // the step's output set: Q^{n+1} (pass B) in, the new state out; k_commit of the next step (or
+    // the host) commits it if no error has been raised by then
+    if (blockIdx.x == 0 && threadIdx.x == 0) b.ctl[CTL_PENDING] = 1u;
     Tile T;
     if (!tile_begin(P, b, ts, T)) {
         if (threadIdx.x == 0) atomicOr(b.err, EB_HALO);
         return;
     }
+    const StateSet out = state_out(b);
     for (int t = threadIdx.x; t < T.H; t += PT) {
         SlotInfo s = slot_info(P, b, ts, T, t);
         float rho = P.rho0 * (1.f + b.dhat[s.g]);
@@ -927,8 +947,8 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
         float pr = b.p[s.g] * irho * irho;
         sp[t] = s.e;
         if (CONS) {
-            float q1 = P.qnew ? b.sq11[s.g] : b.mq11[s.g];
-            float q2 = P.qnew ? b.sq12[s.g] : b.mq12[s.g];
+            float q1 = P.qnew ? out.q11[s.g] : b.mq11[s.g];
+            float q2 = P.qnew ? out.q12[s.g] : b.mq12[s.g];
             sb[t] = make_float4(pr, irho, b.mux[s.g], b.muy[s.g]);
             sc[t] = make_float2(q1 * irho * irho, q2 * irho * irho);
             if (EL) {
@@ -1039,29 +1059,50 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
             int kx = wrap_count(xn, P.L), ky = wrap_count(yn, P.L);
             xn = xn + 0.0;
             yn = yn + 0.0;
-            if (kx | ky) {   // periodic image count of this particle (pathlines)
-                int2 &im = b.img[b.mid[gi]];
-                im.x += kx;
-                im.y += ky;
-            }
+            if (kx | ky) add_crossing(b, b.mid[gi], kx, ky);   // periodic image count (pathlines)
         }
         float dn = dhat + P.half_dt * kri;
         if (!(isfinite(unx) && isfinite(uny) && isfinite(dn) && in_box(xn, P.bitsL) &&
-              in_box(yn, P.bitsL) && isfinite(b.sq11[gi]) && isfinite(b.sq12[gi])))
+              in_box(yn, P.bitsL) && isfinite(out.q11[gi]) && isfinite(out.q12[gi])))
             atomicOr(b.err, EB_NONFINITE);
-        b.sx[gi] = xn;
-        b.sy[gi] = yn;
-        b.sux[gi] = unx;
-        b.suy[gi] = uny;
-        b.sdr[gi] = dn;
-        b.sax[gi] = ax;
-        b.say[gi] = ay;
-        b.sid[gi] = b.mid[gi];
+        out.x[gi] = xn;
+        out.y[gi] = yn;
+        out.ux[gi] = unx;
+        out.uy[gi] = uny;
+        out.dr[gi] = dn;
+        out.ax[gi] = ax;
+        out.ay[gi] = ay;
+        out.id[gi] = b.mid[gi];
         if (P.record) {
             b.rec_apd[2 * gi + 0] = apx;
             b.rec_apd[2 * gi + 1] = apy;
         }
     }
+}
+
+// First node of every step: the previous step is complete -- commit its output set -- unless an
+// error has been raised since it began (then nothing here changes: the host rolls back).  Also
+// starts this step's crossing log.  One thread.
+__global__ void k_commit(Bufs b)
+{
+    if (*(volatile uint32_t *)b.err != 0u) return;
+    volatile uint32_t *c = b.ctl;
+    if (c[CTL_PENDING]) {
+        c[CTL_CUR] ^= 1u;
+        c[CTL_PENDING] = 0u;
+        c[CTL_COMMITS] += 1u;
+    }
+    c[CTL_XLOG] = 0u;
+}
+
+// Takes back the image-count changes of a failed step's logged crossings.
+__global__ void k_undo_crossings(Bufs b, int n_log)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_log) return;
+    const int4 e = b.xlog[k];
+    atomicSub(&b.img[e.x].x, e.y);
+    atomicSub(&b.img[e.x].y, e.z);
 }
 
 // Copies the re-sort decision into the condition of the step graph's IF / ELSE node.
@@ -1410,6 +1451,19 @@ cudaError_t launch_kernel(int k, const DevParams &P, const Bufs &b, cudaStream_t
 cudaError_t launch_set_condition(const Bufs &b, cudaGraphConditionalHandle h, cudaStream_t s)
 {
     k_set_condition<<<1, 1, 0, s>>>(b, h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_commit(const Bufs &b, cudaStream_t s)
+{
+    k_commit<<<1, 1, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_undo_crossings(const Bufs &b, int n_log, cudaStream_t s)
+{
+    if (n_log <= 0) return cudaSuccess;
+    k_undo_crossings<<<blocks_for(n_log, 256), 256, 0, s>>>(b, n_log);
     return cudaGetLastError();
 }
 

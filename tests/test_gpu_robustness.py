@@ -521,3 +521,100 @@ def test_isolated_particle_is_a_singular_correction_tensor(B, orc):
         B.ann_step(ctx, 1)
     finally:
         B.ann_destroy(ctx)
+
+
+def _bits(state):
+    """The state's arrays as raw bytes, so that NaN compares equal to itself bit for bit."""
+    return {f: np.ascontiguousarray(v).view(np.uint8) for f, v in state.items()}
+
+
+def test_failed_step_leaves_the_last_completed_state(B):
+    """Section 3.1's boundary contract: a step that fails leaves the state of the last completed
+    step.  A strongly active flow (zeta = 50, eta = 0.01) in ANN_DT_CHECK mode accelerates until its
+    midpoint velocity breaks 0.25 h / (c0 + max|u|) in pass C of some step k, after pass B has
+    written Q^{n+1} and (for a re-sorting step) the cell structure has moved.  A reference context
+    steps one call at a time to find k; a second context runs all the steps in one call.  The
+    second one reports CFL_VIOLATION, and its state, step count, time and pathline image counts
+    equal the reference's after step k - 1 bit for bit.  Reloading a checkpoint then continues
+    both bit-identically."""
+    import os
+    import tempfile
+
+    nx = 64
+    ic = random_velocity_ic(nx, 31, u_scale=1e-3)
+    p = params(nx, zeta=50.0, eta=0.01, dt=1e-4)
+    gp = gpu_params(B, p, ic["n"])
+    gp.dt_mode = 2
+    ids = np.arange(0, ic["n"], 7, dtype=np.int64)
+    ref, run = B.ann_create(gp), B.ann_create(gp)
+    tmp = tempfile.mkdtemp()
+    try:
+        for c in (ref, run):
+            B.ann_set_particles(c, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"], ic["rho"])
+        good, k = None, None
+        for step in range(1, 81):
+            try:
+                B.ann_step(ref, 1)
+            except B.AnnError as e:
+                assert e.status == -13, e
+                k = step
+                break
+            good = (B.ann_get_state(ref, ic["n"]), B.ann_get_unwrapped(ref, ids))
+            if step == 1:
+                B.ann_save_state(ref, os.path.join(tmp, "s1.bin"))
+        assert k is not None and k >= 3, "the flow should break the CFL bound after a few steps"
+        with pytest.raises(B.AnnError) as e:
+            B.ann_step(run, k + 5)
+        assert e.value.status == -13
+        d = B.ann_get_diagnostics(run)
+        assert d["step"] == k - 1 and d["error_bits"] & 32
+        assert d["t"] == pytest.approx((k - 1) * p["dt"], rel=1e-12)
+        got = B.ann_get_state(run, ic["n"])
+        want = _bits(good[0])
+        for f, v in _bits(got).items():
+            assert np.array_equal(v, want[f]), f
+        assert np.array_equal(B.ann_get_unwrapped(run, ids), good[1])
+        # the reference, also rolled back, holds the same state
+        for f, v in _bits(B.ann_get_state(ref, ic["n"])).items():
+            assert np.array_equal(v, want[f]), f
+        # a checkpoint load clears the error; both contexts continue identically
+        for c in (ref, run):
+            B.ann_load_state(c, os.path.join(tmp, "s1.bin"))
+            B.ann_step(c, 1)
+        a, b = _bits(B.ann_get_state(ref, ic["n"])), _bits(B.ann_get_state(run, ic["n"]))
+        for f in a:
+            assert np.array_equal(a[f], b[f]), f
+    finally:
+        B.ann_destroy(ref)
+        B.ann_destroy(run)
+
+
+def test_singular_step_fails_without_a_trace(B, orc):
+    """The degenerate case of Eq. 22 (a particle with no neighbour, alpha = 0) fails the step in
+    pass B with SINGULAR_ALPHA after pass B has written Q^{n+1} into the step's output set; the
+    state read back afterwards is the loaded one, bit for bit, at step 0."""
+    nx = 64
+    ic = si.jittered_lattice(nx, seed=6)
+    h = 1.3 / nx
+    x, y = ic["x"].copy(), ic["y"].copy()
+    dx, dy = x - 0.5, y - 0.5
+    r = np.hypot(dx, dy)
+    k0 = int(np.argmin(r))
+    scale = np.where(r < 4.0 * h, 4.0 * h / np.maximum(r, 1e-12), 1.0)
+    x, y = 0.5 + dx * scale, 0.5 + dy * scale
+    x[k0], y[k0] = 0.5, 0.5                      # the isolated particle
+    rp, _ = orc.neighbors(x, y, 1.0, h)
+    assert rp[k0 + 1] == rp[k0]
+    ctx = B.ann_create(gpu_params(B, params(nx), nx * nx))
+    try:
+        B.ann_set_particles(ctx, x, y, ic["ux"], ic["uy"], ic["q11"], ic["q12"])
+        put = _bits(B.ann_get_state(ctx, nx * nx))
+        with pytest.raises(B.AnnError) as e:
+            B.ann_step(ctx, 3)
+        assert e.value.status == -7
+        d = B.ann_get_diagnostics(ctx)
+        assert d["step"] == 0 and d["t"] == 0.0 and d["error_bits"] & 16
+        for f, v in _bits(B.ann_get_state(ctx, nx * nx)).items():
+            assert np.array_equal(v, put[f]), f
+    finally:
+        B.ann_destroy(ctx)

@@ -86,9 +86,9 @@ def test_reference_arm_line(tmp_path):
 def test_launch_count_of_the_step_graph():
     import bench
 
-    # predictor + branch condition + (filter | five re-sort kernels) + passes B, C, D
-    assert bench.launches_in_steps(1, 0) == 6
-    assert bench.launches_in_steps(1, 1) == 10
-    assert bench.launches_in_steps(100, 7) == 628
+    # commit + predictor + branch condition + (filter | five re-sort kernels) + passes B, C, D
+    assert bench.launches_in_steps(1, 0) == 7
+    assert bench.launches_in_steps(1, 1) == 11
+    assert bench.launches_in_steps(100, 7) == 728
     assert set(bench.RESORT_BRANCH) | {"predict", "pass_a", "pass_b", "pass_c", "pass_d"} == set(
         bench.FLOPS_PER_PAIR) | {"predict", "cell_keys", "cell_scan", "cell_scatter", "cell_order"}
