@@ -151,3 +151,33 @@ def smooth_ic(nx, seed, u_amp=1e-2):
     ic["q12"] = 0.8 * np.sin(2 * th)
     ic["rho"] = 1.0 + 1e-4 * np.cos(tp * (x + y))
     return ic
+
+
+def maxerr_group(gpu_parts, ref_parts):
+    """Element-wise error of a (vector or tensor) field: max over particles of |g_i - o_i| divided
+    by max over particles of |o_i|, the components of a particle taken together.  A few particles
+    wrong at 1e-3 pass a normwise bound at 1M particles but not this one."""
+    g = np.stack([np.ravel(np.asarray(a, dtype=np.float64)) for a in gpu_parts], axis=1)
+    o = np.stack([np.ravel(np.asarray(a, dtype=np.float64)) for a in ref_parts], axis=1)
+    scale = np.sqrt((o * o).sum(axis=1)).max()
+    diff = np.sqrt(((g - o) ** 2).sum(axis=1)).max()
+    if scale == 0.0:
+        return float(diff)
+    return float(diff / scale)
+
+
+def compare_state_max(gpu, orc_state, x0, y0, rho0=1.0, L=1.0):
+    """Element-wise errors of every state field (maxerr_group); displacements net of one FP64 unit
+    of L per coordinate, the resolution of a stored position."""
+    dg = np.stack([min_image(gpu["x"] - x0, L), min_image(gpu["y"] - y0, L)], axis=1)
+    do = np.stack([min_image(orc_state["x"] - x0, L), min_image(orc_state["y"] - y0, L)], axis=1)
+    noise = math.sqrt(2.0) * np.spacing(L)
+    scale = np.sqrt((do * do).sum(axis=1)).max()
+    diff = max(0.0, np.sqrt(((dg - do) ** 2).sum(axis=1)).max() - noise)
+    return {
+        "disp": diff / scale if scale > 0 else diff,
+        "u": maxerr_group([gpu["ux"], gpu["uy"]], [orc_state["ux"], orc_state["uy"]]),
+        "Q": maxerr_group([gpu["q11"], gpu["q12"]], [orc_state["q11"], orc_state["q12"]]),
+        "a": maxerr_group([gpu["ax"], gpu["ay"]], [orc_state["ax"], orc_state["ay"]]),
+        "drho": maxerr_group([gpu["drho"]], [orc_state["rho"] / rho0 - 1.0]),
+    }

