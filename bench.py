@@ -935,6 +935,32 @@ def run_ours(args):
     return 0
 
 
+LONG_RUN_MEMBERS = ((0.02, 0.04), (0.05, 0.04), (0.1, 0.04), (0.1, 0.02), (0.1, 0.01))
+
+
+def long_run(steps: int, every: int, nx: int = 256):
+    """Long-run statistics of the 256^2 configuration (results section): the activities
+    zeta = 0.02, 0.05, 0.1 at K = 0.04 and, at zeta = 0.1, K = 0.02 and 0.01, as one ensemble,
+    from the configurations' random director and from the results section's perturbed nematic.
+    Prints one JSON line: per initial condition and member, the statistics every `every` steps
+    and their means over the last ten snapshots."""
+    from paper_2108_08919_gb300 import build as cuda_build
+    from paper_2108_08919_gb300 import longrun
+
+    cuda_build.build()
+    out = {"metric": "long-run statistics", "workload": f"{nx}^2 members, zeta x K, scaled eta = 0.03, dt = 1e-4",
+           "steps": steps, "every": every, "runs": {}}
+    for init in ("random_director", "perturbed_nematic"):
+        res = longrun.run(LONG_RUN_MEMBERS, nx=nx, steps=steps, every=every, initial=init)
+        keep = ("step", "t", "vrms", "mean_q", "defect_density", "corr_zero", "slope")
+        out["runs"][init] = {
+            "seconds": res["seconds"], "summary": longrun.summary(res),
+            "series": [{"zeta": m["zeta"], "K": m["K"], "failed": m["failed"],
+                        "snapshots": [{k: s[k] for k in keep} for s in m["snapshots"]]} for m in res["members"]]}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -951,7 +977,12 @@ def main():
     ap.add_argument("--surrogate-cycles", type=int, default=0,
                     help="only run this many surrogate cycles (recorded step + jump) at the headline size, "
                          "untrained weights, and print their wall time (for launch lists and profiles)")
+    ap.add_argument("--long-run", type=int, default=0, metavar="STEPS",
+                    help="only run the long-run statistics (this many steps per member) and print them")
+    ap.add_argument("--long-run-every", type=int, default=500, help="snapshot interval of --long-run")
     args = ap.parse_args()
+    if args.long_run > 0:
+        return long_run(args.long_run, args.long_run_every)
     if args.impl == "reference":
         return run_reference(args)
     if args.surrogate_cycles > 0:

@@ -68,6 +68,19 @@ def wrap_positions(p: np.ndarray, L: float) -> np.ndarray:
     return p
 
 
+def perturbed_nematic(nx: int, *, L: float = 1.0, seed: int = 0, angle: float = 0.0,
+                      spread: float = 0.1, q0: float = 1.0) -> dict:
+    """The results section's initial condition read literally: an ordered nematic (order q0, one
+    director angle ``angle``) slightly perturbed, at rest.  The jittered lattice of
+    ``jittered_lattice(nx, seed=seed)`` with each particle's director angle ``angle`` plus a uniform
+    perturbation in [-spread/2, spread/2) drawn from the generator stream ``seed + 7919``."""
+    ic = jittered_lattice(nx, L=L, seed=seed)
+    d = (uniform53(seed + 7919, ic["n"]) - 0.5) * spread
+    ic["q11"] = q0 * np.cos(2.0 * (angle + d))
+    ic["q12"] = q0 * np.sin(2.0 * (angle + d))
+    return ic
+
+
 def jittered_lattice(nx: int, ny: int | None = None, *, L: float = 1.0, seed: int = 0,
                      jitter: float = 0.05, q0: float = 1.0, sigma: float = 1e-3,
                      rho0: float = 1.0) -> dict:
