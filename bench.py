@@ -104,9 +104,48 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def fp32_peak_tflops(sm_mhz: float) -> float:
-    """152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    """Nominal FP32 rate: SMs x 128 FP32 lanes x 2 flops (FMA) x clock (context for the measured
+    rate of ann_fp32_fma_peak, which is the roofline's denominator)."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def developed_flow_bench(B, stream, steps: int = 6000, u_max: float = 0.1, seed: int = 5):
+    """Steps of the headline workload from a moving state, so that the re-sort branch runs as in a
+    developed flow: the box-scale cellular flow u = u_max (sin 2 pi y, sin 2 pi x) (V_rms = u_max, the
+    level of the developed 256^2 long runs; a box-scale field, since particle-scale velocities decay
+    within a few steps at eta = 1), timed over `steps` steps with CUDA events; re-sorts per 1,000
+    steps and the step time beside the headline's (which starts from rest and does not re-sort)."""
+    import numpy as np
+    import torch
+
+    import sph_inputs as si
+
+    ic = si.jittered_lattice(NX, seed=seed)
+    ux = u_max * np.sin(2.0 * np.pi * ic["y"])
+    uy = u_max * np.sin(2.0 * np.pi * ic["x"])
+    p = make_params(B, NX)
+    ctx = B.ann_create(p)
+    try:
+        B.ann_set_stream(ctx, stream)
+        B.ann_set_particles(ctx, ic["x"], ic["y"], ux, uy, ic["q11"], ic["q12"], ic["rho"])
+        B.ann_step(ctx, 20)
+        torch.cuda.synchronize()
+        r0 = B.ann_get_diagnostics(ctx)["resorts"]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            B.ann_step(ctx, steps)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        d = B.ann_get_diagnostics(ctx)
+        ms = e0.elapsed_time(e1)
+    finally:
+        B.ann_destroy(ctx)
+    rs = d["resorts"] - r0
+    return {"steps": steps, "ms_per_step": ms / steps, "resorts": rs, "resorts_per_1000_steps": 1000.0 * rs / steps,
+            "max_speed": d["max_speed"], "u_max": u_max,
+            "particle_steps_per_s": NX * NX * steps / (ms * 1e-3)}
 
 
 class ClockSampler:
@@ -340,9 +379,11 @@ def ensemble_members(count=ENSEMBLE_MEMBERS, seed=2021):
     return out
 
 
-def ensemble_bench(B, steps=100, trial_steps=10, solo_steps=20):
-    """Aggregate particle-steps/s of the ensemble (one graph launch per step, autotuned grouping)
-    against the same members stepped one after another through their own step graphs."""
+def ensemble_bench(B, steps=5000, trial_steps=10, solo_steps=20):
+    """Aggregate particle-steps/s of the ensemble over 5,000 steps (one graph launch per step,
+    autotuned grouping) against the same members stepped one after another through their own step
+    graphs; each member's solo rate shows how far a small member alone leaves the SMs idle (the
+    pair passes of a 128^2 member have 64 tiles of 4 x 4 cells, one block each, for 152 SMs)."""
     import numpy as np  # noqa: F401
 
     import sph_inputs as si
@@ -366,17 +407,23 @@ def ensemble_bench(B, steps=100, trial_steps=10, solo_steps=20):
         B.ann_ensemble_step(ens, steps)
         el = time.perf_counter() - t0
         seq = 0.0
+        solo = []
         for k in range(len(spec)):
             ctx = B.ann_ensemble_member(ens, k)
             B.ann_step(ctx, 1)
             t1 = time.perf_counter()
             B.ann_step(ctx, solo_steps)
-            seq += (time.perf_counter() - t1) / solo_steps
+            dt_k = (time.perf_counter() - t1) / solo_steps
+            seq += dt_k
+            solo.append((spec[k][0] ** 2, spec[k][0] ** 2 / dt_k))
     finally:
         B.ann_ensemble_destroy(ens)
+    solo.sort()
     return {"members": len(spec), "particles": total, "groups": groups, "steps": steps,
             "value": total * steps / el, "unit": METRIC, "ms_per_step": 1e3 * el / steps,
             "sequential_value": total / seq, "sequential_ms_per_step": 1e3 * seq,
+            "solo_rate_smallest_8": sum(r for _, r in solo[:8]) / 8, "solo_rate_largest_8": sum(r for _, r in solo[-8:]) / 8,
+            "solo_sizes": [solo[0][0], solo[-1][0]],
             "speedup_vs_sequential": (total * steps / el) / (total / seq),
             "workload": "64 members, side U[128, 512], zeta log-U[0.01, 0.2], K U[0.01, 0.08], stable dt",
             "timing": "wall clock around synchronised calls"}
@@ -869,6 +916,8 @@ def run_ours(args):
     e2e_value = job_throughput(ws, n, e2e_steps, slowest(e2e_el, dist, "cuda"))
     diag_times = diagnostics_times(B, ctx, n, ic) if rank == 0 else None
     B.ann_destroy(ctx)
+    fma = B.ann_fp32_fma_peak(stream) if rank == 0 else None
+    developed = developed_flow_bench(B, stream) if rank == 0 else None
 
     if rank != 0:
         if dist:
@@ -881,7 +930,8 @@ def run_ours(args):
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     flops_launch = FLOPS_PER_PAIR.get(dom, 0.0) * pairs_per_step
     achieved_tf = flops_launch / (dom_launch_ms * 1e-3) / 1e12 if dom_launch_ms > 0 else 0.0
-    peak_tf = fp32_peak_tflops(sm_mhz)
+    nominal_tf = fp32_peak_tflops(sm_mhz, fma["sms"])
+    peak_tf = max(fma["scalar"], fma["pair"])
     traffic, _ = _traffic_for(dom)
     bytes_launch = BYTES_PER_PARTICLE.get(dom, 0) * n
     line = {
@@ -894,11 +944,12 @@ def run_ours(args):
         "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved_tf,
                      "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
                      "traffic": traffic,
-                     "peak_source": f"FP32 152 SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz "
-                                    f"(sm_max_mhz of MEASURED_PEAKS.json, {src})",
+                     "peak_source": f"measured: project FMA microbenchmark ann_fp32_fma_peak, {fma['sms']} SMs, "
+                                    f"scalar {fma['scalar']:.1f}, two-lane {fma['pair']:.1f} TFLOP/s (the larger); "
+                                    f"nominal {fma['sms']} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz = {nominal_tf:.1f}",
                      "flops_per_launch": flops_launch, "avg_launch_ms": dom_launch_ms,
                      "hbm_achieved_gbs": bytes_launch / (dom_launch_ms * 1e-3) / 1e9,
-                     "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                     "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": src,
                      "hbm_frac": bytes_launch / (dom_launch_ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)},
         "kernel_ms": kms,
         "kernel_launches": klaunch,
@@ -913,6 +964,7 @@ def run_ours(args):
     }
     if diag_times is not None:
         line["diagnostics"] = diag_times
+    line["developed_flow"] = developed
     if ws == 1 and not args.no_ensemble:
         line["ensemble"] = ensemble_bench(B)
     if ws == 1 and not args.no_surrogate:

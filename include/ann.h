@@ -523,6 +523,17 @@ int ann_ensemble_autotune(ann_ensemble *ens, int32_t trial_steps, int32_t *group
 const char *ann_ensemble_last_error(ann_ensemble *ens);
 
 /*
+ * FP32 fused multiply-add throughput of the current device, measured (the roofline of the pair
+ * passes, which are bound by plain FP32 issue).  The paper has no counterpart: this is a measuring
+ * utility.  Runs independent FMA chains on every SM at full occupancy, in the scalar form and in
+ * the two-lane form (one instruction for two lanes), on `stream` (a cudaStream_t, NULL: the legacy
+ * default stream), and returns the best of three timed launches of each in TFLOP/s (2 flops per lane
+ * FMA) and the device's SM count (sms may be NULL).  Synchronises; allocates a small scratch buffer.
+ * Errors: INVALID_ARG (NULL outputs), CUDA.
+ */
+int ann_fp32_fma_peak(void *stream, double *tflops_scalar, double *tflops_pair, int32_t *sms);
+
+/*
  * Velocity moments without any device allocation.  The paper has no counterpart: this is a
  * service entry point for callers that cannot call cudaMalloc -- a host framework that owns a fixed
  * device memory pool or a hard memory budget and forbids allocations after start-up, or a real-time

@@ -128,6 +128,7 @@ def lib() -> ctypes.CDLL:
         "ann_load_state": (i32, [vp, ctypes.c_char_p]),
         "ann_last_error": (ctypes.c_char_p, [vp]),
         "ann_velocity_moments_noalloc": (i32, [vp, vp, vp, ctypes.c_double, i64, vp, vp]),
+        "ann_fp32_fma_peak": (i32, [vp, _P(ctypes.c_double), _P(ctypes.c_double), _P(ctypes.c_int32)]),
         "ann_grid_fields": (i32, [vp, i32, vp, i32]),
         "ann_spectrum_shells": (i32, [i32]),
         "ann_energy_spectrum": (i32, [vp, i32, _P(ctypes.c_double), i32]),
@@ -424,6 +425,16 @@ def ann_load_state(ctx, path: str) -> None:
 
 def ann_last_error(ctx) -> str:
     return lib().ann_last_error(ctx).decode()
+
+
+def ann_fp32_fma_peak(stream=None) -> dict:
+    """Measured FP32 FMA throughput of the current device: {"scalar": TFLOP/s, "pair": TFLOP/s,
+    "sms": SM count}."""
+    a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    handle = getattr(stream, "cuda_stream", stream) if stream is not None else 0
+    _check(lib().ann_fp32_fma_peak(ctypes.c_void_p(int(handle) if handle else 0), ctypes.byref(a), ctypes.byref(b),
+                                   ctypes.byref(n)), None, "ann_fp32_fma_peak")
+    return {"scalar": a.value, "pair": b.value, "sms": n.value}
 
 
 NOALLOC_MAX_N = 2097152

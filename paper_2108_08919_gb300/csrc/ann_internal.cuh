@@ -141,7 +141,9 @@ __device__ __forceinline__ StateSet pick_set(const Bufs &b, bool one)
     s.id = one ? b.st[1].id : b.st[0].id;
     return s;
 }
-__device__ __forceinline__ bool cur_set(const Bufs &b) { return (*(volatile uint32_t *)(b.ctl + CTL_CUR)) != 0u; }
+// ctl[CTL_CUR] changes only in k_commit, a kernel of its own, so the step kernels may read it through
+// the read-only cache (one L2 round trip per SM instead of one per thread).
+__device__ __forceinline__ bool cur_set(const Bufs &b) { return __ldg(b.ctl + CTL_CUR) != 0u; }
 __device__ __forceinline__ StateSet state_in(const Bufs &b) { return pick_set(b, cur_set(b)); }
 __device__ __forceinline__ StateSet state_out(const Bufs &b) { return pick_set(b, !cur_set(b)); }
 
