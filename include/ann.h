@@ -476,6 +476,31 @@ int ann_surrogate_adam(ann_surrogate *sg, double lr);
  * the prediction is not finite (the context's error bit is then set, as a failed step sets it). */
 int ann_surrogate_jump(ann_surrogate *sg, ann_ctx *ctx, const float *tend);
 
+/* Guarded advance: `cycles` surrogate cycles of ctx -- one recorded plain step, then one jump of k
+ * steps -- with the network held to plain SPH.  Every `check_every` cycles (0: never) the cycle is
+ * also run in plain SPH (k + 1 steps) on `shadow`, a second context of the same parameters and n
+ * owned by the caller, from the same state (copied to it on the device), and the jump's increments
+ * of Q and u over the cycle are compared with the plain ones: err = ||dX_jump - dX_plain|| /
+ * ||dX_plain|| over all particles (FP64 sums in a fixed order).  If either error exceeds `tol` (the
+ * configuration's bound is 0.05), or the jump is not finite, ctx takes the plain result of that
+ * cycle and the remaining cycles run as plain steps: the fallback.  The report gives the completed
+ * cycles, the checks, their largest and last errors, and where the fallback happened.  ctx's
+ * recording setting is restored.  Errors: INVALID_ARG (shadow NULL or ctx itself while
+ * check_every > 0, tol <= 0, ctx larger than the network's n_max), STATE, the errors of ann_step
+ * and ann_surrogate_jump (NONFINITE from an unchecked jump), CUDA.  After a fallback from a
+ * non-finite jump ctx is reloaded (ann_set_state): its periodic image counts restart. */
+typedef struct ann_guard_report {
+    int32_t cycles_done;       /* jumps kept */
+    int32_t checks;            /* cycles compared with plain SPH */
+    int32_t fell_back;         /* 1: a check failed; the rest ran in plain SPH */
+    int32_t fallback_cycle;    /* index of the failed check's cycle, -1 if none */
+    int64_t plain_steps;       /* plain steps run after the fallback */
+    double max_err_q, max_err_u;     /* largest errors of the checks */
+    double last_err_q, last_err_u;   /* the last check's errors */
+} ann_guard_report;
+int ann_surrogate_advance(ann_surrogate *sg, ann_ctx *ctx, ann_ctx *shadow, int32_t cycles, int32_t check_every,
+                          double tol, ann_guard_report *report);
+
 /* Whether the jump adds the network's velocity correction ys_u (y2, y3) (on = 1) or not (0, the
  * default).  In the viscous regime of the paper's runs u follows Q almost instantly: the
  * correction gains little on a single jump and, fed back over many jumps, grows a mode of its own,

@@ -153,6 +153,7 @@ def lib() -> ctypes.CDLL:
         "ann_surrogate_gradients": (i32, [vp, _P(ctypes.c_float), _P(ctypes.c_double), _P(ctypes.c_float)]),
         "ann_surrogate_adam": (i32, [vp, ctypes.c_double]),
         "ann_surrogate_jump": (i32, [vp, vp, _P(ctypes.c_float)]),
+        "ann_surrogate_advance": (i32, [vp, vp, vp, i32, i32, ctypes.c_double, vp]),
         "ann_surrogate_set_velocity_correction": (i32, [vp, i32]),
         "ann_surrogate_last_error": (ctypes.c_char_p, [vp]),
         "ann_ensemble_create": (i32, [_P(ann_params), i32, _P(vp)]),
@@ -729,6 +730,23 @@ def ann_surrogate_adam(sg, lr: float) -> None:
 def ann_surrogate_jump(sg, ctx, tend=None) -> None:
     ptr, keep = _tend(tend)
     _scheck(lib().ann_surrogate_jump(sg, ctx, ptr), sg, "ann_surrogate_jump")
+
+
+class ann_guard_report(ctypes.Structure):
+    _fields_ = [("cycles_done", ctypes.c_int32), ("checks", ctypes.c_int32), ("fell_back", ctypes.c_int32),
+                ("fallback_cycle", ctypes.c_int32), ("plain_steps", ctypes.c_int64),
+                ("max_err_q", ctypes.c_double), ("max_err_u", ctypes.c_double),
+                ("last_err_q", ctypes.c_double), ("last_err_u", ctypes.c_double)]
+
+
+def ann_surrogate_advance(sg, ctx, shadow, cycles: int, check_every: int, tol: float = 0.05) -> dict:
+    """Guarded surrogate cycles (recorded plain step + jump), checked against plain SPH on `shadow`
+    every `check_every` cycles; falls back to plain SPH when an error exceeds `tol`.  The report as
+    a dict."""
+    r = ann_guard_report()
+    _scheck(lib().ann_surrogate_advance(sg, ctx, shadow, int(cycles), int(check_every), float(tol), ctypes.byref(r)),
+            sg, "ann_surrogate_advance")
+    return {k: getattr(r, k) for k, _ in r._fields_}
 
 
 def ann_surrogate_set_velocity_correction(sg, on) -> None:

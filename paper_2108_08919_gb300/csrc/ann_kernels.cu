@@ -167,7 +167,7 @@ __device__ __forceinline__ float2 split_offset(double o, const DevParams &P)
     return make_float2(hi, (float)(o - (double)hi));
 }
 
-__global__ void __launch_bounds__(256) k_predict(DevParams P, Bufs b)
+__global__ void __launch_bounds__(256, 8) k_predict(DevParams P, Bufs b)
 {
     if (stopped(b)) return;
     __shared__ float wmax[8];

@@ -329,6 +329,33 @@ inline unsigned nb(size_t n, int t = 256) { return (unsigned)((n + t - 1) / t); 
 // lanes per particle of k_sg_agg<C>
 constexpr int agg_lanes(int C) { return C / (8 * ((C / 8) % SG_AGG_V == 0 ? SG_AGG_V : 1)); }
 
+// Sums over the particles (ID order) of the increments of a checked cycle: |dQ_jump - dQ_plain|^2,
+// |dQ_plain|^2, |du_jump - du_plain|^2, |du_plain|^2, one FP64 partial per block (summed on the
+// host in block order: deterministic).
+__global__ void __launch_bounds__(256) k_sg_guard_sums(int n, const float *const *b, const float *const *j,
+                                                       const float *const *p, double *part)
+{
+    __shared__ double red[4][256];
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (i < n) {
+        for (int c = 0; c < 4; c++) {   // components ux, uy, q11, q12 of the state arrays
+            const double b0 = b[c][i], dj = (double)j[c][i] - b0, dp = (double)p[c][i] - b0;
+            const int w = c < 2 ? 2 : 0;   // u -> slots 2, 3; Q -> slots 0, 1
+            v[w] += (dj - dp) * (dj - dp);
+            v[w + 1] += dp * dp;
+        }
+    }
+    for (int q = 0; q < 4; q++) red[q][threadIdx.x] = v[q];
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+            for (int q = 0; q < 4; q++) red[q][threadIdx.x] += red[q][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) part[4 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
 }  // namespace
 }  // namespace ann
 
@@ -368,6 +395,13 @@ struct ann_surrogate {
     double *loss;
     unsigned *err;
     int adam_t = 0;
+    // the guard of ann_surrogate_advance (allocated on its first call): three ID-ordered states --
+    // before a checked cycle, after its jump, after its plain steps -- and the error partial sums
+    struct GuardState {
+        double *x = nullptr, *y = nullptr;
+        float *f[7] = {};   // ux, uy, q11, q12, drho, ax, ay
+    } gs[3];
+    double *gpart = nullptr;   // 4 partial sums per block
 };
 
 namespace {
@@ -512,6 +546,31 @@ int check_err(ann_surrogate *S, const char *where)
     if (e) return scuda(S, e, where);
     if (h) return sfail(S, ANN_ERR_TIMEOUT, std::string(where) + ": a tensor-core wait timed out");
     return ANN_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Copy the state of ctx (ID order) into guard state k.
+int guard_get(ann_surrogate *S, ann_ctx *ctx, int k)
+{
+    auto &g = S->gs[k];
+    return ann_get_state(ctx, g.x, g.y, g.f[0], g.f[1], g.f[2], g.f[3], g.f[4], g.f[5], g.f[6], 1);
+}
+
+// Give ctx (n particles) the state held in guard state k, with its accelerations.  A context that
+// holds no particles or has an error raised is loaded afresh first (ann_set_state clears the
+// error bits), then updated.
+int guard_put(ann_surrogate *S, ann_ctx *ctx, int k, int64_t n)
+{
+    auto &g = S->gs[k];
+    ann_diag d;
+    if (ann_get_diagnostics(ctx, &d) != ANN_OK || d.error_bits != 0u) {
+        int st = ann_set_state(ctx, n, g.x, g.y, g.f[0], g.f[1], g.f[2], g.f[3], g.f[4], 1);
+        if (st) return st;
+    }
+    return ann_update_state(ctx, g.x, g.y, g.f[0], g.f[1], g.f[2], g.f[3], g.f[4], g.f[5], g.f[6], 1);
 }
 
 }  // namespace
@@ -750,6 +809,124 @@ int ann_surrogate_euler(ann_surrogate *S, float *inc)
     if (!e) e = cudaMemcpyAsync(inc, S->io4, (size_t)S->n * NOUT * sizeof(float), cudaMemcpyDeviceToHost, S->s);
     if (!e) e = cudaStreamSynchronize(S->s);
     return e ? scuda(S, e, "ann_surrogate_euler") : ANN_OK;
+}
+
+int ann_surrogate_advance(ann_surrogate *S, ann_ctx *ctx, ann_ctx *shadow, int32_t cycles, int32_t check_every,
+                          double tol, ann_guard_report *rep)
+{
+    ann::NvtxRange range("ann_surrogate_advance");
+    if (!S || !ctx || !rep || cycles < 0 || check_every < 0 || !(tol > 0.0)) return ANN_ERR_INVALID_ARG;
+    if (check_every > 0 && (!shadow || shadow == ctx)) return ANN_ERR_INVALID_ARG;
+    CtxView v;
+    int st = ctx_view(ctx, &v);
+    if (st) return st;
+    const int64_t n = v.P.n;
+    const int rec0 = v.P.record;
+    if (n > S->nmax) return sfail(S, ANN_ERR_INVALID_ARG, "the context holds more particles than the network's n_max");
+    if (check_every > 0) {
+        CtxView w;
+        st = ctx_view(shadow, &w);
+        if (st == ANN_ERR_STATE) st = ANN_OK;   // a shadow without particles is loaded at the first check
+        if (st) return st;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!S->gpart) {
+        for (int k = 0; k < 3 && !e; k++) {
+            e = sg_alloc(S, S->gs[k].x, (size_t)S->nmax);
+            if (!e) e = sg_alloc(S, S->gs[k].y, (size_t)S->nmax);
+            for (int c = 0; c < 7 && !e; c++) e = sg_alloc(S, S->gs[k].f[c], (size_t)S->nmax);
+        }
+        if (!e) e = sg_alloc(S, S->gpart, 4 * (size_t)nb((int)S->nmax));
+        if (e) return scuda(S, e, "ann_surrogate_advance buffers");
+    }
+    *rep = ann_guard_report{};
+    rep->fallback_cycle = -1;
+    const int k = S->k;
+    int result = ANN_OK;
+    for (int32_t c = 0; c < cycles; c++) {
+        const bool check = check_every > 0 && c % check_every == 0;
+        if (check) {
+            st = guard_get(S, ctx, 0);
+            if (!st) st = guard_put(S, shadow, 0, n);
+            if (st) { result = st; break; }
+        }
+        // the cycle: one recorded plain step, then the jump over k steps
+        st = ann_set_record(ctx, 1);
+        if (!st) st = ann_step(ctx, 1);
+        if (st) { result = st; break; }
+        st = ann_surrogate_jump(S, ctx, nullptr);
+        const bool bad_jump = st == ANN_ERR_NONFINITE;
+        if (st && !bad_jump) { result = st; break; }
+        if (!check) {
+            if (bad_jump) { result = st; break; }
+            rep->cycles_done++;
+            continue;
+        }
+        // the same cycle in plain SPH on the shadow, and the relative errors of the increments
+        st = ann_step(shadow, 1 + k);
+        if (!st) st = guard_get(S, shadow, 2);
+        if (st) { result = st; break; }
+        double eq = INFINITY, eu = INFINITY;
+        if (!bad_jump) {
+            st = guard_get(S, ctx, 1);
+            if (st) { result = st; break; }
+            const float *b[4] = {S->gs[0].f[0], S->gs[0].f[1], S->gs[0].f[2], S->gs[0].f[3]};
+            const float *j[4] = {S->gs[1].f[0], S->gs[1].f[1], S->gs[1].f[2], S->gs[1].f[3]};
+            const float *pl[4] = {S->gs[2].f[0], S->gs[2].f[1], S->gs[2].f[2], S->gs[2].f[3]};
+            const float **dptr = nullptr;
+            const int nbk = nb((int)n);
+            // the three sets of four component pointers travel as a small device array
+            e = cudaMalloc(&dptr, 12 * sizeof(float *));
+            if (!e) {
+                const float *hp[12] = {b[0], b[1], b[2], b[3], j[0], j[1], j[2], j[3], pl[0], pl[1], pl[2], pl[3]};
+                e = cudaMemcpyAsync(dptr, hp, sizeof hp, cudaMemcpyHostToDevice, S->s);
+                if (!e) k_sg_guard_sums<<<nbk, 256, 0, S->s>>>((int)n, dptr, dptr + 4, dptr + 8, S->gpart);
+                if (!e) e = cudaGetLastError();
+                std::vector<double> h(4 * (size_t)nbk);
+                if (!e) e = cudaMemcpyAsync(h.data(), S->gpart, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, S->s);
+                if (!e) e = cudaStreamSynchronize(S->s);
+                cudaFree(dptr);
+                if (!e) {
+                    double sums[4] = {0.0, 0.0, 0.0, 0.0};
+                    for (int q = 0; q < nbk; q++)
+                        for (int t = 0; t < 4; t++) sums[t] += h[4 * (size_t)q + t];
+                    auto rel = [](double num, double den) { return den > 0.0 ? std::sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0); };
+                    eq = rel(sums[0], sums[1]);
+                    eu = rel(sums[2], sums[3]);
+                }
+            }
+            if (e) { result = scuda(S, e, "ann_surrogate_advance check"); break; }
+        }
+        rep->checks++;
+        rep->last_err_q = eq;
+        rep->last_err_u = eu;
+        rep->max_err_q = std::max(rep->max_err_q, eq);
+        rep->max_err_u = std::max(rep->max_err_u, eu);
+        if (!(eq <= tol && eu <= tol)) {
+            // fall back: the context takes the plain result of this cycle, and the remaining cycles
+            // run as plain steps
+            int64_t steps_before = 0;
+            {
+                CtxView w;
+                if (!ctx_view(ctx, &w)) steps_before = w.steps;
+            }
+            ann_diag d;
+            const bool broken = ann_get_diagnostics(ctx, &d) != ANN_OK || d.error_bits != 0u;
+            st = guard_put(S, ctx, 2, n);
+            if (!st && broken) st = ctx_commit_in_place(ctx, steps_before);   // ann_set_state restarted t and the count
+            if (st) { result = st; break; }
+            rep->fell_back = 1;
+            rep->fallback_cycle = c;
+            const int64_t plain = (int64_t)(cycles - c - 1) * (1 + k);
+            st = ann_set_record(ctx, rec0);
+            if (!st) st = ann_step(ctx, plain);
+            rep->plain_steps = plain;
+            return st;
+        }
+        rep->cycles_done++;
+    }
+    int st2 = ann_set_record(ctx, rec0);
+    return result ? result : st2;
 }
 
 int ann_surrogate_set_velocity_correction(ann_surrogate *S, int32_t on)

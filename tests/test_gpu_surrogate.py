@@ -338,3 +338,74 @@ def test_plain_steps_continue_from_a_jump_in_place(B, orc):
     finally:
         B.ann_surrogate_destroy(sg)
         run.close()
+
+
+def _guard_setup(B, nx, seed):
+    ic = random_velocity_ic(nx, seed, u_scale=2e-2)
+    p = params(nx, c0_min=0.05)
+    p["dt"] = stable_dt(p)
+    return ic, p
+
+
+def test_guard_falls_back_to_plain_sph(B):
+    """The guarded advance (ann_surrogate_advance) with an untrained network and a tight bound: the
+    first check finds the jump's increments off the plain ones, the context takes the plain result
+    of that cycle and runs the remaining cycles as plain steps.  The final state matches a context
+    that ran the same number of plain steps from the same start (to FP32 summation order: the
+    shadow's copy of the state is re-sorted afresh), and the step count is the same."""
+    nx, k, cycles = 48, 8, 3
+    ic, p = _guard_setup(B, nx, 41)
+    n = ic["n"]
+    gp = gpu_params(B, p, n)
+    ctx, shadow, ref = B.ann_create(gp), B.ann_create(gp), GpuRun(B, p, ic)
+    sg = B.ann_surrogate_create(n)
+    try:
+        _load(B, ctx, ic)
+        B.ann_surrogate_init(sg, 5)
+        B.ann_surrogate_set_scales(sg, 0.01, 1e-3, 1e-5, k)
+        rep = B.ann_surrogate_advance(sg, ctx, shadow, cycles, 1, 1e-6)
+        assert rep["fell_back"] == 1 and rep["fallback_cycle"] == 0 and rep["checks"] == 1
+        assert rep["cycles_done"] == 0 and rep["plain_steps"] == (cycles - 1) * (k + 1)
+        assert rep["last_err_q"] > 1e-6
+        ref.step(cycles * (k + 1))
+        assert B.ann_get_diagnostics(ctx)["step"] == cycles * (k + 1) == B.ann_get_diagnostics(ref.ctx)["step"]
+        got = B.ann_get_state(ctx, n)
+        want = B.ann_get_state(ref.ctx, n)
+        for f in ("UX", "UY", "Q11", "Q12", "DRHO"):
+            assert relerr(got[f], want[f]) <= 1e-5, f
+    finally:
+        B.ann_surrogate_destroy(sg)
+        B.ann_destroy(ctx)
+        B.ann_destroy(shadow)
+        ref.close()
+
+
+def test_guard_keeps_jumps_that_pass(B):
+    """With a loose bound every check passes: the jumps are kept, the report carries the measured
+    errors of each check, and the checks leave the trajectory bit-identical to the same cycles
+    (recorded plain step + jump) run without the guard."""
+    nx, k, cycles = 48, 8, 4
+    ic, p = _guard_setup(B, nx, 43)
+    n = ic["n"]
+    gp = gpu_params(B, p, n)
+    a, b, shadow = B.ann_create(gp), B.ann_create(gp), B.ann_create(gp)
+    sg = B.ann_surrogate_create(n)
+    try:
+        for c in (a, b):
+            _load(B, c, ic)
+        B.ann_surrogate_init(sg, 5)
+        B.ann_surrogate_set_scales(sg, 0.01, 1e-3, 1e-5, k)
+        rep = B.ann_surrogate_advance(sg, a, shadow, cycles, 2, 1e9)
+        assert rep["fell_back"] == 0 and rep["cycles_done"] == cycles and rep["checks"] == 2
+        assert 0.0 < rep["max_err_q"] < 1e9 and 0.0 < rep["max_err_u"] < 1e9
+        B.ann_set_record(b, 1)
+        for _ in range(cycles):
+            B.ann_step(b, 1)
+            B.ann_surrogate_jump(sg, b, None)
+        sa, sb = B.ann_get_state(a, n), B.ann_get_state(b, n)
+        for f in sa:
+            assert np.array_equal(sa[f], sb[f]), f
+    finally:
+        B.ann_surrogate_destroy(sg)
+        for c in (a, b, shadow):
+            B.ann_destroy(c)
