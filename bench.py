@@ -581,11 +581,18 @@ def _sg_residuals(B, sg, ctx, n, pairs):
     return out
 
 
-def _sg_scales(res):
+def _sg_scales(res, floor: float = 0.0):
+    """Output scales ys of the network's correction: the spread of the residual (true increment
+    minus the explicit one), at least `floor` times the spread of the true increment.  Where the
+    explicit increment is already close (the developed 256^2 flow: 0.3 %), the floor keeps the
+    features, which are divided by ys, at a trainable size."""
     import numpy as np
 
-    ysq = np.std(np.concatenate([(t - e)[:, :2].ravel() for t, e in res]))
-    ysu = np.std(np.concatenate([(t - e)[:, 2:].ravel() for t, e in res]))
+    def spread(cs, of_truth):
+        return np.std(np.concatenate([(t if of_truth else t - e)[:, cs].ravel() for t, e in res]))
+
+    ysq = max(spread(slice(0, 2), False), floor * spread(slice(0, 2), True))
+    ysu = max(spread(slice(2, 4), False), floor * spread(slice(2, 4), True))
     return np.array([ysq, ysq, ysu, ysu])
 
 
@@ -729,9 +736,10 @@ def surrogate_bench(B, max_err=0.05):
     # fine-tuning and evaluation at 1024 x 1024 (the workload of the headline metric)
     try:
         n = NX * NX
-        p1, dt1, sn = _sg_trajectory(B, NX, PARAMS["zeta"], PARAMS["K"], 11, 14, 300, u0=0.02)
-        pairs = _sg_pairs(sn)
-        tr1, te1 = pairs[:10], pairs[10:]
+        # fine-tune on a seed-11 trajectory, hold out a trajectory of another seed (12)
+        p1, dt1, sn = _sg_trajectory(B, NX, PARAMS["zeta"], PARAMS["K"], 11, 10, 300, u0=0.02)
+        _, _, sn_b = _sg_trajectory(B, NX, PARAMS["zeta"], PARAMS["K"], 12, 4, 300, u0=0.02)
+        tr1, te1 = _sg_pairs(sn), _sg_pairs(sn_b)
         us1 = float(np.sqrt(np.mean(np.concatenate([np.r_[a["UX"], a["UY"]] for a, _ in tr1]) ** 2)))
         c1 = B.ann_create(p1)
         try:
@@ -742,7 +750,8 @@ def surrogate_bench(B, max_err=0.05):
             t0 = time.perf_counter()
             l0, l1 = _sg_train(B, sg, c1, n, tr1, res1, ys1, 200, 1e-3)
             e_net, e_eul, e_q, e_u = _sg_eval(B, sg, c1, n, te1, ys1, parts=True)
-            out["finetune"] = {"resolution": NX, "pairs": len(tr1), "iters": 200, "loss_first": l0,
+            out["finetune"] = {"resolution": NX, "pairs": len(tr1), "heldout_pairs": len(te1), "train_seed": 11,
+                               "heldout_seed": 12, "iters": 200, "loss_first": l0,
                                "loss_last": l1, "seconds": time.perf_counter() - t0, "heldout_err": e_net,
                                "euler_err": e_eul, "heldout_q_err_net_euler": e_q,
                                "heldout_u_err_net_euler": e_u, "velocity_correction": False}
@@ -774,28 +783,33 @@ def surrogate_bench(B, max_err=0.05):
                              "steps_per_cycle": SG_K + 1, "speedup": tp / tc,
                              "speedup_used": tp / tc if use else 1.0,
                              "clock": "wall, synchronised calls, min of 20"}
-            # rollout: 25 cycles from the same state, surrogate against plain SPH
-            cyc = 25
+            # rollout: 25 guarded cycles from the held-out seed's state (the library checks every
+            # 5th cycle against plain SPH on a shadow context and falls back past max_err), against
+            # plain SPH from the same state
+            cyc, every = 25, 5
             load()
             B.ann_step(c1, 1)
-            vmax = []
+            shadow = B.ann_create(p1)
             try:
-                for c in range(cyc):
-                    B.ann_step(c1, 1)
-                    if use:
-                        B.ann_surrogate_jump(sg, c1, None)
-                    else:
-                        B.ann_step(c1, SG_K)
-                    vmax.append(B.ann_get_diagnostics(c1)["max_speed"])
+                B.ann_get_diagnostics(c1)   # synchronises
+                t1 = time.perf_counter()
+                guard = B.ann_surrogate_advance(sg, c1, shadow, cyc, every, max_err) if use else None
+                t_guarded = time.perf_counter() - t1
             except B.AnnError as ex:
-                out["rollout"] = {"cycles": cyc, "failed_at_cycle": c, "error": str(ex)[:200],
-                                  "max_speed_per_cycle": vmax}
+                out["rollout"] = {"cycles": cyc, "error": str(ex)[:200]}
                 raise _SgRolloutFailed() from ex
+            finally:
+                B.ann_destroy(shadow)
+            vmax = [B.ann_get_diagnostics(c1)["max_speed"]]
             s_counts, _ = B.ann_defects(c1, 256)
             s_E = B.ann_energy_spectrum(c1, 256)
             s_u = {f: B.ann_get_field(c1, f, n).astype(np.float64) for f in ("UX", "UY", "Q11", "Q12")}
             load()
-            B.ann_step(c1, 1 + cyc * (SG_K + 1))
+            B.ann_step(c1, 1)
+            B.ann_get_diagnostics(c1)
+            t1 = time.perf_counter()
+            B.ann_step(c1, cyc * (SG_K + 1))
+            t_plain_roll = time.perf_counter() - t1
             p_counts, _ = B.ann_defects(c1, 256)
             p_E = B.ann_energy_spectrum(c1, 256)
             p_u = {f: B.ann_get_field(c1, f, n).astype(np.float64) for f in ("UX", "UY", "Q11", "Q12")}
@@ -807,7 +821,10 @@ def surrogate_bench(B, max_err=0.05):
             du = np.concatenate([s_u["UX"] - p_u["UX"], s_u["UY"] - p_u["UY"]])
             un = np.concatenate([p_u["UX"] - a["UX"], p_u["UY"] - a["UY"]])
             out["rollout"] = {"cycles": cyc, "steps": cyc * (SG_K + 1) + 1, "surrogate_used": use,
-                              "max_speed_per_cycle": vmax,
+                              "guard": guard, "check_every": every,
+                              "guarded_ms": 1e3 * t_guarded if use else None, "plain_ms": 1e3 * t_plain_roll,
+                              "guarded_speedup": t_plain_roll / t_guarded if use else 1.0,
+                              "max_speed": vmax,
                               "defect_density": [float(s_counts[0] + s_counts[1]), float(p_counts[0] + p_counts[1])],
                               "defect_density_rel_err": abs(float(s_counts[0] + s_counts[1] - p_counts[0] - p_counts[1]))
                               / max(float(p_counts[0] + p_counts[1]), 1.0),
@@ -827,6 +844,108 @@ def surrogate_bench(B, max_err=0.05):
 
 class _SgRolloutFailed(Exception):
     pass
+
+
+def surrogate_developed_bench(B, nx=256, zeta=0.1, K=0.02, develop=100000, train_pairs=40, heldout_pairs=6,
+                              iters=1500, cycles=40, every=5, max_err=0.05, ys_floor=0.05):
+    """The surrogate in the developed active flow of the long runs: nx^2, the scaled viscosity
+    eta = 0.03 and dt = 1e-4 (paper_2108_08919_gb300.longrun), zeta = 0.1, K = 0.02, run `develop`
+    plain steps from a random director (t = 10: the activity-built order and flow of the long-run
+    tables).  A network initialised afresh is trained on `train_pairs` 8-step pairs of seed 21's
+    developed trajectory, its increments are held out on seed 22's, and a guarded rollout
+    (ann_surrogate_advance, a plain-SPH check every `every` cycles, fallback past max_err) runs
+    from seed 22's developed state beside plain SPH: spectrum slope, defect density, increments."""
+    import numpy as np
+
+    import sph_inputs as si
+    from paper_2108_08919_gb300 import longrun
+
+    t_all = time.perf_counter()
+    p = longrun.member_params(nx, zeta, K)
+    n = nx * nx
+    out = {"resolution": nx, "zeta": zeta, "K": K, "eta": p.eta, "dt": p.dt, "develop_steps": develop,
+           "max_err": max_err}
+
+    def developed(ctx, seed):
+        ic = si.jittered_lattice(nx, seed=seed)
+        B.ann_set_particles(ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"], ic["rho"])
+        B.ann_step(ctx, develop)
+        B.ann_set_record(ctx, 1)
+        B.ann_step(ctx, 1)
+
+    def snaps(ctx, count):
+        got = []
+        for _ in range(count + 1):
+            got.append(_sg_snapshot(B, ctx, n))
+            B.ann_step(ctx, SG_K)
+        return got
+
+    ca, cb, shadow = B.ann_create(p), B.ann_create(p), B.ann_create(p)
+    sg = B.ann_surrogate_create(n)
+    try:
+        developed(ca, 21)
+        developed(cb, 22)
+        tr, te = _sg_pairs(snaps(ca, train_pairs)), _sg_pairs(snaps(cb, heldout_pairs))
+        out["vrms_developed"] = float(np.sqrt(2.0 * B.ann_get_diagnostics(cb)["kinetic_energy"]))
+        B.ann_surrogate_init(sg, 7)
+        us = float(np.sqrt(np.mean(np.concatenate([np.r_[a["UX"], a["UY"]] for a, _ in tr]) ** 2)))
+        B.ann_surrogate_set_scales(sg, us, 1.0, 1.0, SG_K)
+        res = _sg_residuals(B, sg, ca, n, tr)
+        ys = _sg_scales(res, ys_floor)
+        B.ann_surrogate_set_scales(sg, us, ys[0], ys[2], SG_K)
+        t0 = time.perf_counter()
+        l0, l1 = _sg_train(B, sg, ca, n, tr, res, ys, iters, 1e-3)
+        e_net, e_eul, e_q, e_u = _sg_eval(B, sg, ca, n, te, ys, parts=True)
+        out["train"] = {"pairs": len(tr), "seed": 21, "heldout_pairs": len(te), "heldout_seed": 22, "iters": iters,
+                        "ys_floor": ys_floor,
+                        "loss_first": l0, "loss_last": l1, "seconds": time.perf_counter() - t0,
+                        "heldout_err": e_net, "euler_err": e_eul, "heldout_q_err_net_euler": e_q,
+                        "heldout_u_err_net_euler": e_u}
+        a = te[-1][1]
+
+        def load(ctx):
+            B.ann_set_particles(ctx, a["X"], a["Y"], a["UX"], a["UY"], a["Q11"], a["Q12"], 1.0 + a["DRHO"])
+            B.ann_set_record(ctx, 1)
+            B.ann_step(ctx, 1)
+            B.ann_get_diagnostics(ctx)
+
+        load(cb)
+        t1 = time.perf_counter()
+        guard = B.ann_surrogate_advance(sg, cb, shadow, cycles, every, max_err)
+        t_g = time.perf_counter() - t1
+        s_counts, _ = B.ann_defects(cb, nx)
+        s_E = B.ann_energy_spectrum(cb, nx)
+        s_f = {f: B.ann_get_field(cb, f, n).astype(np.float64) for f in ("UX", "UY", "Q11", "Q12")}
+        load(ca)
+        t1 = time.perf_counter()
+        B.ann_step(ca, cycles * (SG_K + 1))
+        t_p = time.perf_counter() - t1
+        p_counts, _ = B.ann_defects(ca, nx)
+        p_E = B.ann_energy_spectrum(ca, nx)
+        p_f = {f: B.ann_get_field(ca, f, n).astype(np.float64) for f in ("UX", "UY", "Q11", "Q12")}
+        w = 2 * np.pi * np.arange(s_E.size)
+        sl_s, sl_p = B.ann_spectrum_slope(s_E, 1.0, w[3], w[20]), B.ann_spectrum_slope(p_E, 1.0, w[3], w[20])
+        ds, dp = float(s_counts[0] + s_counts[1]), float(p_counts[0] + p_counts[1])
+
+        def rel(fa, fb, ref):
+            num = np.linalg.norm(np.concatenate([fa[0] - fb[0], fa[1] - fb[1]]))
+            den = np.linalg.norm(np.concatenate([fb[0] - ref[0], fb[1] - ref[1]]))
+            return float(num / den) if den > 0 else float("nan")
+
+        out["rollout"] = {"cycles": cycles, "check_every": every, "guard": guard,
+                          "guarded_ms": 1e3 * t_g, "plain_ms": 1e3 * t_p, "speedup": t_p / t_g,
+                          "defect_density": [ds, dp], "defect_density_rel_err": abs(ds - dp) / max(dp, 1.0),
+                          "spectrum_slope": [sl_s, sl_p], "spectrum_slope_abs_err": abs(sl_s - sl_p),
+                          "q_increment_rel_err": rel((s_f["Q11"], s_f["Q12"]), (p_f["Q11"], p_f["Q12"]),
+                                                     (a["Q11"], a["Q12"])),
+                          "u_increment_rel_err": rel((s_f["UX"], s_f["UY"]), (p_f["UX"], p_f["UY"]), (a["UX"], a["UY"])),
+                          "slope_range": "w in [2 pi 3, 2 pi 20]", "grid": nx}
+    finally:
+        B.ann_surrogate_destroy(sg)
+        for c in (ca, cb, shadow):
+            B.ann_destroy(c)
+    out["seconds"] = time.perf_counter() - t_all
+    return out
 
 
 def run_ours(args):
@@ -969,6 +1088,7 @@ def run_ours(args):
         line["ensemble"] = ensemble_bench(B)
     if ws == 1 and not args.no_surrogate:
         line["surrogate"] = surrogate_bench(B)
+        line["surrogate_developed"] = surrogate_developed_bench(B)
     if ws == 1 and not args.no_3d:
         line["three_d"] = three_d_bench(B, nx=args.nx3)
     if ws == 1 and not args.no_sweep:
