@@ -1036,7 +1036,7 @@ def run_ours(args):
     diag_times = diagnostics_times(B, ctx, n, ic) if rank == 0 else None
     B.ann_destroy(ctx)
     fma = B.ann_fp32_fma_peak(stream) if rank == 0 else None
-    developed = developed_flow_bench(B, stream) if rank == 0 else None
+    developed = developed_flow_bench(B, stream) if rank == 0 and not args.no_developed_flow else None
 
     if rank != 0:
         if dist:
@@ -1145,6 +1145,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
     ap.add_argument("--no-3d", action="store_true", help="skip the three-dimensional variant's measurement")
     ap.add_argument("--no-sweep", action="store_true", help="skip the activity / elastic-constant sweep")
+    ap.add_argument("--no-developed-flow", action="store_true", help="skip the moving-state re-sort timing")
     ap.add_argument("--nx3", type=int, default=NX3, help="side of the 3D variant's cubic lattice")
     ap.add_argument("--surrogate-cycles", type=int, default=0,
                     help="only run this many surrogate cycles (recorded step + jump) at the headline size, "
