@@ -262,7 +262,9 @@ int ann_get_field(ann_ctx *ctx, int field, void *dst, int64_t bytes, int dst_is_
  * drho = rho/rho0 - 1 and ax, ay FP32; n each, particle-ID order, in one call with one
  * synchronisation: the same values as
  * ann_get_field of ANN_FIELD_X ... _DRHO, _AX, _AY.  A NULL destination is skipped.  dst_is_device
- * as for ann_get_field.  Errors: STATE, CUDA. */
+ * as for ann_get_field.  When every host destination is page-locked memory that the device maps
+ * (cudaHostAlloc, cudaHostRegister), one kernel writes them over the host link in particle order;
+ * other host memory goes through a device staging buffer and copies.  Errors: STATE, CUDA. */
 int ann_get_state(ann_ctx *ctx, double *x, double *y, float *ux, float *uy, float *q11, float *q12,
                   float *drho, float *ax, float *ay, int dst_is_device);
 
@@ -271,7 +273,9 @@ int ann_get_state(ann_ctx *ctx, double *x, double *y, float *ux, float *uy, floa
  * the cell structure: each particle keeps its slot, and the next step re-sorts only if some
  * particle is half the candidate skin away from where the last re-sort put it, as after any step.
  * ann_get_state followed by ann_update_state of the same arrays leaves the trajectory
- * bit-identical.  Errors: INVALID_ARG, STATE (nothing loaded), NONFINITE (also drho <= -1), CUDA. */
+ * bit-identical.  Host arrays that are all page-locked and mapped are read by one kernel over the
+ * host link (no staging copy), as in ann_get_state.  The call returns after the arrays have been
+ * read.  Errors: INVALID_ARG, STATE (nothing loaded), NONFINITE (also drho <= -1), CUDA. */
 int ann_update_state(ann_ctx *ctx, const double *x, const double *y, const float *ux, const float *uy,
                      const float *q11, const float *q12, const float *drho, const float *ax, const float *ay,
                      int is_device);

@@ -587,19 +587,12 @@ __global__ void k_load_state(DevParams P, Bufs b, const double *x, const double 
     b.img[i] = make_int2(0, 0);
 }
 
-// ann_update_state: slot g of the state takes particle ids[g]'s values (ids: the particle at each
-// slot in the order of the last re-sort), so the cell structure and candidate lists stay valid.
-__global__ void k_update_state(DevParams P, Bufs b, const int *ids, const double *x, const double *y,
-                               const float *ux, const float *uy, const float *q11, const float *q12,
-                               const float *drho, const float *ax, const float *ay)
+// Slot g of the state takes particle id's values, checked and re-inserted into the box.
+__device__ __forceinline__ void store_slot(const DevParams &P, const Bufs &b, int g, int id, double xx, double yy,
+                                          float ux, float uy, float q11, float q12, float d, float a0, float a1)
 {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= P.n) return;
-    const int id = ids[g];
-    double xx = x[id], yy = y[id];
-    const float d = drho ? drho[id] : 0.f, a0 = ax ? ax[id] : 0.f, a1 = ay ? ay[id] : 0.f;
-    if (!(isfinite(xx) && isfinite(yy) && isfinite(ux[id]) && isfinite(uy[id]) && isfinite(q11[id]) &&
-          isfinite(q12[id]) && isfinite(d) && d > -1.f && isfinite(a0) && isfinite(a1))) {
+    if (!(isfinite(xx) && isfinite(yy) && isfinite(ux) && isfinite(uy) && isfinite(q11) && isfinite(q12) &&
+          isfinite(d) && d > -1.f && isfinite(a0) && isfinite(a1))) {
         atomicOr(b.err, EB_NONFINITE);
         xx = 0.0;
         yy = 0.0;
@@ -612,14 +605,86 @@ __global__ void k_update_state(DevParams P, Bufs b, const int *ids, const double
     if (yy >= P.L) yy -= P.L;
     b.sx[g] = xx + 0.0;
     b.sy[g] = yy + 0.0;
-    b.sux[g] = ux[id];
-    b.suy[g] = uy[id];
-    b.sq11[g] = q11[id];
-    b.sq12[g] = q12[id];
+    b.sux[g] = ux;
+    b.suy[g] = uy;
+    b.sq11[g] = q11;
+    b.sq12[g] = q12;
     b.sdr[g] = d;
     b.sax[g] = a0;
     b.say[g] = a1;
     b.sid[g] = id;
+}
+
+// ann_update_state from device arrays: slot g takes particle ids[g]'s values (ids: the particle at
+// each slot in the order of the last re-sort), so the cell structure and candidate lists stay valid.
+__global__ void k_update_state(DevParams P, Bufs b, const int *ids, const double *x, const double *y,
+                               const float *ux, const float *uy, const float *q11, const float *q12,
+                               const float *drho, const float *ax, const float *ay)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= P.n) return;
+    const int id = ids[g];
+    store_slot(P, b, g, id, x[id], y[id], ux[id], uy[id], q11[id], q12[id], drho ? drho[id] : 0.f,
+               ax ? ax[id] : 0.f, ay ? ay[id] : 0.f);
+}
+
+// inv[ids[g]] = g: the slot of each particle.
+__global__ void k_invert(const int *ids, int *inv, int n)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) inv[ids[g]] = g;
+}
+
+// ann_update_state from page-locked host arrays that the device maps: thread i reads particle i
+// (a warp reads whole consecutive lines over the host link) and writes its slot inv[i].
+__global__ void k_update_state_mapped(DevParams P, Bufs b, const int *inv, const double *x, const double *y,
+                                      const float *ux, const float *uy, const float *q11, const float *q12,
+                                      const float *drho, const float *ax, const float *ay)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    store_slot(P, b, inv[i], i, x[i], y[i], ux[i], uy[i], q11[i], q12[i], drho ? drho[i] : 0.f,
+               ax ? ax[i] : 0.f, ay ? ay[i] : 0.f);
+}
+
+// ann_get_state into page-locked host arrays that the device maps: particle i's values from its
+// slot inv[i], written in particle order (NULL destinations skipped).
+__global__ void k_get_state_mapped(Bufs b, int n, const int *inv, double *x, double *y, float *ux, float *uy,
+                                   float *q11, float *q12, float *drho, float *ax, float *ay)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int g = inv[i];
+    if (x) x[i] = b.sx[g];
+    if (y) y[i] = b.sy[g];
+    if (ux) ux[i] = b.sux[g];
+    if (uy) uy[i] = b.suy[g];
+    if (q11) q11[i] = b.sq11[g];
+    if (q12) q12[i] = b.sq12[g];
+    if (drho) drho[i] = b.sdr[g];
+    if (ax) ax[i] = b.sax[g];
+    if (ay) ay[i] = b.say[g];
+}
+
+// Device address of a page-locked host array that the device maps (nullptr if p is not one).
+void *mapped_host(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Device addresses of the non-null host arrays p[0..k) if every one is mapped (false otherwise).
+bool all_mapped(const void *const *p, void **d, int k)
+{
+    for (int j = 0; j < k; j++) {
+        d[j] = nullptr;
+        if (p[j] && !(d[j] = mapped_host(p[j]))) return false;
+    }
+    return true;
 }
 
 __global__ void k_deinterleave(const float *src, float *dst, int n, int stride, int comp)
@@ -844,7 +909,27 @@ int ann_update_state(ann_ctx *c, const double *x, const double *y, const float *
     if (!x || !y || !ux || !uy || !q11 || !q12) return fail(c, ANN_ERR_INVALID_ARG, "null input array");
     const size_t n = (size_t)c->P.n;
     const void *dev[9] = {x, y, ux, uy, q11, q12, drho, ax, ay};
+    // the particle at each slot of the last re-sort: M's order when M holds the present state (a
+    // search may have re-sorted into it), else S's
+    const int *ids = c->m_current ? c->b.mid : c->b.sid;
+    const unsigned nb = (unsigned)((n + 255) / 256);
     cudaError_t e = cudaSuccess;
+    void *hd[9];
+    if (!is_device && all_mapped(dev, hd, 9)) {
+        // page-locked host arrays: one kernel reads them over the host link, no staging copy
+        int *inv = static_cast<int *>(c->tmp);
+        k_invert<<<nb, 256, 0, c->stream>>>(ids, inv, (int)n);
+        k_update_state_mapped<<<nb, 256, 0, c->stream>>>(
+            c->P, c->b, inv, (const double *)hd[0], (const double *)hd[1], (const float *)hd[2], (const float *)hd[3],
+            (const float *)hd[4], (const float *)hd[5], (const float *)hd[6], (const float *)hd[7],
+            (const float *)hd[8]);
+        e = cudaGetLastError();
+        if (e) return cuda_fail(c, e, "ann_update_state");
+        c->s_sorted = c->m_current = false;
+        c->rec_valid = false;
+        c->grid_step = -1;
+        return device_status(c);
+    }
     if (!is_device) {
         unsigned char *t = static_cast<unsigned char *>(c->tmp);   // 44 of its >= 56 bytes per particle
         size_t off = 0;
@@ -858,10 +943,7 @@ int ann_update_state(ann_ctx *c, const double *x, const double *y, const float *
         }
         if (e) return cuda_fail(c, e, "ann_update_state copy");
     }
-    // the particle at each slot of the last re-sort: M's order when M holds the present state (a
-    // search may have re-sorted into it), else S's
-    const int *ids = c->m_current ? c->b.mid : c->b.sid;
-    k_update_state<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+    k_update_state<<<nb, 256, 0, c->stream>>>(
         c->P, c->b, ids, (const double *)dev[0], (const double *)dev[1], (const float *)dev[2], (const float *)dev[3],
         (const float *)dev[4], (const float *)dev[5], (const float *)dev[6], (const float *)dev[7],
         (const float *)dev[8]);
@@ -995,6 +1077,21 @@ int ann_get_state(ann_ctx *c, double *x, double *y, float *ux, float *uy, float 
         {b.sax, ax, 4}, {b.say, ay, 4}};
     const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     cudaError_t e = cudaSuccess;
+    const void *dst[9] = {x, y, ux, uy, q11, q12, drho, ax, ay};
+    void *hd[9];
+    if (!dst_is_device && all_mapped(dst, hd, 9)) {
+        // page-locked host arrays: one kernel gathers each particle's slot and writes them in
+        // particle order over the host link, no staging copy
+        const unsigned nb = (unsigned)((n + 255) / 256);
+        int *inv = reinterpret_cast<int *>(tmp);
+        k_invert<<<nb, 256, 0, c->stream>>>(b.sid, inv, (int)n);
+        k_get_state_mapped<<<nb, 256, 0, c->stream>>>(
+            b, (int)n, inv, (double *)hd[0], (double *)hd[1], (float *)hd[2], (float *)hd[3], (float *)hd[4],
+            (float *)hd[5], (float *)hd[6], (float *)hd[7], (float *)hd[8]);
+        e = cudaGetLastError();
+        if (!e) e = cudaStreamSynchronize(c->stream);
+        return e ? cuda_fail(c, e, "ann_get_state") : ANN_OK;
+    }
     size_t off = 0;
     for (const Part &p : parts) {
         unsigned char *stage = tmp + off;

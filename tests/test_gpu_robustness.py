@@ -450,8 +450,9 @@ def test_set_state_is_set_particles_in_native_precision(B):
 
 
 def test_update_state_round_trip_and_moved_particles(B, orc):
-    """ann_get_state -> ann_update_state of the same values between steps (host arrays and device
-    tensors) leaves the trajectory bit-identical to plain steps, with no extra re-sort.  A state
+    """ann_get_state -> ann_update_state of the same values between steps (pageable host arrays,
+    device tensors, and page-locked host arrays, which the kernels read and write over the host
+    link) leaves the trajectory bit-identical to plain steps, with no extra re-sort.  A state
     moved far from where the last re-sort put the particles makes the next step re-sort, and that
     step matches the oracle started from the moved state."""
     import torch
@@ -460,13 +461,18 @@ def test_update_state_round_trip_and_moved_particles(B, orc):
     p = params(64, c0_min=0.05)
     p["dt"] = stable_dt(p)
     a, b = GpuRun(B, p, ic), GpuRun(B, p, ic)
+    pinned = {f: torch.empty(b.n, dtype=torch.float64 if f in ("X", "Y") else torch.float32).pin_memory().numpy()
+              for f in B.FULL_STATE}
     try:
         a.step(12)
-        b.step(4)
-        for k in range(8):
-            st = B.ann_get_state(b.ctx, b.n)
-            if k % 2:
-                st = {f: torch.from_numpy(v).cuda() for f, v in st.items()}
+        b.step(3)
+        for k in range(9):
+            if k % 3 == 2:
+                st = B.ann_get_state(b.ctx, b.n, out=pinned)
+            else:
+                st = B.ann_get_state(b.ctx, b.n)
+                if k % 3 == 1:
+                    st = {f: torch.from_numpy(v).cuda() for f, v in st.items()}
             B.ann_update_state(b.ctx, st)
             b.step(1)
         sa, sb = B.ann_get_state(a.ctx, a.n), B.ann_get_state(b.ctx, b.n)
@@ -487,6 +493,57 @@ def test_update_state_round_trip_and_moved_particles(B, orc):
         want, _ = orc.step(oracle_params(orc, p, "cells"), st, 1, record=True)
         errs = compare_state(b.state(), want, moved["X"], moved["Y"])
         assert all(e <= 1e-5 for e in errs.values()), errs
+    finally:
+        a.close()
+        b.close()
+
+
+def test_state_transfer_through_page_locked_host_memory(B):
+    """ann_get_state into page-locked host arrays (one kernel writes them over the host link) gives
+    the bytes of the staged copy, with some destinations NULL and with a mix of page-locked and
+    pageable arrays (which takes the staged path); ann_update_state from page-locked arrays, with
+    DRHO, AX and AY left out, gives the state that the same pageable arrays give."""
+    import torch
+
+    def pin(v):
+        return torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy()
+
+    ic = random_velocity_ic(48, 23)
+    p = params(48, c0_min=0.05)
+    p["dt"] = stable_dt(p)
+    a, b = GpuRun(B, p, ic), GpuRun(B, p, ic)
+    try:
+        a.step(5)
+        b.step(5)
+        ref = B.ann_get_state(a.ctx, a.n)
+        full = B.ann_get_state(a.ctx, a.n, out={f: pin(np.zeros_like(v)) for f, v in ref.items()})
+        part = B.ann_get_state(a.ctx, a.n, out={f: pin(np.zeros_like(ref[f])) for f in ("Y", "UX", "Q12", "AY")})
+        mixed = {f: (pin(np.zeros_like(v)) if i % 2 else np.zeros_like(v)) for i, (f, v) in enumerate(ref.items())}
+        mixed = B.ann_get_state(a.ctx, a.n, out=mixed)
+        for f in B.FULL_STATE:
+            assert np.array_equal(full[f], ref[f]), f
+            assert np.array_equal(mixed[f], ref[f]), f
+        for f, v in part.items():
+            assert np.array_equal(v, ref[f]), f
+        # a new state (velocities halved, positions shifted by a tenth of a cell), DRHO/AX/AY absent
+        new = {"X": np.mod(ref["X"] + 0.002, 1.0), "Y": ref["Y"], "UX": 0.5 * ref["UX"], "UY": 0.5 * ref["UY"],
+               "Q11": ref["Q11"], "Q12": ref["Q12"]}
+        B.ann_update_state(a.ctx, {f: pin(v) for f, v in new.items()})
+        B.ann_update_state(b.ctx, new)
+        sa, sb = B.ann_get_state(a.ctx, a.n), B.ann_get_state(b.ctx, b.n)
+        for f in B.FULL_STATE:
+            assert np.array_equal(sa[f], sb[f]), f
+        assert np.all(sa["DRHO"] == 0.0) and np.all(sa["AX"] == 0.0)
+        a.step(3)
+        b.step(3)
+        sa, sb = B.ann_get_state(a.ctx, a.n), B.ann_get_state(b.ctx, b.n)
+        for f in B.FULL_STATE:
+            assert np.array_equal(sa[f], sb[f]), f
+        bad = {f: pin(v) for f, v in new.items()}
+        bad["UY"][3] = np.nan
+        with pytest.raises(B.AnnError) as e:
+            B.ann_update_state(a.ctx, bad)
+        assert e.value.status == -6
     finally:
         a.close()
         b.close()
