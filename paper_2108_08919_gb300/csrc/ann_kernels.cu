@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(PT) k_pass_a_resort(DevParams P, Bufs b)
             cnt = MAXV;
         }
         float sw = P.W0;
-        int cv = 0, nn = 0;
+        int cv = 0, nn = 0, nlow = 0;
         unsigned long long mask = 0ull;
         for (int k = 0; k < cnt; k++) {
             int j = my[k * PT];   // slot (the coarse scan stores slots)
@@ -498,17 +498,25 @@ __global__ void __launch_bounds__(PT) k_pass_a_resort(DevParams P, Bufs b)
                 mask |= (unsigned long long)in << cv;
             }
             my[cv * PT] = (uint16_t)(j << 4);   // byte offset of the slot
+            nlow += cand & (j < si);
             cv += cand;
         }
+        // The kept candidates are in ascending slot order; the list starts at the first slot after
+        // si and wraps around.  The threads of a warp hold consecutive slots, so at each step of
+        // their walks they load mostly distinct, consecutive slots, which spreads the staged loads
+        // of the pair passes over the shared-memory banks (ascending order: ~2x the bank conflicts).
+        auto at = [&](int k) { return (uint32_t)my[(k + nlow < cv ? k + nlow : k + nlow - cv) * PT]; };
         uint2 *out = b.vnbr + gi;
         for (int k = 0; k < cv; k += 4) {
-            uint32_t s0 = my[k * PT];
-            uint32_t s1 = (k + 1 < cv) ? my[(k + 1) * PT] : 0u;
-            uint32_t s2 = (k + 2 < cv) ? my[(k + 2) * PT] : 0u;
-            uint32_t s3 = (k + 3 < cv) ? my[(k + 3) * PT] : 0u;
+            uint32_t s0 = at(k);
+            uint32_t s1 = (k + 1 < cv) ? at(k + 1) : 0u;
+            uint32_t s2 = (k + 2 < cv) ? at(k + 2) : 0u;
+            uint32_t s3 = (k + 3 < cv) ? at(k + 3) : 0u;
             *out = make_uint2(s0 | (s1 << 16), s2 | (s3 << 16));
             out += P.n;
         }
+        if (nlow > 0 && nlow < cv)   // the mask follows the list: bit k is candidate k
+            mask = (mask >> nlow) | ((mask & ((1ull << nlow) - 1ull)) << (cv - nlow));
         b.vcnt[gi] = cv;
         if (!FROM_REF) {
             b.nnbr[gi] = nn;
