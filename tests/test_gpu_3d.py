@@ -113,11 +113,40 @@ def test_steps_match_the_oracle(B, O, kind):
     if kind == "fast":
         # u is FP32 and carries the drift: the velocity differences that feed grad u, a, the Q rate,
         # the density and the pressure keep log2(|U| / |u - U|) ~ 7 fewer bits than in the other
-        # cases, so those fields get 2^7 x the bound
+        # cases.  Their bound is the floor that FP32 storage alone sets: the oracle's own FP64
+        # steps from a state rounded as the library stores it after every step, against the FP64
+        # run.  The FP32 path adds its own roundings of the same size (the pair terms), so it stays
+        # within a few times that floor; the bound is 3 times it (or 2e-5 where that is larger).
+        floor = _storage_floor(O, ic, p, steps, want, rec)
         loose = {"gradu", "a", "qrate", "rho-1", "p"}
-        assert max(v for k, v in errs.items() if k in loose) < 2e-5 * 2 ** 7, errs
+        print(kind, "storage floor", {k: f"{floor[k]:.2e}" for k in loose},
+              "ratio", {k: f"{errs[k] / floor[k]:.2f}" for k in loose})
+        for k in loose:
+            assert errs[k] <= max(2e-5, 3.0 * floor[k]), (k, errs[k], floor[k])
         errs = {k: v for k, v in errs.items() if k not in loose}
     assert max(errs.values()) < 2e-5, errs
+
+
+def _round32_3d(st):
+    """The oracle's state rounded as the library stores it: positions FP64, u and Q FP32, the
+    density as its FP32 deviation from 1."""
+    r = dict(st)
+    r["u"] = np.asarray(st["u"], np.float32).astype(np.float64)
+    r["q"] = np.asarray(st["q"], np.float32).astype(np.float64)
+    r["rho"] = 1.0 + np.asarray(np.asarray(st["rho"]) - 1.0, np.float32).astype(np.float64)
+    return r
+
+
+def _storage_floor(O, ic, p, steps, want, rec):
+    """Relative change of the oracle's fields after `steps` FP64 steps when the state is rounded to
+    the library's storage precision before every step."""
+    P = O.make_params(**p)
+    st = {"x": ic["x"], "y": ic["y"], "z": ic["z"], "u": ic["u"], "q": ic["q"], "rho": ic["rho"]}
+    for k in range(steps):
+        st, rec32 = O.step(P, _round32_3d(st), 1, record=True)
+    return {"gradu": relerr(rec32["gradu"], rec["gradu"]), "a": relerr(st["a"], want["a"]),
+            "qrate": relerr(rec32["qrate"], rec["qrate"]), "p": relerr(rec32["p"], rec["p"]),
+            "rho-1": relerr(st["rho"] - 1.0, want["rho"] - 1.0)}
 
 
 def test_full_size_two_steps(B, O):
