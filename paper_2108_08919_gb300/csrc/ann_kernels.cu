@@ -979,22 +979,9 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
         float4 eci = (CONS && EL) ? se[si] : make_float4(0.f, 0.f, 0.f, 0.f);
         int c = b.nnbr[gi];
         unsigned long long em = b.emask[gi];   // bit k: candidate k is a neighbour
-        // per-particle inputs of the epilogue, loaded ahead of the neighbour loop
-        float dhat = b.dhat[gi], kri = b.kr[gi], swi = b.sumW[gi];
-        float B11 = 0.f, B12 = 0.f, B22 = 0.f, dvx = 0.f, dvy = 0.f;
-        if (!CONS) {
-            B11 = b.B11[gi];
-            B12 = b.B12[gi];
-            B22 = b.B22[gi];
-            dvx = b.divx[gi];
-            dvy = b.divy[gi];
-        }
-        double mxi = b.mx[gi], myi = b.my[gi];
-        float elx = 0.f, ely = 0.f;
-        if (EL && !CONS) {
-            elx = b.delx[gi];
-            ely = b.dely[gi];
-        }
+        // the epilogue's other per-particle inputs are loaded after the neighbour loop: held across
+        // it they would take 11 registers (and spill), while other warps hide their latency there
+        float dhat = b.dhat[gi];
         float rho = P.rho0 * (1.f + dhat);
         // paper mode: pressure and viscous sums share grad_i W, so they accumulate as one vector
         //   w = sum_j V_j F [ -rho_i (p_i/rho_i^2 + p_j/rho_j^2) + kv (u_ij . d) / r^2 ] d,
@@ -1042,6 +1029,21 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
                 sd = fma2(d, bc(rinv2 * kp.rinv), sd);
             }
         });
+        float kri = b.kr[gi], swi = b.sumW[gi];
+        float B11 = 0.f, B12 = 0.f, B22 = 0.f, dvx = 0.f, dvy = 0.f;
+        if (!CONS) {
+            B11 = b.B11[gi];
+            B12 = b.B12[gi];
+            B22 = b.B22[gi];
+            dvx = b.divx[gi];
+            dvy = b.divy[gi];
+        }
+        const double mxi = b.mx[gi], myi = b.my[gi];
+        float elx = 0.f, ely = 0.f;
+        if (EL && !CONS) {
+            elx = b.delx[gi];
+            ely = b.dely[gi];
+        }
         float ax, ay;
         if (CONS) {
             ax = P.mass * w.x;
