@@ -846,15 +846,17 @@ class _SgRolloutFailed(Exception):
     pass
 
 
-def surrogate_developed_bench(B, nx=256, zeta=0.1, K=0.02, develop=100000, train_pairs=40, heldout_pairs=6,
-                              iters=1500, cycles=40, every=5, max_err=0.05, ys_floor=0.05):
+def surrogate_developed_bench(B, nx=256, zeta=0.1, K=0.02, develop=100000, train_seeds=(21, 23, 25, 27, 29, 31),
+                              pairs_per_seed=8, heldout_seed=22, heldout_pairs=6, iters=1500, cycles=40, every=5,
+                              max_err=0.05, ys_floor=0.05):
     """The surrogate in the developed active flow of the long runs: nx^2, the scaled viscosity
-    eta = 0.03 and dt = 1e-4 (paper_2108_08919_gb300.longrun), zeta = 0.1, K = 0.02, run `develop`
-    plain steps from a random director (t = 10: the activity-built order and flow of the long-run
-    tables).  A network initialised afresh is trained on `train_pairs` 8-step pairs of seed 21's
-    developed trajectory, its increments are held out on seed 22's, and a guarded rollout
+    eta = 0.03 and dt = 1e-4 (paper_2108_08919_gb300.longrun), zeta = 0.1, K = 0.02.  One ensemble
+    runs `develop` plain steps from a random director for every training seed and the held-out
+    seed (t = 10: the activity-built order and flow of the long-run tables).  The network (output
+    layer initialised to zero) is trained on `pairs_per_seed` 8-step pairs of each training seed's
+    developed trajectory, its increments are held out on another seed's, and a guarded rollout
     (ann_surrogate_advance, a plain-SPH check every `every` cycles, fallback past max_err) runs
-    from seed 22's developed state beside plain SPH: spectrum slope, defect density, increments."""
+    from the held-out developed state beside plain SPH: spectrum slope, defect density, increments."""
     import numpy as np
 
     import sph_inputs as si
@@ -863,15 +865,9 @@ def surrogate_developed_bench(B, nx=256, zeta=0.1, K=0.02, develop=100000, train
     t_all = time.perf_counter()
     p = longrun.member_params(nx, zeta, K)
     n = nx * nx
+    seeds = list(train_seeds) + [heldout_seed]
     out = {"resolution": nx, "zeta": zeta, "K": K, "eta": p.eta, "dt": p.dt, "develop_steps": develop,
            "max_err": max_err}
-
-    def developed(ctx, seed):
-        ic = si.jittered_lattice(nx, seed=seed)
-        B.ann_set_particles(ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"], ic["rho"])
-        B.ann_step(ctx, develop)
-        B.ann_set_record(ctx, 1)
-        B.ann_step(ctx, 1)
 
     def snaps(ctx, count):
         got = []
@@ -882,10 +878,33 @@ def surrogate_developed_bench(B, nx=256, zeta=0.1, K=0.02, develop=100000, train
 
     ca, cb, shadow = B.ann_create(p), B.ann_create(p), B.ann_create(p)
     sg = B.ann_surrogate_create(n)
+    ens = B.ann_ensemble_create([p] * len(seeds))
     try:
-        developed(ca, 21)
-        developed(cb, 22)
-        tr, te = _sg_pairs(snaps(ca, train_pairs)), _sg_pairs(snaps(cb, heldout_pairs))
+        for k, seed in enumerate(seeds):
+            ic = si.jittered_lattice(nx, seed=seed)
+            B.ann_set_particles(B.ann_ensemble_member(ens, k), ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"],
+                                ic["q12"], ic["rho"])
+        t0 = time.perf_counter()
+        try:
+            B.ann_ensemble_step(ens, develop)
+        except B.AnnError as e:   # a failed member keeps its last completed state; the others ran on
+            out["develop_error"] = str(e)
+        out["develop_seconds"] = time.perf_counter() - t0
+
+        def take(k, ctx):
+            # continue member k's developed trajectory on ctx, with the last acceleration, recorded
+            st = B.ann_get_state(B.ann_ensemble_member(ens, k), n)
+            B.ann_set_state(ctx, st)
+            B.ann_update_state(ctx, st)
+            B.ann_set_record(ctx, 1)
+            B.ann_step(ctx, 1)
+
+        tr = []
+        for k in range(len(train_seeds)):
+            take(k, ca)
+            tr += _sg_pairs(snaps(ca, pairs_per_seed))
+        take(len(train_seeds), cb)
+        te = _sg_pairs(snaps(cb, heldout_pairs))
         out["vrms_developed"] = float(np.sqrt(2.0 * B.ann_get_diagnostics(cb)["kinetic_energy"]))
         B.ann_surrogate_init(sg, 7)
         us = float(np.sqrt(np.mean(np.concatenate([np.r_[a["UX"], a["UY"]] for a, _ in tr]) ** 2)))
@@ -896,8 +915,8 @@ def surrogate_developed_bench(B, nx=256, zeta=0.1, K=0.02, develop=100000, train
         t0 = time.perf_counter()
         l0, l1 = _sg_train(B, sg, ca, n, tr, res, ys, iters, 1e-3)
         e_net, e_eul, e_q, e_u = _sg_eval(B, sg, ca, n, te, ys, parts=True)
-        out["train"] = {"pairs": len(tr), "seed": 21, "heldout_pairs": len(te), "heldout_seed": 22, "iters": iters,
-                        "ys_floor": ys_floor,
+        out["train"] = {"pairs": len(tr), "seeds": list(train_seeds), "heldout_pairs": len(te),
+                        "heldout_seed": heldout_seed, "iters": iters, "ys_floor": ys_floor,
                         "loss_first": l0, "loss_last": l1, "seconds": time.perf_counter() - t0,
                         "heldout_err": e_net, "euler_err": e_eul, "heldout_q_err_net_euler": e_q,
                         "heldout_u_err_net_euler": e_u}
@@ -923,6 +942,14 @@ def surrogate_developed_bench(B, nx=256, zeta=0.1, K=0.02, develop=100000, train
         p_counts, _ = B.ann_defects(ca, nx)
         p_E = B.ann_energy_spectrum(ca, nx)
         p_f = {f: B.ann_get_field(ca, f, n).astype(np.float64) for f in ("UX", "UY", "Q11", "Q12")}
+        # the same cycles without the guard's checks (recorded plain step + jump): what the checks cost
+        load(cb)
+        t1 = time.perf_counter()
+        for _ in range(cycles):
+            B.ann_step(cb, 1)
+            B.ann_surrogate_jump(sg, cb, None)
+        B.ann_get_diagnostics(cb)
+        t_u = time.perf_counter() - t1
         w = 2 * np.pi * np.arange(s_E.size)
         sl_s, sl_p = B.ann_spectrum_slope(s_E, 1.0, w[3], w[20]), B.ann_spectrum_slope(p_E, 1.0, w[3], w[20])
         ds, dp = float(s_counts[0] + s_counts[1]), float(p_counts[0] + p_counts[1])
@@ -934,6 +961,7 @@ def surrogate_developed_bench(B, nx=256, zeta=0.1, K=0.02, develop=100000, train
 
         out["rollout"] = {"cycles": cycles, "check_every": every, "guard": guard,
                           "guarded_ms": 1e3 * t_g, "plain_ms": 1e3 * t_p, "speedup": t_p / t_g,
+                          "unguarded_ms": 1e3 * t_u, "unguarded_speedup": t_p / t_u,
                           "defect_density": [ds, dp], "defect_density_rel_err": abs(ds - dp) / max(dp, 1.0),
                           "spectrum_slope": [sl_s, sl_p], "spectrum_slope_abs_err": abs(sl_s - sl_p),
                           "q_increment_rel_err": rel((s_f["Q11"], s_f["Q12"]), (p_f["Q11"], p_f["Q12"]),
@@ -942,6 +970,7 @@ def surrogate_developed_bench(B, nx=256, zeta=0.1, K=0.02, develop=100000, train
                           "slope_range": "w in [2 pi 3, 2 pi 20]", "grid": nx}
     finally:
         B.ann_surrogate_destroy(sg)
+        B.ann_ensemble_destroy(ens)
         for c in (ca, cb, shadow):
             B.ann_destroy(c)
     out["seconds"] = time.perf_counter() - t_all

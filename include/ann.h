@@ -440,8 +440,9 @@ void ann_surrogate_destroy(ann_surrogate *sg);
 int ann_surrogate_set_params(ann_surrogate *sg, const float *params);
 int ann_surrogate_get_params(ann_surrogate *sg, float *params);
 
-/* Seeded He initialisation: weights N(0, 2 / fan_in) (output layer half that standard deviation),
- * biases 0, normals by Box-Muller from a counter-based SplitMix64 stream; resets the optimiser. */
+/* Seeded He initialisation of the hidden layers: weights N(0, 2 / fan_in), normals by Box-Muller
+ * from a counter-based SplitMix64 stream; biases and the output layer (Wo, bo) 0, so that the
+ * untrained network predicts the explicit increment.  Resets the optimiser. */
 int ann_surrogate_init(ann_surrogate *sg, uint64_t seed);
 
 /* Velocity scale us of the inputs, increment scales ys_q, ys_u of the outputs (all > 0), and the

@@ -788,8 +788,11 @@ int ann_surrogate_init(ann_surrogate *S, uint64_t seed)
     };
     std::vector<float> p(NPARAM, 0.f);
     struct M { int off, rows, cols; double gain; };
+    // the output layer starts at zero: an untrained network predicts the explicit increment, and
+    // training moves it only as far as the data pull (a random output layer starts the prediction
+    // tens of percent off, and in the developed flow it never came back on held-out trajectories)
     const M ms[] = {{O_W1, WIDTH, 2 * F0, 1.0}, {O_P1, MSG, WIDTH, 1.0}, {O_W2, WIDTH, WIDTH + MSG, 1.0},
-                    {O_P2, MSG, WIDTH, 1.0}, {O_W3, WIDTH, WIDTH + MSG, 1.0}, {O_WO, NOUT, WIDTH, 0.5}};
+                    {O_P2, MSG, WIDTH, 1.0}, {O_W3, WIDTH, WIDTH + MSG, 1.0}};
     for (const M &m : ms) {
         double sd = m.gain * std::sqrt(2.0 / m.cols);
         for (int k = 0; k < m.rows * m.cols; k++) {

@@ -289,6 +289,12 @@ def test_jump_applies_the_public_forward(B):
         B.ann_step(ctx, 2)
         s0 = {f: B.ann_get_field(ctx, f, n).astype(np.float64) for f in ("Q11", "Q12", "UX", "UY")}
         B.ann_surrogate_init(sg, 5)
+        w = B.ann_surrogate_get_params(sg)
+        out = w[-(4 * 128 + 4):]
+        assert not out.any()   # the output layer starts at zero: the untrained jump is the explicit one
+        out[:] = 0.05 * np.cos(np.arange(out.size) * 0.7)   # a nonzero correction to apply
+        w[-(4 * 128 + 4):] = out
+        B.ann_surrogate_set_params(sg, w)
         ysq, ysu = 1e-3, 1e-5
         B.ann_surrogate_set_scales(sg, 0.01, ysq, ysu, k)
         B.ann_surrogate_load(sg, ctx, None)
@@ -303,6 +309,7 @@ def test_jump_applies_the_public_forward(B):
         B.ann_destroy(ctx)
     ulp = 2.0 ** -23 * max(np.abs(s1["Q11"]).max(), np.abs(s1["Q12"]).max())
     corr = np.stack([s1["Q11"] - s0["Q11"] - inc[:, 0], s1["Q12"] - s0["Q12"] - inc[:, 1]], axis=1)
+    assert np.abs(y[:, :2]).max() > 0.01
     assert np.abs(corr - ysq * y[:, :2]).max() < 4 * ulp
     assert np.abs(s1["UX"] - s0["UX"] - inc[:, 2]).max() < 1e-7 and np.abs(s1["UY"] - s0["UY"] - inc[:, 3]).max() < 1e-7
 
