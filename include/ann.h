@@ -62,7 +62,7 @@ extern "C" {
 #define ANN_ERR_CFL_VIOLATION (-13)  /* dt_mode ANN_DT_CHECK: the step's dt exceeded a stability limit */
 
 /* Limits of the device kernels. */
-#define ANN_MAX_NEIGHBORS 64         /* neighbours per particle */
+#define ANN_MAX_NEIGHBORS 128        /* neighbours (and candidates within 3h (1 + skin)) per particle */
 #define ANN_MAX_PER_CELL 64          /* particles per cell */
 
 /* momentum_mode */

@@ -114,7 +114,7 @@ int64_t device_bytes(const ann_params &p)
     int64_t per = 2 * 8 + 7 * 4 + 4 + 16      // S
                   + 2 * 8 + 5 * 4 + 16 + 4    // M
                   + 3 * 4                     // key, rank, perm
-                  + 4 + 8                     // neighbour counts, neighbour masks
+                  + 4                         // neighbour counts (the neighbour bits sit in the lists)
                   + (MAXV / 2) * 4 + 4 + 16 + 4   // candidate lists, counts, split at re-sort, cell
                   + 11 * 4                    // intermediates
                   + 10 * 4                    // recording
@@ -298,7 +298,7 @@ cudaError_t alloc_all(ann_ctx *c)
     A_(say, n); A_(sid, n); A_(sxi, n);
     A_(mx, n); A_(my, n); A_(mux, n); A_(muy, n); A_(mq11, n); A_(mq12, n); A_(mdr, n); A_(xi, n); A_(mid, n);
     A_(cell_count, ncell + 1); A_(cell_start, ncell + 1); A_(key, n); A_(rank, n); A_(perm, n);
-    A_(nnbr, n); A_(emask, n);
+    A_(nnbr, n);
     A_(vnbr, n * (MAXV / 4)); A_(vcnt, n); A_(xi_ref, n); A_(mkey, n); A_(rebuild, 1); A_(resorts, 1);
     A_(sumW, n); A_(V, n); A_(B11, n); A_(B12, n); A_(B22, n); A_(kr, n); A_(dh, n); A_(dhat, n);
     A_(p, n); A_(divx, n); A_(divy, n);

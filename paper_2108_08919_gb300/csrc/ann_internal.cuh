@@ -26,14 +26,15 @@ constexpr int TILE = 4;
 constexpr int HALO = TILE + 2;
 constexpr int NHC = HALO * HALO;      // halo cells per tile
 constexpr int HCAP = 1024;            // halo particles a tile may stage
-constexpr int MAXN = 64;              // neighbours per particle (ANN_MAX_NEIGHBORS)
+constexpr int MAXN = 128;             // neighbours per particle (ANN_MAX_NEIGHBORS)
+constexpr int MAXN2H = 64;            // neighbours closer than 2h kept in the surrogate's graph
 constexpr int MAXC = 64;              // particles per cell (ANN_MAX_PER_CELL)
 constexpr int PT = 256;               // threads per pair-pass block
 constexpr int NKERNELS = 10;
 // Candidate ("Verlet") lists hold every pair within 3h (1 + SKIN) at the last re-sort; they stay
 // valid until some particle has moved SKIN/2 * 3h.  Cells are at least 3h (1 + SKIN) wide.
 constexpr double SKIN = 0.02;
-constexpr int MAXV = 64;              // candidates per particle
+constexpr int MAXV = 128;             // candidates per particle (two 64-bit neighbour masks)
 constexpr int SCAN_CHUNK = 4096;      // cells per block of the cell-count scan
 
 // Sticky device error bits.
@@ -106,7 +107,6 @@ struct Bufs {
     int *mid;
     uint32_t *cell_count, *cell_start, *key, *rank, *perm;
     int *nnbr;          // neighbours per particle (exact support test)
-    unsigned long long *emask;   // bit k set: candidate k is a neighbour
     uint2 *vnbr;        // candidate lists: 16-bit slot byte offsets, four per 64-bit word, word m of particle g at [m n + g]
     int *vcnt;
     uint32_t *rebuild;  // non-zero: this step re-sorts and rebuilds the candidate lists
@@ -202,8 +202,9 @@ cudaError_t enqueue_mixing(const DevParams &P, const Bufs &b, const unsigned cha
 // support (3h) the SPH means of (ux, uy, Q11, Q12) and of the recorded acceleration, and from them
 // the network's input rows.
 struct GraphOut {
-    int *nbr;               // MAXN x n neighbour sorted indices (2h)
-    float *W;               // MAXN x n kernel values W(|x_i - x_j|)
+    int *nbr;               // MAXN2H x n neighbour sorted indices (2h)
+    float *W;               // MAXN2H x n kernel values W(|x_i - x_j|)
+    unsigned *overflow;     // set when a particle has more than MAXN2H neighbours closer than 2h
     int *cnt2;              // n: neighbours closer than 2h
     float *S2;              // n: W(0) + sum_j W over them
     double *x, *y;          // n: positions

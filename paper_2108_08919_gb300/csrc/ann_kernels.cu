@@ -432,6 +432,13 @@ __device__ __forceinline__ bool in_support(float r2, const DevParams &P, const B
 // are rebuilt (used after a checkpoint is loaded).
 // ---------------------------------------------------------------------------------------------
 
+// Candidate lists hold the byte offset 16 * slot of each candidate's 16-byte staging slot, two
+// 16-bit entries per 32-bit half of a 64-bit word; the mask keeps every offset inside the HCAP
+// staged slots.  Bit 0 of an entry (free: offsets are multiples of 16) is the candidate's neighbour
+// bit of the present step (within 3h by the exact test), set by pass A; bits 1..3 are zero.
+constexpr uint32_t SLOT_OFF_MASK = (HCAP - 1) << 4;
+static_assert(((HCAP - 1) << 4) <= 0xffff, "slot offsets must fit 16 bits");
+
 constexpr int SMEM_A = HCAP * (16 + 4 + 1) + MAXV * PT * 2;
 
 template <bool FROM_REF>
@@ -485,19 +492,19 @@ __global__ void __launch_bounds__(PT) k_pass_a_resort(DevParams P, Bufs b)
         }
         float sw = P.W0;
         int cv = 0, nn = 0, nlow = 0;
-        unsigned long long mask = 0ull;
         for (int k = 0; k < cnt; k++) {
             int j = my[k * PT];   // slot (the coarse scan stores slots)
             float2 d = pair_d(pi, pos[j]);
             float r2 = len2(d);
             bool cand = r2 < P.R2v;
+            bool in = false;
             if (!FROM_REF && cand) {
                 sw += kernel_w<true>(r2, P);
-                bool in = in_support(r2, P, b, gi, sg[j]);
+                in = in_support(r2, P, b, gi, sg[j]);
                 nn += in;
-                mask |= (unsigned long long)in << cv;
             }
-            my[cv * PT] = (uint16_t)(j << 4);   // byte offset of the slot
+            // byte offset of the slot; bit 0 (free: offsets are multiples of 16) carries the support bit
+            my[cv * PT] = (uint16_t)((j << 4) | (int)in);
             nlow += cand & (j < si);
             cv += cand;
         }
@@ -515,12 +522,9 @@ __global__ void __launch_bounds__(PT) k_pass_a_resort(DevParams P, Bufs b)
             *out = make_uint2(s0 | (s1 << 16), s2 | (s3 << 16));
             out += P.n;
         }
-        if (nlow > 0 && nlow < cv)   // the mask follows the list: bit k is candidate k
-            mask = (mask >> nlow) | ((mask & ((1ull << nlow) - 1ull)) << (cv - nlow));
         b.vcnt[gi] = cv;
         if (!FROM_REF) {
             b.nnbr[gi] = nn;
-            b.emask[gi] = mask;
             b.sumW[gi] = sw;
             b.V[gi] = 1.0f / sw;
             b.xi_ref[gi] = b.xi[gi];   // the split positions this re-sort used
@@ -580,17 +584,12 @@ __global__ void __launch_bounds__(PT) k_pass_a_resort(DevParams P, Bufs b)
 #define BOUNDS_D __launch_bounds__(PT)
 #endif
 
-// Candidate lists hold the byte offset 16 * slot of each candidate's 16-byte staging slot, two
-// 16-bit entries per word; the mask keeps every offset inside the HCAP staged slots.
-constexpr uint32_t SLOT_OFF_MASK = (HCAP - 1) << 4;
-static_assert(((HCAP - 1) << 4) <= 0xffff, "slot offsets must fit 16 bits");
-
 // Visit the candidates of particle gi (c of them, four per 64-bit list word) in order, keeping the
 // next PF words in flight while the current ones are processed: fn(byte offset of the slot,
-// candidate index, bit), bit = the candidate's bit of `em` (nonzero iff set; 0 when em = 0).
+// candidate index, bit), bit = the entry's neighbour bit (nonzero iff the candidate is a neighbour).
 // Word m (candidates 4m .. 4m + 3) is loaded only when 4m < c.
 template <int PF, typename Fn>
-__device__ __forceinline__ void for_each_slot(const uint2 *list, int n, int gi, int c, unsigned long long em, Fn &&fn)
+__device__ __forceinline__ void for_each_slot(const uint2 *list, int n, int gi, int c, Fn &&fn)
 {
     static_assert(PF >= 1 && PF <= 3, "prefetch distance");
     const uint2 *p = list + gi;
@@ -605,25 +604,24 @@ __device__ __forceinline__ void for_each_slot(const uint2 *list, int n, int gi, 
         for (int m = 0; m < PF; m++) r[m] = r[m + 1];
         r[PF] = (k + 4 * (PF + 1) < c) ? __ldg(p) : make_uint2(0u, 0u);   // word k/4 + PF + 1
         p += n;
-        unsigned b4 = (unsigned)em;
-        em >>= 4;
-        fn((int)(w.x & SLOT_OFF_MASK), k, b4 & 1u);
-        fn((int)((w.x >> 16) & SLOT_OFF_MASK), k + 1, b4 & 2u);
-        fn((int)(w.y & SLOT_OFF_MASK), k + 2, b4 & 4u);
-        fn((int)((w.y >> 16) & SLOT_OFF_MASK), k + 3, b4 & 8u);
+        fn((int)(w.x & SLOT_OFF_MASK), k, w.x & 1u);
+        fn((int)((w.x >> 16) & SLOT_OFF_MASK), k + 1, w.x & 0x10000u);
+        fn((int)(w.y & SLOT_OFF_MASK), k + 2, w.y & 1u);
+        fn((int)((w.y >> 16) & SLOT_OFF_MASK), k + 3, w.y & 0x10000u);
     }
     unsigned long long w64 = ((unsigned long long)r[0].y << 32) | r[0].x;
-    for (int t = 0; k < c; k++, t++)   // the last 0 to 3 candidates
-        fn((int)((unsigned)(w64 >> (16 * t)) & SLOT_OFF_MASK), k, (unsigned)(em >> t) & 1u);
+    for (int t = 0; k < c; k++, t++) {   // the last 0 to 3 candidates
+        const unsigned e = (unsigned)(w64 >> (16 * t));
+        fn((int)(e & SLOT_OFF_MASK), k, e & 1u);
+    }
 }
 
 // Candidates of particle gi.  Beyond the support the clamped kernel gives W = F = 0 exactly, and
 // adding +0 or -0 leaves an FP32 sum unchanged, so sums over candidates equal sums over neighbours.
 template <int PF, typename Fn>
-__device__ __forceinline__ void for_each_candidate(const DevParams &P, const Bufs &b, int gi, unsigned long long em,
-                                                   Fn &&fn)
+__device__ __forceinline__ void for_each_candidate(const DevParams &P, const Bufs &b, int gi, Fn &&fn)
 {
-    for_each_slot<PF>(b.vnbr, P.n, gi, b.vcnt[gi], em, fn);
+    for_each_slot<PF>(b.vnbr, P.n, gi, b.vcnt[gi], fn);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -657,30 +655,55 @@ __global__ void BOUNDS_A k_pass_a_filter(DevParams P, Bufs b)
         float4 pi = pos[si];
         float sw = P.W0;
         int c = b.vcnt[gi];
-        // neighbour bits enter at the top of (mhi:mlo) and move down one place per candidate; the
-        // FP32 test decides outside the rounding band, and a candidate inside it (rare) is only
-        // noted here and decided in FP64 by the second walk below
-        uint32_t mlo = 0u, mhi = 0u;
+        // one walk over the list words, setting each candidate's neighbour bit by the FP32 test;
+        // a candidate inside the rounding band around (3h)^2 (rare) is only noted here and decided
+        // in FP64 by a second walk.  A word is stored only when a bit changed (a pair crossed 3h).
+        int nn = 0;
         bool band = false;
-        for_each_slot<ANN_PF_A>(b.vnbr, P.n, gi, c, 0ull, [&](int o, int, unsigned) {
-            float2 d = pair_d(pi, slot_at(pos, o));
-            float r2 = len2(d);
+        auto test = [&](uint32_t e) {
+            const uint32_t o = e & SLOT_OFF_MASK;
+            float r2 = len2(pair_d(pi, slot_at(pos, (int)o)));
             sw += kernel_w<true>(r2, P);
-            uint32_t in = r2 < P.R2lo;
+            const uint32_t in = r2 < P.R2lo;
             band |= (r2 >= P.R2lo) & (r2 < P.R2hi);
-            mlo = __funnelshift_r(mlo, mhi, 1);
-            mhi = __funnelshift_r(mhi, in, 1);
-        });
-        unsigned long long mask = ((unsigned long long)mhi << 32) | mlo;
-        mask = c > 0 ? mask >> (64 - c) : 0ull;   // candidate k at bit k
-        if (band) {
-            for_each_slot<1>(b.vnbr, P.n, gi, c, 0ull, [&](int o, int kc, unsigned) {
-                float r2 = len2(pair_d(pi, slot_at(pos, o)));
-                if (r2 >= P.R2lo && in_support(r2, P, b, gi, slot_at(sg, o))) mask |= 1ull << kc;
-            });
+            nn += (int)in;
+            return o | in;
+        };
+        uint2 *p = b.vnbr + gi;
+        uint2 nxt = c > 0 ? *p : make_uint2(0u, 0u);   // plain loads: this kernel writes the words
+        int k = 0;
+        for (; k + 3 < c; k += 4, p += P.n) {
+            const uint2 w = nxt;
+            if (k + 4 < c) nxt = p[P.n];   // the next word, in flight while this one is done
+            const uint32_t e0 = test(w.x & 0xffffu), e1 = test(w.x >> 16), e2 = test(w.y & 0xffffu),
+                           e3 = test(w.y >> 16);
+            const uint2 v = make_uint2(e0 | (e1 << 16), e2 | (e3 << 16));
+            if (v.x != w.x || v.y != w.y) *p = v;
         }
-        b.nnbr[gi] = __popcll(mask);
-        b.emask[gi] = mask;
+        if (k < c) {   // the last word, 1 to 3 candidates (the rest of it is zero)
+            const uint2 w = nxt;
+            uint32_t e[4] = {w.x & 0xffffu, w.x >> 16, w.y & 0xffffu, w.y >> 16};
+            for (int t = 0; t < c - k; t++) e[t] = test(e[t]);
+            const uint2 v = make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
+            if (v.x != w.x || v.y != w.y) *p = v;
+        }
+        if (band) {   // the band's candidates, decided in FP64 (the FP32 test left their bit 0)
+            uint2 *q = b.vnbr + gi;
+            for (int k0 = 0; k0 < c; k0 += 4, q += P.n) {
+                uint2 w = *q;
+                uint32_t e[4] = {w.x & 0xffffu, w.x >> 16, w.y & 0xffffu, w.y >> 16};
+                for (int t = 0; t < 4 && k0 + t < c; t++) {
+                    const int o = (int)(e[t] & SLOT_OFF_MASK);
+                    float r2 = len2(pair_d(pi, slot_at(pos, o)));
+                    if (r2 >= P.R2lo && in_support(r2, P, b, gi, slot_at(sg, o))) {
+                        e[t] |= 1u;
+                        nn++;
+                    }
+                }
+                *q = make_uint2(e[0] | (e[1] << 16), e[2] | (e[3] << 16));
+            }
+        }
+        b.nnbr[gi] = nn;
         b.sumW[gi] = sw;
         b.V[gi] = 1.0f / sw;
     }
@@ -730,7 +753,7 @@ __global__ void BOUNDS_B k_pass_b(DevParams P, Bufs b)
         float a22 = 0.f;
         float di = b.mdr[gi];   // loaded ahead of the neighbour loop
         const float2 ui = f2(bi.x, bi.y), qi = f2(bi.z, bi.w);
-        for_each_candidate<ANN_PF_B>(P, b, gi, 0ull, [&](int o, int, unsigned) {
+        for_each_candidate<ANN_PF_B>(P, b, gi, [&](int o, int, unsigned) {
             float4 bj = slot_at(sb, o);
             float2 d = pair_d(pi, slot_at(sp, o));
             KernelPowers kp = kernel_powers<true>(len2(d), P);
@@ -879,7 +902,7 @@ __global__ void BOUNDS_C k_pass_c(DevParams P, Bufs b)
         float2 gq1 = f2(0.f, 0.f), gq2 = f2(0.f, 0.f), ge1 = f2(0.f, 0.f), ge2 = f2(0.f, 0.f),
                ge3 = f2(0.f, 0.f);
         const float2 qi = f2(bi.z, bi.w);
-        for_each_candidate<ANN_PF_C>(P, b, gi, 0ull, [&](int o, int, unsigned) {
+        for_each_candidate<ANN_PF_C>(P, b, gi, [&](int o, int, unsigned) {
             float4 bj = slot_at(sb, o);
             float2 d = pair_d(pi, slot_at(sp, o));
             KernelPowers kp = kernel_powers<true>(len2(d), P);
@@ -978,7 +1001,6 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
         float2 ci = CONS ? sc[si] : make_float2(0.f, 0.f);
         float4 eci = (CONS && EL) ? se[si] : make_float4(0.f, 0.f, 0.f, 0.f);
         int c = b.nnbr[gi];
-        unsigned long long em = b.emask[gi];   // bit k: candidate k is a neighbour
         // the epilogue's other per-particle inputs are loaded after the neighbour loop: held across
         // it they would take 11 registers (and spill), while other warps hide their latency there
         float dhat = b.dhat[gi];
@@ -993,7 +1015,7 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
         const float2 ui = f2(bi.z, bi.w);
         float2 w = f2(0.f, 0.f), su = f2(0.f, 0.f), sd = f2(0.f, 0.f);
         float sr = 0.f;
-        for_each_candidate<ANN_PF_D>(P, b, gi, em, [&](int o, int, unsigned in) {
+        for_each_candidate<ANN_PF_D>(P, b, gi, [&](int o, int, unsigned in) {
             float4 bj = slot_at(sb, o);
             float2 d = pair_d(pi, slot_at(sp, o));
             float r2 = len2(d);
@@ -1180,8 +1202,7 @@ __global__ void __launch_bounds__(PT) k_export_nbrs(DevParams P, Bufs b, int *co
         int si = inner_slot(ts, T, q);
         int gi = sg[si];
         int k = 0;
-        unsigned long long emask = b.emask[gi];
-        for_each_candidate<1>(P, b, gi, emask, [&](int o, int, unsigned in) {
+        for_each_candidate<1>(P, b, gi, [&](int o, int, unsigned in) {
             int j = o >> 4;
             if (in && j < T.H && k < MAXN) {
                 cols[(size_t)k * P.n + gi] = b.mid[sg[j]];
@@ -1231,7 +1252,7 @@ __global__ void __launch_bounds__(PT) k_export_graph(DevParams P, Bufs b, GraphO
         float s2 = P.W0;
         float4 m4 = make_float4(P.W0 * ui.x, P.W0 * ui.y, P.W0 * ui.z, P.W0 * ui.w);
         float2 m2 = make_float2(P.W0 * ai.x, P.W0 * ai.y);
-        for_each_candidate<1>(P, b, gi, b.emask[gi], [&](int off, int, unsigned in) {
+        for_each_candidate<1>(P, b, gi, [&](int off, int, unsigned in) {
             int j = off >> 4;
             if (in && j < T.H) {
                 float r2 = len2(pair_d(pi, slot_at(pos, off)));
@@ -1244,11 +1265,15 @@ __global__ void __launch_bounds__(PT) k_export_graph(DevParams P, Bufs b, GraphO
                 m4.w = fmaf(w, uj.w, m4.w);
                 m2.x = fmaf(w, aj.x, m2.x);
                 m2.y = fmaf(w, aj.y, m2.y);
-                if (r2 < r2net && k < MAXN) {
-                    o.nbr[(size_t)k * P.n + gi] = sg[j];
-                    o.W[(size_t)k * P.n + gi] = w;
-                    s2 += w;
-                    k++;
+                if (r2 < r2net) {
+                    if (k < MAXN2H) {
+                        o.nbr[(size_t)k * P.n + gi] = sg[j];
+                        o.W[(size_t)k * P.n + gi] = w;
+                        s2 += w;
+                        k++;
+                    } else {
+                        *o.overflow = 1u;   // the graph cannot hold this particle's neighbours
+                    }
                 }
             }
         });
@@ -1310,7 +1335,7 @@ __global__ void __launch_bounds__(PT) k_export_increment(DevParams P, Bufs b, co
         float4 pi = pos[si];
         float2 ai = sa[si];
         float2 m2 = make_float2(P.W0 * ai.x, P.W0 * ai.y);
-        for_each_candidate<1>(P, b, gi, b.emask[gi], [&](int off, int, unsigned in) {
+        for_each_candidate<1>(P, b, gi, [&](int off, int, unsigned in) {
             int j = off >> 4;
             if (in && j < T.H) {
                 float w = kernel_w<true>(len2(pair_d(pi, slot_at(pos, off))), P);

@@ -394,6 +394,7 @@ struct ann_surrogate {
     float *bop;             // bo padded to 16
     double *loss;
     unsigned *err;
+    unsigned *ovf;   // the graph export found more than MAXN2H neighbours closer than 2h
     int adam_t = 0;
     // the guard of ann_surrogate_advance (allocated on its first call): three ID-ordered states --
     // before a checked cycle, after its jump, after its plain steps -- and the error partial sums
@@ -589,7 +590,7 @@ int ann_surrogate_create(int64_t n_max, ann_surrogate **out)
     size_t n = (size_t)n_max, K2 = WIDTH + MSG;
     cudaError_t e = cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking);
 #define SA_(p, c) if (!e) e = sg_alloc(S, S->p, c)
-    SA_(nbr, (size_t)MAXN * n); SA_(W, (size_t)MAXN * n); SA_(dr, n); SA_(cnt2, n); SA_(S2, n);
+    SA_(nbr, (size_t)MAXN2H * n); SA_(W, (size_t)MAXN2H * n); SA_(dr, n); SA_(cnt2, n); SA_(S2, n);
     SA_(agg1, 2 * n);
     SA_(x, n); SA_(y, n); SA_(u4, n); SA_(inc, 4 * n); SA_(ids, n); SA_(tend_id, 8 * n);
     SA_(io4, 4 * n);
@@ -601,7 +602,7 @@ int ann_surrogate_create(int64_t n_max, ann_surrogate **out)
     SA_(W1b, WIDTH * 2 * F0); SA_(P1b, MSG * WIDTH); SA_(W2b, WIDTH * K2); SA_(P2b, MSG * WIDTH);
     SA_(W3b, WIDTH * K2); SA_(Wob, NOUTP * WIDTH); SA_(W3T, K2 * WIDTH); SA_(W2T, K2 * WIDTH);
     SA_(P2T, WIDTH * MSG); SA_(P1T, WIDTH * MSG); SA_(WoT, WIDTH * NOUTP); SA_(bop, NOUTP);
-    SA_(loss, 1); SA_(err, 1);
+    SA_(loss, 1); SA_(err, 1); SA_(ovf, 1);
 #undef SA_
     if (!e) e = cudaStreamSynchronize(S->s);
     if (e) {
@@ -687,15 +688,20 @@ int ann_surrogate_load(ann_surrogate *S, ann_ctx *ctx, const float *tend)
     S->rho0 = v.P.rho0;
     S->gammaK = (double)v.P.Gamma * (double)v.P.K;
     const double kdt = S->k * S->dt;
-    GraphOut o{S->nbr, S->W, S->cnt2, S->S2, S->x, S->y, S->u4, S->dr, S->ids, S->agg1, S->tend_id, S->X0,
+    GraphOut o{S->nbr, S->W, S->ovf, S->cnt2, S->S2, S->x, S->y, S->u4, S->dr, S->ids, S->agg1, S->tend_id, S->X0,
                (float)(1.0 / S->us),
                {(float)(kdt / S->ysu), (float)(kdt / S->ysq), (float)(S->gammaK * kdt / S->ysq), (float)kdt}};
     // the export forms the support means of (u, Q) and a and the network's input rows; its second
     // walk gives the explicit increment k dt (m11, m12, agg(agg(a)))
     cudaError_t e = cudaStreamSynchronize(v.stream);
+    if (!e) e = cudaMemsetAsync(S->ovf, 0, sizeof(unsigned), S->s);
     if (!e) e = enqueue_export_graph(v.P, v.b, o, (float)kdt, S->inc, S->s);
+    unsigned ovf = 0u;
+    if (!e) e = cudaMemcpyAsync(&ovf, S->ovf, sizeof ovf, cudaMemcpyDeviceToHost, S->s);
     if (!e) e = cudaStreamSynchronize(S->s);
     if (e) return scuda(S, e, "ann_surrogate_load");
+    if (ovf) return sfail(S, ANN_ERR_NBR_OVERFLOW, "ann_surrogate_load: a particle has more neighbours closer than 2h "
+                                                   "than the network's graph holds (64)");
     S->loaded = true;
     return ANN_OK;
 }

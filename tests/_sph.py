@@ -181,3 +181,15 @@ def compare_state_max(gpu, orc_state, x0, y0, rho0=1.0, L=1.0):
         "a": maxerr_group([gpu["ax"], gpu["ay"]], [orc_state["ax"], orc_state["ay"]]),
         "drho": maxerr_group([gpu["drho"]], [orc_state["rho"] / rho0 - 1.0]),
     }
+
+
+def cluster_ic(nx, seed, radius, factor, u_scale=1e-3):
+    """A jittered lattice with the particles of the disk |x - (1/2, 1/2)| < radius pulled towards
+    its centre by `factor` (density 1/factor^2 there, an empty ring around it): a dense cluster
+    whose particles have more neighbours than the lattice's 44."""
+    ic = random_velocity_ic(nx, seed, u_scale=u_scale)
+    dx, dy = ic["x"] - 0.5, ic["y"] - 0.5
+    inside = np.hypot(dx, dy) < radius
+    ic["x"] = np.where(inside, 0.5 + factor * dx, ic["x"])
+    ic["y"] = np.where(inside, 0.5 + factor * dy, ic["y"])
+    return ic

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import sph_inputs as si
-from _sph import (GpuRun, compare_state, compare_state_max, oracle_params, oracle_state, params,
+from _sph import (GpuRun, cluster_ic, compare_state, compare_state_max, oracle_params, oracle_state, params,
                   random_velocity_ic, relerr, relerr_group, smooth_ic, stable_dt)
 
 pytestmark = pytest.mark.gpu
@@ -59,11 +59,13 @@ def _nbr_case(name):
     if name == "lattice256":
         ic = si.jittered_lattice(256, seed=1)
         return ic, 1.3 / 256
+    if name == "cluster":          # a dense disk: up to 112 candidates, 82 particles above 64
+        return cluster_ic(64, 3, 0.1, 0.65), 1.3 / 64
     raise KeyError(name)
 
 
 @pytest.mark.parametrize("case", ["lattice64", "ragged45", "random3000", "three_cells", "faces",
-                                  "lattice256"])
+                                  "lattice256", "cluster"])
 def test_neighbor_lists_bit_exact(B, orc, case):
     ic, h = _nbr_case(case)
     n = len(ic["x"])

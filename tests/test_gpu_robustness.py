@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import sph_inputs as si
-from _sph import (GpuRun, compare_state, gpu_params, oracle_params, oracle_state, params,
+from _sph import (GpuRun, cluster_ic, compare_state, gpu_params, oracle_params, oracle_state, params,
                   random_velocity_ic, stable_dt)
 
 pytestmark = pytest.mark.gpu
@@ -104,6 +104,46 @@ def test_overfull_cell_is_reported_not_faulted(B):
         assert B.ann_get_diagnostics(ctx)["error_bits"] & 1
         # the context stays usable: a fresh load clears the sticky bits
         B.ann_set_particles(ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"])
+        B.ann_step(ctx, 1)
+    finally:
+        B.ann_destroy(ctx)
+
+
+def test_dense_cluster_beyond_64_candidates_matches_the_oracle(B, orc):
+    """A dense cluster (particles with up to 112 candidates, 82 of them above 64): the lists, masks
+    and sums reach past the first 64 candidates in every pass -- the re-sort step and two steps
+    that filter the same lists -- and the state stays within the parity bound of the oracle."""
+    ic = cluster_ic(64, 3, 0.1, 0.65, u_scale=1e-3)
+    p = params(64, c0_min=0.05)
+    p["dt"] = stable_dt(p)
+    run = GpuRun(B, p, ic)
+    st = oracle_state(ic)
+    P = oracle_params(orc, p, "brute")
+    try:
+        for _ in range(3):
+            run.step(1)
+            st, _ = orc.step(P, st, 1)
+            errs = compare_state(run.state(), st, ic["x"], ic["y"])
+            assert all(e <= 1e-5 for e in errs.values()), errs
+        d = B.ann_get_diagnostics(run.ctx)
+        assert d["nbr_max"] > 64 and d["resorts"] == 1 and d["error_bits"] == 0, d
+    finally:
+        run.close()
+
+
+def test_cluster_beyond_the_list_capacity_is_reported(B):
+    """A cluster whose particles have up to ~165 candidates, beyond the 128 a list holds: the step
+    reports NBR_OVERFLOW (no fault, no silent truncation) and the context stays usable."""
+    ic = cluster_ic(64, 3, 0.12, 0.55)
+    ctx = B.ann_create(gpu_params(B, params(64), 64 * 64))
+    try:
+        B.ann_set_particles(ctx, ic["x"], ic["y"], ic["ux"], ic["uy"], ic["q11"], ic["q12"])
+        with pytest.raises(B.AnnError) as e:
+            B.ann_step(ctx, 1)
+        assert e.value.status == -5
+        assert B.ann_get_diagnostics(ctx)["error_bits"] & 4
+        lat = si.jittered_lattice(64, seed=3)
+        B.ann_set_particles(ctx, lat["x"], lat["y"], lat["ux"], lat["uy"], lat["q11"], lat["q12"])
         B.ann_step(ctx, 1)
     finally:
         B.ann_destroy(ctx)
