@@ -1153,7 +1153,7 @@ def long_run(steps: int, every: int, nx: int = 256):
            "steps": steps, "every": every, "runs": {}}
     for init in ("random_director", "perturbed_nematic"):
         res = longrun.run(LONG_RUN_MEMBERS, nx=nx, steps=steps, every=every, initial=init)
-        keep = ("step", "t", "vrms", "mean_q", "defect_density", "corr_zero", "slope")
+        keep = ("step", "t", "vrms", "mean_q", "defect_density", "corr_zero", "slope", "nbr_max")
         out["runs"][init] = {
             "seconds": res["seconds"], "summary": longrun.summary(res),
             "series": [{"zeta": m["zeta"], "K": m["K"], "failed": m["failed"],

@@ -46,7 +46,8 @@ def member_params(nx: int, zeta: float, K: float, eta: float = 0.03, dt: float =
 
 
 def snapshot(ctx, M: int, shells=(3, 20)):
-    """Statistics of the present state: t, rms velocity, kinetic energy, mean q, defect counts and
+    """Statistics of the present state: t, rms velocity, kinetic energy, mean q, the mean and largest
+    neighbour counts (particle disorder: 44 on the initial lattice), defect counts and
     density (per unit area of the unit box), the vorticity correlation's zero-crossing and 0.2-max
     lengths, and the spectrum's slope over the shells n in [shells[0], shells[1]] (w = 2 pi n)."""
     d = B.ann_get_diagnostics(ctx)
@@ -57,6 +58,7 @@ def snapshot(ctx, M: int, shells=(3, 20)):
     counts, _ = B.ann_defects(ctx, M)
     return {"step": int(d["step"]), "t": d["t"], "vrms": math.sqrt(2.0 * d["kinetic_energy"]),
             "kinetic_energy": d["kinetic_energy"], "max_speed": d["max_speed"], "mean_q": d["mean_q"],
+            "nbr_mean": d["nbr_mean"], "nbr_max": int(d["nbr_max"]),
             "defects_plus": int(counts[0]), "defects_minus": int(counts[1]),
             "defect_density": float(counts[0] + counts[1]), "corr_zero": l0, "corr_02": l02, "slope": slope,
             "spectrum": E.tolist()}
@@ -125,7 +127,7 @@ def run(members, nx: int = 256, steps: int = 20000, every: int = 500, eta: float
 def summary(result, tail: int = 10):
     """Per member: the mean of each statistic over the last `tail` snapshots (the developed state)."""
     out = []
-    keys = ("vrms", "mean_q", "defect_density", "corr_zero", "corr_02", "slope")
+    keys = ("vrms", "mean_q", "defect_density", "corr_zero", "corr_02", "slope", "nbr_mean", "nbr_max")
     for m in result["members"]:
         snaps = [s for s in m["snapshots"] if s["step"] > 0][-tail:]
         row = {"zeta": m["zeta"], "K": m["K"], "l_Q": m["l_Q"], "failed": m["failed"], "snapshots": len(snaps)}
