@@ -144,6 +144,7 @@ def test_ten_steps_64(B, orc):
     """The 64 x 64 set-up: random director, S = 1, 1e-3 noise, u = 0, dt = 1e-4, zeta = 0.05."""
     ic = si.jittered_lattice(64, seed=0)
     worst = _ten_steps(B, orc, 64, params(64), ic, "brute")
+    print("64 ten steps", {k: f"{v:.2e}" for k, v in worst.items()})
     bad = {k: e for k, e in worst.items() if not e <= TOL}
     assert not bad, worst
 
@@ -157,6 +158,7 @@ def test_ten_steps_256(B, orc, zeta):
     p = params(256, zeta=zeta)
     p["dt"] = stable_dt(p)
     worst = _ten_steps(B, orc, 256, p, ic, "cells")
+    print(f"256 zeta {zeta} ten steps", {k: f"{v:.2e}" for k, v in worst.items()})
     bad = {k: e for k, e in worst.items() if not e <= TOL}
     assert not bad, worst
 
