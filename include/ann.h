@@ -453,7 +453,8 @@ int ann_surrogate_set_scales(ann_surrogate *sg, double us, double ys_q, double y
  * positions; afterwards the context's next step re-sorts).  tend: host n x 8 FP32, component-major
  * (ax, ay, m11, m12, lapQ11, lapQ12, div u, vort u; component c of particle ID i at c n + i), or
  * NULL to take them from the context's last step, which must have run with ann_set_record(ctx, 1)
- * (STATE otherwise). */
+ * (STATE otherwise).  The network's graph holds up to 64 neighbours closer than 2h per particle
+ * (~21 on a lattice); a denser cluster returns NBR_OVERFLOW instead of dropping neighbours. */
 int ann_surrogate_load(ann_surrogate *sg, ann_ctx *ctx, const float *tend);
 
 /* Network outputs y of the loaded state: host n x 4 FP32, ID order (may be NULL). */
