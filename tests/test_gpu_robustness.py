@@ -109,6 +109,43 @@ def test_overfull_cell_is_reported_not_faulted(B):
         B.ann_destroy(ctx)
 
 
+def test_neighbour_bits_follow_pairs_crossing_the_cutoff(B, orc):
+    """Between re-sorts pass A rewrites each list entry's neighbour bit in place.  Uniform random
+    positions in a shear flow u = (2 sin 2 pi y, 0) (no displacement term, so nothing else moves the
+    particles): pairs cross 3h every step while no particle leaves half the skin, so the
+    neighbour counts change from step to step on the lists of the first step.  At every step they
+    equal the oracle's (FP64 definition, brute force) for one step from the same state."""
+    import math
+
+    nx = 64
+    p = params(nx, c0_min=0.05, apd=0)
+    p["dt"] = stable_dt(p)
+    ic = si.uniform_random(nx * nx, seed=29)
+    ic["ux"] = 2.0 * np.sin(2.0 * math.pi * ic["y"])
+    ic["uy"] = np.zeros(ic["n"])
+    run = GpuRun(B, p, ic)
+    P = oracle_params(orc, p, "brute")
+    prev, changed = None, 0
+    try:
+        run.step(1)
+        for _ in range(4):
+            g = run.state()
+            st = {"x": g["x"], "y": g["y"], "ux": g["ux"], "uy": g["uy"], "q11": g["q11"], "q12": g["q12"],
+                  "rho": 1.0 + g["drho"], "ax": g["ax"], "ay": g["ay"]}
+            _, rec = orc.step(P, st, 1, record=True)
+            run.step(1)
+            nn = run.field("NNBR")
+            assert np.array_equal(nn, rec["nnbr"])
+            if prev is not None:
+                changed += int((nn != prev).sum())
+            prev = nn
+        d = B.ann_get_diagnostics(run.ctx)
+    finally:
+        run.close()
+    assert d["resorts"] == 1, d   # steps 2 to 5 filtered the lists of the first
+    assert changed > 50, changed
+
+
 def test_dense_cluster_beyond_64_candidates_matches_the_oracle(B, orc):
     """A dense cluster (particles with up to 112 candidates, 82 of them above 64): the lists, masks
     and sums reach past the first 64 candidates in every pass -- the re-sort step and two steps
