@@ -379,7 +379,8 @@ def _state_ptrs(arrays: dict, names, required, what: str):
 def ann_get_state(ctx, n: int, out=None) -> dict:
     """The state fields X, Y (float64), UX, UY, Q11, Q12, DRHO and the last step's AX, AY (float32)
     in particle-ID order, in one call: new numpy arrays, or written into ``out`` (a dict of numpy
-    arrays, or of CUDA tensors, with some or all of those names)."""
+    arrays, or of CUDA tensors, with some or all of those names).  Numpy arrays in page-locked
+    memory (e.g. ``torch.empty(n).pin_memory().numpy()``) are written by the device directly."""
     if out is None:
         out = {f: np.empty(n, dtype=field_dtype(f)) for f in FULL_STATE}
     ptrs, dev, m = _state_ptrs(out, FULL_STATE, (), "out")
@@ -392,7 +393,7 @@ def ann_get_state(ctx, n: int, out=None) -> dict:
 def ann_update_state(ctx, state: dict) -> None:
     """Replace the present state, keeping the step count and the cell structure (see the header): a
     dict with the names of ann_get_state (DRHO, AX, AY optional), all numpy arrays or all CUDA
-    tensors, in particle-ID order."""
+    tensors, in particle-ID order.  Page-locked numpy arrays are read by the device directly."""
     ptrs, dev, _ = _state_ptrs(state, FULL_STATE, ("X", "Y", "UX", "UY", "Q11", "Q12"), "state")
     _check(lib().ann_update_state(ctx, *ptrs, 1 if dev else 0), ctx, "ann_update_state")
 
