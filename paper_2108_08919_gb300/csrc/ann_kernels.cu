@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(256, 8) k_predict(DevParams P, Bufs b)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool rs = resorting(b);
     float sp = 0.f;
+    int moved = 0;   // this particle left half the skin: the step re-sorts
     if (i < P.n) {
         // the committed state in, the predicted positions and velocities into the other set
         const StateSet in = state_in(b), out = state_out(b);
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(256, 8) k_predict(DevParams P, Bufs b)
             float4 xi = make_float4(sx_.x, sy_.x, sx_.y, sy_.y);
             float4 rf = b.xi_ref[i];
             float ddx = (xi.x - rf.x) + (xi.z - rf.z), ddy = (xi.y - rf.y) + (xi.w - rf.w);
-            if (ddx * ddx + ddy * ddy > P.skin_max2) *(volatile uint32_t *)b.rebuild = 1u;
+            moved = ddx * ddx + ddy * ddy > P.skin_max2;
             b.mx[i] = x;
             b.my[i] = y;
             b.xi[i] = xi;
@@ -233,7 +234,9 @@ __global__ void __launch_bounds__(256, 8) k_predict(DevParams P, Bufs b)
     }
     for (int o = 16; o > 0; o >>= 1) sp = fmaxf(sp, __shfl_xor_sync(FULL, sp, o));
     if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = sp;
-    __syncthreads();
+    // one flag store per block (a store from every particle that moved would queue on one address
+    // when many move at once, e.g. after ann_update_state)
+    if (__syncthreads_or(moved) && threadIdx.x == 0) *(volatile uint32_t *)b.rebuild = 1u;
     if (threadIdx.x < 32) {
         sp = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0.f;
         for (int o = 16; o > 0; o >>= 1) sp = fmaxf(sp, __shfl_xor_sync(FULL, sp, o));
