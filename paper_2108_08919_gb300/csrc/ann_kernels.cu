@@ -930,7 +930,13 @@ __global__ void BOUNDS_C k_pass_c(DevParams P, Bufs b)
         float e1x = ge1.x, e1y = ge1.y, e2x = ge2.x, e2y = ge2.y, e3x = ge3.x, e3y = ge3.y;
         float dhat = bi.y - P.beta * shep / swi;
         b.dhat[gi] = dhat;
-        b.p[gi] = pref * expm1f(P.gamma_eos * log1pf(dhat));
+        const float pg = pref * expm1f(P.gamma_eos * log1pf(dhat));
+        b.p[gi] = pg;
+        {   // p / rho_hat^2 for pass D's staging, by the same operations pass D used to form it
+            float rho = P.rho0 * (1.f + dhat);
+            float irho = 1.f / rho;
+            b.prr[gi] = pg * irho * irho;
+        }
         if (QNEW) {
             float q1x = g1x * B11 + g1y * B12, q1y = g1x * B12 + g1y * B22;
             float q2x = g2x * B11 + g2y * B12, q2y = g2x * B12 + g2y * B22;
@@ -976,11 +982,11 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
     const StateSet out = state_out(b);
     for (int t = threadIdx.x; t < T.H; t += PT) {
         SlotInfo s = slot_info(P, b, ts, T, t);
-        float rho = P.rho0 * (1.f + b.dhat[s.g]);
-        float irho = 1.f / rho;
-        float pr = b.p[s.g] * irho * irho;
         sp[t] = s.e;
         if (CONS) {
+            float rho = P.rho0 * (1.f + b.dhat[s.g]);
+            float irho = 1.f / rho;
+            float pr = b.p[s.g] * irho * irho;
             float q1 = P.qnew ? out.q11[s.g] : b.mq11[s.g];
             float q2 = P.qnew ? out.q12[s.g] : b.mq12[s.g];
             sb[t] = make_float4(pr, irho, b.mux[s.g], b.muy[s.g]);
@@ -991,7 +997,7 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
                 se[t] = make_float4(pe.x * ir2, pe.y * ir2, pe.z * ir2, 0.f);
             }
         } else {
-            sb[t] = make_float4(b.V[s.g], pr, b.mux[s.g], b.muy[s.g]);
+            sb[t] = make_float4(b.V[s.g], b.prr[s.g], b.mux[s.g], b.muy[s.g]);
         }
         sg[t] = s.g;
     }
