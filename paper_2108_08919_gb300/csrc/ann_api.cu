@@ -116,7 +116,7 @@ int64_t device_bytes(const ann_params &p)
                   + 3 * 4                     // key, rank, perm
                   + 4                         // neighbour counts (the neighbour bits sit in the lists)
                   + (MAXV / 2) * 4 + 4 + 16 + 4   // candidate lists, counts, split at re-sort, cell
-                  + 12 * 4                    // intermediates (with p / rho_hat^2 for pass D)
+                  + 11 * 4 + 16               // intermediates, pass D's staged record (V, p/rho^2, u)
                   + 10 * 4                    // recording
                   + 16 + 8                    // elastic stress and its divergence
                   + 8 + 1 + 4                 // image counts, colour, inverse order (diagnostics)
@@ -301,7 +301,7 @@ cudaError_t alloc_all(ann_ctx *c)
     A_(nnbr, n);
     A_(vnbr, n * (MAXV / 4)); A_(vcnt, n); A_(xi_ref, n); A_(mkey, n); A_(rebuild, 1); A_(resorts, 1);
     A_(sumW, n); A_(V, n); A_(B11, n); A_(B12, n); A_(B22, n); A_(kr, n); A_(dh, n); A_(dhat, n);
-    A_(p, n); A_(prr, n); A_(divx, n); A_(divy, n);
+    A_(p, n); A_(rd, n); A_(divx, n); A_(divy, n);
     A_(rec_gu, 4 * n); A_(rec_lap, 2 * n); A_(rec_apd, 2 * n); A_(rec_qrate, 2 * n);
     A_(pel, n); A_(delx, n); A_(dely, n); A_(img, n);
     A_(err, 1); A_(maxu, 1); A_(band, 1);

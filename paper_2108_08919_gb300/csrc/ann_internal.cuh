@@ -112,7 +112,7 @@ struct Bufs {
     uint32_t *rebuild;  // non-zero: this step re-sorts and rebuilds the candidate lists
     uint32_t *resorts;  // number of re-sort steps since the particles were loaded
     float *sumW, *V, *B11, *B12, *B22, *kr, *dh, *dhat, *p, *divx, *divy;
-    float *prr;   // p / rho_hat^2 (pass C), the pressure term pass D stages
+    float4 *rd;   // (V, p / rho_hat^2, ux, uy) per particle (pass C): the record pass D stages
     float *rec_gu, *rec_lap, *rec_apd, *rec_qrate;   // 4n, 2n, 2n, 2n (recording only)
     float4 *pel;        // elastic stress (11, 12, 22, -) of Eq. 12 (elastic_stress only)
     float *delx, *dely; // its corrected divergence (paper momentum only)

@@ -932,10 +932,10 @@ __global__ void BOUNDS_C k_pass_c(DevParams P, Bufs b)
         b.dhat[gi] = dhat;
         const float pg = pref * expm1f(P.gamma_eos * log1pf(dhat));
         b.p[gi] = pg;
-        {   // p / rho_hat^2 for pass D's staging, by the same operations pass D used to form it
+        {   // pass D's staged record (V, p / rho_hat^2, u): one 16-byte load per staged slot there
             float rho = P.rho0 * (1.f + dhat);
             float irho = 1.f / rho;
-            b.prr[gi] = pg * irho * irho;
+            b.rd[gi] = make_float4(bi.x, pg * irho * irho, b.mux[gi], b.muy[gi]);
         }
         if (QNEW) {
             float q1x = g1x * B11 + g1y * B12, q1y = g1x * B12 + g1y * B22;
@@ -997,7 +997,7 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
                 se[t] = make_float4(pe.x * ir2, pe.y * ir2, pe.z * ir2, 0.f);
             }
         } else {
-            sb[t] = make_float4(b.V[s.g], b.prr[s.g], b.mux[s.g], b.muy[s.g]);
+            sb[t] = b.rd[s.g];
         }
         sg[t] = s.g;
     }
