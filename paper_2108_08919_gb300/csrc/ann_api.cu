@@ -116,7 +116,8 @@ int64_t device_bytes(const ann_params &p)
                   + 3 * 4                     // key, rank, perm
                   + 4                         // neighbour counts (the neighbour bits sit in the lists)
                   + (MAXV / 2) * 4 + 4 + 16 + 4   // candidate lists, counts, split at re-sort, cell
-                  + 11 * 4 + 16               // intermediates, pass D's staged record (V, p/rho^2, u)
+                  + 4 * 4 + 3 * 16            // intermediates: sum W, V, delta_half, p; (B, k), (div Q, delta_hat,
+                                              // sum W) and pass D's staged record (V, p/rho^2, u) as float4
                   + 10 * 4                    // recording
                   + 16 + 8                    // elastic stress and its divergence
                   + 8 + 1 + 4                 // image counts, colour, inverse order (diagnostics)
@@ -300,8 +301,8 @@ cudaError_t alloc_all(ann_ctx *c)
     A_(cell_count, ncell + 1); A_(cell_start, ncell + 1); A_(key, n); A_(rank, n); A_(perm, n);
     A_(nnbr, n);
     A_(vnbr, n * (MAXV / 4)); A_(vcnt, n); A_(xi_ref, n); A_(mkey, n); A_(rebuild, 1); A_(resorts, 1);
-    A_(sumW, n); A_(V, n); A_(B11, n); A_(B12, n); A_(B22, n); A_(kr, n); A_(dh, n); A_(dhat, n);
-    A_(p, n); A_(rd, n); A_(divx, n); A_(divy, n);
+    A_(sumW, n); A_(V, n); A_(bk, n); A_(dh, n);
+    A_(p, n); A_(rd, n); A_(cq, n);
     A_(rec_gu, 4 * n); A_(rec_lap, 2 * n); A_(rec_apd, 2 * n); A_(rec_qrate, 2 * n);
     A_(pel, n); A_(delx, n); A_(dely, n); A_(img, n);
     A_(err, 1); A_(maxu, 1); A_(band, 1);
@@ -531,15 +532,13 @@ bool field_of(ann_ctx *c, int f, Field &out)
     case ANN_FIELD_AY: out = {b.say, 4, true, 1, 0}; return true;
     case ANN_FIELD_SUMW: out.ptr = b.sumW; return true;
     case ANN_FIELD_V: out.ptr = b.V; return true;
-    case ANN_FIELD_B11: out.ptr = b.B11; return true;
-    case ANN_FIELD_B12: out.ptr = b.B12; return true;
-    case ANN_FIELD_B22: out.ptr = b.B22; return true;
-    case ANN_FIELD_K: out.ptr = b.kr; return true;
+    case ANN_FIELD_B11: case ANN_FIELD_B12: case ANN_FIELD_B22: case ANN_FIELD_K:
+        out = {b.bk, 4, false, 4, f - ANN_FIELD_B11}; return true;
     case ANN_FIELD_DRHO_HALF: out.ptr = b.dh; return true;
-    case ANN_FIELD_DRHO_HAT: out.ptr = b.dhat; return true;
+    case ANN_FIELD_DRHO_HAT: out = {b.cq, 4, false, 4, 2}; return true;
     case ANN_FIELD_P: out.ptr = b.p; return true;
-    case ANN_FIELD_DIVQX: out.ptr = b.divx; return true;
-    case ANN_FIELD_DIVQY: out.ptr = b.divy; return true;
+    case ANN_FIELD_DIVQX: case ANN_FIELD_DIVQY:
+        out = {b.cq, 4, false, 4, f - ANN_FIELD_DIVQX}; return true;
     case ANN_FIELD_NNBR: out.ptr = b.nnbr; return true;
     case ANN_FIELD_GRADU_XX: case ANN_FIELD_GRADU_XY: case ANN_FIELD_GRADU_YX: case ANN_FIELD_GRADU_YY:
         out = {b.rec_gu, 4, false, 4, f - ANN_FIELD_GRADU_XX}; return true;

@@ -111,7 +111,9 @@ struct Bufs {
     int *vcnt;
     uint32_t *rebuild;  // non-zero: this step re-sorts and rebuilds the candidate lists
     uint32_t *resorts;  // number of re-sort steps since the particles were loaded
-    float *sumW, *V, *B11, *B12, *B22, *kr, *dh, *dhat, *p, *divx, *divy;
+    float *sumW, *V, *dh, *p;
+    float4 *bk;   // (B11, B12, B22, k) per particle (pass B): the correction tensor and continuity rate
+    float4 *cq;   // (div Q x, div Q y, delta_hat, sum W) per particle (pass C), read by pass D
     float4 *rd;   // (V, p / rho_hat^2, ux, uy) per particle (pass C): the record pass D stages
     float *rec_gu, *rec_lap, *rec_apd, *rec_qrate;   // 4n, 2n, 2n, 2n (recording only)
     float4 *pel;        // elastic stress (11, 12, 22, -) of Eq. 12 (elastic_stress only)

@@ -825,16 +825,13 @@ __global__ void BOUNDS_B k_pass_b(DevParams P, Bufs b)
             float p12 = 2.f * lam * q2 * QH - lam * (2.f * c * h2 + 2.f * h0 * q2);
             b.pel[gi] = make_float4(p11, p12, p22, 0.f);
         }
-        b.B11[gi] = B11;
-        b.B12[gi] = B12;
-        b.B22[gi] = B22;
-        b.kr[gi] = kr;
+        b.bk[gi] = make_float4(B11, B12, B22, kr);
         b.dh[gi] = di + P.half_dt * kr;
-        if (QOLD) {
+        if (QOLD) {   // div Q^n for pass D (pass C then leaves the divergence part of cq alone)
             float q1x = g1x * B11 + g1y * B12, q1y = g1x * B12 + g1y * B22;
             float q2x = g2x * B11 + g2y * B12, q2y = g2x * B12 + g2y * B22;
-            b.divx[gi] = q1x + q2y;
-            b.divy[gi] = q2x - q1y;
+            float2 *dq = reinterpret_cast<float2 *>(b.cq + gi);
+            *dq = make_float2(q1x + q2y, q2x - q1y);
         }
         if (P.record) {
             b.rec_gu[4 * gi + 0] = D00;
@@ -896,9 +893,10 @@ __global__ void BOUNDS_C k_pass_c(DevParams P, Bufs b)
         float swi = b.sumW[gi];   // loaded ahead of the neighbour loop
         float B11 = 0.f, B12 = 0.f, B22 = 0.f;
         if (QNEW || EL) {
-            B11 = b.B11[gi];
-            B12 = b.B12[gi];
-            B22 = b.B22[gi];
+            const float4 bb = b.bk[gi];
+            B11 = bb.x;
+            B12 = bb.y;
+            B22 = bb.z;
         }
         float4 ei = EL ? se[si] : make_float4(0.f, 0.f, 0.f, 0.f);
         // two-lane accumulators: corrected-gradient raw sums of q11, q12 and of Pi11, Pi12, Pi22
@@ -929,7 +927,6 @@ __global__ void BOUNDS_C k_pass_c(DevParams P, Bufs b)
         float g1x = gq1.x, g1y = gq1.y, g2x = gq2.x, g2y = gq2.y;
         float e1x = ge1.x, e1y = ge1.y, e2x = ge2.x, e2y = ge2.y, e3x = ge3.x, e3y = ge3.y;
         float dhat = bi.y - P.beta * shep / swi;
-        b.dhat[gi] = dhat;
         const float pg = pref * expm1f(P.gamma_eos * log1pf(dhat));
         b.p[gi] = pg;
         {   // pass D's staged record (V, p / rho_hat^2, u): one 16-byte load per staged slot there
@@ -940,8 +937,10 @@ __global__ void BOUNDS_C k_pass_c(DevParams P, Bufs b)
         if (QNEW) {
             float q1x = g1x * B11 + g1y * B12, q1y = g1x * B12 + g1y * B22;
             float q2x = g2x * B11 + g2y * B12, q2y = g2x * B12 + g2y * B22;
-            b.divx[gi] = q1x + q2y;
-            b.divy[gi] = q2x - q1y;
+            b.cq[gi] = make_float4(q1x + q2y, q2x - q1y, dhat, swi);
+        } else {   // div Q^n came from pass B
+            float2 *hs = reinterpret_cast<float2 *>(b.cq + gi) + 1;
+            *hs = make_float2(dhat, swi);
         }
         if (EL) {   // div Pi = (d_x Pi11 + d_y Pi12, d_x Pi12 + d_y Pi22), corrected gradients
             float p11x = e1x * B11 + e1y * B12;
@@ -984,7 +983,7 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
         SlotInfo s = slot_info(P, b, ts, T, t);
         sp[t] = s.e;
         if (CONS) {
-            float rho = P.rho0 * (1.f + b.dhat[s.g]);
+            float rho = P.rho0 * (1.f + reinterpret_cast<const float *>(b.cq + s.g)[2]);
             float irho = 1.f / rho;
             float pr = b.p[s.g] * irho * irho;
             float q1 = P.qnew ? out.q11[s.g] : b.mq11[s.g];
@@ -1012,7 +1011,7 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
         int c = b.nnbr[gi];
         // the epilogue's other per-particle inputs are loaded after the neighbour loop: held across
         // it they would take 11 registers (and spill), while other warps hide their latency there
-        float dhat = b.dhat[gi];
+        float dhat = reinterpret_cast<const float *>(b.cq + gi)[2];
         float rho = P.rho0 * (1.f + dhat);
         // paper mode: pressure and viscous sums share grad_i W, so they accumulate as one vector
         //   w = sum_j V_j F [ -rho_i (p_i/rho_i^2 + p_j/rho_j^2) + kv (u_ij . d) / r^2 ] d,
@@ -1060,14 +1059,15 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
                 sd = fma2(d, bc(rinv2 * kp.rinv), sd);
             }
         });
-        float kri = b.kr[gi], swi = b.sumW[gi];
+        const float4 bb = b.bk[gi], cc = b.cq[gi];
+        float kri = bb.w, swi = cc.w;
         float B11 = 0.f, B12 = 0.f, B22 = 0.f, dvx = 0.f, dvy = 0.f;
         if (!CONS) {
-            B11 = b.B11[gi];
-            B12 = b.B12[gi];
-            B22 = b.B22[gi];
-            dvx = b.divx[gi];
-            dvy = b.divy[gi];
+            B11 = bb.x;
+            B12 = bb.y;
+            B22 = bb.z;
+            dvx = cc.x;
+            dvy = cc.y;
         }
         const double mxi = b.mx[gi], myi = b.my[gi];
         float elx = 0.f, ely = 0.f;
@@ -1387,7 +1387,8 @@ __global__ void __launch_bounds__(256) k_diag_partial(DevParams P, Bufs b, doubl
         v[6] += nn;
         v[7] = fmin(v[7], nn);
         v[8] = fmax(v[8], nn);
-        double b11 = b.B11[g], b12 = b.B12[g], b22 = b.B22[g];
+        const float4 bb = b.bk[g];
+        double b11 = bb.x, b12 = bb.y, b22 = bb.z;
         double detb = b11 * b22 - b12 * b12;
         v[9] = fmin(v[9], detb != 0.0 ? (double)(1.0f / (float)detb) : 1e300);
     }
