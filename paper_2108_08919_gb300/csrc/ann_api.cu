@@ -297,7 +297,7 @@ cudaError_t alloc_all(ann_ctx *c)
 #define A_(p, cnt) if ((e = dalloc(c, b.p, cnt))) return e
     A_(sx, n); A_(sy, n); A_(sux, n); A_(suy, n); A_(sq11, n); A_(sq12, n); A_(sdr, n); A_(sax, n);
     A_(say, n); A_(sid, n); A_(sxi, n);
-    A_(mx, n); A_(my, n); A_(mux, n); A_(muy, n); A_(mq11, n); A_(mq12, n); A_(mdr, n); A_(xi, n); A_(mid, n);
+    A_(mx, n); A_(my, n); A_(mu4, n); A_(mdr, n); A_(xi, n); A_(mid, n);
     A_(cell_count, ncell + 1); A_(cell_start, ncell + 1); A_(key, n); A_(rank, n); A_(perm, n);
     A_(nnbr, n);
     A_(vnbr, n * (MAXV / 4)); A_(vcnt, n); A_(xi_ref, n); A_(mkey, n); A_(rebuild, 1); A_(resorts, 1);
@@ -1356,8 +1356,8 @@ int diag_source(ann_ctx *c, DiagSrc &src)
         if (st) return st;
         c->m_current = true;
     }
-    if (c->s_sorted) src = DiagSrc{b.sx, b.sy, b.sux, b.suy, b.sq11, b.sq12};
-    else src = DiagSrc{b.mx, b.my, b.mux, b.muy, b.mq11, b.mq12};
+    if (c->s_sorted) src = DiagSrc{b.sx, b.sy, b.sux, b.suy, b.sq11, b.sq12, nullptr};
+    else src = DiagSrc{b.mx, b.my, nullptr, nullptr, nullptr, nullptr, b.mu4};
     return ANN_OK;
 }
 

@@ -30,7 +30,7 @@ __global__ void k_grid_prep(DevParams P, Bufs b, DiagSrc src, float2 *off, float
     if (oy > 0.5 * P.L) oy -= P.L;
     else if (oy < -0.5 * P.L) oy += P.L;
     off[s] = make_float2((float)ox, (float)oy);
-    fld[s] = make_float4(src.ux[s], src.uy[s], src.q11[s], src.q12[s]);
+    fld[s] = src.u4 ? src.u4[s] : make_float4(src.ux[s], src.uy[s], src.q11[s], src.q12[s]);
 }
 
 constexpr int GRID_TILE = 16;   // a block covers 16 x 16 nodes

@@ -100,7 +100,8 @@ struct Bufs {
     const double *origin;   // origin[c] = c * cell, c < n_c (cell-corner coordinates)
     int *sid;
     double *mx, *my;
-    float *mux, *muy, *mq11, *mq12, *mdr;
+    float4 *mu4;   // (ux, uy, q11, q12) of the evaluation copy, one record per particle
+    float *mdr;
     float4 *xi;         // cell-local offset split as (hi_x, hi_y, lo_x, lo_y), hi on the q grid
     float4 *xi_ref;     // split offset at the last re-sort (candidate lists were built from it)
     uint32_t *mkey;     // cell each particle was assigned to at the last re-sort
@@ -187,7 +188,8 @@ int diag_blocks(int n);
 // last re-sort (mkey, cell_start).
 struct DiagSrc {
     const double *x, *y;
-    const float *ux, *uy, *q11, *q12;
+    const float *ux, *uy, *q11, *q12;   // separate arrays, or
+    const float4 *u4;                   // (ux, uy, q11, q12) records when not null
 };
 // grid: 5 x M x M doubles (ux, uy, q11, q12, Shepard weight sum), [field][iy][ix]
 cudaError_t enqueue_grid(const DevParams &P, const Bufs &b, DiagSrc src, int M, float2 *off, float4 *fld,

@@ -224,10 +224,7 @@ __global__ void __launch_bounds__(256, 8) k_predict(DevParams P, Bufs b)
             b.mx[i] = x;
             b.my[i] = y;
             b.xi[i] = xi;
-            b.mux[i] = ux;
-            b.muy[i] = uy;
-            b.mq11[i] = in.q11[i];
-            b.mq12[i] = in.q12[i];
+            b.mu4[i] = make_float4(ux, uy, in.q11[i], in.q12[i]);
             b.mdr[i] = in.dr[i];
             b.mid[i] = in.id[i];
         }
@@ -401,10 +398,7 @@ __global__ void __launch_bounds__(256) k_cell_order(DevParams P, Bufs b)
         b.my[g] = out.y[old];
         b.xi[g] = b.sxi[old];
         b.mkey[g] = (uint32_t)c;
-        b.mux[g] = out.ux[old];
-        b.muy[g] = out.uy[old];
-        b.mq11[g] = in.q11[old];
-        b.mq12[g] = in.q12[old];
+        b.mu4[g] = make_float4(out.ux[old], out.uy[old], in.q11[old], in.q12[old]);
         b.mdr[g] = in.dr[old];
         b.mid[g] = in.id[old];
     }
@@ -739,7 +733,7 @@ __global__ void BOUNDS_B k_pass_b(DevParams P, Bufs b)
     for (int t = threadIdx.x; t < T.H; t += PT) {
         SlotInfo s = slot_info(P, b, ts, T, t);
         sp[t] = s.e;
-        sb[t] = make_float4(b.mux[s.g], b.muy[s.g], b.mq11[s.g], b.mq12[s.g]);
+        sb[t] = b.mu4[s.g];
         sv[t] = b.V[s.g];
         sg[t] = s.g;
     }
@@ -932,7 +926,8 @@ __global__ void BOUNDS_C k_pass_c(DevParams P, Bufs b)
         {   // pass D's staged record (V, p / rho_hat^2, u): one 16-byte load per staged slot there
             float rho = P.rho0 * (1.f + dhat);
             float irho = 1.f / rho;
-            b.rd[gi] = make_float4(bi.x, pg * irho * irho, b.mux[gi], b.muy[gi]);
+            const float2 u = *reinterpret_cast<const float2 *>(b.mu4 + gi);
+            b.rd[gi] = make_float4(bi.x, pg * irho * irho, u.x, u.y);
         }
         if (QNEW) {
             float q1x = g1x * B11 + g1y * B12, q1y = g1x * B12 + g1y * B22;
@@ -986,9 +981,10 @@ __global__ void BOUNDS_D k_pass_d(DevParams P, Bufs b)
             float rho = P.rho0 * (1.f + reinterpret_cast<const float *>(b.cq + s.g)[2]);
             float irho = 1.f / rho;
             float pr = b.p[s.g] * irho * irho;
-            float q1 = P.qnew ? out.q11[s.g] : b.mq11[s.g];
-            float q2 = P.qnew ? out.q12[s.g] : b.mq12[s.g];
-            sb[t] = make_float4(pr, irho, b.mux[s.g], b.muy[s.g]);
+            const float4 m4 = b.mu4[s.g];
+            float q1 = P.qnew ? out.q11[s.g] : m4.z;
+            float q2 = P.qnew ? out.q12[s.g] : m4.w;
+            sb[t] = make_float4(pr, irho, m4.x, m4.y);
             sc[t] = make_float2(q1 * irho * irho, q2 * irho * irho);
             if (EL) {
                 float4 pe = b.pel[s.g];
@@ -1246,7 +1242,7 @@ __global__ void __launch_bounds__(PT) k_export_graph(DevParams P, Bufs b, GraphO
         SlotInfo s = slot_info(P, b, ts, T, t);
         pos[t] = s.e;
         sg[t] = s.g;
-        su[t] = make_float4(b.mux[s.g], b.muy[s.g], b.mq11[s.g], b.mq12[s.g]);
+        su[t] = b.mu4[s.g];
         const int id = b.mid[s.g];
         sa[t] = make_float2(o.tend_id[id], o.tend_id[(size_t)P.n + id]);
     }
