@@ -56,13 +56,13 @@ FLOPS_PER_PAIR = {"pass_a": 27.0, "pass_a_resort": 24 + 15.5, "pass_b": 70.0, "p
 #   pass_a        split position, candidate lists in; count, sum W, V out (a list word is
 #                 rewritten only when a neighbour bit changes: a few per step)              124
 #   pass_b        split position, V, u, Q, delta, lists in; Q^{n+1}, (B, k) as one record,
-#                 delta_half out                                                           164
-#   pass_c        split position, V, delta_half, Q^{n+1}, sum W, (B, k), u, lists in; p,
+#                 pass C's staged record (V, delta_half, Q^{n+1}) out                      176
+#   pass_c        split position, (V, delta_half, Q^{n+1}), sum W, (B, k), u, lists in; p,
 #                 (div Q, delta_hat, sum W) and pass D's staged record (V, p/rho^2, u) out 192
 #   pass_d        everything the momentum, corrector and APD read (V, p, u as one staged
 #                 record; (B, k) and (div Q, delta_hat, sum W) as two); the new state out 216
 BYTES_PER_PARTICLE = {"predict": 148, "cell_scan": 0.5, "cell_scatter": 16, "cell_order": 116,
-                      "pass_a_resort": 140, "pass_a": 124, "pass_b": 164, "pass_c": 192,
+                      "pass_a_resort": 140, "pass_a": 124, "pass_b": 176, "pass_c": 192,
                       "pass_d": 216}
 RESORT_BRANCH = ("cell_keys", "cell_scan", "cell_scatter", "cell_order", "pass_a_resort")
 

@@ -301,7 +301,7 @@ cudaError_t alloc_all(ann_ctx *c)
     A_(cell_count, ncell + 1); A_(cell_start, ncell + 1); A_(key, n); A_(rank, n); A_(perm, n);
     A_(nnbr, n);
     A_(vnbr, n * (MAXV / 4)); A_(vcnt, n); A_(xi_ref, n); A_(mkey, n); A_(rebuild, 1); A_(resorts, 1);
-    A_(sumW, n); A_(V, n); A_(bk, n); A_(dh, n);
+    A_(sumW, n); A_(V, n); A_(bk, n); A_(cr, n);
     A_(p, n); A_(rd, n); A_(cq, n);
     A_(rec_gu, 4 * n); A_(rec_lap, 2 * n); A_(rec_apd, 2 * n); A_(rec_qrate, 2 * n);
     A_(pel, n); A_(delx, n); A_(dely, n); A_(img, n);
@@ -534,7 +534,7 @@ bool field_of(ann_ctx *c, int f, Field &out)
     case ANN_FIELD_V: out.ptr = b.V; return true;
     case ANN_FIELD_B11: case ANN_FIELD_B12: case ANN_FIELD_B22: case ANN_FIELD_K:
         out = {b.bk, 4, false, 4, f - ANN_FIELD_B11}; return true;
-    case ANN_FIELD_DRHO_HALF: out.ptr = b.dh; return true;
+    case ANN_FIELD_DRHO_HALF: out = {b.cr, 4, false, 4, 1}; return true;
     case ANN_FIELD_DRHO_HAT: out = {b.cq, 4, false, 4, 2}; return true;
     case ANN_FIELD_P: out.ptr = b.p; return true;
     case ANN_FIELD_DIVQX: case ANN_FIELD_DIVQY:

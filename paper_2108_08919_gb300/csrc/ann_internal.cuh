@@ -112,7 +112,8 @@ struct Bufs {
     int *vcnt;
     uint32_t *rebuild;  // non-zero: this step re-sorts and rebuilds the candidate lists
     uint32_t *resorts;  // number of re-sort steps since the particles were loaded
-    float *sumW, *V, *dh, *p;
+    float *sumW, *V, *p;
+    float4 *cr;   // (V, delta_half, Q11^{n+1}, Q12^{n+1}) per particle (pass B): the record pass C stages
     float4 *bk;   // (B11, B12, B22, k) per particle (pass B): the correction tensor and continuity rate
     float4 *cq;   // (div Q x, div Q y, delta_hat, sum W) per particle (pass C), read by pass D
     float4 *rd;   // (V, p / rho_hat^2, ux, uy) per particle (pass C): the record pass D stages

@@ -801,10 +801,11 @@ __global__ void BOUNDS_B k_pass_b(DevParams P, Bufs b)
                    P.Gamma * (hb * q1 + P.K * lap1);
         float m2 = lam * divu * q2 + 2.f * cl * E12 + 2.f * om * q1 - 2.f * lam * QE * q2 +
                    P.Gamma * (hb * q2 + P.K * lap2);
+        const float q1n = q1 + P.dt * m1, q2n = q2 + P.dt * m2;
         {
             const StateSet out = state_out(b);   // Q^{n+1} into the step's output set
-            out.q11[gi] = q1 + P.dt * m1;
-            out.q12[gi] = q2 + P.dt * m2;
+            out.q11[gi] = q1n;
+            out.q12[gi] = q2n;
         }
         if (P.elastic) {
             // Elastic stress of Eq. (12) without -p I: with H = H_tl + h0 I (h0 from the B term),
@@ -820,7 +821,7 @@ __global__ void BOUNDS_B k_pass_b(DevParams P, Bufs b)
             b.pel[gi] = make_float4(p11, p12, p22, 0.f);
         }
         b.bk[gi] = make_float4(B11, B12, B22, kr);
-        b.dh[gi] = di + P.half_dt * kr;
+        b.cr[gi] = make_float4(sv[si], di + P.half_dt * kr, q1n, q2n);   // pass C's staged record
         if (QOLD) {   // div Q^n for pass D (pass C then leaves the divergence part of cq alone)
             float q1x = g1x * B11 + g1y * B12, q1y = g1x * B12 + g1y * B22;
             float q2x = g2x * B11 + g2y * B12, q2y = g2x * B12 + g2y * B22;
@@ -866,8 +867,7 @@ __global__ void BOUNDS_C k_pass_c(DevParams P, Bufs b)
     for (int t = threadIdx.x; t < T.H; t += PT) {
         SlotInfo s = slot_info(P, b, ts, T, t);
         sp[t] = s.e;
-        sb[t] = QNEW ? make_float4(b.V[s.g], b.dh[s.g], out.q11[s.g], out.q12[s.g])
-                     : make_float4(b.V[s.g], b.dh[s.g], 0.f, 0.f);
+        sb[t] = b.cr[s.g];   // (V, delta_half, Q^{n+1}); pass C reads Q^{n+1} only with QNEW
         if (EL) se[t] = b.pel[s.g];
         sg[t] = s.g;
     }
