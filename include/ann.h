@@ -121,7 +121,8 @@ typedef struct ann_diag {
     double t;                    /* simulated time */
     int64_t step;                /* completed steps */
     double momentum[2];          /* sum_i m_i u_i; m_i = rho_i V_i (paper mode) or rho0 L^2/n */
-    double kinetic_energy;       /* 1/2 <|u|^2>, the spatial mean of the paper's Eq. 31 */
+    double kinetic_energy;       /* 1/2 <|u|^2> over the particles (by Parseval, the sum of the
+                                    spectrum E(w) of Eq. 31 over all shells, up to gridding) */
     double max_speed;            /* max |u| */
     double c0;                   /* sound speed of the last step */
     double mass;                 /* sum_i m_i */
