@@ -153,6 +153,58 @@ def developed_flow_bench(B, stream, steps: int = 6000, u_max: float = 0.1, seed:
             "particle_steps_per_s": NX * NX * steps / (ms * 1e-3)}
 
 
+def size_sweep_bench(B, stream, sizes=(256, 512, 1024, 2048, 4096, 8192), work=3e9, warmup=5):
+    """Throughput of the headline set-up (from rest, h = 1.3 dx, stable dt) against the lattice side:
+    each size timed with CUDA events over about `work` particle-steps (20 to 3,000 steps).  Sides
+    above 1024 tile the unit box with copies of a jittered 1024^2 lattice shrunk to fit, which keeps
+    the particle spacing and neighbour statistics of the smaller sizes."""
+    import numpy as np
+    import torch
+
+    import sph_inputs as si
+
+    out = []
+    for nx in sizes:
+        base = min(nx, 1024)
+        ic = si.jittered_lattice(base, seed=3)
+        R = nx // base
+        if R * base != nx:
+            raise ValueError(f"lattice side {nx} is not a multiple of {base}")
+        t = np.arange(R * R)
+        sx, sy = ((t % R) / R)[:, None], ((t // R) / R)[:, None]
+        x = si.wrap_positions((ic["x"][None, :] / R + sx).ravel(), 1.0)
+        y = si.wrap_positions((ic["y"][None, :] / R + sy).ravel(), 1.0)
+        fields = [np.tile(ic[k], R * R) for k in ("ux", "uy", "q11", "q12", "rho")]
+        n = nx * nx
+        steps = int(min(3000, max(20, work // n)))
+        p = make_params(B, nx)
+        ctx = B.ann_create(p)
+        try:
+            B.ann_set_stream(ctx, stream)
+            B.ann_set_particles(ctx, x, y, *fields)
+            del x, y, fields
+            B.ann_step(ctx, warmup)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                B.ann_step(ctx, steps)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            d = B.ann_get_diagnostics(ctx)
+            g = B.ann_grid_info(p)
+        finally:
+            B.ann_destroy(ctx)
+        out.append({"nx": nx, "particles": n, "tiles": g.tiles_per_side ** 2, "steps": steps,
+                    "ms_per_step": ms / steps, "particle_steps_per_s": n * steps / (ms * 1e-3),
+                    "device_gb": g.device_bytes / 1e9, "error_bits": d["error_bits"]})
+        print(f"size sweep {nx}^2: {out[-1]['particle_steps_per_s']:.3e} particle-steps/s, "
+              f"{out[-1]['ms_per_step']:.4f} ms per step", file=sys.stderr, flush=True)
+    return {"sizes": out, "set-up": "from rest, h = 1.3 dx, zeta 0.08, K 0.02, stable dt; sides above 1024 "
+                                    "are copies of a 1024^2 jittered lattice", "clock": "CUDA events"}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -1127,6 +1179,8 @@ def run_ours(args):
         line["three_d"] = three_d_bench(B, nx=args.nx3)
     if ws == 1 and not args.no_sweep:
         line["sweep"] = sweep_bench(B)
+    if ws == 1 and args.size_sweep:
+        line["size_sweep"] = size_sweep_bench(B, stream, tuple(int(v) for v in args.size_sweep.split(",")))
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(NX)
         ms, cores = oracle_grid_ms(NX, DIAG_M)
@@ -1181,6 +1235,8 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the activity / elastic-constant sweep")
     ap.add_argument("--no-developed-flow", action="store_true", help="skip the moving-state re-sort timing")
     ap.add_argument("--nx3", type=int, default=NX3, help="side of the 3D variant's cubic lattice")
+    ap.add_argument("--size-sweep", default="", metavar="SIDES",
+                    help="also time the step at these lattice sides (comma-separated, e.g. 256,1024,8192)")
     ap.add_argument("--surrogate-cycles", type=int, default=0,
                     help="only run this many surrogate cycles (recorded step + jump) at the headline size, "
                          "untrained weights, and print their wall time (for launch lists and profiles)")

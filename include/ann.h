@@ -287,8 +287,9 @@ int ann_get_diagnostics(ann_ctx *ctx, ann_diag *out);
 /* Neighbour lists of the current positions (no time advance): builds the cell sort and pass A at
  * the present configuration and writes them as CSR in particle IDs, each row ascending: rowptr has
  * n+1 entries (host), cols `cap` entries (host).  With cols == NULL only rowptr is written, so a
- * caller can size cols from rowptr[n].  Errors: INVALID_ARG (cap < rowptr[n]), STATE, the step's
- * device errors, CUDA, OOM. */
+ * caller can size cols from rowptr[n].  The export takes a device buffer of 4 ANN_MAX_NEIGHBORS
+ * bytes per particle (from the context's allocator, if it has one) for the duration of the call.
+ * Errors: INVALID_ARG (cap < rowptr[n]), STATE, the step's device errors, CUDA, OOM. */
 int ann_get_neighbors(ann_ctx *ctx, int64_t *rowptr, int32_t *cols, int64_t cap);
 
 /* Write / read the full state (positions, velocities, Q, density, a, internal particle order, t,

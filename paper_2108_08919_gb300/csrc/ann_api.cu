@@ -123,7 +123,7 @@ int64_t device_bytes(const ann_params &p)
                   + 8 + 1 + 4                 // image counts, colour, inverse order (diagnostics)
                   + 2 * 8 + 7 * 4 + 4         // the second state set (a step writes it, rollback keeps the first)
                   + 2;                        // crossing log (n/8 entries of 16 bytes)
-    int64_t tmp = std::max<int64_t>(7 * 8, MAXN * 4) * n;
+    int64_t tmp = 7 * 8 * n;                  // staging of state and field transfers
     return per * n + tmp + 2 * 4 * (ncell + 1) + 4096;
 }
 
@@ -323,7 +323,7 @@ cudaError_t alloc_all(ann_ctx *c)
     }
     b.origin = origin;
     unsigned char *tmp = nullptr;
-    if ((e = dalloc(c, tmp, std::max<size_t>(7 * 8, MAXN * 4) * n))) return e;
+    if ((e = dalloc(c, tmp, (size_t)(7 * 8) * n))) return e;
     c->tmp = tmp;
     if ((e = dalloc(c, c->colors, n))) return e;
     if ((e = dalloc(c, c->inv, n))) return e;
@@ -866,7 +866,7 @@ int ann_set_state(ann_ctx *c, int64_t n, const double *x, const double *y, const
     if (e) return cuda_fail(c, e, "ann_set_state");
     const void *dev[7] = {x, y, ux, uy, q11, q12, drho};
     if (!is_device) {
-        unsigned char *t = static_cast<unsigned char *>(c->tmp);   // 36 of its >= 56 bytes per particle
+        unsigned char *t = static_cast<unsigned char *>(c->tmp);   // 36 of its 56 bytes per particle
         size_t off = 0;
         for (int k = 0; k < 7; k++) {
             const size_t bytes = (k < 2 ? 8 : 4) * (size_t)n;
@@ -930,7 +930,7 @@ int ann_update_state(ann_ctx *c, const double *x, const double *y, const float *
         return device_status(c);
     }
     if (!is_device) {
-        unsigned char *t = static_cast<unsigned char *>(c->tmp);   // 44 of its >= 56 bytes per particle
+        unsigned char *t = static_cast<unsigned char *>(c->tmp);   // 44 of its 56 bytes per particle
         size_t off = 0;
         for (int k = 0; k < 9 && !e; k++) {
             const size_t bytes = (k < 2 ? 8 : 4) * n;
@@ -1069,7 +1069,7 @@ int ann_get_state(ann_ctx *c, double *x, double *y, float *ux, float *uy, float 
     const size_t n = (size_t)c->P.n;
     const Bufs &b = c->b;
     // each field is un-permuted into its own part of the staging buffer (44 bytes per particle of
-    // the >= 56 it holds), so all copies are in flight before the one synchronisation
+    // the 56 it holds), so all copies are in flight before the one synchronisation
     unsigned char *tmp = static_cast<unsigned char *>(c->tmp);
     struct Part { const void *src; void *dst; int es; } parts[9] = {
         {b.sx, x, 8}, {b.sy, y, 8}, {b.sux, ux, 4}, {b.suy, uy, 4}, {b.sq11, q11, 4}, {b.sq12, q12, 4}, {b.sdr, drho, 4},
@@ -1169,16 +1169,26 @@ int ann_get_neighbors(ann_ctx *c, int64_t *rowptr, int32_t *cols, int64_t cap)
     for (int i = 0; i < n; i++) rowptr[i + 1] = rowptr[i] + cnt[i + 1];
     if (!cols) return ANN_OK;
     if (cap < rowptr[n]) return fail(c, ANN_ERR_INVALID_ARG, "cols capacity below rowptr[n]");
-    int *dcols = static_cast<int *>(c->tmp);
-    e = enqueue_export_nbrs(c->P, c->b, dcols, c->stream);
+    // the export (MAXN entries per particle, column-major) takes a device buffer of its own for the
+    // duration of the call, so a context does not hold 4 MAXN bytes per particle between calls
     std::vector<int> hc;
     try {
         hc.resize((size_t)MAXN * n);
     } catch (...) {
         return fail(c, ANN_ERR_OOM, "host allocation");
     }
-    if (!e) e = cudaMemcpyAsync(hc.data(), dcols, sizeof(int) * (size_t)MAXN * n, cudaMemcpyDeviceToHost, c->stream);
-    if (!e) e = cudaStreamSynchronize(c->stream);
+    const size_t dbytes = sizeof(int) * (size_t)MAXN * n;
+    void *dv = nullptr;
+    if (dev_alloc(c, &dv, dbytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, ANN_ERR_OOM, "ann_get_neighbors: device buffer of the export");
+    }
+    int *dcols = static_cast<int *>(dv);
+    e = enqueue_export_nbrs(c->P, c->b, dcols, c->stream);
+    if (!e) e = cudaMemcpyAsync(hc.data(), dcols, dbytes, cudaMemcpyDeviceToHost, c->stream);
+    const cudaError_t es = cudaStreamSynchronize(c->stream);
+    if (!e) e = es;
+    dev_free(c, dv, dbytes);
     if (e) return cuda_fail(c, e, "ann_get_neighbors export");
     for (int g = 0; g < n; g++) {
         int i = mid[g];

@@ -1,0 +1,116 @@
+"""The largest problem of the GPU tests: 8192 x 8192 = 67,108,864 particles, every particle checked.
+
+The unit box holds 8 x 8 copies of a moving 1024 x 1024 pattern (random velocities 2e-2, density
+noise, c0 >= 0.2, so pressure, viscous and APD terms act) shrunk to side 1/8, with h = 1.3 / 8192.
+Every sum of the step runs over neighbours within 3h and the box is periodic, so the big box evolves
+as the pattern does on its own box of side 1/8 (the oracle-side pin of this premise is
+`test_periodic_copies_evolve_as_the_pattern`): the FP64 oracle steps the pattern once and each of
+the 64 copies is compared with it, with the bounds of the full-size moving-state parity cases.
+
+At this size the candidate lists span 32 x 2^26 words (word indices up to 2^31 - 1), the context
+holds ~46 GB of device memory and the host state transfers move ~3 GB per call.
+"""
+import numpy as np
+import pytest
+
+from _sph import (GpuRun, oracle_params, oracle_state, params, periodic_copies, random_velocity_ic, relerr_group,
+                  stable_dt)
+
+pytestmark = pytest.mark.gpu
+
+R = 8        # copies per side
+NX0 = 1024   # the pattern's lattice
+TOL = 1e-5
+FLOOR_FACTOR = 3.0   # the acceleration's bound over its FP32 storage floor, as in the moving-state cases
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_08919_gb300 import binding, build
+
+    build.build()
+    return binding
+
+
+def _round32(st):
+    return {k: (v if k in ("x", "y") else np.asarray(v, np.float32).astype(np.float64)) for k, v in st.items()}
+
+
+def _sums(gpu_rows, ref):
+    """For the copies (each GPU field reshaped to (copies, n0)) against the pattern's fields, the
+    components of a vector taken together: ||g - o||_2, ||o||_2 over all copies, and the largest
+    per-particle |g_i - o_i| and |o_i|."""
+    num = den = 0.0
+    diff2 = scale2 = None
+    for g, o in zip(gpu_rows, ref):
+        d = g - o[None, :]
+        num += float(np.einsum("ij,ij->", d, d))
+        den += g.shape[0] * float(o @ o)
+        diff2 = d * d if diff2 is None else diff2 + d * d
+        scale2 = o * o if scale2 is None else scale2 + o * o
+    return np.sqrt(num), np.sqrt(den), float(np.sqrt(diff2.max())), float(np.sqrt(scale2.max()))
+
+
+def _errors(gpu_rows, ref, noise_norm=0.0, noise_elem=0.0):
+    """Normwise and element-wise relative errors, each net of an absolute noise allowance."""
+    dn, on, de, oe = _sums(gpu_rows, ref)
+    norm = max(0.0, dn - noise_norm) / on if on > 0 else dn
+    elem = max(0.0, de - noise_elem) / oe if oe > 0 else de
+    return float(norm), float(elem)
+
+
+def test_largest_size_every_particle_against_the_oracle(B, orc):
+    ic0 = random_velocity_ic(NX0, 13, u_scale=2e-2, rho_scale=2e-4)
+    big, pat = periodic_copies(ic0, R)
+    n0, n = pat["n"], big["n"]
+    p0 = params(NX0, L=1.0 / R, h=1.3 / (R * NX0), c0_min=0.2)   # the pattern's box; h = 1.3 dx
+    p0["dt"] = stable_dt(p0)
+    p = dict(p0, L=1.0)
+    assert p["h"] == pytest.approx(1.3 / (R * NX0), rel=1e-15)
+    bx, by = big["x"].reshape(R * R, n0), big["y"].reshape(R * R, n0)
+    run = GpuRun(B, p, big)
+    del big
+    st = oracle_state(pat)
+    P = oracle_params(orc, p0, "cells")
+    worst = {}
+    try:
+        for _ in range(2):
+            run.step(1)
+            st32, _ = orc.step(P, _round32(st), 1)
+            st, rec = orc.step(P, st, 1, record=True)
+            rows = lambda name: run.field(name).reshape(R * R, n0)
+            errs = {
+                "u": _errors([rows("UX"), rows("UY")], [st["ux"], st["uy"]]),
+                "Q": _errors([rows("Q11"), rows("Q12")], [st["q11"], st["q12"]]),
+                "drho": _errors([rows("DRHO")], [st["rho"] - 1.0]),
+                "a": _errors([rows("AX"), rows("AY")], [st["ax"], st["ay"]]),
+            }
+            # displacements from the start (minimum image), net of one FP64 unit of L per
+            # coordinate, the resolution of a stored position
+            dg = [(rows("X") - bx + 0.5) % 1.0 - 0.5, (rows("Y") - by + 0.5) % 1.0 - 0.5]
+            half = 0.5 / R
+            do = [(st["x"] - pat["x"] + half) % (2 * half) - half, (st["y"] - pat["y"] + half) % (2 * half) - half]
+            errs["disp"] = _errors(dg, do, np.sqrt(2.0 * n) * np.spacing(1.0), np.sqrt(2.0) * np.spacing(1.0))
+            del dg
+            floor_a = relerr_group([st32["ax"], st32["ay"]], [st["ax"], st["ay"]])
+            for k, (nm, em) in errs.items():
+                w = worst.setdefault(k, [0.0, 0.0])
+                w[0], w[1] = max(w[0], nm), max(w[1], em)
+            worst.setdefault("a_floor", [0.0])[0] = max(worst.get("a_floor", [0.0])[0], floor_a)
+        nnbr = run.field("NNBR").astype(np.int64).reshape(R * R, n0)
+        assert np.array_equal(nnbr, np.broadcast_to(rec["nnbr"], nnbr.shape))
+        d = B.ann_get_diagnostics(run.ctx)
+        assert d["error_bits"] == 0
+        assert (d["nbr_min"], d["nbr_max"]) == (int(rec["nnbr"].min()), int(rec["nnbr"].max()))
+    finally:
+        run.close()
+    print(f"{n} particles:", {k: [f"{e:.2e}" for e in v] for k, v in worst.items()})
+    bad = {k: v for k, v in worst.items() if k not in ("a", "a_floor") and not max(v) <= TOL}
+    lim_a = max(TOL, FLOOR_FACTOR * worst["a_floor"][0])
+    if not worst["a"][0] <= lim_a:
+        bad["a"] = (worst["a"][0], lim_a)
+    assert not bad, (bad, worst)

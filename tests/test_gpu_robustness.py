@@ -434,8 +434,9 @@ def test_dt_check_mode_reports_cfl_violations(B):
 
 def test_context_on_the_torch_caching_allocator(B):
     """Every device buffer of a context made by ann_create_with_allocator comes from the given
-    allocator (here PyTorch's caching allocator) and goes back to it on destroy; the steps and the
-    flow diagnostics are bit-identical to a context on cudaMalloc."""
+    allocator (here PyTorch's caching allocator) and goes back to it on destroy (the neighbour
+    export's transient buffer at the end of its call); the steps and the flow diagnostics are
+    bit-identical to a context on cudaMalloc."""
     import torch
 
     ic = random_velocity_ic(96, 5)
@@ -456,6 +457,14 @@ def test_context_on_the_torch_caching_allocator(B):
             assert np.array_equal(B.ann_get_field(ctx, f, ref.n), B.ann_get_field(ref.ctx, f, ref.n)), f
         assert np.array_equal(B.ann_energy_spectrum(ctx, 64), B.ann_energy_spectrum(ref.ctx, 64))
         assert torch.cuda.memory_allocated() - base > held   # the spectrum's scratch
+        # the neighbour export's buffer (4 ANN_MAX_NEIGHBORS bytes per particle) comes from the
+        # allocator for the call only
+        before = torch.cuda.memory_allocated()
+        torch.cuda.reset_peak_memory_stats()
+        rp, cols = B.ann_get_neighbors(ctx, ref.n)
+        assert torch.cuda.max_memory_allocated() - before >= 4 * 128 * ref.n
+        assert torch.cuda.memory_allocated() == before
+        assert rp[-1] == cols.size and np.all(np.diff(rp) >= 0)
     finally:
         B.ann_destroy(ctx)
         ref.close()

@@ -10,6 +10,8 @@ and invariants.
 * Trace of the unprojected m: 2 lambda (1 - 2c) Q:E + 2 c lambda div u + Gamma B tr(Q^2)/3.
 * Pair-antisymmetric momentum mode: total momentum is conserved to 1e-12 over 100 steps.
 * Translation invariance of the whole step; ghost-layer and cell-grid searches give the same step.
+* Periodic copies: R x R copies of a pattern on the unit box evolve as the pattern on a box of
+  side 1/R (the premise of the GPU's largest-size parity case).
 """
 import math
 
@@ -152,6 +154,34 @@ def test_translation_invariance(orc):
     dxs = (b["x"] - a["x"] - 0.37 + 0.5) % 1.0 - 0.5
     dys = (b["y"] - a["y"] - 0.81 + 0.5) % 1.0 - 0.5
     assert np.abs(dxs).max() < 1e-12 and np.abs(dys).max() < 1e-12
+
+
+def test_periodic_copies_evolve_as_the_pattern(orc):
+    """2 x 2 copies of a moving 32 x 32 pattern, shrunk to a box of side 1/2 and tiling the unit
+    box (same h): the big box's three steps are the pattern's own three steps on the box of side
+    1/2, copied.  Every sum of the step is local and the box periodic, so only rounding differs."""
+    from _sph import periodic_copies
+
+    ic0 = si.jittered_lattice(32, seed=8)
+    r = si.uniform53(208, 2 * ic0["n"]).reshape(2, ic0["n"]) - 0.5
+    ic0["ux"], ic0["uy"] = 2e-2 * r[0], 2e-2 * r[1]
+    big, pat = periodic_copies(ic0, 2)
+    h = 1.3 / 64
+    kw = dict(h=h, c0_min=0.2, dt=2e-5, eta=0.1, nbr_mode="cells")
+    a, ra = orc.step(orc.make_params(L=0.5, **kw), {k: pat[k] for k in ("x", "y", "ux", "uy", "q11", "q12", "rho")},
+                     3, record=True)
+    b, rb = orc.step(orc.make_params(L=1.0, **kw), {k: big[k] for k in ("x", "y", "ux", "uy", "q11", "q12", "rho")},
+                     3, record=True)
+    n0 = ic0["n"]
+    assert np.array_equal(rb["nnbr"].reshape(4, n0), np.broadcast_to(ra["nnbr"], (4, n0)))
+    for k in ("ux", "uy", "q11", "q12", "rho", "ax", "ay"):
+        got = b[k].reshape(4, n0)
+        assert np.abs(got - a[k]).max() <= 1e-11 * np.abs(a[k]).max(), k
+    for k in ("x", "y"):
+        dg = ((b[k] - big[k] + 0.5) % 1.0 - 0.5).reshape(4, n0)
+        do = (a[k] - pat[k] + 0.25) % 0.5 - 0.25
+        assert np.abs(dg - do).max() <= 4e-16, k
+        assert np.abs(do).max() > 1e-8   # the particles did move
 
 
 def test_search_modes_give_identical_steps(orc):
