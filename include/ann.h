@@ -89,7 +89,7 @@ extern "C" {
  *   Pi_el = 2 lambda M (Q:H) - lambda (H M + M H), M = Q + c_shift I, to the momentum through the
  *   corrected divergence (paper mode) or the pair-antisymmetric form (conservative mode).  The
  *   paper neglects it (text under Eq. 13); default 0.
- * Valid ranges (ann_validate_params): n >= 1, L > 0, 0 < h, 3h <= L/3 (at least three cells across
+ * Valid ranges (ann_validate_params): 1 <= n <= 2^29, L > 0, 0 < h, 3h <= L/3 (at least three cells across
  * the box), dt > 0, rho0 > 0, eta >= 0, Gamma >= 0, gamma_eos > 0, 0 <= beta <= 1, c0_min >= 0, and
  * at most ANN_MAX_NEIGHBORS expected neighbours (pi (3h)^2 n / L^2 <= 0.85 ANN_MAX_NEIGHBORS).
  */

@@ -130,7 +130,9 @@ int64_t device_bytes(const ann_params &p)
 int validate(const ann_params *p, std::string &why)
 {
     if (!p) { why = "null parameters"; return ANN_ERR_INVALID_ARG; }
-    if (p->n < 1 || p->n > (int64_t)1 << 30) { why = "n must be in [1, 2^30]"; return ANN_ERR_INVALID_ARG; }
+    // 2^29 keeps every per-particle index of the kernels (up to 4 n for the recorded gradient) in
+    // int32; at ~663 bytes per particle that is 356 GB, beyond one GPU's memory anyway
+    if (p->n < 1 || p->n > (int64_t)1 << 29) { why = "n must be in [1, 2^29]"; return ANN_ERR_INVALID_ARG; }
     if (!finite_pos(p->L) || !finite_pos(p->h) || !finite_pos(p->dt) || !finite_pos(p->rho0)) {
         why = "L, h, dt and rho0 must be finite and positive";
         return ANN_ERR_INVALID_ARG;

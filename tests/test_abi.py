@@ -91,6 +91,13 @@ def test_validation_rejects(B, field, value):
     assert B.ann_validate_params(p) == -1
 
 
+def test_particle_count_limit(B):
+    """n up to 2^29 (every per-particle index of the kernels stays in int32); one more is refused."""
+    for n, status in ((1 << 29, 0), ((1 << 29) + 1, -1)):
+        p = B.ann_default_params(n=n, h=1.3 / math.sqrt(n))
+        assert B.ann_validate_params(p) == status, n
+
+
 def test_validation_rejects_crowded_support(B):
     p = B.ann_default_params()
     p.h = 2.0 / 64   # pi (6 dx)^2 = 113 expected neighbours > list capacity
