@@ -153,11 +153,13 @@ def developed_flow_bench(B, stream, steps: int = 6000, u_max: float = 0.1, seed:
             "particle_steps_per_s": NX * NX * steps / (ms * 1e-3)}
 
 
-def size_sweep_bench(B, stream, sizes=(256, 512, 1024, 2048, 4096, 8192), work=3e9, warmup=5):
+def size_sweep_bench(B, stream, sizes=(256, 512, 1024, 2048, 4096, 8192), work=3e9, warmup=5, peak_tf=None):
     """Throughput of the headline set-up (from rest, h = 1.3 dx, stable dt) against the lattice side:
-    each size timed with CUDA events over about `work` particle-steps (20 to 3,000 steps).  Sides
-    above 1024 tile the unit box with copies of a jittered 1024^2 lattice shrunk to fit, which keeps
-    the particle spacing and neighbour statistics of the smaller sizes."""
+    each size timed with CUDA events over about `work` particle-steps (20 to 3,000 steps), then the
+    per-kernel device times of the profile loop over a tenth of those steps (at least 5), with pass
+    D's FP32 rate against `peak_tf`.  Sides above 1024 tile the unit box with copies of a jittered
+    1024^2 lattice shrunk to fit, which keeps the particle spacing and neighbour statistics of the
+    smaller sizes."""
     import numpy as np
     import torch
 
@@ -194,11 +196,18 @@ def size_sweep_bench(B, stream, sizes=(256, 512, 1024, 2048, 4096, 8192), work=3
             ms = e0.elapsed_time(e1)
             d = B.ann_get_diagnostics(ctx)
             g = B.ann_grid_info(p)
+            psteps = max(5, steps // 10)
+            kprof = B.ann_step_profile(ctx, psteps)
         finally:
             B.ann_destroy(ctx)
-        out.append({"nx": nx, "particles": n, "tiles": g.tiles_per_side ** 2, "steps": steps,
-                    "ms_per_step": ms / steps, "particle_steps_per_s": n * steps / (ms * 1e-3),
-                    "device_gb": g.device_bytes / 1e9, "error_bits": d["error_bits"]})
+        kus = {k: 1e3 * v / psteps for k, v in kprof.items() if v > 0}
+        row = {"nx": nx, "particles": n, "tiles": g.tiles_per_side ** 2, "steps": steps,
+               "ms_per_step": ms / steps, "particle_steps_per_s": n * steps / (ms * 1e-3),
+               "device_gb": g.device_bytes / 1e9, "error_bits": d["error_bits"], "kernel_us": kus}
+        if peak_tf and kus.get("pass_d"):
+            tf = FLOPS_PER_PAIR["pass_d"] * d["nbr_mean"] * n / (kus["pass_d"] * 1e-6) / 1e12
+            row["pass_d_tflops"], row["pass_d_frac"] = tf, tf / peak_tf
+        out.append(row)
         print(f"size sweep {nx}^2: {out[-1]['particle_steps_per_s']:.3e} particle-steps/s, "
               f"{out[-1]['ms_per_step']:.4f} ms per step", file=sys.stderr, flush=True)
     return {"sizes": out, "set-up": "from rest, h = 1.3 dx, zeta 0.08, K 0.02, stable dt; sides above 1024 "
@@ -1180,7 +1189,8 @@ def run_ours(args):
     if ws == 1 and not args.no_sweep:
         line["sweep"] = sweep_bench(B)
     if ws == 1 and args.size_sweep:
-        line["size_sweep"] = size_sweep_bench(B, stream, tuple(int(v) for v in args.size_sweep.split(",")))
+        line["size_sweep"] = size_sweep_bench(B, stream, tuple(int(v) for v in args.size_sweep.split(",")),
+                                              peak_tf=peak_tf)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(NX)
         ms, cores = oracle_grid_ms(NX, DIAG_M)
