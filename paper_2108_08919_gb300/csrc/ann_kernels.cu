@@ -532,9 +532,11 @@ __global__ void __launch_bounds__(PT) k_pass_a_resort(DevParams P, Bufs b)
 // Occupancy hints of the pair passes (minimum resident blocks of PT threads per SM; 0 leaves the
 // register budget to the compiler) and the list-word prefetch distance of each (1 to 3 words of
 // four candidates).
-// The defaults are the measured best on GB300 at 1M particles: the register caps they imply
-// (32, 48, 40, 48) raise the resident warps to what the staged shared memory allows, which hides
-// the latency of the list and gather loads better than the instruction savings of more registers.
+// The defaults are the measured best on GB300 at 1M and 16M particles: the register caps they
+// imply (32, 48, 48, 48; pass C takes 46 and runs without spills) keep the resident warps
+// near what the staged shared memory allows, which hides the latency of the list and gather loads
+// better than the instruction savings of more registers (pass D at 4 blocks per SM, 64 registers
+// and no spills, is 8 % slower than at 5).
 #ifndef ANN_MINB_A
 #define ANN_MINB_A 8
 #endif
@@ -542,7 +544,7 @@ __global__ void __launch_bounds__(PT) k_pass_a_resort(DevParams P, Bufs b)
 #define ANN_MINB_B 5
 #endif
 #ifndef ANN_MINB_C
-#define ANN_MINB_C 6
+#define ANN_MINB_C 5
 #endif
 #ifndef ANN_MINB_D
 #define ANN_MINB_D 5
