@@ -160,7 +160,6 @@ def size_sweep_bench(B, stream, sizes=(256, 512, 1024, 2048, 4096, 8192), work=3
     D's FP32 rate against `peak_tf`.  Sides above 1024 tile the unit box with copies of a jittered
     1024^2 lattice shrunk to fit, which keeps the particle spacing and neighbour statistics of the
     smaller sizes."""
-    import numpy as np
     import torch
 
     import sph_inputs as si
@@ -168,15 +167,13 @@ def size_sweep_bench(B, stream, sizes=(256, 512, 1024, 2048, 4096, 8192), work=3
     out = []
     for nx in sizes:
         base = min(nx, 1024)
-        ic = si.jittered_lattice(base, seed=3)
         R = nx // base
         if R * base != nx:
             raise ValueError(f"lattice side {nx} is not a multiple of {base}")
-        t = np.arange(R * R)
-        sx, sy = ((t % R) / R)[:, None], ((t // R) / R)[:, None]
-        x = si.wrap_positions((ic["x"][None, :] / R + sx).ravel(), 1.0)
-        y = si.wrap_positions((ic["y"][None, :] / R + sy).ravel(), 1.0)
-        fields = [np.tile(ic[k], R * R) for k in ("ux", "uy", "q11", "q12", "rho")]
+        big, _ = si.periodic_copies(si.jittered_lattice(base, seed=3), R)
+        x, y = big["x"], big["y"]
+        fields = [big[k] for k in ("ux", "uy", "q11", "q12", "rho")]
+        del big
         n = nx * nx
         steps = int(min(3000, max(20, work // n)))
         p = make_params(B, nx)

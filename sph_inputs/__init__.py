@@ -19,6 +19,8 @@ zero initial velocity and a slightly perturbed nematic orientation):
   ``Q12 = q sin(2 theta) + g12`` (2D: Q = 2q(nn - I/2), §2).  Velocity is zero, density is rho0.
 * ``uniform_random``: ``n`` positions uniform in the box (irregular cell occupancy, ragged sizes).
 * ``hex_lattice``: a triangular lattice patch (used by operator pins that need isotropic moments).
+* ``periodic_copies``: R x R copies of a 2D input shrunk to side L / R, tiling the box of side L
+  (large boxes with the spacing and neighbourhoods of a small one).
 * ``jittered_lattice3``: the 3D variant, an ``nx^3`` cubic lattice (ID ``ix + nx (iy + nx iz)``),
   eight uniforms per particle in ID order: jitter ``jx, jy, jz``, a director uniform on the sphere
   (``cos(polar)``, azimuth) for a uniaxial ``Q = s0 (d d - I/3)``, and optional velocities.
@@ -37,6 +39,7 @@ __all__ = [
     "uniform_random",
     "hex_lattice",
     "wrap_positions",
+    "periodic_copies",
 ]
 
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -188,3 +191,28 @@ def hex_lattice(spacing: float, *, L: float = 1.0, origin=(0.0, 0.0)) -> dict:
     p = np.array(pts, dtype=np.float64)
     n = p.shape[0]
     return {"n": n, "x": p[:, 0].copy(), "y": p[:, 1].copy(), "id": np.arange(n, dtype=np.int32)}
+
+
+def periodic_copies(ic0: dict, R: int, L: float = 1.0) -> tuple[dict, dict]:
+    """R x R copies of the 2D input ``ic0`` (positions in ``[0, L)``) shrunk to a box of side
+    ``L / R``, tiling the box of side ``L``: copy ``t = ty R + tx`` holds particle ``t n0 + i`` at the
+    shrunk position of particle ``i`` shifted by ``(tx, ty) L / R``; the other per-particle arrays
+    (``ux, uy, q11, q12, rho`` where present) are repeated.  Returns ``(big, pattern)``: the big
+    box's input and the pattern on its own box of side ``L / R``.  A power-of-two ``R`` keeps the
+    shrunk positions exact."""
+    n0 = len(ic0["x"])
+    L0 = L / R
+    x0 = np.asarray(ic0["x"], dtype=np.float64) / R
+    y0 = np.asarray(ic0["y"], dtype=np.float64) / R
+    t = np.arange(R * R)
+    sx = ((t % R) * L0)[:, None]
+    sy = ((t // R) * L0)[:, None]
+    big = {"n": R * R * n0,
+           "x": wrap_positions((x0[None, :] + sx).ravel(), L),
+           "y": wrap_positions((y0[None, :] + sy).ravel(), L)}
+    pattern = {"n": n0, "x": x0, "y": y0}
+    for k in ("ux", "uy", "q11", "q12", "rho"):
+        if k in ic0:
+            big[k] = np.tile(np.asarray(ic0[k], dtype=np.float64), R * R)
+            pattern[k] = np.asarray(ic0[k], dtype=np.float64)
+    return big, pattern

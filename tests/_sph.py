@@ -196,25 +196,7 @@ def cluster_ic(nx, seed, radius, factor, u_scale=1e-3):
 
 
 def periodic_copies(ic0, R, L=1.0):
-    """R x R copies of the pattern ic0 (positions in [0, L)) shrunk to a box of side L / R, tiling
-    the box of side L: copy t = ty R + tx holds particle t n0 + i at the shrunk position of particle
-    i shifted by (tx, ty) L / R.  Returns (big, pattern): the big box's input and the pattern on its
-    own box of side L / R.  The method is local and the box periodic, so with the same h the big
-    box evolves as R x R copies of the pattern (c0 takes the largest speed, which the copies share).
-    R a power of two keeps the shrunk positions exact."""
-    n0 = len(ic0["x"])
-    L0 = L / R
-    x0 = ic0["x"] / R
-    y0 = ic0["y"] / R
-    t = np.arange(R * R)
-    sx = ((t % R) * L0)[:, None]
-    sy = ((t // R) * L0)[:, None]
-    big = {"n": R * R * n0,
-           "x": si.wrap_positions((x0[None, :] + sx).ravel(), L),
-           "y": si.wrap_positions((y0[None, :] + sy).ravel(), L)}
-    pattern = {"n": n0, "x": x0, "y": y0}
-    for k in ("ux", "uy", "q11", "q12", "rho"):
-        if k in ic0:
-            big[k] = np.tile(ic0[k], R * R)
-            pattern[k] = ic0[k]
-    return big, pattern
+    """R x R shrunk copies of ic0 tiling the box (`sph_inputs.periodic_copies`).  The method is
+    local and the box periodic, so with the same h the big box evolves as R x R copies of the
+    pattern on its own box of side L / R (c0 takes the largest speed, which the copies share)."""
+    return si.periodic_copies(ic0, R, L)

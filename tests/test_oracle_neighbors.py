@@ -120,3 +120,33 @@ def test_strict_cutoff(orc):
     x[1] = np.nextafter(0.5, 0.0)  # one ulp closer: inside
     rp, _ = orc.neighbors(x, y, 1.0, h, "brute")
     assert rp[1] - rp[0] == 1
+
+
+
+def test_periodic_copies_tile_the_box():
+    """sph_inputs.periodic_copies: n = R^2 n0 particles in [0, L); copy t holds the pattern shrunk
+    by R and shifted by (t mod R, t div R) L / R, exactly for R a power of two; the other arrays are
+    repeated; every particle of every copy has the nearest-neighbour distance of its original in
+    the pattern's own periodic box (the copies meet without overlap or gap)."""
+    ic0 = si.jittered_lattice(8, seed=4, jitter=0.3)
+    ic0["ux"] = si.uniform53(40, ic0["n"]) - 0.5
+    R, n0 = 4, ic0["n"]
+    big, pat = si.periodic_copies(ic0, R)
+    assert big["n"] == R * R * n0 == len(big["x"]) == len(big["q11"])
+    assert np.all((big["x"] >= 0) & (big["x"] < 1) & (big["y"] >= 0) & (big["y"] < 1))
+    assert np.array_equal(pat["x"], ic0["x"] / R) and np.array_equal(pat["ux"], ic0["ux"])
+    t = np.arange(R * R)
+    assert np.array_equal(big["x"].reshape(R * R, n0), pat["x"][None, :] + ((t % R) / R)[:, None])
+    assert np.array_equal(big["y"].reshape(R * R, n0), pat["y"][None, :] + ((t // R) / R)[:, None])
+    assert np.array_equal(big["ux"].reshape(R * R, n0), np.broadcast_to(ic0["ux"], (R * R, n0)))
+
+    def nearest(x, y, L):
+        d = np.stack([x[:, None] - x[None, :], y[:, None] - y[None, :]], axis=-1)
+        d = (d + 0.5 * L) % L - 0.5 * L
+        r = np.sqrt((d * d).sum(-1))
+        np.fill_diagonal(r, np.inf)
+        return r.min(axis=1)
+
+    nb = nearest(big["x"], big["y"], 1.0).reshape(R * R, n0)
+    npat = nearest(pat["x"], pat["y"], 1.0 / R)
+    assert np.allclose(nb, np.broadcast_to(npat, nb.shape), rtol=0, atol=1e-15)
