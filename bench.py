@@ -177,7 +177,11 @@ def size_sweep_bench(B, stream, sizes=(256, 512, 1024, 2048, 4096, 8192), work=3
         n = nx * nx
         steps = int(min(3000, max(20, work // n)))
         p = make_params(B, nx)
-        ctx = B.ann_create(p)
+        try:
+            ctx = B.ann_create(p)
+        except B.AnnError as e:   # e.g. a box larger than the device memory: recorded, not fatal
+            out.append({"nx": nx, "particles": n, "error": str(e)})
+            continue
         try:
             B.ann_set_stream(ctx, stream)
             B.ann_set_particles(ctx, x, y, *fields)
@@ -205,8 +209,8 @@ def size_sweep_bench(B, stream, sizes=(256, 512, 1024, 2048, 4096, 8192), work=3
             tf = FLOPS_PER_PAIR["pass_d"] * d["nbr_mean"] * n / (kus["pass_d"] * 1e-6) / 1e12
             row["pass_d_tflops"], row["pass_d_frac"] = tf, tf / peak_tf
         out.append(row)
-        print(f"size sweep {nx}^2: {out[-1]['particle_steps_per_s']:.3e} particle-steps/s, "
-              f"{out[-1]['ms_per_step']:.4f} ms per step", file=sys.stderr, flush=True)
+        print(f"size sweep {nx}^2: {row['particle_steps_per_s']:.3e} particle-steps/s, "
+              f"{row['ms_per_step']:.4f} ms per step", file=sys.stderr, flush=True)
     return {"sizes": out, "set-up": "from rest, h = 1.3 dx, zeta 0.08, K 0.02, stable dt; sides above 1024 "
                                     "are copies of a 1024^2 jittered lattice", "clock": "CUDA events"}
 
