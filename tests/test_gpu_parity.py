@@ -8,7 +8,8 @@
 * Moving states (random and smooth velocities, c0 > 0, so pressure, viscous and APD terms all act)
   at the full tilings: 10 steps at 256 x 256 and at 1024 x 1024, every state field within
   1e-5 both normwise and element-wise (the largest per-particle error over the field's largest
-  per-particle value).
+  per-particle value); the momentum variants (conservative form, elastic stress, Q^n, no APD)
+  from a moving state at 256 x 256, five steps.
 """
 import numpy as np
 import pytest
@@ -267,6 +268,25 @@ def test_ten_steps_1024_moving(B, orc, kind):
     p["dt"] = stable_dt(p)
     norm, elem, floor = _parity_steps(B, orc, p, ic, 10)
     print(f"1024 {kind} normwise", {k: f"{v:.2e}" for k, v in norm.items()},
+          "element-wise", {k: f"{v:.2e}" for k, v in elem.items()}, "a floor", floor)
+    bad = _check_moving(norm, elem, floor)
+    assert not bad, (bad, norm, elem, floor)
+
+
+@pytest.mark.parametrize("variant", ["conservative", "q_old", "elastic", "elastic_conservative", "no_apd"])
+def test_variants_256_moving(B, orc, variant):
+    """The momentum variants over the full 256 x 256 tiling from a moving state (random velocities
+    2e-2, density noise, c0 >= 0.2): five steps, every particle, with the bounds of the moving-state
+    cases (state fields 1e-5 normwise and element-wise, the acceleration 1e-5 or 3 x its FP32
+    storage floor)."""
+    kw = {"conservative": dict(conservative=1), "q_old": dict(q_new_in_momentum=0), "no_apd": dict(apd=0),
+          "elastic": dict(elastic=1, A=0.3, B=0.2, C=0.5),
+          "elastic_conservative": dict(elastic=1, conservative=1, A=0.3, B=0.2, C=0.5)}[variant]
+    ic = _moving_ic("random_u", 256)
+    p = params(256, c0_min=0.2, **kw)
+    p["dt"] = stable_dt(p)
+    norm, elem, floor = _parity_steps(B, orc, p, ic, 5)
+    print(f"256 {variant} normwise", {k: f"{v:.2e}" for k, v in norm.items()},
           "element-wise", {k: f"{v:.2e}" for k, v in elem.items()}, "a floor", floor)
     bad = _check_moving(norm, elem, floor)
     assert not bad, (bad, norm, elem, floor)
